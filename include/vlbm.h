@@ -1,0 +1,167 @@
+/*
+ * vlbm.h -- C ABI of the GB300 vielbein lattice Boltzmann library (libvlbm.so).
+ *
+ * The library advances the discrete Boltzmann equation on the unit sphere of
+ * Ambrus, Busuioc, Gabbana et al., arXiv 2504.15574, Sec. 3 (Eq. Lf):
+ *
+ *   d f_k/dt = L[f]_k = - flux-form advection in theta and phi  (Sec. 3.5, Eq. discrete_advection_sphere)
+ *                       - geometric force via K^H, Ktilde^H       (Sec. 3.3, Eqs. df, kernels)
+ *                       - (f_k - f^eq_k) / tau                    (Sec. 3.2, App. A.2 Eq. feq_Q=4)
+ *
+ * with the D2Q16 Gauss-Hermite velocity set (App. A.2, Tab. velocity_set_Q=4),
+ * WENO-5 fluxes (Eqs. fluxes_W5, WENO5_delta, WENO5_sigma), periodic phi and
+ * pole boundary conditions (Sec. 3.6, Eqs. bcs_phi, bcs_theta) and SSP-RK3
+ * time stepping (Sec. 3.7).  Every step runs in CUDA kernels for sm_103a; there
+ * is no CPU fallback: without a usable GPU every call that needs one returns
+ * VLBM_ERR_CUDA.
+ *
+ * Conventions shared by every entry point:
+ *   - Grid: n_theta rows x n_phi columns, cell-centred (Eq. discrete_coord_sphere):
+ *     theta_s = pi (s - 1/2) / n_theta, phi_q = 2 pi (q - 1/2) / n_phi.
+ *   - Host moment arrays are row-major [n_theta][n_phi] doubles; element
+ *     (s-1)*n_phi + (q-1) is cell (s, q).  Velocities are vielbein (orthonormal
+ *     frame) components u^theta-hat, u^phi-hat; rho = n (particle mass 1), T0 = 1.
+ *   - Population arrays are [16][n_theta][n_phi] doubles, population
+ *     k = 4 a + b with v_theta = v[a], v_phi = v[b] and v ascending
+ *     (v[0] = -sqrt(3+sqrt6) < v[1] < v[2] < v[3] = sqrt(3+sqrt6)).
+ *   - Ownership: the caller owns every host buffer and may reuse it as soon as
+ *     the call returns (the library copies, it keeps no host pointer).  The
+ *     library owns its device memory and the handle.
+ *   - Threading: a handle is used by one host thread at a time.  Its kernels
+ *     run on the stream given in vlbm_options (NULL: a stream the handle owns).
+ *   - Errors: every int-returning call returns VLBM_OK or a negative code;
+ *     vlbm_last_error() gives a message.  A NULL handle or buffer is VLBM_ERR_ARG.
+ */
+#ifndef VLBM_H
+#define VLBM_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define VLBM_API __attribute__((visibility("default")))
+#else
+#define VLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define VLBM_OK               0
+#define VLBM_ERR_ARG         -1  /* invalid argument (size, pointer, parameter) */
+#define VLBM_ERR_UNSUPPORTED -2  /* valid request this build does not implement */
+#define VLBM_ERR_CUDA        -3  /* CUDA error, including no device and out of memory */
+#define VLBM_ERR_NONFINITE   -4  /* the non-finite guard found a NaN/Inf population */
+#define VLBM_ERR_TIMEOUT     -5  /* a bounded device-side wait gave up */
+
+/* Velocity sets (App. A): the enum value is the quadrature order Q. */
+#define VLBM_D2Q9  3             /* reserved: returns VLBM_ERR_UNSUPPORTED */
+#define VLBM_D2Q16 4
+
+/* Storage / arithmetic precision of the populations. */
+#define VLBM_FP64 0              /* f in FP64, same operation order as the FP64 oracle */
+#define VLBM_FP32 1              /* delta f = f - w_k rho_ref in FP32, FP64 tables */
+
+typedef struct vlbm vlbm_t;
+
+typedef struct vlbm_options {
+    int precision;      /* VLBM_FP64 (default) or VLBM_FP32 */
+    double weno_eps;    /* regulariser of the WENO weights, wt_i = delta_i/(sigma_i+eps)^2; default 1e-6 */
+    double radius;      /* sphere radius R; default 1 */
+    int polar_filter;   /* 1: block-average rings near the poles after every stage (not in the
+                           paper; lets dt follow the theta spacing); default 0 */
+    int guard;          /* 1: vlbm_step checks every population for NaN/Inf once per call; default 1 */
+    void *stream;       /* cudaStream_t to run on, or NULL for a stream the handle creates */
+    double rho_ref;     /* VLBM_FP32 only: reference density of the deviation storage;
+                           <= 0 means the area-weighted mean of the initial rho; default 0 */
+} vlbm_options;
+
+/* Diagnostics in FP64 (not in the paper).  Area element R^2 sin(theta) dtheta dphi. */
+typedef struct vlbm_diag {
+    double time;        /* simulated time t = steps * dt */
+    long long steps;    /* RK3 steps taken since the last init/set */
+    double mass;        /* sum rho dA */
+    double momentum[3]; /* Cartesian sum rho (u^theta e_theta + u^phi e_phi) dA */
+    double energy;      /* sum_k f_k |v_k|^2 / 2 dA (reported; the isothermal BGK does not conserve it) */
+    double pole_flux;   /* sum over steps of dt * RK-weighted mass flux through both poles;
+                           mass - mass0 - pole_flux vanishes to round-off (FP64 path) */
+    double mass0;       /* mass at the last init/set */
+    int nonfinite;      /* 1 if any population is NaN/Inf */
+} vlbm_diag;
+
+/* Fills *opt with the defaults listed above.  NULL-safe. */
+VLBM_API void vlbm_default_options(vlbm_options *opt);
+
+/* Creates a solver on an n_theta x n_phi grid.
+ *   velocity_set: VLBM_D2Q16 (VLBM_D2Q9 -> VLBM_ERR_UNSUPPORTED).
+ *   n_theta >= 6 (three WENO ghost rows per pole), n_phi even or 1,
+ *   n_theta <= 65536, n_phi <= 65536; tau > 0 (BGK relaxation time, Sec. 3.2);
+ *   dt > 0 (the caller chooses it; see vlbm_max_stable_dt); opt may be NULL.
+ * Allocates the device state (three population arrays with ghost rows and
+ * columns); the handle owns it.  *out is set to NULL on failure. */
+VLBM_API int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
+                const vlbm_options *opt, vlbm_t **out);
+
+/* Sets f to the equilibrium of the given moments (Eq. feq_Q=4); with T != NULL
+ * the third-order Hermite projection of a Maxwellian at temperature T is used
+ * instead (the BGK target stays at T0 = 1).  Resets t, steps and the pole-flux
+ * budget.  Host arrays, layout [n_theta][n_phi]; T may be NULL. */
+VLBM_API int vlbm_init_moments(vlbm_t *h, const double *rho, const double *u_theta, const double *u_phi,
+                      const double *T);
+
+/* Advances n >= 0 SSP-RK3 steps (Sec. 3.7) and waits for them.  Returns
+ * VLBM_ERR_NONFINITE if the guard finds a NaN/Inf (the state is then left as
+ * computed, readable for debugging) and VLBM_ERR_TIMEOUT if a device wait gave up. */
+VLBM_API int vlbm_step(vlbm_t *h, int n);
+
+/* Enqueues n steps on the handle's stream and returns without waiting or
+ * checking (for timing and overlap); errors surface at the next vlbm_step,
+ * vlbm_sync or read-back. */
+VLBM_API int vlbm_step_async(vlbm_t *h, int n);
+
+/* Waits for the handle's stream and reports deferred device errors. */
+VLBM_API int vlbm_sync(vlbm_t *h);
+
+/* Moments of the current state (Eq. f_moments_sum): rho, u^theta-hat, u^phi-hat and,
+ * if T != NULL, T = sum_k f_k |v_k - u|^2 / (2 n).  Host outputs [n_theta][n_phi]. */
+VLBM_API int vlbm_moments(vlbm_t *h, double *rho, double *u_theta, double *u_phi, double *T);
+
+/* Copies the populations out / in as FP64 host arrays [16][n_theta][n_phi]
+ * (checkpoint / resume; the FP32 path converts to and from f = w_k rho_ref + delta f).
+ * vlbm_set_populations resets t, steps and the pole-flux budget. */
+VLBM_API int vlbm_get_populations(vlbm_t *h, double *f);
+VLBM_API int vlbm_set_populations(vlbm_t *h, const double *f);
+
+/* FP64 diagnostics of the current state (see vlbm_diag). */
+VLBM_API int vlbm_diagnostics(vlbm_t *h, vlbm_diag *out);
+
+/* Largest dt this library considers stable: 0.25 min(dtheta, sin(dtheta/2) dphi) / v_max
+ * without the polar filter, 0.25 dtheta / v_max with it (v_max = sqrt(3+sqrt6),
+ * R = 1), capped at tau (the paper keeps dt below tau, Sec. 5).  Needs no GPU. */
+VLBM_API int vlbm_max_stable_dt(int n_theta, int n_phi, int velocity_set, double tau, int polar_filter,
+                       double *out);
+
+/* Per-stage kernel time of the last vlbm_profile_step call, and the number of
+ * kernels one step launches.  vlbm_profile_step runs n steps launching each
+ * stage kernel individually between CUDA events on the handle's stream and
+ * stores, in ms_per_stage[0..2], the mean device time of stage kernel 1, 2, 3
+ * (ms_per_stage may be NULL).  Returns the launch count per step in *launches
+ * (may be NULL). */
+VLBM_API int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches);
+
+/* Bytes of device memory the handle holds. */
+VLBM_API size_t vlbm_device_bytes(const vlbm_t *h);
+
+/* Last error message of a handle (or of the last failed vlbm_create when h is NULL).
+ * The string stays valid until the next call on that handle. */
+VLBM_API const char *vlbm_last_error(const vlbm_t *h);
+
+/* Frees the handle and its device memory.  NULL-safe. */
+VLBM_API void vlbm_destroy(vlbm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLBM_H */

@@ -1,0 +1,747 @@
+// vlbm_api.cu -- host side of libvlbm.so: the C ABI of include/vlbm.h.
+//
+// Owns the device state of one solver (three population arrays for the SSP-RK3
+// stages of arXiv 2504.15574 Sec. 3.7, per-row geometry tables, scratch for
+// read-back and diagnostics), builds the FP64 tables of the velocity space
+// (App. A.2) and of the grid (Sec. 3.4), encodes the TMA descriptors of the
+// FP32 path, and enqueues steps as CUDA graphs on the handle's stream.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vlbm.h"
+#include "vlbm_internal.h"
+
+using namespace vk;
+
+struct vlbm {
+    int nt = 0, np = 0, prec = VLBM_FP64;
+    double tau = 0, dt = 0, eps = 1e-6, R = 1.0;
+    int filter = 0, guard = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Layout L{};
+    size_t elem = 8;
+    void *F = nullptr, *A = nullptr, *B = nullptr;
+    size_t arr_bytes = 0;
+    // FP64 geometry
+    double *d_sin_ext = nullptr, *d_cot = nullptr, *d_sin_t = nullptr, *d_cos_t = nullptr;
+    std::vector<double> sin_t, cos_t;
+    // FP32 tables
+    float *d_sin_ext_f = nullptr, *d_rref = nullptr;
+    FaceConst *d_face = nullptr;
+    RowConst *d_row = nullptr;
+    // polar filter
+    int *d_frows = nullptr, *d_fblocks = nullptr;
+    int nfrows = 0;
+    // diagnostics, budget, I/O scratch
+    double *d_pole = nullptr, *d_budget = nullptr, *d_mom = nullptr, *d_dense = nullptr;
+    double *d_part = nullptr, *d_diag = nullptr;
+    unsigned *d_flags = nullptr, *h_flags = nullptr;
+    CUtensorMap tmF{}, tmA{}, tmB{};
+    cudaGraphExec_t g1 = nullptr, g16 = nullptr;
+    VelD vd{};
+    VelF vf{};
+    double rho_ref = 0.0, rho_ref_opt = 0.0;
+    long long steps = 0;
+    double mass0 = 0.0;
+    std::string err;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double prof_ms[3] = {0, 0, 0};
+    size_t dev_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(vlbm_t *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define CK(h, call)                                                                                       \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return fail((h), VLBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+// ---- velocity space (App. A.2), FP64 --------------------------------------------
+// He_l by the three-term recurrence He_{l+1} = x He_l - l He_{l-1}.
+double hermite_he(int l, double x)
+{
+    double prev = 1.0, cur = x;
+    if (l == 0) return 1.0;
+    for (int m = 1; m < l; ++m) {
+        double next = x * cur - (double)m * prev;
+        prev = cur;
+        cur = next;
+    }
+    return cur;
+}
+
+double fact(int l)
+{
+    double r = 1.0;
+    for (int m = 2; m <= l; ++m) r *= (double)m;
+    return r;
+}
+
+void velocity_tables(VelD &c)
+{
+    // ascending roots of He_4 = x^4 - 6x^2 + 3; weights Q!/He_5(v)^2 (Eq. GH_weights)
+    const double outer = std::sqrt(3.0 + std::sqrt(6.0));
+    const double inner = std::sqrt(3.0 - std::sqrt(6.0));
+    c.v[0] = -outer;
+    c.v[1] = -inner;
+    c.v[2] = inner;
+    c.v[3] = outer;
+    for (int a = 0; a < 4; ++a) {
+        const double h = hermite_he(5, c.v[a]);
+        c.w[a] = fact(4) / (h * h);
+    }
+    // Eqs. (KH), (KtildeH)
+    for (int k = 0; k < 4; ++k)
+        for (int kp = 0; kp < 4; ++kp) {
+            double sk = 0.0, skt = 0.0;
+            for (int l = 0; l < 4; ++l) {
+                const double hk = hermite_he(l + 1, c.v[k]);
+                sk += hk * hermite_he(l, c.v[kp]) / fact(l);
+                double inner_l = hermite_he(l + 1, c.v[kp]);
+                if (l > 0) inner_l += (double)l * hermite_he(l - 1, c.v[kp]);
+                skt += hk * inner_l / fact(l);
+            }
+            c.K[k * 4 + kp] = -c.w[k] * sk;
+            c.Kt[k * 4 + kp] = -c.w[k] * skt;
+        }
+}
+
+// ---- grid (Eq. discrete_coord_sphere): north half evaluated, south half mirrored
+void row_tables(int nt, std::vector<double> &s, std::vector<double> &c)
+{
+    s.assign(nt, 0.0);
+    c.assign(nt, 0.0);
+    const double dth = M_PI / (double)nt;
+    for (int i = 0; i < nt; ++i) {
+        const int m = nt - 1 - i;
+        if (i <= m) {
+            const double th = ((double)i + 0.5) * dth;
+            s[i] = std::sin(th);
+            c[i] = (i == m) ? 0.0 : std::cos(th);
+        } else {
+            s[i] = s[m];
+            c[i] = -c[m];
+        }
+    }
+}
+
+// sin(theta) of padded row pr (row r = pr - GR); ghost rows carry the sine of their own angle
+double sin_padded(const std::vector<double> &s, int nt, int pr)
+{
+    const int r = pr - GR;
+    if (r < 0) return -s[-1 - r];
+    if (r >= nt) return -s[2 * nt - 1 - r];
+    return s[r];
+}
+
+// Polar ring filter block size (not in the paper): smallest power of two b with
+// b sin(theta) dphi >= dtheta / 4, dividing n_phi.
+int filter_block(int nt, int np, double sin_i)
+{
+    if (np < 2) return 1;
+    const double want = (M_PI / nt) / (4.0 * sin_i * (2.0 * M_PI / np));
+    int b = 1;
+    while ((double)b < want && b < np) b *= 2;
+    while (np % b != 0) b /= 2;
+    return b;
+}
+
+template <typename T>
+int upload(vlbm_t *h, T **dst, const T *src, size_t n)
+{
+    if (!*dst) {
+        CK(h, cudaMalloc((void **)dst, n * sizeof(T)));
+        h->dev_bytes += n * sizeof(T);
+    }
+    CK(h, cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return VLBM_OK;
+}
+
+int dalloc(vlbm_t *h, void **p, size_t bytes)
+{
+    CK(h, cudaMalloc(p, bytes));
+    CK(h, cudaMemset(*p, 0, bytes));
+    h->dev_bytes += bytes;
+    return VLBM_OK;
+}
+
+// FP32 tables that depend on rho_ref: per-face sine forms, per-row reference tendency.
+int build_f32_tables(vlbm_t *h)
+{
+    const int nt = h->nt;
+    const double R = h->R, dth = M_PI / nt, dph = 2.0 * M_PI / h->np;
+    const VelD &c = h->vd;
+    VelF &f = h->vf;
+    for (int a = 0; a < 4; ++a) {
+        f.v[a] = (float)c.v[a];
+        f.w[a] = (float)c.w[a];
+    }
+    for (int q = 0; q < 16; ++q) {
+        f.K[q] = (float)c.K[q];
+        f.Kt[q] = (float)c.Kt[q];
+        f.wr[q] = (float)(c.w[q / 4] * c.w[q % 4] * h->rho_ref);
+    }
+    f.rho_ref = (float)h->rho_ref;
+
+    // faces fi = 0..nt between rows fi-1 and fi; upwind-ordered sine stencils
+    std::vector<FaceConst> face(2 * (size_t)(nt + 1));
+    std::vector<double> plin(2 * (size_t)(nt + 1));
+    for (int fi = 0; fi <= nt; ++fi)
+        for (int dir = 0; dir < 2; ++dir) {
+            double x[5];
+            for (int m = 0; m < 5; ++m) {
+                const int r = (dir == 0) ? (fi - 3 + m) : (fi + 2 - m);
+                x[m] = sin_padded(h->sin_t, nt, r + GR);
+            }
+            const double a = x[0], b = x[1], cc = x[2], d = x[3], e = x[4];
+            FaceConst F;
+            const double A1 = a - 2 * b + cc, A2 = b - 2 * cc + d, A3 = cc - 2 * d + e;
+            F.sa1 = (float)A1;
+            F.sb1 = (float)(a - 4 * b + 3 * cc);
+            F.sa2 = (float)A2;
+            F.sb2 = (float)(b - d);
+            F.sa3 = (float)A3;
+            F.sb3 = (float)(3 * cc - 4 * d + e);
+            F.corr = (float)(0.1 * (A1 - A2) / 3.0 + 0.3 * (A2 - A3) / 6.0);
+            F.pad = 0.0f;
+            face[2 * fi + dir] = F;
+            plin[2 * fi + dir] = (2 * a - 13 * b + 47 * cc + 27 * d - 3 * e) / 60.0;
+        }
+    std::vector<RowConst> row(nt);
+    std::vector<float> rref((size_t)nt * 16);
+    for (int i = 0; i < nt; ++i) {
+        const double s = h->sin_t[i], cot = h->cos_t[i] / h->sin_t[i];
+        row[i].inv_dth = (float)(1.0 / (R * s * dth));
+        row[i].inv_dph = (float)(1.0 / (R * s * dph));
+        row[i].cotR = (float)(cot / R);
+        row[i].pad = 0.0f;
+        for (int k = 0; k < 16; ++k) {
+            const int a = k / 4, b = k % 4;
+            const double va = c.v[a], vb = c.v[b];
+            const double wr = c.w[a] * c.w[b] * h->rho_ref;
+            const int dir = va > 0 ? 0 : 1;
+            const double adv = -va * wr * (plin[2 * (i + 1) + dir] - plin[2 * i + dir]) / (R * s * dth);
+            double kw = 0.0, ktw = 0.0;
+            for (int m = 0; m < 4; ++m) {
+                kw += c.K[a * 4 + m] * c.w[m] * c.w[b] * h->rho_ref;
+                ktw += c.Kt[b * 4 + m] * c.w[a] * c.w[m] * h->rho_ref;
+            }
+            const double force = cot / R * (vb * vb * kw - va * ktw);
+            rref[(size_t)i * 16 + k] = (float)(adv - force);
+        }
+    }
+    int rc;
+    if ((rc = upload(h, &h->d_face, face.data(), face.size()))) return rc;
+    if ((rc = upload(h, &h->d_row, row.data(), row.size()))) return rc;
+    if ((rc = upload(h, &h->d_rref, rref.data(), rref.size()))) return rc;
+    return VLBM_OK;
+}
+
+int encode_map(vlbm_t *h, CUtensorMap *m, void *base)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        CK(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn)
+            return fail(h, VLBM_ERR_CUDA, "cuTensorMapEncodeTiled not available from the driver");
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)(h->nt + 2 * GR), (cuuint64_t)NK};
+    cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * sizeof(float), (cuuint64_t)h->L.plane * sizeof(float)};
+    cuuint32_t box[3] = {(cuuint32_t)(F32_TILE_COLS + 2 * GC), (cuuint32_t)(F32_TILE_ROWS + 2 * GR), (cuuint32_t)NK};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, VLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return VLBM_OK;
+}
+
+// Enqueues one RK3 step (all stages, filters, budget) on the handle's stream.
+void enqueue_step(vlbm_t *h, int stage_only = 0)
+{
+    cudaStream_t s = h->stream;
+    const size_t pole_per = (size_t)2 * NK * h->np;
+    for (int st = 1; st <= 3; ++st) {
+        if (stage_only && stage_only != st) continue;
+        void *in = (st == 1) ? h->F : (st == 2) ? h->A : h->B;
+        void *out = (st == 1) ? h->A : (st == 2) ? h->B : h->F;
+        if (h->prec == VLBM_FP64) {
+            StageD p;
+            p.in = (const double *)in;
+            p.fold = (const double *)h->F;
+            p.out = (double *)out;
+            p.sin_ext = h->d_sin_ext;
+            p.cot = h->d_cot;
+            p.pole = h->d_pole + (size_t)(st - 1) * pole_per;
+            p.L = h->L;
+            p.dth = M_PI / h->nt;
+            p.dph = 2.0 * M_PI / h->np;
+            p.R = h->R;
+            p.tau = h->tau;
+            p.dt = h->dt;
+            p.eps = h->eps;
+            p.stage = st;
+            p.c = h->vd;
+            launch_stage_f64(p, s);
+            if (h->nfrows) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
+        } else {
+            StageF p;
+            p.in = (const float *)in;
+            p.fold = (const float *)h->F;
+            p.out = (float *)out;
+            p.sin_ext = h->d_sin_ext_f;
+            p.face = h->d_face;
+            p.row = h->d_row;
+            p.rref = h->d_rref;
+            p.err = h->d_flags;
+            p.L = h->L;
+            p.tau_inv = (float)(1.0 / h->tau);
+            p.dt = (float)h->dt;
+            p.eps = (float)h->eps;
+            p.stage = st;
+            p.c = h->vf;
+            const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
+            launch_stage_f32(tm, p, s);
+            if (h->nfrows) launch_filter_f32((float *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
+        }
+    }
+    if (!stage_only && h->prec == VLBM_FP64)
+        launch_pole_budget(h->d_pole, h->np, h->R, 2.0 * M_PI / h->np, h->dt, h->d_budget, s);
+}
+
+int kernels_per_step(const vlbm_t *h)
+{
+    int n = 3 + (h->nfrows ? 3 : 0);
+    if (h->prec == VLBM_FP64) n += 1;
+    return n;
+}
+
+int build_graph(vlbm_t *h, int nsteps, cudaGraphExec_t *exec)
+{
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < nsteps; ++q) enqueue_step(h);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return fail(h, VLBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, VLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return VLBM_OK;
+}
+
+void drop_graphs(vlbm_t *h)
+{
+    if (h->g1) cudaGraphExecDestroy(h->g1);
+    if (h->g16) cudaGraphExecDestroy(h->g16);
+    h->g1 = h->g16 = nullptr;
+}
+
+// After the populations changed from outside a step: ghosts, counters, mass0.
+int after_reset(vlbm_t *h)
+{
+    if (h->prec == VLBM_FP64) launch_fill_ghosts_f64((double *)h->F, h->L, h->stream);
+    else launch_fill_ghosts_f32((float *)h->F, h->L, h->stream);
+    CK(h, cudaMemsetAsync(h->d_budget, 0, sizeof(double), h->stream));
+    CK(h, cudaMemsetAsync(h->d_flags, 0, sizeof(unsigned) * 4, h->stream));
+    CK(h, cudaGetLastError());
+    h->steps = 0;
+    vlbm_diag d;
+    int rc = vlbm_diagnostics(h, &d);
+    if (rc) return rc;
+    h->mass0 = d.mass;
+    return VLBM_OK;
+}
+
+// rho_ref of the FP32 deviation storage: the option, else the area-weighted mean density.
+void choose_rho_ref(vlbm_t *h, const std::vector<double> &rho)
+{
+    if (h->rho_ref_opt > 0.0) {
+        h->rho_ref = h->rho_ref_opt;
+        return;
+    }
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < h->nt; ++i)
+        for (int j = 0; j < h->np; ++j) {
+            num += h->sin_t[i] * rho[(size_t)i * h->np + j];
+            den += h->sin_t[i];
+        }
+    h->rho_ref = num / den;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vlbm_default_options(vlbm_options *opt)
+{
+    if (!opt) return;
+    opt->precision = VLBM_FP64;
+    opt->weno_eps = 1e-6;
+    opt->radius = 1.0;
+    opt->polar_filter = 0;
+    opt->guard = 1;
+    opt->stream = nullptr;
+    opt->rho_ref = 0.0;
+}
+
+int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt, const vlbm_options *opt,
+                vlbm_t **out)
+{
+    if (!out) return fail(nullptr, VLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (velocity_set == VLBM_D2Q9) return fail(nullptr, VLBM_ERR_UNSUPPORTED, "D2Q9 is not implemented");
+    if (velocity_set != VLBM_D2Q16) return fail(nullptr, VLBM_ERR_ARG, "unknown velocity set");
+    if (n_theta < 6 || n_theta > 65536) return fail(nullptr, VLBM_ERR_ARG, "n_theta must be in [6, 65536]");
+    if (n_phi < 1 || n_phi > 65536 || (n_phi != 1 && n_phi % 2 != 0))
+        return fail(nullptr, VLBM_ERR_ARG, "n_phi must be 1 or even, at most 65536");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(nullptr, VLBM_ERR_ARG, "tau must be > 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, VLBM_ERR_ARG, "dt must be > 0");
+    vlbm_options o;
+    vlbm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != VLBM_FP64 && o.precision != VLBM_FP32) return fail(nullptr, VLBM_ERR_ARG, "bad precision");
+    if (!(o.weno_eps > 0.0) || !(o.radius > 0.0)) return fail(nullptr, VLBM_ERR_ARG, "weno_eps and radius must be > 0");
+
+    vlbm_t *h = new vlbm_t();
+    h->nt = n_theta;
+    h->np = n_phi;
+    h->prec = o.precision;
+    h->tau = tau;
+    h->dt = dt;
+    h->eps = o.weno_eps;
+    h->R = o.radius;
+    h->filter = o.polar_filter ? 1 : 0;
+    h->guard = o.guard ? 1 : 0;
+    h->rho_ref_opt = o.rho_ref;
+    h->elem = (h->prec == VLBM_FP64) ? sizeof(double) : sizeof(float);
+    h->L.nt = n_theta;
+    h->L.np = n_phi;
+    h->L.pitch = ((n_phi + 2 * GC) + 3) / 4 * 4;
+    h->L.plane = (size_t)(n_theta + 2 * GR) * (size_t)h->L.pitch;
+    h->arr_bytes = (size_t)NK * h->L.plane * h->elem;
+    velocity_tables(h->vd);
+    row_tables(n_theta, h->sin_t, h->cos_t);
+
+    auto bail = [&](int rc) {
+        std::string m = h->err;
+        vlbm_destroy(h);
+        g_create_error = m;
+        return rc;
+    };
+    int rc;
+    int ndev = 0;
+    cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0) {
+        delete h;
+        return fail(nullptr, VLBM_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(ce));
+    }
+    if (o.stream) {
+        h->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(nullptr, VLBM_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        h->own_stream = true;
+    }
+    if ((rc = dalloc(h, &h->F, h->arr_bytes)) || (rc = dalloc(h, &h->A, h->arr_bytes)) ||
+        (rc = dalloc(h, &h->B, h->arr_bytes)))
+        return bail(rc);
+    // geometry
+    std::vector<double> sext(n_theta + 2 * GR + F32_TILE_ROWS, 0.0), cot(n_theta);
+    for (int pr = 0; pr < n_theta + 2 * GR; ++pr) sext[pr] = sin_padded(h->sin_t, n_theta, pr);
+    for (int i = 0; i < n_theta; ++i) cot[i] = h->cos_t[i] / h->sin_t[i];
+    if ((rc = upload(h, &h->d_sin_ext, sext.data(), sext.size())) || (rc = upload(h, &h->d_cot, cot.data(), cot.size())) ||
+        (rc = upload(h, &h->d_sin_t, h->sin_t.data(), h->sin_t.size())) ||
+        (rc = upload(h, &h->d_cos_t, h->cos_t.data(), h->cos_t.size())))
+        return bail(rc);
+    std::vector<float> sextf(sext.begin(), sext.end());
+    if ((rc = upload(h, &h->d_sin_ext_f, sextf.data(), sextf.size()))) return bail(rc);
+    // polar filter rows
+    if (h->filter) {
+        std::vector<int> rows, blocks;
+        for (int i = 0; i < n_theta; ++i) {
+            const int b = filter_block(n_theta, n_phi, h->sin_t[i]);
+            if (b > 1) {
+                rows.push_back(i);
+                blocks.push_back(b);
+            }
+        }
+        h->nfrows = (int)rows.size();
+        if (h->nfrows &&
+            ((rc = upload(h, &h->d_frows, rows.data(), rows.size())) || (rc = upload(h, &h->d_fblocks, blocks.data(), blocks.size()))))
+            return bail(rc);
+    }
+    if ((rc = dalloc(h, (void **)&h->d_pole, sizeof(double) * 3 * 2 * NK * (size_t)n_phi)) ||
+        (rc = dalloc(h, (void **)&h->d_budget, sizeof(double) * 8)) ||
+        (rc = dalloc(h, (void **)&h->d_mom, sizeof(double) * 4 * (size_t)n_theta * n_phi)) ||
+        (rc = dalloc(h, (void **)&h->d_part, sizeof(double) * diag_partials(h->L))) ||
+        (rc = dalloc(h, (void **)&h->d_diag, sizeof(double) * 8)) ||
+        (rc = dalloc(h, (void **)&h->d_flags, sizeof(unsigned) * 4)))
+        return bail(rc);
+    if (cudaMallocHost((void **)&h->h_flags, sizeof(unsigned) * 4) != cudaSuccess) {
+        h->err = "cudaMallocHost failed";
+        return bail(VLBM_ERR_CUDA);
+    }
+    for (int q = 0; q < 4; ++q)
+        if (cudaEventCreate(&h->ev[q]) != cudaSuccess) {
+            h->err = "cudaEventCreate failed";
+            return bail(VLBM_ERR_CUDA);
+        }
+    if (h->prec == VLBM_FP32) {
+        if ((rc = encode_map(h, &h->tmF, h->F)) || (rc = encode_map(h, &h->tmA, h->A)) ||
+            (rc = encode_map(h, &h->tmB, h->B)))
+            return bail(rc);
+        // the stage kernel needs more than the default 48 KB of dynamic shared
+        // memory; set that once here, outside any graph capture
+        CK(h, prepare_stage_f32());
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        h->err = "device synchronize after create failed";
+        return bail(VLBM_ERR_CUDA);
+    }
+    *out = h;
+    return VLBM_OK;
+}
+
+int vlbm_init_moments(vlbm_t *h, const double *rho, const double *u_theta, const double *u_phi, const double *T)
+{
+    if (!h || !rho || !u_theta || !u_phi) return fail(h, VLBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)h->nt * h->np;
+    double *d = h->d_mom;
+    CK(h, cudaMemcpyAsync(d, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(d + n, u_theta, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(d + 2 * n, u_phi, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (T) CK(h, cudaMemcpyAsync(d + 3 * n, T, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (h->prec == VLBM_FP64) {
+        launch_init_f64((double *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->stream);
+    } else {
+        std::vector<double> r(rho, rho + n);
+        const double old = h->rho_ref;
+        choose_rho_ref(h, r);
+        if (old != h->rho_ref || !h->d_face) {
+            int rc = build_f32_tables(h);
+            if (rc) return rc;
+            drop_graphs(h);
+        }
+        launch_init_f32((float *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->rho_ref,
+                        h->stream);
+    }
+    CK(h, cudaGetLastError());
+    return after_reset(h);
+}
+
+int vlbm_set_populations(vlbm_t *h, const double *f)
+{
+    if (!h || !f) return fail(h, VLBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)NK * h->nt * h->np;
+    if (!h->d_dense) {
+        int rc = dalloc(h, (void **)&h->d_dense, n * sizeof(double));
+        if (rc) return rc;
+    }
+    CK(h, cudaMemcpyAsync(h->d_dense, f, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (h->prec == VLBM_FP64) {
+        launch_unpack_f64(h->d_dense, h->L, (double *)h->F, h->stream);
+    } else {
+        const size_t cells = (size_t)h->nt * h->np;
+        std::vector<double> rho(cells, 0.0);
+        for (int k = 0; k < NK; ++k)
+            for (size_t c = 0; c < cells; ++c) rho[c] += f[(size_t)k * cells + c];
+        const double old = h->rho_ref;
+        choose_rho_ref(h, rho);
+        if (old != h->rho_ref || !h->d_face) {
+            int rc = build_f32_tables(h);
+            if (rc) return rc;
+            drop_graphs(h);
+        }
+        launch_unpack_f32(h->d_dense, h->L, (float *)h->F, h->vd, h->rho_ref, h->stream);
+    }
+    CK(h, cudaGetLastError());
+    return after_reset(h);
+}
+
+int vlbm_get_populations(vlbm_t *h, double *f)
+{
+    if (!h || !f) return fail(h, VLBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)NK * h->nt * h->np;
+    if (!h->d_dense) {
+        int rc = dalloc(h, (void **)&h->d_dense, n * sizeof(double));
+        if (rc) return rc;
+    }
+    if (h->prec == VLBM_FP64) launch_pack_f64((const double *)h->F, h->L, h->d_dense, h->stream);
+    else launch_pack_f32((const float *)h->F, h->L, h->d_dense, h->vd, h->rho_ref, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(f, h->d_dense, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return VLBM_OK;
+}
+
+int vlbm_step_async(vlbm_t *h, int n)
+{
+    if (!h || n < 0) return fail(h, VLBM_ERR_ARG, "bad handle or step count");
+    if (h->prec == VLBM_FP32 && !h->d_face) return fail(h, VLBM_ERR_ARG, "FP32 state not initialised");
+    if (n == 0) return VLBM_OK;
+    int rc;
+    if (!h->g1 && (rc = build_graph(h, 1, &h->g1))) return rc;
+    if (n >= 16 && !h->g16 && (rc = build_graph(h, 16, &h->g16))) return rc;
+    int left = n;
+    while (left >= 16) {
+        CK(h, cudaGraphLaunch(h->g16, h->stream));
+        left -= 16;
+    }
+    while (left-- > 0) CK(h, cudaGraphLaunch(h->g1, h->stream));
+    h->steps += n;
+    return VLBM_OK;
+}
+
+int vlbm_sync(vlbm_t *h)
+{
+    if (!h) return fail(h, VLBM_ERR_ARG, "NULL handle");
+    CK(h, cudaMemcpyAsync(h->h_flags, h->d_flags, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaGetLastError());
+    if (h->h_flags[0] & 1u) return fail(h, VLBM_ERR_TIMEOUT, "a tile load did not complete within its time limit");
+    if (h->h_flags[1]) return fail(h, VLBM_ERR_NONFINITE, "non-finite population found by the guard");
+    return VLBM_OK;
+}
+
+int vlbm_step(vlbm_t *h, int n)
+{
+    int rc = vlbm_step_async(h, n);
+    if (rc) return rc;
+    if (h->guard && n > 0) {
+        if (h->prec == VLBM_FP64) launch_guard_f64((const double *)h->F, h->L, h->d_flags + 1, h->stream);
+        else launch_guard_f32((const float *)h->F, h->L, h->d_flags + 1, h->stream);
+        CK(h, cudaGetLastError());
+    }
+    return vlbm_sync(h);
+}
+
+int vlbm_moments(vlbm_t *h, double *rho, double *u_theta, double *u_phi, double *T)
+{
+    if (!h || !rho || !u_theta || !u_phi) return fail(h, VLBM_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)h->nt * h->np;
+    double *d = h->d_mom;
+    if (h->prec == VLBM_FP64)
+        launch_moments_f64((const double *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->stream);
+    else
+        launch_moments_f32((const float *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd,
+                           h->rho_ref, h->stream);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(u_theta, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(u_phi, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (T) CK(h, cudaMemcpyAsync(T, d + 3 * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return VLBM_OK;
+}
+
+int vlbm_diagnostics(vlbm_t *h, vlbm_diag *out)
+{
+    if (!h || !out) return fail(h, VLBM_ERR_ARG, "NULL argument");
+    const double area = h->R * h->R * (M_PI / h->nt) * (2.0 * M_PI / h->np);
+    if (h->prec == VLBM_FP64)
+        launch_diagnostics_f64((const double *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->vd, area, h->d_part, h->d_diag,
+                               h->stream);
+    else
+        launch_diagnostics_f32((const float *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->vd, area, h->rho_ref, h->d_part,
+                               h->d_diag, h->stream);
+    CK(h, cudaGetLastError());
+    double v[8];
+    CK(h, cudaMemcpyAsync(v, h->d_diag, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(v + 6, h->d_budget, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    out->time = (double)h->steps * h->dt;
+    out->steps = h->steps;
+    out->mass = v[0];
+    out->momentum[0] = v[1];
+    out->momentum[1] = v[2];
+    out->momentum[2] = v[3];
+    out->energy = v[4];
+    out->nonfinite = v[5] > 0.0 ? 1 : 0;
+    out->pole_flux = (h->prec == VLBM_FP64) ? v[6] : NAN;
+    out->mass0 = h->mass0;
+    return VLBM_OK;
+}
+
+int vlbm_max_stable_dt(int n_theta, int n_phi, int velocity_set, double tau, int polar_filter, double *out)
+{
+    if (!out) return VLBM_ERR_ARG;
+    if (velocity_set == VLBM_D2Q9) return VLBM_ERR_UNSUPPORTED;
+    if (velocity_set != VLBM_D2Q16 || n_theta < 6 || n_phi < 1 || !(tau > 0.0)) return VLBM_ERR_ARG;
+    const double vmax = std::sqrt(3.0 + std::sqrt(6.0));
+    const double dth = M_PI / n_theta, dph = 2.0 * M_PI / n_phi;
+    double lim = polar_filter ? dth : std::fmin(dth, std::sin(dth / 2.0) * dph);
+    if (n_phi == 1) lim = dth;
+    double dt = 0.25 * lim / vmax;
+    if (dt > tau) dt = tau;
+    *out = dt;
+    return VLBM_OK;
+}
+
+int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches)
+{
+    if (!h || n < 1) return fail(h, VLBM_ERR_ARG, "bad handle or step count");
+    if (h->prec == VLBM_FP32 && !h->d_face) return fail(h, VLBM_ERR_ARG, "FP32 state not initialised");
+    double acc[3] = {0, 0, 0};
+    for (int q = 0; q < n; ++q) {
+        for (int st = 1; st <= 3; ++st) {
+            CK(h, cudaEventRecord(h->ev[0], h->stream));
+            enqueue_step(h, st);
+            CK(h, cudaEventRecord(h->ev[1], h->stream));
+            CK(h, cudaEventSynchronize(h->ev[1]));
+            float ms = 0.0f;
+            CK(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+            acc[st - 1] += ms;
+        }
+    }
+    h->steps += n;
+    for (int st = 0; st < 3; ++st) h->prof_ms[st] = acc[st] / n;
+    if (ms_per_stage)
+        for (int st = 0; st < 3; ++st) ms_per_stage[st] = h->prof_ms[st];
+    if (launches) *launches = kernels_per_step(h);
+    return vlbm_sync(h);
+}
+
+size_t vlbm_device_bytes(const vlbm_t *h) { return h ? h->dev_bytes : 0; }
+
+const char *vlbm_last_error(const vlbm_t *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void vlbm_destroy(vlbm_t *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_sin_ext_f, h->d_rref,
+                    h->d_face, h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
+                    h->d_part, h->d_diag, h->d_flags};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (h->h_flags) cudaFreeHost(h->h_flags);
+    for (int q = 0; q < 4; ++q)
+        if (h->ev[q]) cudaEventDestroy(h->ev[q]);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// vlbm_internal.h -- definitions shared by the translation units of libvlbm.so.
+//
+// Device layout of a population array (FP64 or FP32):
+//   16 planes, plane k holds rows r = -GR .. n_theta+GR-1 and columns
+//   c = -GC .. n_phi+GC-1 of population k = 4a + b (v_theta = v[a], v_phi = v[b]).
+//   Element (k, r, c) lives at k * plane + (r + GR) * pitch + (c + GC).
+//   The pitch is n_phi + 2 GC rounded up to a multiple of 4 elements, so every
+//   row starts on a 16-byte boundary (TMA tiles, float4 / double2 accesses).
+//   Ghost rows beyond a pole hold the population that the pole boundary
+//   condition of arXiv 2504.15574 Sec. 3.6 (Eq. bcs_theta) maps there:
+//   ghost (k, -1-i, c) = f(15-k, i, c + n_phi/2) and ghost (k, n_theta+i, c) =
+//   f(15-k, n_theta-1-i, c + n_phi/2); ghost columns hold the periodic images
+//   (Eq. bcs_phi).  Every kernel that writes an interior cell also writes all
+//   of its images, so stencils read ghosts like interior data.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace vk {
+
+constexpr int NK = 16;   // D2Q16 populations
+constexpr int GR = 3;    // ghost rows per pole (WENO-5 half-width)
+constexpr int GC = 4;    // ghost columns per side (3 needed, 4 keeps TMA x-coordinates 16-byte aligned)
+
+struct Layout {
+    int nt, np, pitch;
+    size_t plane;        // (nt + 2 GR) * pitch elements
+    __host__ __device__ size_t at(int k, int r, int c) const {
+        return (size_t)k * plane + (size_t)(r + GR) * (size_t)pitch + (size_t)(c + GC);
+    }
+};
+
+// Velocity-space constants (App. A.2): v ascending, 1-D weights, kernels.
+struct VelD { double v[4], w[4], K[16], Kt[16]; };
+struct VelF { float v[4], w[4], K[16], Kt[16], wr[16]; float rho_ref; };   // wr = w_k rho_ref
+
+// ---- FP64 stage (parity path) -------------------------------------------------
+struct StageD {
+    const double *in;      // stage input g (padded layout)
+    const double *fold;    // f at the start of the step (own cell only), stages 2 and 3
+    double *out;           // stage output (padded layout); may alias fold in stage 3
+    const double *sin_ext; // sin(theta) at padded rows 0 .. nt+2GR-1 (negative at ghost rows)
+    const double *cot;     // cos/sin per interior row
+    double *pole;          // [2][16][np] fluxes through the north/south pole faces, or NULL
+    Layout L;
+    double dth, dph, R, tau, dt, eps;
+    int stage;             // 1, 2, 3
+    VelD c;
+};
+void launch_stage_f64(const StageD &p, cudaStream_t s);
+
+// ---- FP32 deviation stage (throughput path) -------------------------------------
+// Per theta face and upwind direction: the smoothness linear forms of the stencil applied to
+// sin(theta) and corr = 0.1 (P1-P2) + 0.3 (P3-P2) of sin(theta) (ideal-weight interpolant minus P2).
+struct FaceConst { float sa1, sb1, sa2, sb2, sa3, sb3, corr, pad; };
+struct RowConst { float inv_dth, inv_dph, cotR, pad; };            // 1/(R sin dth), 1/(R sin dph), cot/R
+
+struct StageF {
+    const float *in;        // stage input delta g (padded layout) -- read by TMA
+    const float *fold;      // delta f at the start of the step (own cell), stages 2 and 3
+    float *out;
+    const float *sin_ext;   // [nt + 2GR + TILE_ROWS] sin at padded rows, zero beyond
+    const FaceConst *face;  // [nt+1][2]: face between rows fi-1 and fi, dir 0: v>0, 1: v<0
+    const RowConst *row;    // [nt]
+    const float *rref;      // [nt][16] FP64-derived tendency of the reference state w_k rho_ref
+    unsigned *err;          // device error flag (bit 0: TMA wait timeout)
+    Layout L;
+    float tau_inv, dt, eps;
+    int stage;
+    VelF c;
+};
+void launch_stage_f32(const CUtensorMap &tm_in, const StageF &p, cudaStream_t s);
+constexpr int F32_TILE_ROWS = 8;
+constexpr int F32_TILE_COLS = 32;
+size_t stage_f32_smem_bytes();
+cudaError_t prepare_stage_f32();   // sets the kernel's dynamic shared-memory limit
+
+// ---- shared helpers (FP64 arithmetic, any precision storage) ---------------------
+// Initial populations of moments (rho, ut, up, T) -> padded array (FP64) or
+// deviation array (FP32, minus w_k rho_ref).  T may be NULL.
+void launch_init_f64(double *f, const Layout &L, const double *rho, const double *ut, const double *up,
+                     const double *T, const VelD &c, cudaStream_t s);
+void launch_init_f32(float *f, const Layout &L, const double *rho, const double *ut, const double *up,
+                     const double *T, const VelD &c, double rho_ref, cudaStream_t s);
+// Moments (rho, ut, up, T) of a padded FP64 array / FP32 deviation array.
+void launch_moments_f64(const double *f, const Layout &L, double *rho, double *ut, double *up, double *T,
+                        const VelD &c, cudaStream_t s);
+void launch_moments_f32(const float *f, const Layout &L, double *rho, double *ut, double *up, double *T,
+                        const VelD &c, double rho_ref, cudaStream_t s);
+// Fill every ghost row / column from the interior.
+void launch_fill_ghosts_f64(double *f, const Layout &L, cudaStream_t s);
+void launch_fill_ghosts_f32(float *f, const Layout &L, cudaStream_t s);
+// Dense [16][nt][np] FP64 <-> padded storage.
+void launch_pack_f64(const double *f, const Layout &L, double *dense, cudaStream_t s);
+void launch_unpack_f64(const double *dense, const Layout &L, double *f, cudaStream_t s);
+void launch_pack_f32(const float *f, const Layout &L, double *dense, const VelD &c, double rho_ref, cudaStream_t s);
+void launch_unpack_f32(const double *dense, const Layout &L, float *f, const VelD &c, double rho_ref,
+                       cudaStream_t s);
+// Polar ring filter (not in the paper): rows listed in `rows` with block sizes `blocks`.
+void launch_filter_f64(double *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s);
+void launch_filter_f32(float *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s);
+// FP64 diagnostics: out[0] mass, [1..3] momentum, [4] energy, [5] non-finite count.
+// `part` is scratch of at least diag_partials(L) doubles.
+size_t diag_partials(const Layout &L);
+void launch_diagnostics_f64(const double *f, const Layout &L, const double *sin_t, const double *cos_t,
+                            const VelD &c, double area, double *part, double *out, cudaStream_t s);
+void launch_diagnostics_f32(const float *f, const Layout &L, const double *sin_t, const double *cos_t,
+                            const VelD &c, double area, double rho_ref, double *part, double *out,
+                            cudaStream_t s);
+// Non-finite guard: sets *flag to 1 if any interior population is NaN/Inf.
+void launch_guard_f64(const double *f, const Layout &L, unsigned *flag, cudaStream_t s);
+void launch_guard_f32(const float *f, const Layout &L, unsigned *flag, cudaStream_t s);
+// Pole mass-flux budget: budget += dt * (m1/6 + m2/6 + 2 m3/3), m_s = -R dph sum (F_south - F_north).
+void launch_pole_budget(const double *pole3, int np, double R, double dph, double dt, double *budget,
+                        cudaStream_t s);
+
+}  // namespace vk

@@ -1,0 +1,264 @@
+"""ctypes binding of libvlbm.so (the C ABI declared in include/vlbm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  The functions keep the C names (``vlbm_create``,
+``vlbm_init_moments``, ``vlbm_step``, ``vlbm_moments``, ``vlbm_destroy``, ...);
+``Solver`` is a small object wrapper over them.  There is no fallback: if the
+library is missing this module raises, and without a GPU the calls that need
+one raise ``VlbmError`` with code VLBM_ERR_CUDA.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvlbm.so")
+
+VLBM_OK, VLBM_ERR_ARG, VLBM_ERR_UNSUPPORTED, VLBM_ERR_CUDA, VLBM_ERR_NONFINITE, VLBM_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+VLBM_D2Q9, VLBM_D2Q16 = 3, 4
+VLBM_FP64, VLBM_FP32 = 0, 1
+NK = 16
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"vlbm error {code}: {msg}")
+        self.code = code
+
+
+class vlbm_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("weno_eps", ctypes.c_double), ("radius", ctypes.c_double),
+                ("polar_filter", ctypes.c_int), ("guard", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("rho_ref", ctypes.c_double)]
+
+
+class vlbm_diag(ctypes.Structure):
+    _fields_ = [("time", ctypes.c_double), ("steps", ctypes.c_longlong), ("mass", ctypes.c_double),
+                ("momentum", ctypes.c_double * 3), ("energy", ctypes.c_double), ("pole_flux", ctypes.c_double),
+                ("mass0", ctypes.c_double), ("nonfinite", ctypes.c_int)]
+
+
+_PD = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+# name -> (restype, argtypes); mirrors include/vlbm.h
+SIGNATURES = {
+    "vlbm_default_options": (None, [ctypes.POINTER(vlbm_options)]),
+    "vlbm_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(vlbm_options), ctypes.POINTER(_H)]),
+    "vlbm_init_moments": (ctypes.c_int, [_H, _PD, _PD, _PD, _PD]),
+    "vlbm_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "vlbm_step_async": (ctypes.c_int, [_H, ctypes.c_int]),
+    "vlbm_sync": (ctypes.c_int, [_H]),
+    "vlbm_moments": (ctypes.c_int, [_H, _PD, _PD, _PD, _PD]),
+    "vlbm_get_populations": (ctypes.c_int, [_H, _PD]),
+    "vlbm_set_populations": (ctypes.c_int, [_H, _PD]),
+    "vlbm_diagnostics": (ctypes.c_int, [_H, ctypes.POINTER(vlbm_diag)]),
+    "vlbm_max_stable_dt": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                          _PD]),
+    "vlbm_profile_step": (ctypes.c_int, [_H, ctypes.c_int, _PD, ctypes.POINTER(ctypes.c_int)]),
+    "vlbm_device_bytes": (ctypes.c_size_t, [_H]),
+    "vlbm_last_error": (ctypes.c_char_p, [_H]),
+    "vlbm_destroy": (None, [_H]),
+}
+
+
+def load(path: str | None = None):
+    """Loads libvlbm.so (built by paper_2504_15574_gb300.build); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} not found: build it with paper_2504_15574_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc, h=None):
+    if rc != VLBM_OK:
+        msg = load().vlbm_last_error(h)
+        raise VlbmError(rc, msg.decode() if msg else "")
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_PD)
+
+
+def _host(a, shape):
+    if a is None:
+        return None
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
+
+
+# ---- the C names -----------------------------------------------------------------
+
+def vlbm_default_options() -> vlbm_options:
+    o = vlbm_options()
+    load().vlbm_default_options(ctypes.byref(o))
+    return o
+
+
+def vlbm_create(n_theta, n_phi, velocity_set, tau, dt, opt: vlbm_options | None = None):
+    h = _H()
+    rc = load().vlbm_create(int(n_theta), int(n_phi), int(velocity_set), float(tau), float(dt),
+                            ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    _check(rc, None)
+    return h
+
+
+def vlbm_init_moments(h, rho, u_theta, u_phi, T=None, shape=None):
+    _check(load().vlbm_init_moments(h, _p(rho), _p(u_theta), _p(u_phi), _p(T)), h)
+
+
+def vlbm_step(h, n):
+    _check(load().vlbm_step(h, int(n)), h)
+
+
+def vlbm_step_async(h, n):
+    _check(load().vlbm_step_async(h, int(n)), h)
+
+
+def vlbm_sync(h):
+    _check(load().vlbm_sync(h), h)
+
+
+def vlbm_moments(h, rho, u_theta, u_phi, T=None):
+    _check(load().vlbm_moments(h, _p(rho), _p(u_theta), _p(u_phi), _p(T)), h)
+
+
+def vlbm_get_populations(h, f):
+    _check(load().vlbm_get_populations(h, _p(f)), h)
+
+
+def vlbm_set_populations(h, f):
+    _check(load().vlbm_set_populations(h, _p(f)), h)
+
+
+def vlbm_diagnostics(h) -> dict:
+    d = vlbm_diag()
+    _check(load().vlbm_diagnostics(h, ctypes.byref(d)), h)
+    return {"time": d.time, "steps": d.steps, "mass": d.mass, "px": d.momentum[0], "py": d.momentum[1],
+            "pz": d.momentum[2], "energy": d.energy, "pole_flux": d.pole_flux, "mass0": d.mass0,
+            "nonfinite": d.nonfinite}
+
+
+def vlbm_max_stable_dt(n_theta, n_phi, tau, polar_filter=False, velocity_set=VLBM_D2Q16) -> float:
+    out = ctypes.c_double()
+    rc = load().vlbm_max_stable_dt(int(n_theta), int(n_phi), int(velocity_set), float(tau), int(bool(polar_filter)),
+                                   ctypes.byref(out))
+    _check(rc, None)
+    return out.value
+
+
+def vlbm_profile_step(h, n):
+    ms = (ctypes.c_double * 3)()
+    launches = ctypes.c_int()
+    _check(load().vlbm_profile_step(h, int(n), ms, ctypes.byref(launches)), h)
+    return list(ms), launches.value
+
+
+def vlbm_device_bytes(h) -> int:
+    return int(load().vlbm_device_bytes(h))
+
+
+def vlbm_last_error(h=None) -> str:
+    m = load().vlbm_last_error(h)
+    return m.decode() if m else ""
+
+
+def vlbm_destroy(h):
+    load().vlbm_destroy(h)
+
+
+# ---- object wrapper --------------------------------------------------------------
+
+class Solver:
+    """One vLBM solver on the GPU: ``Solver(n_theta, n_phi, tau, dt, precision="fp64"|"fp32")``."""
+
+    def __init__(self, n_theta, n_phi, tau, dt, precision="fp64", eps=1e-6, R=1.0, polar_filter=False,
+                 guard=True, stream=None, rho_ref=0.0):
+        o = vlbm_default_options()
+        o.precision = VLBM_FP32 if precision in ("fp32", VLBM_FP32) else VLBM_FP64
+        o.weno_eps = float(eps)
+        o.radius = float(R)
+        o.polar_filter = int(bool(polar_filter))
+        o.guard = int(bool(guard))
+        o.stream = stream
+        o.rho_ref = float(rho_ref)
+        self.n_theta, self.n_phi = int(n_theta), int(n_phi)
+        self.tau, self.dt = float(tau), float(dt)
+        self.precision = "fp32" if o.precision == VLBM_FP32 else "fp64"
+        self.h = vlbm_create(n_theta, n_phi, VLBM_D2Q16, tau, dt, o)
+
+    @property
+    def shape(self):
+        return (self.n_theta, self.n_phi)
+
+    def init_moments(self, rho, u_theta, u_phi, T=None):
+        s = self.shape
+        rho, ut, up, T = _host(rho, s), _host(u_theta, s), _host(u_phi, s), _host(T, s)
+        vlbm_init_moments(self.h, rho, ut, up, T)
+
+    def step(self, n=1):
+        vlbm_step(self.h, n)
+
+    def step_async(self, n=1):
+        vlbm_step_async(self.h, n)
+
+    def sync(self):
+        vlbm_sync(self.h)
+
+    def moments(self, with_T=False):
+        s = self.shape
+        rho, ut, up = np.empty(s), np.empty(s), np.empty(s)
+        T = np.empty(s) if with_T else None
+        vlbm_moments(self.h, rho, ut, up, T)
+        return (rho, ut, up, T) if with_T else (rho, ut, up)
+
+    def get_populations(self):
+        f = np.empty((NK,) + self.shape)
+        vlbm_get_populations(self.h, f)
+        return f
+
+    def set_populations(self, f):
+        vlbm_set_populations(self.h, _host(f, (NK,) + self.shape))
+
+    def diagnostics(self):
+        return vlbm_diagnostics(self.h)
+
+    def profile_step(self, n=1):
+        return vlbm_profile_step(self.h, n)
+
+    def device_bytes(self):
+        return vlbm_device_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            vlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

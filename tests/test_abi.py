@@ -1,0 +1,78 @@
+"""The C-ABI library loads on a machine without a GPU, exports every entry point
+include/vlbm.h declares, and validates arguments before touching the device."""
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "vlbm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2504_15574_gb300 import build, vlbm
+    build.build()
+    return vlbm.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"VLBM_API\s+[^;(]*?\b(vlbm_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("vlbm_create", "vlbm_init_moments", "vlbm_step", "vlbm_moments", "vlbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2504_15574_gb300 import vlbm
+    out = subprocess.run(["nm", "-D", "--defined-only", vlbm.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(vlbm_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+    # the Python binding covers every declared entry point
+    assert set(declared_functions()) <= set(vlbm.SIGNATURES)
+
+
+def test_max_stable_dt_needs_no_gpu(lib):
+    from paper_2504_15574_gb300 import vlbm
+    vmax = math.sqrt(3 + math.sqrt(6))
+    dt = vlbm.vlbm_max_stable_dt(32, 64, 1.0)
+    dth = math.pi / 32
+    assert dt == pytest.approx(0.25 * min(dth, math.sin(dth / 2) * (2 * math.pi / 64)) / vmax, rel=1e-15)
+    assert vlbm.vlbm_max_stable_dt(32, 64, 1.0, polar_filter=True) == pytest.approx(0.25 * dth / vmax, rel=1e-15)
+    assert vlbm.vlbm_max_stable_dt(32, 64, 1e-9) == 1e-9      # capped at tau
+    with pytest.raises(vlbm.VlbmError) as e:
+        vlbm.vlbm_max_stable_dt(32, 64, 1.0, velocity_set=vlbm.VLBM_D2Q9)
+    assert e.value.code == vlbm.VLBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("args,code", [
+    ((5, 64, 4, 0.1, 1e-3), -1),      # n_theta < 6
+    ((32, 63, 4, 0.1, 1e-3), -1),     # odd n_phi
+    ((32, 64, 4, 0.0, 1e-3), -1),     # tau <= 0
+    ((32, 64, 4, 0.1, -1.0), -1),     # dt <= 0
+    ((32, 64, 7, 0.1, 1e-3), -1),     # unknown velocity set
+    ((32, 64, 3, 0.1, 1e-3), -2),     # D2Q9 reserved
+])
+def test_create_rejects_bad_arguments_before_the_gpu(lib, args, code):
+    from paper_2504_15574_gb300 import vlbm
+    with pytest.raises(vlbm.VlbmError) as e:
+        vlbm.vlbm_create(*args)
+    assert e.value.code == code
+    assert vlbm.vlbm_last_error()
+
+
+def test_null_handles_are_argument_errors(lib):
+    import ctypes
+    assert lib.vlbm_step(None, 1) == -1
+    assert lib.vlbm_moments(None, None, None, None, None) == -1
+    lib.vlbm_destroy(None)   # NULL-safe
