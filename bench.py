@@ -48,7 +48,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    return ap.parse_args()
+    # profiling only (ncu captures of a smaller grid); the benchmark line uses the defaults
+    ap.add_argument("--n-theta", type=int, default=1024)
+    ap.add_argument("--n-phi", type=int, default=2048)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    args = ap.parse_args()
+    global NT, NP, DT
+    NT, NP = args.n_theta, args.n_phi
+    DT = 0.25 * (math.pi / NT) / VMAX
+    return args
 
 
 def dist_info():
@@ -219,7 +227,7 @@ def run_ours(args):
 
     if rank == 0:
         cpu = None
-        if world == 1 and os.environ.get("VLBM_BENCH_NO_CPU", "0") != "1":
+        if world == 1 and not args.no_cpu:
             val, el, cores = oracle_sample(2, 0)
             cpu = {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                    "sample": f"2 full RK3 steps of the 1024x2048 workload ({el:.1f} s)"}
@@ -228,7 +236,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_theta": NT, "n_phi": NP, "Q": 16, "global_batch": world,
+            "config": {"workload": WORKLOAD.replace("1024x2048", f"{NT}x{NP}"), "n_theta": NT, "n_phi": NP,
+                       "Q": 16, "global_batch": world,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (three 134 MB population arrays per replica)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

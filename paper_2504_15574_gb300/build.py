@@ -21,7 +21,10 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libvlbm.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no FMA contraction either (aarch64 g++ contracts by default), so the FP64
+# tables equal an uncontracted evaluation of the same formulas on any host
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+          "-Xcompiler", "-ffp-contract=off",
           "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 UNITS = {
     "vlbm_api.cu": [],
