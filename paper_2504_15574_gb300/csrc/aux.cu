@@ -32,8 +32,7 @@ __device__ __forceinline__ void ghost_source(const Layout &L, int k, int r, int 
     cs = cc;
 }
 
-template <typename T>
-__global__ void fill_ghosts_kernel(T *f, const Layout L)
+__global__ void fill_ghosts_kernel(double *f, const Layout L)
 {
     const int c = (int)(blockIdx.x * blockDim.x + threadIdx.x) - GC;
     const int r = (int)blockIdx.y - GR;
@@ -62,29 +61,12 @@ __global__ void unpack_f64_kernel(const double *dense, const Layout L, double *f
     f[L.at(k, i, j)] = dense[((size_t)k * L.nt + i) * L.np + j];
 }
 
-__global__ void pack_f32_kernel(const float *f, const Layout L, double *dense, const VelD c, double rho_ref)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y, k = blockIdx.z;
-    if (j >= L.np) return;
-    dense[((size_t)k * L.nt + i) * L.np + j] = c.w[k / 4] * c.w[k % 4] * rho_ref + (double)f[L.at(k, i, j)];
-}
-
-__global__ void unpack_f32_kernel(const double *dense, const Layout L, float *f, const VelD c, double rho_ref)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y, k = blockIdx.z;
-    if (j >= L.np) return;
-    f[L.at(k, i, j)] = (float)(dense[((size_t)k * L.nt + i) * L.np + j] - c.w[k / 4] * c.w[k % 4] * rho_ref);
-}
-
 constexpr int DIAG_THREADS = 256;
 constexpr int NDIAG = 6;
 
 // One block per row: partial sums of the row in a fixed order.
-template <typename T>
-__global__ void diag_rows_kernel(const T *f, const Layout L, const double *sin_t, const double *cos_t, const VelD c,
-                                 double area, double rho_ref, double *part)
+__global__ void diag_rows_kernel(const double *f, const Layout L, const double *sin_t, const double *cos_t, const VelD c,
+                                 double area, double *part)
 {
     const int i = blockIdx.x;
     const double st = sin_t[i], ct = cos_t[i];
@@ -97,8 +79,7 @@ __global__ void diag_rows_kernel(const T *f, const Layout L, const double *sin_t
         double n = 0.0, jt = 0.0, jp = 0.0, e = 0.0, bad = 0.0;
         for (int k = 0; k < NK; ++k) {
             const double va = c.v[k / 4], vb = c.v[k % 4];
-            double fk = (double)f[L.at(k, i, j)];
-            if (rho_ref != 0.0) fk = c.w[k / 4] * c.w[k % 4] * rho_ref + fk;
+            const double fk = f[L.at(k, i, j)];
             if (!isfinite(fk)) bad = 1.0;
             n += fk;
             jt += fk * va;
@@ -143,9 +124,8 @@ __global__ void diag_final_kernel(const double *part, int nrows, double *out)
 }
 
 template <typename T>
-__global__ void guard_kernel(const T *f, const Layout L, unsigned *flag)
+__global__ void guard_kernel(const T *f, size_t total, unsigned *flag)
 {
-    const size_t total = (size_t)NK * L.plane;
     bool bad = false;
     for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (size_t)gridDim.x * blockDim.x) {
         const T v = f[x];
@@ -185,13 +165,7 @@ __global__ void pole_budget_kernel(const double *pole3, int np, double R, double
 void launch_fill_ghosts_f64(double *f, const Layout &L, cudaStream_t s)
 {
     dim3 grid((L.np + 2 * GC + 127) / 128, L.nt + 2 * GR, NK);
-    fill_ghosts_kernel<double><<<grid, 128, 0, s>>>(f, L);
-}
-
-void launch_fill_ghosts_f32(float *f, const Layout &L, cudaStream_t s)
-{
-    dim3 grid((L.np + 2 * GC + 127) / 128, L.nt + 2 * GR, NK);
-    fill_ghosts_kernel<float><<<grid, 128, 0, s>>>(f, L);
+    fill_ghosts_kernel<<<grid, 128, 0, s>>>(f, L);
 }
 
 void launch_pack_f64(const double *f, const Layout &L, double *dense, cudaStream_t s)
@@ -206,44 +180,28 @@ void launch_unpack_f64(const double *dense, const Layout &L, double *f, cudaStre
     unpack_f64_kernel<<<grid, 128, 0, s>>>(dense, L, f);
 }
 
-void launch_pack_f32(const float *f, const Layout &L, double *dense, const VelD &c, double rho_ref, cudaStream_t s)
-{
-    dim3 grid((L.np + 127) / 128, L.nt, NK);
-    pack_f32_kernel<<<grid, 128, 0, s>>>(f, L, dense, c, rho_ref);
-}
-
-void launch_unpack_f32(const double *dense, const Layout &L, float *f, const VelD &c, double rho_ref,
-                       cudaStream_t s)
-{
-    dim3 grid((L.np + 127) / 128, L.nt, NK);
-    unpack_f32_kernel<<<grid, 128, 0, s>>>(dense, L, f, c, rho_ref);
-}
-
 size_t diag_partials(const Layout &L) { return (size_t)NDIAG * L.nt; }
 
 void launch_diagnostics_f64(const double *f, const Layout &L, const double *sin_t, const double *cos_t,
                             const VelD &c, double area, double *part, double *out, cudaStream_t s)
 {
-    diag_rows_kernel<double><<<L.nt, DIAG_THREADS, 0, s>>>(f, L, sin_t, cos_t, c, area, 0.0, part);
+    diag_rows_kernel<<<L.nt, DIAG_THREADS, 0, s>>>(f, L, sin_t, cos_t, c, area, part);
     diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(part, L.nt, out);
 }
 
-void launch_diagnostics_f32(const float *f, const Layout &L, const double *sin_t, const double *cos_t,
-                            const VelD &c, double area, double rho_ref, double *part, double *out,
-                            cudaStream_t s)
+void launch_diag_final(const double *part, int nrows, double *out, cudaStream_t s)
 {
-    diag_rows_kernel<float><<<L.nt, DIAG_THREADS, 0, s>>>(f, L, sin_t, cos_t, c, area, rho_ref, part);
-    diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(part, L.nt, out);
+    diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(part, nrows, out);
 }
 
-void launch_guard_f64(const double *f, const Layout &L, unsigned *flag, cudaStream_t s)
+void launch_guard_f64(const double *f, size_t n, unsigned *flag, cudaStream_t s)
 {
-    guard_kernel<double><<<152 * 8, 256, 0, s>>>(f, L, flag);
+    guard_kernel<double><<<152 * 8, 256, 0, s>>>(f, n, flag);
 }
 
-void launch_guard_f32(const float *f, const Layout &L, unsigned *flag, cudaStream_t s)
+void launch_guard_f32(const float *f, size_t n, unsigned *flag, cudaStream_t s)
 {
-    guard_kernel<float><<<152 * 8, 256, 0, s>>>(f, L, flag);
+    guard_kernel<float><<<152 * 8, 256, 0, s>>>(f, n, flag);
 }
 
 void launch_pole_budget(const double *pole3, int np, double R, double dph, double dt, double *budget,

@@ -1,31 +1,34 @@
-// stage_f32.cu -- FP32 deviation-storage RK3 stage, the throughput path.
+// stage_f32.cu -- FP32 deviation-storage path (the throughput path).
 //
-// Computes one SSP-RK3 stage (arXiv 2504.15574 Sec. 3.7) of the vLBM operator
-// L[f] (Eq. Lf) for a tile of TY x TX cells and all 16 populations:
-//   1. one TMA box brings the stage input (16 planes x (TY+6) x (TX+8), ghost
-//      rows and columns included by the storage layout) into shared memory;
-//   2. the phi-face WENO-5 fluxes (Eqs. fluxes_W5, WENO5_delta, WENO5_sigma)
-//      of all 16 populations are computed once per face into shared memory;
-//   3. the tile is scaled in place by sin(theta) (the theta flux is a
-//      finite-difference WENO on g = sin(theta) f, Eq. discrete_advection_sphere)
-//      and the theta-face fluxes are computed once per face;
-//   4. each thread takes one cell: moments (Eq. f_moments_sum), equilibrium
-//      (Eq. feq_Q=4), BGK (Sec. 3.2), force through K^H / Ktilde^H (Eq. df),
-//      flux differences, and the stage combination; the result is written to
-//      the cell and to its ghost images.
+// State.  The device array holds dg = sin(theta) (f - w_k rho_ref) in FP32: the
+// deviation from the reference state w_k rho_ref (rho_ref an FP64 constant),
+// premultiplied by sin(theta) so that the stage input is directly the nodal
+// variable of the theta flux (arXiv 2504.15574 Eq. discrete_advection_sphere, read
+// as a finite-difference WENO on g = sin(theta) f).  Populations are stored in
+// pairs: pair p = 4 g + b holds populations (a = 2g, b) and (a = 2g + 1, b) as one
+// float2, so that both members share the sign of v_theta and the value of v_phi
+// and every per-population operation runs as one packed f32x2 instruction.
+// Layout of vlbm_internal.h with 8 pair planes of float2 elements.  Pole ghost
+// rows hold -dg of the mirrored pair with swapped members (the ghost's sine is
+// negative, Eq. bcs_theta maps v -> -v); ghost columns hold periodic images.
 //
-// Storage is the deviation delta f = f - w_k rho_ref.  The reference state
-// w_k rho_ref is uniform in phi, so the phi fluxes of f and delta f differ by a
-// constant that cancels in the flux difference.  In theta, the WENO weights are
-// those of the full g = sin(theta) (w_k rho_ref + delta f): every linear form of
-// the stencil is the delta-f part plus w_k rho_ref times the same form of
-// sin(theta), precomputed in FP64 per face.  The reconstruction is written as
-//   ghat = P2 + wbar1 (P1 - P2) + wbar3 (P3 - P2),
-// whose reference part splits into the ideal-weight interpolant of sin(theta)
-// (its flux difference, and the force of the reference state, are folded into
-// the FP64-derived per-row tendency rref) and a correction proportional to the
-// deviation of the weights from the ideal ones.  The result equals the method
-// on f up to FP32 rounding of deviation-sized quantities.
+// One stage (Sec. 3.7) of L[f] (Eq. Lf) per kernel launch, for a tile of TY x TX
+// cells and all 16 populations:
+//   1. one TMA box (8 pair planes x (TY+6) x (TX+8) float2) into shared memory;
+//   2. phi faces and theta faces of all pairs, each face once, into shared memory
+//      (WENO-5, Eqs. fluxes_W5, WENO5_delta, WENO5_sigma).  On dg the phi weights
+//      use eps sin^2(theta) (the WENO weights are invariant under g -> s g with
+//      eps -> s^2 eps), and the theta weights are those of the full
+//      g = sin(theta) w_k rho_ref + dg: each smoothness form is the dg part plus
+//      w_k rho_ref times the form of sin(theta) (FP64 table).  The reconstruction
+//      is written P2 + wbar1 (P1 - P2) + wbar3 (P3 - P2); its reference part is
+//      the ideal-weight interpolant (folded, with the force of the reference
+//      state, into the FP64-derived tendency rref) minus corr, plus the weight
+//      terms, which use the full forms;
+//   3. per cell: moments (Eq. f_moments_sum), equilibrium (Eq. feq_Q=4), BGK,
+//      force through K^H / Ktilde^H (Eq. df), flux differences and the stage
+//      combination, all on dg (the operator commutes with the row factor), then
+//      the store of the cell and of its ghost images.
 #include "vlbm_internal.h"
 
 namespace vk {
@@ -34,24 +37,42 @@ namespace {
 
 constexpr int TY = F32_TILE_ROWS;
 constexpr int TX = F32_TILE_COLS;
-constexpr int SR = TY + 2 * GR;     // shared-memory rows of the tile
-constexpr int SC = TX + 2 * GC;     // shared-memory columns of the tile
-constexpr int NT = TY * TX;         // threads per CTA, one cell each in the cell phase
-constexpr int NFT = NK * (TY + 1) * TX;
-constexpr int NFP = NK * TY * (TX + 1);
-constexpr unsigned TILE_BYTES = NK * SR * SC * sizeof(float);
+constexpr int NP2 = 8;                 // population pairs
+constexpr int SR = TY + 2 * GR;        // tile rows in shared memory
+constexpr int SC = TX + 2 * GC;        // tile columns in shared memory
+constexpr int NT = TY * TX;            // threads per CTA
+constexpr unsigned TILE_BYTES = NP2 * SR * SC * sizeof(float2);
+static_assert(NT == 256 && TX == 32 && TY == 8, "the face loops assume 8 warps x 32 lanes");
 
 struct __align__(128) Smem {
-    float tile[NK][SR][SC];
-    float ft[NK][TY + 1][TX];
-    float fp[NK][TY][TX + 1];
+    float2 tile[NP2][SR][SC];
+    float2 ft[NP2][TY + 1][TX];       // theta faces: face fy between cell rows fy-1 and fy
+    float2 fp[NP2][TY][TX + 1];       // phi faces: face fx between cell columns fx-1 and fx
     unsigned long long bar;
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void *p)
+typedef float2 f2;
+
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
 {
-    return (unsigned)__cvta_generic_to_shared(p);
+    unsigned long long x = *reinterpret_cast<unsigned long long *>(&a), y = *reinterpret_cast<unsigned long long *>(&b), d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+    return *reinterpret_cast<f2 *>(&d);
 }
+__device__ __forceinline__ f2 splat(float x) { return make_float2(x, x); }
+__device__ __forceinline__ f2 swap2(f2 a) { return make_float2(a.y, a.x); }
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns()
 {
@@ -60,12 +81,12 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Waits on phase 0 of an mbarrier for at most limit_ns; returns false on timeout.
-__device__ __forceinline__ bool wait_tile(unsigned long long *bar, unsigned long long limit_ns)
+// Waits on phase 0 of an mbarrier for at most limit_ns; false on timeout.
+__device__ __forceinline__ bool wait_phase0(unsigned long long *bar, unsigned long long limit_ns)
 {
-    unsigned done = 0;
     unsigned long long t0 = 0;
     for (unsigned it = 0;; ++it) {
+        unsigned done;
         asm volatile(
             "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
             : "=r"(done)
@@ -80,64 +101,59 @@ __device__ __forceinline__ bool wait_tile(unsigned long long *bar, unsigned long
     }
 }
 
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
+// Stencil linear forms on upwind-ordered values a..e (packed pairs).
+struct Forms { f2 p2, A1, B1, A2, B2, A3, B3; };
 
-// Weighted WENO-5 combination from the stencil's linear forms.
-//   a..e upwind-ordered values; A_i, B_i the smoothness forms, p2 the central
-//   candidate.  Returns p2 + wbar1 (A1 - A2)/3 + wbar3 (A2 - A3)/6 and the
-//   normalised weights wbar1, wbar3.
-__device__ __forceinline__ float weno_combine(float p2, float A1, float B1, float A2, float B2, float A3,
-                                              float B3, float eps, float &w1n, float &w3n)
+__device__ __forceinline__ Forms forms(f2 a, f2 b, f2 c, f2 d, f2 e)
 {
-    const float c13 = 13.0f / 12.0f;
-    float s1 = fmaf(A1 * c13, A1, fmaf(B1 * 0.25f, B1, eps));
-    float s2 = fmaf(A2 * c13, A2, fmaf(B2 * 0.25f, B2, eps));
-    float s3 = fmaf(A3 * c13, A3, fmaf(B3 * 0.25f, B3, eps));
-    float q1 = s1 * s1, q2 = s2 * s2, q3 = s3 * s3;
-    float t1 = 0.1f * (q2 * q3);   // delta_1 / q1 scaled by q1 q2 q3
-    float t2 = 0.6f * (q1 * q3);
-    float t3 = 0.3f * (q1 * q2);
-    float r = rcp_approx(t1 + t2 + t3);
-    w1n = t1 * r;
-    w3n = t3 * r;
-    return fmaf(w1n, (A1 - A2) * (1.0f / 3.0f), fmaf(w3n, (A2 - A3) * (1.0f / 6.0f), p2));
-}
-
-// Linear forms of an upwind-ordered stencil.
-struct Forms { float p2, A1, B1, A2, B2, A3, B3; };
-__device__ __forceinline__ Forms forms(float a, float b, float c, float d, float e)
-{
+    const f2 m2 = splat(-2.0f), m4 = splat(-4.0f), p3 = splat(3.0f);
     Forms F;
-    F.A1 = fmaf(-2.0f, b, a) + c;
-    F.B1 = fmaf(3.0f, c, fmaf(-4.0f, b, a));
-    F.A2 = fmaf(-2.0f, c, b) + d;
-    F.B2 = b - d;
-    F.A3 = fmaf(-2.0f, d, c) + e;
-    F.B3 = fmaf(3.0f, c, fmaf(-4.0f, d, e));
-    // p2 = (-b + 5c + 2d)/6
-    F.p2 = fmaf(5.0f / 6.0f, c, fmaf(1.0f / 3.0f, d, b * (-1.0f / 6.0f)));
+    F.A1 = fma2(m2, b, add2(a, c));
+    F.B1 = fma2(p3, c, fma2(m4, b, a));
+    F.A2 = fma2(m2, c, add2(b, d));
+    F.B2 = sub2(b, d);
+    F.A3 = fma2(m2, d, add2(c, e));
+    F.B3 = fma2(p3, c, fma2(m4, d, e));
+    // P2 = (-b + 5c + 2d) / 6
+    F.p2 = fma2(splat(5.0f / 6.0f), c, fma2(splat(1.0f / 3.0f), d, mul2(splat(-1.0f / 6.0f), b)));
     return F;
 }
 
-__device__ __forceinline__ void store_images(float *f, const Layout &L, int k, int i, int j, float v)
+// P2 + wbar1 (A1 - A2)/3 + wbar3 (A2 - A3)/6 with wbar_i = d_i q_j q_k / sum,
+// q_i = (sigma_i + eps)^2, sigma_i = 13/12 A_i^2 + 1/4 B_i^2.
+__device__ __forceinline__ f2 weno_combine(const Forms &F, f2 eps)
 {
-    const int np = L.np;
-    auto put_row = [&](int kk, int r, int c) {
-        f[L.at(kk, r, c)] = v;
-        for (int m = 1; c - m * np >= -GC; ++m) f[L.at(kk, r, c - m * np)] = v;
-        for (int m = 1; c + m * np < np + GC; ++m) f[L.at(kk, r, c + m * np)] = v;
-    };
-    put_row(k, i, j);
+    const f2 c13 = splat(13.0f / 12.0f), c14 = splat(0.25f);
+    const f2 s1 = fma2(mul2(F.A1, c13), F.A1, fma2(mul2(F.B1, c14), F.B1, eps));
+    const f2 s2 = fma2(mul2(F.A2, c13), F.A2, fma2(mul2(F.B2, c14), F.B2, eps));
+    const f2 s3 = fma2(mul2(F.A3, c13), F.A3, fma2(mul2(F.B3, c14), F.B3, eps));
+    const f2 q1 = mul2(s1, s1), q2 = mul2(s2, s2), q3 = mul2(s3, s3);
+    const f2 q23 = mul2(q2, q3), q12 = mul2(q1, q2);
+    const f2 sum = fma2(splat(0.1f), q23, fma2(splat(0.6f), mul2(q1, q3), mul2(splat(0.3f), q12)));
+    const f2 r = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
+    // 0.1/3 q23 (A1 - A2) + 0.3/6 q12 (A2 - A3)
+    const f2 num = fma2(mul2(splat(0.1f / 3.0f), q23), sub2(F.A1, F.A2), mul2(mul2(splat(0.05f), q12), sub2(F.A2, F.A3)));
+    return fma2(num, r, F.p2);
+}
+
+// Writes v at pair-plane cell (p, i, j) and at its ghost images.
+__device__ __forceinline__ void put_cols(f2 *f, const Layout &L, int p, int r, int c, f2 v)
+{
+    f[L.at(p, r, c)] = v;
+    for (int m = 1; c - m * L.np >= -GC; ++m) f[L.at(p, r, c - m * L.np)] = v;
+    for (int m = 1; c + m * L.np < L.np + GC; ++m) f[L.at(p, r, c + m * L.np)] = v;
+}
+
+__device__ __forceinline__ int image_pair(int p) { return 4 * (1 - (p >> 2)) + (3 - (p & 3)); }
+
+__device__ __forceinline__ void store_images(f2 *f, const Layout &L, int p, int i, int j, f2 v)
+{
+    put_cols(f, L, p, i, j, v);
     if (i < GR || i >= L.nt - GR) {
-        int jj = j + np / 2;
-        if (jj >= np) jj -= np;
-        int r = (i < GR) ? (-1 - i) : (2 * L.nt - 1 - i);
-        put_row(NK - 1 - k, r, jj);
+        int jj = j + L.np / 2;
+        if (jj >= L.np) jj -= L.np;
+        const int r = (i < GR) ? (-1 - i) : (2 * L.nt - 1 - i);
+        put_cols(f, L, image_pair(p), r, jj, make_float2(-v.y, -v.x));
     }
 }
 
@@ -146,11 +162,11 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const int q0 = blockIdx.x * TX;
     const int i0 = blockIdx.y * TY;
     const Layout L = p.L;
 
-    // ---- 1. TMA load of the tile (rows i0-3 .. i0+TY+2, columns q0-4 .. q0+TX+3)
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -165,122 +181,355 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
             : "memory");
     }
     __syncthreads();
-    if (!wait_tile(&S.bar, 1000000000ull)) {
-        // the copy did not complete within 1 s: flag it, give the copy one more
-        // bounded second to land in this CTA's shared memory, then leave
+    if (!wait_phase0(&S.bar, 1000000000ull)) {
+        // the copy did not complete within 1 s: flag it, give it one more bounded
+        // second to land in this CTA's shared memory, then leave
         if (tid == 0) atomicOr(p.err, 1u);
-        wait_tile(&S.bar, 1000000000ull);
+        wait_phase0(&S.bar, 1000000000ull);
         return;
     }
 
-    // ---- 2. phi faces: face fx lies between tile columns fx-1 and fx (fx = 0..TX)
-    const float eps = p.eps;
-    for (int e = tid; e < NFP; e += NT) {
-        const int k = e / (TY * (TX + 1));
-        const int rem = e - k * (TY * (TX + 1));
-        const int fy = rem / (TX + 1);
-        const int fx = rem - fy * (TX + 1);
-        const float vb = p.c.v[k & 3];
-        const float *row = &S.tile[k][fy + GR][0];
-        // v > 0: columns fx-3 .. fx+1 ; v < 0: columns fx+2 .. fx-2 (smem column = column + GC)
-        const int base = (vb > 0.0f) ? (fx + GC - 3) : (fx + GC + 2);
-        const int st = (vb > 0.0f) ? 1 : -1;
-        Forms F = forms(row[base], row[base + st], row[base + 2 * st], row[base + 3 * st], row[base + 4 * st]);
-        float w1, w3;
-        const float gh = weno_combine(F.p2, F.A1, F.B1, F.A2, F.B2, F.A3, F.B3, eps, w1, w3);
-        S.fp[k][fy][fx] = vb * gh;
+    // ---- phi faces: warp = cell row fy, lane = face fx (west face of column fx)
+    {
+        const int fy = warp;
+        const int irow = min(i0 + fy, L.nt - 1);
+        const f2 eps = splat(p.row[irow].eps_s2);
+#pragma unroll 2
+        for (int q = 0; q < NP2; ++q) {
+            const float vb = p.c.vphi[q & 3];
+            const f2 *row = &S.tile[q][fy + GR][0];
+            Forms F;
+            if (vb > 0.0f) {   // columns fx-3 .. fx+1  (shared column = column + GC)
+                F = forms(row[lane + 1], row[lane + 2], row[lane + 3], row[lane + 4], row[lane + 5]);
+            } else {           // columns fx+2 .. fx-2
+                F = forms(row[lane + 6], row[lane + 5], row[lane + 4], row[lane + 3], row[lane + 2]);
+            }
+            S.fp[q][fy][lane] = mul2(splat(vb), weno_combine(F, eps));
+        }
+        // east face of the last column: 64 (pair, row) combinations on 2 warps
+        if (tid < NP2 * TY) {
+            const int q = tid >> 3, ry = tid & 7;
+            const int ir = min(i0 + ry, L.nt - 1);
+            const float vb = p.c.vphi[q & 3];
+            const f2 *row = &S.tile[q][ry + GR][0];
+            const int fx = TX;
+            Forms F = (vb > 0.0f) ? forms(row[fx + 1], row[fx + 2], row[fx + 3], row[fx + 4], row[fx + 5])
+                                  : forms(row[fx + 6], row[fx + 5], row[fx + 4], row[fx + 3], row[fx + 2]);
+            S.fp[q][ry][fx] = mul2(splat(vb), weno_combine(F, splat(p.row[ir].eps_s2)));
+        }
     }
 
-    // own-cell deviations, read before the tile is rescaled
-    const int cy = tid / TX, cx = tid - (tid / TX) * TX;
-    float df[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) df[k] = S.tile[k][cy + GR][cx + GC];
-    __syncthreads();
-
-    // ---- 3. g = sin(theta) delta f in place, then theta faces
-    for (int e = tid; e < NK * SR * (SC / 4); e += NT) {
-        const int r = (e / (SC / 4)) % SR;
-        const float s = p.sin_ext[i0 + r];
-        float4 *q = reinterpret_cast<float4 *>(&S.tile[0][0][0]) + e;
-        float4 x = *q;
-        x.x *= s; x.y *= s; x.z *= s; x.w *= s;
-        *q = x;
-    }
-    __syncthreads();
-    for (int e = tid; e < NFT; e += NT) {
-        const int k = e / ((TY + 1) * TX);
-        const int rem = e - k * ((TY + 1) * TX);
-        const int fy = rem / TX;
-        const int fx = rem - fy * TX;
-        const float va = p.c.v[k >> 2];
-        const int dir = (va > 0.0f) ? 0 : 1;
-        // v > 0: rows fy-3 .. fy+1 ; v < 0: rows fy+2 .. fy-2 (smem row = row + GR)
-        const int base = (dir == 0) ? (fy + GR - 3) : (fy + GR + 2);
-        const int st = (dir == 0) ? 1 : -1;
-        const float *col = &S.tile[k][0][fx + GC];
-        Forms F = forms(col[base * SC], col[(base + st) * SC], col[(base + 2 * st) * SC],
-                        col[(base + 3 * st) * SC], col[(base + 4 * st) * SC]);
-        int fi = i0 + fy;
-        if (fi > L.nt) fi = L.nt;
-        const FaceConst fc = p.face[2 * fi + dir];
-        const float wr = p.c.wr[k];
-        float w1, w3;
-        const float gh = weno_combine(F.p2, fmaf(wr, fc.sa1, F.A1), fmaf(wr, fc.sb1, F.B1),
-                                      fmaf(wr, fc.sa2, F.A2), fmaf(wr, fc.sb2, F.B2), fmaf(wr, fc.sa3, F.A3),
-                                      fmaf(wr, fc.sb3, F.B3), eps, w1, w3);
-        // the reference part of P2 is the ideal-weight interpolant minus corr
-        S.ft[k][fy][fx] = va * fmaf(-wr, fc.corr, gh);
+    // ---- theta faces: 72 (pair, face row) combinations, 9 per warp; lane = column
+    {
+        const f2 eps = splat(p.eps);
+#pragma unroll 1
+        for (int it = 0; it < 9; ++it) {
+            const int c = warp + 8 * it;
+            const int q = c / 9, fy = c - 9 * (c / 9);
+            const int g = q >> 2;
+            const int fi = min(i0 + fy, L.nt);
+            const FaceConst fc = p.face[2 * fi + (g ? 0 : 1)];
+            const f2 wr = p.c.wr[q];
+            const f2 *col = &S.tile[q][0][lane + GC];
+            Forms F;
+            if (g) {   // v_theta > 0: rows fy-3 .. fy+1 (shared row = row + GR)
+                F = forms(col[(fy + 0) * SC], col[(fy + 1) * SC], col[(fy + 2) * SC], col[(fy + 3) * SC],
+                          col[(fy + 4) * SC]);
+            } else {   // v_theta < 0: rows fy+2 .. fy-2
+                F = forms(col[(fy + 5) * SC], col[(fy + 4) * SC], col[(fy + 3) * SC], col[(fy + 2) * SC],
+                          col[(fy + 1) * SC]);
+            }
+            F.A1 = fma2(wr, splat(fc.sa1), F.A1);
+            F.B1 = fma2(wr, splat(fc.sb1), F.B1);
+            F.A2 = fma2(wr, splat(fc.sa2), F.A2);
+            F.B2 = fma2(wr, splat(fc.sb2), F.B2);
+            F.A3 = fma2(wr, splat(fc.sa3), F.A3);
+            F.B3 = fma2(wr, splat(fc.sb3), F.B3);
+            F.p2 = fma2(wr, splat(-fc.corr), F.p2);
+            S.ft[q][fy][lane] = mul2(p.c.vth[g], weno_combine(F, eps));
+        }
     }
     __syncthreads();
 
-    // ---- 4. one cell per thread
+    // ---- one cell per thread: warp = cell row, lane = column
+    const int cy = warp, cx = lane;
     const int i = i0 + cy, j = q0 + cx;
     if (i >= L.nt || j >= L.np) return;
-    float dn = 0.0f, jt = 0.0f, jp = 0.0f;
+    const RowF rc = p.row[i];
+    f2 G[NP2];
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        dn += df[k];
-        jt = fmaf(df[k], p.c.v[k >> 2], jt);
-        jp = fmaf(df[k], p.c.v[k & 3], jp);
+    for (int q = 0; q < NP2; ++q) G[q] = S.tile[q][cy + GR][cx + GC];
+    // moments of delta f = dg / s
+    f2 sn = G[0], sjt = mul2(p.c.vth[0], G[0]), sjp = mul2(splat(p.c.vphi[0]), G[0]);
+#pragma unroll
+    for (int q = 1; q < NP2; ++q) {
+        sn = add2(sn, G[q]);
+        sjt = fma2(p.c.vth[q >> 2], G[q], sjt);
+        sjp = fma2(splat(p.c.vphi[q & 3]), G[q], sjp);
     }
-    const float n = p.c.rho_ref + dn;
-    const float ninv = 1.0f / n;
-    const float ut = jt * ninv, up = jp * ninv;
+    const float SG = sn.x + sn.y;                         // sum_k dg_k = s dn
+    const float n = fmaf(SG, rc.inv_s, p.c.rho_ref);
+    const float nin = 1.0f / n;
+    const float ut = (sjt.x + sjt.y) * rc.inv_s * nin;
+    const float up = (sjp.x + sjp.y) * rc.inv_s * nin;
     const float u2 = fmaf(ut, ut, up * up);
-    const RowConst rc = p.row[i];
-    const float *rr = p.rref + (size_t)i * NK;
+    const float sn_n = rc.s * n;
+    const f2 h0 = splat(-0.5f * u2), h1 = splat(fmaf(-0.5f, u2, 1.0f));
+    const f2 *rr = p.rref + (size_t)i * NP2;
 
+    f2 out[NP2];
 #pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        const int a = k >> 2, b = k & 3;
-        const float va = p.c.v[a], vb = p.c.v[b];
-        const float wk = p.c.w[a] * p.c.w[b];
-        const float xi = fmaf(va, ut, vb * up);
-        const float poly = xi + 0.5f * fmaf(xi, xi, -u2) + xi * fmaf(xi, xi, -3.0f * u2) * (1.0f / 6.0f);
-        const float dfeq = wk * fmaf(n, poly, dn);
-        float kg = 0.0f, ktg = 0.0f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            kg = fmaf(p.c.K[a * 4 + m], df[4 * m + b], kg);
-            ktg = fmaf(p.c.Kt[b * 4 + m], df[4 * a + m], ktg);
-        }
-        const float force = rc.cotR * fmaf(vb * vb, kg, -va * ktg);
-        const float adv_t = (S.ft[k][cy][cx] - S.ft[k][cy + 1][cx]) * rc.inv_dth;
-        const float adv_p = (S.fp[k][cy][cx] - S.fp[k][cy][cx + 1]) * rc.inv_dph;
-        const float Lk = (adv_t + adv_p) - force - (df[k] - dfeq) * p.tau_inv + rr[k];
-        float outv;
+    for (int q = 0; q < NP2; ++q) {
+        const int g = q >> 2, b = q & 3;
+        const f2 vt = p.c.vth[g];
+        const float vb = p.c.vphi[b];
+        // equilibrium deviation times s: w (s dn + s n poly(xi)), poly = xi + (xi^2-u^2)/2 + xi(xi^2-3u^2)/6
+        const f2 xi = fma2(vt, splat(ut), splat(vb * up));
+        const f2 poly = fma2(xi, fma2(xi, fma2(xi, splat(1.0f / 6.0f), splat(0.5f)), h1), h0);
+        const f2 sfeq = mul2(p.c.w2[q], fma2(splat(sn_n), poly, splat(SG)));
+        // force on dg: K along k_theta (pairs (0,b),(1,b) and (2,b),(3,b), with swapped partners), Ktilde along k_phi
+        const f2 P0 = G[b], P1 = G[4 + b];
+        const f2 *kc = p.c.kpair[g];
+        const f2 kg = fma2(kc[0], P0, fma2(kc[1], swap2(P0), fma2(kc[2], P1, mul2(kc[3], swap2(P1)))));
+        const float *kt = p.c.Kt + 4 * b;
+        const f2 *Gg = G + 4 * g;
+        const f2 ktg = fma2(splat(kt[0]), Gg[0], fma2(splat(kt[1]), Gg[1], fma2(splat(kt[2]), Gg[2], mul2(splat(kt[3]), Gg[3]))));
+        const f2 force = mul2(splat(rc.cotR), fma2(splat(vb * vb), kg, mul2(p.c.mvth[g], ktg)));
+        // flux differences
+        const f2 adv_t = mul2(sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]), splat(p.inv_dth));
+        const f2 adv_p = mul2(sub2(S.fp[q][cy][cx], S.fp[q][cy][cx + 1]), splat(rc.inv_dph));
+        // L on dg: advection - force - (dg - s feq_dev)/tau + s rref
+        f2 Lq = sub2(add2(add2(adv_t, adv_p), rr[q]), force);
+        Lq = fma2(sub2(G[q], sfeq), splat(-p.tau_inv), Lq);
         if (p.stage == 1) {
-            outv = fmaf(p.dt, Lk, df[k]);
-        } else if (p.stage == 2) {
-            const float f0 = p.fold[L.at(k, i, j)];
-            outv = fmaf(0.25f * p.dt, Lk, fmaf(0.75f, f0, 0.25f * df[k]));
+            out[q] = fma2(splat(p.dt), Lq, G[q]);
         } else {
-            const float f0 = p.fold[L.at(k, i, j)];
-            outv = fmaf((2.0f / 3.0f) * p.dt, Lk, fmaf(1.0f / 3.0f, f0, (2.0f / 3.0f) * df[k]));
+            const f2 f0 = p.fold[L.at(q, i, j)];
+            if (p.stage == 2)
+                out[q] = fma2(splat(0.25f * p.dt), Lq, fma2(splat(0.75f), f0, mul2(splat(0.25f), G[q])));
+            else
+                out[q] = fma2(splat((2.0f / 3.0f) * p.dt), Lq, fma2(splat(1.0f / 3.0f), f0, mul2(splat(2.0f / 3.0f), G[q])));
         }
-        store_images(p.out, L, k, i, j, outv);
     }
+    const bool plain = (i >= GR && i < L.nt - GR && j >= GC && j < L.np - GC);
+    if (plain) {
+#pragma unroll
+        for (int q = 0; q < NP2; ++q) p.out[L.at(q, i, j)] = out[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < NP2; ++q) store_images(p.out, L, q, i, j, out[q]);
+    }
+}
+
+// ---- FP32 layout helpers (FP64 arithmetic) -----------------------------------------
+
+__device__ __forceinline__ double finit64(double n, double wk, double va, double vb, double ut, double up, double T)
+{
+    const double xi = va * ut + vb * up;
+    const double u2 = ut * ut + up * up;
+    if (T == 1.0) return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
+    const double v2 = va * va + vb * vb;
+    const double dT = T - 1.0;
+    const double second = xi * xi - u2 + dT * (v2 - 2.0);
+    const double third = xi * (xi * xi - 3.0 * u2) + 3.0 * dT * xi * (v2 - 4.0);
+    return n * wk * (1.0 + xi + 0.5 * second + third / 6.0);
+}
+
+// population k = 4a + b lives in pair 4 (a/2) + b, member a % 2
+__device__ __forceinline__ int pair_of(int k) { return 4 * ((k >> 2) >> 1) + (k & 3); }
+__device__ __forceinline__ int member_of(int k) { return (k >> 2) & 1; }
+
+__global__ void init_f32_kernel(f2 *f, const Layout L, const double *rho, const double *ut, const double *up,
+                                const double *temp, const VelD c, double rho_ref, const double *sin_t)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= L.np) return;
+    const size_t cell = (size_t)i * L.np + j;
+    const double tt = temp ? temp[cell] : 1.0;
+    const double s = sin_t[i];
+    float v[16];
+    for (int k = 0; k < NK; ++k) {
+        const int a = k / 4, b = k % 4;
+        const double wk = c.w[a] * c.w[b];
+        v[k] = (float)(s * (finit64(rho[cell], wk, c.v[a], c.v[b], ut[cell], up[cell], tt) - wk * rho_ref));
+    }
+    for (int q = 0; q < NP2; ++q) {
+        const int g = q >> 2, b = q & 3;
+        f[L.at(q, i, j)] = make_float2(v[4 * (2 * g) + b], v[4 * (2 * g + 1) + b]);
+    }
+}
+
+__global__ void moments_f32_kernel(const f2 *f, const Layout L, double *rho, double *ut, double *up, double *temp,
+                                   const VelD c, double rho_ref, const double *sin_t)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= L.np) return;
+    const double inv_s = 1.0 / sin_t[i];
+    double fk[NK];
+    for (int k = 0; k < NK; ++k) {
+        const f2 pr = f[L.at(pair_of(k), i, j)];
+        const double d = (double)(member_of(k) ? pr.y : pr.x) * inv_s;
+        fk[k] = c.w[k / 4] * c.w[k % 4] * rho_ref + d;
+    }
+    double n = 0.0, jt = 0.0, jp = 0.0;
+    for (int k = 0; k < NK; ++k) {
+        n += fk[k];
+        jt += fk[k] * c.v[k / 4];
+        jp += fk[k] * c.v[k % 4];
+    }
+    const size_t cell = (size_t)i * L.np + j;
+    const double u1 = jt / n, u2 = jp / n;
+    rho[cell] = n;
+    ut[cell] = u1;
+    up[cell] = u2;
+    if (temp) {
+        double e = 0.0;
+        for (int k = 0; k < NK; ++k) {
+            const double ct = c.v[k / 4] - u1, cp = c.v[k % 4] - u2;
+            e += fk[k] * (ct * ct + cp * cp);
+        }
+        temp[cell] = e / (2.0 * n);
+    }
+}
+
+__global__ void pack_f32_kernel(const f2 *f, const Layout L, double *dense, const VelD c, double rho_ref,
+                                const double *sin_t)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y, k = blockIdx.z;
+    if (j >= L.np) return;
+    const f2 pr = f[L.at(pair_of(k), i, j)];
+    const double d = (double)(member_of(k) ? pr.y : pr.x) / sin_t[i];
+    dense[((size_t)k * L.nt + i) * L.np + j] = c.w[k / 4] * c.w[k % 4] * rho_ref + d;
+}
+
+__global__ void unpack_f32_kernel(const double *dense, const Layout L, f2 *f, const VelD c, double rho_ref,
+                                  const double *sin_t)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y, q = blockIdx.z;
+    if (j >= L.np) return;
+    const int g = q >> 2, b = q & 3;
+    float m[2];
+    for (int h = 0; h < 2; ++h) {
+        const int a = 2 * g + h, k = 4 * a + b;
+        m[h] = (float)(sin_t[i] * (dense[((size_t)k * L.nt + i) * L.np + j] - c.w[a] * c.w[b] * rho_ref));
+    }
+    f[L.at(q, i, j)] = make_float2(m[0], m[1]);
+}
+
+__global__ void fill_ghosts_f32_kernel(f2 *f, const Layout L)
+{
+    const int c = (int)(blockIdx.x * blockDim.x + threadIdx.x) - GC;
+    const int r = (int)blockIdx.y - GR;
+    const int q = blockIdx.z;
+    if (c >= L.np + GC) return;
+    if (r >= 0 && r < L.nt && c >= 0 && c < L.np) return;
+    int rs = r, qs = q, shift = 0;
+    bool pole = false;
+    if (r < 0) {
+        rs = -1 - r;
+        pole = true;
+    } else if (r >= L.nt) {
+        rs = 2 * L.nt - 1 - r;
+        pole = true;
+    }
+    if (pole) {
+        qs = image_pair(q);
+        shift = L.np / 2;
+    }
+    int cc = (c + shift) % L.np;
+    if (cc < 0) cc += L.np;
+    const f2 v = f[L.at(qs, rs, cc)];
+    f[L.at(q, r, c)] = pole ? make_float2(-v.y, -v.x) : v;
+}
+
+// Polar ring filter, one CTA per (filtered row, pair plane): the mean over each
+// aligned block of b columns, summed in FP64 (slices of 32 columns, then the
+// slices in order), written to the block's cells and their ghost images.
+__global__ void filter_f32_kernel(f2 *f, const Layout L, const int *rows, const int *blocks)
+{
+    const int i = rows[blockIdx.x];
+    const int b = blocks[blockIdx.x];
+    const int q = blockIdx.y;
+    const int nblk = L.np / b;
+    const int slices = (b + 31) / 32;
+    __shared__ double2 part[256];
+    for (int base = 0; base < nblk * slices; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const bool live = t < nblk * slices;
+        double2 s = make_double2(0.0, 0.0);
+        if (live) {
+            const int blk = t / slices, sl = t - blk * slices;
+            const int j0 = blk * b + sl * 32, j1 = min(j0 + 32, blk * b + b);
+            for (int jj = j0; jj < j1; ++jj) {
+                const f2 v = f[L.at(q, i, jj)];
+                s.x += v.x;
+                s.y += v.y;
+            }
+        }
+        part[threadIdx.x] = s;
+        __syncthreads();
+        // slices of one block are consecutive threads (blockDim is a multiple of slices)
+        if (live && (t % slices) == 0) {
+            double2 tot = make_double2(0.0, 0.0);
+            for (int m = 0; m < slices; ++m) {
+                tot.x += part[threadIdx.x + m].x;
+                tot.y += part[threadIdx.x + m].y;
+            }
+            const int blk = t / slices;
+            const f2 mean = make_float2((float)(tot.x / b), (float)(tot.y / b));
+            for (int jj = blk * b; jj < blk * b + b; ++jj) store_images(f, L, q, i, jj, mean);
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int DIAG_THREADS = 256;
+constexpr int NDIAG = 6;
+
+__global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *sin_t, const double *cos_t,
+                                     const VelD c, double area, double rho_ref, double *part)
+{
+    const int i = blockIdx.x;
+    const double st = sin_t[i], ct = cos_t[i], inv_s = 1.0 / st;
+    const double dph = 6.283185307179586476925286766559 / L.np;
+    double acc[NDIAG] = {0, 0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < L.np; j += DIAG_THREADS) {
+        double sp, cp;
+        sincos((j + 0.5) * dph, &sp, &cp);
+        double n = 0.0, jt = 0.0, jp = 0.0, e = 0.0, bad = 0.0;
+        for (int k = 0; k < NK; ++k) {
+            const double va = c.v[k / 4], vb = c.v[k % 4];
+            const f2 pr = f[L.at(pair_of(k), i, j)];
+            const double d = (double)(member_of(k) ? pr.y : pr.x);
+            if (!isfinite(d)) bad = 1.0;
+            const double fk = c.w[k / 4] * c.w[k % 4] * rho_ref + d * inv_s;
+            n += fk;
+            jt += fk * va;
+            jp += fk * vb;
+            e += fk * (va * va + vb * vb);
+        }
+        const double dA = st * area;
+        acc[0] += n * dA;
+        acc[1] += (jt * ct * cp - jp * sp) * dA;
+        acc[2] += (jt * ct * sp + jp * cp) * dA;
+        acc[3] += (-jt * st) * dA;
+        acc[4] += 0.5 * e * dA;
+        acc[5] += bad;
+    }
+    __shared__ double red[NDIAG][DIAG_THREADS];
+    for (int qq = 0; qq < NDIAG; ++qq) red[qq][threadIdx.x] = acc[qq];
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int qq = 0; qq < NDIAG; ++qq) red[qq][threadIdx.x] += red[qq][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int qq = 0; qq < NDIAG; ++qq) part[(size_t)qq * L.nt + i] = red[qq][0];
 }
 
 }  // namespace
@@ -297,6 +546,54 @@ void launch_stage_f32(const CUtensorMap &tm_in, const StageF &p, cudaStream_t s)
 {
     dim3 grid((p.L.np + TX - 1) / TX, (p.L.nt + TY - 1) / TY);
     stage_f32_kernel<<<grid, NT, stage_f32_smem_bytes(), s>>>(tm_in, p);
+}
+
+void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,
+                     const double *T, const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s)
+{
+    dim3 grid((L.np + 127) / 128, L.nt);
+    init_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref, sin_t);
+}
+
+void launch_moments_f32(const float2 *f, const Layout &L, double *rho, double *ut, double *up, double *T,
+                        const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s)
+{
+    dim3 grid((L.np + 127) / 128, L.nt);
+    moments_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref, sin_t);
+}
+
+void launch_pack_f32(const float2 *f, const Layout &L, double *dense, const VelD &c, double rho_ref,
+                     const double *sin_t, cudaStream_t s)
+{
+    dim3 grid((L.np + 127) / 128, L.nt, NK);
+    pack_f32_kernel<<<grid, 128, 0, s>>>(f, L, dense, c, rho_ref, sin_t);
+}
+
+void launch_unpack_f32(const double *dense, const Layout &L, float2 *f, const VelD &c, double rho_ref,
+                       const double *sin_t, cudaStream_t s)
+{
+    dim3 grid((L.np + 127) / 128, L.nt, NP2);
+    unpack_f32_kernel<<<grid, 128, 0, s>>>(dense, L, f, c, rho_ref, sin_t);
+}
+
+void launch_fill_ghosts_f32(float2 *f, const Layout &L, cudaStream_t s)
+{
+    dim3 grid((L.np + 2 * GC + 127) / 128, L.nt + 2 * GR, NP2);
+    fill_ghosts_f32_kernel<<<grid, 128, 0, s>>>(f, L);
+}
+
+void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s)
+{
+    if (nrows <= 0) return;
+    dim3 grid(nrows, NP2);
+    filter_f32_kernel<<<grid, 256, 0, s>>>(f, L, rows, blocks);
+}
+
+void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,
+                            const VelD &c, double area, double rho_ref, double *part, double *out, cudaStream_t s)
+{
+    diag_rows_f32_kernel<<<L.nt, DIAG_THREADS, 0, s>>>(f, L, sin_t, cos_t, c, area, rho_ref, part);
+    launch_diag_final(part, L.nt, out, s);
 }
 
 }  // namespace vk

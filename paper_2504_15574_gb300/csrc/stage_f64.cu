@@ -245,13 +245,6 @@ void launch_init_f64(double *f, const Layout &L, const double *rho, const double
     init_kernel<double><<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, 0.0);
 }
 
-void launch_init_f32(float *f, const Layout &L, const double *rho, const double *ut, const double *up,
-                     const double *T, const VelD &c, double rho_ref, cudaStream_t s)
-{
-    dim3 grid((L.np + 127) / 128, L.nt);
-    init_kernel<float><<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref);
-}
-
 void launch_moments_f64(const double *f, const Layout &L, double *rho, double *ut, double *up, double *T,
                         const VelD &c, cudaStream_t s)
 {
@@ -259,26 +252,11 @@ void launch_moments_f64(const double *f, const Layout &L, double *rho, double *u
     moments_kernel<double><<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, 0.0);
 }
 
-void launch_moments_f32(const float *f, const Layout &L, double *rho, double *ut, double *up, double *T,
-                        const VelD &c, double rho_ref, cudaStream_t s)
-{
-    dim3 grid((L.np + 127) / 128, L.nt);
-    moments_kernel<float><<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref);
-}
-
 void launch_filter_f64(double *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s)
 {
     if (nrows <= 0) return;
-    dim3 grid((L.np + 127) / 128 > 0 ? 1 : 1, nrows, NK);
-    grid.x = (L.np / 2 + 127) / 128 + 1;
-    filter_kernel<double><<<grid, 128, 0, s>>>(f, L, rows, blocks, nrows);
-}
-
-void launch_filter_f32(float *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s)
-{
-    if (nrows <= 0) return;
     dim3 grid((L.np / 2 + 127) / 128 + 1, nrows, NK);
-    filter_kernel<float><<<grid, 128, 0, s>>>(f, L, rows, blocks, nrows);
+    filter_kernel<double><<<grid, 128, 0, s>>>(f, L, rows, blocks, nrows);
 }
 
 }  // namespace vk

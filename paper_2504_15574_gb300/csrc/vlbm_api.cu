@@ -32,9 +32,9 @@ struct vlbm {
     double *d_sin_ext = nullptr, *d_cot = nullptr, *d_sin_t = nullptr, *d_cos_t = nullptr;
     std::vector<double> sin_t, cos_t;
     // FP32 tables
-    float *d_sin_ext_f = nullptr, *d_rref = nullptr;
+    float2 *d_rref = nullptr;
     FaceConst *d_face = nullptr;
-    RowConst *d_row = nullptr;
+    RowF *d_row = nullptr;
     // polar filter
     int *d_frows = nullptr, *d_fblocks = nullptr;
     int nfrows = 0;
@@ -182,23 +182,32 @@ int dalloc(vlbm_t *h, void **p, size_t bytes)
     return VLBM_OK;
 }
 
-// FP32 tables that depend on rho_ref: per-face sine forms, per-row reference tendency.
+// FP32 tables that depend on rho_ref: packed velocity constants, per-face sine forms,
+// per-row constants and the per-row tendency of the reference state (times sin(theta)).
 int build_f32_tables(vlbm_t *h)
 {
     const int nt = h->nt;
     const double R = h->R, dth = M_PI / nt, dph = 2.0 * M_PI / h->np;
     const VelD &c = h->vd;
     VelF &f = h->vf;
-    for (int a = 0; a < 4; ++a) {
-        f.v[a] = (float)c.v[a];
-        f.w[a] = (float)c.w[a];
+    const double rr = h->rho_ref;
+    for (int g = 0; g < 2; ++g) {
+        f.vth[g] = make_float2((float)c.v[2 * g], (float)c.v[2 * g + 1]);
+        f.mvth[g] = make_float2((float)-c.v[2 * g], (float)-c.v[2 * g + 1]);
+        const int a0 = 2 * g, a1 = 2 * g + 1;
+        f.kpair[g][0] = make_float2((float)c.K[a0 * 4 + 0], (float)c.K[a1 * 4 + 1]);
+        f.kpair[g][1] = make_float2((float)c.K[a0 * 4 + 1], (float)c.K[a1 * 4 + 0]);
+        f.kpair[g][2] = make_float2((float)c.K[a0 * 4 + 2], (float)c.K[a1 * 4 + 3]);
+        f.kpair[g][3] = make_float2((float)c.K[a0 * 4 + 3], (float)c.K[a1 * 4 + 2]);
     }
-    for (int q = 0; q < 16; ++q) {
-        f.K[q] = (float)c.K[q];
-        f.Kt[q] = (float)c.Kt[q];
-        f.wr[q] = (float)(c.w[q / 4] * c.w[q % 4] * h->rho_ref);
+    for (int b = 0; b < 4; ++b) f.vphi[b] = (float)c.v[b];
+    for (int q = 0; q < 8; ++q) {
+        const int g = q / 4, b = q % 4;
+        f.w2[q] = make_float2((float)(c.w[2 * g] * c.w[b]), (float)(c.w[2 * g + 1] * c.w[b]));
+        f.wr[q] = make_float2((float)(c.w[2 * g] * c.w[b] * rr), (float)(c.w[2 * g + 1] * c.w[b] * rr));
     }
-    f.rho_ref = (float)h->rho_ref;
+    for (int q = 0; q < 16; ++q) f.Kt[q] = (float)c.Kt[q];
+    f.rho_ref = (float)rr;
 
     // faces fi = 0..nt between rows fi-1 and fi; upwind-ordered sine stencils
     std::vector<FaceConst> face(2 * (size_t)(nt + 1));
@@ -224,27 +233,37 @@ int build_f32_tables(vlbm_t *h)
             face[2 * fi + dir] = F;
             plin[2 * fi + dir] = (2 * a - 13 * b + 47 * cc + 27 * d - 3 * e) / 60.0;
         }
-    std::vector<RowConst> row(nt);
-    std::vector<float> rref((size_t)nt * 16);
+    std::vector<RowF> row(nt);
+    std::vector<float2> rref((size_t)nt * 8);
     for (int i = 0; i < nt; ++i) {
         const double s = h->sin_t[i], cot = h->cos_t[i] / h->sin_t[i];
-        row[i].inv_dth = (float)(1.0 / (R * s * dth));
-        row[i].inv_dph = (float)(1.0 / (R * s * dph));
-        row[i].cotR = (float)(cot / R);
-        row[i].pad = 0.0f;
+        RowF rc;
+        rc.s = (float)s;
+        rc.inv_s = (float)(1.0 / s);
+        rc.inv_dph = (float)(1.0 / (R * s * dph));
+        rc.cotR = (float)(cot / R);
+        rc.eps_s2 = (float)(h->eps * s * s);
+        rc.pad0 = rc.pad1 = rc.pad2 = 0.0f;
+        row[i] = rc;
+        double rk[16];
         for (int k = 0; k < 16; ++k) {
             const int a = k / 4, b = k % 4;
             const double va = c.v[a], vb = c.v[b];
-            const double wr = c.w[a] * c.w[b] * h->rho_ref;
+            const double wr = c.w[a] * c.w[b] * rr;
             const int dir = va > 0 ? 0 : 1;
+            // theta advection of the reference part with ideal weights, and its force
             const double adv = -va * wr * (plin[2 * (i + 1) + dir] - plin[2 * i + dir]) / (R * s * dth);
             double kw = 0.0, ktw = 0.0;
             for (int m = 0; m < 4; ++m) {
-                kw += c.K[a * 4 + m] * c.w[m] * c.w[b] * h->rho_ref;
-                ktw += c.Kt[b * 4 + m] * c.w[a] * c.w[m] * h->rho_ref;
+                kw += c.K[a * 4 + m] * c.w[m] * c.w[b] * rr;
+                ktw += c.Kt[b * 4 + m] * c.w[a] * c.w[m] * rr;
             }
             const double force = cot / R * (vb * vb * kw - va * ktw);
-            rref[(size_t)i * 16 + k] = (float)(adv - force);
+            rk[k] = s * (adv - force);
+        }
+        for (int q = 0; q < 8; ++q) {
+            const int g = q / 4, b = q % 4;
+            rref[(size_t)i * 8 + q] = make_float2((float)rk[4 * (2 * g) + b], (float)rk[4 * (2 * g + 1) + b]);
         }
     }
     int rc;
@@ -265,11 +284,12 @@ int encode_map(vlbm_t *h, CUtensorMap *m, void *base)
             return fail(h, VLBM_ERR_CUDA, "cuTensorMapEncodeTiled not available from the driver");
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)(h->nt + 2 * GR), (cuuint64_t)NK};
-    cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * sizeof(float), (cuuint64_t)h->L.plane * sizeof(float)};
-    cuuint32_t box[3] = {(cuuint32_t)(F32_TILE_COLS + 2 * GC), (cuuint32_t)(F32_TILE_ROWS + 2 * GR), (cuuint32_t)NK};
+    // pair planes of float2, described as 8-byte elements
+    cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)(h->nt + 2 * GR), (cuuint64_t)(NK / 2)};
+    cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * sizeof(float2), (cuuint64_t)h->L.plane * sizeof(float2)};
+    cuuint32_t box[3] = {(cuuint32_t)(F32_TILE_COLS + 2 * GC), (cuuint32_t)(F32_TILE_ROWS + 2 * GR), (cuuint32_t)(NK / 2)};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+    CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(h, VLBM_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -306,10 +326,9 @@ void enqueue_step(vlbm_t *h, int stage_only = 0)
             if (h->nfrows) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         } else {
             StageF p;
-            p.in = (const float *)in;
-            p.fold = (const float *)h->F;
-            p.out = (float *)out;
-            p.sin_ext = h->d_sin_ext_f;
+            p.in = (const float2 *)in;
+            p.fold = (const float2 *)h->F;
+            p.out = (float2 *)out;
             p.face = h->d_face;
             p.row = h->d_row;
             p.rref = h->d_rref;
@@ -318,11 +337,12 @@ void enqueue_step(vlbm_t *h, int stage_only = 0)
             p.tau_inv = (float)(1.0 / h->tau);
             p.dt = (float)h->dt;
             p.eps = (float)h->eps;
+            p.inv_dth = (float)(1.0 / (h->R * (M_PI / h->nt)));
             p.stage = st;
             p.c = h->vf;
             const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
             launch_stage_f32(tm, p, s);
-            if (h->nfrows) launch_filter_f32((float *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
+            if (h->nfrows) launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         }
     }
     if (!stage_only && h->prec == VLBM_FP64)
@@ -360,7 +380,7 @@ void drop_graphs(vlbm_t *h)
 int after_reset(vlbm_t *h)
 {
     if (h->prec == VLBM_FP64) launch_fill_ghosts_f64((double *)h->F, h->L, h->stream);
-    else launch_fill_ghosts_f32((float *)h->F, h->L, h->stream);
+    else launch_fill_ghosts_f32((float2 *)h->F, h->L, h->stream);
     CK(h, cudaMemsetAsync(h->d_budget, 0, sizeof(double), h->stream));
     CK(h, cudaMemsetAsync(h->d_flags, 0, sizeof(unsigned) * 4, h->stream));
     CK(h, cudaGetLastError());
@@ -475,8 +495,6 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
         (rc = upload(h, &h->d_sin_t, h->sin_t.data(), h->sin_t.size())) ||
         (rc = upload(h, &h->d_cos_t, h->cos_t.data(), h->cos_t.size())))
         return bail(rc);
-    std::vector<float> sextf(sext.begin(), sext.end());
-    if ((rc = upload(h, &h->d_sin_ext_f, sextf.data(), sextf.size()))) return bail(rc);
     // polar filter rows
     if (h->filter) {
         std::vector<int> rows, blocks;
@@ -544,8 +562,8 @@ int vlbm_init_moments(vlbm_t *h, const double *rho, const double *u_theta, const
             if (rc) return rc;
             drop_graphs(h);
         }
-        launch_init_f32((float *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->rho_ref,
-                        h->stream);
+        launch_init_f32((float2 *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->rho_ref,
+                        h->d_sin_t, h->stream);
     }
     CK(h, cudaGetLastError());
     return after_reset(h);
@@ -574,7 +592,7 @@ int vlbm_set_populations(vlbm_t *h, const double *f)
             if (rc) return rc;
             drop_graphs(h);
         }
-        launch_unpack_f32(h->d_dense, h->L, (float *)h->F, h->vd, h->rho_ref, h->stream);
+        launch_unpack_f32(h->d_dense, h->L, (float2 *)h->F, h->vd, h->rho_ref, h->d_sin_t, h->stream);
     }
     CK(h, cudaGetLastError());
     return after_reset(h);
@@ -589,7 +607,7 @@ int vlbm_get_populations(vlbm_t *h, double *f)
         if (rc) return rc;
     }
     if (h->prec == VLBM_FP64) launch_pack_f64((const double *)h->F, h->L, h->d_dense, h->stream);
-    else launch_pack_f32((const float *)h->F, h->L, h->d_dense, h->vd, h->rho_ref, h->stream);
+    else launch_pack_f32((const float2 *)h->F, h->L, h->d_dense, h->vd, h->rho_ref, h->d_sin_t, h->stream);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(f, h->d_dense, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -630,8 +648,8 @@ int vlbm_step(vlbm_t *h, int n)
     int rc = vlbm_step_async(h, n);
     if (rc) return rc;
     if (h->guard && n > 0) {
-        if (h->prec == VLBM_FP64) launch_guard_f64((const double *)h->F, h->L, h->d_flags + 1, h->stream);
-        else launch_guard_f32((const float *)h->F, h->L, h->d_flags + 1, h->stream);
+        if (h->prec == VLBM_FP64) launch_guard_f64((const double *)h->F, NK * h->L.plane, h->d_flags + 1, h->stream);
+        else launch_guard_f32((const float *)h->F, NK * h->L.plane, h->d_flags + 1, h->stream);
         CK(h, cudaGetLastError());
     }
     return vlbm_sync(h);
@@ -645,8 +663,8 @@ int vlbm_moments(vlbm_t *h, double *rho, double *u_theta, double *u_phi, double 
     if (h->prec == VLBM_FP64)
         launch_moments_f64((const double *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->stream);
     else
-        launch_moments_f32((const float *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd,
-                           h->rho_ref, h->stream);
+        launch_moments_f32((const float2 *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd,
+                           h->rho_ref, h->d_sin_t, h->stream);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(u_theta, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -664,8 +682,8 @@ int vlbm_diagnostics(vlbm_t *h, vlbm_diag *out)
         launch_diagnostics_f64((const double *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->vd, area, h->d_part, h->d_diag,
                                h->stream);
     else
-        launch_diagnostics_f32((const float *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->vd, area, h->rho_ref, h->d_part,
-                               h->d_diag, h->stream);
+        launch_diagnostics_f32((const float2 *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->vd, area, h->rho_ref,
+                               h->d_part, h->d_diag, h->stream);
     CK(h, cudaGetLastError());
     double v[8];
     CK(h, cudaMemcpyAsync(v, h->d_diag, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -732,7 +750,7 @@ void vlbm_destroy(vlbm_t *h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
-    void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_sin_ext_f, h->d_rref,
+    void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_rref,
                     h->d_face, h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
                     h->d_part, h->d_diag, h->d_flags};
     for (void *p : bufs)

@@ -35,7 +35,6 @@ struct Layout {
 
 // Velocity-space constants (App. A.2): v ascending, 1-D weights, kernels.
 struct VelD { double v[4], w[4], K[16], Kt[16]; };
-struct VelF { float v[4], w[4], K[16], Kt[16], wr[16]; float rho_ref; };   // wr = w_k rho_ref
 
 // ---- FP64 stage (parity path) -------------------------------------------------
 struct StageD {
@@ -53,22 +52,36 @@ struct StageD {
 void launch_stage_f64(const StageD &p, cudaStream_t s);
 
 // ---- FP32 deviation stage (throughput path) -------------------------------------
+// The FP32 array holds dg = sin(theta) (f - w_k rho_ref) in 8 pair planes of float2:
+// pair p = 4 g + b holds populations (2g, b) and (2g+1, b).
 // Per theta face and upwind direction: the smoothness linear forms of the stencil applied to
 // sin(theta) and corr = 0.1 (P1-P2) + 0.3 (P3-P2) of sin(theta) (ideal-weight interpolant minus P2).
 struct FaceConst { float sa1, sb1, sa2, sb2, sa3, sb3, corr, pad; };
-struct RowConst { float inv_dth, inv_dph, cotR, pad; };            // 1/(R sin dth), 1/(R sin dph), cot/R
+// Per interior row: s = sin(theta), 1/s, 1/(R s dphi), cot(theta)/R, eps s^2.
+struct RowF { float s, inv_s, inv_dph, cotR, eps_s2, pad0, pad1, pad2; };
+// Velocity-space constants as packed pairs (member x: a = 2g, member y: a = 2g+1).
+struct VelF {
+    float2 vth[2];       // (v[2g], v[2g+1])
+    float2 mvth[2];      // -(v[2g], v[2g+1])
+    float vphi[4];       // v[b]
+    float2 w2[8];        // (w[2g] w[b], w[2g+1] w[b])
+    float2 wr[8];        // w2 * rho_ref
+    float2 kpair[2][4];  // K along k_theta as pair coefficients: (K[2g][0],K[2g+1][1]), (K[2g][1],K[2g+1][0]),
+                         // (K[2g][2],K[2g+1][3]), (K[2g][3],K[2g+1][2])
+    float Kt[16];        // Ktilde[b][m]
+    float rho_ref;
+};
 
 struct StageF {
-    const float *in;        // stage input delta g (padded layout) -- read by TMA
-    const float *fold;      // delta f at the start of the step (own cell), stages 2 and 3
-    float *out;
-    const float *sin_ext;   // [nt + 2GR + TILE_ROWS] sin at padded rows, zero beyond
+    const float2 *in;       // stage input dg (read by TMA through the tensor map)
+    const float2 *fold;     // dg at the start of the step (own cell), stages 2 and 3
+    float2 *out;
     const FaceConst *face;  // [nt+1][2]: face between rows fi-1 and fi, dir 0: v>0, 1: v<0
-    const RowConst *row;    // [nt]
-    const float *rref;      // [nt][16] FP64-derived tendency of the reference state w_k rho_ref
+    const RowF *row;        // [nt]
+    const float2 *rref;     // [nt][8] s * (FP64-derived tendency of the reference state)
     unsigned *err;          // device error flag (bit 0: TMA wait timeout)
     Layout L;
-    float tau_inv, dt, eps;
+    float tau_inv, dt, eps, inv_dth;   // inv_dth = 1/(R dtheta)
     int stage;
     VelF c;
 };
@@ -78,41 +91,38 @@ constexpr int F32_TILE_COLS = 32;
 size_t stage_f32_smem_bytes();
 cudaError_t prepare_stage_f32();   // sets the kernel's dynamic shared-memory limit
 
-// ---- shared helpers (FP64 arithmetic, any precision storage) ---------------------
-// Initial populations of moments (rho, ut, up, T) -> padded array (FP64) or
-// deviation array (FP32, minus w_k rho_ref).  T may be NULL.
+void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,
+                     const double *T, const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s);
+void launch_moments_f32(const float2 *f, const Layout &L, double *rho, double *ut, double *up, double *T,
+                        const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s);
+void launch_pack_f32(const float2 *f, const Layout &L, double *dense, const VelD &c, double rho_ref,
+                     const double *sin_t, cudaStream_t s);
+void launch_unpack_f32(const double *dense, const Layout &L, float2 *f, const VelD &c, double rho_ref,
+                       const double *sin_t, cudaStream_t s);
+void launch_fill_ghosts_f32(float2 *f, const Layout &L, cudaStream_t s);
+void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s);
+void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,
+                            const VelD &c, double area, double rho_ref, double *part, double *out, cudaStream_t s);
+
+// ---- FP64 helpers -------------------------------------------------------------------
 void launch_init_f64(double *f, const Layout &L, const double *rho, const double *ut, const double *up,
                      const double *T, const VelD &c, cudaStream_t s);
-void launch_init_f32(float *f, const Layout &L, const double *rho, const double *ut, const double *up,
-                     const double *T, const VelD &c, double rho_ref, cudaStream_t s);
-// Moments (rho, ut, up, T) of a padded FP64 array / FP32 deviation array.
 void launch_moments_f64(const double *f, const Layout &L, double *rho, double *ut, double *up, double *T,
                         const VelD &c, cudaStream_t s);
-void launch_moments_f32(const float *f, const Layout &L, double *rho, double *ut, double *up, double *T,
-                        const VelD &c, double rho_ref, cudaStream_t s);
-// Fill every ghost row / column from the interior.
 void launch_fill_ghosts_f64(double *f, const Layout &L, cudaStream_t s);
-void launch_fill_ghosts_f32(float *f, const Layout &L, cudaStream_t s);
-// Dense [16][nt][np] FP64 <-> padded storage.
 void launch_pack_f64(const double *f, const Layout &L, double *dense, cudaStream_t s);
 void launch_unpack_f64(const double *dense, const Layout &L, double *f, cudaStream_t s);
-void launch_pack_f32(const float *f, const Layout &L, double *dense, const VelD &c, double rho_ref, cudaStream_t s);
-void launch_unpack_f32(const double *dense, const Layout &L, float *f, const VelD &c, double rho_ref,
-                       cudaStream_t s);
 // Polar ring filter (not in the paper): rows listed in `rows` with block sizes `blocks`.
 void launch_filter_f64(double *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s);
-void launch_filter_f32(float *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s);
 // FP64 diagnostics: out[0] mass, [1..3] momentum, [4] energy, [5] non-finite count.
 // `part` is scratch of at least diag_partials(L) doubles.
 size_t diag_partials(const Layout &L);
 void launch_diagnostics_f64(const double *f, const Layout &L, const double *sin_t, const double *cos_t,
                             const VelD &c, double area, double *part, double *out, cudaStream_t s);
-void launch_diagnostics_f32(const float *f, const Layout &L, const double *sin_t, const double *cos_t,
-                            const VelD &c, double area, double rho_ref, double *part, double *out,
-                            cudaStream_t s);
-// Non-finite guard: sets *flag to 1 if any interior population is NaN/Inf.
-void launch_guard_f64(const double *f, const Layout &L, unsigned *flag, cudaStream_t s);
-void launch_guard_f32(const float *f, const Layout &L, unsigned *flag, cudaStream_t s);
+void launch_diag_final(const double *part, int nrows, double *out, cudaStream_t s);
+// Non-finite guard over a whole array of n floats / doubles: sets *flag to 1 on NaN/Inf.
+void launch_guard_f64(const double *f, size_t n, unsigned *flag, cudaStream_t s);
+void launch_guard_f32(const float *f, size_t n, unsigned *flag, cudaStream_t s);
 // Pole mass-flux budget: budget += dt * (m1/6 + m2/6 + 2 m3/3), m_s = -R dph sum (F_south - F_north).
 void launch_pole_budget(const double *pole3, int np, double R, double dph, double dt, double *budget,
                         cudaStream_t s);
