@@ -18,7 +18,8 @@
 //   2. phi faces and theta faces of all pairs, each face once, into shared memory
 //      (WENO-5, Eqs. fluxes_W5, WENO5_delta, WENO5_sigma).  On dg the phi weights
 //      use eps sin^2(theta) (the WENO weights are invariant under g -> s g with
-//      eps -> s^2 eps), and the theta weights are those of the full
+//      eps -> s^2 eps; each (sigma + eps) is evaluated divided by its eps), and
+//      the theta weights are those of the full
 //      g = sin(theta) w_k rho_ref + dg: each smoothness form is the dg part plus
 //      w_k rho_ref times the form of sin(theta) (FP64 table).  The reconstruction
 //      is written P2 + wbar1 (P1 - P2) + wbar3 (P3 - P2); its reference part is
@@ -120,13 +121,16 @@ __device__ __forceinline__ Forms forms(f2 a, f2 b, f2 c, f2 d, f2 e)
 }
 
 // P2 + wbar1 (A1 - A2)/3 + wbar3 (A2 - A3)/6 with wbar_i = d_i q_j q_k / sum,
-// q_i = (sigma_i + eps)^2, sigma_i = 13/12 A_i^2 + 1/4 B_i^2.
-__device__ __forceinline__ f2 weno_combine(const Forms &F, f2 eps)
+// q_i = (sigma_i + eps)^2, sigma_i = 13/12 A_i^2 + 1/4 B_i^2.  The weights are
+// ratios, so every (sigma_i + eps) is evaluated divided by eps (kinv = 1/eps):
+// then q_i >= 1 and the products q_j q_k neither underflow (eps sin^2 reaches
+// 1e-12 at the pole rows) nor overflow for sigma_i up to ~1e9 eps.
+__device__ __forceinline__ f2 weno_combine(const Forms &F, float kinv)
 {
-    const f2 c13 = splat(13.0f / 12.0f), c14 = splat(0.25f);
-    const f2 s1 = fma2(mul2(F.A1, c13), F.A1, fma2(mul2(F.B1, c14), F.B1, eps));
-    const f2 s2 = fma2(mul2(F.A2, c13), F.A2, fma2(mul2(F.B2, c14), F.B2, eps));
-    const f2 s3 = fma2(mul2(F.A3, c13), F.A3, fma2(mul2(F.B3, c14), F.B3, eps));
+    const f2 c13 = splat((13.0f / 12.0f) * kinv), c14 = splat(0.25f * kinv), one = splat(1.0f);
+    const f2 s1 = fma2(mul2(F.A1, c13), F.A1, fma2(mul2(F.B1, c14), F.B1, one));
+    const f2 s2 = fma2(mul2(F.A2, c13), F.A2, fma2(mul2(F.B2, c14), F.B2, one));
+    const f2 s3 = fma2(mul2(F.A3, c13), F.A3, fma2(mul2(F.B3, c14), F.B3, one));
     const f2 q1 = mul2(s1, s1), q2 = mul2(s2, s2), q3 = mul2(s3, s3);
     const f2 q23 = mul2(q2, q3), q12 = mul2(q1, q2);
     const f2 sum = fma2(splat(0.1f), q23, fma2(splat(0.6f), mul2(q1, q3), mul2(splat(0.3f), q12)));
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
     {
         const int fy = warp;
         const int irow = min(i0 + fy, L.nt - 1);
-        const f2 eps = splat(p.row[irow].eps_s2);
+        const float kinv = p.row[irow].kphi;
 #pragma unroll 2
         for (int q = 0; q < NP2; ++q) {
             const float vb = p.c.vphi[q & 3];
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
             } else {           // columns fx+2 .. fx-2
                 F = forms(row[lane + 6], row[lane + 5], row[lane + 4], row[lane + 3], row[lane + 2]);
             }
-            S.fp[q][fy][lane] = mul2(splat(vb), weno_combine(F, eps));
+            S.fp[q][fy][lane] = mul2(splat(vb), weno_combine(F, kinv));
         }
         // east face of the last column: 64 (pair, row) combinations on 2 warps
         if (tid < NP2 * TY) {
@@ -215,13 +219,13 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
             const int fx = TX;
             Forms F = (vb > 0.0f) ? forms(row[fx + 1], row[fx + 2], row[fx + 3], row[fx + 4], row[fx + 5])
                                   : forms(row[fx + 6], row[fx + 5], row[fx + 4], row[fx + 3], row[fx + 2]);
-            S.fp[q][ry][fx] = mul2(splat(vb), weno_combine(F, splat(p.row[ir].eps_s2)));
+            S.fp[q][ry][fx] = mul2(splat(vb), weno_combine(F, p.row[ir].kphi));
         }
     }
 
     // ---- theta faces: 72 (pair, face row) combinations, 9 per warp; lane = column
     {
-        const f2 eps = splat(p.eps);
+        const float kinv = p.ktheta;
 #pragma unroll 1
         for (int it = 0; it < 9; ++it) {
             const int c = warp + 8 * it;
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
             F.A3 = fma2(wr, splat(fc.sa3), F.A3);
             F.B3 = fma2(wr, splat(fc.sb3), F.B3);
             F.p2 = fma2(wr, splat(-fc.corr), F.p2);
-            S.ft[q][fy][lane] = mul2(p.c.vth[g], weno_combine(F, eps));
+            S.ft[q][fy][lane] = mul2(p.c.vth[g], weno_combine(F, kinv));
         }
     }
     __syncthreads();

@@ -242,7 +242,7 @@ int build_f32_tables(vlbm_t *h)
         rc.inv_s = (float)(1.0 / s);
         rc.inv_dph = (float)(1.0 / (R * s * dph));
         rc.cotR = (float)(cot / R);
-        rc.eps_s2 = (float)(h->eps * s * s);
+        rc.kphi = (float)(1.0 / (h->eps * s * s));
         rc.pad0 = rc.pad1 = rc.pad2 = 0.0f;
         row[i] = rc;
         double rk[16];
@@ -336,7 +336,7 @@ void enqueue_step(vlbm_t *h, int stage_only = 0)
             p.L = h->L;
             p.tau_inv = (float)(1.0 / h->tau);
             p.dt = (float)h->dt;
-            p.eps = (float)h->eps;
+            p.ktheta = (float)(1.0 / h->eps);
             p.inv_dth = (float)(1.0 / (h->R * (M_PI / h->nt)));
             p.stage = st;
             p.c = h->vf;

@@ -57,8 +57,8 @@ void launch_stage_f64(const StageD &p, cudaStream_t s);
 // Per theta face and upwind direction: the smoothness linear forms of the stencil applied to
 // sin(theta) and corr = 0.1 (P1-P2) + 0.3 (P3-P2) of sin(theta) (ideal-weight interpolant minus P2).
 struct FaceConst { float sa1, sb1, sa2, sb2, sa3, sb3, corr, pad; };
-// Per interior row: s = sin(theta), 1/s, 1/(R s dphi), cot(theta)/R, eps s^2.
-struct RowF { float s, inv_s, inv_dph, cotR, eps_s2, pad0, pad1, pad2; };
+// Per interior row: s = sin(theta), 1/s, 1/(R s dphi), cot(theta)/R, 1/(eps s^2).
+struct RowF { float s, inv_s, inv_dph, cotR, kphi, pad0, pad1, pad2; };
 // Velocity-space constants as packed pairs (member x: a = 2g, member y: a = 2g+1).
 struct VelF {
     float2 vth[2];       // (v[2g], v[2g+1])
@@ -81,7 +81,7 @@ struct StageF {
     const float2 *rref;     // [nt][8] s * (FP64-derived tendency of the reference state)
     unsigned *err;          // device error flag (bit 0: TMA wait timeout)
     Layout L;
-    float tau_inv, dt, eps, inv_dth;   // inv_dth = 1/(R dtheta)
+    float tau_inv, dt, ktheta, inv_dth;   // ktheta = 1/eps, inv_dth = 1/(R dtheta)
     int stage;
     VelF c;
 };
