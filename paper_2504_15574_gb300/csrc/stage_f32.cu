@@ -223,34 +223,68 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
         }
     }
 
-    // ---- theta faces: 72 (pair, face row) combinations, 9 per warp; lane = column
+    // ---- theta faces: warp = pair, lane = column, marching over the TY+1 face rows.
+    // Consecutive faces share their second differences (the smoothness forms of the
+    // three candidate stencils are centred on consecutive rows), so each step adds
+    // one new row.  With x the tile column (rows 0..SR-1), for v > 0 face fy uses
+    // x[fy..fy+4] in upwind order, for v < 0 it uses x[fy+5..fy+1].
     {
+        const int q = warp, g = q >> 2;
         const float kinv = p.ktheta;
-#pragma unroll 1
-        for (int it = 0; it < 9; ++it) {
-            const int c = warp + 8 * it;
-            const int q = c / 9, fy = c - 9 * (c / 9);
-            const int g = q >> 2;
-            const int fi = min(i0 + fy, L.nt);
-            const FaceConst fc = p.face[2 * fi + (g ? 0 : 1)];
-            const f2 wr = p.c.wr[q];
-            const f2 *col = &S.tile[q][0][lane + GC];
-            Forms F;
-            if (g) {   // v_theta > 0: rows fy-3 .. fy+1 (shared row = row + GR)
-                F = forms(col[(fy + 0) * SC], col[(fy + 1) * SC], col[(fy + 2) * SC], col[(fy + 3) * SC],
-                          col[(fy + 4) * SC]);
-            } else {   // v_theta < 0: rows fy+2 .. fy-2
-                F = forms(col[(fy + 5) * SC], col[(fy + 4) * SC], col[(fy + 3) * SC], col[(fy + 2) * SC],
-                          col[(fy + 1) * SC]);
+        const f2 c13 = splat((13.0f / 12.0f) * kinv), c14 = splat(0.25f * kinv), one = splat(1.0f);
+        const f2 wr = p.c.wr[q];
+        const f2 vt = p.c.vth[g];
+        const f2 *col = &S.tile[q][0][lane + GC];
+        const float *dsin = p.dsin + i0;     // first differences of sin at tile rows
+        const float *d2sin = p.d2sin + i0;   // second differences of sin at tile rows
+        // dd[r] = x[r] - x[r-1] (deviation), df[r] = full g difference, D2[r] full second difference
+        f2 x[SR], dd[SR], dfu[SR], D2[SR], Qp[SR];
+#pragma unroll
+        for (int r = 0; r < SR; ++r) x[r] = col[r * SC];
+#pragma unroll
+        for (int r = 1; r < SR; ++r) {
+            dd[r] = sub2(x[r], x[r - 1]);
+            dfu[r] = fma2(wr, splat(dsin[r]), dd[r]);
+        }
+#pragma unroll
+        for (int r = 1; r < SR - 1; ++r) {
+            D2[r] = fma2(wr, splat(d2sin[r]), sub2(dd[r + 1], dd[r]));
+            Qp[r] = fma2(mul2(D2[r], c13), D2[r], one);
+        }
+        const f2 two = splat(2.0f), m2 = splat(-2.0f);
+        const FaceConst *fcp = p.face + 2 * i0 + (g ? 0 : 1);
+#pragma unroll
+        for (int fy = 0; fy <= TY; ++fy) {
+            const float corr = fcp[2 * min(fy, L.nt - i0)].corr;
+            f2 B1, B2, B3, Q1, Q2, Q3, d12, d23, p2;
+            if (g) {   // v_theta > 0: a..e = x[fy..fy+4]
+                Q1 = Qp[fy + 1]; Q2 = Qp[fy + 2]; Q3 = Qp[fy + 3];
+                B1 = fma2(two, dfu[fy + 2], D2[fy + 1]);
+                B2 = add2(dfu[fy + 2], dfu[fy + 3]);
+                B3 = fma2(m2, dfu[fy + 3], D2[fy + 3]);
+                d12 = sub2(D2[fy + 1], D2[fy + 2]);
+                d23 = sub2(D2[fy + 2], D2[fy + 3]);
+                p2 = fma2(splat(1.0f / 6.0f), dd[fy + 2], fma2(splat(1.0f / 3.0f), dd[fy + 3], x[fy + 2]));
+            } else {   // v_theta < 0: a..e = x[fy+5..fy+1]
+                Q1 = Qp[fy + 4]; Q2 = Qp[fy + 3]; Q3 = Qp[fy + 2];
+                B1 = fma2(m2, dfu[fy + 4], D2[fy + 4]);
+                B2 = add2(dfu[fy + 4], dfu[fy + 3]);
+                B3 = fma2(two, dfu[fy + 3], D2[fy + 2]);
+                d12 = sub2(D2[fy + 4], D2[fy + 3]);
+                d23 = sub2(D2[fy + 3], D2[fy + 2]);
+                p2 = fma2(splat(-1.0f / 6.0f), dd[fy + 4], fma2(splat(-1.0f / 3.0f), dd[fy + 3], x[fy + 3]));
             }
-            F.A1 = fma2(wr, splat(fc.sa1), F.A1);
-            F.B1 = fma2(wr, splat(fc.sb1), F.B1);
-            F.A2 = fma2(wr, splat(fc.sa2), F.A2);
-            F.B2 = fma2(wr, splat(fc.sb2), F.B2);
-            F.A3 = fma2(wr, splat(fc.sa3), F.A3);
-            F.B3 = fma2(wr, splat(fc.sb3), F.B3);
-            F.p2 = fma2(wr, splat(-fc.corr), F.p2);
-            S.ft[q][fy][lane] = mul2(p.c.vth[g], weno_combine(F, kinv));
+            const f2 s1 = fma2(mul2(B1, c14), B1, Q1);
+            const f2 s2 = fma2(mul2(B2, c14), B2, Q2);
+            const f2 s3 = fma2(mul2(B3, c14), B3, Q3);
+            const f2 q1 = mul2(s1, s1), q2 = mul2(s2, s2), q3 = mul2(s3, s3);
+            const f2 q23 = mul2(q2, q3), q12 = mul2(q1, q2);
+            const f2 sum = fma2(splat(0.1f), q23, fma2(splat(0.6f), mul2(q1, q3), mul2(splat(0.3f), q12)));
+            const f2 rr = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
+            const f2 num = fma2(mul2(splat(0.1f / 3.0f), q23), d12, mul2(mul2(splat(0.05f), q12), d23));
+            // the reference part of P2 is the ideal-weight interpolant minus corr
+            const f2 gh = fma2(num, rr, fma2(wr, splat(-corr), p2));
+            S.ft[q][fy][lane] = mul2(vt, gh);
         }
     }
     __syncthreads();
@@ -259,7 +293,17 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
     const int cy = warp, cx = lane;
     const int i = i0 + cy, j = q0 + cx;
     if (i >= L.nt || j >= L.np) return;
+    // start the global loads of the step's own-cell start values and row tables early
+    f2 F0[NP2];
+    if (p.stage != 1) {
+#pragma unroll
+        for (int q = 0; q < NP2; ++q) F0[q] = p.fold[L.at(q, i, j)];
+    }
     const RowF rc = p.row[i];
+    const f2 *rr = p.rref + (size_t)i * NP2;
+    f2 R0[NP2];
+#pragma unroll
+    for (int q = 0; q < NP2; ++q) R0[q] = rr[q];
     f2 G[NP2];
 #pragma unroll
     for (int q = 0; q < NP2; ++q) G[q] = S.tile[q][cy + GR][cx + GC];
@@ -279,7 +323,6 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
     const float u2 = fmaf(ut, ut, up * up);
     const float sn_n = rc.s * n;
     const f2 h0 = splat(-0.5f * u2), h1 = splat(fmaf(-0.5f, u2, 1.0f));
-    const f2 *rr = p.rref + (size_t)i * NP2;
 
     f2 out[NP2];
 #pragma unroll
@@ -303,12 +346,12 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
         const f2 adv_t = mul2(sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]), splat(p.inv_dth));
         const f2 adv_p = mul2(sub2(S.fp[q][cy][cx], S.fp[q][cy][cx + 1]), splat(rc.inv_dph));
         // L on dg: advection - force - (dg - s feq_dev)/tau + s rref
-        f2 Lq = sub2(add2(add2(adv_t, adv_p), rr[q]), force);
+        f2 Lq = sub2(add2(add2(adv_t, adv_p), R0[q]), force);
         Lq = fma2(sub2(G[q], sfeq), splat(-p.tau_inv), Lq);
         if (p.stage == 1) {
             out[q] = fma2(splat(p.dt), Lq, G[q]);
         } else {
-            const f2 f0 = p.fold[L.at(q, i, j)];
+            const f2 f0 = F0[q];
             if (p.stage == 2)
                 out[q] = fma2(splat(0.25f * p.dt), Lq, fma2(splat(0.75f), f0, mul2(splat(0.25f), G[q])));
             else

@@ -33,6 +33,7 @@ struct vlbm {
     std::vector<double> sin_t, cos_t;
     // FP32 tables
     float2 *d_rref = nullptr;
+    float *d_dsin = nullptr, *d_d2sin = nullptr;
     FaceConst *d_face = nullptr;
     RowF *d_row = nullptr;
     // polar filter
@@ -266,7 +267,19 @@ int build_f32_tables(vlbm_t *h)
             rref[(size_t)i * 8 + q] = make_float2((float)rk[4 * (2 * g) + b], (float)rk[4 * (2 * g + 1) + b]);
         }
     }
+    // differences of sin at padded rows (pr-1, pr, pr+1 inside [0, nt + 2GR))
+    const int npr = nt + 2 * GR + F32_TILE_ROWS;
+    std::vector<float> ds(npr, 0.0f), d2s(npr, 0.0f);
+    for (int pr = 0; pr < npr; ++pr) {
+        if (pr >= 1 && pr < nt + 2 * GR)
+            ds[pr] = (float)(sin_padded(h->sin_t, nt, pr) - sin_padded(h->sin_t, nt, pr - 1));
+        if (pr >= 1 && pr + 1 < nt + 2 * GR)
+            d2s[pr] = (float)(sin_padded(h->sin_t, nt, pr - 1) - 2.0 * sin_padded(h->sin_t, nt, pr) +
+                              sin_padded(h->sin_t, nt, pr + 1));
+    }
     int rc;
+    if ((rc = upload(h, &h->d_dsin, ds.data(), ds.size()))) return rc;
+    if ((rc = upload(h, &h->d_d2sin, d2s.data(), d2s.size()))) return rc;
     if ((rc = upload(h, &h->d_face, face.data(), face.size()))) return rc;
     if ((rc = upload(h, &h->d_row, row.data(), row.size()))) return rc;
     if ((rc = upload(h, &h->d_rref, rref.data(), rref.size()))) return rc;
@@ -332,6 +345,8 @@ void enqueue_step(vlbm_t *h, int stage_only = 0)
             p.face = h->d_face;
             p.row = h->d_row;
             p.rref = h->d_rref;
+            p.dsin = h->d_dsin;
+            p.d2sin = h->d_d2sin;
             p.err = h->d_flags;
             p.L = h->L;
             p.tau_inv = (float)(1.0 / h->tau);
@@ -750,7 +765,7 @@ void vlbm_destroy(vlbm_t *h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
-    void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_rref,
+    void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_rref, h->d_dsin, h->d_d2sin,
                     h->d_face, h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
                     h->d_part, h->d_diag, h->d_flags};
     for (void *p : bufs)

@@ -79,6 +79,8 @@ struct StageF {
     const FaceConst *face;  // [nt+1][2]: face between rows fi-1 and fi, dir 0: v>0, 1: v<0
     const RowF *row;        // [nt]
     const float2 *rref;     // [nt][8] s * (FP64-derived tendency of the reference state)
+    const float *dsin;      // [nt + 2GR + TY] sin(pr) - sin(pr-1) at padded row pr (0 where undefined)
+    const float *d2sin;     // [nt + 2GR + TY] sin(pr-1) - 2 sin(pr) + sin(pr+1)
     unsigned *err;          // device error flag (bit 0: TMA wait timeout)
     Layout L;
     float tau_inv, dt, ktheta, inv_dth;   // ktheta = 1/eps, inv_dth = 1/(R dtheta)
