@@ -75,6 +75,7 @@ typedef struct vlbm_options {
     void *stream;       /* cudaStream_t to run on, or NULL for a stream the handle creates */
     double rho_ref;     /* VLBM_FP32 only: reference density of the deviation storage;
                            <= 0 means the area-weighted mean of the initial rho; default 0 */
+    int tile_rows;      /* VLBM_FP32 only: rows per stage tile, 4 or 8 (0: 8); tiles are 32 columns wide */
 } vlbm_options;
 
 /* Diagnostics in FP64 (not in the paper).  Area element R^2 sin(theta) dtheta dphi. */
@@ -159,6 +160,46 @@ VLBM_API const char *vlbm_last_error(const vlbm_t *h);
 
 /* Frees the handle and its device memory.  NULL-safe. */
 VLBM_API void vlbm_destroy(vlbm_t *h);
+
+/* ---- Batched ensembles (not in the paper) ----------------------------------------
+ * Many independent FP32 runs of uneven grid sizes, advanced together: one
+ * persistent kernel launch per RK3 stage walks the (run, tile) work items of all
+ * runs, and vlbm_batch_step captures its step loop as a CUDA graph.  Every run
+ * follows the same method and numerics as a VLBM_FP32 solver (the batch is a
+ * scheduling of the same stage, not a different method). */
+typedef struct vlbm_batch vlbm_batch_t;
+
+/* Creates nruns FP32 solvers; arrays of length nruns give each run's grid, tau
+ * and dt (same constraints as vlbm_create).  opt->precision must be VLBM_FP32
+ * (VLBM_ERR_UNSUPPORTED otherwise); opt->stream is the batch's stream. */
+VLBM_API int vlbm_batch_create(int nruns, const int *n_theta, const int *n_phi, const double *tau,
+                               const double *dt, const vlbm_options *opt, vlbm_batch_t **out);
+/* Initial moments of run `run` (as vlbm_init_moments).  Every run must be
+ * initialised before the first step. */
+VLBM_API int vlbm_batch_init_moments(vlbm_batch_t *b, int run, const double *rho, const double *u_theta,
+                                     const double *u_phi, const double *T);
+/* Advances every run n steps (graph-launched) and waits; the guard (if enabled)
+ * checks all runs once per call.  _async enqueues without waiting. */
+VLBM_API int vlbm_batch_step(vlbm_batch_t *b, int n);
+VLBM_API int vlbm_batch_step_async(vlbm_batch_t *b, int n);
+VLBM_API int vlbm_batch_sync(vlbm_batch_t *b);
+/* Moments of run `run` (as vlbm_moments). */
+VLBM_API int vlbm_batch_moments(vlbm_batch_t *b, int run, double *rho, double *u_theta, double *u_phi, double *T);
+/* Launch schedule: tile rows (4 or 8; tiles are 32 columns wide) and persistent CTAs
+ * per SM (0: the occupancy limit). */
+VLBM_API int vlbm_batch_set_schedule(vlbm_batch_t *b, int tile_rows, int ctas_per_sm);
+/* Autotuner: times every schedule (tile rows x CTAs per SM) on the batch's own
+ * state, restores the state, and applies the fastest.  With cache_path != NULL the
+ * result is looked up in / stored to that JSON file, keyed by GPU and grid mix.
+ * Outputs (each may be NULL): chosen tile rows, CTAs per SM, ms per step. */
+VLBM_API int vlbm_batch_tune(vlbm_batch_t *b, const char *cache_path, int *tile_rows, int *ctas_per_sm,
+                             double *ms_per_step);
+/* Times n graph-launched steps with CUDA events on the batch stream. */
+VLBM_API int vlbm_batch_profile(vlbm_batch_t *b, int n, double *ms_per_step, int *launches_per_step);
+/* Total cells over all runs. */
+VLBM_API size_t vlbm_batch_cells(const vlbm_batch_t *b);
+VLBM_API const char *vlbm_batch_last_error(const vlbm_batch_t *b);
+VLBM_API void vlbm_batch_destroy(vlbm_batch_t *b);
 
 #ifdef __cplusplus
 }

@@ -36,19 +36,21 @@ namespace vk {
 
 namespace {
 
-constexpr int TY = F32_TILE_ROWS;
 constexpr int TX = F32_TILE_COLS;
 constexpr int NP2 = 8;                 // population pairs
-constexpr int SR = TY + 2 * GR;        // tile rows in shared memory
 constexpr int SC = TX + 2 * GC;        // tile columns in shared memory
-constexpr int NT = TY * TX;            // threads per CTA
-constexpr unsigned TILE_BYTES = NP2 * SR * SC * sizeof(float2);
-static_assert(NT == 256 && TX == 32 && TY == 8, "the face loops assume 8 warps x 32 lanes");
 
-struct __align__(128) Smem {
-    float2 tile[NP2][SR][SC];
-    float2 ft[NP2][TY + 1][TX];       // theta faces: face fy between cell rows fy-1 and fy
-    float2 fp[NP2][TY][TX + 1];       // phi faces: face fx between cell columns fx-1 and fx
+template <int TY>
+struct __align__(128) SmemT {
+    float2 tile[NP2][TY + 2 * GR][SC];  // TMA destination (must stay first)
+    float2 ft[NP2][TY + 1][TX];         // theta faces: face fy between cell rows fy-1 and fy
+    float2 fp[NP2][TY][TX + 1];         // phi faces: face fx between cell columns fx-1 and fx
+    float2 ds2[TY + 2 * GR];            // (dsin, dsin) at the tile rows
+    float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
+    float2 cw[NP2][TY + 1];             // -w rho_ref corr per pair and theta face row
+    float2 rr[TY][NP2];                 // s rref per cell row and pair
+    RowF rowc[TY];
+    RunF run;                           // batch kernel: this tile's run
     unsigned long long bar;
 };
 
@@ -82,16 +84,16 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Waits on phase 0 of an mbarrier for at most limit_ns; false on timeout.
-__device__ __forceinline__ bool wait_phase0(unsigned long long *bar, unsigned long long limit_ns)
+// Waits for the mbarrier phase with the given parity for at most limit_ns; false on timeout.
+__device__ __forceinline__ bool wait_phase(unsigned long long *bar, unsigned parity, unsigned long long limit_ns)
 {
     unsigned long long t0 = 0;
     for (unsigned it = 0;; ++it) {
         unsigned done;
         asm volatile(
-            "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], 0; selp.u32 %0, 1, 0, P; }"
+            "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
             : "=r"(done)
-            : "r"(smem_u32(bar))
+            : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
         if ((it & 255u) == 0u) {
@@ -161,19 +163,27 @@ __device__ __forceinline__ void store_images(f2 *f, const Layout &L, int p, int 
     }
 }
 
-__global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant__ CUtensorMap tm, const StageF p)
+
+// One stage of one TY x TX tile of one run.  The mbarrier is initialised by the
+// caller; `parity` is the phase this tile's load completes.  Returns false if
+// the tile load did not arrive in time (every thread of the CTA agrees).
+template <int TY>
+__device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int stage, const CUtensorMap *tm, int bx,
+                                           int by, SmemT<TY> &S, unsigned parity, unsigned *err)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    constexpr int SR = TY + 2 * GR;
+    constexpr int NT = TY * 32;
+    constexpr unsigned TILE_BYTES = NP2 * SR * SC * sizeof(float2);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int q0 = blockIdx.x * TX;
-    const int i0 = blockIdx.y * TY;
-    const Layout L = p.L;
+    const int q0 = bx * TX;
+    const int i0 = by * TY;
+    const Layout L = R.L;
+    const float2 *in = (stage == 1) ? R.F : (stage == 2) ? R.A : R.B;
+    float2 *out = (stage == 1) ? R.A : (stage == 2) ? R.B : R.F;
+    (void)in;
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.bar)),
                      "r"(TILE_BYTES)
@@ -181,110 +191,136 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.tile[0][0][0])),
-            "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(q0), "r"(i0), "r"(0), "r"(smem_u32(&S.bar))
+            "l"(reinterpret_cast<unsigned long long>(tm)), "r"(q0), "r"(i0), "r"(0), "r"(smem_u32(&S.bar))
             : "memory");
     }
+    // per-tile tables while the tile is in flight
+    {
+        int t = tid;
+        if (t < SR) {
+            S.ds2[t] = splat(R.dsin[i0 + t]);
+        } else if ((t -= SR) < SR) {
+            S.d2s2[t] = splat(R.d2sin[i0 + t]);
+        } else if ((t -= SR) < NP2 * (TY + 1)) {
+            const int q = t / (TY + 1), fy = t - q * (TY + 1);
+            const int fi = min(i0 + fy, L.nt);
+            const float corr = R.face[2 * fi + ((q >> 2) ? 0 : 1)].corr;
+            S.cw[q][fy] = make_float2(-R.wr[q].x * corr, -R.wr[q].y * corr);
+        } else if ((t -= NP2 * (TY + 1)) < TY) {
+            S.rowc[t] = R.row[min(i0 + t, L.nt - 1)];
+        } else if ((t -= TY) < TY * NP2) {
+            const int ry = t >> 3, q = t & 7;
+            S.rr[ry][q] = R.rref[(size_t)min(i0 + ry, L.nt - 1) * NP2 + q];
+        }
+    }
     __syncthreads();
-    if (!wait_phase0(&S.bar, 1000000000ull)) {
+    const bool ok = __syncthreads_and(wait_phase(&S.bar, parity, 1000000000ull));
+    if (!ok) {
         // the copy did not complete within 1 s: flag it, give it one more bounded
         // second to land in this CTA's shared memory, then leave
-        if (tid == 0) atomicOr(p.err, 1u);
-        wait_phase0(&S.bar, 1000000000ull);
-        return;
+        if (tid == 0) atomicOr(err, 1u);
+        wait_phase(&S.bar, parity, 1000000000ull);
+        return false;
     }
 
     // ---- phi faces: warp = cell row fy, lane = face fx (west face of column fx)
     {
         const int fy = warp;
-        const int irow = min(i0 + fy, L.nt - 1);
-        const float kinv = p.row[irow].kphi;
+        const float kinv = S.rowc[fy].kphi;
 #pragma unroll 2
         for (int q = 0; q < NP2; ++q) {
-            const float vb = p.c.vphi[q & 3];
+            const f2 vb = c.vphi2[q & 3];
             const f2 *row = &S.tile[q][fy + GR][0];
             Forms F;
-            if (vb > 0.0f) {   // columns fx-3 .. fx+1  (shared column = column + GC)
+            if (vb.x > 0.0f) {   // columns fx-3 .. fx+1  (shared column = column + GC)
                 F = forms(row[lane + 1], row[lane + 2], row[lane + 3], row[lane + 4], row[lane + 5]);
-            } else {           // columns fx+2 .. fx-2
+            } else {             // columns fx+2 .. fx-2
                 F = forms(row[lane + 6], row[lane + 5], row[lane + 4], row[lane + 3], row[lane + 2]);
             }
-            S.fp[q][fy][lane] = mul2(splat(vb), weno_combine(F, kinv));
+            S.fp[q][fy][lane] = mul2(vb, weno_combine(F, kinv));
         }
-        // east face of the last column: 64 (pair, row) combinations on 2 warps
+        // east face of the last column: NP2 x TY (pair, row) combinations
         if (tid < NP2 * TY) {
-            const int q = tid >> 3, ry = tid & 7;
-            const int ir = min(i0 + ry, L.nt - 1);
-            const float vb = p.c.vphi[q & 3];
+            const int q = tid / TY, ry = tid - (tid / TY) * TY;
+            const f2 vb = c.vphi2[q & 3];
             const f2 *row = &S.tile[q][ry + GR][0];
             const int fx = TX;
-            Forms F = (vb > 0.0f) ? forms(row[fx + 1], row[fx + 2], row[fx + 3], row[fx + 4], row[fx + 5])
-                                  : forms(row[fx + 6], row[fx + 5], row[fx + 4], row[fx + 3], row[fx + 2]);
-            S.fp[q][ry][fx] = mul2(splat(vb), weno_combine(F, p.row[ir].kphi));
+            Forms F = (vb.x > 0.0f) ? forms(row[fx + 1], row[fx + 2], row[fx + 3], row[fx + 4], row[fx + 5])
+                                    : forms(row[fx + 6], row[fx + 5], row[fx + 4], row[fx + 3], row[fx + 2]);
+            S.fp[q][ry][fx] = mul2(vb, weno_combine(F, S.rowc[ry].kphi));
         }
     }
 
     // ---- theta faces: warp = pair, lane = column, marching over the TY+1 face rows.
     // Consecutive faces share their second differences (the smoothness forms of the
-    // three candidate stencils are centred on consecutive rows), so each step adds
-    // one new row.  With x the tile column (rows 0..SR-1), for v > 0 face fy uses
-    // x[fy..fy+4] in upwind order, for v < 0 it uses x[fy+5..fy+1].
+    // three candidate stencils are centred on consecutive rows).  With x the tile
+    // column (rows 0..SR-1), for v > 0 face fy uses x[fy..fy+4] in upwind order,
+    // for v < 0 it uses x[fy+5..fy+1].  The smoothness forms are those of the full
+    // g = dg + w rho_ref sin(theta) (first and second differences of sin from the
+    // FP64 tables); P2 is taken on dg alone.
     {
-        const int q = warp, g = q >> 2;
-        const float kinv = p.ktheta;
+        const float kinv = R.ktheta;
         const f2 c13 = splat((13.0f / 12.0f) * kinv), c14 = splat(0.25f * kinv), one = splat(1.0f);
-        const f2 wr = p.c.wr[q];
-        const f2 vt = p.c.vth[g];
-        const f2 *col = &S.tile[q][0][lane + GC];
-        const float *dsin = p.dsin + i0;     // first differences of sin at tile rows
-        const float *d2sin = p.d2sin + i0;   // second differences of sin at tile rows
-        // dd[r] = x[r] - x[r-1] (deviation), df[r] = full g difference, D2[r] full second difference
-        f2 x[SR], dd[SR], dfu[SR], D2[SR], Qp[SR];
-#pragma unroll
-        for (int r = 0; r < SR; ++r) x[r] = col[r * SC];
-#pragma unroll
-        for (int r = 1; r < SR; ++r) {
-            dd[r] = sub2(x[r], x[r - 1]);
-            dfu[r] = fma2(wr, splat(dsin[r]), dd[r]);
-        }
-#pragma unroll
-        for (int r = 1; r < SR - 1; ++r) {
-            D2[r] = fma2(wr, splat(d2sin[r]), sub2(dd[r + 1], dd[r]));
-            Qp[r] = fma2(mul2(D2[r], c13), D2[r], one);
-        }
         const f2 two = splat(2.0f), m2 = splat(-2.0f);
-        const FaceConst *fcp = p.face + 2 * i0 + (g ? 0 : 1);
+#pragma unroll 1
+        for (int q = warp; q < NP2; q += NT / 32) {
+            const int g = q >> 2;
+            const f2 wr = R.wr[q];
+            const f2 vt = c.vth[g];
+            const f2 *col = &S.tile[q][0][lane + GC];
+            // values are produced one row ahead of their first use (face fy needs rows up to fy+5)
+            f2 x[SR], dd[SR], dfu[SR], D2[SR], Qp[SR];
 #pragma unroll
-        for (int fy = 0; fy <= TY; ++fy) {
-            const float corr = fcp[2 * min(fy, L.nt - i0)].corr;
-            f2 B1, B2, B3, Q1, Q2, Q3, d12, d23, p2;
-            if (g) {   // v_theta > 0: a..e = x[fy..fy+4]
-                Q1 = Qp[fy + 1]; Q2 = Qp[fy + 2]; Q3 = Qp[fy + 3];
-                B1 = fma2(two, dfu[fy + 2], D2[fy + 1]);
-                B2 = add2(dfu[fy + 2], dfu[fy + 3]);
-                B3 = fma2(m2, dfu[fy + 3], D2[fy + 3]);
-                d12 = sub2(D2[fy + 1], D2[fy + 2]);
-                d23 = sub2(D2[fy + 2], D2[fy + 3]);
-                p2 = fma2(splat(1.0f / 6.0f), dd[fy + 2], fma2(splat(1.0f / 3.0f), dd[fy + 3], x[fy + 2]));
-            } else {   // v_theta < 0: a..e = x[fy+5..fy+1]
-                Q1 = Qp[fy + 4]; Q2 = Qp[fy + 3]; Q3 = Qp[fy + 2];
-                B1 = fma2(m2, dfu[fy + 4], D2[fy + 4]);
-                B2 = add2(dfu[fy + 4], dfu[fy + 3]);
-                B3 = fma2(two, dfu[fy + 3], D2[fy + 2]);
-                d12 = sub2(D2[fy + 4], D2[fy + 3]);
-                d23 = sub2(D2[fy + 3], D2[fy + 2]);
-                p2 = fma2(splat(-1.0f / 6.0f), dd[fy + 4], fma2(splat(-1.0f / 3.0f), dd[fy + 3], x[fy + 3]));
+            for (int r = 0; r < 5; ++r) x[r] = col[r * SC];
+#pragma unroll
+            for (int r = 1; r < 5; ++r) {
+                dd[r] = sub2(x[r], x[r - 1]);
+                dfu[r] = fma2(wr, S.ds2[r], dd[r]);
             }
-            const f2 s1 = fma2(mul2(B1, c14), B1, Q1);
-            const f2 s2 = fma2(mul2(B2, c14), B2, Q2);
-            const f2 s3 = fma2(mul2(B3, c14), B3, Q3);
-            const f2 q1 = mul2(s1, s1), q2 = mul2(s2, s2), q3 = mul2(s3, s3);
-            const f2 q23 = mul2(q2, q3), q12 = mul2(q1, q2);
-            const f2 sum = fma2(splat(0.1f), q23, fma2(splat(0.6f), mul2(q1, q3), mul2(splat(0.3f), q12)));
-            const f2 rr = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
-            const f2 num = fma2(mul2(splat(0.1f / 3.0f), q23), d12, mul2(mul2(splat(0.05f), q12), d23));
-            // the reference part of P2 is the ideal-weight interpolant minus corr
-            const f2 gh = fma2(num, rr, fma2(wr, splat(-corr), p2));
-            S.ft[q][fy][lane] = mul2(vt, gh);
+#pragma unroll
+            for (int r = 1; r < 4; ++r) {
+                D2[r] = fma2(wr, S.d2s2[r], sub2(dd[r + 1], dd[r]));
+                Qp[r] = fma2(mul2(D2[r], c13), D2[r], one);
+            }
+#pragma unroll
+            for (int fy = 0; fy <= TY; ++fy) {
+                {   // extend the window to row fy + 5
+                    const int r = fy + 5;
+                    x[r] = col[r * SC];
+                    dd[r] = sub2(x[r], x[r - 1]);
+                    dfu[r] = fma2(wr, S.ds2[r], dd[r]);
+                    D2[r - 1] = fma2(wr, S.d2s2[r - 1], sub2(dd[r], dd[r - 1]));
+                    Qp[r - 1] = fma2(mul2(D2[r - 1], c13), D2[r - 1], one);
+                }
+                f2 B1, B2, B3, Q1, Q2, Q3, d12, d23, p2;
+                if (g) {   // v_theta > 0: a..e = x[fy..fy+4]
+                    Q1 = Qp[fy + 1]; Q2 = Qp[fy + 2]; Q3 = Qp[fy + 3];
+                    B1 = fma2(two, dfu[fy + 2], D2[fy + 1]);
+                    B2 = add2(dfu[fy + 2], dfu[fy + 3]);
+                    B3 = fma2(m2, dfu[fy + 3], D2[fy + 3]);
+                    d12 = sub2(D2[fy + 1], D2[fy + 2]);
+                    d23 = sub2(D2[fy + 2], D2[fy + 3]);
+                    p2 = fma2(splat(1.0f / 6.0f), dd[fy + 2], fma2(splat(1.0f / 3.0f), dd[fy + 3], x[fy + 2]));
+                } else {   // v_theta < 0: a..e = x[fy+5..fy+1]
+                    Q1 = Qp[fy + 4]; Q2 = Qp[fy + 3]; Q3 = Qp[fy + 2];
+                    B1 = fma2(m2, dfu[fy + 4], D2[fy + 4]);
+                    B2 = add2(dfu[fy + 4], dfu[fy + 3]);
+                    B3 = fma2(two, dfu[fy + 3], D2[fy + 2]);
+                    d12 = sub2(D2[fy + 4], D2[fy + 3]);
+                    d23 = sub2(D2[fy + 3], D2[fy + 2]);
+                    p2 = fma2(splat(-1.0f / 6.0f), dd[fy + 4], fma2(splat(-1.0f / 3.0f), dd[fy + 3], x[fy + 3]));
+                }
+                const f2 s1 = fma2(mul2(B1, c14), B1, Q1);
+                const f2 s2 = fma2(mul2(B2, c14), B2, Q2);
+                const f2 s3 = fma2(mul2(B3, c14), B3, Q3);
+                const f2 q1 = mul2(s1, s1), q2 = mul2(s2, s2), q3 = mul2(s3, s3);
+                const f2 q23 = mul2(q2, q3), q12 = mul2(q1, q2);
+                const f2 sum = fma2(splat(0.1f), q23, fma2(splat(0.6f), mul2(q1, q3), mul2(splat(0.3f), q12)));
+                const f2 rr = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
+                const f2 num = fma2(mul2(splat(0.1f / 3.0f), q23), d12, mul2(mul2(splat(0.05f), q12), d23));
+                // the reference part of P2 is the ideal-weight interpolant minus corr
+                S.ft[q][fy][lane] = mul2(vt, fma2(num, rr, add2(S.cw[q][fy], p2)));
+            }
         }
     }
     __syncthreads();
@@ -292,79 +328,116 @@ __global__ void __launch_bounds__(NT, 3) stage_f32_kernel(const __grid_constant_
     // ---- one cell per thread: warp = cell row, lane = column
     const int cy = warp, cx = lane;
     const int i = i0 + cy, j = q0 + cx;
-    if (i >= L.nt || j >= L.np) return;
-    // start the global loads of the step's own-cell start values and row tables early
+    if (i >= L.nt || j >= L.np) return true;
+    // start the global loads of the step's own-cell start values early
     f2 F0[NP2];
-    if (p.stage != 1) {
+    if (stage != 1) {
 #pragma unroll
-        for (int q = 0; q < NP2; ++q) F0[q] = p.fold[L.at(q, i, j)];
+        for (int q = 0; q < NP2; ++q) F0[q] = R.F[L.at(q, i, j)];
     }
-    const RowF rc = p.row[i];
-    const f2 *rr = p.rref + (size_t)i * NP2;
-    f2 R0[NP2];
-#pragma unroll
-    for (int q = 0; q < NP2; ++q) R0[q] = rr[q];
+    const RowF rc = S.rowc[cy];
     f2 G[NP2];
 #pragma unroll
     for (int q = 0; q < NP2; ++q) G[q] = S.tile[q][cy + GR][cx + GC];
     // moments of delta f = dg / s
-    f2 sn = G[0], sjt = mul2(p.c.vth[0], G[0]), sjp = mul2(splat(p.c.vphi[0]), G[0]);
+    f2 sn = G[0], sjt = mul2(c.vth[0], G[0]), sjp = mul2(c.vphi2[0], G[0]);
 #pragma unroll
     for (int q = 1; q < NP2; ++q) {
         sn = add2(sn, G[q]);
-        sjt = fma2(p.c.vth[q >> 2], G[q], sjt);
-        sjp = fma2(splat(p.c.vphi[q & 3]), G[q], sjp);
+        sjt = fma2(c.vth[q >> 2], G[q], sjt);
+        sjp = fma2(c.vphi2[q & 3], G[q], sjp);
     }
     const float SG = sn.x + sn.y;                         // sum_k dg_k = s dn
-    const float n = fmaf(SG, rc.inv_s, p.c.rho_ref);
+    const float n = fmaf(SG, rc.inv_s, R.rho_ref);
     const float nin = 1.0f / n;
     const float ut = (sjt.x + sjt.y) * rc.inv_s * nin;
     const float up = (sjp.x + sjp.y) * rc.inv_s * nin;
     const float u2 = fmaf(ut, ut, up * up);
-    const float sn_n = rc.s * n;
     const f2 h0 = splat(-0.5f * u2), h1 = splat(fmaf(-0.5f, u2, 1.0f));
+    const f2 ut2 = splat(ut), snn = splat(rc.s * n), sg2 = splat(SG);
+    const f2 cot2 = splat(rc.cotR), idth = splat(R.inv_dth), idph = splat(rc.inv_dph), mtau = splat(-R.tau_inv);
 
-    f2 out[NP2];
+    f2 o[NP2];
 #pragma unroll
     for (int q = 0; q < NP2; ++q) {
         const int g = q >> 2, b = q & 3;
-        const f2 vt = p.c.vth[g];
-        const float vb = p.c.vphi[b];
         // equilibrium deviation times s: w (s dn + s n poly(xi)), poly = xi + (xi^2-u^2)/2 + xi(xi^2-3u^2)/6
-        const f2 xi = fma2(vt, splat(ut), splat(vb * up));
+        const f2 xi = fma2(c.vth[g], ut2, mul2(c.vphi2[b], splat(up)));
         const f2 poly = fma2(xi, fma2(xi, fma2(xi, splat(1.0f / 6.0f), splat(0.5f)), h1), h0);
-        const f2 sfeq = mul2(p.c.w2[q], fma2(splat(sn_n), poly, splat(SG)));
+        const f2 sfeq = mul2(c.w2[q], fma2(snn, poly, sg2));
         // force on dg: K along k_theta (pairs (0,b),(1,b) and (2,b),(3,b), with swapped partners), Ktilde along k_phi
         const f2 P0 = G[b], P1 = G[4 + b];
-        const f2 *kc = p.c.kpair[g];
-        const f2 kg = fma2(kc[0], P0, fma2(kc[1], swap2(P0), fma2(kc[2], P1, mul2(kc[3], swap2(P1)))));
-        const float *kt = p.c.Kt + 4 * b;
+        const f2 kg = fma2(c.kpair[g][0], P0, fma2(c.kpair[g][1], swap2(P0), fma2(c.kpair[g][2], P1, mul2(c.kpair[g][3], swap2(P1)))));
         const f2 *Gg = G + 4 * g;
-        const f2 ktg = fma2(splat(kt[0]), Gg[0], fma2(splat(kt[1]), Gg[1], fma2(splat(kt[2]), Gg[2], mul2(splat(kt[3]), Gg[3]))));
-        const f2 force = mul2(splat(rc.cotR), fma2(splat(vb * vb), kg, mul2(p.c.mvth[g], ktg)));
+        const f2 ktg = fma2(c.Kt2[4 * b], Gg[0], fma2(c.Kt2[4 * b + 1], Gg[1], fma2(c.Kt2[4 * b + 2], Gg[2], mul2(c.Kt2[4 * b + 3], Gg[3]))));
+        const f2 force = mul2(cot2, fma2(c.vphisq2[b], kg, mul2(c.mvth[g], ktg)));
         // flux differences
-        const f2 adv_t = mul2(sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]), splat(p.inv_dth));
-        const f2 adv_p = mul2(sub2(S.fp[q][cy][cx], S.fp[q][cy][cx + 1]), splat(rc.inv_dph));
+        const f2 adv_t = mul2(sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]), idth);
+        const f2 adv_p = mul2(sub2(S.fp[q][cy][cx], S.fp[q][cy][cx + 1]), idph);
         // L on dg: advection - force - (dg - s feq_dev)/tau + s rref
-        f2 Lq = sub2(add2(add2(adv_t, adv_p), R0[q]), force);
-        Lq = fma2(sub2(G[q], sfeq), splat(-p.tau_inv), Lq);
-        if (p.stage == 1) {
-            out[q] = fma2(splat(p.dt), Lq, G[q]);
+        f2 Lq = sub2(add2(add2(adv_t, adv_p), S.rr[cy][q]), force);
+        Lq = fma2(sub2(G[q], sfeq), mtau, Lq);
+        if (stage == 1) {
+            o[q] = fma2(splat(R.dt), Lq, G[q]);
+        } else if (stage == 2) {
+            o[q] = fma2(splat(0.25f * R.dt), Lq, fma2(splat(0.75f), F0[q], mul2(splat(0.25f), G[q])));
         } else {
-            const f2 f0 = F0[q];
-            if (p.stage == 2)
-                out[q] = fma2(splat(0.25f * p.dt), Lq, fma2(splat(0.75f), f0, mul2(splat(0.25f), G[q])));
-            else
-                out[q] = fma2(splat((2.0f / 3.0f) * p.dt), Lq, fma2(splat(1.0f / 3.0f), f0, mul2(splat(2.0f / 3.0f), G[q])));
+            o[q] = fma2(splat((2.0f / 3.0f) * R.dt), Lq, fma2(splat(1.0f / 3.0f), F0[q], mul2(splat(2.0f / 3.0f), G[q])));
         }
     }
     const bool plain = (i >= GR && i < L.nt - GR && j >= GC && j < L.np - GC);
     if (plain) {
 #pragma unroll
-        for (int q = 0; q < NP2; ++q) p.out[L.at(q, i, j)] = out[q];
+        for (int q = 0; q < NP2; ++q) out[L.at(q, i, j)] = o[q];
     } else {
 #pragma unroll
-        for (int q = 0; q < NP2; ++q) store_images(p.out, L, q, i, j, out[q]);
+        for (int q = 0; q < NP2; ++q) store_images(out, L, q, i, j, o[q]);
+    }
+    return true;
+}
+
+template <int TY>
+__global__ void __launch_bounds__(TY * 32, 24 / TY) stage_f32_kernel(const __grid_constant__ CUtensorMap tm,
+                                                                      const RunF R, const VelC c, int stage,
+                                                                      unsigned *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemT<TY> &S = *reinterpret_cast<SmemT<TY> *>(smem_raw);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    stage_tile<TY>(R, c, stage, &tm, blockIdx.x, blockIdx.y, S, 0u, err);
+}
+
+// Persistent batch stage: CTA b takes work items b, b + gridDim.x, ...; a work item
+// is (run, tile index within the run).  The run's parameters are copied into
+// shared memory per item.
+template <int TY>
+__global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const RunF *runs, const CUtensorMap *tms,
+                                                                            const int2 *work, int ntiles, const VelC c,
+                                                                            int stage, unsigned *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SmemT<TY> &S = *reinterpret_cast<SmemT<TY> *>(smem_raw);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    unsigned parity = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int2 w = work[t];
+        {
+            const unsigned *src = reinterpret_cast<const unsigned *>(runs + w.x);
+            unsigned *dst = reinterpret_cast<unsigned *>(&S.run);
+            for (int m = threadIdx.x; m < (int)(sizeof(RunF) / 4); m += blockDim.x) dst[m] = src[m];
+        }
+        __syncthreads();
+        const int tx = S.run.tiles_x;
+        if (!stage_tile<TY>(S.run, c, stage, tms + 3 * w.x + (stage - 1), w.y % tx, w.y / tx, S, parity, err))
+            return;
+        parity ^= 1u;
+        __syncthreads();   // every thread is done with this tile's shared memory
     }
 }
 
@@ -581,18 +654,48 @@ __global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *
 
 }  // namespace
 
-size_t stage_f32_smem_bytes() { return sizeof(Smem) + 128; }
+template <int TY>
+static size_t smem_bytes() { return sizeof(SmemT<TY>) + 128; }
 
 cudaError_t prepare_stage_f32()
 {
-    return cudaFuncSetAttribute(stage_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)stage_f32_smem_bytes());
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(stage_f32_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<8>())))
+        return e;
+    if ((e = cudaFuncSetAttribute(stage_f32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<4>())))
+        return e;
+    if ((e = cudaFuncSetAttribute(batch_stage_f32_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<8>())))
+        return e;
+    return cudaFuncSetAttribute(batch_stage_f32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<4>());
 }
 
-void launch_stage_f32(const CUtensorMap &tm_in, const StageF &p, cudaStream_t s)
+int stage_f32_max_ctas_per_sm(int ty)
 {
-    dim3 grid((p.L.np + TX - 1) / TX, (p.L.nt + TY - 1) / TY);
-    stage_f32_kernel<<<grid, NT, stage_f32_smem_bytes(), s>>>(tm_in, p);
+    int n = 0;
+    if (ty == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<4>, 128, smem_bytes<4>());
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<8>, 256, smem_bytes<8>());
+    return n;
+}
+
+void launch_stage_f32(const CUtensorMap &tm_in, const RunF &run, const VelC &c, int stage, int ty, unsigned *err,
+                      cudaStream_t s)
+{
+    if (ty == 4) {
+        dim3 grid((run.L.np + TX - 1) / TX, (run.L.nt + 3) / 4);
+        stage_f32_kernel<4><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, run, c, stage, err);
+    } else {
+        dim3 grid((run.L.np + TX - 1) / TX, (run.L.nt + 7) / 8);
+        stage_f32_kernel<8><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, run, c, stage, err);
+    }
+}
+
+void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
+                            int stage, int ty, int ctas, unsigned *err, cudaStream_t s)
+{
+    if (ty == 4) batch_stage_f32_kernel<4><<<ctas, 128, smem_bytes<4>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+    else batch_stage_f32_kernel<8><<<ctas, 256, smem_bytes<8>(), s>>>(runs, tms, work, ntiles, c, stage, err);
 }
 
 void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/vlbm.h"
@@ -46,7 +47,9 @@ struct vlbm {
     CUtensorMap tmF{}, tmA{}, tmB{};
     cudaGraphExec_t g1 = nullptr, g16 = nullptr;
     VelD vd{};
-    VelF vf{};
+    VelC vc{};     // FP32 path: packed velocity constants
+    RunF run{};    // FP32 path: per-run stage parameters
+    int ty = 8;    // FP32 path: tile rows
     double rho_ref = 0.0, rho_ref_opt = 0.0;
     long long steps = 0;
     double mass0 = 0.0;
@@ -190,7 +193,7 @@ int build_f32_tables(vlbm_t *h)
     const int nt = h->nt;
     const double R = h->R, dth = M_PI / nt, dph = 2.0 * M_PI / h->np;
     const VelD &c = h->vd;
-    VelF &f = h->vf;
+    VelC &f = h->vc;
     const double rr = h->rho_ref;
     for (int g = 0; g < 2; ++g) {
         f.vth[g] = make_float2((float)c.v[2 * g], (float)c.v[2 * g + 1]);
@@ -201,14 +204,18 @@ int build_f32_tables(vlbm_t *h)
         f.kpair[g][2] = make_float2((float)c.K[a0 * 4 + 2], (float)c.K[a1 * 4 + 3]);
         f.kpair[g][3] = make_float2((float)c.K[a0 * 4 + 3], (float)c.K[a1 * 4 + 2]);
     }
-    for (int b = 0; b < 4; ++b) f.vphi[b] = (float)c.v[b];
+    for (int b = 0; b < 4; ++b) {
+        f.vphi2[b] = make_float2((float)c.v[b], (float)c.v[b]);
+        f.vphisq2[b] = make_float2((float)(c.v[b] * c.v[b]), (float)(c.v[b] * c.v[b]));
+    }
+    RunF &run = h->run;
     for (int q = 0; q < 8; ++q) {
         const int g = q / 4, b = q % 4;
         f.w2[q] = make_float2((float)(c.w[2 * g] * c.w[b]), (float)(c.w[2 * g + 1] * c.w[b]));
-        f.wr[q] = make_float2((float)(c.w[2 * g] * c.w[b] * rr), (float)(c.w[2 * g + 1] * c.w[b] * rr));
+        run.wr[q] = make_float2((float)(c.w[2 * g] * c.w[b] * rr), (float)(c.w[2 * g + 1] * c.w[b] * rr));
     }
-    for (int q = 0; q < 16; ++q) f.Kt[q] = (float)c.Kt[q];
-    f.rho_ref = (float)rr;
+    for (int q = 0; q < 16; ++q) f.Kt2[q] = make_float2((float)c.Kt[q], (float)c.Kt[q]);
+    run.rho_ref = (float)rr;
 
     // faces fi = 0..nt between rows fi-1 and fi; upwind-ordered sine stencils
     std::vector<FaceConst> face(2 * (size_t)(nt + 1));
@@ -268,7 +275,7 @@ int build_f32_tables(vlbm_t *h)
         }
     }
     // differences of sin at padded rows (pr-1, pr, pr+1 inside [0, nt + 2GR))
-    const int npr = nt + 2 * GR + F32_TILE_ROWS;
+    const int npr = nt + 2 * GR + F32_TILE_ROWS_MAX;
     std::vector<float> ds(npr, 0.0f), d2s(npr, 0.0f);
     for (int pr = 0; pr < npr; ++pr) {
         if (pr >= 1 && pr < nt + 2 * GR)
@@ -283,11 +290,26 @@ int build_f32_tables(vlbm_t *h)
     if ((rc = upload(h, &h->d_face, face.data(), face.size()))) return rc;
     if ((rc = upload(h, &h->d_row, row.data(), row.size()))) return rc;
     if ((rc = upload(h, &h->d_rref, rref.data(), rref.size()))) return rc;
+    run.F = (float2 *)h->F;
+    run.A = (float2 *)h->A;
+    run.B = (float2 *)h->B;
+    run.face = h->d_face;
+    run.row = h->d_row;
+    run.rref = h->d_rref;
+    run.dsin = h->d_dsin;
+    run.d2sin = h->d_d2sin;
+    run.L = h->L;
+    run.tau_inv = (float)(1.0 / h->tau);
+    run.dt = (float)h->dt;
+    run.ktheta = (float)(1.0 / h->eps);
+    run.inv_dth = (float)(1.0 / (h->R * (M_PI / h->nt)));
+    run.tiles_x = (h->np + F32_TILE_COLS - 1) / F32_TILE_COLS;
     return VLBM_OK;
 }
 
-int encode_map(vlbm_t *h, CUtensorMap *m, void *base)
+int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0)
 {
+    if (ty == 0) ty = h->ty;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -300,7 +322,7 @@ int encode_map(vlbm_t *h, CUtensorMap *m, void *base)
     // pair planes of float2, described as 8-byte elements
     cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)(h->nt + 2 * GR), (cuuint64_t)(NK / 2)};
     cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * sizeof(float2), (cuuint64_t)h->L.plane * sizeof(float2)};
-    cuuint32_t box[3] = {(cuuint32_t)(F32_TILE_COLS + 2 * GC), (cuuint32_t)(F32_TILE_ROWS + 2 * GR), (cuuint32_t)(NK / 2)};
+    cuuint32_t box[3] = {(cuuint32_t)(F32_TILE_COLS + 2 * GC), (cuuint32_t)(ty + 2 * GR), (cuuint32_t)(NK / 2)};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -338,25 +360,8 @@ void enqueue_step(vlbm_t *h, int stage_only = 0)
             launch_stage_f64(p, s);
             if (h->nfrows) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         } else {
-            StageF p;
-            p.in = (const float2 *)in;
-            p.fold = (const float2 *)h->F;
-            p.out = (float2 *)out;
-            p.face = h->d_face;
-            p.row = h->d_row;
-            p.rref = h->d_rref;
-            p.dsin = h->d_dsin;
-            p.d2sin = h->d_d2sin;
-            p.err = h->d_flags;
-            p.L = h->L;
-            p.tau_inv = (float)(1.0 / h->tau);
-            p.dt = (float)h->dt;
-            p.ktheta = (float)(1.0 / h->eps);
-            p.inv_dth = (float)(1.0 / (h->R * (M_PI / h->nt)));
-            p.stage = st;
-            p.c = h->vf;
             const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
-            launch_stage_f32(tm, p, s);
+            launch_stage_f32(tm, h->run, h->vc, st, h->ty, h->d_flags, s);
             if (h->nfrows) launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         }
     }
@@ -437,6 +442,7 @@ void vlbm_default_options(vlbm_options *opt)
     opt->guard = 1;
     opt->stream = nullptr;
     opt->rho_ref = 0.0;
+    opt->tile_rows = 0;
 }
 
 int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt, const vlbm_options *opt,
@@ -468,6 +474,7 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     h->filter = o.polar_filter ? 1 : 0;
     h->guard = o.guard ? 1 : 0;
     h->rho_ref_opt = o.rho_ref;
+    h->ty = (o.tile_rows == 4) ? 4 : 8;
     h->elem = (h->prec == VLBM_FP64) ? sizeof(double) : sizeof(float);
     h->L.nt = n_theta;
     h->L.np = n_phi;
@@ -503,7 +510,7 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
         (rc = dalloc(h, &h->B, h->arr_bytes)))
         return bail(rc);
     // geometry
-    std::vector<double> sext(n_theta + 2 * GR + F32_TILE_ROWS, 0.0), cot(n_theta);
+    std::vector<double> sext(n_theta + 2 * GR + F32_TILE_ROWS_MAX, 0.0), cot(n_theta);
     for (int pr = 0; pr < n_theta + 2 * GR; ++pr) sext[pr] = sin_padded(h->sin_t, n_theta, pr);
     for (int i = 0; i < n_theta; ++i) cot[i] = h->cos_t[i] / h->sin_t[i];
     if ((rc = upload(h, &h->d_sin_ext, sext.data(), sext.size())) || (rc = upload(h, &h->d_cot, cot.data(), cot.size())) ||
@@ -775,6 +782,413 @@ void vlbm_destroy(vlbm_t *h)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
+}
+
+}  // extern "C"
+
+struct vlbm_batch {
+    std::vector<vlbm_t *> runs;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int ty = 8, ctas_per_sm = 0, nsm = 0;
+    RunF *d_runs = nullptr;
+    CUtensorMap *d_tms = nullptr;
+    int2 *d_work = nullptr;
+    int ntiles = 0;
+    bool dirty = true;
+    int guard = 1;
+    VelC vc{};
+    unsigned *d_flags = nullptr, *h_flags = nullptr;
+    cudaGraphExec_t g1 = nullptr, g16 = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    std::string err;
+    long long steps = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// Batched ensembles (FP32): many independent runs of uneven grid sizes advanced by
+// one persistent kernel launch per RK3 stage, the n-step loop captured as a CUDA
+// graph.  Each member is a full FP32 solver (its own arrays and tables); the batch
+// adds the run table, the work list of (run, tile) items, the per-run tensor maps
+// and the launch schedule (tile rows, CTAs per SM) chosen by vlbm_batch_tune.
+// ---------------------------------------------------------------------------------
+thread_local std::string g_batch_error;
+
+int bfail(vlbm_batch_t *b, int code, const std::string &msg)
+{
+    if (b) b->err = msg;
+    else g_batch_error = msg;
+    return code;
+}
+
+#define BCK(b, call)                                                                                      \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess)                                                                            \
+            return bfail((b), VLBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+void batch_drop_graphs(vlbm_batch_t *b)
+{
+    if (b->g1) cudaGraphExecDestroy(b->g1);
+    if (b->g16) cudaGraphExecDestroy(b->g16);
+    b->g1 = b->g16 = nullptr;
+}
+
+// Uploads the run table, tensor maps (for the current tile rows) and work list.
+int batch_refresh(vlbm_batch_t *b)
+{
+    if (!b->dirty) return VLBM_OK;
+    const int nr = (int)b->runs.size();
+    std::vector<RunF> runs(nr);
+    std::vector<CUtensorMap> tms(3 * (size_t)nr);
+    std::vector<int2> work;
+    for (int r = 0; r < nr; ++r) {
+        vlbm_t *h = b->runs[r];
+        if (!h->d_face) return bfail(b, VLBM_ERR_ARG, "run " + std::to_string(r) + " is not initialised");
+        runs[r] = h->run;
+        int rc;
+        if ((rc = encode_map(h, &tms[3 * r + 0], h->F, b->ty)) || (rc = encode_map(h, &tms[3 * r + 1], h->A, b->ty)) ||
+            (rc = encode_map(h, &tms[3 * r + 2], h->B, b->ty)))
+            return bfail(b, rc, h->err);
+        const int tx = runs[r].tiles_x, tyn = (h->nt + b->ty - 1) / b->ty;
+        for (int t = 0; t < tx * tyn; ++t) work.push_back(make_int2(r, t));
+        b->vc = h->vc;
+    }
+    b->ntiles = (int)work.size();
+    if (!b->d_runs) BCK(b, cudaMalloc(&b->d_runs, sizeof(RunF) * nr));
+    if (!b->d_tms) BCK(b, cudaMalloc(&b->d_tms, sizeof(CUtensorMap) * 3 * nr));
+    if (b->d_work) cudaFree(b->d_work);
+    BCK(b, cudaMalloc(&b->d_work, sizeof(int2) * work.size()));
+    BCK(b, cudaMemcpy(b->d_runs, runs.data(), sizeof(RunF) * nr, cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_tms, tms.data(), sizeof(CUtensorMap) * 3 * nr, cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice));
+    batch_drop_graphs(b);
+    b->dirty = false;
+    return VLBM_OK;
+}
+
+int batch_ctas(const vlbm_batch_t *b)
+{
+    const int per = b->ctas_per_sm > 0 ? b->ctas_per_sm : stage_f32_max_ctas_per_sm(b->ty);
+    return std::max(1, std::min(b->ntiles, per * b->nsm));
+}
+
+void batch_enqueue_step(vlbm_batch_t *b)
+{
+    const int ctas = batch_ctas(b);
+    for (int st = 1; st <= 3; ++st) {
+        launch_batch_stage_f32(b->d_runs, b->d_tms, b->d_work, b->ntiles, b->vc, st, b->ty, ctas, b->d_flags, b->stream);
+        for (vlbm_t *h : b->runs) {
+            if (!h->nfrows) continue;
+            void *out = (st == 1) ? h->A : (st == 2) ? h->B : h->F;
+            launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, b->stream);
+        }
+    }
+}
+
+int batch_build_graph(vlbm_batch_t *b, int nsteps, cudaGraphExec_t *exec)
+{
+    cudaGraph_t g = nullptr;
+    BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < nsteps; ++q) batch_enqueue_step(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) return bfail(b, VLBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, VLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return VLBM_OK;
+}
+
+std::string batch_signature(const vlbm_batch_t *b)
+{
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::vector<std::pair<int, int>> g;
+    for (const vlbm_t *h : b->runs) g.push_back({h->nt, h->np});
+    std::sort(g.begin(), g.end());
+    std::string key = std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount) + "sm|";
+    for (size_t i = 0; i < g.size();) {
+        size_t j = i;
+        while (j < g.size() && g[j] == g[i]) ++j;
+        key += std::to_string(j - i) + "x" + std::to_string(g[i].first) + "x" + std::to_string(g[i].second) + ";";
+        i = j;
+    }
+    return key;
+}
+
+// The tuning cache is a JSON object, one entry per line:
+//   "signature": {"tile_rows": 8, "ctas_per_sm": 3, "ms_per_step": 1.25},
+bool cache_lookup(const char *path, const std::string &key, int *ty, int *ctas, double *ms)
+{
+    if (!path) return false;
+    FILE *fp = fopen(path, "r");
+    if (!fp) return false;
+    char line[4096];
+    bool found = false;
+    const std::string tag = "\"" + key + "\"";
+    while (fgets(line, sizeof line, fp)) {
+        std::string l(line);
+        if (l.find(tag) == std::string::npos) continue;
+        if (sscanf(l.c_str() + l.find("{"), "{\"tile_rows\": %d, \"ctas_per_sm\": %d, \"ms_per_step\": %lf", ty, ctas, ms) == 3)
+            found = true;
+    }
+    fclose(fp);
+    return found;
+}
+
+void cache_store(const char *path, const std::string &key, int ty, int ctas, double ms)
+{
+    if (!path) return;
+    std::vector<std::string> keep;
+    if (FILE *fp = fopen(path, "r")) {
+        char line[4096];
+        while (fgets(line, sizeof line, fp)) {
+            std::string l(line);
+            if (l.find("\": {") == std::string::npos || l.find("\"" + key + "\"") != std::string::npos) continue;
+            while (!l.empty() && (l.back() == '\n' || l.back() == ',')) l.pop_back();
+            keep.push_back(l);
+        }
+        fclose(fp);
+    }
+    char buf[512];
+    snprintf(buf, sizeof buf, "  \"%s\": {\"tile_rows\": %d, \"ctas_per_sm\": %d, \"ms_per_step\": %.6f}", key.c_str(), ty,
+             ctas, ms);
+    keep.push_back(buf);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *fp = fopen(tmp.c_str(), "w");
+    if (!fp) return;
+    fprintf(fp, "{\n");
+    for (size_t i = 0; i < keep.size(); ++i) fprintf(fp, "%s%s\n", keep[i].c_str(), i + 1 < keep.size() ? "," : "");
+    fprintf(fp, "}\n");
+    fclose(fp);
+    rename(tmp.c_str(), path);
+}
+
+}  // namespace (reopened below for the C entry points)
+
+extern "C" {
+
+int vlbm_batch_create(int nruns, const int *n_theta, const int *n_phi, const double *tau, const double *dt,
+                      const vlbm_options *opt, vlbm_batch_t **out)
+{
+    if (!out) return bfail(nullptr, VLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nruns < 1 || !n_theta || !n_phi || !tau || !dt) return bfail(nullptr, VLBM_ERR_ARG, "bad run arrays");
+    vlbm_options o;
+    vlbm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != VLBM_FP32) return bfail(nullptr, VLBM_ERR_UNSUPPORTED, "batches run the FP32 path only");
+    vlbm_batch_t *b = new vlbm_batch_t();
+    b->guard = o.guard ? 1 : 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, VLBM_ERR_CUDA, "no CUDA device");
+    }
+    if (o.stream) {
+        b->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return bfail(nullptr, VLBM_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        b->own_stream = true;
+    }
+    o.stream = b->stream;
+    o.guard = 0;
+    o.tile_rows = 8;
+    for (int r = 0; r < nruns; ++r) {
+        vlbm_t *h = nullptr;
+        int rc = vlbm_create(n_theta[r], n_phi[r], VLBM_D2Q16, tau[r], dt[r], &o, &h);
+        if (rc) {
+            std::string m = "run " + std::to_string(r) + ": " + vlbm_last_error(nullptr);
+            vlbm_batch_destroy(b);
+            return bfail(nullptr, rc, m);
+        }
+        b->runs.push_back(h);
+    }
+    if (cudaMalloc(&b->d_flags, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(b->d_flags, 0, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost(&b->h_flags, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess) {
+        vlbm_batch_destroy(b);
+        return bfail(nullptr, VLBM_ERR_CUDA, "batch allocation failed");
+    }
+    *out = b;
+    return VLBM_OK;
+}
+
+int vlbm_batch_init_moments(vlbm_batch_t *b, int run, const double *rho, const double *u_theta, const double *u_phi,
+                            const double *T)
+{
+    if (!b || run < 0 || run >= (int)b->runs.size()) return bfail(b, VLBM_ERR_ARG, "bad batch or run index");
+    int rc = vlbm_init_moments(b->runs[run], rho, u_theta, u_phi, T);
+    if (rc) return bfail(b, rc, b->runs[run]->err);
+    b->dirty = true;
+    b->steps = 0;
+    return VLBM_OK;
+}
+
+int vlbm_batch_set_schedule(vlbm_batch_t *b, int tile_rows, int ctas_per_sm)
+{
+    if (!b || (tile_rows != 4 && tile_rows != 8) || ctas_per_sm < 0) return bfail(b, VLBM_ERR_ARG, "bad schedule");
+    if (ctas_per_sm > stage_f32_max_ctas_per_sm(tile_rows)) return bfail(b, VLBM_ERR_ARG, "ctas_per_sm above occupancy");
+    if (tile_rows != b->ty) b->dirty = true;
+    b->ty = tile_rows;
+    b->ctas_per_sm = ctas_per_sm;
+    batch_drop_graphs(b);
+    return VLBM_OK;
+}
+
+int vlbm_batch_step_async(vlbm_batch_t *b, int n)
+{
+    if (!b || n < 0) return bfail(b, VLBM_ERR_ARG, "bad batch or step count");
+    if (n == 0) return VLBM_OK;
+    int rc;
+    if ((rc = batch_refresh(b))) return rc;
+    if (!b->g1 && (rc = batch_build_graph(b, 1, &b->g1))) return rc;
+    if (n >= 16 && !b->g16 && (rc = batch_build_graph(b, 16, &b->g16))) return rc;
+    int left = n;
+    while (left >= 16) {
+        BCK(b, cudaGraphLaunch(b->g16, b->stream));
+        left -= 16;
+    }
+    while (left-- > 0) BCK(b, cudaGraphLaunch(b->g1, b->stream));
+    b->steps += n;
+    for (vlbm_t *h : b->runs) h->steps += n;
+    return VLBM_OK;
+}
+
+int vlbm_batch_sync(vlbm_batch_t *b)
+{
+    if (!b) return bfail(b, VLBM_ERR_ARG, "NULL batch");
+    BCK(b, cudaMemcpyAsync(b->h_flags, b->d_flags, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    BCK(b, cudaGetLastError());
+    if (b->h_flags[0] & 1u) return bfail(b, VLBM_ERR_TIMEOUT, "a tile load did not complete within its time limit");
+    if (b->h_flags[1]) return bfail(b, VLBM_ERR_NONFINITE, "non-finite population found by the guard");
+    return VLBM_OK;
+}
+
+int vlbm_batch_step(vlbm_batch_t *b, int n)
+{
+    int rc = vlbm_batch_step_async(b, n);
+    if (rc) return rc;
+    if (b->guard && n > 0) {
+        for (vlbm_t *h : b->runs) launch_guard_f32((const float *)h->F, NK * h->L.plane, b->d_flags + 1, b->stream);
+        BCK(b, cudaGetLastError());
+    }
+    return vlbm_batch_sync(b);
+}
+
+int vlbm_batch_moments(vlbm_batch_t *b, int run, double *rho, double *u_theta, double *u_phi, double *T)
+{
+    if (!b || run < 0 || run >= (int)b->runs.size()) return bfail(b, VLBM_ERR_ARG, "bad batch or run index");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    int rc = vlbm_moments(b->runs[run], rho, u_theta, u_phi, T);
+    if (rc) return bfail(b, rc, b->runs[run]->err);
+    return VLBM_OK;
+}
+
+int vlbm_batch_profile(vlbm_batch_t *b, int n, double *ms_per_step, int *launches_per_step)
+{
+    if (!b || n < 1) return bfail(b, VLBM_ERR_ARG, "bad batch or step count");
+    int rc = vlbm_batch_step_async(b, 1);   // builds the graph outside the timed region
+    if (rc) return rc;
+    BCK(b, cudaEventRecord(b->ev[0], b->stream));
+    if ((rc = vlbm_batch_step_async(b, n))) return rc;
+    BCK(b, cudaEventRecord(b->ev[1], b->stream));
+    BCK(b, cudaEventSynchronize(b->ev[1]));
+    float ms = 0.0f;
+    BCK(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+    if (ms_per_step) *ms_per_step = ms / n;
+    if (launches_per_step) {
+        int l = 3;
+        for (vlbm_t *h : b->runs)
+            if (h->nfrows) l += 3;
+        *launches_per_step = l;
+    }
+    return vlbm_batch_sync(b);
+}
+
+int vlbm_batch_tune(vlbm_batch_t *b, const char *cache_path, int *tile_rows, int *ctas_per_sm, double *ms_per_step)
+{
+    if (!b) return bfail(b, VLBM_ERR_ARG, "NULL batch");
+    int rc;
+    if ((rc = batch_refresh(b))) return rc;
+    const std::string key = batch_signature(b);
+    int best_ty = 8, best_c = 0;
+    double best = 0.0;
+    if (!cache_lookup(cache_path, key, &best_ty, &best_c, &best)) {
+        // measure every schedule on a copy of the state, then put the state back
+        std::vector<void *> backup;
+        for (vlbm_t *h : b->runs) {
+            void *p = nullptr;
+            BCK(b, cudaMalloc(&p, h->arr_bytes));
+            BCK(b, cudaMemcpyAsync(p, h->F, h->arr_bytes, cudaMemcpyDeviceToDevice, b->stream));
+            backup.push_back(p);
+        }
+        best = 1e300;
+        for (int ty : {4, 8}) {
+            const int maxc = stage_f32_max_ctas_per_sm(ty);
+            for (int c = 1; c <= maxc; ++c) {
+                if ((rc = vlbm_batch_set_schedule(b, ty, c))) return rc;
+                double ms = 0.0;
+                if ((rc = vlbm_batch_profile(b, 2, &ms, nullptr))) return rc;
+                if (ms < best) {
+                    best = ms;
+                    best_ty = ty;
+                    best_c = c;
+                }
+            }
+        }
+        for (size_t r = 0; r < b->runs.size(); ++r) {
+            vlbm_t *h = b->runs[r];
+            BCK(b, cudaMemcpyAsync(h->F, backup[r], h->arr_bytes, cudaMemcpyDeviceToDevice, b->stream));
+            h->steps = 0;
+        }
+        BCK(b, cudaStreamSynchronize(b->stream));
+        for (void *p : backup) cudaFree(p);
+        b->steps = 0;
+        cache_store(cache_path, key, best_ty, best_c, best);
+    }
+    if ((rc = vlbm_batch_set_schedule(b, best_ty, best_c))) return rc;
+    if (tile_rows) *tile_rows = best_ty;
+    if (ctas_per_sm) *ctas_per_sm = best_c;
+    if (ms_per_step) *ms_per_step = best;
+    return VLBM_OK;
+}
+
+size_t vlbm_batch_cells(const vlbm_batch_t *b)
+{
+    size_t n = 0;
+    if (b)
+        for (const vlbm_t *h : b->runs) n += (size_t)h->nt * h->np;
+    return n;
+}
+
+const char *vlbm_batch_last_error(const vlbm_batch_t *b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+void vlbm_batch_destroy(vlbm_batch_t *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (vlbm_t *h : b->runs) vlbm_destroy(h);
+    if (b->d_runs) cudaFree(b->d_runs);
+    if (b->d_tms) cudaFree(b->d_tms);
+    if (b->d_work) cudaFree(b->d_work);
+    if (b->d_flags) cudaFree(b->d_flags);
+    if (b->h_flags) cudaFreeHost(b->h_flags);
+    for (int q = 0; q < 2; ++q)
+        if (b->ev[q]) cudaEventDestroy(b->ev[q]);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 }  // extern "C"

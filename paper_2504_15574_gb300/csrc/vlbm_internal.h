@@ -59,39 +59,45 @@ void launch_stage_f64(const StageD &p, cudaStream_t s);
 struct FaceConst { float sa1, sb1, sa2, sb2, sa3, sb3, corr, pad; };
 // Per interior row: s = sin(theta), 1/s, 1/(R s dphi), cot(theta)/R, 1/(eps s^2).
 struct RowF { float s, inv_s, inv_dph, cotR, kphi, pad0, pad1, pad2; };
-// Velocity-space constants as packed pairs (member x: a = 2g, member y: a = 2g+1).
-struct VelF {
-    float2 vth[2];       // (v[2g], v[2g+1])
-    float2 mvth[2];      // -(v[2g], v[2g+1])
-    float vphi[4];       // v[b]
-    float2 w2[8];        // (w[2g] w[b], w[2g+1] w[b])
-    float2 wr[8];        // w2 * rho_ref
-    float2 kpair[2][4];  // K along k_theta as pair coefficients: (K[2g][0],K[2g+1][1]), (K[2g][1],K[2g+1][0]),
-                         // (K[2g][2],K[2g+1][3]), (K[2g][3],K[2g+1][2])
-    float Kt[16];        // Ktilde[b][m]
-    float rho_ref;
-};
-
-struct StageF {
-    const float2 *in;       // stage input dg (read by TMA through the tensor map)
-    const float2 *fold;     // dg at the start of the step (own cell), stages 2 and 3
-    float2 *out;
-    const FaceConst *face;  // [nt+1][2]: face between rows fi-1 and fi, dir 0: v>0, 1: v<0
-    const RowF *row;        // [nt]
-    const float2 *rref;     // [nt][8] s * (FP64-derived tendency of the reference state)
-    const float *dsin;      // [nt + 2GR + TY] sin(pr) - sin(pr-1) at padded row pr (0 where undefined)
-    const float *d2sin;     // [nt + 2GR + TY] sin(pr-1) - 2 sin(pr) + sin(pr+1)
-    unsigned *err;          // device error flag (bit 0: TMA wait timeout)
+// Per-run parameters of the FP32 stage: one solver, or one member of a batch.
+struct RunF {
+    float2 *F, *A, *B;         // dg at the step start, after stage 1, after stage 2 (pair layout)
+    const FaceConst *face;     // [nt+1][2]: face between rows fi-1 and fi, dir 0: v>0, 1: v<0
+    const RowF *row;           // [nt]
+    const float2 *rref;        // [nt][8] s * (FP64-derived tendency of the reference state)
+    const float *dsin;         // [nt + 2GR + 8] sin(pr) - sin(pr-1) at padded row pr (0 where undefined)
+    const float *d2sin;        // [nt + 2GR + 8] sin(pr-1) - 2 sin(pr) + sin(pr+1)
     Layout L;
     float tau_inv, dt, ktheta, inv_dth;   // ktheta = 1/eps, inv_dth = 1/(R dtheta)
-    int stage;
-    VelF c;
+    float2 wr[8];              // w_k rho_ref per pair
+    float rho_ref;
+    int tiles_x;               // tiles per row of this run for the launch's tile shape
 };
-void launch_stage_f32(const CUtensorMap &tm_in, const StageF &p, cudaStream_t s);
-constexpr int F32_TILE_ROWS = 8;
+
+// Velocity-space constants shared by every run, pre-duplicated into pairs where they
+// multiply packed operands.
+struct VelC {
+    float2 vth[2];       // (v[2g], v[2g+1])
+    float2 mvth[2];      // -(v[2g], v[2g+1])
+    float2 vphi2[4];     // (v[b], v[b])
+    float2 vphisq2[4];   // (v[b]^2, v[b]^2)
+    float2 w2[8];        // (w[2g] w[b], w[2g+1] w[b])
+    float2 kpair[2][4];  // K along k_theta as pair coefficients: (K[2g][0],K[2g+1][1]), (K[2g][1],K[2g+1][0]),
+                         // (K[2g][2],K[2g+1][3]), (K[2g][3],K[2g+1][2])
+    float2 Kt2[16];      // (Ktilde[b][m], Ktilde[b][m])
+};
+
 constexpr int F32_TILE_COLS = 32;
-size_t stage_f32_smem_bytes();
-cudaError_t prepare_stage_f32();   // sets the kernel's dynamic shared-memory limit
+constexpr int F32_TILE_ROWS_MAX = 8;
+// One stage of one run, tile rows ty (4 or 8).  tm describes the stage input array.
+cudaError_t prepare_stage_f32();   // sets the kernels' dynamic shared-memory limits
+void launch_stage_f32(const CUtensorMap &tm_in, const RunF &run, const VelC &c, int stage, int ty,
+                      unsigned *err, cudaStream_t s);
+// One stage of a batch: a persistent grid of `ctas` CTAs walks `ntiles` work items
+// (run, tile) over the run table `runs` (device) and tensor maps `tms` ([run][3], device).
+void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
+                            int stage, int ty, int ctas, unsigned *err, cudaStream_t s);
+int stage_f32_max_ctas_per_sm(int ty);
 
 void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,
                      const double *T, const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s);

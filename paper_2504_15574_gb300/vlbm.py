@@ -36,7 +36,7 @@ class VlbmError(RuntimeError):
 class vlbm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("weno_eps", ctypes.c_double), ("radius", ctypes.c_double),
                 ("polar_filter", ctypes.c_int), ("guard", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("rho_ref", ctypes.c_double)]
+                ("rho_ref", ctypes.c_double), ("tile_rows", ctypes.c_int)]
 
 
 class vlbm_diag(ctypes.Structure):
@@ -67,6 +67,20 @@ SIGNATURES = {
     "vlbm_device_bytes": (ctypes.c_size_t, [_H]),
     "vlbm_last_error": (ctypes.c_char_p, [_H]),
     "vlbm_destroy": (None, [_H]),
+    "vlbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         _PD, _PD, ctypes.POINTER(vlbm_options), ctypes.POINTER(_H)]),
+    "vlbm_batch_init_moments": (ctypes.c_int, [_H, ctypes.c_int, _PD, _PD, _PD, _PD]),
+    "vlbm_batch_step": (ctypes.c_int, [_H, ctypes.c_int]),
+    "vlbm_batch_step_async": (ctypes.c_int, [_H, ctypes.c_int]),
+    "vlbm_batch_sync": (ctypes.c_int, [_H]),
+    "vlbm_batch_moments": (ctypes.c_int, [_H, ctypes.c_int, _PD, _PD, _PD, _PD]),
+    "vlbm_batch_set_schedule": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    "vlbm_batch_tune": (ctypes.c_int, [_H, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       _PD]),
+    "vlbm_batch_profile": (ctypes.c_int, [_H, ctypes.c_int, _PD, ctypes.POINTER(ctypes.c_int)]),
+    "vlbm_batch_cells": (ctypes.c_size_t, [_H]),
+    "vlbm_batch_last_error": (ctypes.c_char_p, [_H]),
+    "vlbm_batch_destroy": (None, [_H]),
 }
 
 
@@ -190,7 +204,7 @@ class Solver:
     """One vLBM solver on the GPU: ``Solver(n_theta, n_phi, tau, dt, precision="fp64"|"fp32")``."""
 
     def __init__(self, n_theta, n_phi, tau, dt, precision="fp64", eps=1e-6, R=1.0, polar_filter=False,
-                 guard=True, stream=None, rho_ref=0.0):
+                 guard=True, stream=None, rho_ref=0.0, tile_rows=0):
         o = vlbm_default_options()
         o.precision = VLBM_FP32 if precision in ("fp32", VLBM_FP32) else VLBM_FP64
         o.weno_eps = float(eps)
@@ -199,6 +213,7 @@ class Solver:
         o.guard = int(bool(guard))
         o.stream = stream
         o.rho_ref = float(rho_ref)
+        o.tile_rows = int(tile_rows)
         self.n_theta, self.n_phi = int(n_theta), int(n_phi)
         self.tau, self.dt = float(tau), float(dt)
         self.precision = "fp32" if o.precision == VLBM_FP32 else "fp64"
@@ -262,3 +277,87 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---- batched ensembles -----------------------------------------------------------
+
+def _bcheck(rc, b=None):
+    if rc != VLBM_OK:
+        msg = load().vlbm_batch_last_error(b)
+        raise VlbmError(rc, msg.decode() if msg else "")
+
+
+class Batch:
+    """Many FP32 runs of uneven grids advanced together (vlbm_batch_*).
+
+    grids: list of (n_theta, n_phi); tau, dt: scalars or per-run sequences."""
+
+    def __init__(self, grids, tau, dt, eps=1e-6, R=1.0, polar_filter=False, guard=True, stream=None):
+        lib = load()
+        n = len(grids)
+        self.grids = [(int(a), int(b)) for a, b in grids]
+        nt = (ctypes.c_int * n)(*[g[0] for g in self.grids])
+        np_ = (ctypes.c_int * n)(*[g[1] for g in self.grids])
+        taus = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, dtype=np.float64), (n,)))
+        dts = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)))
+        o = vlbm_default_options()
+        o.precision = VLBM_FP32
+        o.weno_eps = float(eps)
+        o.radius = float(R)
+        o.polar_filter = int(bool(polar_filter))
+        o.guard = int(bool(guard))
+        o.stream = stream
+        self.b = _H()
+        _bcheck(lib.vlbm_batch_create(n, nt, np_, _p(taus), _p(dts), ctypes.byref(o), ctypes.byref(self.b)))
+
+    def __len__(self):
+        return len(self.grids)
+
+    def init_moments(self, run, rho, u_theta, u_phi, T=None):
+        s = self.grids[run]
+        _bcheck(load().vlbm_batch_init_moments(self.b, int(run), _p(_host(rho, s)), _p(_host(u_theta, s)),
+                                               _p(_host(u_phi, s)), _p(_host(T, s))), self.b)
+
+    def step(self, n=1):
+        _bcheck(load().vlbm_batch_step(self.b, int(n)), self.b)
+
+    def step_async(self, n=1):
+        _bcheck(load().vlbm_batch_step_async(self.b, int(n)), self.b)
+
+    def sync(self):
+        _bcheck(load().vlbm_batch_sync(self.b), self.b)
+
+    def moments(self, run, with_T=False):
+        s = self.grids[run]
+        rho, ut, up = np.empty(s), np.empty(s), np.empty(s)
+        T = np.empty(s) if with_T else None
+        _bcheck(load().vlbm_batch_moments(self.b, int(run), _p(rho), _p(ut), _p(up), _p(T)), self.b)
+        return (rho, ut, up, T) if with_T else (rho, ut, up)
+
+    def set_schedule(self, tile_rows, ctas_per_sm=0):
+        _bcheck(load().vlbm_batch_set_schedule(self.b, int(tile_rows), int(ctas_per_sm)), self.b)
+
+    def tune(self, cache_path=None):
+        ty, c, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        path = cache_path.encode() if cache_path else None
+        _bcheck(load().vlbm_batch_tune(self.b, path, ctypes.byref(ty), ctypes.byref(c), ctypes.byref(ms)), self.b)
+        return {"tile_rows": ty.value, "ctas_per_sm": c.value, "ms_per_step": ms.value}
+
+    def profile(self, n=1):
+        ms, l = ctypes.c_double(), ctypes.c_int()
+        _bcheck(load().vlbm_batch_profile(self.b, int(n), ctypes.byref(ms), ctypes.byref(l)), self.b)
+        return ms.value, l.value
+
+    def cells(self):
+        return int(load().vlbm_batch_cells(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().vlbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,91 @@
+"""Batched ensembles (vlbm_batch_*): every member of a batch of uneven grids
+advances exactly as a standalone FP32 solver does (the batch only schedules the
+same stage computation), for every launch schedule; the autotuner picks a
+schedule, restores the state and caches its choice."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from parity import clamped_dt, require_gpu
+from paper_2504_15574_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    require_gpu()
+    from paper_2504_15574_gb300 import build, vlbm
+    build.build()
+    vlbm.load()
+    return vlbm
+
+
+GRIDS = [(16, 32), (24, 48), (13, 10), (64, 128), (32, 64), (6, 2)]
+TAU = 2e-3
+
+
+def _batch(V, **kw):
+    dts = [clamped_dt(nt, np_, TAU) for nt, np_ in GRIDS]
+    b = V.Batch(GRIDS, TAU, dts, **kw)
+    for r, (nt, np_) in enumerate(GRIDS):
+        b.init_moments(r, *inputs.gaussian_vortices(nt, np_, run=100 + r))
+    return b, dts
+
+
+def _singles(V, dts, steps):
+    out = []
+    for r, (nt, np_) in enumerate(GRIDS):
+        s = V.Solver(nt, np_, TAU, dts[r], precision="fp32")
+        s.init_moments(*inputs.gaussian_vortices(nt, np_, run=100 + r))
+        s.step(steps)
+        out.append(s.moments())
+        s.close()
+    return out
+
+
+@pytest.mark.parametrize("schedule", [(8, 0), (4, 0), (8, 1), (4, 2)])
+def test_batch_members_equal_standalone_solvers_bitwise(V, schedule):
+    b, dts = _batch(V)
+    b.set_schedule(*schedule)
+    b.step(20)
+    ref = _singles(V, dts, 20)
+    for r in range(len(GRIDS)):
+        got = b.moments(r)
+        for x, y in zip(got, ref[r]):
+            assert np.array_equal(x, y), (r, schedule)
+    b.close()
+
+
+def test_autotuner_restores_state_and_caches(V, tmp_path):
+    cache = str(tmp_path / "tune.json")
+    b, dts = _batch(V)
+    choice = b.tune(cache)
+    assert choice["tile_rows"] in (4, 8) and choice["ctas_per_sm"] >= 1 and choice["ms_per_step"] > 0
+    entries = json.load(open(cache))
+    assert len(entries) == 1
+    (key, val), = entries.items()
+    assert val["tile_rows"] == choice["tile_rows"] and "x64x128" in key
+    b.step(10)
+    ref = _singles(V, dts, 10)
+    for r in range(len(GRIDS)):
+        assert np.array_equal(b.moments(r)[0], ref[r][0])
+    # a second tune of the same grid mix comes from the cache
+    b2, _ = _batch(V)
+    assert b2.tune(cache) == choice
+    b.close()
+    b2.close()
+
+
+def test_batch_rejects_fp64(V):
+    import ctypes
+    with pytest.raises(V.VlbmError) as e:
+        o = V.vlbm_default_options()
+        h = V._H()
+        nt = (ctypes.c_int * 1)(16)
+        np_ = (ctypes.c_int * 1)(32)
+        t = np.array([1e-3])
+        V._bcheck(V.load().vlbm_batch_create(1, nt, np_, V._p(t), V._p(t), ctypes.byref(o), ctypes.byref(h)))
+    assert e.value.code == V.VLBM_ERR_UNSUPPORTED
