@@ -201,6 +201,45 @@ VLBM_API size_t vlbm_batch_cells(const vlbm_batch_t *b);
 VLBM_API const char *vlbm_batch_last_error(const vlbm_batch_t *b);
 VLBM_API void vlbm_batch_destroy(vlbm_batch_t *b);
 
+/* ---- Learned correction (not in the paper) -------------------------------------
+ * A 4-layer 3x3 convolutional network (4 -> 32 -> 32 -> 32 -> 3 channels, ReLU
+ * between) on a coarse grid, mapping the moments (rho, u^theta, u^phi, T) of a
+ * coarse FP32 solver after a step to a correction (drho, du^theta, du^phi)
+ * toward a finer run.  Padding follows the sphere: periodic in phi; beyond a
+ * pole, the row on the opposite meridian with the input's velocity channels
+ * negated (Sec. 3.6, Eq. bcs_theta, applied to moments).  BF16 activations and
+ * weights, FP32 accumulation on the tensor cores, FP32 master weights and Adam.
+ * Host arrays: inputs [4][n_theta][n_phi] (rho, u^theta, u^phi, T), targets and
+ * outputs [3][n_theta][n_phi] (drho, du^theta, du^phi), physical units; the
+ * network sees inputs / in_scale and predicts targets / out_scale.  Loss: the
+ * sin(theta)-area-weighted mean square of the scaled residual. */
+typedef struct vlbm_lc vlbm_lc_t;
+
+/* Creates a network for an n_theta x n_phi grid (n_phi even) with weights drawn
+ * from splitmix64(seed). */
+VLBM_API int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **out);
+/* Number of FP32 parameters; layout per layer l = 0..3: W[co][ci][3][3] then b[co]. */
+VLBM_API int vlbm_lc_num_params(const vlbm_lc_t *lc);
+VLBM_API int vlbm_lc_get_weights(vlbm_lc_t *lc, float *w);
+/* Sets the weights and resets the Adam state. */
+VLBM_API int vlbm_lc_set_weights(vlbm_lc_t *lc, const float *w);
+/* in_scale[4] divides (rho-1, u^theta, u^phi, T-1); out_scale[3] multiplies the outputs. */
+VLBM_API int vlbm_lc_set_scales(vlbm_lc_t *lc, const double *in_scale, const double *out_scale);
+/* Forward pass: outputs in physical units (drho not mean-corrected). */
+VLBM_API int vlbm_lc_predict(vlbm_lc_t *lc, const double *inputs, double *outputs);
+/* Loss and its gradient with respect to every parameter (grad: num_params floats; either may be NULL). */
+VLBM_API int vlbm_lc_gradients(vlbm_lc_t *lc, const double *inputs, const double *targets, double *loss,
+                               float *grad);
+/* One Adam step (beta 0.9 / 0.999) on one (inputs, targets) sample; returns the loss before the step. */
+VLBM_API int vlbm_lc_train_step(vlbm_lc_t *lc, const double *inputs, const double *targets, float lr,
+                                double *loss);
+/* Corrects an FP32 solver on the network's grid in place: moments of its state,
+ * forward pass, drho with its area mean removed (mass is kept), then
+ * f += f^eq(rho + drho, u + du) - f^eq(rho, u) (Eq. feq_Q=4).  Device-resident. */
+VLBM_API int vlbm_lc_apply(vlbm_lc_t *lc, vlbm_t *h);
+VLBM_API const char *vlbm_lc_last_error(const vlbm_lc_t *lc);
+VLBM_API void vlbm_lc_destroy(vlbm_lc_t *lc);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,8 @@ UNITS = {
     "stage_f64.cu": ["-fmad=false"],
     "stage_f32.cu": [],
     "aux.cu": [],
+    "lc.cu": [],
+    "lc_api.cu": [],
 }
 
 

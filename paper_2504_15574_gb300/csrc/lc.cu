@@ -1,0 +1,581 @@
+// lc.cu -- learned correction for a coarse vLBM (not in the paper).
+//
+// A small convolutional network nudges the moments of a coarse FP32 solver
+// toward those of a finer run after each coarse step.  Layers: 3x3 convolutions
+// 4 -> H -> H -> H -> 3 with ReLU between, on the coarse cell grid.  Padding
+// follows the boundary conditions of the sphere (arXiv 2504.15574 Sec. 3.6):
+// periodic in phi, and beyond a pole the row on the opposite meridian
+// (column + N_phi/2) with the vector channels (u^theta, u^phi of the input
+// layer) negated.
+//
+// Arithmetic: activations and weights in BF16, products accumulated in FP32 on
+// the tensor cores (mma.sync m16n8k16, BF16 in, FP32 out); master weights, Adam
+// moments, losses and gradients of the weights in FP32.  Every convolution,
+// forward and backward, is a "valid" 3x3 convolution over an explicitly padded
+// channels-last tensor [rows][cols][channels]:
+//   forward:        Y  = conv(pad(X), W)
+//   backward data:  dP = conv(zero-pad-2(dY), W flipped and transposed), then the
+//                   adjoint of pad() folds ghost gradients onto their sources;
+//   backward weight: dW[co][tap][ci] = sum_p dY[p][co] pad(X)[p + tap][ci].
+#include <cuda_bf16.h>
+
+#include "vlbm_internal.h"
+#include "lc_internal.h"
+
+namespace vk {
+
+namespace {
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x = lo (low 16 bits), .y = hi
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+__device__ __forceinline__ unsigned pack_raw(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    __nv_bfloat162 v;
+    v.x = lo;
+    v.y = hi;
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+// D = A (16x16 bf16, row) * B (16x8 bf16, col) + C, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(float d[4], const unsigned a[4], const unsigned b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ---- padding and its adjoint ------------------------------------------------------
+// X [H][W][C] -> Xp [H+2][W+2][C]; ghost rows take the mirrored row at column + W/2,
+// with the channels in `negmask` negated; ghost columns wrap.
+__global__ void pad_kernel(const __nv_bfloat16 *X, int H, int W, int C, unsigned negmask, __nv_bfloat16 *Xp)
+{
+    const int c = threadIdx.x;           // blockDim.x = C
+    const int xp = blockIdx.x, yp = blockIdx.y;
+    if (c >= C) return;
+    int y = yp - 1, x = xp - 1;
+    bool flip = false;
+    if (y < 0) {
+        y = 0;
+        x += W / 2;
+        flip = true;
+    } else if (y >= H) {
+        y = H - 1;
+        x += W / 2;
+        flip = true;
+    }
+    x %= W;
+    if (x < 0) x += W;
+    __nv_bfloat16 v = X[((size_t)y * W + x) * C + c];
+    if (flip && ((negmask >> c) & 1u)) v = __hneg(v);
+    Xp[((size_t)yp * (W + 2) + xp) * C + c] = v;
+}
+
+// adjoint of pad_kernel: dX[y][x] = dXp[y+1][x+1] + ghost copies that read (y, x)
+__global__ void unpad_kernel(const float *dXp, int H, int W, int C, unsigned negmask, float *dX)
+{
+    const int c = threadIdx.x;
+    const int x = blockIdx.x, y = blockIdx.y;
+    if (c >= C) return;
+    const int Wp = W + 2;
+    auto at = [&](int yp, int xp) { return dXp[((size_t)yp * Wp + xp) * C + c]; };
+    float s = at(y + 1, x + 1);
+    // ghost columns (xp = 0 reads x = W-1, xp = W+1 reads x = 0), in the interior rows
+    if (x == W - 1) s += at(y + 1, 0);
+    if (x == 0) s += at(y + 1, W + 1);
+    // ghost rows: row yp = 0 (or H+1), column xp reads row 0 (or H-1) at column xp-1+W/2 (mod W)
+    const float sg = ((negmask >> c) & 1u) ? -1.0f : 1.0f;
+    for (int pole = 0; pole < 2; ++pole) {
+        const int yrow = pole ? H - 1 : 0;
+        if (y != yrow) continue;
+        const int yp = pole ? H + 1 : 0;
+        for (int xp = 0; xp < Wp; ++xp) {
+            int xs = (xp - 1 + W / 2) % W;
+            if (xs < 0) xs += W;
+            if (xs == x) s += sg * at(yp, xp);
+        }
+    }
+    dX[((size_t)y * W + x) * C + c] = s;
+}
+
+// ---- valid 3x3 convolution on the tensor cores --------------------------------------
+// Xp [Hp][Wp][Ci] bf16 (Ci multiple of 16), Wt [Co][9][Ci] bf16 (Co multiple of 8, <= 32),
+// out [Hp-2][Wp-2][Co]: Yf (fp32, optional) and Yb (bf16, optional, after ReLU if relu).
+// CTA: one output row, 64 consecutive output columns, 4 warps of 16 pixels.
+constexpr int CONV_PIX = 64;
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16 *Xp, int Hp, int Wp,
+                                                       const __nv_bfloat16 *Wt, const float *bias, float *Yf,
+                                                       __nv_bfloat16 *Yb, int relu)
+{
+    constexpr int XS = CI + 8;           // padded channel stride in shared memory (bank spread)
+    constexpr int WS = 9 * CI + 8;
+    __shared__ __align__(16) __nv_bfloat16 xs[3][CONV_PIX + 2][XS];
+    __shared__ __align__(16) __nv_bfloat16 ws[CO][WS];
+    const int Ho = Hp - 2, Wo = Wp - 2;
+    const int y = blockIdx.y, x0 = blockIdx.x * CONV_PIX;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // stage the input rows y..y+2, columns x0..x0+65 (zero beyond Wp) and the weights
+    for (int e = tid; e < 3 * (CONV_PIX + 2) * CI; e += blockDim.x) {
+        const int c = e % CI, rest = e / CI, xx = rest % (CONV_PIX + 2), r = rest / (CONV_PIX + 2);
+        const int gx = x0 + xx;
+        xs[r][xx][c] = (gx < Wp) ? Xp[((size_t)(y + r) * Wp + gx) * CI + c] : __float2bfloat16(0.0f);
+    }
+    for (int e = tid; e < CO * 9 * CI; e += blockDim.x) ws[e / (9 * CI)][e % (9 * CI)] = Wt[e];
+    __syncthreads();
+
+    const int g = lane >> 2, t = lane & 3;
+    float acc[CO / 8][4];
+#pragma unroll
+    for (int nb = 0; nb < CO / 8; ++nb)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[nb][q] = 0.0f;
+    const int pbase = warp * 16;        // this warp's first pixel within the CTA tile
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+        for (int kc = 0; kc < CI / 16; ++kc) {
+            const int k0 = kc * 16 + 2 * t;
+            unsigned a[4];
+            a[0] = *reinterpret_cast<const unsigned *>(&xs[dy][pbase + g + dx][k0]);
+            a[1] = *reinterpret_cast<const unsigned *>(&xs[dy][pbase + g + 8 + dx][k0]);
+            a[2] = *reinterpret_cast<const unsigned *>(&xs[dy][pbase + g + dx][k0 + 8]);
+            a[3] = *reinterpret_cast<const unsigned *>(&xs[dy][pbase + g + 8 + dx][k0 + 8]);
+#pragma unroll
+            for (int nb = 0; nb < CO / 8; ++nb) {
+                unsigned b[2];
+                b[0] = *reinterpret_cast<const unsigned *>(&ws[nb * 8 + g][tap * CI + k0]);
+                b[1] = *reinterpret_cast<const unsigned *>(&ws[nb * 8 + g][tap * CI + k0 + 8]);
+                mma_bf16(acc[nb], a, b);
+            }
+        }
+    }
+    // epilogue: rows g and g+8 of the warp tile, columns 2t, 2t+1 of each n-block
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int x = x0 + pbase + g + 8 * half;
+        if (x >= Wo) continue;
+        const size_t o = ((size_t)y * Wo + x) * CO;
+#pragma unroll
+        for (int nb = 0; nb < CO / 8; ++nb) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int co = nb * 8 + 2 * t + u;
+                float v = acc[nb][2 * half + u] + (bias ? bias[co] : 0.0f);
+                if (Yf) Yf[o + co] = v;
+                if (relu) v = fmaxf(v, 0.0f);
+                if (Yb) Yb[o + co] = __float2bfloat16(v);
+            }
+        }
+    }
+    (void)Ho;
+}
+
+// ---- weight gradient on the tensor cores ---------------------------------------------
+// dY [H][W][CO] bf16 (gradient at the pre-activation), Xp [H+2][W+2][CI] bf16.
+// One CTA per output row: part[row][9][CO][CI] and partb[row][CO] (bias) in FP32.
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) wgrad_kernel(const __nv_bfloat16 *dY, const __nv_bfloat16 *Xp, int H, int W,
+                                                     float *part, float *partb)
+{
+    constexpr int NPIX = 64;
+    __shared__ __align__(16) __nv_bfloat16 dys[NPIX][CO + 8];
+    __shared__ __align__(16) __nv_bfloat16 xs[3][NPIX + 2][CI + 8];
+    const int y = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    // warp w: taps w, w+4, w+8 (<9); each tap: (CO/16) x (CI/8) accumulator tiles
+    float acc[3][CO / 16][CI / 8][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int m = 0; m < CO / 16; ++m)
+#pragma unroll
+            for (int n = 0; n < CI / 8; ++n)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[a][m][n][q] = 0.0f;
+    float bsum = 0.0f;
+    for (int x0 = 0; x0 < W; x0 += NPIX) {
+        __syncthreads();
+        for (int e = tid; e < NPIX * CO; e += blockDim.x) {
+            const int p = e / CO, c = e % CO;
+            dys[p][c] = (x0 + p < W) ? dY[((size_t)y * W + x0 + p) * CO + c] : __float2bfloat16(0.0f);
+        }
+        for (int e = tid; e < 3 * (NPIX + 2) * CI; e += blockDim.x) {
+            const int c = e % CI, rest = e / CI, xx = rest % (NPIX + 2), r = rest / (NPIX + 2);
+            const int gx = x0 + xx;
+            xs[r][xx][c] = (gx < W + 2) ? Xp[((size_t)(y + r) * (W + 2) + gx) * CI + c] : __float2bfloat16(0.0f);
+        }
+        __syncthreads();
+        if (tid < CO)
+            for (int p = 0; p < NPIX; ++p) bsum += __bfloat162float(dys[p][tid]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int tap = warp + 4 * a;
+            if (tap >= 9) break;
+            const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+            for (int ks = 0; ks < NPIX / 16; ++ks) {
+                const int p0 = ks * 16 + 2 * t;   // k = pixel
+#pragma unroll
+                for (int m = 0; m < CO / 16; ++m) {
+                    // A[m = co][k = pixel] = dY[pixel][co]
+                    unsigned av[4];
+                    const int co0 = m * 16 + g;
+                    av[0] = pack_raw(dys[p0][co0], dys[p0 + 1][co0]);
+                    av[1] = pack_raw(dys[p0][co0 + 8], dys[p0 + 1][co0 + 8]);
+                    av[2] = pack_raw(dys[p0 + 8][co0], dys[p0 + 9][co0]);
+                    av[3] = pack_raw(dys[p0 + 8][co0 + 8], dys[p0 + 9][co0 + 8]);
+#pragma unroll
+                    for (int n = 0; n < CI / 8; ++n) {
+                        // B[k = pixel][n = ci] = Xp[y + dy][pixel + dx][ci]
+                        const int ci = n * 8 + g;
+                        unsigned bv[2];
+                        bv[0] = pack_raw(xs[dy][p0 + dx][ci], xs[dy][p0 + 1 + dx][ci]);
+                        bv[1] = pack_raw(xs[dy][p0 + 8 + dx][ci], xs[dy][p0 + 9 + dx][ci]);
+                        mma_bf16(acc[a][m][n], av, bv);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int tap = warp + 4 * a;
+        if (tap >= 9) break;
+#pragma unroll
+        for (int m = 0; m < CO / 16; ++m)
+#pragma unroll
+            for (int n = 0; n < CI / 8; ++n)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int co = m * 16 + g + 8 * (q >> 1);
+                    const int ci = n * 8 + 2 * t + (q & 1);
+                    part[(((size_t)y * 9 + tap) * CO + co) * CI + ci] = acc[a][m][n][q];
+                }
+    }
+    if (tid < CO) partb[(size_t)y * CO + tid] = bsum;
+}
+
+// sums partials over rows in order: out[i] = sum_r part[r][i]
+__global__ void reduce_rows_kernel(const float *part, int rows, int n, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int r = 0; r < rows; ++r) s += part[(size_t)r * n + i];
+    out[i] = s;
+}
+
+// ---- elementwise pieces -------------------------------------------------------------
+// dP (bf16, zero-padded by 2 on rows and columns, channel count CP >= C) from the
+// FP32 gradient at a layer output and the ReLU mask of that output (mask NULL: none).
+__global__ void grad_pad2_kernel(const float *dY, const __nv_bfloat16 *act, int H, int W, int C, int CP,
+                                 __nv_bfloat16 *dP)
+{
+    const int c = threadIdx.x;
+    const int xp = blockIdx.x, yp = blockIdx.y;
+    if (c >= CP) return;
+    const int y = yp - 2, x = xp - 2;
+    float v = 0.0f;
+    if (c < C && y >= 0 && y < H && x >= 0 && x < W) {
+        const size_t i = ((size_t)y * W + x) * C + c;
+        v = dY[i];
+        if (act && __bfloat162float(act[i]) <= 0.0f) v = 0.0f;
+    }
+    dP[((size_t)yp * (W + 4) + xp) * CP + c] = __float2bfloat16(v);
+}
+
+// the un-padded gradient at the pre-activation (bf16), for the weight gradient
+__global__ void grad_pre_kernel(const float *dY, const __nv_bfloat16 *act, int n, int C, int CP,
+                                __nv_bfloat16 *dPre)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * CP) return;
+    const int c = i % CP, p = i / CP;
+    float v = 0.0f;
+    if (c < C) {
+        v = dY[(size_t)p * C + c];
+        if (act && __bfloat162float(act[(size_t)p * C + c]) <= 0.0f) v = 0.0f;
+    }
+    dPre[i] = __float2bfloat16(v);
+}
+
+// area-weighted mean-square loss against targets [3][H][W] (scaled), gradient into dY [H][W][CO]
+__global__ void loss_kernel(const float *Y, int CO, const double *target, const double *sin_t, int H, int W,
+                            float3 inv_scale, double wsum, float *dY, double *part)
+{
+    __shared__ double red[256];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < H * W) {
+        const int y = i / W;
+        const double w = sin_t[y] / wsum;
+        const float sc[3] = {inv_scale.x, inv_scale.y, inv_scale.z};
+        for (int c = 0; c < CO; ++c) {
+            float g = 0.0f;
+            if (c < 3) {
+                const double d = (double)Y[(size_t)i * CO + c] - target[(size_t)c * H * W + i] * sc[c];
+                l += w * d * d / 3.0;
+                g = (float)(2.0 * w * d / 3.0);
+            }
+            dY[(size_t)i * CO + c] = g;
+        }
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sum_kernel(const double *part, int n, double *out)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// Adam on FP32 master weights (bias-corrected), then the bf16 copies.
+__global__ void adam_kernel(float *w, const float *g, float *m, float *v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// bf16 weight layouts of one layer from its FP32 master [CO][CI][3][3]:
+//   fwd [COp][9][CIp] and bwd-data [CIp2][9][COp2] (taps flipped, channels swapped)
+__global__ void weights_bf16_kernel(const float *w, int CO, int CI, int COp, int CIp, __nv_bfloat16 *fwd, int CIp2,
+                                    int COp2, __nv_bfloat16 *bwd)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < COp * 9 * CIp) {
+        const int ci = i % CIp, tap = (i / CIp) % 9, co = i / (9 * CIp);
+        fwd[i] = __float2bfloat16((co < CO && ci < CI) ? w[((size_t)co * CI + ci) * 9 + tap] : 0.0f);
+    }
+    if (bwd && i < CIp2 * 9 * COp2) {
+        const int co = i % COp2, tap = (i / COp2) % 9, ci = i / (9 * COp2);
+        const int ftap = 8 - tap;
+        bwd[i] = __float2bfloat16((co < CO && ci < CI) ? w[((size_t)co * CI + ci) * 9 + ftap] : 0.0f);
+    }
+}
+
+// weight gradient from [9][CO][CI] into the master layout [CO][CI][3][3]
+__global__ void wgrad_layout_kernel(const float *g9, int CO, int CI, int COp, int CIp, float *g)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= CO * CI * 9) return;
+    const int tap = i % 9, ci = (i / 9) % CI, co = i / (9 * CI);
+    g[i] = g9[((size_t)tap * COp + co) * CIp + ci];
+}
+
+// network input from the moments of a coarse solver: [(rho-1)/s0, ut/s1, up/s2, (T-1)/s3, 0 ...]
+__global__ void features_kernel(const double *rho, const double *ut, const double *up, const double *T, int n,
+                                float4 inv_scale, __nv_bfloat16 *X0)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v[LC_CIN] = {0};
+    v[0] = (float)((rho[i] - 1.0) * inv_scale.x);
+    v[1] = (float)(ut[i] * inv_scale.y);
+    v[2] = (float)(up[i] * inv_scale.z);
+    v[3] = (float)((T ? T[i] - 1.0 : 0.0) * inv_scale.w);
+#pragma unroll
+    for (int c = 0; c < LC_CIN; ++c) X0[(size_t)i * LC_CIN + c] = __float2bfloat16(v[c]);
+}
+
+// output [H][W][CO] -> (drho, dut, dup) [3][H][W] in physical units, and sin-weighted drho partial sums
+__global__ void outputs_kernel(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out,
+                               double *part)
+{
+    __shared__ double red[256];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (i < H * W) {
+        const double d0 = (double)Y[(size_t)i * CO + 0] * scale.x;
+        out[i] = d0;
+        out[(size_t)H * W + i] = (double)Y[(size_t)i * CO + 1] * scale.y;
+        out[(size_t)2 * H * W + i] = (double)Y[(size_t)i * CO + 2] * scale.z;
+        s = d0 * sin_t[i / W];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__device__ __forceinline__ double feq_lc(double n, double wk, double va, double vb, double ut, double up)
+{
+    const double xi = va * ut + vb * up;
+    const double u2 = ut * ut + up * up;
+    return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
+}
+
+// f += feq(rho + drho - mean, u + du) - feq(rho, u), on the FP32 pair layout (dg = s (f - w rho_ref))
+__global__ void nudge_kernel(float2 *f, const Layout L, const double *mom, const double *delta, const double *mean,
+                             double wsum, const VelD c, const double *sin_t)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= L.np) return;
+    const size_t n = (size_t)L.nt * L.np, cell = (size_t)i * L.np + j;
+    const double rho = mom[cell], ut = mom[n + cell], up = mom[2 * n + cell];
+    const double r2 = rho + delta[cell] - (*mean) / wsum, u2t = ut + delta[n + cell], u2p = up + delta[2 * n + cell];
+    const double s = sin_t[i];
+    for (int q = 0; q < 8; ++q) {
+        const int g = q >> 2, b = q & 3;
+        float2 v = f[L.at(q, i, j)];
+        const int a0 = 2 * g, a1 = 2 * g + 1;
+        const double d0 = feq_lc(r2, c.w[a0] * c.w[b], c.v[a0], c.v[b], u2t, u2p) -
+                          feq_lc(rho, c.w[a0] * c.w[b], c.v[a0], c.v[b], ut, up);
+        const double d1 = feq_lc(r2, c.w[a1] * c.w[b], c.v[a1], c.v[b], u2t, u2p) -
+                          feq_lc(rho, c.w[a1] * c.w[b], c.v[a1], c.v[b], ut, up);
+        v.x = (float)((double)v.x + s * d0);
+        v.y = (float)((double)v.y + s * d1);
+        f[L.at(q, i, j)] = v;
+    }
+}
+
+template <int CI, int CO>
+void conv_launch(const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias, float *Yf,
+                 __nv_bfloat16 *Yb, int relu, cudaStream_t s)
+{
+    dim3 grid((Wp - 2 + CONV_PIX - 1) / CONV_PIX, Hp - 2);
+    conv3x3_kernel<CI, CO><<<grid, 128, 0, s>>>(Xp, Hp, Wp, Wt, bias, Yf, Yb, relu);
+}
+
+template <int CI, int CO>
+void wgrad_launch(const __nv_bfloat16 *dY, const __nv_bfloat16 *Xp, int H, int W, float *part, float *partb,
+                  cudaStream_t s)
+{
+    wgrad_kernel<CI, CO><<<H, 128, 0, s>>>(dY, Xp, H, W, part, partb);
+}
+
+}  // namespace
+
+// ---- the network ----------------------------------------------------------------------
+// Layer l: CI_l -> CO_l; padded channel counts: input 16 (4 used), hidden 32, output 8 (3 used).
+void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
+             float *Yf, __nv_bfloat16 *Yb, int relu, cudaStream_t s)
+{
+    if (layer == 0) conv_launch<LC_CIN, LC_HID>(Xp, Hp, Wp, Wt, bias, Yf, Yb, relu, s);
+    else if (layer < LC_LAYERS - 1) conv_launch<LC_HID, LC_HID>(Xp, Hp, Wp, Wt, bias, Yf, Yb, relu, s);
+    else conv_launch<LC_HID, LC_COUT>(Xp, Hp, Wp, Wt, bias, Yf, Yb, relu, s);
+}
+
+// backward-data convolution of layer l >= 1: input dP [H+4][W+4][COp2], output dXp [H+2][W+2][CI_l]
+void lc_conv_bwd(int layer, const __nv_bfloat16 *dP, int H, int W, const __nv_bfloat16 *Wb, float *dXp, cudaStream_t s)
+{
+    if (layer < LC_LAYERS - 1) conv_launch<LC_HID, LC_HID>(dP, H + 4, W + 4, Wb, nullptr, dXp, nullptr, 0, s);
+    else conv_launch<LC_COUTP2, LC_HID>(dP, H + 4, W + 4, Wb, nullptr, dXp, nullptr, 0, s);
+}
+
+void lc_wgrad(int layer, const __nv_bfloat16 *dPre, const __nv_bfloat16 *Xp, int H, int W, float *part, float *partb,
+              cudaStream_t s)
+{
+    if (layer == 0) wgrad_launch<LC_CIN, LC_HID>(dPre, Xp, H, W, part, partb, s);
+    else if (layer < LC_LAYERS - 1) wgrad_launch<LC_HID, LC_HID>(dPre, Xp, H, W, part, partb, s);
+    else wgrad_launch<LC_HID, LC_COUTP2>(dPre, Xp, H, W, part, partb, s);
+}
+
+void lc_pad(const __nv_bfloat16 *X, int H, int W, int C, unsigned negmask, __nv_bfloat16 *Xp, cudaStream_t s)
+{
+    pad_kernel<<<dim3(W + 2, H + 2), C, 0, s>>>(X, H, W, C, negmask, Xp);
+}
+
+void lc_unpad(const float *dXp, int H, int W, int C, unsigned negmask, float *dX, cudaStream_t s)
+{
+    unpad_kernel<<<dim3(W, H), C, 0, s>>>(dXp, H, W, C, negmask, dX);
+}
+
+void lc_grad_pad2(const float *dY, const __nv_bfloat16 *act, int H, int W, int C, int CP, __nv_bfloat16 *dP,
+                  cudaStream_t s)
+{
+    grad_pad2_kernel<<<dim3(W + 4, H + 4), CP, 0, s>>>(dY, act, H, W, C, CP, dP);
+}
+
+void lc_grad_pre(const float *dY, const __nv_bfloat16 *act, int n, int C, int CP, __nv_bfloat16 *dPre, cudaStream_t s)
+{
+    grad_pre_kernel<<<(n * CP + 255) / 256, 256, 0, s>>>(dY, act, n, C, CP, dPre);
+}
+
+void lc_reduce_rows(const float *part, int rows, int n, float *out, cudaStream_t s)
+{
+    reduce_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(part, rows, n, out);
+}
+
+void lc_loss(const float *Y, int CO, const double *target, const double *sin_t, int H, int W, float3 inv_scale,
+             double wsum, float *dY, double *part, double *loss, cudaStream_t s)
+{
+    const int nb = (H * W + 255) / 256;
+    loss_kernel<<<nb, 256, 0, s>>>(Y, CO, target, sin_t, H, W, inv_scale, wsum, dY, part);
+    sum_kernel<<<1, 256, 0, s>>>(part, nb, loss);
+}
+
+void lc_adam(float *w, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps, float c1,
+             float c2, cudaStream_t s)
+{
+    adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, lr, b1, b2, eps, c1, c2);
+}
+
+void lc_weights_bf16(const float *w, int CO, int CI, int COp, int CIp, __nv_bfloat16 *fwd, int CIp2, int COp2,
+                     __nv_bfloat16 *bwd, cudaStream_t s)
+{
+    const int n = max(COp * 9 * CIp, CIp2 * 9 * COp2);
+    weights_bf16_kernel<<<(n + 255) / 256, 256, 0, s>>>(w, CO, CI, COp, CIp, fwd, CIp2, COp2, bwd);
+}
+
+void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g, cudaStream_t s)
+{
+    const int n = CO * CI * 9;
+    wgrad_layout_kernel<<<(n + 255) / 256, 256, 0, s>>>(g9, CO, CI, COp, CIp, g);
+}
+
+void lc_features(const double *rho, const double *ut, const double *up, const double *T, int n, float4 inv_scale,
+                 __nv_bfloat16 *X0, cudaStream_t s)
+{
+    features_kernel<<<(n + 255) / 256, 256, 0, s>>>(rho, ut, up, T, n, inv_scale, X0);
+}
+
+void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
+                double *mean, cudaStream_t s)
+{
+    const int nb = (H * W + 255) / 256;
+    outputs_kernel<<<nb, 256, 0, s>>>(Y, CO, H, W, scale, sin_t, out, part);
+    sum_kernel<<<1, 256, 0, s>>>(part, nb, mean);
+}
+
+void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,
+              const VelD &c, const double *sin_t, cudaStream_t s)
+{
+    dim3 grid((L.np + 127) / 128, L.nt);
+    nudge_kernel<<<grid, 128, 0, s>>>(f, L, mom, delta, mean, wsum, c, sin_t);
+}
+
+}  // namespace vk

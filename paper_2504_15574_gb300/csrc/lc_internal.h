@@ -1,0 +1,43 @@
+// lc_internal.h -- shapes and launchers of the learned-correction network (lc.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "vlbm_internal.h"
+
+namespace vk {
+
+constexpr int LC_LAYERS = 4;
+constexpr int LC_IN = 4;        // rho - 1, u^theta, u^phi, T - 1
+constexpr int LC_CIN = 16;      // input channels padded for the k = 16 tensor-core step
+constexpr int LC_HID = 32;      // hidden channels
+constexpr int LC_OUT = 3;       // drho, du^theta, du^phi
+constexpr int LC_COUT = 8;      // output channels padded to an n = 8 tile
+constexpr int LC_COUTP2 = 16;   // output-gradient channels padded for the k = 16 step (backward data)
+
+void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
+             float *Yf, __nv_bfloat16 *Yb, int relu, cudaStream_t s);
+void lc_conv_bwd(int layer, const __nv_bfloat16 *dP, int H, int W, const __nv_bfloat16 *Wb, float *dXp, cudaStream_t s);
+void lc_wgrad(int layer, const __nv_bfloat16 *dPre, const __nv_bfloat16 *Xp, int H, int W, float *part, float *partb,
+              cudaStream_t s);
+void lc_pad(const __nv_bfloat16 *X, int H, int W, int C, unsigned negmask, __nv_bfloat16 *Xp, cudaStream_t s);
+void lc_unpad(const float *dXp, int H, int W, int C, unsigned negmask, float *dX, cudaStream_t s);
+void lc_grad_pad2(const float *dY, const __nv_bfloat16 *act, int H, int W, int C, int CP, __nv_bfloat16 *dP,
+                  cudaStream_t s);
+void lc_grad_pre(const float *dY, const __nv_bfloat16 *act, int n, int C, int CP, __nv_bfloat16 *dPre, cudaStream_t s);
+void lc_reduce_rows(const float *part, int rows, int n, float *out, cudaStream_t s);
+void lc_loss(const float *Y, int CO, const double *target, const double *sin_t, int H, int W, float3 inv_scale,
+             double wsum, float *dY, double *part, double *loss, cudaStream_t s);
+void lc_adam(float *w, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps, float c1,
+             float c2, cudaStream_t s);
+void lc_weights_bf16(const float *w, int CO, int CI, int COp, int CIp, __nv_bfloat16 *fwd, int CIp2, int COp2,
+                     __nv_bfloat16 *bwd, cudaStream_t s);
+void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g, cudaStream_t s);
+void lc_features(const double *rho, const double *ut, const double *up, const double *T, int n, float4 inv_scale,
+                 __nv_bfloat16 *X0, cudaStream_t s);
+void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
+                double *mean, cudaStream_t s);
+void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,
+              const VelD &c, const double *sin_t, cudaStream_t s);
+
+}  // namespace vk

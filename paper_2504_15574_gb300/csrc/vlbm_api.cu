@@ -16,48 +16,9 @@
 
 #include "../../include/vlbm.h"
 #include "vlbm_internal.h"
+#include "vlbm_handle.h"
 
 using namespace vk;
-
-struct vlbm {
-    int nt = 0, np = 0, prec = VLBM_FP64;
-    double tau = 0, dt = 0, eps = 1e-6, R = 1.0;
-    int filter = 0, guard = 1;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    Layout L{};
-    size_t elem = 8;
-    void *F = nullptr, *A = nullptr, *B = nullptr;
-    size_t arr_bytes = 0;
-    // FP64 geometry
-    double *d_sin_ext = nullptr, *d_cot = nullptr, *d_sin_t = nullptr, *d_cos_t = nullptr;
-    std::vector<double> sin_t, cos_t;
-    // FP32 tables
-    float2 *d_rref = nullptr;
-    float *d_dsin = nullptr, *d_d2sin = nullptr;
-    FaceConst *d_face = nullptr;
-    RowF *d_row = nullptr;
-    // polar filter
-    int *d_frows = nullptr, *d_fblocks = nullptr;
-    int nfrows = 0;
-    // diagnostics, budget, I/O scratch
-    double *d_pole = nullptr, *d_budget = nullptr, *d_mom = nullptr, *d_dense = nullptr;
-    double *d_part = nullptr, *d_diag = nullptr;
-    unsigned *d_flags = nullptr, *h_flags = nullptr;
-    CUtensorMap tmF{}, tmA{}, tmB{};
-    cudaGraphExec_t g1 = nullptr, g16 = nullptr;
-    VelD vd{};
-    VelC vc{};     // FP32 path: packed velocity constants
-    RunF run{};    // FP32 path: per-run stage parameters
-    int ty = 8;    // FP32 path: tile rows
-    double rho_ref = 0.0, rho_ref_opt = 0.0;
-    long long steps = 0;
-    double mass0 = 0.0;
-    std::string err;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    double prof_ms[3] = {0, 0, 0};
-    size_t dev_bytes = 0;
-};
 
 namespace {
 

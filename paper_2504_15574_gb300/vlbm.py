@@ -81,6 +81,17 @@ SIGNATURES = {
     "vlbm_batch_cells": (ctypes.c_size_t, [_H]),
     "vlbm_batch_last_error": (ctypes.c_char_p, [_H]),
     "vlbm_batch_destroy": (None, [_H]),
+    "vlbm_lc_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(_H)]),
+    "vlbm_lc_num_params": (ctypes.c_int, [_H]),
+    "vlbm_lc_get_weights": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float)]),
+    "vlbm_lc_set_weights": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float)]),
+    "vlbm_lc_set_scales": (ctypes.c_int, [_H, _PD, _PD]),
+    "vlbm_lc_predict": (ctypes.c_int, [_H, _PD, _PD]),
+    "vlbm_lc_gradients": (ctypes.c_int, [_H, _PD, _PD, _PD, ctypes.POINTER(ctypes.c_float)]),
+    "vlbm_lc_train_step": (ctypes.c_int, [_H, _PD, _PD, ctypes.c_float, _PD]),
+    "vlbm_lc_apply": (ctypes.c_int, [_H, _H]),
+    "vlbm_lc_last_error": (ctypes.c_char_p, [_H]),
+    "vlbm_lc_destroy": (None, [_H]),
 }
 
 
@@ -355,6 +366,76 @@ class Batch:
         if getattr(self, "b", None):
             load().vlbm_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- learned correction ----------------------------------------------------------
+
+class LearnedCorrection:
+    """The coarse-grid correction network (vlbm_lc_*)."""
+
+    def __init__(self, n_theta, n_phi, seed=1, in_scale=(1e-3, 1e-2, 1e-2, 1e-3), out_scale=(1e-5, 1e-4, 1e-4)):
+        self.shape = (int(n_theta), int(n_phi))
+        self.h = _H()
+        rc = load().vlbm_lc_create(self.shape[0], self.shape[1], int(seed), ctypes.byref(self.h))
+        if rc:
+            raise VlbmError(rc, "vlbm_lc_create failed")
+        self.set_scales(in_scale, out_scale)
+
+    def _chk(self, rc):
+        if rc != VLBM_OK:
+            m = load().vlbm_lc_last_error(self.h)
+            raise VlbmError(rc, m.decode() if m else "")
+
+    def set_scales(self, in_scale, out_scale):
+        self.in_scale = np.asarray(in_scale, dtype=np.float64)
+        self.out_scale = np.asarray(out_scale, dtype=np.float64)
+        self._chk(load().vlbm_lc_set_scales(self.h, _p(self.in_scale), _p(self.out_scale)))
+
+    def num_params(self):
+        return int(load().vlbm_lc_num_params(self.h))
+
+    def get_weights(self):
+        w = np.empty(self.num_params(), dtype=np.float32)
+        self._chk(load().vlbm_lc_get_weights(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._chk(load().vlbm_lc_set_weights(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def predict(self, x):
+        x = _host(x, (4,) + self.shape)
+        out = np.empty((3,) + self.shape)
+        self._chk(load().vlbm_lc_predict(self.h, _p(x), _p(out)))
+        return out
+
+    def gradients(self, x, t):
+        x, t = _host(x, (4,) + self.shape), _host(t, (3,) + self.shape)
+        loss = ctypes.c_double()
+        g = np.empty(self.num_params(), dtype=np.float32)
+        self._chk(load().vlbm_lc_gradients(self.h, _p(x), _p(t), ctypes.byref(loss),
+                                           g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return loss.value, g
+
+    def train_step(self, x, t, lr):
+        x, t = _host(x, (4,) + self.shape), _host(t, (3,) + self.shape)
+        loss = ctypes.c_double()
+        self._chk(load().vlbm_lc_train_step(self.h, _p(x), _p(t), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def apply(self, solver):
+        self._chk(load().vlbm_lc_apply(self.h, solver.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().vlbm_lc_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -74,7 +74,9 @@ def test_autotuner_restores_state_and_caches(V, tmp_path):
         assert np.array_equal(b.moments(r)[0], ref[r][0])
     # a second tune of the same grid mix comes from the cache
     b2, _ = _batch(V)
-    assert b2.tune(cache) == choice
+    again = b2.tune(cache)
+    assert (again["tile_rows"], again["ctas_per_sm"]) == (choice["tile_rows"], choice["ctas_per_sm"])
+    assert again["ms_per_step"] == pytest.approx(choice["ms_per_step"], rel=1e-4)
     b.close()
     b2.close()
 

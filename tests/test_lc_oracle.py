@@ -1,0 +1,58 @@
+"""Pins of the CPU reference of the learned-correction network (FP64):
+the padding's adjoint, the pole reflection, and backpropagation against
+central finite differences."""
+import numpy as np
+import pytest
+
+from oracle import lc_oracle as L
+from paper_2504_15574_gb300 import inputs
+
+
+def test_unpad_is_the_adjoint_of_pad():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(5, 6, 8))
+    y = rng.normal(size=(5, 8, 10))
+    for neg in ([], [1, 2]):
+        assert np.isclose((L.pad(x, neg) * y).sum(), (x * L.unpad(y, neg)).sum(), rtol=1e-13)
+
+
+def test_pole_ghost_row_is_the_opposite_meridian_with_vectors_negated():
+    x = np.arange(3 * 4 * 8, dtype=float).reshape(3, 4, 8)
+    xp = L.pad(x, [1])
+    # ghost of column q (padded q+1) is row 0 at column q + W/2
+    for q in range(8):
+        assert xp[0, 0, q + 1] == x[0, 0, (q + 4) % 8]
+        assert xp[1, 0, q + 1] == -x[1, 0, (q + 4) % 8]
+        assert xp[2, -1, q + 1] == x[2, -1, (q + 4) % 8]
+    assert np.array_equal(xp[:, 1:-1, 0], x[:, :, -1]) and np.array_equal(xp[:, 1:-1, -1], x[:, :, 0])
+
+
+def _sample(H, W, seed):
+    rho, ut, up, _ = inputs.gaussian_vortices(H, W, run=seed, umax=0.05)
+    T = 1.0 + 0.01 * np.cos(np.arange(H))[:, None] * np.ones((1, W))
+    x = np.stack([rho + 1e-3 * np.sin(np.arange(W))[None, :], ut, up, T])
+    t = 1e-4 * inputs.SplitMix64(seed).normal_array((3, H, W))
+    return x, t
+
+
+def test_backprop_matches_finite_differences():
+    H, W = 6, 8
+    x, t = _sample(H, W, 3)
+    p = L.init_params(7)
+    p[-3:] = [0.01, -0.02, 0.03]
+    ins, outs = [1e-3, 2e-2, 2e-2, 1e-2], [1e-4, 1e-4, 1e-4]
+    loss, g = L.loss_and_grad(p, x, t, ins, outs)
+    rng = np.random.default_rng(1)
+    idx = rng.choice(p.size, 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        lp, _ = L.loss_and_grad(p + e, x, t, ins, outs)
+        lm, _ = L.loss_and_grad(p - e, x, t, ins, outs)
+        fd = (lp - lm) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9 * max(1.0, abs(loss)))
+
+
+def test_parameter_count():
+    assert L.num_params() == 32 * 4 * 9 + 32 + 2 * (32 * 32 * 9 + 32) + 3 * 32 * 9 + 3
