@@ -240,6 +240,32 @@ VLBM_API int vlbm_lc_apply(vlbm_lc_t *lc, vlbm_t *h);
 VLBM_API const char *vlbm_lc_last_error(const vlbm_lc_t *lc);
 VLBM_API void vlbm_lc_destroy(vlbm_lc_t *lc);
 
+/* ---- Diagnostics without device allocation --------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that cannot
+ * call cudaMalloc where they need the numbers: code running while a stream is
+ * captured into a CUDA graph, latency-bound loops that cannot afford an
+ * allocation's device synchronisation, and hosts whose device memory comes from
+ * their own pool.  It reduces a population array the caller owns and writes to a
+ * device buffer the caller owns; the library allocates nothing.
+ *
+ *   f_dev:   device pointer, FP64 populations, dense layout [16][n_theta][n_phi]
+ *            (the layout of vlbm_get_populations), read only;
+ *   out_dev: device pointer to 6 doubles: mass, Cartesian momentum x, y, z, energy
+ *            sum_k f_k |v_k|^2 / 2 (area element R^2 sin(theta) dtheta dphi, as in
+ *            vlbm_diagnostics) and the count of rows holding a NaN/Inf population;
+ *   stream:  cudaStream_t to run on (NULL: the legacy default stream).  The call
+ *            only enqueues; the caller synchronises before reading out_dev.
+ * Scratch: a fixed array inside the library sized for n_theta <= VLBM_NOALLOC_MAX_ROWS
+ * (768 KiB per GPU that loads the library, held until exit); larger grids return
+ * VLBM_ERR_ARG.  The first call on each device looks up that array's address and
+ * should come before any stream capture.  All calls share the one array, so calls
+ * whose kernels overlap on the GPU race with each other.  Errors:
+ * VLBM_ERR_ARG / VLBM_ERR_CUDA, message in vlbm_noalloc_last_error(). */
+#define VLBM_NOALLOC_MAX_ROWS 16384
+VLBM_API int vlbm_diagnostics_noalloc(const double *f_dev, int n_theta, int n_phi, double radius, double *out_dev,
+                                      void *stream);
+VLBM_API const char *vlbm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,7 @@ UNITS = {
     "aux.cu": [],
     "lc.cu": [],
     "lc_api.cu": [],
+    "noalloc.cu": [],
 }
 
 

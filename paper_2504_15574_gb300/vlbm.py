@@ -92,6 +92,9 @@ SIGNATURES = {
     "vlbm_lc_apply": (ctypes.c_int, [_H, _H]),
     "vlbm_lc_last_error": (ctypes.c_char_p, [_H]),
     "vlbm_lc_destroy": (None, [_H]),
+    "vlbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
+    "vlbm_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 
@@ -442,3 +445,14 @@ class LearnedCorrection:
             self.close()
         except Exception:
             pass
+
+
+def vlbm_diagnostics_noalloc(f_dev_ptr, n_theta, n_phi, radius, out_dev_ptr, stream=None):
+    """Diagnostics of a caller-owned device array with no allocation in the library
+    (for callers that cannot call cudaMalloc, e.g. inside a graph capture).  Takes raw
+    device addresses; enqueues on `stream` and returns without waiting."""
+    rc = load().vlbm_diagnostics_noalloc(ctypes.c_void_p(f_dev_ptr), int(n_theta), int(n_phi), float(radius),
+                                         ctypes.c_void_p(out_dev_ptr), stream)
+    if rc != VLBM_OK:
+        m = load().vlbm_noalloc_last_error()
+        raise VlbmError(rc, m.decode() if m else "")
