@@ -223,7 +223,8 @@ VLBM_API int vlbm_lc_num_params(const vlbm_lc_t *lc);
 VLBM_API int vlbm_lc_get_weights(vlbm_lc_t *lc, float *w);
 /* Sets the weights and resets the Adam state. */
 VLBM_API int vlbm_lc_set_weights(vlbm_lc_t *lc, const float *w);
-/* in_scale[4] divides (rho-1, u^theta, u^phi, T-1); out_scale[3] multiplies the outputs. */
+/* in_scale[4] divides (rho-1, u^theta, u^phi, T-1) (each scaled input is then clamped to
+ * [-8, 8]); out_scale[3] multiplies the outputs. */
 VLBM_API int vlbm_lc_set_scales(vlbm_lc_t *lc, const double *in_scale, const double *out_scale);
 /* Forward pass: outputs in physical units (drho not mean-corrected). */
 VLBM_API int vlbm_lc_predict(vlbm_lc_t *lc, const double *inputs, double *outputs);

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Same definitions as the
 CUDA network, written out with numpy: inputs (rho-1, u^theta, u^phi, T-1)
-divided by in_scale; 3x3 convolutions 4 -> 32 -> 32 -> 32 -> 3 with ReLU between;
+divided by in_scale and clamped to [-8, 8]; 3x3 convolutions 4 -> 32 -> 32 -> 32 -> 3 with ReLU between;
 padding periodic in phi and, beyond a pole, the row on the opposite meridian
 (column + W/2) with the input's velocity channels negated (the pole boundary
 condition of arXiv 2504.15574 Sec. 3.6 applied to moments); loss = the
@@ -79,9 +79,14 @@ def conv_valid(xp, w, b):
     return y
 
 
+CLAMP = 8.0
+
+
 def features(inputs, in_scale):
+    """Scaled inputs, each clamped to [-CLAMP, CLAMP]."""
     rho, ut, up, T = inputs
-    return np.stack([(rho - 1.0) / in_scale[0], ut / in_scale[1], up / in_scale[2], (T - 1.0) / in_scale[3]])
+    x = np.stack([(rho - 1.0) / in_scale[0], ut / in_scale[1], up / in_scale[2], (T - 1.0) / in_scale[3]])
+    return np.clip(x, -CLAMP, CLAMP)
 
 
 def area_weights(H, W):

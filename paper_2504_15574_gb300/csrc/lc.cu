@@ -392,7 +392,8 @@ __global__ void wgrad_layout_kernel(const float *g9, int CO, int CI, int COp, in
     g[i] = g9[((size_t)tap * COp + co) * CIp + ci];
 }
 
-// network input from the moments of a coarse solver: [(rho-1)/s0, ut/s1, up/s2, (T-1)/s3, 0 ...]
+// network input from the moments of a coarse solver: [(rho-1)/s0, ut/s1, up/s2, (T-1)/s3, 0 ...],
+// each clamped to [-LC_CLAMP, LC_CLAMP] so that states outside the training range stay bounded
 __global__ void features_kernel(const double *rho, const double *ut, const double *up, const double *T, int n,
                                 float4 inv_scale, __nv_bfloat16 *X0)
 {
@@ -404,7 +405,7 @@ __global__ void features_kernel(const double *rho, const double *ut, const doubl
     v[2] = (float)(up[i] * inv_scale.z);
     v[3] = (float)((T ? T[i] - 1.0 : 0.0) * inv_scale.w);
 #pragma unroll
-    for (int c = 0; c < LC_CIN; ++c) X0[(size_t)i * LC_CIN + c] = __float2bfloat16(v[c]);
+    for (int c = 0; c < LC_CIN; ++c) X0[(size_t)i * LC_CIN + c] = __float2bfloat16(fminf(fmaxf(v[c], -LC_CLAMP), LC_CLAMP));
 }
 
 // output [H][W][CO] -> (drho, dut, dup) [3][H][W] in physical units, and sin-weighted drho partial sums

@@ -14,6 +14,7 @@ constexpr int LC_HID = 32;      // hidden channels
 constexpr int LC_OUT = 3;       // drho, du^theta, du^phi
 constexpr int LC_COUT = 8;      // output channels padded to an n = 8 tile
 constexpr int LC_COUTP2 = 16;   // output-gradient channels padded for the k = 16 step (backward data)
+constexpr float LC_CLAMP = 8.0f;   // bound of every scaled input feature
 
 void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
              float *Yf, __nv_bfloat16 *Yb, int relu, cudaStream_t s);

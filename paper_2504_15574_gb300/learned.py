@@ -105,39 +105,50 @@ class Setup:
         return b
 
 
-def make_samples(setup: Setup, seeds, n_steps, spinup=0):
-    """(inputs [N,4,H,W], targets [N,3,H,W]) from fine runs of the given seeds."""
+def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=8):
+    """(inputs [N,4,H,W], targets [N,3,H,W]) from coarse rollouts beside fine runs.
+
+    One coarse solver per seed starts from the downsampled fine state and is
+    re-started from it every `reinit_every` coarse steps; after each coarse step
+    the sample is (coarse moments, downsampled fine moments minus them).  With a
+    network, its correction is applied after each sample (so later rounds see the
+    states the corrected rollout visits)."""
     fb = setup.fine_batch(seeds)
     if spinup:
         fb.step(spinup * setup.factor)
-    cs = setup.coarse_solver()
+    cs = [setup.coarse_solver() for _ in seeds]
     X, Y = [], []
-    for _ in range(n_steps):
-        prev = [downsample(*fb.moments(r, with_T=True)) for r in range(len(seeds))]
+    for k in range(n_steps):
+        if k % reinit_every == 0:
+            for r in range(len(seeds)):
+                cs[r].init_moments(*downsample(*fb.moments(r, with_T=True)))
         fb.step(setup.factor)
         for r in range(len(seeds)):
-            cs.init_moments(*prev[r])
-            cs.step(1)
-            c = cs.moments(with_T=True)
+            cs[r].step(1)
+            c = cs[r].moments(with_T=True)
             d = downsample(*fb.moments(r, with_T=True))
             X.append(np.stack(c))
             Y.append(np.stack([d[0] - c[0], d[1] - c[1], d[2] - c[2]]))
-    cs.close()
+            if net is not None:
+                net.apply(cs[r])
+    for c in cs:
+        c.close()
     fb.close()
     return np.array(X), np.array(Y)
 
 
 def scales(X, Y):
-    """Per-channel input and output scales from the sample spread."""
+    """Per-channel input and output scales from the sample spread (T floored at 1e-3)."""
     ins = [max(np.abs(X[:, 0] - 1).max(), 1e-12), max(np.abs(X[:, 1]).max(), 1e-12),
-           max(np.abs(X[:, 2]).max(), 1e-12), max(np.abs(X[:, 3] - 1).max(), 1e-12)]
+           max(np.abs(X[:, 2]).max(), 1e-12), max(np.abs(X[:, 3] - 1).max(), 1e-3)]
     outs = [max(Y[:, c].std(), 1e-16) for c in range(3)]
     return ins, outs
 
 
-def train(setup: Setup, X, Y, epochs=4, lr=2e-3, seed=1, log=None):
-    ins, outs = scales(X, Y)
-    net = vlbm.LearnedCorrection(*setup.coarse, seed=seed, in_scale=ins, out_scale=outs)
+def train(setup: Setup, X, Y, epochs=4, lr=2e-3, seed=1, log=None, net=None):
+    if net is None:
+        ins, outs = scales(X, Y)
+        net = vlbm.LearnedCorrection(*setup.coarse, seed=seed, in_scale=ins, out_scale=outs)
     rng = np.random.default_rng(seed)
     hist = []
     for ep in range(epochs):
@@ -201,19 +212,29 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=40, help="coarse steps of training data per seed")
     ap.add_argument("--spinup", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--rounds", type=int, default=2, help="data rounds; later rounds roll out with the network")
     ap.add_argument("--eval-seeds", type=int, default=3)
     ap.add_argument("--eval-steps", type=int, default=60)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     setup = Setup(coarse=a.coarse)
-    t0 = time.perf_counter()
-    X, Y = make_samples(setup, list(range(1000, 1000 + a.train_seeds)), a.steps, spinup=a.spinup)
-    t_data = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    net, hist = train(setup, X, Y, epochs=a.epochs, log=print)
-    t_train = time.perf_counter() - t0
+    seeds = list(range(1000, 1000 + a.train_seeds))
+    t_data = t_train = 0.0
+    net, hist, Xs, Ys = None, [], [], []
+    for rnd in range(a.rounds):
+        t0 = time.perf_counter()
+        X, Y = make_samples(setup, seeds, a.steps, spinup=a.spinup, net=net)
+        Xs.append(X)
+        Ys.append(Y)
+        t_data += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        net, h = train(setup, np.concatenate(Xs), np.concatenate(Ys), epochs=a.epochs, log=print, net=net,
+                       lr=2e-3 * 0.5**rnd)
+        hist += h
+        t_train += time.perf_counter() - t0
     res = evaluate(setup, net, list(range(5000, 5000 + a.eval_seeds)), a.eval_steps)
-    res.update({"samples": int(len(X)), "loss_history": hist, "seconds_data": t_data, "seconds_train": t_train})
+    res.update({"samples": int(sum(len(x) for x in Xs)), "loss_history": hist, "seconds_data": t_data,
+                "seconds_train": t_train, "rounds": a.rounds})
     line = json.dumps(res)
     print(line)
     if a.out:
