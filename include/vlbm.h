@@ -185,6 +185,8 @@ VLBM_API int vlbm_batch_step_async(vlbm_batch_t *b, int n);
 VLBM_API int vlbm_batch_sync(vlbm_batch_t *b);
 /* Moments of run `run` (as vlbm_moments). */
 VLBM_API int vlbm_batch_moments(vlbm_batch_t *b, int run, double *rho, double *u_theta, double *u_phi, double *T);
+/* Populations of run `run` as FP64 host array [16][n_theta][n_phi] (as vlbm_get_populations). */
+VLBM_API int vlbm_batch_get_populations(vlbm_batch_t *b, int run, double *f);
 /* Launch schedule: tile rows (4 or 8; tiles are 32 columns wide) and persistent CTAs
  * per SM (0: the occupancy limit). */
 VLBM_API int vlbm_batch_set_schedule(vlbm_batch_t *b, int tile_rows, int ctas_per_sm);

@@ -995,6 +995,15 @@ int vlbm_batch_init_moments(vlbm_batch_t *b, int run, const double *rho, const d
     return VLBM_OK;
 }
 
+int vlbm_batch_get_populations(vlbm_batch_t *b, int run, double *f)
+{
+    if (!b || run < 0 || run >= (int)b->runs.size()) return bfail(b, VLBM_ERR_ARG, "bad batch or run index");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    int rc = vlbm_get_populations(b->runs[run], f);
+    if (rc) return bfail(b, rc, b->runs[run]->err);
+    return VLBM_OK;
+}
+
 int vlbm_batch_set_schedule(vlbm_batch_t *b, int tile_rows, int ctas_per_sm)
 {
     if (!b || (tile_rows != 4 && tile_rows != 8) || ctas_per_sm < 0) return bfail(b, VLBM_ERR_ARG, "bad schedule");

@@ -8,9 +8,9 @@ moments toward the block-averaged state of a fine run.  Pieces:
   Cartesian 3-vector (projected back on the coarse cell's vielbein frame, so the
   rotating frame near the poles is not averaged component-wise) and of T;
 - ``make_samples``: fine runs (a ``Batch`` of FP32 solvers, Gaussian-vortex
-  starts) advanced ``factor`` fine steps per coarse step; at each coarse step the
-  coarse solver starts from the downsampled fine state, takes one step, and the
-  sample is (coarse moments after the step, downsampled fine moments minus them);
+  starts) advanced ``factor`` fine steps per coarse step; coarse rollouts beside
+  them start from the block-averaged fine populations; after each coarse step the
+  sample is (coarse moments, downsampled fine moments minus them);
 - ``train``: Adam on those samples;
 - ``evaluate``: rollouts of plain coarse, coarse + correction and the fine run
   on held-out seeds; area-weighted relative L2 error of the vorticity (and of
@@ -56,6 +56,17 @@ def downsample(rho, ut, up, T, factor=4):
     _, ce_th, ce_ph = _frames(H, W)
     uc = mc / rc[None]
     return rc, (uc * ce_th).sum(0), (uc * ce_ph).sum(0), Tc
+
+
+def downsample_populations(f, factor=4):
+    """sin(theta)-area-weighted block means of every population [16][Hf][Wf] -> [16][H][W].
+    Keeps the non-equilibrium part of the fine state (a coarse start from moments alone
+    would begin with an equilibrium transient)."""
+    _, Hf, Wf = f.shape
+    H, W = Hf // factor, Wf // factor
+    s = np.sin((np.arange(Hf) + 0.5) * math.pi / Hf)[:, None] * np.ones((1, Wf))
+    ws = s.reshape(H, factor, W, factor).sum(axis=(1, 3))
+    return (f * s[None]).reshape(16, H, factor, W, factor).sum(axis=(2, 4)) / ws[None]
 
 
 def vorticity(ut, up):
@@ -105,11 +116,11 @@ class Setup:
         return b
 
 
-def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=8):
+def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=16):
     """(inputs [N,4,H,W], targets [N,3,H,W]) from coarse rollouts beside fine runs.
 
-    One coarse solver per seed starts from the downsampled fine state and is
-    re-started from it every `reinit_every` coarse steps; after each coarse step
+    One coarse solver per seed starts from the block-averaged fine populations and
+    is re-started from them every `reinit_every` coarse steps; after each coarse step
     the sample is (coarse moments, downsampled fine moments minus them).  With a
     network, its correction is applied after each sample (so later rounds see the
     states the corrected rollout visits)."""
@@ -121,7 +132,7 @@ def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=
     for k in range(n_steps):
         if k % reinit_every == 0:
             for r in range(len(seeds)):
-                cs[r].init_moments(*downsample(*fb.moments(r, with_T=True)))
+                cs[r].set_populations(downsample_populations(fb.get_populations(r), setup.factor))
         fb.step(setup.factor)
         for r in range(len(seeds)):
             cs[r].step(1)
@@ -163,10 +174,11 @@ def train(setup: Setup, X, Y, epochs=4, lr=2e-3, seed=1, log=None, net=None):
     return net, hist
 
 
-def evaluate(setup: Setup, net, seeds, n_steps):
+def evaluate(setup: Setup, net, seeds, n_steps, spinup=20):
     """Rollouts from the downsampled fine start: errors after n_steps coarse steps and wall times."""
     fb = setup.fine_batch(seeds)
-    starts = [downsample(*fb.moments(r, with_T=True)) for r in range(len(seeds))]
+    fb.step(spinup * setup.factor)
+    starts = [downsample_populations(fb.get_populations(r), setup.factor) for r in range(len(seeds))]
     t0 = time.perf_counter()
     fb.step(n_steps * setup.factor)
     t_fine = (time.perf_counter() - t0) / (n_steps * len(seeds))
@@ -178,7 +190,7 @@ def evaluate(setup: Setup, net, seeds, n_steps):
         cs = setup.coarse_solver()
         el = 0.0
         for r in range(len(seeds)):
-            cs.init_moments(*starts[r])
+            cs.set_populations(starts[r])
             t0 = time.perf_counter()
             for _ in range(n_steps):
                 cs.step(1)
@@ -208,8 +220,8 @@ def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--coarse", type=int, nargs=2, default=[128, 256])
-    ap.add_argument("--train-seeds", type=int, default=6)
-    ap.add_argument("--steps", type=int, default=40, help="coarse steps of training data per seed")
+    ap.add_argument("--train-seeds", type=int, default=12)
+    ap.add_argument("--steps", type=int, default=48, help="coarse steps of training data per seed")
     ap.add_argument("--spinup", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--rounds", type=int, default=2, help="data rounds; later rounds roll out with the network")

@@ -75,6 +75,7 @@ SIGNATURES = {
     "vlbm_batch_sync": (ctypes.c_int, [_H]),
     "vlbm_batch_moments": (ctypes.c_int, [_H, ctypes.c_int, _PD, _PD, _PD, _PD]),
     "vlbm_batch_set_schedule": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    "vlbm_batch_get_populations": (ctypes.c_int, [_H, ctypes.c_int, _PD]),
     "vlbm_batch_tune": (ctypes.c_int, [_H, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        _PD]),
     "vlbm_batch_profile": (ctypes.c_int, [_H, ctypes.c_int, _PD, ctypes.POINTER(ctypes.c_int)]),
@@ -347,6 +348,11 @@ class Batch:
         T = np.empty(s) if with_T else None
         _bcheck(load().vlbm_batch_moments(self.b, int(run), _p(rho), _p(ut), _p(up), _p(T)), self.b)
         return (rho, ut, up, T) if with_T else (rho, ut, up)
+
+    def get_populations(self, run):
+        f = np.empty((NK,) + self.grids[run])
+        _bcheck(load().vlbm_batch_get_populations(self.b, int(run), _p(f)), self.b)
+        return f
 
     def set_schedule(self, tile_rows, ctas_per_sm=0):
         _bcheck(load().vlbm_batch_set_schedule(self.b, int(tile_rows), int(ctas_per_sm)), self.b)

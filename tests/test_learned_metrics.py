@@ -45,3 +45,14 @@ def test_downsample_preserves_uniform_and_rotating_states():
     wf = np.sin(th)[:, None] * one
     wc = wf.reshape(Hf // 4, 4, Wf // 4, 4).sum(axis=(1, 3))
     assert (rc * wc).sum() == pytest.approx((rho * wf).sum(), rel=1e-13)
+
+
+def test_population_downsampling_keeps_mass_and_density():
+    from paper_2504_15574_gb300.learned import downsample_populations
+    rng = np.random.default_rng(3)
+    Hf, Wf = 16, 32
+    f = 0.05 + 0.01 * rng.random((16, Hf, Wf))
+    fc = downsample_populations(f)
+    rho_f, rho_c = f.sum(0), fc.sum(0)
+    rc, _, _, _ = downsample(rho_f, 0 * rho_f, 0 * rho_f, 1 + 0 * rho_f)
+    assert np.allclose(rho_c, rc, rtol=1e-14)
