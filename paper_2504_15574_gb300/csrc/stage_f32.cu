@@ -566,44 +566,93 @@ __global__ void fill_ghosts_f32_kernel(f2 *f, const Layout L)
     f[L.at(q, r, c)] = pole ? make_float2(-v.y, -v.x) : v;
 }
 
-// Polar ring filter, one CTA per (filtered row, pair plane): the mean over each
-// aligned block of b columns, summed in FP64 (slices of 32 columns, then the
-// slices in order), written to the block's cells and their ghost images.
-__global__ void filter_f32_kernel(f2 *f, const Layout L, const int *rows, const int *blocks)
+// Polar ring filter, one CTA per (filtered row, pair plane).  The row is walked in
+// windows of 2048 columns; each of the 256 threads owns 8 consecutive columns.
+// Block sums are FP64: per-thread sums of 8 columns, then a pairwise tree over
+// the threads of each aligned block (deterministic order); every thread then
+// writes the mean to its 8 columns and their ghost images.  Blocks wider than a
+// window (b > 2048, only for n_phi above ~25000) take the slice path below.
+constexpr int FILT_THREADS = 256;
+constexpr int FILT_COLS = 8;
+constexpr int FILT_WIN = FILT_THREADS * FILT_COLS;
+
+__global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const Layout L, const int *rows,
+                                                                   const int *blocks)
 {
     const int i = rows[blockIdx.x];
     const int b = blocks[blockIdx.x];
     const int q = blockIdx.y;
-    const int nblk = L.np / b;
-    const int slices = (b + 31) / 32;
-    __shared__ double2 part[256];
-    for (int base = 0; base < nblk * slices; base += blockDim.x) {
-        const int t = base + threadIdx.x;
-        const bool live = t < nblk * slices;
-        double2 s = make_double2(0.0, 0.0);
-        if (live) {
-            const int blk = t / slices, sl = t - blk * slices;
-            const int j0 = blk * b + sl * 32, j1 = min(j0 + 32, blk * b + b);
-            for (int jj = j0; jj < j1; ++jj) {
-                const f2 v = f[L.at(q, i, jj)];
-                s.x += v.x;
-                s.y += v.y;
+    const int t = threadIdx.x;
+    __shared__ double2 part[FILT_THREADS];
+    if (b <= FILT_WIN) {
+        for (int w0 = 0; w0 < L.np; w0 += FILT_WIN) {
+            const int c0 = w0 + t * FILT_COLS, c1 = min(c0 + FILT_COLS, L.np);
+            f2 v[FILT_COLS];
+#pragma unroll
+            for (int m = 0; m < FILT_COLS; ++m) v[m] = (c0 + m < c1) ? f[L.at(q, i, c0 + m)] : make_float2(0.f, 0.f);
+            if (b < FILT_COLS) {
+                // blocks lie inside this thread's columns
+                for (int j0 = 0; j0 < c1 - c0; j0 += b) {
+                    double sx = 0.0, sy = 0.0;
+                    for (int m = 0; m < b; ++m) {
+                        sx += v[j0 + m].x;
+                        sy += v[j0 + m].y;
+                    }
+                    const f2 mean = make_float2((float)(sx / b), (float)(sy / b));
+                    for (int m = 0; m < b; ++m) store_images(f, L, q, i, c0 + j0 + m, mean);
+                }
+                continue;
             }
-        }
-        part[threadIdx.x] = s;
-        __syncthreads();
-        // slices of one block are consecutive threads (blockDim is a multiple of slices)
-        if (live && (t % slices) == 0) {
-            double2 tot = make_double2(0.0, 0.0);
-            for (int m = 0; m < slices; ++m) {
-                tot.x += part[threadIdx.x + m].x;
-                tot.y += part[threadIdx.x + m].y;
+            double sx = 0.0, sy = 0.0;
+#pragma unroll
+            for (int m = 0; m < FILT_COLS; ++m) {
+                sx += v[m].x;
+                sy += v[m].y;
             }
-            const int blk = t / slices;
+            part[t] = make_double2(sx, sy);
+            __syncthreads();
+            const int per = b / FILT_COLS;   // threads per block (a power of two)
+            for (int st = 1; st < per; st *= 2) {
+                if ((t % (2 * st)) == 0) {
+                    part[t].x += part[t + st].x;
+                    part[t].y += part[t + st].y;
+                }
+                __syncthreads();
+            }
+            const double2 tot = part[(t / per) * per];
             const f2 mean = make_float2((float)(tot.x / b), (float)(tot.y / b));
-            for (int jj = blk * b; jj < blk * b + b; ++jj) store_images(f, L, q, i, jj, mean);
+            for (int c = c0; c < c1; ++c) store_images(f, L, q, i, c, mean);
+            __syncthreads();   // part[] is reused by the next window
         }
+        return;
+    }
+    // very wide blocks: slices of 32 columns summed per thread, slices in order per block
+    const int nblk = L.np / b;
+    const int slices = b / 32;
+    for (int blk = 0; blk < nblk; ++blk) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int sl = t; sl < slices; sl += FILT_THREADS) {
+            double sx = 0.0, sy = 0.0;
+            for (int m = 0; m < 32; ++m) {
+                const f2 x = f[L.at(q, i, blk * b + sl * 32 + m)];
+                sx += x.x;
+                sy += x.y;
+            }
+            acc.x += sx;
+            acc.y += sy;
+        }
+        part[t] = acc;
         __syncthreads();
+        for (int st = FILT_THREADS / 2; st > 0; st >>= 1) {
+            if (t < st) {
+                part[t].x += part[t + st].x;
+                part[t].y += part[t + st].y;
+            }
+            __syncthreads();
+        }
+        const f2 mean = make_float2((float)(part[0].x / b), (float)(part[0].y / b));
+        __syncthreads();
+        for (int c = t; c < b; c += FILT_THREADS) store_images(f, L, q, i, blk * b + c, mean);
     }
 }
 
@@ -736,7 +785,7 @@ void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *b
 {
     if (nrows <= 0) return;
     dim3 grid(nrows, NP2);
-    filter_f32_kernel<<<grid, 256, 0, s>>>(f, L, rows, blocks);
+    filter_f32_kernel<<<grid, FILT_THREADS, 0, s>>>(f, L, rows, blocks);
 }
 
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,

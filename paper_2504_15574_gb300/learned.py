@@ -116,14 +116,16 @@ class Setup:
         return b
 
 
-def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=16):
+def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=1):
     """(inputs [N,4,H,W], targets [N,3,H,W]) from coarse rollouts beside fine runs.
 
     One coarse solver per seed starts from the block-averaged fine populations and
-    is re-started from them every `reinit_every` coarse steps; after each coarse step
-    the sample is (coarse moments, downsampled fine moments minus them).  With a
-    network, its correction is applied after each sample (so later rounds see the
-    states the corrected rollout visits)."""
+    is re-started from them every `reinit_every` coarse steps (default: every step,
+    so each target is the one-step gap of a coarse step taken from the fine state,
+    the correction a per-step nudge has to supply); after each coarse step the
+    sample is (coarse moments, downsampled fine moments minus them).  With a
+    network and reinit_every > 1, its correction is applied after each sample (so
+    later rounds see the states the corrected rollout visits)."""
     fb = setup.fine_batch(seeds)
     if spinup:
         fb.step(spinup * setup.factor)
@@ -220,11 +222,12 @@ def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--coarse", type=int, nargs=2, default=[128, 256])
-    ap.add_argument("--train-seeds", type=int, default=12)
+    ap.add_argument("--train-seeds", type=int, default=16)
     ap.add_argument("--steps", type=int, default=48, help="coarse steps of training data per seed")
     ap.add_argument("--spinup", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=4)
-    ap.add_argument("--rounds", type=int, default=2, help="data rounds; later rounds roll out with the network")
+    ap.add_argument("--rounds", type=int, default=1, help="data rounds; later rounds roll out with the network")
+    ap.add_argument("--reinit-every", type=int, default=1, help="coarse steps between restarts from the fine state")
     ap.add_argument("--eval-seeds", type=int, default=3)
     ap.add_argument("--eval-steps", type=int, default=60)
     ap.add_argument("--out", default=None)
@@ -235,7 +238,7 @@ def main(argv=None):
     net, hist, Xs, Ys = None, [], [], []
     for rnd in range(a.rounds):
         t0 = time.perf_counter()
-        X, Y = make_samples(setup, seeds, a.steps, spinup=a.spinup, net=net)
+        X, Y = make_samples(setup, seeds, a.steps, spinup=a.spinup, net=net, reinit_every=a.reinit_every)
         Xs.append(X)
         Ys.append(Y)
         t_data += time.perf_counter() - t0
