@@ -204,12 +204,13 @@ VLBM_API const char *vlbm_batch_last_error(const vlbm_batch_t *b);
 VLBM_API void vlbm_batch_destroy(vlbm_batch_t *b);
 
 /* ---- Learned correction (not in the paper) -------------------------------------
- * A 4-layer 3x3 convolutional network (4 -> 32 -> 32 -> 32 -> 3 channels, ReLU
+ * A 4-layer 3x3 convolutional network (6 -> 32 -> 32 -> 32 -> 3 channels, ReLU
  * between) on a coarse grid, mapping the moments (rho, u^theta, u^phi, T) of a
- * coarse FP32 solver after a step to a correction (drho, du^theta, du^phi)
- * toward a finer run.  Padding follows the sphere: periodic in phi; beyond a
- * pole, the row on the opposite meridian with the input's velocity channels
- * negated (Sec. 3.6, Eq. bcs_theta, applied to moments).  BF16 activations and
+ * coarse FP32 solver after a step, plus cos(theta) and sin(theta) of each row,
+ * to a correction (drho, du^theta, du^phi) toward a finer run.  Padding follows
+ * the sphere: periodic in phi; beyond a pole, the row on the opposite meridian
+ * with the velocity channels and sin(theta) negated (Sec. 3.6, Eq. bcs_theta,
+ * applied to moments).  BF16 activations and
  * weights, FP32 accumulation on the tensor cores, FP32 master weights and Adam.
  * Host arrays: inputs [4][n_theta][n_phi] (rho, u^theta, u^phi, T), targets and
  * outputs [3][n_theta][n_phi] (drho, du^theta, du^phi), physical units; the
@@ -220,7 +221,8 @@ typedef struct vlbm_lc vlbm_lc_t;
 /* Creates a network for an n_theta x n_phi grid (n_phi even) with weights drawn
  * from splitmix64(seed). */
 VLBM_API int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **out);
-/* Number of FP32 parameters; layout per layer l = 0..3: W[co][ci][3][3] then b[co]. */
+/* Number of FP32 parameters; layout per layer l = 0..3: W[co][ci][3][3] then b[co]
+ * (input channels of layer 0: rho-1, u^theta, u^phi, T-1, cos theta, sin theta). */
 VLBM_API int vlbm_lc_num_params(const vlbm_lc_t *lc);
 VLBM_API int vlbm_lc_get_weights(vlbm_lc_t *lc, float *w);
 /* Sets the weights and resets the Adam state. */

@@ -2,9 +2,10 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Same definitions as the
 CUDA network, written out with numpy: inputs (rho-1, u^theta, u^phi, T-1)
-divided by in_scale and clamped to [-8, 8]; 3x3 convolutions 4 -> 32 -> 32 -> 32 -> 3 with ReLU between;
-padding periodic in phi and, beyond a pole, the row on the opposite meridian
-(column + W/2) with the input's velocity channels negated (the pole boundary
+divided by in_scale and clamped to [-8, 8], plus cos(theta) and sin(theta) of the row;
+3x3 convolutions 6 -> 32 -> 32 -> 32 -> 3 with ReLU between; padding periodic in phi
+and, beyond a pole, the row on the opposite meridian (column + W/2) with the
+input's velocity channels and sin(theta) negated (the pole boundary
 condition of arXiv 2504.15574 Sec. 3.6 applied to moments); loss = the
 sin(theta)-area-weighted mean over cells and the 3 channels of
 (y - target / out_scale)^2.  Parameters are one flat FP32/FP64 vector, per layer
@@ -16,7 +17,8 @@ import math
 
 import numpy as np
 
-LAYERS = [(4, 32), (32, 32), (32, 32), (32, 3)]
+LAYERS = [(6, 32), (32, 32), (32, 32), (32, 3)]
+NEG = [1, 2, 5]   # input channels odd across a pole: u^theta, u^phi, sin(theta)
 
 
 def unflatten(p):
@@ -83,10 +85,13 @@ CLAMP = 8.0
 
 
 def features(inputs, in_scale):
-    """Scaled inputs, each clamped to [-CLAMP, CLAMP]."""
+    """Scaled moments clamped to [-CLAMP, CLAMP], then cos(theta) and sin(theta) of the cell row."""
     rho, ut, up, T = inputs
     x = np.stack([(rho - 1.0) / in_scale[0], ut / in_scale[1], up / in_scale[2], (T - 1.0) / in_scale[3]])
-    return np.clip(x, -CLAMP, CLAMP)
+    H, W = rho.shape
+    th = (np.arange(H) + 0.5) * math.pi / H
+    lat = np.stack([np.cos(th)[:, None] * np.ones((1, W)), np.sin(th)[:, None] * np.ones((1, W))])
+    return np.concatenate([np.clip(x, -CLAMP, CLAMP), lat])
 
 
 def area_weights(H, W):
@@ -101,7 +106,7 @@ def forward(params, inputs, in_scale):
     x = features(inputs, in_scale)
     cache = []
     for l, (w, b) in enumerate(unflatten(params)):
-        xp = pad(x, [1, 2] if l == 0 else [])
+        xp = pad(x, NEG if l == 0 else [])
         y = conv_valid(xp, w, b)
         cache.append((xp, y))
         x = np.maximum(y, 0.0) if l < len(LAYERS) - 1 else y

@@ -6,7 +6,7 @@
 // follows the boundary conditions of the sphere (arXiv 2504.15574 Sec. 3.6):
 // periodic in phi, and beyond a pole the row on the opposite meridian
 // (column + N_phi/2) with the vector channels (u^theta, u^phi of the input
-// layer) negated.
+// layer, and its sin(theta) channel) negated.
 //
 // Arithmetic: activations and weights in BF16, products accumulated in FP32 on
 // the tensor cores (mma.sync m16n8k16, BF16 in, FP32 out); master weights, Adam
@@ -392,20 +392,26 @@ __global__ void wgrad_layout_kernel(const float *g9, int CO, int CI, int COp, in
     g[i] = g9[((size_t)tap * COp + co) * CIp + ci];
 }
 
-// network input from the moments of a coarse solver: [(rho-1)/s0, ut/s1, up/s2, (T-1)/s3, 0 ...],
-// each clamped to [-LC_CLAMP, LC_CLAMP] so that states outside the training range stay bounded
-__global__ void features_kernel(const double *rho, const double *ut, const double *up, const double *T, int n,
-                                float4 inv_scale, __nv_bfloat16 *X0)
+// network input from the moments of a coarse solver: [(rho-1)/s0, ut/s1, up/s2, (T-1)/s3, cos theta,
+// sin theta, 0 ...]; the moment channels are clamped to [-LC_CLAMP, LC_CLAMP] so that states outside the
+// training range stay bounded.  The latitude channels let the (translation-equivariant) convolutions
+// depend on theta, as the coarse scheme's error does.
+__global__ void features_kernel(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
+                                const double *sin_t, const double *cos_t, float4 inv_scale, __nv_bfloat16 *X0)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= H * W) return;
     float v[LC_CIN] = {0};
     v[0] = (float)((rho[i] - 1.0) * inv_scale.x);
     v[1] = (float)(ut[i] * inv_scale.y);
     v[2] = (float)(up[i] * inv_scale.z);
     v[3] = (float)((T ? T[i] - 1.0 : 0.0) * inv_scale.w);
 #pragma unroll
-    for (int c = 0; c < LC_CIN; ++c) X0[(size_t)i * LC_CIN + c] = __float2bfloat16(fminf(fmaxf(v[c], -LC_CLAMP), LC_CLAMP));
+    for (int c = 0; c < 4; ++c) v[c] = fminf(fmaxf(v[c], -LC_CLAMP), LC_CLAMP);
+    v[4] = (float)cos_t[i / W];
+    v[5] = (float)sin_t[i / W];
+#pragma unroll
+    for (int c = 0; c < LC_CIN; ++c) X0[(size_t)i * LC_CIN + c] = __float2bfloat16(v[c]);
 }
 
 // output [H][W][CO] -> (drho, dut, dup) [3][H][W] in physical units, and sin-weighted drho partial sums
@@ -558,10 +564,10 @@ void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g
     wgrad_layout_kernel<<<(n + 255) / 256, 256, 0, s>>>(g9, CO, CI, COp, CIp, g);
 }
 
-void lc_features(const double *rho, const double *ut, const double *up, const double *T, int n, float4 inv_scale,
-                 __nv_bfloat16 *X0, cudaStream_t s)
+void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
+                 const double *sin_t, const double *cos_t, float4 inv_scale, __nv_bfloat16 *X0, cudaStream_t s)
 {
-    features_kernel<<<(n + 255) / 256, 256, 0, s>>>(rho, ut, up, T, n, inv_scale, X0);
+    features_kernel<<<(H * W + 255) / 256, 256, 0, s>>>(rho, ut, up, T, H, W, sin_t, cos_t, inv_scale, X0);
 }
 
 void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,

@@ -26,7 +26,7 @@ struct vlbm_lc {
     int nparam = 0;
     float *d_w = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
     __nv_bfloat16 *d_wf[LC_LAYERS] = {}, *d_wb[LC_LAYERS] = {};
-    double *d_sin = nullptr, *d_in = nullptr, *d_tg = nullptr, *d_out = nullptr, *d_part = nullptr, *d_scal = nullptr;
+    double *d_sin = nullptr, *d_cos = nullptr, *d_in = nullptr, *d_tg = nullptr, *d_out = nullptr, *d_part = nullptr, *d_scal = nullptr;
     __nv_bfloat16 *d_x0 = nullptr, *d_xp[LC_LAYERS] = {}, *d_z[LC_LAYERS] = {};
     float *d_y = nullptr, *d_dy = nullptr, *d_dxp = nullptr, *d_dx = nullptr;
     __nv_bfloat16 *d_dp = nullptr, *d_dpre = nullptr;
@@ -86,9 +86,10 @@ int forward(vlbm_lc_t *n)
     const int H = n->H, W = n->W, HW = H * W;
     const float4 is = make_float4(1.0f / n->in_scale[0], 1.0f / n->in_scale[1], 1.0f / n->in_scale[2],
                                   1.0f / n->in_scale[3]);
-    lc_features(n->d_in, n->d_in + HW, n->d_in + 2 * (size_t)HW, n->d_in + 3 * (size_t)HW, HW, is, n->d_x0, n->stream);
-    // the input layer's vector channels (u^theta, u^phi) change sign across a pole
-    lc_pad(n->d_x0, H, W, LC_CIN, 0x6u, n->d_xp[0], n->stream);
+    lc_features(n->d_in, n->d_in + HW, n->d_in + 2 * (size_t)HW, n->d_in + 3 * (size_t)HW, H, W, n->d_sin, n->d_cos,
+                is, n->d_x0, n->stream);
+    // the input layer's vector channels (u^theta, u^phi) and sin(theta) change sign across a pole
+    lc_pad(n->d_x0, H, W, LC_CIN, LC_NEGMASK, n->d_xp[0], n->stream);
     for (int l = 0; l < LC_LAYERS; ++l) {
         const bool last = (l == LC_LAYERS - 1);
         lc_conv(l, n->d_xp[l], H + 2, W + 2, n->d_wf[l], n->d_w + n->boff[l], last ? n->d_y : nullptr,
@@ -189,6 +190,7 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
         A(&n->d_z[l], HW * LC_HID);
     }
     A(&n->d_sin, (size_t)n_theta);
+    A(&n->d_cos, (size_t)n_theta);
     A(&n->d_in, 4 * HW);
     A(&n->d_tg, 3 * HW);
     A(&n->d_out, 3 * HW);
@@ -209,14 +211,16 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
         return rc;
     }
     // cell-centre sines (north half evaluated, mirrored) and the area-weight sum
-    std::vector<double> sn(n_theta);
+    std::vector<double> sn(n_theta), cs(n_theta);
     const double dth = M_PI / n_theta;
     for (int i = 0; i < n_theta; ++i) {
         const int m = n_theta - 1 - i;
         sn[i] = (i <= m) ? std::sin((i + 0.5) * dth) : sn[m];
+        cs[i] = (i < m) ? std::cos((i + 0.5) * dth) : (i == m ? 0.0 : -cs[m]);
     }
     for (int i = 0; i < n_theta; ++i) n->wsum += sn[i] * n_phi;
     if (cudaMemcpy(n->d_sin, sn.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(n->d_cos, cs.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(n->d_w, w.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
         refresh_bf16(n) != VLBM_OK || cudaStreamSynchronize(n->stream) != cudaSuccess) {
         vlbm_lc_destroy(n);

@@ -8,13 +8,14 @@
 namespace vk {
 
 constexpr int LC_LAYERS = 4;
-constexpr int LC_IN = 4;        // rho - 1, u^theta, u^phi, T - 1
+constexpr int LC_IN = 6;        // rho - 1, u^theta, u^phi, T - 1, cos(theta), sin(theta)
 constexpr int LC_CIN = 16;      // input channels padded for the k = 16 tensor-core step
 constexpr int LC_HID = 32;      // hidden channels
 constexpr int LC_OUT = 3;       // drho, du^theta, du^phi
 constexpr int LC_COUT = 8;      // output channels padded to an n = 8 tile
 constexpr int LC_COUTP2 = 16;   // output-gradient channels padded for the k = 16 step (backward data)
 constexpr float LC_CLAMP = 8.0f;   // bound of every scaled input feature
+constexpr unsigned LC_NEGMASK = (1u << 1) | (1u << 2) | (1u << 5);   // input channels odd across a pole
 
 void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
              float *Yf, __nv_bfloat16 *Yb, int relu, cudaStream_t s);
@@ -34,8 +35,8 @@ void lc_adam(float *w, const float *g, float *m, float *v, int n, float lr, floa
 void lc_weights_bf16(const float *w, int CO, int CI, int COp, int CIp, __nv_bfloat16 *fwd, int CIp2, int COp2,
                      __nv_bfloat16 *bwd, cudaStream_t s);
 void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g, cudaStream_t s);
-void lc_features(const double *rho, const double *ut, const double *up, const double *T, int n, float4 inv_scale,
-                 __nv_bfloat16 *X0, cudaStream_t s);
+void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
+                 const double *sin_t, const double *cos_t, float4 inv_scale, __nv_bfloat16 *X0, cudaStream_t s);
 void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
                 double *mean, cudaStream_t s);
 void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,

@@ -568,13 +568,90 @@ __global__ void fill_ghosts_f32_kernel(f2 *f, const Layout L)
 
 // Polar ring filter, one CTA per (filtered row, pair plane).  The row is walked in
 // windows of 2048 columns; each of the 256 threads owns 8 consecutive columns.
-// Block sums are FP64: per-thread sums of 8 columns, then a pairwise tree over
-// the threads of each aligned block (deterministic order); every thread then
-// writes the mean to its 8 columns and their ghost images.  Blocks wider than a
-// window (b > 2048, only for n_phi above ~25000) take the slice path below.
+// Block sums are compensated: every addition is Knuth's error-free TwoSum, so a
+// partial sum is an unevaluated pair hi + lo of floats that carries the exact sum
+// of its inputs up to the rounding of the small lo parts (relative error ~2^-46).
+// Partials are combined across the threads of an aligned block by xor shuffles
+// (the lower lane's partial always first, so both partners form the same pair)
+// and, for blocks wider than a warp, through shared memory in warp order.  The
+// block mean is the pair scaled by the exact 1/b and rounded once to FP32, which is
+// the value of an FP64 accumulation (to ~2^-46) at FP32-pipe cost: GB300's FP64
+// rate is 1/64 of its FP32 rate.  Blocks wider than a window (b > 2048, only for
+// n_phi above ~25000) take the slice path below.
 constexpr int FILT_THREADS = 256;
 constexpr int FILT_COLS = 8;
 constexpr int FILT_WIN = FILT_THREADS * FILT_COLS;
+
+struct FF { f2 hi, lo; };   // a float-float pair per member
+
+__device__ __forceinline__ void two_sum(f2 a, f2 b, f2 &s, f2 &e)
+{
+    s = add2(a, b);
+    const f2 v = sub2(s, a);
+    e = add2(sub2(a, sub2(s, v)), sub2(b, v));
+}
+
+// (a.hi + a.lo) + (b.hi + b.lo) as a renormalised pair; a is the lower-index partial
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    f2 s, e, hi, lo;
+    two_sum(a.hi, b.hi, s, e);
+    e = add2(e, add2(a.lo, b.lo));
+    two_sum(s, e, hi, lo);
+    return FF{hi, lo};
+}
+
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int m)
+{
+    FF r;
+    r.hi.x = __shfl_xor_sync(0xffffffffu, a.hi.x, m);
+    r.hi.y = __shfl_xor_sync(0xffffffffu, a.hi.y, m);
+    r.lo.x = __shfl_xor_sync(0xffffffffu, a.lo.x, m);
+    r.lo.y = __shfl_xor_sync(0xffffffffu, a.lo.y, m);
+    return r;
+}
+
+// mean of the block whose sum is a.hi + a.lo: with r = 1/b exact (b a power of two),
+// lo r is exact and fma(hi, r, lo r) rounds hi r + lo r once, so the result is the
+// correctly rounded mean of the pair (the value an FP64 total scaled and rounded to
+// FP32 would give, without the FP64 pipe)
+__device__ __forceinline__ f2 ff_mean(FF a, float inv_b)
+{
+    return make_float2(fmaf(a.hi.x, inv_b, a.lo.x * inv_b), fmaf(a.hi.y, inv_b, a.lo.y * inv_b));
+}
+
+// ghost images of cell (p, i, j): periodic columns and, on the first/last GR rows, the pole image
+__device__ __forceinline__ void store_ghosts(f2 *f, const Layout &L, int p, int i, int j, f2 v)
+{
+    for (int m = 1; j - m * L.np >= -GC; ++m) f[L.at(p, i, j - m * L.np)] = v;
+    for (int m = 1; j + m * L.np < L.np + GC; ++m) f[L.at(p, i, j + m * L.np)] = v;
+    if (i < GR || i >= L.nt - GR) {
+        int jj = j + L.np / 2;
+        if (jj >= L.np) jj -= L.np;
+        const int r = (i < GR) ? (-1 - i) : (2 * L.nt - 1 - i);
+        put_cols(f, L, image_pair(p), r, jj, make_float2(-v.y, -v.x));
+    }
+}
+
+// means of the aligned blocks of B columns within one thread's FILT_COLS columns (n valid)
+template <int B>
+__device__ __forceinline__ void thread_block_means(f2 (&v)[FILT_COLS], int n, float inv_b)
+{
+#pragma unroll
+    for (int j0 = 0; j0 < FILT_COLS; j0 += B) {
+        if (j0 >= n) break;
+        FF a{v[j0], splat(0.0f)};
+#pragma unroll
+        for (int m = 1; m < B; ++m) {
+            f2 e;
+            two_sum(a.hi, v[j0 + m], a.hi, e);
+            a.lo = add2(a.lo, e);
+        }
+        const f2 mean = ff_mean(a, inv_b);
+#pragma unroll
+        for (int m = 0; m < B; ++m) v[j0 + m] = mean;
+    }
+}
 
 __global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const Layout L, const int *rows,
                                                                    const int *blocks)
@@ -582,76 +659,93 @@ __global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const L
     const int i = rows[blockIdx.x];
     const int b = blocks[blockIdx.x];
     const int q = blockIdx.y;
-    const int t = threadIdx.x;
-    __shared__ double2 part[FILT_THREADS];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const float inv_b = 1.0f / (float)b;   // exact: b is a power of two
+    __shared__ FF wpart[FILT_THREADS / 32];
+    const bool ghost_row = (i < GR || i >= L.nt - GR);
     if (b <= FILT_WIN) {
         for (int w0 = 0; w0 < L.np; w0 += FILT_WIN) {
-            const int c0 = w0 + t * FILT_COLS, c1 = min(c0 + FILT_COLS, L.np);
+            const int c0 = w0 + t * FILT_COLS;
+            const int n = max(0, min(FILT_COLS, L.np - c0));
+            f2 *row = f + L.at(q, i, 0);
             f2 v[FILT_COLS];
+            if (n == FILT_COLS) {
+                // 8 columns = 64 bytes at a 32-byte aligned offset (pitch and c0 + GC are multiples of 4)
+                const float4 *src = reinterpret_cast<const float4 *>(row + c0);
 #pragma unroll
-            for (int m = 0; m < FILT_COLS; ++m) v[m] = (c0 + m < c1) ? f[L.at(q, i, c0 + m)] : make_float2(0.f, 0.f);
+                for (int m = 0; m < FILT_COLS / 2; ++m) {
+                    const float4 x = src[m];
+                    v[2 * m] = make_float2(x.x, x.y);
+                    v[2 * m + 1] = make_float2(x.z, x.w);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < FILT_COLS; ++m) v[m] = (m < n) ? row[c0 + m] : make_float2(0.f, 0.f);
+            }
             if (b < FILT_COLS) {
-                // blocks lie inside this thread's columns
-                for (int j0 = 0; j0 < c1 - c0; j0 += b) {
-                    double sx = 0.0, sy = 0.0;
-                    for (int m = 0; m < b; ++m) {
-                        sx += v[j0 + m].x;
-                        sy += v[j0 + m].y;
-                    }
-                    const f2 mean = make_float2((float)(sx / b), (float)(sy / b));
-                    for (int m = 0; m < b; ++m) store_images(f, L, q, i, c0 + j0 + m, mean);
-                }
-                continue;
-            }
-            double sx = 0.0, sy = 0.0;
+                // blocks lie inside this thread's columns (b divides n_phi, so also n)
+                if (b == 2) thread_block_means<2>(v, n, inv_b);
+                else thread_block_means<4>(v, n, inv_b);
+            } else {
+                FF a{v[0], splat(0.0f)};
 #pragma unroll
-            for (int m = 0; m < FILT_COLS; ++m) {
-                sx += v[m].x;
-                sy += v[m].y;
-            }
-            part[t] = make_double2(sx, sy);
-            __syncthreads();
-            const int per = b / FILT_COLS;   // threads per block (a power of two)
-            for (int st = 1; st < per; st *= 2) {
-                if ((t % (2 * st)) == 0) {
-                    part[t].x += part[t + st].x;
-                    part[t].y += part[t + st].y;
+                for (int m = 1; m < FILT_COLS; ++m) {
+                    f2 e;
+                    two_sum(a.hi, v[m], a.hi, e);
+                    a.lo = add2(a.lo, e);
                 }
-                __syncthreads();
+                const int per = b / FILT_COLS;   // threads per block (a power of two)
+                const int wl = min(per, 32);
+                for (int m = 1; m < wl; m <<= 1) {
+                    const FF o = ff_shfl_xor(a, m);
+                    a = (lane & m) ? ff_add(o, a) : ff_add(a, o);
+                }
+                if (per > 32) {
+                    // blocks of per/32 warps: warp partials in warp order
+                    if (lane == 0) wpart[warp] = a;
+                    __syncthreads();
+                    const int wpb = per / 32, wfirst = (warp / wpb) * wpb;
+                    a = wpart[wfirst];
+                    for (int k = 1; k < wpb; ++k) a = ff_add(a, wpart[wfirst + k]);
+                    __syncthreads();   // wpart is reused by the next window
+                }
+                const f2 mean = ff_mean(a, inv_b);
+#pragma unroll
+                for (int m = 0; m < FILT_COLS; ++m) v[m] = mean;
             }
-            const double2 tot = part[(t / per) * per];
-            const f2 mean = make_float2((float)(tot.x / b), (float)(tot.y / b));
-            for (int c = c0; c < c1; ++c) store_images(f, L, q, i, c, mean);
-            __syncthreads();   // part[] is reused by the next window
+            if (n == FILT_COLS) {
+                float4 *dst = reinterpret_cast<float4 *>(row + c0);
+#pragma unroll
+                for (int m = 0; m < FILT_COLS / 2; ++m) dst[m] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
+            } else {
+                for (int m = 0; m < n; ++m) row[c0 + m] = v[m];
+            }
+            if (ghost_row || c0 < GC || c0 + n > L.np - GC) {
+                for (int m = 0; m < n; ++m) store_ghosts(f, L, q, i, c0 + m, v[m]);
+            }
         }
         return;
     }
-    // very wide blocks: slices of 32 columns summed per thread, slices in order per block
+    // very wide blocks: each thread sums columns t, t + 256, ... of the block, then
+    // the CTA combines the thread partials (warps by shuffles, then in warp order)
     const int nblk = L.np / b;
-    const int slices = b / 32;
     for (int blk = 0; blk < nblk; ++blk) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int sl = t; sl < slices; sl += FILT_THREADS) {
-            double sx = 0.0, sy = 0.0;
-            for (int m = 0; m < 32; ++m) {
-                const f2 x = f[L.at(q, i, blk * b + sl * 32 + m)];
-                sx += x.x;
-                sy += x.y;
-            }
-            acc.x += sx;
-            acc.y += sy;
+        FF a{splat(0.0f), splat(0.0f)};
+        for (int c = t; c < b; c += FILT_THREADS) {
+            f2 e;
+            two_sum(a.hi, f[L.at(q, i, blk * b + c)], a.hi, e);
+            a.lo = add2(a.lo, e);
         }
-        part[t] = acc;
-        __syncthreads();
-        for (int st = FILT_THREADS / 2; st > 0; st >>= 1) {
-            if (t < st) {
-                part[t].x += part[t + st].x;
-                part[t].y += part[t + st].y;
-            }
-            __syncthreads();
+        for (int m = 1; m < 32; m <<= 1) {
+            const FF o = ff_shfl_xor(a, m);
+            a = (lane & m) ? ff_add(o, a) : ff_add(a, o);
         }
-        const f2 mean = make_float2((float)(part[0].x / b), (float)(part[0].y / b));
+        if (lane == 0) wpart[warp] = a;
         __syncthreads();
+        a = wpart[0];
+        for (int k = 1; k < FILT_THREADS / 32; ++k) a = ff_add(a, wpart[k]);
+        __syncthreads();
+        const f2 mean = ff_mean(a, inv_b);
         for (int c = t; c < b; c += FILT_THREADS) store_images(f, L, q, i, blk * b + c, mean);
     }
 }

@@ -91,8 +91,20 @@ def rel_l2(a, ref):
     return float(np.sqrt((w * (a - ref) ** 2).sum() / (w * ref**2).sum()))
 
 
+def clamped_dt(n_theta, n_phi, tau):
+    """0.25 min(dtheta, sin(dtheta/2) dphi) / v_max, capped at tau (the stable step without the polar filter)."""
+    dth = math.pi / n_theta
+    lim = min(dth, math.sin(dth / 2) * 2 * math.pi / n_phi)
+    return min(0.25 * lim / math.sqrt(3 + math.sqrt(6)), tau)
+
+
 class Setup:
-    """Grids, time steps and relaxation time of one learned-coarse experiment."""
+    """Grids, time steps and relaxation time of one learned-coarse experiment.
+
+    With the polar filter, dt follows the theta spacing (0.25 dtheta / v_max, capped at
+    tau) and a coarse step is `factor` fine steps.  Without it, dt follows the pole
+    rows (clamped rule, ~ 1 / (n_theta n_phi)) and a coarse step is `substeps` fine
+    steps (factor^2 for equal aspect ratios)."""
 
     def __init__(self, coarse=(128, 256), factor=4, tau=2e-3, polar_filter=True):
         self.coarse = tuple(coarse)
@@ -101,9 +113,13 @@ class Setup:
         self.tau = float(tau)
         self.polar_filter = bool(polar_filter)
         vmax = math.sqrt(3 + math.sqrt(6))
-        # dt follows the theta spacing (polar filter on), coarse dt = factor x fine dt, capped at tau
-        self.dt_c = min(0.25 * (math.pi / self.coarse[0]) / vmax, self.tau)
-        self.dt_f = self.dt_c / factor
+        if self.polar_filter:
+            self.dt_c = min(0.25 * (math.pi / self.coarse[0]) / vmax, self.tau)
+            self.substeps = self.factor
+        else:
+            self.dt_c = clamped_dt(*self.coarse, self.tau)
+            self.substeps = math.ceil(self.dt_c / clamped_dt(*self.fine, self.tau) - 1e-9)
+        self.dt_f = self.dt_c / self.substeps
 
     def coarse_solver(self):
         return vlbm.Solver(*self.coarse, self.tau, self.dt_c, precision="fp32", polar_filter=self.polar_filter,
@@ -116,26 +132,29 @@ class Setup:
         return b
 
 
-def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=1):
+def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=1, stride=1):
     """(inputs [N,4,H,W], targets [N,3,H,W]) from coarse rollouts beside fine runs.
 
     One coarse solver per seed starts from the block-averaged fine populations and
     is re-started from them every `reinit_every` coarse steps (default: every step,
     so each target is the one-step gap of a coarse step taken from the fine state,
     the correction a per-step nudge has to supply); after each coarse step the
-    sample is (coarse moments, downsampled fine moments minus them).  With a
-    network and reinit_every > 1, its correction is applied after each sample (so
-    later rounds see the states the corrected rollout visits)."""
+    sample is (coarse moments, downsampled fine moments minus them).  With
+    reinit_every = 1, the fine runs advance `stride` coarse steps between samples.
+    With a network and reinit_every > 1, its correction is applied after each
+    sample (so later rounds see the states the corrected rollout visits)."""
     fb = setup.fine_batch(seeds)
     if spinup:
-        fb.step(spinup * setup.factor)
+        fb.step(spinup * setup.substeps)
     cs = [setup.coarse_solver() for _ in seeds]
     X, Y = [], []
     for k in range(n_steps):
         if k % reinit_every == 0:
+            if reinit_every == 1 and k and stride > 1:
+                fb.step((stride - 1) * setup.substeps)
             for r in range(len(seeds)):
                 cs[r].set_populations(downsample_populations(fb.get_populations(r), setup.factor))
-        fb.step(setup.factor)
+        fb.step(setup.substeps)
         for r in range(len(seeds)):
             cs[r].step(1)
             c = cs[r].moments(with_T=True)
@@ -144,6 +163,51 @@ def make_samples(setup: Setup, seeds, n_steps, spinup=0, net=None, reinit_every=
             Y.append(np.stack([d[0] - c[0], d[1] - c[1], d[2] - c[2]]))
             if net is not None:
                 net.apply(cs[r])
+    for c in cs:
+        c.close()
+    fb.close()
+    return np.array(X), np.array(Y)
+
+
+def make_drift_samples(setup: Setup, seeds, windows, settle=64, span=32, spans=4, spinup=0):
+    """(inputs [N,4,H,W], targets [N,3,H,W]): per-step drift of the coarse run away from the fine run.
+
+    Each window restarts the coarse solvers from the block-averaged fine populations,
+    lets the restart transient settle for `settle` coarse steps, then records `spans`
+    samples: after each further `span` steps, the coarse moments and the growth of the
+    gap (downsampled fine minus coarse) over that span divided by `span`.  The restart
+    offset cancels in the difference, so the target is the error the coarse scheme
+    adds per step, which a per-step correction has to remove."""
+    fb = setup.fine_batch(seeds)
+    if spinup:
+        fb.step(spinup * setup.substeps)
+    cs = [setup.coarse_solver() for _ in seeds]
+
+    def gaps():
+        out = []
+        for r in range(len(seeds)):
+            c = cs[r].moments(with_T=True)
+            d = downsample(*fb.moments(r, with_T=True))
+            out.append((np.stack(c), np.stack([d[0] - c[0], d[1] - c[1], d[2] - c[2]])))
+        return out
+
+    X, Y = [], []
+    for _ in range(windows):
+        for r in range(len(seeds)):
+            cs[r].set_populations(downsample_populations(fb.get_populations(r), setup.factor))
+        fb.step(settle * setup.substeps)
+        for c in cs:
+            c.step(settle)
+        prev = gaps()
+        for _ in range(spans):
+            fb.step(span * setup.substeps)
+            for c in cs:
+                c.step(span)
+            cur = gaps()
+            for (x, g1), (_, g0) in zip(cur, prev):
+                X.append(x)
+                Y.append((g1 - g0) / span)
+            prev = cur
     for c in cs:
         c.close()
     fb.close()
@@ -179,10 +243,10 @@ def train(setup: Setup, X, Y, epochs=4, lr=2e-3, seed=1, log=None, net=None):
 def evaluate(setup: Setup, net, seeds, n_steps, spinup=20):
     """Rollouts from the downsampled fine start: errors after n_steps coarse steps and wall times."""
     fb = setup.fine_batch(seeds)
-    fb.step(spinup * setup.factor)
+    fb.step(spinup * setup.substeps)
     starts = [downsample_populations(fb.get_populations(r), setup.factor) for r in range(len(seeds))]
     t0 = time.perf_counter()
-    fb.step(n_steps * setup.factor)
+    fb.step(n_steps * setup.substeps)
     t_fine = (time.perf_counter() - t0) / (n_steps * len(seeds))
     refs = [downsample(*fb.moments(r, with_T=True)) for r in range(len(seeds))]
     fb.close()
@@ -205,7 +269,7 @@ def evaluate(setup: Setup, net, seeds, n_steps, spinup=20):
                               "rho": rel_l2(rho - 1.0, ref[0] - 1.0)})
         times[mode] = el / (n_steps * len(seeds))
         cs.close()
-    # a fine step per coarse step costs `factor` fine steps; the batch advanced all seeds together
+    # a coarse step stands for `substeps` fine steps; the batch advanced all seeds together
     out = {"seeds": list(seeds), "coarse_steps": n_steps, "t_end": n_steps * setup.dt_c,
            "grid_coarse": list(setup.coarse), "grid_fine": list(setup.fine),
            "vort_err_plain": float(np.mean([e["vort"] for e in res["plain"]])),

@@ -52,6 +52,11 @@ CASES = {
     "minimum_6x2": (6, 2, 0.05, 1e-3, lambda: inputs.gaussian_vortices(6, 2, 8, umax=0.1), 40, False),
     "wide_row_8x4096": (8, 4096, 0.05, clamped_dt(8, 4096, 0.05), lambda: inputs.gaussian_vortices(8, 4096, 2), 3,
                         False),
+    # polar filter blocks wider than a warp's 256 columns (b = 1024 on the first rows)
+    "filter_wide_blocks_64x8192": (64, 8192, 0.01, literal_dt(64) / 2,
+                                   lambda: inputs.gaussian_vortices(64, 8192, 6), 3, True),
+    # polar filter blocks wider than one 2048-column window (b = 8192 on the pole rows)
+    "filter_window_blocks_8x32768": (8, 32768, 0.01, 0.01, lambda: inputs.gaussian_vortices(8, 32768, 7), 3, True),
 }
 
 
@@ -116,6 +121,8 @@ FP32_CASES = {
     "filter_vortices_16x32": (1e-7, 2e-4, 2e-5),
     "minimum_6x2": (1e-7, 2e-4, 2e-5),
     "wide_row_8x4096": (1e-7, 1e-3, 5e-7),
+    "filter_wide_blocks_64x8192": (1e-7, 2e-4, 2e-5),
+    "filter_window_blocks_8x32768": (1e-7, 2e-4, 2e-5),
 }
 
 

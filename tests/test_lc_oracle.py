@@ -55,4 +55,4 @@ def test_backprop_matches_finite_differences():
 
 
 def test_parameter_count():
-    assert L.num_params() == 32 * 4 * 9 + 32 + 2 * (32 * 32 * 9 + 32) + 3 * 32 * 9 + 3
+    assert L.num_params() == 32 * 6 * 9 + 32 + 2 * (32 * 32 * 9 + 32) + 3 * 32 * 9 + 3
