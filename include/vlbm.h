@@ -204,13 +204,15 @@ VLBM_API const char *vlbm_batch_last_error(const vlbm_batch_t *b);
 VLBM_API void vlbm_batch_destroy(vlbm_batch_t *b);
 
 /* ---- Learned correction (not in the paper) -------------------------------------
- * A 4-layer 3x3 convolutional network (6 -> 32 -> 32 -> 32 -> 3 channels, ReLU
+ * A 4-layer 3x3 convolutional network (16 -> 32 -> 32 -> 32 -> 3 channels, ReLU
  * between) on a coarse grid, mapping the moments (rho, u^theta, u^phi, T) of a
- * coarse FP32 solver after a step, plus cos(theta) and sin(theta) of each row,
- * to a correction (drho, du^theta, du^phi) toward a finer run.  Padding follows
- * the sphere: periodic in phi; beyond a pole, the row on the opposite meridian
- * with the velocity channels and sin(theta) negated (Sec. 3.6, Eq. bcs_theta,
- * applied to moments).  BF16 activations and
+ * coarse FP32 solver, cos(theta) and sin(theta) of each row, and undivided 6th
+ * differences of rho, u^theta, u^phi and 4th differences of u^theta, u^phi along
+ * theta and along phi (formed in FP64), to a correction (drho, du^theta, du^phi)
+ * toward a finer run.  Padding and the differences follow the sphere: periodic in
+ * phi; beyond a pole, the row on the opposite meridian with the velocity
+ * components (and their differences, and sin(theta)) negated (Sec. 3.6, Eq.
+ * bcs_theta, applied to moments).  BF16 activations and
  * weights, FP32 accumulation on the tensor cores, FP32 master weights and Adam.
  * Host arrays: inputs [4][n_theta][n_phi] (rho, u^theta, u^phi, T), targets and
  * outputs [3][n_theta][n_phi] (drho, du^theta, du^phi), physical units; the
@@ -218,17 +220,20 @@ VLBM_API void vlbm_batch_destroy(vlbm_batch_t *b);
  * sin(theta)-area-weighted mean square of the scaled residual. */
 typedef struct vlbm_lc vlbm_lc_t;
 
-/* Creates a network for an n_theta x n_phi grid (n_phi even) with weights drawn
- * from splitmix64(seed). */
+/* Creates a network for an n_theta x n_phi grid (n_theta >= 4, n_phi even) with
+ * weights drawn from splitmix64(seed). */
 VLBM_API int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **out);
 /* Number of FP32 parameters; layout per layer l = 0..3: W[co][ci][3][3] then b[co]
- * (input channels of layer 0: rho-1, u^theta, u^phi, T-1, cos theta, sin theta). */
+ * (input channels of layer 0: rho-1, u^theta, u^phi, T-1, cos theta, sin theta,
+ * d6_theta rho, d6_phi rho, d6_theta u^theta, d6_phi u^theta, d6_theta u^phi,
+ * d6_phi u^phi, d4_theta u^theta, d4_phi u^theta, d4_theta u^phi, d4_phi u^phi). */
 VLBM_API int vlbm_lc_num_params(const vlbm_lc_t *lc);
 VLBM_API int vlbm_lc_get_weights(vlbm_lc_t *lc, float *w);
 /* Sets the weights and resets the Adam state. */
 VLBM_API int vlbm_lc_set_weights(vlbm_lc_t *lc, const float *w);
-/* in_scale[4] divides (rho-1, u^theta, u^phi, T-1) (each scaled input is then clamped to
- * [-8, 8]); out_scale[3] multiplies the outputs. */
+/* in_scale[14] divides the 14 data channels (rho-1, u^theta, u^phi, T-1 and the ten
+ * differences in the order above; each scaled input is then clamped to [-8, 8]);
+ * out_scale[3] multiplies the outputs. */
 VLBM_API int vlbm_lc_set_scales(vlbm_lc_t *lc, const double *in_scale, const double *out_scale);
 /* Forward pass: outputs in physical units (drho not mean-corrected). */
 VLBM_API int vlbm_lc_predict(vlbm_lc_t *lc, const double *inputs, double *outputs);

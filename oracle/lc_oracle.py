@@ -1,11 +1,12 @@
 """Plain FP64 CPU reference of the learned-correction network (not in the paper).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Same definitions as the
-CUDA network, written out with numpy: inputs (rho-1, u^theta, u^phi, T-1)
-divided by in_scale and clamped to [-8, 8], plus cos(theta) and sin(theta) of the row;
-3x3 convolutions 6 -> 32 -> 32 -> 32 -> 3 with ReLU between; padding periodic in phi
-and, beyond a pole, the row on the opposite meridian (column + W/2) with the
-input's velocity channels and sin(theta) negated (the pole boundary
+CUDA network, written out with numpy: inputs (rho-1, u^theta, u^phi, T-1) and
+undivided 4th / 6th differences of the moments along theta and phi, divided by
+in_scale and clamped to [-8, 8], plus cos(theta) and sin(theta) of the row;
+3x3 convolutions 16 -> 32 -> 32 -> 32 -> 3 with ReLU between; padding (and the
+differences' halo) periodic in phi and, beyond a pole, the row on the opposite
+meridian (column + W/2) with velocity channels and sin(theta) negated (the pole boundary
 condition of arXiv 2504.15574 Sec. 3.6 applied to moments); loss = the
 sin(theta)-area-weighted mean over cells and the 3 channels of
 (y - target / out_scale)^2.  Parameters are one flat FP32/FP64 vector, per layer
@@ -17,8 +18,9 @@ import math
 
 import numpy as np
 
-LAYERS = [(6, 32), (32, 32), (32, 32), (32, 3)]
-NEG = [1, 2, 5]   # input channels odd across a pole: u^theta, u^phi, sin(theta)
+LAYERS = [(16, 32), (32, 32), (32, 32), (32, 3)]
+# input channels odd across a pole: u^theta, u^phi, sin(theta) and the velocity differences
+NEG = [1, 2, 5] + list(range(8, 16))
 
 
 def unflatten(p):
@@ -84,14 +86,56 @@ def conv_valid(xp, w, b):
 CLAMP = 8.0
 
 
+def extend(a, odd, halo=3):
+    """a [H][W] -> [H+2 halo][W+2 halo]: columns wrap; a row beyond a pole is the
+    mirrored row on the opposite meridian, negated for a velocity component."""
+    H, W = a.shape
+    sgn = -1.0 if odd else 1.0
+    rows = []
+    for r in range(-halo, H + halo):
+        if r < 0:
+            rows.append(sgn * np.roll(a[-1 - r], -(W // 2)))
+        elif r >= H:
+            rows.append(sgn * np.roll(a[2 * H - 1 - r], -(W // 2)))
+        else:
+            rows.append(a[r])
+    e = np.array(rows)
+    return np.concatenate([e[:, W - halo:], e, e[:, :halo]], axis=1)
+
+
+D4 = [1.0, -4.0, 6.0, -4.0, 1.0]
+D6 = [1.0, -6.0, 15.0, -20.0, 15.0, -6.0, 1.0]
+
+
+def difference(a, odd, stencil, axis):
+    """Undivided difference with the given stencil along theta (axis 0) or phi (axis 1)."""
+    H, W = a.shape
+    e = extend(a, odd)
+    h = len(stencil) // 2
+    out = np.zeros((H, W))
+    for m, w in enumerate(stencil):
+        o = 3 + m - h
+        out += w * (e[o:o + H, 3:3 + W] if axis == 0 else e[3:3 + H, o:o + W])
+    return out
+
+
 def features(inputs, in_scale):
-    """Scaled moments clamped to [-CLAMP, CLAMP], then cos(theta) and sin(theta) of the cell row."""
+    """The 16 input channels: rho-1, u^theta, u^phi, T-1, then cos(theta), sin(theta),
+    then d6_theta rho, d6_phi rho, d6_theta u^theta, d6_phi u^theta, d6_theta u^phi,
+    d6_phi u^phi, d4_theta u^theta, d4_phi u^theta, d4_theta u^phi, d4_phi u^phi.  The 14
+    data channels are divided by in_scale and clamped to [-CLAMP, CLAMP]."""
     rho, ut, up, T = inputs
-    x = np.stack([(rho - 1.0) / in_scale[0], ut / in_scale[1], up / in_scale[2], (T - 1.0) / in_scale[3]])
     H, W = rho.shape
+    data = [rho - 1.0, ut, up, T - 1.0,
+            difference(rho, False, D6, 0), difference(rho, False, D6, 1),
+            difference(ut, True, D6, 0), difference(ut, True, D6, 1),
+            difference(up, True, D6, 0), difference(up, True, D6, 1),
+            difference(ut, True, D4, 0), difference(ut, True, D4, 1),
+            difference(up, True, D4, 0), difference(up, True, D4, 1)]
+    x = np.clip(np.stack([d / s for d, s in zip(data, in_scale)]), -CLAMP, CLAMP)
     th = (np.arange(H) + 0.5) * math.pi / H
     lat = np.stack([np.cos(th)[:, None] * np.ones((1, W)), np.sin(th)[:, None] * np.ones((1, W))])
-    return np.concatenate([np.clip(x, -CLAMP, CLAMP), lat])
+    return np.concatenate([x[:4], lat, x[4:]])
 
 
 def area_weights(H, W):
@@ -101,9 +145,12 @@ def area_weights(H, W):
     return w / w.sum()
 
 
-def forward(params, inputs, in_scale):
-    """Returns the net output [3][H][W] (scaled units) and the per-layer tensors."""
+def forward(params, inputs, in_scale, quantize=None):
+    """Returns the net output [3][H][W] (scaled units) and the per-layer tensors.
+    quantize (optional) maps the input features to a storage precision (e.g. BF16)."""
     x = features(inputs, in_scale)
+    if quantize is not None:
+        x = quantize(x)
     cache = []
     for l, (w, b) in enumerate(unflatten(params)):
         xp = pad(x, NEG if l == 0 else [])
@@ -113,9 +160,9 @@ def forward(params, inputs, in_scale):
     return x, cache
 
 
-def loss_and_grad(params, inputs, targets, in_scale, out_scale):
+def loss_and_grad(params, inputs, targets, in_scale, out_scale, quantize=None):
     """Loss and d loss / d params by explicit backpropagation."""
-    y, cache = forward(params, inputs, in_scale)
+    y, cache = forward(params, inputs, in_scale, quantize)
     H, W = y.shape[1:]
     aw = area_weights(H, W)
     t = np.stack([targets[c] / out_scale[c] for c in range(3)])

@@ -392,26 +392,78 @@ __global__ void wgrad_layout_kernel(const float *g9, int CO, int CI, int COp, in
     g[i] = g9[((size_t)tap * COp + co) * CIp + ci];
 }
 
-// network input from the moments of a coarse solver: [(rho-1)/s0, ut/s1, up/s2, (T-1)/s3, cos theta,
-// sin theta, 0 ...]; the moment channels are clamped to [-LC_CLAMP, LC_CLAMP] so that states outside the
-// training range stay bounded.  The latitude channels let the (translation-equivariant) convolutions
-// depend on theta, as the coarse scheme's error does.
+// Value of a moment field at grid point (r, c) for -3 <= r < H + 3: columns wrap; a
+// row beyond a pole is the mirrored row on the opposite meridian (c + W/2), negated
+// for a velocity component (sgn = -1), as the pole condition of Sec. 3.6 maps it.
+__device__ __forceinline__ double lc_at(const double *a, int H, int W, int r, int c, double sgn)
+{
+    double s = 1.0;
+    if (r < 0 || r >= H) {
+        r = (r < 0) ? (-1 - r) : (2 * H - 1 - r);
+        c += W / 2;
+        s = sgn;
+    }
+    c %= W;
+    if (c < 0) c += W;
+    return s * a[(size_t)r * W + c];
+}
+
+// undivided 4th and 6th differences of a field along theta (dir 0) or phi (dir 1) at (i, j)
+__device__ __forceinline__ void lc_differences(const double *a, int H, int W, int i, int j, int dir, double sgn,
+                                               double &d4, double &d6)
+{
+    double x[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m)
+        x[m] = dir ? lc_at(a, H, W, i, j + m - 3, sgn) : lc_at(a, H, W, i + m - 3, j, sgn);
+    d4 = x[1] - 4.0 * x[2] + 6.0 * x[3] - 4.0 * x[4] + x[5];
+    d6 = x[0] - 6.0 * x[1] + 15.0 * x[2] - 20.0 * x[3] + 15.0 * x[4] - 6.0 * x[5] + x[6];
+}
+
+// network input from the moments of a coarse solver (channel order in lc_internal.h):
+// the moments and their undivided 4th / 6th differences are formed in FP64, divided
+// by their scales and clamped to [-LC_CLAMP, LC_CLAMP] before the BF16 rounding (a
+// BF16 field could not resolve the high-order differences that carry a coarse
+// scheme's truncation error); the latitude channels let the translation-equivariant
+// convolutions depend on theta.
 __global__ void features_kernel(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                                const double *sin_t, const double *cos_t, float4 inv_scale, __nv_bfloat16 *X0)
+                                const double *sin_t, const double *cos_t, const LcInScale sc, __nv_bfloat16 *X0)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= H * W) return;
-    float v[LC_CIN] = {0};
-    v[0] = (float)((rho[i] - 1.0) * inv_scale.x);
-    v[1] = (float)(ut[i] * inv_scale.y);
-    v[2] = (float)(up[i] * inv_scale.z);
-    v[3] = (float)((T ? T[i] - 1.0 : 0.0) * inv_scale.w);
+    const int r = i / W, c = i - r * W;
+    double raw[LC_NSCALE];
+    raw[0] = rho[i] - 1.0;
+    raw[1] = ut[i];
+    raw[2] = up[i];
+    raw[3] = T ? T[i] - 1.0 : 0.0;
+    double d4, d6;
+    lc_differences(rho, H, W, r, c, 0, 1.0, d4, d6);
+    raw[4] = d6;
+    lc_differences(rho, H, W, r, c, 1, 1.0, d4, d6);
+    raw[5] = d6;
+    lc_differences(ut, H, W, r, c, 0, -1.0, d4, d6);
+    raw[6] = d6;
+    raw[10] = d4;
+    lc_differences(ut, H, W, r, c, 1, -1.0, d4, d6);
+    raw[7] = d6;
+    raw[11] = d4;
+    lc_differences(up, H, W, r, c, 0, -1.0, d4, d6);
+    raw[8] = d6;
+    raw[12] = d4;
+    lc_differences(up, H, W, r, c, 1, -1.0, d4, d6);
+    raw[9] = d6;
+    raw[13] = d4;
+    float v[LC_CIN];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] = fminf(fmaxf(v[c], -LC_CLAMP), LC_CLAMP);
-    v[4] = (float)cos_t[i / W];
-    v[5] = (float)sin_t[i / W];
+    for (int q = 0; q < LC_NSCALE; ++q) {
+        const float x = (float)(raw[q] * (double)sc.inv[q]);
+        v[q < 4 ? q : q + 2] = fminf(fmaxf(x, -LC_CLAMP), LC_CLAMP);
+    }
+    v[4] = (float)cos_t[r];
+    v[5] = (float)sin_t[r];
 #pragma unroll
-    for (int c = 0; c < LC_CIN; ++c) X0[(size_t)i * LC_CIN + c] = __float2bfloat16(v[c]);
+    for (int q = 0; q < LC_CIN; ++q) X0[(size_t)i * LC_CIN + q] = __float2bfloat16(v[q]);
 }
 
 // output [H][W][CO] -> (drho, dut, dup) [3][H][W] in physical units, and sin-weighted drho partial sums
@@ -565,7 +617,8 @@ void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g
 }
 
 void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                 const double *sin_t, const double *cos_t, float4 inv_scale, __nv_bfloat16 *X0, cudaStream_t s)
+                 const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *X0,
+                 cudaStream_t s)
 {
     features_kernel<<<(H * W + 255) / 256, 256, 0, s>>>(rho, ut, up, T, H, W, sin_t, cos_t, inv_scale, X0);
 }

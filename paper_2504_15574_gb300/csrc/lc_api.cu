@@ -32,7 +32,8 @@ struct vlbm_lc {
     __nv_bfloat16 *d_dp = nullptr, *d_dpre = nullptr;
     float *d_wpart = nullptr, *d_bpart = nullptr, *d_g9 = nullptr;
     double wsum = 0.0;
-    float in_scale[4] = {1e-3f, 1e-2f, 1e-2f, 1e-3f};
+    float in_scale[LC_NSCALE] = {1e-3f, 1e-2f, 1e-2f, 1e-3f, 1e-6f, 1e-6f, 1e-5f, 1e-5f, 1e-5f,
+                                 1e-5f, 1e-5f, 1e-5f, 1e-5f, 1e-5f};
     float out_scale[3] = {1e-5f, 1e-4f, 1e-4f};
     long long t = 0;
     std::vector<void *> bufs;
@@ -84,11 +85,11 @@ int refresh_bf16(vlbm_lc_t *n)
 int forward(vlbm_lc_t *n)
 {
     const int H = n->H, W = n->W, HW = H * W;
-    const float4 is = make_float4(1.0f / n->in_scale[0], 1.0f / n->in_scale[1], 1.0f / n->in_scale[2],
-                                  1.0f / n->in_scale[3]);
+    LcInScale is;
+    for (int q = 0; q < LC_NSCALE; ++q) is.inv[q] = 1.0f / n->in_scale[q];
     lc_features(n->d_in, n->d_in + HW, n->d_in + 2 * (size_t)HW, n->d_in + 3 * (size_t)HW, H, W, n->d_sin, n->d_cos,
                 is, n->d_x0, n->stream);
-    // the input layer's vector channels (u^theta, u^phi) and sin(theta) change sign across a pole
+    // the input layer's velocity channels, their differences and sin(theta) change sign across a pole
     lc_pad(n->d_x0, H, W, LC_CIN, LC_NEGMASK, n->d_xp[0], n->stream);
     for (int l = 0; l < LC_LAYERS; ++l) {
         const bool last = (l == LC_LAYERS - 1);
@@ -142,7 +143,7 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
 {
     if (!out) return VLBM_ERR_ARG;
     *out = nullptr;
-    if (n_theta < 2 || n_phi < 2 || n_phi % 2) return VLBM_ERR_ARG;
+    if (n_theta < 4 || n_phi < 2 || n_phi % 2) return VLBM_ERR_ARG;
     vlbm_lc_t *n = new vlbm_lc_t();
     n->H = n_theta;
     n->W = n_phi;
@@ -256,11 +257,11 @@ int vlbm_lc_set_weights(vlbm_lc_t *n, const float *w)
 int vlbm_lc_set_scales(vlbm_lc_t *n, const double *in_scale, const double *out_scale)
 {
     if (!n || !in_scale || !out_scale) return VLBM_ERR_ARG;
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < LC_NSCALE; ++q)
         if (!(in_scale[q] > 0.0)) return lfail(n, VLBM_ERR_ARG, "scales must be > 0");
     for (int q = 0; q < 3; ++q)
         if (!(out_scale[q] > 0.0)) return lfail(n, VLBM_ERR_ARG, "scales must be > 0");
-    for (int q = 0; q < 4; ++q) n->in_scale[q] = (float)in_scale[q];
+    for (int q = 0; q < LC_NSCALE; ++q) n->in_scale[q] = (float)in_scale[q];
     for (int q = 0; q < 3; ++q) n->out_scale[q] = (float)out_scale[q];
     return VLBM_OK;
 }

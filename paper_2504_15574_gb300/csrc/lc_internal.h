@@ -8,14 +8,21 @@
 namespace vk {
 
 constexpr int LC_LAYERS = 4;
-constexpr int LC_IN = 6;        // rho - 1, u^theta, u^phi, T - 1, cos(theta), sin(theta)
+// Input channels: 0 rho - 1, 1 u^theta, 2 u^phi, 3 T - 1, 4 cos(theta), 5 sin(theta), then the
+// undivided differences 6 d6_theta rho, 7 d6_phi rho, 8 d6_theta u^theta, 9 d6_phi u^theta,
+// 10 d6_theta u^phi, 11 d6_phi u^phi, 12 d4_theta u^theta, 13 d4_phi u^theta, 14 d4_theta u^phi,
+// 15 d4_phi u^phi (d4 = [1 -4 6 -4 1], d6 = [1 -6 15 -20 15 -6 1] along a grid line).
+constexpr int LC_IN = 16;
+constexpr int LC_NSCALE = 14;   // scaled channels: 0-3 and 6-15
 constexpr int LC_CIN = 16;      // input channels padded for the k = 16 tensor-core step
 constexpr int LC_HID = 32;      // hidden channels
 constexpr int LC_OUT = 3;       // drho, du^theta, du^phi
 constexpr int LC_COUT = 8;      // output channels padded to an n = 8 tile
 constexpr int LC_COUTP2 = 16;   // output-gradient channels padded for the k = 16 step (backward data)
 constexpr float LC_CLAMP = 8.0f;   // bound of every scaled input feature
-constexpr unsigned LC_NEGMASK = (1u << 1) | (1u << 2) | (1u << 5);   // input channels odd across a pole
+// input channels odd across a pole: the velocity components, their differences and sin(theta)
+constexpr unsigned LC_NEGMASK = (1u << 1) | (1u << 2) | (1u << 5) | (0xFFu << 8);
+struct LcInScale { float inv[LC_NSCALE]; };
 
 void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
              float *Yf, __nv_bfloat16 *Yb, int relu, cudaStream_t s);
@@ -36,7 +43,8 @@ void lc_weights_bf16(const float *w, int CO, int CI, int COp, int CIp, __nv_bflo
                      __nv_bfloat16 *bwd, cudaStream_t s);
 void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g, cudaStream_t s);
 void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                 const double *sin_t, const double *cos_t, float4 inv_scale, __nv_bfloat16 *X0, cudaStream_t s);
+                 const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *X0,
+                 cudaStream_t s);
 void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
                 double *mean, cudaStream_t s);
 void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,

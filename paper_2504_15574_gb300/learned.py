@@ -214,10 +214,40 @@ def make_drift_samples(setup: Setup, seeds, windows, settle=64, span=32, spans=4
     return np.array(X), np.array(Y)
 
 
+def _extend_theta(a, odd, halo=3):
+    """[..., H, W] -> [..., H + 2 halo, W]: rows beyond a pole from the opposite meridian."""
+    W = a.shape[-1]
+    sgn = -1.0 if odd else 1.0
+    north = sgn * np.roll(a[..., :halo, :][..., ::-1, :], -(W // 2), axis=-1)
+    south = sgn * np.roll(a[..., -halo:, :][..., ::-1, :], -(W // 2), axis=-1)
+    return np.concatenate([north, a, south], axis=-2)
+
+
+def _differences(X):
+    """The ten difference channels the network's feature kernel forms (for their scales)."""
+    D4, D6 = [1.0, -4.0, 6.0, -4.0, 1.0], [1.0, -6.0, 15.0, -20.0, 15.0, -6.0, 1.0]
+
+    def diff(a, odd, st, axis):
+        h = len(st) // 2
+        if axis == 1:
+            return sum(w * np.roll(a, h - m, axis=-1) for m, w in enumerate(st))
+        e = _extend_theta(a, odd)
+        H = a.shape[-2]
+        return sum(w * e[..., 3 + m - h:3 + m - h + H, :] for m, w in enumerate(st))
+
+    rho, ut, up = X[:, 0], X[:, 1], X[:, 2]
+    return [diff(rho, False, D6, 0), diff(rho, False, D6, 1), diff(ut, True, D6, 0), diff(ut, True, D6, 1),
+            diff(up, True, D6, 0), diff(up, True, D6, 1), diff(ut, True, D4, 0), diff(ut, True, D4, 1),
+            diff(up, True, D4, 0), diff(up, True, D4, 1)]
+
+
 def scales(X, Y):
-    """Per-channel input and output scales from the sample spread (T floored at 1e-3)."""
+    """Per-channel input and output scales from the sample spread: the largest |value| of
+    rho-1, u^theta, u^phi, T-1 (T floored at 1e-3), the std of each difference channel, and
+    the std of each target channel."""
     ins = [max(np.abs(X[:, 0] - 1).max(), 1e-12), max(np.abs(X[:, 1]).max(), 1e-12),
            max(np.abs(X[:, 2]).max(), 1e-12), max(np.abs(X[:, 3] - 1).max(), 1e-3)]
+    ins += [max(float(d.std()), 1e-30) for d in _differences(X)]
     outs = [max(Y[:, c].std(), 1e-16) for c in range(3)]
     return ins, outs
 
@@ -272,6 +302,8 @@ def evaluate(setup: Setup, net, seeds, n_steps, spinup=20):
     # a coarse step stands for `substeps` fine steps; the batch advanced all seeds together
     out = {"seeds": list(seeds), "coarse_steps": n_steps, "t_end": n_steps * setup.dt_c,
            "grid_coarse": list(setup.coarse), "grid_fine": list(setup.fine),
+           "vort_err_plain_per_seed": [e["vort"] for e in res["plain"]],
+           "vort_err_learned_per_seed": [e["vort"] for e in res["learned"]],
            "vort_err_plain": float(np.mean([e["vort"] for e in res["plain"]])),
            "vort_err_learned": float(np.mean([e["vort"] for e in res["learned"]])),
            "rho_err_plain": float(np.mean([e["rho"] for e in res["plain"]])),
@@ -286,35 +318,38 @@ def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--coarse", type=int, nargs=2, default=[128, 256])
+    ap.add_argument("--polar-filter", action="store_true", help="filter on (dt by the theta spacing)")
+    ap.add_argument("--targets", choices=["drift", "one-step"], default="drift")
     ap.add_argument("--train-seeds", type=int, default=16)
-    ap.add_argument("--steps", type=int, default=48, help="coarse steps of training data per seed")
+    ap.add_argument("--windows", type=int, default=8, help="drift targets: restart windows per seed")
+    ap.add_argument("--steps", type=int, default=48, help="one-step targets: samples per seed")
     ap.add_argument("--spinup", type=int, default=20)
-    ap.add_argument("--epochs", type=int, default=4)
-    ap.add_argument("--rounds", type=int, default=1, help="data rounds; later rounds roll out with the network")
-    ap.add_argument("--reinit-every", type=int, default=1, help="coarse steps between restarts from the fine state")
-    ap.add_argument("--eval-seeds", type=int, default=3)
-    ap.add_argument("--eval-steps", type=int, default=60)
+    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--eval-seeds", type=int, default=4)
+    ap.add_argument("--eval-steps", type=int, nargs="+", default=[300, 1000])
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
-    setup = Setup(coarse=a.coarse)
+    setup = Setup(coarse=a.coarse, polar_filter=a.polar_filter)
     seeds = list(range(1000, 1000 + a.train_seeds))
-    t_data = t_train = 0.0
-    net, hist, Xs, Ys = None, [], [], []
-    for rnd in range(a.rounds):
-        t0 = time.perf_counter()
-        X, Y = make_samples(setup, seeds, a.steps, spinup=a.spinup, net=net, reinit_every=a.reinit_every)
-        Xs.append(X)
-        Ys.append(Y)
-        t_data += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        net, h = train(setup, np.concatenate(Xs), np.concatenate(Ys), epochs=a.epochs, log=print, net=net,
-                       lr=2e-3 * 0.5**rnd)
-        hist += h
-        t_train += time.perf_counter() - t0
-    res = evaluate(setup, net, list(range(5000, 5000 + a.eval_seeds)), a.eval_steps)
-    res.update({"samples": int(sum(len(x) for x in Xs)), "loss_history": hist, "seconds_data": t_data,
-                "seconds_train": t_train, "rounds": a.rounds})
-    line = json.dumps(res)
+    t0 = time.perf_counter()
+    if a.targets == "drift":
+        X, Y = make_drift_samples(setup, seeds, a.windows, spinup=a.spinup)
+    else:
+        X, Y = make_samples(setup, seeds, a.steps, spinup=a.spinup)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, hist = train(setup, X, Y, epochs=a.epochs, log=print)
+    t_train = time.perf_counter() - t0
+    out = {"grid_coarse": list(setup.coarse), "grid_fine": list(setup.fine), "polar_filter": setup.polar_filter,
+           "dt_coarse": setup.dt_c, "fine_steps_per_coarse_step": setup.substeps, "targets": a.targets,
+           "samples": int(len(X)), "loss_history": hist, "seconds_data": t_data, "seconds_train": t_train,
+           "horizons": []}
+    for n in a.eval_steps:
+        res = evaluate(setup, net, list(range(5000, 5000 + a.eval_seeds)), n, spinup=a.spinup)
+        out["horizons"].append(res)
+        print(json.dumps({k: res[k] for k in ("coarse_steps", "vort_err_plain", "vort_err_learned", "rho_err_plain",
+                                              "rho_err_learned", "speedup_learned_vs_fine")}))
+    line = json.dumps(out)
     print(line)
     if a.out:
         with open(a.out, "w") as fh:

@@ -388,7 +388,10 @@ class Batch:
 class LearnedCorrection:
     """The coarse-grid correction network (vlbm_lc_*)."""
 
-    def __init__(self, n_theta, n_phi, seed=1, in_scale=(1e-3, 1e-2, 1e-2, 1e-3), out_scale=(1e-5, 1e-4, 1e-4)):
+    # scales of the 14 data channels: rho-1, u^theta, u^phi, T-1, then the ten differences
+    DEFAULT_IN_SCALE = (1e-3, 1e-2, 1e-2, 1e-3) + (1e-6,) * 2 + (1e-5,) * 8
+
+    def __init__(self, n_theta, n_phi, seed=1, in_scale=DEFAULT_IN_SCALE, out_scale=(1e-5, 1e-4, 1e-4)):
         self.shape = (int(n_theta), int(n_phi))
         self.h = _H()
         rc = load().vlbm_lc_create(self.shape[0], self.shape[1], int(seed), ctypes.byref(self.h))
@@ -404,6 +407,8 @@ class LearnedCorrection:
     def set_scales(self, in_scale, out_scale):
         self.in_scale = np.asarray(in_scale, dtype=np.float64)
         self.out_scale = np.asarray(out_scale, dtype=np.float64)
+        if self.in_scale.shape != (14,) or self.out_scale.shape != (3,):
+            raise ValueError("in_scale takes 14 values, out_scale 3")
         self._chk(load().vlbm_lc_set_scales(self.h, _p(self.in_scale), _p(self.out_scale)))
 
     def num_params(self):

@@ -40,7 +40,7 @@ def test_backprop_matches_finite_differences():
     x, t = _sample(H, W, 3)
     p = L.init_params(7)
     p[-3:] = [0.01, -0.02, 0.03]
-    ins, outs = [1e-3, 2e-2, 2e-2, 1e-2], [1e-4, 1e-4, 1e-4]
+    ins, outs = [1e-3, 2e-2, 2e-2, 1e-2] + [1e-3] * 10, [1e-4, 1e-4, 1e-4]
     loss, g = L.loss_and_grad(p, x, t, ins, outs)
     rng = np.random.default_rng(1)
     idx = rng.choice(p.size, 40, replace=False)
@@ -55,4 +55,36 @@ def test_backprop_matches_finite_differences():
 
 
 def test_parameter_count():
-    assert L.num_params() == 32 * 6 * 9 + 32 + 2 * (32 * 32 * 9 + 32) + 3 * 32 * 9 + 3
+    assert L.num_params() == 32 * 16 * 9 + 32 + 2 * (32 * 32 * 9 + 32) + 3 * 32 * 9 + 3
+
+
+def test_phi_differences_of_a_fourier_mode_are_powers_of_the_second_difference():
+    # the undivided second difference of cos(k phi) on a periodic grid is (2 cos(k dphi) - 2) cos(k phi)
+    H, W, k = 5, 16, 3
+    phi = (np.arange(W) + 0.5) * 2 * np.pi / W
+    a = np.cos(k * phi)[None, :] * np.ones((H, 1))
+    lam = 2 * np.cos(k * 2 * np.pi / W) - 2
+    assert np.allclose(L.difference(a, False, L.D4, 1), lam ** 2 * a, atol=1e-12)
+    assert np.allclose(L.difference(a, False, L.D6, 1), lam ** 3 * a, atol=1e-12)
+    # a row-independent even mode continues unchanged across a pole: no theta difference
+    a2 = np.cos(2 * phi)[None, :] * np.ones((H, 1))
+    assert np.allclose(L.difference(a2, False, L.D6, 0), 0.0, atol=1e-12)
+
+
+def test_theta_differences_continue_smooth_fields_across_the_poles():
+    # cos(theta) and the components of a uniform Cartesian flow (u_theta = cos(theta) cos(phi),
+    # u_phi = -sin(phi)) continue across a pole as the same smooth functions of the row index,
+    # so their theta differences are powers of the second difference on every row
+    H, W = 8, 12
+    th = (np.arange(H) + 0.5) * np.pi / H
+    ph = (np.arange(W) + 0.5) * 2 * np.pi / W
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    lam = 2 * np.cos(np.pi / H) - 2
+    z = np.cos(TH)
+    assert np.allclose(L.difference(z, False, L.D6, 0), lam ** 3 * z, atol=1e-12)
+    ut, up = np.cos(TH) * np.cos(PH), -np.sin(PH)
+    assert np.allclose(L.difference(ut, True, L.D4, 0), lam ** 2 * ut, atol=1e-12)
+    assert np.allclose(L.difference(ut, True, L.D6, 0), lam ** 3 * ut, atol=1e-12)
+    assert np.allclose(L.difference(up, True, L.D6, 0), 0.0, atol=1e-12)
+    # the wrong sign rule (a velocity treated as a scalar) breaks it at the pole rows
+    assert not np.allclose(L.difference(ut, False, L.D6, 0), lam ** 3 * ut, atol=1e-6)
