@@ -143,12 +143,13 @@ VLBM_API int vlbm_diagnostics(vlbm_t *h, vlbm_diag *out);
 VLBM_API int vlbm_max_stable_dt(int n_theta, int n_phi, int velocity_set, double tau, int polar_filter,
                        double *out);
 
-/* Per-stage kernel time of the last vlbm_profile_step call, and the number of
- * kernels one step launches.  vlbm_profile_step runs n steps launching each
- * stage kernel individually between CUDA events on the handle's stream and
- * stores, in ms_per_stage[0..2], the mean device time of stage kernel 1, 2, 3
- * (ms_per_stage may be NULL).  Returns the launch count per step in *launches
- * (may be NULL). */
+/* Per-kernel time of the stages, and the number of kernels one step launches.
+ * vlbm_profile_step runs n steps launching each stage kernel and each polar
+ * filter individually between CUDA events on the handle's stream and stores,
+ * in ms_per_stage[0..2], the mean device time of stage kernel 1, 2, 3 and in
+ * ms_per_stage[3..5] that of the polar filter after stage 1, 2, 3 (0 when the
+ * filter is off); ms_per_stage (6 doubles) may be NULL.  Returns the launch
+ * count per step in *launches (may be NULL). */
 VLBM_API int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches);
 
 /* Bytes of device memory the handle holds. */

@@ -292,8 +292,10 @@ int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0)
     return VLBM_OK;
 }
 
-// Enqueues one RK3 step (all stages, filters, budget) on the handle's stream.
-void enqueue_step(vlbm_t *h, int stage_only = 0)
+// Enqueues one RK3 step (all stages, filters, budget) on the handle's stream.  With
+// stage_only = 1..3, only that stage; part 1 launches its stage kernel alone, part 2
+// its polar filter alone (part 0: both).
+void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
 {
     cudaStream_t s = h->stream;
     const size_t pole_per = (size_t)2 * NK * h->np;
@@ -318,12 +320,12 @@ void enqueue_step(vlbm_t *h, int stage_only = 0)
             p.eps = h->eps;
             p.stage = st;
             p.c = h->vd;
-            launch_stage_f64(p, s);
-            if (h->nfrows) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
+            if (part != 2) launch_stage_f64(p, s);
+            if (h->nfrows && part != 1) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         } else {
             const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
-            launch_stage_f32(tm, h->run, h->vc, st, h->ty, h->d_flags, s);
-            if (h->nfrows) launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
+            if (part != 2) launch_stage_f32(tm, h->run, h->vc, st, h->ty, h->d_flags, s);
+            if (h->nfrows && part != 1) launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         }
     }
     if (!stage_only && h->prec == VLBM_FP64)
@@ -704,22 +706,30 @@ int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches)
 {
     if (!h || n < 1) return fail(h, VLBM_ERR_ARG, "bad handle or step count");
     if (h->prec == VLBM_FP32 && !h->d_face) return fail(h, VLBM_ERR_ARG, "FP32 state not initialised");
-    double acc[3] = {0, 0, 0};
+    double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int q = 0; q < n; ++q) {
         for (int st = 1; st <= 3; ++st) {
             CK(h, cudaEventRecord(h->ev[0], h->stream));
-            enqueue_step(h, st);
+            enqueue_step(h, st, 1);
             CK(h, cudaEventRecord(h->ev[1], h->stream));
-            CK(h, cudaEventSynchronize(h->ev[1]));
-            float ms = 0.0f;
+            enqueue_step(h, st, 2);
+            CK(h, cudaEventRecord(h->ev[2], h->stream));
+            CK(h, cudaEventSynchronize(h->ev[2]));
+            float ms = 0.0f, mf = 0.0f;
             CK(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+            CK(h, cudaEventElapsedTime(&mf, h->ev[1], h->ev[2]));
             acc[st - 1] += ms;
+            acc[st + 2] += h->nfrows ? mf : 0.0f;
         }
+        // the step's pole budget (FP64), outside the timed launches
+        if (h->prec == VLBM_FP64)
+            launch_pole_budget(h->d_pole, h->np, h->R, 2.0 * M_PI / h->np, h->dt, h->d_budget, h->stream);
     }
+    CK(h, cudaGetLastError());
     h->steps += n;
     for (int st = 0; st < 3; ++st) h->prof_ms[st] = acc[st] / n;
     if (ms_per_stage)
-        for (int st = 0; st < 3; ++st) ms_per_stage[st] = h->prof_ms[st];
+        for (int k = 0; k < 6; ++k) ms_per_stage[k] = acc[k] / n;
     if (launches) *launches = kernels_per_step(h);
     return vlbm_sync(h);
 }

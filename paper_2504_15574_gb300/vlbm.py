@@ -194,10 +194,11 @@ def vlbm_max_stable_dt(n_theta, n_phi, tau, polar_filter=False, velocity_set=VLB
 
 
 def vlbm_profile_step(h, n):
-    ms = (ctypes.c_double * 3)()
+    """(stage kernel ms [3], polar filter ms [3], kernels per step)"""
+    ms = (ctypes.c_double * 6)()
     launches = ctypes.c_int()
     _check(load().vlbm_profile_step(h, int(n), ms, ctypes.byref(launches)), h)
-    return list(ms), launches.value
+    return list(ms[:3]), list(ms[3:]), launches.value
 
 
 def vlbm_device_bytes(h) -> int:
