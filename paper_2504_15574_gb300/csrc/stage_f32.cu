@@ -653,12 +653,9 @@ __device__ __forceinline__ void thread_block_means(f2 (&v)[FILT_COLS], int n, fl
     }
 }
 
-__global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const Layout L, const int *rows,
-                                                                   const int *blocks)
+// Filters row i (block size b) of pair plane q; called by all FILT_THREADS threads of a CTA.
+__device__ __forceinline__ void filter_row_f32(f2 *f, const Layout &L, int i, int b, int q)
 {
-    const int i = rows[blockIdx.x];
-    const int b = blocks[blockIdx.x];
-    const int q = blockIdx.y;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const float inv_b = 1.0f / (float)b;   // exact: b is a power of two
     __shared__ FF wpart[FILT_THREADS / 32];
@@ -748,6 +745,23 @@ __global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const L
         const f2 mean = ff_mean(a, inv_b);
         for (int c = t; c < b; c += FILT_THREADS) store_images(f, L, q, i, blk * b + c, mean);
     }
+}
+
+// One CTA per (filtered row, pair plane) of one run.
+__global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const Layout L, const int *rows,
+                                                                   const int *blocks)
+{
+    filter_row_f32(f, L, rows[blockIdx.x], blocks[blockIdx.x], blockIdx.y);
+}
+
+// One CTA per (run, filtered row) item of a batch and pair plane: the row of the
+// run's output array of `stage`.
+__global__ void __launch_bounds__(FILT_THREADS) batch_filter_f32_kernel(const RunF *runs, const int4 *items, int stage)
+{
+    const int4 it = items[blockIdx.x];   // (run, row, block size, unused)
+    const RunF &R = runs[it.x];
+    f2 *out = (stage == 1) ? R.A : (stage == 2) ? R.B : R.F;
+    filter_row_f32(out, R.L, it.y, it.z, blockIdx.y);
 }
 
 constexpr int DIAG_THREADS = 256;
@@ -873,6 +887,12 @@ void launch_fill_ghosts_f32(float2 *f, const Layout &L, cudaStream_t s)
 {
     dim3 grid((L.np + 2 * GC + 127) / 128, L.nt + 2 * GR, NP2);
     fill_ghosts_f32_kernel<<<grid, 128, 0, s>>>(f, L);
+}
+
+void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int stage, cudaStream_t s)
+{
+    if (nitems <= 0) return;
+    batch_filter_f32_kernel<<<dim3(nitems, NP2), FILT_THREADS, 0, s>>>(runs, items, stage);
 }
 
 void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s)

@@ -766,6 +766,8 @@ struct vlbm_batch {
     CUtensorMap *d_tms = nullptr;
     int2 *d_work = nullptr;
     int ntiles = 0;
+    int4 *d_fitems = nullptr;   // polar filter: (run, row, block size, 0) of every filtered row
+    int nfitems = 0;
     bool dirty = true;
     int guard = 1;
     VelC vc{};
@@ -829,6 +831,22 @@ int batch_refresh(vlbm_batch_t *b)
         b->vc = h->vc;
     }
     b->ntiles = (int)work.size();
+    std::vector<int4> fitems;
+    for (int r = 0; r < nr; ++r) {
+        const vlbm_t *h = b->runs[r];
+        if (!h->filter) continue;
+        for (int i = 0; i < h->nt; ++i) {
+            const int bs = filter_block(h->nt, h->np, h->sin_t[i]);
+            if (bs > 1) fitems.push_back(make_int4(r, i, bs, 0));
+        }
+    }
+    b->nfitems = (int)fitems.size();
+    if (b->d_fitems) cudaFree(b->d_fitems);
+    b->d_fitems = nullptr;
+    if (b->nfitems) {
+        BCK(b, cudaMalloc(&b->d_fitems, sizeof(int4) * fitems.size()));
+        BCK(b, cudaMemcpy(b->d_fitems, fitems.data(), sizeof(int4) * fitems.size(), cudaMemcpyHostToDevice));
+    }
     if (!b->d_runs) BCK(b, cudaMalloc(&b->d_runs, sizeof(RunF) * nr));
     if (!b->d_tms) BCK(b, cudaMalloc(&b->d_tms, sizeof(CUtensorMap) * 3 * nr));
     if (b->d_work) cudaFree(b->d_work);
@@ -852,11 +870,8 @@ void batch_enqueue_step(vlbm_batch_t *b)
     const int ctas = batch_ctas(b);
     for (int st = 1; st <= 3; ++st) {
         launch_batch_stage_f32(b->d_runs, b->d_tms, b->d_work, b->ntiles, b->vc, st, b->ty, ctas, b->d_flags, b->stream);
-        for (vlbm_t *h : b->runs) {
-            if (!h->nfrows) continue;
-            void *out = (st == 1) ? h->A : (st == 2) ? h->B : h->F;
-            launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, b->stream);
-        }
+        // one polar-filter launch over the filtered rows of every run
+        launch_batch_filter_f32(b->d_runs, b->d_fitems, b->nfitems, st, b->stream);
     }
 }
 
@@ -1088,10 +1103,7 @@ int vlbm_batch_profile(vlbm_batch_t *b, int n, double *ms_per_step, int *launche
     BCK(b, cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
     if (ms_per_step) *ms_per_step = ms / n;
     if (launches_per_step) {
-        int l = 3;
-        for (vlbm_t *h : b->runs)
-            if (h->nfrows) l += 3;
-        *launches_per_step = l;
+        *launches_per_step = 3 + (b->nfitems ? 3 : 0);
     }
     return vlbm_batch_sync(b);
 }
@@ -1163,6 +1175,7 @@ void vlbm_batch_destroy(vlbm_batch_t *b)
     if (b->d_runs) cudaFree(b->d_runs);
     if (b->d_tms) cudaFree(b->d_tms);
     if (b->d_work) cudaFree(b->d_work);
+    if (b->d_fitems) cudaFree(b->d_fitems);
     if (b->d_flags) cudaFree(b->d_flags);
     if (b->h_flags) cudaFreeHost(b->h_flags);
     for (int q = 0; q < 2; ++q)

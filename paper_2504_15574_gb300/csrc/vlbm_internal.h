@@ -109,6 +109,8 @@ void launch_unpack_f32(const double *dense, const Layout &L, float2 *f, const Ve
                        const double *sin_t, cudaStream_t s);
 void launch_fill_ghosts_f32(float2 *f, const Layout &L, cudaStream_t s);
 void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s);
+// Polar filter of every (run, row, block size) item of a batch on the output array of `stage`.
+void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int stage, cudaStream_t s);
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,
                             const VelD &c, double area, double rho_ref, double *part, double *out, cudaStream_t s);
 

@@ -35,10 +35,10 @@ def _batch(V, **kw):
     return b, dts
 
 
-def _singles(V, dts, steps):
+def _singles(V, dts, steps, **kw):
     out = []
     for r, (nt, np_) in enumerate(GRIDS):
-        s = V.Solver(nt, np_, TAU, dts[r], precision="fp32")
+        s = V.Solver(nt, np_, TAU, dts[r], precision="fp32", **kw)
         s.init_moments(*inputs.gaussian_vortices(nt, np_, run=100 + r))
         s.step(steps)
         out.append(s.moments())
@@ -56,6 +56,21 @@ def test_batch_members_equal_standalone_solvers_bitwise(V, schedule):
         got = b.moments(r)
         for x, y in zip(got, ref[r]):
             assert np.array_equal(x, y), (r, schedule)
+    b.close()
+
+
+def test_batch_with_polar_filter_equals_standalone_solvers_bitwise(V):
+    """One batched filter launch per stage over the filtered rows of every run gives each
+    member the state of a standalone solver with its own filter launches."""
+    b, dts = _batch(V, polar_filter=True)
+    b.set_schedule(8, 0)
+    b.step(20)
+    ref = _singles(V, dts, 20, polar_filter=True)
+    for r in range(len(GRIDS)):
+        for x, y in zip(b.moments(r), ref[r]):
+            assert np.array_equal(x, y), r
+    ms, launches = b.profile(2)
+    assert launches == 6
     b.close()
 
 
