@@ -248,6 +248,12 @@ VLBM_API int vlbm_lc_train_step(vlbm_lc_t *lc, const double *inputs, const doubl
  * forward pass, drho with its area mean removed (mass is kept), then
  * f += f^eq(rho + drho, u + du) - f^eq(rho, u) (Eq. feq_Q=4).  Device-resident. */
 VLBM_API int vlbm_lc_apply(vlbm_lc_t *lc, vlbm_t *h);
+/* Learned-coarse rollout: `steps` times (one RK3 step of h, then the correction of
+ * vlbm_lc_apply), enqueued on the solver's stream as a captured CUDA graph (built on
+ * the first call for this solver; rebuilt after vlbm_lc_set_scales or for another
+ * solver) with no host synchronisation between steps; returns after the last step
+ * with the solver's status (vlbm_sync).  h must be FP32 on the network's grid. */
+VLBM_API int vlbm_lc_rollout(vlbm_lc_t *lc, vlbm_t *h, int steps);
 VLBM_API const char *vlbm_lc_last_error(const vlbm_lc_t *lc);
 VLBM_API void vlbm_lc_destroy(vlbm_lc_t *lc);
 

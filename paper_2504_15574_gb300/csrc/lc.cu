@@ -51,29 +51,25 @@ __device__ __forceinline__ void mma_bf16(float d[4], const unsigned a[4], const 
 }
 
 // ---- padding and its adjoint ------------------------------------------------------
-// X [H][W][C] -> Xp [H+2][W+2][C]; ghost rows take the mirrored row at column + W/2,
-// with the channels in `negmask` negated; ghost columns wrap.
-__global__ void pad_kernel(const __nv_bfloat16 *X, int H, int W, int C, unsigned negmask, __nv_bfloat16 *Xp)
+// A padded tensor Xp [H+2][W+2][C] holds X [H][W][C] at (y+1, x+1); its ghost columns
+// wrap in phi and its ghost rows are the first/last row on the opposite meridian
+// (column + W/2), with the channels in a sign mask negated (the pole condition of
+// Sec. 3.6 applied to moments).  Producers write every value at all its positions:
+
+// calls put(padded row, padded column, pole image?) for every position of interior (y, x)
+template <class Put>
+__device__ __forceinline__ void for_padded_positions(int H, int W, int y, int x, Put put)
 {
-    const int c = threadIdx.x;           // blockDim.x = C
-    const int xp = blockIdx.x, yp = blockIdx.y;
-    if (c >= C) return;
-    int y = yp - 1, x = xp - 1;
-    bool flip = false;
-    if (y < 0) {
-        y = 0;
-        x += W / 2;
-        flip = true;
-    } else if (y >= H) {
-        y = H - 1;
-        x += W / 2;
-        flip = true;
+    put(y + 1, x + 1, false);
+    if (x == W - 1) put(y + 1, 0, false);
+    if (x == 0) put(y + 1, W + 1, false);
+    for (int side = 0; side < 2; ++side) {
+        if ((side == 0 && y != 0) || (side == 1 && y != H - 1)) continue;
+        const int r = side ? H + 1 : 0;
+        put(r, (x - W / 2 + W) % W + 1, true);
+        if (x == (W / 2 + W - 1) % W) put(r, 0, true);
+        if (x == W / 2 % W) put(r, W + 1, true);
     }
-    x %= W;
-    if (x < 0) x += W;
-    __nv_bfloat16 v = X[((size_t)y * W + x) * C + c];
-    if (flip && ((negmask >> c) & 1u)) v = __hneg(v);
-    Xp[((size_t)yp * (W + 2) + xp) * C + c] = v;
 }
 
 // adjoint of pad_kernel: dX[y][x] = dXp[y+1][x+1] + ghost copies that read (y, x)
@@ -112,7 +108,7 @@ constexpr int CONV_PIX = 64;
 template <int CI, int CO>
 __global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16 *Xp, int Hp, int Wp,
                                                        const __nv_bfloat16 *Wt, const float *bias, float *Yf,
-                                                       __nv_bfloat16 *Yb, int relu)
+                                                       __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu)
 {
     constexpr int XS = CI + 8;           // padded channel stride in shared memory (bank spread)
     constexpr int WS = 9 * CI + 8;
@@ -121,13 +117,19 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16 *Xp, i
     const int Ho = Hp - 2, Wo = Wp - 2;
     const int y = blockIdx.y, x0 = blockIdx.x * CONV_PIX;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // stage the input rows y..y+2, columns x0..x0+65 (zero beyond Wp) and the weights
-    for (int e = tid; e < 3 * (CONV_PIX + 2) * CI; e += blockDim.x) {
-        const int c = e % CI, rest = e / CI, xx = rest % (CONV_PIX + 2), r = rest / (CONV_PIX + 2);
+    // stage the input rows y..y+2, columns x0..x0+65 (zero beyond Wp) and the weights, 16 bytes
+    // (8 channels) per access: CI, XS and WS are multiples of 8
+    constexpr int CV = CI / 8;
+    for (int e = tid; e < 3 * (CONV_PIX + 2) * CV; e += blockDim.x) {
+        const int cv = e % CV, rest = e / CV, xx = rest % (CONV_PIX + 2), r = rest / (CONV_PIX + 2);
         const int gx = x0 + xx;
-        xs[r][xx][c] = (gx < Wp) ? Xp[((size_t)(y + r) * Wp + gx) * CI + c] : __float2bfloat16(0.0f);
+        const uint4 v = (gx < Wp) ? *reinterpret_cast<const uint4 *>(Xp + ((size_t)(y + r) * Wp + gx) * CI + 8 * cv)
+                                  : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(&xs[r][xx][8 * cv]) = v;
     }
-    for (int e = tid; e < CO * 9 * CI; e += blockDim.x) ws[e / (9 * CI)][e % (9 * CI)] = Wt[e];
+    constexpr int WV = 9 * CI / 8;
+    for (int e = tid; e < CO * WV; e += blockDim.x)
+        *reinterpret_cast<uint4 *>(&ws[e / WV][8 * (e % WV)]) = *reinterpret_cast<const uint4 *>(Wt + 8 * e);
     __syncthreads();
 
     const int g = lane >> 2, t = lane & 3;
@@ -165,17 +167,26 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16 *Xp, i
         const size_t o = ((size_t)y * Wo + x) * CO;
 #pragma unroll
         for (int nb = 0; nb < CO / 8; ++nb) {
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int co = nb * 8 + 2 * t + u;
-                float v = acc[nb][2 * half + u] + (bias ? bias[co] : 0.0f);
-                if (Yf) Yf[o + co] = v;
-                if (relu) v = fmaxf(v, 0.0f);
-                if (Yb) Yb[o + co] = __float2bfloat16(v);
+            const int co = nb * 8 + 2 * t;
+            float v0 = acc[nb][2 * half] + (bias ? bias[co] : 0.0f);
+            float v1 = acc[nb][2 * half + 1] + (bias ? bias[co + 1] : 0.0f);
+            if (Yf) {
+                Yf[o + co] = v0;
+                Yf[o + co + 1] = v1;
             }
+            if (relu) {
+                v0 = fmaxf(v0, 0.0f);
+                v1 = fmaxf(v1, 0.0f);
+            }
+            const __nv_bfloat162 pr = __floats2bfloat162_rn(v0, v1);
+            if (Yb) *reinterpret_cast<__nv_bfloat162 *>(Yb + o + co) = pr;
+            // hidden activations carry no sign flip across the poles
+            if (Ypad)
+                for_padded_positions(Ho, Wo, y, x, [&](int prow, int pcol, bool) {
+                    *reinterpret_cast<__nv_bfloat162 *>(Ypad + ((size_t)prow * (Wo + 2) + pcol) * CO + co) = pr;
+                });
         }
     }
-    (void)Ho;
 }
 
 // ---- weight gradient on the tensor cores ---------------------------------------------
@@ -427,7 +438,7 @@ __device__ __forceinline__ void lc_differences(const double *a, int H, int W, in
 // scheme's truncation error); the latitude channels let the translation-equivariant
 // convolutions depend on theta.
 __global__ void features_kernel(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                                const double *sin_t, const double *cos_t, const LcInScale sc, __nv_bfloat16 *X0)
+                                const double *sin_t, const double *cos_t, const LcInScale sc, __nv_bfloat16 *Xp)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= H * W) return;
@@ -462,8 +473,19 @@ __global__ void features_kernel(const double *rho, const double *ut, const doubl
     }
     v[4] = (float)cos_t[r];
     v[5] = (float)sin_t[r];
+    // the padded input of layer 0 at all positions of (r, c); pole images negate LC_NEGMASK
+    uint4 plain[2], image[2];
+    __nv_bfloat16 *pb = reinterpret_cast<__nv_bfloat16 *>(plain), *ib = reinterpret_cast<__nv_bfloat16 *>(image);
 #pragma unroll
-    for (int q = 0; q < LC_CIN; ++q) X0[(size_t)i * LC_CIN + q] = __float2bfloat16(v[q]);
+    for (int q = 0; q < LC_CIN; ++q) {
+        pb[q] = __float2bfloat16(v[q]);
+        ib[q] = ((LC_NEGMASK >> q) & 1u) ? __hneg(pb[q]) : pb[q];
+    }
+    for_padded_positions(H, W, r, c, [&](int pr, int pc, bool img) {
+        uint4 *dst = reinterpret_cast<uint4 *>(Xp + ((size_t)pr * (W + 2) + pc) * LC_CIN);
+        dst[0] = img ? image[0] : plain[0];
+        dst[1] = img ? image[1] : plain[1];
+    });
 }
 
 // output [H][W][CO] -> (drho, dut, dup) [3][H][W] in physical units, and sin-weighted drho partial sums
@@ -489,14 +511,53 @@ __global__ void outputs_kernel(const float *Y, int CO, int H, int W, float3 scal
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-__device__ __forceinline__ double feq_lc(double n, double wk, double va, double vb, double ut, double up)
+// Moments (rho, u^theta, u^phi, T) of the FP32 pair layout (dg = s (f - w rho_ref)) in FP32
+// arithmetic on the deviations: n = rho_ref + sum dg / s, j = sum v dg / s (the reference
+// state carries no momentum), and T - 1 = (rho_ref |u|^2 + sum df |v - u|^2 - 2 dn) / (2 n),
+// using sum_k w_k |v_k|^2 = 2 (T0 = 1); stored as FP64 for the feature kernel.
+__global__ void lc_moments_kernel(const float2 *f, const Layout L, const VelD c, double rho_ref,
+                                  const double *sin_t, double *mom)
 {
-    const double xi = va * ut + vb * up;
-    const double u2 = ut * ut + up * up;
-    return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= L.np) return;
+    const float inv_s = (float)(1.0 / sin_t[i]);
+    float2 g[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) g[q] = f[L.at(q, i, j)];
+    float dn = 0.0f, jt = 0.0f, jp = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int gq = q >> 2, b = q & 3;
+        const float va0 = (float)c.v[2 * gq], va1 = (float)c.v[2 * gq + 1], vb = (float)c.v[b];
+        dn += g[q].x + g[q].y;
+        jt += va0 * g[q].x + va1 * g[q].y;
+        jp += vb * (g[q].x + g[q].y);
+    }
+    dn *= inv_s;
+    const float n = (float)rho_ref + dn;
+    const float ut = jt * inv_s / n, up = jp * inv_s / n;
+    float e = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int gq = q >> 2, b = q & 3;
+        const float va0 = (float)c.v[2 * gq] - ut, va1 = (float)c.v[2 * gq + 1] - ut, vb = (float)c.v[b] - up;
+        e += g[q].x * (va0 * va0 + vb * vb) + g[q].y * (va1 * va1 + vb * vb);
+    }
+    e *= inv_s;
+    const float tm1 = ((float)rho_ref * (ut * ut + up * up) + e - 2.0f * dn) / (2.0f * n);
+    const size_t HW = (size_t)L.nt * L.np, cell = (size_t)i * L.np + j;
+    mom[cell] = (double)n;
+    mom[HW + cell] = (double)ut;
+    mom[2 * HW + cell] = (double)up;
+    mom[3 * HW + cell] = 1.0 + (double)tm1;
 }
 
-// f += feq(rho + drho - mean, u + du) - feq(rho, u), on the FP32 pair layout (dg = s (f - w rho_ref))
+// f += feq(rho + drho - mean, u + du) - feq(rho, u) on the FP32 pair layout, the equilibrium
+// difference written in differences (FP32 keeps the relative precision of a small correction):
+// with P(xi, u^2) = 1 + xi + (xi^2 - u^2)/2 + xi (xi^2 - 3 u^2)/6 (Eq. feq_Q=4 over n w),
+// feq' - feq = w [ (rho' - rho) P' + rho (P' - P) ] and P' - P expanded in dxi = v . du and
+// d(u^2) = du . (2u + du).
 __global__ void nudge_kernel(float2 *f, const Layout L, const double *mom, const double *delta, const double *mean,
                              double wsum, const VelD c, const double *sin_t)
 {
@@ -504,29 +565,39 @@ __global__ void nudge_kernel(float2 *f, const Layout L, const double *mom, const
     const int i = blockIdx.y;
     if (j >= L.np) return;
     const size_t n = (size_t)L.nt * L.np, cell = (size_t)i * L.np + j;
-    const double rho = mom[cell], ut = mom[n + cell], up = mom[2 * n + cell];
-    const double r2 = rho + delta[cell] - (*mean) / wsum, u2t = ut + delta[n + cell], u2p = up + delta[2 * n + cell];
-    const double s = sin_t[i];
+    const float rho = (float)mom[cell], ut = (float)mom[n + cell], up = (float)mom[2 * n + cell];
+    const float drho = (float)(delta[cell] - (*mean) / wsum), dut = (float)delta[n + cell],
+                dup = (float)delta[2 * n + cell];
+    const float ut2 = ut + dut, up2 = up + dup;
+    const float usq = ut * ut + up * up, usq2 = ut2 * ut2 + up2 * up2;
+    const float dusq = dut * (ut + ut2) + dup * (up + up2);
+    const float s = (float)sin_t[i];
     for (int q = 0; q < 8; ++q) {
         const int g = q >> 2, b = q & 3;
         float2 v = f[L.at(q, i, j)];
-        const int a0 = 2 * g, a1 = 2 * g + 1;
-        const double d0 = feq_lc(r2, c.w[a0] * c.w[b], c.v[a0], c.v[b], u2t, u2p) -
-                          feq_lc(rho, c.w[a0] * c.w[b], c.v[a0], c.v[b], ut, up);
-        const double d1 = feq_lc(r2, c.w[a1] * c.w[b], c.v[a1], c.v[b], u2t, u2p) -
-                          feq_lc(rho, c.w[a1] * c.w[b], c.v[a1], c.v[b], ut, up);
-        v.x = (float)((double)v.x + s * d0);
-        v.y = (float)((double)v.y + s * d1);
+        float d[2];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int a = 2 * g + m;
+            const float va = (float)c.v[a], vb = (float)c.v[b], w = (float)(c.w[a] * c.w[b]);
+            const float xi = va * ut + vb * up, dxi = va * dut + vb * dup, xi2 = xi + dxi;
+            const float P2 = 1.0f + xi2 + 0.5f * (xi2 * xi2 - usq2) + xi2 * (xi2 * xi2 - 3.0f * usq2) / 6.0f;
+            const float dP = dxi + 0.5f * (dxi * (xi + xi2) - dusq) +
+                             (dxi * (xi2 * xi2 + xi2 * xi + xi * xi) - 3.0f * (dxi * usq2 + xi * dusq)) / 6.0f;
+            d[m] = w * (drho * P2 + rho * dP);
+        }
+        v.x += s * d[0];
+        v.y += s * d[1];
         f[L.at(q, i, j)] = v;
     }
 }
 
 template <int CI, int CO>
 void conv_launch(const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias, float *Yf,
-                 __nv_bfloat16 *Yb, int relu, cudaStream_t s)
+                 __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s)
 {
     dim3 grid((Wp - 2 + CONV_PIX - 1) / CONV_PIX, Hp - 2);
-    conv3x3_kernel<CI, CO><<<grid, 128, 0, s>>>(Xp, Hp, Wp, Wt, bias, Yf, Yb, relu);
+    conv3x3_kernel<CI, CO><<<grid, 128, 0, s>>>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu);
 }
 
 template <int CI, int CO>
@@ -541,18 +612,18 @@ void wgrad_launch(const __nv_bfloat16 *dY, const __nv_bfloat16 *Xp, int H, int W
 // ---- the network ----------------------------------------------------------------------
 // Layer l: CI_l -> CO_l; padded channel counts: input 16 (4 used), hidden 32, output 8 (3 used).
 void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
-             float *Yf, __nv_bfloat16 *Yb, int relu, cudaStream_t s)
+             float *Yf, __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s)
 {
-    if (layer == 0) conv_launch<LC_CIN, LC_HID>(Xp, Hp, Wp, Wt, bias, Yf, Yb, relu, s);
-    else if (layer < LC_LAYERS - 1) conv_launch<LC_HID, LC_HID>(Xp, Hp, Wp, Wt, bias, Yf, Yb, relu, s);
-    else conv_launch<LC_HID, LC_COUT>(Xp, Hp, Wp, Wt, bias, Yf, Yb, relu, s);
+    if (layer == 0) conv_launch<LC_CIN, LC_HID>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu, s);
+    else if (layer < LC_LAYERS - 1) conv_launch<LC_HID, LC_HID>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu, s);
+    else conv_launch<LC_HID, LC_COUT>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu, s);
 }
 
 // backward-data convolution of layer l >= 1: input dP [H+4][W+4][COp2], output dXp [H+2][W+2][CI_l]
 void lc_conv_bwd(int layer, const __nv_bfloat16 *dP, int H, int W, const __nv_bfloat16 *Wb, float *dXp, cudaStream_t s)
 {
-    if (layer < LC_LAYERS - 1) conv_launch<LC_HID, LC_HID>(dP, H + 4, W + 4, Wb, nullptr, dXp, nullptr, 0, s);
-    else conv_launch<LC_COUTP2, LC_HID>(dP, H + 4, W + 4, Wb, nullptr, dXp, nullptr, 0, s);
+    if (layer < LC_LAYERS - 1) conv_launch<LC_HID, LC_HID>(dP, H + 4, W + 4, Wb, nullptr, dXp, nullptr, nullptr, 0, s);
+    else conv_launch<LC_COUTP2, LC_HID>(dP, H + 4, W + 4, Wb, nullptr, dXp, nullptr, nullptr, 0, s);
 }
 
 void lc_wgrad(int layer, const __nv_bfloat16 *dPre, const __nv_bfloat16 *Xp, int H, int W, float *part, float *partb,
@@ -561,11 +632,6 @@ void lc_wgrad(int layer, const __nv_bfloat16 *dPre, const __nv_bfloat16 *Xp, int
     if (layer == 0) wgrad_launch<LC_CIN, LC_HID>(dPre, Xp, H, W, part, partb, s);
     else if (layer < LC_LAYERS - 1) wgrad_launch<LC_HID, LC_HID>(dPre, Xp, H, W, part, partb, s);
     else wgrad_launch<LC_HID, LC_COUTP2>(dPre, Xp, H, W, part, partb, s);
-}
-
-void lc_pad(const __nv_bfloat16 *X, int H, int W, int C, unsigned negmask, __nv_bfloat16 *Xp, cudaStream_t s)
-{
-    pad_kernel<<<dim3(W + 2, H + 2), C, 0, s>>>(X, H, W, C, negmask, Xp);
 }
 
 void lc_unpad(const float *dXp, int H, int W, int C, unsigned negmask, float *dX, cudaStream_t s)
@@ -617,10 +683,10 @@ void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g
 }
 
 void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                 const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *X0,
+                 const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *Xp,
                  cudaStream_t s)
 {
-    features_kernel<<<(H * W + 255) / 256, 256, 0, s>>>(rho, ut, up, T, H, W, sin_t, cos_t, inv_scale, X0);
+    features_kernel<<<(H * W + 255) / 256, 256, 0, s>>>(rho, ut, up, T, H, W, sin_t, cos_t, inv_scale, Xp);
 }
 
 void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
@@ -629,6 +695,13 @@ void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double
     const int nb = (H * W + 255) / 256;
     outputs_kernel<<<nb, 256, 0, s>>>(Y, CO, H, W, scale, sin_t, out, part);
     sum_kernel<<<1, 256, 0, s>>>(part, nb, mean);
+}
+
+void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref, const double *sin_t, double *mom,
+                cudaStream_t s)
+{
+    dim3 grid((L.np + 127) / 128, L.nt);
+    lc_moments_kernel<<<grid, 128, 0, s>>>(f, L, c, rho_ref, sin_t, mom);
 }
 
 void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,

@@ -27,7 +27,7 @@ struct vlbm_lc {
     float *d_w = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
     __nv_bfloat16 *d_wf[LC_LAYERS] = {}, *d_wb[LC_LAYERS] = {};
     double *d_sin = nullptr, *d_cos = nullptr, *d_in = nullptr, *d_tg = nullptr, *d_out = nullptr, *d_part = nullptr, *d_scal = nullptr;
-    __nv_bfloat16 *d_x0 = nullptr, *d_xp[LC_LAYERS] = {}, *d_z[LC_LAYERS] = {};
+    __nv_bfloat16 *d_xp[LC_LAYERS] = {}, *d_z[LC_LAYERS] = {};
     float *d_y = nullptr, *d_dy = nullptr, *d_dxp = nullptr, *d_dx = nullptr;
     __nv_bfloat16 *d_dp = nullptr, *d_dpre = nullptr;
     float *d_wpart = nullptr, *d_bpart = nullptr, *d_g9 = nullptr;
@@ -37,6 +37,8 @@ struct vlbm_lc {
     float out_scale[3] = {1e-5f, 1e-4f, 1e-4f};
     long long t = 0;
     std::vector<void *> bufs;
+    cudaGraphExec_t g_exec = nullptr;   // vlbm_lc_rollout: one corrected step of solver g_solver
+    vlbm_t *g_solver = nullptr;
 };
 
 namespace {
@@ -81,21 +83,20 @@ int refresh_bf16(vlbm_lc_t *n)
     return VLBM_OK;
 }
 
-// forward pass on inputs already in d_in ([4][H][W], physical units); output in d_y
-int forward(vlbm_lc_t *n)
+// forward pass on the moments in4 ([4][H][W] device, physical units), on stream s; output in d_y.
+// keep: also store each hidden layer's unpadded activations (d_z) for the backward pass.
+int forward(vlbm_lc_t *n, const double *in4, cudaStream_t s, bool keep = true)
 {
     const int H = n->H, W = n->W, HW = H * W;
     LcInScale is;
     for (int q = 0; q < LC_NSCALE; ++q) is.inv[q] = 1.0f / n->in_scale[q];
-    lc_features(n->d_in, n->d_in + HW, n->d_in + 2 * (size_t)HW, n->d_in + 3 * (size_t)HW, H, W, n->d_sin, n->d_cos,
-                is, n->d_x0, n->stream);
-    // the input layer's velocity channels, their differences and sin(theta) change sign across a pole
-    lc_pad(n->d_x0, H, W, LC_CIN, LC_NEGMASK, n->d_xp[0], n->stream);
+    // the padded input of layer 0 (velocity channels, their differences and sin(theta) change
+    // sign across a pole); each hidden layer writes the next layer's padded input itself
+    lc_features(in4, in4 + HW, in4 + 2 * (size_t)HW, in4 + 3 * (size_t)HW, H, W, n->d_sin, n->d_cos, is, n->d_xp[0], s);
     for (int l = 0; l < LC_LAYERS; ++l) {
         const bool last = (l == LC_LAYERS - 1);
         lc_conv(l, n->d_xp[l], H + 2, W + 2, n->d_wf[l], n->d_w + n->boff[l], last ? n->d_y : nullptr,
-                last ? nullptr : n->d_z[l], last ? 0 : 1, n->stream);
-        if (!last) lc_pad(n->d_z[l], H, W, LC_HID, 0u, n->d_xp[l + 1], n->stream);
+                (last || !keep) ? nullptr : n->d_z[l], last ? nullptr : n->d_xp[l + 1], last ? 0 : 1, s);
     }
     LCK(n, cudaGetLastError());
     return VLBM_OK;
@@ -123,6 +124,29 @@ int backward(vlbm_lc_t *n)
         lc_conv_bwd(l, n->d_dp, H, W, n->d_wb[l], n->d_dxp, n->stream);
         lc_unpad(n->d_dxp, H, W, LC_HID, 0u, n->d_dy, n->stream);      // gradient at the output of layer l-1
     }
+    LCK(n, cudaGetLastError());
+    return VLBM_OK;
+}
+
+int check_solver(vlbm_lc_t *n, vlbm_t *h)
+{
+    if (!n || !h) return VLBM_ERR_ARG;
+    if (h->prec != VLBM_FP32 || h->nt != n->H || h->np != n->W)
+        return lfail(n, VLBM_ERR_ARG, "the solver must be FP32 on the network's grid");
+    return VLBM_OK;
+}
+
+// The correction of solver h's current state, enqueued on stream s without host
+// synchronisation: moments, forward pass, outputs (drho area mean), nudge, ghost fill.
+int enqueue_correction(vlbm_lc_t *n, vlbm_t *h, cudaStream_t s)
+{
+    lc_moments((const float2 *)h->F, h->L, h->vd, h->rho_ref, h->d_sin_t, h->d_mom, s);
+    int rc;
+    if ((rc = forward(n, h->d_mom, s, false))) return rc;
+    const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
+    lc_outputs(n->d_y, LC_COUT, n->H, n->W, sc, n->d_sin, n->d_out, n->d_part, n->d_scal + 1, s);
+    lc_nudge((float2 *)h->F, h->L, h->d_mom, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, s);
+    launch_fill_ghosts_f32((float2 *)h->F, h->L, s);
     LCK(n, cudaGetLastError());
     return VLBM_OK;
 }
@@ -197,7 +221,6 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
     A(&n->d_out, 3 * HW);
     A(&n->d_part, HW / 256 + 2);
     A(&n->d_scal, 4);
-    A(&n->d_x0, HW * LC_CIN);
     A(&n->d_y, HW * LC_COUT);
     A(&n->d_dy, HW * LC_HID);
     A(&n->d_dxp, HWp * LC_HID);
@@ -262,6 +285,10 @@ int vlbm_lc_set_scales(vlbm_lc_t *n, const double *in_scale, const double *out_s
     for (int q = 0; q < 3; ++q)
         if (!(out_scale[q] > 0.0)) return lfail(n, VLBM_ERR_ARG, "scales must be > 0");
     for (int q = 0; q < LC_NSCALE; ++q) n->in_scale[q] = (float)in_scale[q];
+    if (n->g_exec) {   // the scales are kernel arguments of the captured rollout step
+        cudaGraphExecDestroy(n->g_exec);
+        n->g_exec = nullptr;
+    }
     for (int q = 0; q < 3; ++q) n->out_scale[q] = (float)out_scale[q];
     return VLBM_OK;
 }
@@ -270,7 +297,7 @@ int vlbm_lc_predict(vlbm_lc_t *n, const double *inputs, double *outputs)
 {
     if (!n || !inputs || !outputs) return VLBM_ERR_ARG;
     int rc;
-    if ((rc = upload_io(n, inputs, nullptr)) || (rc = forward(n))) return rc;
+    if ((rc = upload_io(n, inputs, nullptr)) || (rc = forward(n, n->d_in, n->stream))) return rc;
     const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
     lc_outputs(n->d_y, LC_COUT, n->H, n->W, sc, n->d_sin, n->d_out, n->d_part, n->d_scal + 1, n->stream);
     LCK(n, cudaMemcpyAsync(outputs, n->d_out, sizeof(double) * 3 * n->H * n->W, cudaMemcpyDeviceToHost, n->stream));
@@ -282,7 +309,7 @@ int vlbm_lc_gradients(vlbm_lc_t *n, const double *inputs, const double *targets,
 {
     if (!n || !inputs || !targets) return VLBM_ERR_ARG;
     int rc;
-    if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n)) || (rc = backward(n))) return rc;
+    if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n, n->d_in, n->stream)) || (rc = backward(n))) return rc;
     if (loss) LCK(n, cudaMemcpyAsync(loss, n->d_scal, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
     if (grad) LCK(n, cudaMemcpyAsync(grad, n->d_g, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost, n->stream));
     LCK(n, cudaStreamSynchronize(n->stream));
@@ -293,7 +320,7 @@ int vlbm_lc_train_step(vlbm_lc_t *n, const double *inputs, const double *targets
 {
     if (!n || !inputs || !targets || !(lr > 0.0f)) return VLBM_ERR_ARG;
     int rc;
-    if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n)) || (rc = backward(n))) return rc;
+    if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n, n->d_in, n->stream)) || (rc = backward(n))) return rc;
     n->t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - std::pow(b1, (float)n->t), c2 = 1.0f - std::pow(b2, (float)n->t);
@@ -306,23 +333,43 @@ int vlbm_lc_train_step(vlbm_lc_t *n, const double *inputs, const double *targets
 
 int vlbm_lc_apply(vlbm_lc_t *n, vlbm_t *h)
 {
-    if (!n || !h) return VLBM_ERR_ARG;
-    if (h->prec != VLBM_FP32 || h->nt != n->H || h->np != n->W)
-        return lfail(n, VLBM_ERR_ARG, "the solver must be FP32 on the network's grid");
-    const size_t HW = (size_t)n->H * n->W;
-    // moments of the solver's current state, on the solver's stream, then the network on its stream
-    launch_moments_f32((const float2 *)h->F, h->L, h->d_mom, h->d_mom + HW, h->d_mom + 2 * HW, h->d_mom + 3 * HW, h->vd,
-                       h->rho_ref, h->d_sin_t, h->stream);
-    LCK(n, cudaMemcpyAsync(n->d_in, h->d_mom, 4 * HW * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    LCK(n, cudaStreamSynchronize(h->stream));
     int rc;
-    if ((rc = forward(n))) return rc;
-    const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
-    lc_outputs(n->d_y, LC_COUT, n->H, n->W, sc, n->d_sin, n->d_out, n->d_part, n->d_scal + 1, n->stream);
-    lc_nudge((float2 *)h->F, h->L, n->d_in, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, n->stream);
-    launch_fill_ghosts_f32((float2 *)h->F, h->L, n->stream);
-    LCK(n, cudaGetLastError());
-    LCK(n, cudaStreamSynchronize(n->stream));
+    if ((rc = check_solver(n, h)) || (rc = enqueue_correction(n, h, h->stream))) return rc;
+    LCK(n, cudaStreamSynchronize(h->stream));
+    return VLBM_OK;
+}
+
+int vlbm_lc_rollout(vlbm_lc_t *n, vlbm_t *h, int steps)
+{
+    int rc;
+    if ((rc = check_solver(n, h))) return rc;
+    if (steps < 0) return lfail(n, VLBM_ERR_ARG, "negative step count");
+    if (steps == 0) return VLBM_OK;
+    if (!h->d_face) return lfail(n, VLBM_ERR_ARG, "FP32 state not initialised");
+    if (n->g_solver != h && n->g_exec) {
+        cudaGraphExecDestroy(n->g_exec);
+        n->g_exec = nullptr;
+    }
+    if (!n->g_exec) {
+        // one corrected coarse step (the solver's RK3 step, then the correction) as a graph
+        cudaGraph_t g = nullptr;
+        LCK(n, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        solver_enqueue_step(h);
+        rc = enqueue_correction(n, h, h->stream);
+        cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return lfail(n, VLBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&n->g_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return lfail(n, VLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        n->g_solver = h;
+    }
+    for (int q = 0; q < steps; ++q) LCK(n, cudaGraphLaunch(n->g_exec, h->stream));
+    solver_count_steps(h, steps);
+    if ((rc = vlbm_sync(h))) return lfail(n, rc, vlbm_last_error(h));
     return VLBM_OK;
 }
 
@@ -332,6 +379,7 @@ void vlbm_lc_destroy(vlbm_lc_t *n)
 {
     if (!n) return;
     if (n->stream) cudaStreamSynchronize(n->stream);
+    if (n->g_exec) cudaGraphExecDestroy(n->g_exec);
     for (void *p : n->bufs) cudaFree(p);
     if (n->stream) cudaStreamDestroy(n->stream);
     delete n;

@@ -24,12 +24,13 @@ constexpr float LC_CLAMP = 8.0f;   // bound of every scaled input feature
 constexpr unsigned LC_NEGMASK = (1u << 1) | (1u << 2) | (1u << 5) | (0xFFu << 8);
 struct LcInScale { float inv[LC_NSCALE]; };
 
+// Layer `layer` on the padded input Xp: FP32 pre-activations Yf, BF16 (ReLU) outputs Yb
+// [H][W][CO] and / or the next layer's padded input Ypad [H+2][W+2][CO] (any may be NULL).
 void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
-             float *Yf, __nv_bfloat16 *Yb, int relu, cudaStream_t s);
+             float *Yf, __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s);
 void lc_conv_bwd(int layer, const __nv_bfloat16 *dP, int H, int W, const __nv_bfloat16 *Wb, float *dXp, cudaStream_t s);
 void lc_wgrad(int layer, const __nv_bfloat16 *dPre, const __nv_bfloat16 *Xp, int H, int W, float *part, float *partb,
               cudaStream_t s);
-void lc_pad(const __nv_bfloat16 *X, int H, int W, int C, unsigned negmask, __nv_bfloat16 *Xp, cudaStream_t s);
 void lc_unpad(const float *dXp, int H, int W, int C, unsigned negmask, float *dX, cudaStream_t s);
 void lc_grad_pad2(const float *dY, const __nv_bfloat16 *act, int H, int W, int C, int CP, __nv_bfloat16 *dP,
                   cudaStream_t s);
@@ -43,8 +44,11 @@ void lc_weights_bf16(const float *w, int CO, int CI, int COp, int CIp, __nv_bflo
                      __nv_bfloat16 *bwd, cudaStream_t s);
 void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g, cudaStream_t s);
 void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                 const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *X0,
+                 const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *Xp,
                  cudaStream_t s);
+// (rho, u^theta, u^phi, T) [4][H][W] of a solver's FP32 state, FP32 arithmetic on the deviations.
+void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref, const double *sin_t, double *mom,
+                cudaStream_t s);
 void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
                 double *mean, cudaStream_t s);
 void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,

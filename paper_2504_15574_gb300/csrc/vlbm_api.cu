@@ -393,6 +393,10 @@ void choose_rho_ref(vlbm_t *h, const std::vector<double> &rho)
 
 }  // namespace
 
+void solver_enqueue_step(vlbm_t *h) { enqueue_step(h); }
+
+void solver_count_steps(vlbm_t *h, int n) { h->steps += n; }
+
 extern "C" {
 
 void vlbm_default_options(vlbm_options *opt)

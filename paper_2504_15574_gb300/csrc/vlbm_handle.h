@@ -50,3 +50,8 @@ struct vlbm {
     size_t dev_bytes = 0;
 };
 
+// Library-internal entry points on a solver (vlbm_api.cu), for the other host units.
+// Enqueues one RK3 step of h on its stream (stages, polar filters, pole budget).
+void solver_enqueue_step(vlbm_t *h);
+// Adds n steps to h's step counter (steps enqueued outside vlbm_step).
+void solver_count_steps(vlbm_t *h, int n);

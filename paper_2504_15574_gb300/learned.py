@@ -288,10 +288,10 @@ def evaluate(setup: Setup, net, seeds, n_steps, spinup=20):
         for r in range(len(seeds)):
             cs.set_populations(starts[r])
             t0 = time.perf_counter()
-            for _ in range(n_steps):
-                cs.step(1)
-                if mode == "learned":
-                    net.apply(cs)
+            if mode == "learned":
+                net.rollout(cs, n_steps)
+            else:
+                cs.step(n_steps)
             el += time.perf_counter() - t0
             rho, ut, up = cs.moments()
             ref = refs[r]
@@ -328,8 +328,26 @@ def main(argv=None):
     ap.add_argument("--eval-seeds", type=int, default=4)
     ap.add_argument("--eval-steps", type=int, nargs="+", default=[300, 1000])
     ap.add_argument("--out", default=None)
+    ap.add_argument("--timing-steps", type=int, default=0,
+                    help="only time this many corrected coarse steps of an untrained network (no data, no training)")
     a = ap.parse_args(argv)
     setup = Setup(coarse=a.coarse, polar_filter=a.polar_filter)
+    if a.timing_steps:
+        net = vlbm.LearnedCorrection(*setup.coarse, seed=1)
+        cs = setup.coarse_solver()
+        cs.init_moments(*inputs.gaussian_vortices(*setup.coarse, run=5000)[:3])
+        net.rollout(cs, 3)
+        t0 = time.perf_counter()
+        net.rollout(cs, a.timing_steps)
+        ms = (time.perf_counter() - t0) / a.timing_steps * 1e3
+        t0 = time.perf_counter()
+        cs.step(a.timing_steps)
+        ms_plain = (time.perf_counter() - t0) / a.timing_steps * 1e3
+        print(json.dumps({"grid_coarse": list(setup.coarse), "steps": a.timing_steps,
+                          "ms_per_corrected_step": ms, "ms_per_plain_step": ms_plain}))
+        cs.close()
+        net.close()
+        return
     seeds = list(range(1000, 1000 + a.train_seeds))
     t0 = time.perf_counter()
     if a.targets == "drift":

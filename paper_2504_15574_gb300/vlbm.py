@@ -91,6 +91,7 @@ SIGNATURES = {
     "vlbm_lc_gradients": (ctypes.c_int, [_H, _PD, _PD, _PD, ctypes.POINTER(ctypes.c_float)]),
     "vlbm_lc_train_step": (ctypes.c_int, [_H, _PD, _PD, ctypes.c_float, _PD]),
     "vlbm_lc_apply": (ctypes.c_int, [_H, _H]),
+    "vlbm_lc_rollout": (ctypes.c_int, [_H, _H, ctypes.c_int]),
     "vlbm_lc_last_error": (ctypes.c_char_p, [_H]),
     "vlbm_lc_destroy": (None, [_H]),
     "vlbm_diagnostics_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -446,6 +447,10 @@ class LearnedCorrection:
 
     def apply(self, solver):
         self._chk(load().vlbm_lc_apply(self.h, solver.h))
+
+    def rollout(self, solver, steps):
+        """`steps` corrected coarse steps (step, then correction) as device graph launches."""
+        self._chk(load().vlbm_lc_rollout(self.h, solver.h, int(steps)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -163,6 +163,33 @@ def test_apply_keeps_mass_and_moves_the_moments(V):
     assert np.abs(ut1 - ut0).max() > 1e-6 and np.abs(r1 - r0).max() > 1e-7
 
 
+def test_rollout_equals_stepping_and_applying_bitwise(V):
+    """vlbm_lc_rollout (one captured graph per corrected step) gives the state of
+    vlbm_step(1) followed by vlbm_lc_apply, step by step; rebuilt after new scales."""
+    H, W = 16, 32
+    net = V.LearnedCorrection(H, W, seed=4, in_scale=IN_SCALE, out_scale=OUT_SCALE)
+    p = net.get_weights()
+    p[-3:] = [0.5, 0.3, -0.2]
+    net.set_weights(p)
+    a = V.Solver(H, W, 2e-3, 1e-4, precision="fp32", guard=False)
+    b = V.Solver(H, W, 2e-3, 1e-4, precision="fp32", guard=False)
+    for s in (a, b):
+        s.init_moments(*inputs.gaussian_vortices(H, W, run=6))
+    net.rollout(a, 5)
+    for _ in range(5):
+        b.step(1)
+        net.apply(b)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    net.set_scales(IN_SCALE, tuple(2 * np.asarray(OUT_SCALE)))
+    net.rollout(a, 2)
+    for _ in range(2):
+        b.step(1)
+        net.apply(b)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    a.close()
+    b.close()
+
+
 def test_trained_correction_beats_the_plain_coarse_run_on_held_out_seeds(V):
     """Small learned-coarse experiment (coarse 32 x 64 from fine 128 x 256, clamped dt, 16
     fine steps per coarse step): trained on the per-step drift of the coarse run away from
