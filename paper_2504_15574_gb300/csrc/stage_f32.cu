@@ -194,6 +194,15 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             "l"(reinterpret_cast<unsigned long long>(tm)), "r"(q0), "r"(i0), "r"(0), "r"(smem_u32(&S.bar))
             : "memory");
     }
+    // stages 2, 3: pull this thread's cell of the step's start values toward L2 now
+    if (stage != 1) {
+        const int pi = i0 + warp, pj = q0 + lane;
+        if (pi < L.nt && pj < L.np) {
+#pragma unroll
+            for (int q = 0; q < NP2; ++q)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(R.F + L.at(q, pi, pj)));
+        }
+    }
     // per-tile tables while the tile is in flight
     {
         int t = tid;

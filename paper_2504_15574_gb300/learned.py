@@ -320,11 +320,11 @@ def main(argv=None):
     ap.add_argument("--coarse", type=int, nargs=2, default=[128, 256])
     ap.add_argument("--polar-filter", action="store_true", help="filter on (dt by the theta spacing)")
     ap.add_argument("--targets", choices=["drift", "one-step"], default="drift")
-    ap.add_argument("--train-seeds", type=int, default=16)
-    ap.add_argument("--windows", type=int, default=8, help="drift targets: restart windows per seed")
+    ap.add_argument("--train-seeds", type=int, default=32)
+    ap.add_argument("--windows", type=int, default=16, help="drift targets: restart windows per seed")
     ap.add_argument("--steps", type=int, default=48, help="one-step targets: samples per seed")
     ap.add_argument("--spinup", type=int, default=20)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--eval-seeds", type=int, default=4)
     ap.add_argument("--eval-steps", type=int, nargs="+", default=[300, 1000])
     ap.add_argument("--out", default=None)
