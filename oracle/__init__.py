@@ -51,6 +51,7 @@ def _load():
         lib.vo_create.restype = ctypes.c_void_p
         lib.vo_create.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, ctypes.c_int]
         lib.vo_destroy.argtypes = [ctypes.c_void_p]
+        lib.vo_set_scheme.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         lib.vo_quadrature.argtypes = [P, P]
         lib.vo_kernels.argtypes = [P, P]
         lib.vo_weno5.restype = D
@@ -118,7 +119,10 @@ def equilibrium(n, ut, up, T=1.0):
 class Oracle:
     """FP64 CPU vLBM on an n_theta x n_phi grid (mirror of the C ABI)."""
 
-    def __init__(self, n_theta, n_phi, tau, dt, eps=1e-6, R=1.0, polar_filter=False):
+    SCHEMES = {"weno5": 0, "u1": 1, "u2": 2, "u3": 3}
+
+    def __init__(self, n_theta, n_phi, tau, dt, eps=1e-6, R=1.0, polar_filter=False, scheme="weno5",
+                 komissarov=False):
         lib = _load()
         self._lib = lib
         self.n_theta, self.n_phi = int(n_theta), int(n_phi)
@@ -128,6 +132,8 @@ class Oracle:
         if not h:
             raise ValueError("oracle: invalid arguments")
         self._h = ctypes.c_void_p(h)
+        if lib.vo_set_scheme(self._h, self.SCHEMES[scheme], 1 if komissarov else 0) != 0:
+            raise ValueError("oracle: unknown scheme")
 
     def close(self):
         if getattr(self, "_h", None):

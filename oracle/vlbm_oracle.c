@@ -17,7 +17,11 @@
  *     k_phi at fixed k_theta (App. A.3);
  *   - flux-form advection on the cell-centred grid, Sec. 3.4-3.5
  *     Eqs. (discrete_coord_sphere), (discrete_advection_sphere);
- *   - WENO-5 fluxes, Eqs. (fluxes_W5), (WENO5_delta), (WENO5_sigma);
+ *   - WENO-5 fluxes, Eqs. (fluxes_W5), (WENO5_delta), (WENO5_sigma), or the
+ *     first/second/third-order upwind fluxes U1-U3, Eq. (fluxes_U1-3);
+ *   - optionally the "Komissarov" theta flux, Eqs. (Komissarov_scheme),
+ *     (Komissarov_sin_cos): d/dcos(theta) of the interface flux times the
+ *     interface sine, V = v_theta, reconstruction on f;
  *   - periodic phi and pole boundary conditions, Sec. 3.6 Eqs. (bcs_phi),
  *     (bcs_theta);
  *   - SSP-RK3 time stepping and the operator L[f], Sec. 3.7 Eq. (Lf).
@@ -33,6 +37,9 @@
  *       projection of the Maxwellian; the BGK target stays at T0 = 1.
  *   R19 sin/cos tables are built on the northern half and mirrored; the
  *       equator row of an odd grid gets cos = 0 exactly.
+ *   R8  the Komissarov interface angles are theta_{s+-1/2} = (s - 1/2 +- 1/2) dth
+ *       for the 1-based row s (the printed sin((s+1) dth), sin(s dth) is off by
+ *       one); its ghost rows take the mapped population f itself (no sine).
  *
  * Layout: populations f[k][i][j], k = 4*a + b (a = k_theta index, b = k_phi
  * index, velocities ascending), i = theta row 0..nt-1 (theta_i = (i+1/2) dth),
@@ -170,10 +177,15 @@ double vo_weno5(double a, double b, double c, double d, double e, double eps)
 /* Solver state                                                               */
 /* ------------------------------------------------------------------------- */
 
+enum { VO_WENO5 = 0, VO_U1 = 1, VO_U2 = 2, VO_U3 = 3 };
+
 typedef struct vo_state {
     int nt, np;
     double tau, dt, eps, R;
     int filter;            /* polar ring filter on/off (not in the paper) */
+    int scheme;            /* VO_WENO5 (default), VO_U1, VO_U2, VO_U3 */
+    int komissarov;        /* theta flux in the Komissarov form */
+    double *sin_f, *cos_f; /* per theta interface i = 0..nt, theta = i dth */
     double dth, dph;
     double v[NV], w[NV];
     double K[NV * NV], Kt[NV * NV];
@@ -230,6 +242,8 @@ vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R,
     o->sin_t = (double *)malloc(sizeof(double) * nt);
     o->cos_t = (double *)malloc(sizeof(double) * nt);
     o->cot_t = (double *)malloc(sizeof(double) * nt);
+    o->sin_f = (double *)malloc(sizeof(double) * (nt + 1));
+    o->cos_f = (double *)malloc(sizeof(double) * (nt + 1));
     o->fblock = (int *)malloc(sizeof(int) * nt);
     /* Eq. (discrete_coord_sphere); north half computed, south half mirrored. */
     for (int i = 0; i < nt; ++i) {
@@ -244,6 +258,19 @@ vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R,
         }
     }
     for (int i = 0; i < nt; ++i) o->cot_t[i] = o->cos_t[i] / o->sin_t[i];
+    /* interfaces theta_i = i dth (reading R8), northern half computed and mirrored */
+    if (o->sin_f && o->cos_f)
+        for (int i = 0; i <= nt; ++i) {
+            int m = nt - i;
+            if (i <= m) {
+                double th = (double)i * o->dth;
+                o->sin_f[i] = (i == 0) ? 0.0 : sin(th);
+                o->cos_f[i] = (i == m) ? 0.0 : cos(th);
+            } else {
+                o->sin_f[i] = o->sin_f[m];
+                o->cos_f[i] = -o->cos_f[m];
+            }
+        }
     for (int i = 0; i < nt; ++i) o->fblock[i] = filter_block(o, i);
     size_t n = plane(o) * NK;
     o->f = (double *)calloc(n, sizeof(double));
@@ -252,9 +279,9 @@ vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R,
     o->L = (double *)calloc(n, sizeof(double));
     o->Ft = (double *)calloc((size_t)NK * (size_t)(nt + 1) * (size_t)np, sizeof(double));
     o->Fp = (double *)calloc((size_t)NK * (size_t)nt * (size_t)(np + 1), sizeof(double));
-    if (!o->sin_t || !o->cos_t || !o->cot_t || !o->fblock || !o->f || !o->f1 || !o->f2 || !o->L ||
-        !o->Ft || !o->Fp) {
-        free(o->sin_t); free(o->cos_t); free(o->cot_t); free(o->fblock);
+    if (!o->sin_t || !o->cos_t || !o->cot_t || !o->sin_f || !o->cos_f || !o->fblock || !o->f || !o->f1 ||
+        !o->f2 || !o->L || !o->Ft || !o->Fp) {
+        free(o->sin_t); free(o->cos_t); free(o->cot_t); free(o->sin_f); free(o->cos_f); free(o->fblock);
         free(o->f); free(o->f1); free(o->f2); free(o->L); free(o->Ft); free(o->Fp);
         free(o);
         return NULL;
@@ -265,9 +292,19 @@ vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R,
 void vo_destroy(vo_state *o)
 {
     if (!o) return;
-    free(o->sin_t); free(o->cos_t); free(o->cot_t); free(o->fblock);
+    free(o->sin_t); free(o->cos_t); free(o->cot_t); free(o->sin_f); free(o->cos_f); free(o->fblock);
     free(o->f); free(o->f1); free(o->f2); free(o->L); free(o->Ft); free(o->Fp);
     free(o);
+}
+
+/* Selects the advection scheme (VO_WENO5, VO_U1, VO_U2, VO_U3) and the Komissarov
+ * theta flux; returns -1 for an unknown scheme. */
+int vo_set_scheme(vo_state *o, int scheme, int komissarov)
+{
+    if (!o || scheme < VO_WENO5 || scheme > VO_U3) return -1;
+    o->scheme = scheme;
+    o->komissarov = komissarov ? 1 : 0;
+    return 0;
 }
 
 void vo_geometry(const vo_state *o, double *sin_t, double *cos_t, int *fblock)
@@ -309,24 +346,51 @@ static double g_theta(const vo_state *o, const double *f, int k, int i, int j)
     return -o->sin_t[ii] * f[idx(o, kk, ii, jj)];
 }
 
+/* f at any row i in [-3, nt+2] for the Komissarov theta flux: rows beyond a pole
+ * read the mirrored row and population of Eq. (bcs_theta) without a sine. */
+static double f_theta(const vo_state *o, const double *f, int k, int i, int j)
+{
+    int nt = o->nt;
+    if (i >= 0 && i < nt) return f[idx(o, k, i, j)];
+    int jj = wrap_col(o, j + o->np / 2);
+    int ii = (i < 0) ? -1 - i : 2 * nt - 1 - i;
+    return f[idx(o, NK - 1 - k, ii, jj)];
+}
+
+/* Interface value from the upwind-ordered values a..e (a furthest upwind, c the
+ * upwind cell, d the downwind cell): WENO-5 of Eqs. (fluxes_W5)-(WENO5_sigma), or
+ * the upwind stencils of Eq. (fluxes_U1-3): U1 c, U2 (3c - b)/2, U3 (2d + 5c - b)/6. */
+static double recon(const vo_state *o, double a, double b, double c, double d, double e)
+{
+    switch (o->scheme) {
+    case VO_U1: return c;
+    case VO_U2: return 1.5 * c - 0.5 * b;
+    case VO_U3: return (2.0 * d + 5.0 * c - b) / 6.0;
+    default: return vo_weno5(a, b, c, d, e, o->eps);
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* The operator L[g] of Eq. (Lf)                                              */
 /* ------------------------------------------------------------------------- */
 
-/* Theta flux through the interface between rows i-1 and i (i = 0..nt),
- * Eq. (discrete_advection_sphere) with Eq. (fluxes_W5) on g = sin(theta) f. */
+/* Theta flux through the interface between rows i-1 and i (i = 0..nt):
+ * Eq. (discrete_advection_sphere), the reconstruction on g = sin(theta) f; or,
+ * Komissarov form, v_theta sin(theta_i) times the reconstruction on f
+ * (Eq. Komissarov_scheme with V = v_theta). */
 static double flux_theta(const vo_state *o, const double *f, int k, int i, int j)
 {
     double vth = o->v[k / 4];
+    double (*val)(const vo_state *, const double *, int, int, int) = o->komissarov ? f_theta : g_theta;
     double gh;
     if (vth > 0.0) {
-        gh = vo_weno5(g_theta(o, f, k, i - 3, j), g_theta(o, f, k, i - 2, j), g_theta(o, f, k, i - 1, j),
-                      g_theta(o, f, k, i, j), g_theta(o, f, k, i + 1, j), o->eps);
+        gh = recon(o, val(o, f, k, i - 3, j), val(o, f, k, i - 2, j), val(o, f, k, i - 1, j),
+                   val(o, f, k, i, j), val(o, f, k, i + 1, j));
     } else {
-        gh = vo_weno5(g_theta(o, f, k, i + 2, j), g_theta(o, f, k, i + 1, j), g_theta(o, f, k, i, j),
-                      g_theta(o, f, k, i - 1, j), g_theta(o, f, k, i - 2, j), o->eps);
+        gh = recon(o, val(o, f, k, i + 2, j), val(o, f, k, i + 1, j), val(o, f, k, i, j),
+                   val(o, f, k, i - 1, j), val(o, f, k, i - 2, j));
     }
-    return vth * gh;
+    return o->komissarov ? vth * o->sin_f[i] * gh : vth * gh;
 }
 
 /* Phi flux through the interface between columns j-1 and j (j = 0..np). */
@@ -336,11 +400,11 @@ static double flux_phi(const vo_state *o, const double *f, int k, int i, int j)
     const double *row = f + idx(o, k, i, 0);
     double gh;
     if (vph > 0.0) {
-        gh = vo_weno5(row[wrap_col(o, j - 3)], row[wrap_col(o, j - 2)], row[wrap_col(o, j - 1)],
-                      row[wrap_col(o, j)], row[wrap_col(o, j + 1)], o->eps);
+        gh = recon(o, row[wrap_col(o, j - 3)], row[wrap_col(o, j - 2)], row[wrap_col(o, j - 1)],
+                   row[wrap_col(o, j)], row[wrap_col(o, j + 1)]);
     } else {
-        gh = vo_weno5(row[wrap_col(o, j + 2)], row[wrap_col(o, j + 1)], row[wrap_col(o, j)],
-                      row[wrap_col(o, j - 1)], row[wrap_col(o, j - 2)], o->eps);
+        gh = recon(o, row[wrap_col(o, j + 2)], row[wrap_col(o, j + 1)], row[wrap_col(o, j)],
+                   row[wrap_col(o, j - 1)], row[wrap_col(o, j - 2)]);
     }
     return vph * gh;
 }
@@ -395,7 +459,9 @@ static double operator_L(vo_state *o, const double *g, double *L)
                 double ftm = o->Ft[((size_t)k * (size_t)(nt + 1) + (size_t)i) * (size_t)np + (size_t)j];
                 double fpp = o->Fp[((size_t)k * (size_t)nt + (size_t)i) * (size_t)(np + 1) + (size_t)(j + 1)];
                 double fpm = o->Fp[((size_t)k * (size_t)nt + (size_t)i) * (size_t)(np + 1) + (size_t)j];
-                double adv_t = -(ftp - ftm) / (R * o->sin_t[i] * o->dth);
+                /* Komissarov: -d/dcos(theta) of the interface fluxes (Eq. Komissarov_scheme) */
+                double adv_t = o->komissarov ? -(ftp - ftm) / (R * (o->cos_f[i] - o->cos_f[i + 1]))
+                                             : -(ftp - ftm) / (R * o->sin_t[i] * o->dth);
                 double adv_p = -(fpp - fpm) / (R * o->sin_t[i] * o->dph);
                 L[idx(o, k, i, j)] = adv_t + adv_p - force - (gk[k] - feq) / o->tau;
             }
