@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--n-theta", type=int, default=1024)
     ap.add_argument("--n-phi", type=int, default=2048)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--scheme", default="weno5", choices=["weno5", "u1", "u2", "u3"],
+                    help="advection scheme (the headline workload is weno5)")
+    ap.add_argument("--komissarov", action="store_true", help="Komissarov theta flux (upwind schemes)")
     args = ap.parse_args()
     global NT, NP, DT
     NT, NP = args.n_theta, args.n_phi
@@ -137,13 +140,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(steps, warmup, budget_s):
+def oracle_sample(steps, warmup, budget_s, scheme="weno5", komissarov=False):
     """The FP64 CPU oracle on the same workload (1024 x 2048 shock cap): `warmup` full RK3 steps
     (at most one), then up to `steps` timed full RK3 steps, stopping once `budget_s` seconds of
     timed work have run.  Returns (MLUPS, seconds, steps timed, threads)."""
     import oracle
     from paper_2504_15574_gb300 import inputs
-    o = oracle.Oracle(NT, NP, tau=TAU, dt=DT, polar_filter=True)
+    o = oracle.Oracle(NT, NP, tau=TAU, dt=DT, polar_filter=True, scheme=scheme, komissarov=komissarov)
     o.init_moments(*inputs.shock_cap(NT, NP))
     if warmup:
         o.step(1)
@@ -157,18 +160,25 @@ def oracle_sample(steps, warmup, budget_s):
     return NT * NP * done / el / 1e6, el, done, cores
 
 
+def workload_name(args):
+    w = WORKLOAD.replace("1024x2048", f"{NT}x{NP}")
+    if args.scheme != "weno5":
+        w = w.replace("WENO-5", args.scheme.upper() + (" + Komissarov theta flux" if args.komissarov else ""))
+    return w
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    val, el, done, cores = oracle_sample(args.steps, args.warmup, 60.0)
+    val, el, done, cores = oracle_sample(args.steps, args.warmup, 60.0, args.scheme, args.komissarov)
     sample = (f"{done} of the {args.steps} requested full RK3 steps of the 1024x2048 workload "
               f"(timed work bounded at 60 s; {el:.1f} s) after {min(args.warmup, 1)} warm-up step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": done, "warmup": args.warmup, "ms_per_step": el / done * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_theta": NT, "n_phi": NP, "Q": 16, "parallelism": "host cores"},
+        "config": {"workload": workload_name(args), "n_theta": NT, "n_phi": NP, "Q": 16, "parallelism": "host cores"},
         "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -186,7 +196,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()          # a real stream: the library captures CUDA graphs on it
     torch.cuda.set_stream(stream)
     rho, ut, up, T = inputs.shock_cap(NT, NP)
-    s = vlbm.Solver(NT, NP, TAU, DT, precision="fp32", polar_filter=True, stream=stream.cuda_stream)
+    s = vlbm.Solver(NT, NP, TAU, DT, precision="fp32", polar_filter=True, stream=stream.cuda_stream,
+                    scheme=args.scheme, komissarov=args.komissarov)
     s.init_moments(rho, ut, up, T)
 
     def barrier():
@@ -237,7 +248,7 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu:
-            val, el, done, cores = oracle_sample(1000, 1, 15.0)
+            val, el, done, cores = oracle_sample(1000, 1, 15.0, args.scheme, args.komissarov)
             cpu = {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                    "sample": f"{done} full RK3 steps of the 1024x2048 workload after 1 warm-up step "
                              f"(bounded at 15 s of timed work; {el:.1f} s)"}
@@ -246,7 +257,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("1024x2048", f"{NT}x{NP}"), "n_theta": NT, "n_phi": NP,
+            "config": {"workload": workload_name(args), "n_theta": NT, "n_phi": NP,
                        "Q": 16, "global_batch": world,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (three 134 MB population arrays per replica)"},

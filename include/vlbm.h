@@ -59,6 +59,13 @@ extern "C" {
 #define VLBM_D2Q9  3             /* reserved: returns VLBM_ERR_UNSUPPORTED */
 #define VLBM_D2Q16 4
 
+/* Advection schemes (Sec. 3.5): WENO-5, Eqs. (fluxes_W5)-(WENO5_sigma), or the
+ * first/second/third-order upwind fluxes of Eq. (fluxes_U1-3). */
+#define VLBM_WENO5 0
+#define VLBM_U1    1
+#define VLBM_U2    2
+#define VLBM_U3    3
+
 /* Storage / arithmetic precision of the populations. */
 #define VLBM_FP64 0              /* f in FP64, same operation order as the FP64 oracle */
 #define VLBM_FP32 1              /* delta f = f - w_k rho_ref in FP32, FP64 tables */
@@ -76,6 +83,11 @@ typedef struct vlbm_options {
     double rho_ref;     /* VLBM_FP32 only: reference density of the deviation storage;
                            <= 0 means the area-weighted mean of the initial rho; default 0 */
     int tile_rows;      /* VLBM_FP32 only: rows per stage tile, 4 or 8 (0: 8); tiles are 32 columns wide */
+    int scheme;         /* VLBM_WENO5 (default), VLBM_U1, VLBM_U2 or VLBM_U3, in theta and phi */
+    int komissarov;     /* 1: theta flux in the Komissarov form of Eqs. (Komissarov_scheme),
+                           (Komissarov_sin_cos): -d/dcos(theta) of v_theta sin(theta_{s+-1/2}) times
+                           the reconstruction of f at the interfaces theta_{s+-1/2} = (s - 1/2 +- 1/2)
+                           dtheta; no flux crosses a pole; default 0 */
 } vlbm_options;
 
 /* Diagnostics in FP64 (not in the paper).  Area element R^2 sin(theta) dtheta dphi. */

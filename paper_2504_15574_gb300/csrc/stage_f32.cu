@@ -49,6 +49,8 @@ struct __align__(128) SmemT {
     float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
     float2 cw[NP2][TY + 1];             // -w rho_ref corr per pair and theta face row
     float2 rr[TY][NP2];                 // s rref per cell row and pair
+    float2 isp2[TY + 2 * GR];           // upwind schemes, Komissarov: (1/sin, 1/sin) at the tile rows
+    float2 sf2[TY + 1];                 // upwind schemes, Komissarov: interface sines of the face rows
     RowF rowc[TY];
     RunF run;                           // batch kernel: this tile's run
     unsigned long long bar;
@@ -167,7 +169,9 @@ __device__ __forceinline__ void store_images(f2 *f, const Layout &L, int p, int 
 // One stage of one TY x TX tile of one run.  The mbarrier is initialised by the
 // caller; `parity` is the phase this tile's load completes.  Returns false if
 // the tile load did not arrive in time (every thread of the CTA agrees).
-template <int TY>
+// LIN: the upwind schemes U1-U3 (Eq. fluxes_U1-3, optionally with the Komissarov theta flux)
+// instead of WENO-5.
+template <int TY, bool LIN>
 __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int stage, const CUtensorMap *tm, int bx,
                                            int by, SmemT<TY> &S, unsigned parity, unsigned *err)
 {
@@ -220,6 +224,10 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         } else if ((t -= TY) < TY * NP2) {
             const int ry = t >> 3, q = t & 7;
             S.rr[ry][q] = R.rref[(size_t)min(i0 + ry, L.nt - 1) * NP2 + q];
+        } else if (LIN && (t -= TY * NP2) < SR) {
+            S.isp2[t] = splat(R.isp[i0 + t]);
+        } else if (LIN && (t -= SR) < TY + 1) {
+            S.sf2[t] = splat(R.sfc[i0 + t]);
         }
     }
     __syncthreads();
@@ -233,7 +241,29 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     }
 
     // ---- phi faces: warp = cell row fy, lane = face fx (west face of column fx)
-    {
+    if constexpr (LIN) {
+        // upwind schemes on dg: x_up2, x_up, x_down are the columns fx-2, fx-1, fx for v > 0
+        // and fx+1, fx, fx-1 for v < 0 (shared column = column + GC)
+        const int fy = warp;
+        const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
+#pragma unroll
+        for (int q = 0; q < NP2; ++q) {
+            const f2 vb = c.vphi2[q & 3];
+            const f2 *row = &S.tile[q][fy + GR][0];
+            const f2 rec = (vb.x > 0.0f) ? fma2(l0, row[lane + 2], fma2(l1, row[lane + 3], mul2(l2, row[lane + 4])))
+                                         : fma2(l0, row[lane + 5], fma2(l1, row[lane + 4], mul2(l2, row[lane + 3])));
+            S.fp[q][fy][lane] = mul2(vb, rec);
+        }
+        if (tid < NP2 * TY) {
+            const int q = tid / TY, ry = tid - (tid / TY) * TY;
+            const f2 vb = c.vphi2[q & 3];
+            const f2 *row = &S.tile[q][ry + GR][0];
+            const int fx = TX;
+            const f2 rec = (vb.x > 0.0f) ? fma2(l0, row[fx + 2], fma2(l1, row[fx + 3], mul2(l2, row[fx + 4])))
+                                         : fma2(l0, row[fx + 5], fma2(l1, row[fx + 4], mul2(l2, row[fx + 3])));
+            S.fp[q][ry][fx] = mul2(vb, rec);
+        }
+    } else {
         const int fy = warp;
         const float kinv = S.rowc[fy].kphi;
 #pragma unroll 2
@@ -260,14 +290,39 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         }
     }
 
-    // ---- theta faces: warp = pair, lane = column, marching over the TY+1 face rows.
+    // ---- upwind schemes, theta faces: warp = pair, lane = column; the column's values are dg
+    // (nodal g = sin f), or for the Komissarov flux df = dg / sin (ghost rows: the mapped
+    // population's df), then v_theta times the interface sine times the reconstruction
+    if constexpr (LIN) {
+        const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
+        const bool kom = R.komissarov != 0;
+#pragma unroll 1
+        for (int q = warp; q < NP2; q += NT / 32) {
+            const int g = q >> 2;
+            const f2 vt = c.vth[g];
+            const f2 *col = &S.tile[q][0][lane + GC];
+            f2 x[SR];
+#pragma unroll
+            for (int r = 0; r < SR; ++r) x[r] = kom ? mul2(col[r * SC], S.isp2[r]) : col[r * SC];
+#pragma unroll
+            for (int fy = 0; fy <= TY; ++fy) {
+                // face fy lies between tile rows fy-1 and fy (x index = tile row + GR)
+                const f2 rec = g ? fma2(l0, x[fy + 1], fma2(l1, x[fy + 2], mul2(l2, x[fy + 3])))
+                                 : fma2(l0, x[fy + 4], fma2(l1, x[fy + 3], mul2(l2, x[fy + 2])));
+                const f2 fl = mul2(vt, rec);
+                S.ft[q][fy][lane] = kom ? mul2(fl, S.sf2[fy]) : fl;
+            }
+        }
+    }
+
+    // ---- WENO-5 theta faces: warp = pair, lane = column, marching over the TY+1 face rows.
     // Consecutive faces share their second differences (the smoothness forms of the
     // three candidate stencils are centred on consecutive rows).  With x the tile
     // column (rows 0..SR-1), for v > 0 face fy uses x[fy..fy+4] in upwind order,
     // for v < 0 it uses x[fy+5..fy+1].  The smoothness forms are those of the full
     // g = dg + w rho_ref sin(theta) (first and second differences of sin from the
     // FP64 tables); P2 is taken on dg alone.
-    {
+    if constexpr (!LIN) {
         const float kinv = R.ktheta;
         const f2 c13 = splat((13.0f / 12.0f) * kinv), c14 = splat(0.25f * kinv), one = splat(1.0f);
         const f2 two = splat(2.0f), m2 = splat(-2.0f);
@@ -364,7 +419,9 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const float u2 = fmaf(ut, ut, up * up);
     const f2 h0 = splat(-0.5f * u2), h1 = splat(fmaf(-0.5f, u2, 1.0f));
     const f2 ut2 = splat(ut), snn = splat(rc.s * n), sg2 = splat(SG);
-    const f2 cot2 = splat(rc.cotR), idth = splat(R.inv_dth), idph = splat(rc.inv_dph), mtau = splat(-R.tau_inv);
+    const f2 cot2 = splat(rc.cotR), idph = splat(rc.inv_dph), mtau = splat(-R.tau_inv);
+    // theta flux difference to the dg tendency: 1/(R dtheta), or s / (R dcos) for the Komissarov flux
+    const f2 idth = splat((LIN && R.komissarov) ? rc.kth : R.inv_dth);
 
     f2 o[NP2];
 #pragma unroll
@@ -405,7 +462,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     return true;
 }
 
-template <int TY>
+template <int TY, bool LIN>
 __global__ void __launch_bounds__(TY * 32, 24 / TY) stage_f32_kernel(const __grid_constant__ CUtensorMap tm,
                                                                       const RunF R, const VelC c, int stage,
                                                                       unsigned *err)
@@ -416,13 +473,13 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) stage_f32_kernel(const __gri
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    stage_tile<TY>(R, c, stage, &tm, blockIdx.x, blockIdx.y, S, 0u, err);
+    stage_tile<TY, LIN>(R, c, stage, &tm, blockIdx.x, blockIdx.y, S, 0u, err);
 }
 
 // Persistent batch stage: CTA b takes work items b, b + gridDim.x, ...; a work item
 // is (run, tile index within the run).  The run's parameters are copied into
 // shared memory per item.
-template <int TY>
+template <int TY, bool LIN>
 __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const RunF *runs, const CUtensorMap *tms,
                                                                             const int2 *work, int ntiles, const VelC c,
                                                                             int stage, unsigned *err)
@@ -443,7 +500,7 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const
         }
         __syncthreads();
         const int tx = S.run.tiles_x;
-        if (!stage_tile<TY>(S.run, c, stage, tms + 3 * w.x + (stage - 1), w.y % tx, w.y / tx, S, parity, err))
+        if (!stage_tile<TY, LIN>(S.run, c, stage, tms + 3 * w.x + (stage - 1), w.y % tx, w.y / tx, S, parity, err))
             return;
         parity ^= 1u;
         __syncthreads();   // every thread is done with this tile's shared memory
@@ -823,45 +880,55 @@ __global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *
 template <int TY>
 static size_t smem_bytes() { return sizeof(SmemT<TY>) + 128; }
 
+template <int TY, bool LIN>
+cudaError_t prepare_one()
+{
+    cudaError_t e = cudaFuncSetAttribute(stage_f32_kernel<TY, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_bytes<TY>());
+    if (e) return e;
+    return cudaFuncSetAttribute(batch_stage_f32_kernel<TY, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<TY>());
+}
+
 cudaError_t prepare_stage_f32()
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(stage_f32_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<8>())))
+    if ((e = prepare_one<8, false>()) || (e = prepare_one<4, false>()) || (e = prepare_one<8, true>()))
         return e;
-    if ((e = cudaFuncSetAttribute(stage_f32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<4>())))
-        return e;
-    if ((e = cudaFuncSetAttribute(batch_stage_f32_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem_bytes<8>())))
-        return e;
-    return cudaFuncSetAttribute(batch_stage_f32_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<4>());
+    return prepare_one<4, true>();
 }
 
 int stage_f32_max_ctas_per_sm(int ty)
 {
     int n = 0;
-    if (ty == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<4>, 128, smem_bytes<4>());
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<8>, 256, smem_bytes<8>());
+    if (ty == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<4, false>, 128, smem_bytes<4>());
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<8, false>, 256, smem_bytes<8>());
     return n;
 }
 
-void launch_stage_f32(const CUtensorMap &tm_in, const RunF &run, const VelC &c, int stage, int ty, unsigned *err,
-                      cudaStream_t s)
+void launch_stage_f32(const CUtensorMap &tm_in, const RunF &run, const VelC &c, int stage, int ty, bool lin,
+                      unsigned *err, cudaStream_t s)
 {
+    const dim3 grid((run.L.np + TX - 1) / TX, (run.L.nt + ty - 1) / ty);
     if (ty == 4) {
-        dim3 grid((run.L.np + TX - 1) / TX, (run.L.nt + 3) / 4);
-        stage_f32_kernel<4><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, run, c, stage, err);
+        if (lin) stage_f32_kernel<4, true><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, run, c, stage, err);
+        else stage_f32_kernel<4, false><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, run, c, stage, err);
     } else {
-        dim3 grid((run.L.np + TX - 1) / TX, (run.L.nt + 7) / 8);
-        stage_f32_kernel<8><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, run, c, stage, err);
+        if (lin) stage_f32_kernel<8, true><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, run, c, stage, err);
+        else stage_f32_kernel<8, false><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, run, c, stage, err);
     }
 }
 
 void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
-                            int stage, int ty, int ctas, unsigned *err, cudaStream_t s)
+                            int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s)
 {
-    if (ty == 4) batch_stage_f32_kernel<4><<<ctas, 128, smem_bytes<4>(), s>>>(runs, tms, work, ntiles, c, stage, err);
-    else batch_stage_f32_kernel<8><<<ctas, 256, smem_bytes<8>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+    if (ty == 4) {
+        if (lin) batch_stage_f32_kernel<4, true><<<ctas, 128, smem_bytes<4>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+        else batch_stage_f32_kernel<4, false><<<ctas, 128, smem_bytes<4>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+    } else {
+        if (lin) batch_stage_f32_kernel<8, true><<<ctas, 256, smem_bytes<8>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+        else batch_stage_f32_kernel<8, false><<<ctas, 256, smem_bytes<8>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+    }
 }
 
 void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,

@@ -35,6 +35,18 @@ __device__ __forceinline__ double weno5(double a, double b, double c, double d, 
     return (w1 * p1 + w2 * p2 + w3 * p3) / (w1 + w2 + w3);
 }
 
+// Interface value from upwind-ordered a..e (c the upwind cell, d the downwind cell):
+// WENO-5, or the upwind stencils of Eq. (fluxes_U1-3), in the oracle's expression order.
+__device__ __forceinline__ double recon(int scheme, double a, double b, double c, double d, double e, double eps)
+{
+    switch (scheme) {
+    case VLBM_U1: return c;
+    case VLBM_U2: return 1.5 * c - 0.5 * b;
+    case VLBM_U3: return (2.0 * d + 5.0 * c - b) / 6.0;
+    default: return weno5(a, b, c, d, e, eps);
+    }
+}
+
 // Writes v at interior (k, i, j) and at every ghost image of that cell.
 template <typename T>
 __device__ __forceinline__ void store_with_images(T *f, const Layout &L, int k, int i, int j, T v)
@@ -98,35 +110,41 @@ __global__ void __launch_bounds__(128) stage_f64_kernel(const StageD p)
         }
         const double force = cot_i / R * (vb * vb * kg - va * ktg);
 
-        // theta faces i (north) and i+1 (south) on the nodal g = sin f
+        // theta faces i (north) and i+1 (south) on the nodal g = sin f, or (Komissarov) on f
+        // (ghost rows hold the mapped population's f) times the interface sine
+        const int sc = p.scheme;
         double gt[7];
 #pragma unroll
-        for (int o = 0; o < 7; ++o) gt[o] = p.sin_ext[i + o] * g[L.at(k, i - 3 + o, j)];
-        double fn, fs;
+        for (int o = 0; o < 7; ++o)
+            gt[o] = p.komissarov ? g[L.at(k, i - 3 + o, j)] : p.sin_ext[i + o] * g[L.at(k, i - 3 + o, j)];
+        double rn, rs;
         if (va > 0.0) {
-            fn = va * weno5(gt[0], gt[1], gt[2], gt[3], gt[4], eps);
-            fs = va * weno5(gt[1], gt[2], gt[3], gt[4], gt[5], eps);
+            rn = recon(sc, gt[0], gt[1], gt[2], gt[3], gt[4], eps);
+            rs = recon(sc, gt[1], gt[2], gt[3], gt[4], gt[5], eps);
         } else {
-            fn = va * weno5(gt[5], gt[4], gt[3], gt[2], gt[1], eps);
-            fs = va * weno5(gt[6], gt[5], gt[4], gt[3], gt[2], eps);
+            rn = recon(sc, gt[5], gt[4], gt[3], gt[2], gt[1], eps);
+            rs = recon(sc, gt[6], gt[5], gt[4], gt[3], gt[2], eps);
         }
+        const double fn = p.komissarov ? va * p.sin_f[i] * rn : va * rn;
+        const double fs = p.komissarov ? va * p.sin_f[i + 1] * rs : va * rs;
         // phi faces j (west) and j+1 (east)
         double gp[7];
 #pragma unroll
         for (int o = 0; o < 7; ++o) gp[o] = g[L.at(k, i, j - 3 + o)];
         double fw, fe;
         if (vb > 0.0) {
-            fw = vb * weno5(gp[0], gp[1], gp[2], gp[3], gp[4], eps);
-            fe = vb * weno5(gp[1], gp[2], gp[3], gp[4], gp[5], eps);
+            fw = vb * recon(sc, gp[0], gp[1], gp[2], gp[3], gp[4], eps);
+            fe = vb * recon(sc, gp[1], gp[2], gp[3], gp[4], gp[5], eps);
         } else {
-            fw = vb * weno5(gp[5], gp[4], gp[3], gp[2], gp[1], eps);
-            fe = vb * weno5(gp[6], gp[5], gp[4], gp[3], gp[2], eps);
+            fw = vb * recon(sc, gp[5], gp[4], gp[3], gp[2], gp[1], eps);
+            fe = vb * recon(sc, gp[6], gp[5], gp[4], gp[3], gp[2], eps);
         }
         if (p.pole) {
             if (i == 0) p.pole[(size_t)k * L.np + j] = fn;
             if (i == L.nt - 1) p.pole[((size_t)NK + k) * L.np + j] = fs;
         }
-        const double adv_t = -(fs - fn) / (R * sin_i * p.dth);
+        const double adv_t = p.komissarov ? -(fs - fn) / (R * (p.cos_f[i] - p.cos_f[i + 1]))
+                                          : -(fs - fn) / (R * sin_i * p.dth);
         const double adv_p = -(fe - fw) / (R * sin_i * p.dph);
         const double Lk = adv_t + adv_p - force - (gk[k] - feq) / p.tau;
 

@@ -178,6 +178,20 @@ int build_f32_tables(vlbm_t *h)
     for (int q = 0; q < 16; ++q) f.Kt2[q] = make_float2((float)c.Kt[q], (float)c.Kt[q]);
     run.rho_ref = (float)rr;
 
+    // upwind schemes (Eq. fluxes_U1-3): value = lin0 x_up2 + lin1 x_up + lin2 x_down
+    double lin[3] = {0.0, 1.0, 0.0};
+    if (h->scheme == VLBM_U2) {
+        lin[0] = -0.5;
+        lin[1] = 1.5;
+    } else if (h->scheme == VLBM_U3) {
+        lin[0] = -1.0 / 6.0;
+        lin[1] = 5.0 / 6.0;
+        lin[2] = 1.0 / 3.0;
+    }
+    run.lin0 = (float)lin[0];
+    run.lin1 = (float)lin[1];
+    run.lin2 = (float)lin[2];
+    run.komissarov = h->komissarov;
     // faces fi = 0..nt between rows fi-1 and fi; upwind-ordered sine stencils
     std::vector<FaceConst> face(2 * (size_t)(nt + 1));
     std::vector<double> plin(2 * (size_t)(nt + 1));
@@ -200,7 +214,9 @@ int build_f32_tables(vlbm_t *h)
             F.corr = (float)(0.1 * (A1 - A2) / 3.0 + 0.3 * (A2 - A3) / 6.0);
             F.pad = 0.0f;
             face[2 * fi + dir] = F;
-            plin[2 * fi + dir] = (2 * a - 13 * b + 47 * cc + 27 * d - 3 * e) / 60.0;
+            // the interface value of sin(theta) itself: WENO-5 with ideal weights, or the upwind stencil
+            plin[2 * fi + dir] = (h->scheme == VLBM_WENO5) ? (2 * a - 13 * b + 47 * cc + 27 * d - 3 * e) / 60.0
+                                                           : lin[0] * b + lin[1] * cc + lin[2] * d;
         }
     std::vector<RowF> row(nt);
     std::vector<float2> rref((size_t)nt * 8);
@@ -212,7 +228,8 @@ int build_f32_tables(vlbm_t *h)
         rc.inv_dph = (float)(1.0 / (R * s * dph));
         rc.cotR = (float)(cot / R);
         rc.kphi = (float)(1.0 / (h->eps * s * s));
-        rc.pad0 = rc.pad1 = rc.pad2 = 0.0f;
+        rc.kth = (float)(s / (R * (h->cos_f[i] - h->cos_f[i + 1])));
+        rc.pad1 = rc.pad2 = 0.0f;
         row[i] = rc;
         double rk[16];
         for (int k = 0; k < 16; ++k) {
@@ -220,8 +237,14 @@ int build_f32_tables(vlbm_t *h)
             const double va = c.v[a], vb = c.v[b];
             const double wr = c.w[a] * c.w[b] * rr;
             const int dir = va > 0 ? 0 : 1;
-            // theta advection of the reference part with ideal weights, and its force
-            const double adv = -va * wr * (plin[2 * (i + 1) + dir] - plin[2 * i + dir]) / (R * s * dth);
+            // theta advection of the reference part (WENO-5: with ideal weights; the upwind
+            // schemes are linear, so theirs is exact; Komissarov: the interface sines of
+            // v_theta w rho_ref), and its force
+            double adv;
+            if (h->komissarov)
+                adv = -va * wr * (h->sin_f[i + 1] - h->sin_f[i]) / (R * (h->cos_f[i] - h->cos_f[i + 1]));
+            else
+                adv = -va * wr * (plin[2 * (i + 1) + dir] - plin[2 * i + dir]) / (R * s * dth);
             double kw = 0.0, ktw = 0.0;
             for (int m = 0; m < 4; ++m) {
                 kw += c.K[a * 4 + m] * c.w[m] * c.w[b] * rr;
@@ -245,7 +268,15 @@ int build_f32_tables(vlbm_t *h)
             d2s[pr] = (float)(sin_padded(h->sin_t, nt, pr - 1) - 2.0 * sin_padded(h->sin_t, nt, pr) +
                               sin_padded(h->sin_t, nt, pr + 1));
     }
+    // upwind schemes: 1/sin at padded rows (negative at ghost rows) and the interface sines
+    std::vector<float> isp(npr, 0.0f), sfc(nt + 1 + F32_TILE_ROWS_MAX, 0.0f);
+    for (int pr = 0; pr < nt + 2 * GR; ++pr) isp[pr] = (float)(1.0 / sin_padded(h->sin_t, nt, pr));
+    for (int fi = 0; fi <= nt; ++fi) sfc[fi] = (float)h->sin_f[fi];
     int rc;
+    if ((rc = upload(h, &h->d_isp, isp.data(), isp.size())) || (rc = upload(h, &h->d_sfc, sfc.data(), sfc.size())))
+        return rc;
+    run.isp = h->d_isp;
+    run.sfc = h->d_sfc;
     if ((rc = upload(h, &h->d_dsin, ds.data(), ds.size()))) return rc;
     if ((rc = upload(h, &h->d_d2sin, d2s.data(), d2s.size()))) return rc;
     if ((rc = upload(h, &h->d_face, face.data(), face.size()))) return rc;
@@ -320,11 +351,15 @@ void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
             p.eps = h->eps;
             p.stage = st;
             p.c = h->vd;
+            p.scheme = h->scheme;
+            p.komissarov = h->komissarov;
+            p.sin_f = h->d_sin_f;
+            p.cos_f = h->d_cos_f;
             if (part != 2) launch_stage_f64(p, s);
             if (h->nfrows && part != 1) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         } else {
             const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
-            if (part != 2) launch_stage_f32(tm, h->run, h->vc, st, h->ty, h->d_flags, s);
+            if (part != 2) launch_stage_f32(tm, h->run, h->vc, st, h->ty, h->scheme != VLBM_WENO5, h->d_flags, s);
             if (h->nfrows && part != 1) launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         }
     }
@@ -410,6 +445,8 @@ void vlbm_default_options(vlbm_options *opt)
     opt->stream = nullptr;
     opt->rho_ref = 0.0;
     opt->tile_rows = 0;
+    opt->scheme = VLBM_WENO5;
+    opt->komissarov = 0;
 }
 
 int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt, const vlbm_options *opt,
@@ -429,6 +466,9 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     if (opt) o = *opt;
     if (o.precision != VLBM_FP64 && o.precision != VLBM_FP32) return fail(nullptr, VLBM_ERR_ARG, "bad precision");
     if (!(o.weno_eps > 0.0) || !(o.radius > 0.0)) return fail(nullptr, VLBM_ERR_ARG, "weno_eps and radius must be > 0");
+    if (o.scheme < VLBM_WENO5 || o.scheme > VLBM_U3) return fail(nullptr, VLBM_ERR_ARG, "unknown advection scheme");
+    if (o.precision == VLBM_FP32 && o.scheme == VLBM_WENO5 && o.komissarov)
+        return fail(nullptr, VLBM_ERR_UNSUPPORTED, "the FP32 path runs the Komissarov flux with the upwind schemes only");
 
     vlbm_t *h = new vlbm_t();
     h->nt = n_theta;
@@ -442,6 +482,8 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     h->guard = o.guard ? 1 : 0;
     h->rho_ref_opt = o.rho_ref;
     h->ty = (o.tile_rows == 4) ? 4 : 8;
+    h->scheme = o.scheme;
+    h->komissarov = o.komissarov ? 1 : 0;
     h->elem = (h->prec == VLBM_FP64) ? sizeof(double) : sizeof(float);
     h->L.nt = n_theta;
     h->L.np = n_phi;
@@ -483,6 +525,23 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     if ((rc = upload(h, &h->d_sin_ext, sext.data(), sext.size())) || (rc = upload(h, &h->d_cot, cot.data(), cot.size())) ||
         (rc = upload(h, &h->d_sin_t, h->sin_t.data(), h->sin_t.size())) ||
         (rc = upload(h, &h->d_cos_t, h->cos_t.data(), h->cos_t.size())))
+        return bail(rc);
+    // theta interfaces fi = 0..nt at theta = fi dtheta, northern half computed and mirrored (the
+    // Komissarov flux; sin = 0 exactly at both poles, cos = 0 exactly at the equator)
+    h->sin_f.assign(n_theta + 1, 0.0);
+    h->cos_f.assign(n_theta + 1, 0.0);
+    for (int fi = 0; fi <= n_theta; ++fi) {
+        const int m = n_theta - fi;
+        if (fi <= m) {
+            h->sin_f[fi] = (fi == 0) ? 0.0 : std::sin(fi * (M_PI / n_theta));
+            h->cos_f[fi] = (fi == m) ? 0.0 : std::cos(fi * (M_PI / n_theta));
+        } else {
+            h->sin_f[fi] = h->sin_f[m];
+            h->cos_f[fi] = -h->cos_f[m];
+        }
+    }
+    if ((rc = upload(h, &h->d_sin_f, h->sin_f.data(), h->sin_f.size())) ||
+        (rc = upload(h, &h->d_cos_f, h->cos_f.data(), h->cos_f.size())))
         return bail(rc);
     // polar filter rows
     if (h->filter) {
@@ -747,7 +806,9 @@ void vlbm_destroy(vlbm_t *h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
-    void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_rref, h->d_dsin, h->d_d2sin,
+    void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_sin_f, h->d_cos_f, h->d_isp,
+                    h->d_sfc,
+                    h->d_rref, h->d_dsin, h->d_d2sin,
                     h->d_face, h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
                     h->d_part, h->d_diag, h->d_flags};
     for (void *p : bufs)
@@ -873,7 +934,8 @@ void batch_enqueue_step(vlbm_batch_t *b)
 {
     const int ctas = batch_ctas(b);
     for (int st = 1; st <= 3; ++st) {
-        launch_batch_stage_f32(b->d_runs, b->d_tms, b->d_work, b->ntiles, b->vc, st, b->ty, ctas, b->d_flags, b->stream);
+        launch_batch_stage_f32(b->d_runs, b->d_tms, b->d_work, b->ntiles, b->vc, st, b->ty,
+                               b->runs.front()->scheme != VLBM_WENO5, ctas, b->d_flags, b->stream);
         // one polar-filter launch over the filtered rows of every run
         launch_batch_filter_f32(b->d_runs, b->d_fitems, b->nfitems, st, b->stream);
     }

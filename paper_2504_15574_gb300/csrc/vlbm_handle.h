@@ -22,6 +22,10 @@ struct vlbm {
     size_t arr_bytes = 0;
     // FP64 geometry
     double *d_sin_ext = nullptr, *d_cot = nullptr, *d_sin_t = nullptr, *d_cos_t = nullptr;
+    int scheme = VLBM_WENO5, komissarov = 0;
+    std::vector<double> sin_f, cos_f;                 // theta interfaces fi = 0..nt (theta = fi dtheta)
+    double *d_sin_f = nullptr, *d_cos_f = nullptr;
+    float *d_isp = nullptr, *d_sfc = nullptr;         // FP32 upwind schemes: 1/sin per padded row, interface sines
     std::vector<double> sin_t, cos_t;
     // FP32 tables
     float2 *d_rref = nullptr;

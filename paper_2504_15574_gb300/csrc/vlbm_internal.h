@@ -19,6 +19,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/vlbm.h"
+
 namespace vk {
 
 constexpr int NK = 16;   // D2Q16 populations
@@ -48,6 +50,9 @@ struct StageD {
     double dth, dph, R, tau, dt, eps;
     int stage;             // 1, 2, 3
     VelD c;
+    int scheme;            // VLBM_WENO5 .. VLBM_U3
+    int komissarov;        // theta flux in the Komissarov form
+    const double *sin_f, *cos_f;   // per theta interface fi = 0..nt (theta = fi dtheta)
 };
 void launch_stage_f64(const StageD &p, cudaStream_t s);
 
@@ -57,8 +62,9 @@ void launch_stage_f64(const StageD &p, cudaStream_t s);
 // Per theta face and upwind direction: the smoothness linear forms of the stencil applied to
 // sin(theta) and corr = 0.1 (P1-P2) + 0.3 (P3-P2) of sin(theta) (ideal-weight interpolant minus P2).
 struct FaceConst { float sa1, sb1, sa2, sb2, sa3, sb3, corr, pad; };
-// Per interior row: s = sin(theta), 1/s, 1/(R s dphi), cot(theta)/R, 1/(eps s^2).
-struct RowF { float s, inv_s, inv_dph, cotR, kphi, pad0, pad1, pad2; };
+// Per interior row: s = sin(theta), 1/s, 1/(R s dphi), cot(theta)/R, 1/(eps s^2), and for the
+// Komissarov theta flux kth = s / (R (cos theta_{i-1/2} - cos theta_{i+1/2})).
+struct RowF { float s, inv_s, inv_dph, cotR, kphi, kth, pad1, pad2; };
 // Per-run parameters of the FP32 stage: one solver, or one member of a batch.
 struct RunF {
     float2 *F, *A, *B;         // dg at the step start, after stage 1, after stage 2 (pair layout)
@@ -72,6 +78,11 @@ struct RunF {
     float2 wr[8];              // w_k rho_ref per pair
     float rho_ref;
     int tiles_x;               // tiles per row of this run for the launch's tile shape
+    // upwind schemes U1-U3 (Eq. fluxes_U1-3): interface value = lin0 x_up2 + lin1 x_up + lin2 x_down
+    float lin0, lin1, lin2;
+    int komissarov;            // theta flux in the Komissarov form (upwind schemes)
+    const float *isp;          // [nt + 2GR + 8] 1/sin at padded row pr (negative at ghost rows)
+    const float *sfc;          // [nt + 1 + 8] sin(fi dtheta) of theta interface fi (0 at both poles)
 };
 
 // Velocity-space constants shared by every run, pre-duplicated into pairs where they
@@ -91,12 +102,12 @@ constexpr int F32_TILE_COLS = 32;
 constexpr int F32_TILE_ROWS_MAX = 8;
 // One stage of one run, tile rows ty (4 or 8).  tm describes the stage input array.
 cudaError_t prepare_stage_f32();   // sets the kernels' dynamic shared-memory limits
-void launch_stage_f32(const CUtensorMap &tm_in, const RunF &run, const VelC &c, int stage, int ty,
+void launch_stage_f32(const CUtensorMap &tm_in, const RunF &run, const VelC &c, int stage, int ty, bool lin,
                       unsigned *err, cudaStream_t s);
 // One stage of a batch: a persistent grid of `ctas` CTAs walks `ntiles` work items
 // (run, tile) over the run table `runs` (device) and tensor maps `tms` ([run][3], device).
 void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
-                            int stage, int ty, int ctas, unsigned *err, cudaStream_t s);
+                            int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s);
 int stage_f32_max_ctas_per_sm(int ty);
 
 void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,

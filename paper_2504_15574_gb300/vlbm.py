@@ -36,7 +36,11 @@ class VlbmError(RuntimeError):
 class vlbm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("weno_eps", ctypes.c_double), ("radius", ctypes.c_double),
                 ("polar_filter", ctypes.c_int), ("guard", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("rho_ref", ctypes.c_double), ("tile_rows", ctypes.c_int)]
+                ("rho_ref", ctypes.c_double), ("tile_rows", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("komissarov", ctypes.c_int)]
+
+
+SCHEMES = {"weno5": 0, "u1": 1, "u2": 2, "u3": 3}
 
 
 class vlbm_diag(ctypes.Structure):
@@ -221,8 +225,10 @@ class Solver:
     """One vLBM solver on the GPU: ``Solver(n_theta, n_phi, tau, dt, precision="fp64"|"fp32")``."""
 
     def __init__(self, n_theta, n_phi, tau, dt, precision="fp64", eps=1e-6, R=1.0, polar_filter=False,
-                 guard=True, stream=None, rho_ref=0.0, tile_rows=0):
+                 guard=True, stream=None, rho_ref=0.0, tile_rows=0, scheme="weno5", komissarov=False):
         o = vlbm_default_options()
+        o.scheme = SCHEMES[scheme]
+        o.komissarov = int(bool(komissarov))
         o.precision = VLBM_FP32 if precision in ("fp32", VLBM_FP32) else VLBM_FP64
         o.weno_eps = float(eps)
         o.radius = float(R)
@@ -309,7 +315,8 @@ class Batch:
 
     grids: list of (n_theta, n_phi); tau, dt: scalars or per-run sequences."""
 
-    def __init__(self, grids, tau, dt, eps=1e-6, R=1.0, polar_filter=False, guard=True, stream=None):
+    def __init__(self, grids, tau, dt, eps=1e-6, R=1.0, polar_filter=False, guard=True, stream=None,
+                 scheme="weno5", komissarov=False):
         lib = load()
         n = len(grids)
         self.grids = [(int(a), int(b)) for a, b in grids]
@@ -324,6 +331,8 @@ class Batch:
         o.polar_filter = int(bool(polar_filter))
         o.guard = int(bool(guard))
         o.stream = stream
+        o.scheme = SCHEMES[scheme]
+        o.komissarov = int(bool(komissarov))
         self.b = _H()
         _bcheck(lib.vlbm_batch_create(n, nt, np_, _p(taus), _p(dts), ctypes.byref(o), ctypes.byref(self.b)))
 

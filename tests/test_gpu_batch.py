@@ -74,6 +74,18 @@ def test_batch_with_polar_filter_equals_standalone_solvers_bitwise(V):
     b.close()
 
 
+def test_batch_with_upwind_scheme_equals_standalone_solvers_bitwise(V):
+    """A batch runs the upwind-scheme stage (U3, Komissarov theta flux) for every member."""
+    b, dts = _batch(V, scheme="u3", komissarov=True)
+    b.set_schedule(8, 0)
+    b.step(20)
+    ref = _singles(V, dts, 20, scheme="u3", komissarov=True)
+    for r in range(len(GRIDS)):
+        for x, y in zip(b.moments(r), ref[r]):
+            assert np.array_equal(x, y), r
+    b.close()
+
+
 def test_autotuner_restores_state_and_caches(V, tmp_path):
     cache = str(tmp_path / "tune.json")
     b, dts = _batch(V)

@@ -29,11 +29,14 @@ def V():
     return vlbm
 
 
-def run_pair(V, nt, np_, tau, dt, ic, steps, precision="fp64", polar_filter=False, eps=1e-6):
+def run_pair(V, nt, np_, tau, dt, ic, steps, precision="fp64", polar_filter=False, eps=1e-6, scheme="weno5",
+             komissarov=False):
     rho, ut, up, T = ic
-    o = oracle.Oracle(nt, np_, tau=tau, dt=dt, eps=eps, polar_filter=polar_filter)
+    o = oracle.Oracle(nt, np_, tau=tau, dt=dt, eps=eps, polar_filter=polar_filter, scheme=scheme,
+                      komissarov=komissarov)
     o.init_moments(rho, ut, up, T)
-    g = V.Solver(nt, np_, tau, dt, precision=precision, polar_filter=polar_filter, eps=eps)
+    g = V.Solver(nt, np_, tau, dt, precision=precision, polar_filter=polar_filter, eps=eps, scheme=scheme,
+                 komissarov=komissarov)
     g.init_moments(rho, ut, up, T)
     o.step(steps)
     g.step(steps)
@@ -106,6 +109,33 @@ def test_fp64_checkpoint_resume_is_bitwise(V):
     assert np.array_equal(a.get_populations(), b.get_populations())
 
 
+SCHEME_CASES = [
+    # (scheme, komissarov, nt, np, filter)
+    ("u1", False, 13, 10, False),
+    ("u2", False, 16, 32, False),
+    ("u3", False, 16, 32, False),
+    ("u3", True, 16, 32, False),
+    ("u2", True, 13, 10, False),
+    ("weno5", True, 16, 32, False),
+    ("u3", True, 16, 32, True),
+]
+
+
+@pytest.mark.parametrize("scheme,komissarov,nt,np_,filt", SCHEME_CASES)
+def test_fp64_schemes_match_oracle(V, scheme, komissarov, nt, np_, filt):
+    """Upwind fluxes U1-U3 and the Komissarov theta flux (Sec. 3.5) on the FP64 path,
+    against the oracle's FP64 evaluation of the same scheme."""
+    tau = 0.02
+    dt = literal_dt(nt) / 2 if filt else clamped_dt(nt, np_, tau)
+    ic = inputs.gaussian_vortices(nt, np_, 3, umax=0.08)
+    o, g = run_pair(V, nt, np_, tau, dt, ic, 40, polar_filter=filt, scheme=scheme, komissarov=komissarov)
+    e = errors(g.moments(), o.moments())
+    assert e["rho"] <= FP64_TOL and e["u"] <= FP64_TOL, e
+    if komissarov:
+        # no flux crosses a pole
+        assert g.diagnostics()["pole_flux"] == 0.0
+
+
 # ---- FP32 deviation path ------------------------------------------------------------
 # Stated bounds of the FP32 deviation path (derivation in the design notes):
 # rounding of deviation-sized fluxes (2^-24 relative) amplified by 1/(R sin(theta) dtheta)
@@ -137,6 +167,44 @@ def test_fp32_matches_oracle_within_stated_bound(V, name):
     if tol_drho is not None:
         assert e["drho"] <= tol_drho, e
     assert e["u"] <= tol_u, e
+
+
+# stated bounds of the FP32 upwind schemes (same origin as above; ~3x the worst GB300 value)
+FP32_SCHEME_TOL = {"rho": 1e-7, "drho": 3e-4, "u": 3e-5}
+
+
+@pytest.mark.parametrize("scheme,komissarov,nt,np_,filt", SCHEME_CASES)
+def test_fp32_schemes_match_oracle_within_stated_bound(V, scheme, komissarov, nt, np_, filt):
+    """The FP32 deviation path with the upwind fluxes (the reference state's part of their linear
+    flux differences is exact in the FP64-derived tendency) and the Komissarov theta flux
+    (reconstruction on df = dg / sin, interface sines), against the oracle."""
+    if scheme == "weno5" and komissarov:
+        pytest.skip("the FP32 path runs the Komissarov flux with the upwind schemes only")
+    tau = 0.02
+    dt = literal_dt(nt) / 2 if filt else clamped_dt(nt, np_, tau)
+    ic = inputs.gaussian_vortices(nt, np_, 3, umax=0.08)
+    o, g = run_pair(V, nt, np_, tau, dt, ic, 40, precision="fp32", polar_filter=filt, scheme=scheme,
+                    komissarov=komissarov)
+    e = errors(g.moments(), o.moments())
+    print(scheme, komissarov, e)
+    assert e["rho"] <= FP32_SCHEME_TOL["rho"] and e["drho"] <= FP32_SCHEME_TOL["drho"], e
+    assert e["u"] <= FP32_SCHEME_TOL["u"], e
+
+
+def test_fp32_weno_with_komissarov_is_refused(V):
+    with pytest.raises(V.VlbmError) as ex:
+        V.Solver(16, 32, 0.02, 1e-4, precision="fp32", komissarov=True)
+    assert ex.value.code == -2
+
+
+def test_fp32_u3_komissarov_full_size_1024x2048_one_step(V):
+    """U3 with the Komissarov flux at the throughput grid size, every cell against the oracle."""
+    nt, np_, tau = 1024, 2048, 1e-3
+    o, g = run_pair(V, nt, np_, tau, literal_dt(nt), inputs.shock_cap(nt, np_), 1, precision="fp32",
+                    polar_filter=True, scheme="u3", komissarov=True)
+    e = errors(g.moments(), o.moments())
+    assert e["rho"] <= 1e-6 and e["drho"] <= 1e-6, e
+    assert e["u"] <= 1e-5, e
 
 
 def test_fp32_full_size_1024x2048_one_step(V):
