@@ -77,10 +77,15 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def committed_traffic():
-    """DRAM bytes of the three stage launches of one step from the committed ncu summary
-    (null there once the kernel has changed since the capture)."""
-    path = os.path.join(ROOT, "profiles", "stage_f32_1024x2048.md")
+def committed_traffic(args):
+    """DRAM bytes of the three stage launches of one step from the committed ncu summary of
+    this scheme at 1024 x 2048 (null there once the kernel has changed since the capture,
+    and null for another grid or a scheme without a summary)."""
+    if (NT, NP) != (1024, 2048):
+        return None
+    name = "stage_f32_1024x2048.md" if args.scheme == "weno5" else \
+        f"stage_f32_{args.scheme}{'k' if args.komissarov else ''}_1024x2048.md"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         for line in open(path):
             if line.startswith("traffic_bytes_per_step:"):
@@ -229,7 +234,7 @@ def run_ours(args):
     alg_bytes = cells * sum(BYTES_PER_CELL_STAGE)
     achieved = alg_bytes / (sum(stage_ms) * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
-    traffic = committed_traffic()
+    traffic = committed_traffic(args)
 
     # end to end through the C ABI with host buffers: H2D of the moments, K steps, D2H of the moments
     e2e_steps = args.steps

@@ -170,7 +170,7 @@ def test_fp32_matches_oracle_within_stated_bound(V, name):
 
 
 # stated bounds of the FP32 upwind schemes (same origin as above; ~3x the worst GB300 value)
-FP32_SCHEME_TOL = {"rho": 1e-7, "drho": 3e-4, "u": 3e-5}
+FP32_SCHEME_TOL = {"rho": 5e-8, "drho": 2e-5, "u": 1e-5}
 
 
 @pytest.mark.parametrize("scheme,komissarov,nt,np_,filt", SCHEME_CASES)
