@@ -50,6 +50,11 @@ def _load():
         P = ctypes.POINTER(ctypes.c_double)
         lib.vo_create.restype = ctypes.c_void_p
         lib.vo_create.argtypes = [ctypes.c_int, ctypes.c_int, D, D, D, D, ctypes.c_int]
+        lib.vo_create_q.restype = ctypes.c_void_p
+        lib.vo_create_q.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D, D, D, ctypes.c_int]
+        lib.vo_quadrature_q.argtypes = [ctypes.c_int, P, P]
+        lib.vo_kernels_q.argtypes = [ctypes.c_int, P, P]
+        lib.vo_equilibrium_q.argtypes = [ctypes.c_int, D, D, D, D, P]
         lib.vo_destroy.argtypes = [ctypes.c_void_p]
         lib.vo_set_scheme.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         lib.vo_quadrature.argtypes = [P, P]
@@ -86,22 +91,22 @@ def _f64(a, shape=None):
     return a
 
 
-def quadrature():
-    """Velocities (ascending roots of H_4) and 1-D weights, Eq. (GH_weights)."""
+def quadrature(q=4):
+    """Velocities (ascending roots of H_Q) and 1-D weights, Eq. (GH_weights); Q = 4 or 3."""
     lib = _load()
-    v = np.zeros(4)
-    w = np.zeros(4)
-    lib.vo_quadrature(_ptr(v), _ptr(w))
+    v = np.zeros(q)
+    w = np.zeros(q)
+    lib.vo_quadrature_q(int(q), _ptr(v), _ptr(w))
     return v, w
 
 
-def kernels():
-    """K^H and Ktilde^H of Eqs. (KH), (KtildeH) as 4x4 arrays."""
+def kernels(q=4):
+    """K^H and Ktilde^H of Eqs. (KH), (KtildeH) as Q x Q arrays."""
     lib = _load()
-    K = np.zeros(16)
-    Kt = np.zeros(16)
-    lib.vo_kernels(_ptr(K), _ptr(Kt))
-    return K.reshape(4, 4), Kt.reshape(4, 4)
+    K = np.zeros(q * q)
+    Kt = np.zeros(q * q)
+    lib.vo_kernels_q(int(q), _ptr(K), _ptr(Kt))
+    return K.reshape(q, q), Kt.reshape(q, q)
 
 
 def weno5(a, b, c, d, e, eps=1e-6):
@@ -109,10 +114,10 @@ def weno5(a, b, c, d, e, eps=1e-6):
     return _load().vo_weno5(float(a), float(b), float(c), float(d), float(e), float(eps))
 
 
-def equilibrium(n, ut, up, T=1.0):
-    """Populations of the third-order Hermite equilibrium (T = 1: Eq. feq_Q=4)."""
-    out = np.zeros(NK)
-    _load().vo_equilibrium(float(n), float(ut), float(up), float(T), _ptr(out))
+def equilibrium(n, ut, up, T=1.0, q=4):
+    """Populations of the Hermite equilibrium of order Q (T = 1: Eq. feq_Q=4, or Eq. feq_Q=3)."""
+    out = np.zeros(q * q)
+    _load().vo_equilibrium_q(int(q), float(n), float(ut), float(up), float(T), _ptr(out))
     return out
 
 
@@ -122,13 +127,14 @@ class Oracle:
     SCHEMES = {"weno5": 0, "u1": 1, "u2": 2, "u3": 3}
 
     def __init__(self, n_theta, n_phi, tau, dt, eps=1e-6, R=1.0, polar_filter=False, scheme="weno5",
-                 komissarov=False):
+                 komissarov=False, q=4):
         lib = _load()
         self._lib = lib
+        self.q, self.nk = int(q), int(q) * int(q)
         self.n_theta, self.n_phi = int(n_theta), int(n_phi)
         self.tau, self.dt, self.eps, self.R = float(tau), float(dt), float(eps), float(R)
-        h = lib.vo_create(self.n_theta, self.n_phi, self.tau, self.dt, self.eps, self.R,
-                          1 if polar_filter else 0)
+        h = lib.vo_create_q(self.q, self.n_theta, self.n_phi, self.tau, self.dt, self.eps, self.R,
+                            1 if polar_filter else 0)
         if not h:
             raise ValueError("oracle: invalid arguments")
         self._h = ctypes.c_void_p(h)
@@ -159,12 +165,12 @@ class Oracle:
             raise RuntimeError("oracle init_moments failed")
 
     def set_populations(self, f):
-        f = _f64(f, (NK,) + self.shape)
+        f = _f64(f, (self.nk,) + self.shape)
         if self._lib.vo_set_populations(self._h, _ptr(f)):
             raise RuntimeError("oracle set_populations failed")
 
     def get_populations(self):
-        f = np.zeros((NK,) + self.shape)
+        f = np.zeros((self.nk,) + self.shape)
         self._lib.vo_get_populations(self._h, _ptr(f))
         return f
 
@@ -180,13 +186,13 @@ class Oracle:
         return (rho, ut, up, T) if with_T else (rho, ut, up)
 
     def operator(self, g):
-        """L[g] plus interface fluxes (Ft: [16, nt+1, np], Fp: [16, nt, np+1]) and
+        """L[g] plus interface fluxes (Ft: [Q^2, nt+1, np], Fp: [Q^2, nt, np+1]) and
         the pole mass-flux rate."""
-        g = _f64(g, (NK,) + self.shape)
+        g = _f64(g, (self.nk,) + self.shape)
         nt, np_ = self.shape
-        L = np.zeros((NK, nt, np_))
-        Ft = np.zeros((NK, nt + 1, np_))
-        Fp = np.zeros((NK, nt, np_ + 1))
+        L = np.zeros((self.nk, nt, np_))
+        Ft = np.zeros((self.nk, nt + 1, np_))
+        Fp = np.zeros((self.nk, nt, np_ + 1))
         m = self._lib.vo_operator(self._h, _ptr(g), _ptr(L), _ptr(Ft), _ptr(Fp))
         return L, Ft, Fp, m
 

@@ -52,8 +52,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define NV 4
-#define NK 16
+#define NV 4   /* largest quadrature order (Q = 4); Q = 3 uses the first 3 entries */
+#define NK 16  /* largest population count Q^2 */
 
 /* ------------------------------------------------------------------------- */
 /* Velocity space: Gauss-Hermite Q = 4 (Sec. 3.1, App. A.2)                   */
@@ -80,74 +80,94 @@ static double factorial(int l)
     return r;
 }
 
-/* Roots of H_4(x) = x^4 - 6x^2 + 3 in ascending order and the weights
- * w = Q!/H_5(v)^2 (Eq. GH_weights). */
-void vo_quadrature(double v[NV], double w[NV])
+/* Roots of H_Q in ascending order and the weights w = Q!/H_{Q+1}(v)^2 (Eq. GH_weights):
+ * Q = 4, H_4(x) = x^4 - 6x^2 + 3 (App. A.2, Tab. velocity_set_Q=4); Q = 3, H_3(x) = x^3 - 3x,
+ * v = (-sqrt 3, 0, sqrt 3) (App. A.1, Tab. velocity_set_Q=3). */
+void vo_quadrature_q(int q, double *v, double *w)
 {
-    double big = sqrt(3.0 + sqrt(6.0));
-    double small = sqrt(3.0 - sqrt(6.0));
-    v[0] = -big;
-    v[1] = -small;
-    v[2] = small;
-    v[3] = big;
-    for (int a = 0; a < NV; ++a) {
-        double h5 = hermite(5, v[a]);
-        w[a] = factorial(4) / (h5 * h5);
+    if (q == 3) {
+        v[0] = -sqrt(3.0);
+        v[1] = 0.0;
+        v[2] = sqrt(3.0);
+    } else {
+        double big = sqrt(3.0 + sqrt(6.0));
+        double small = sqrt(3.0 - sqrt(6.0));
+        v[0] = -big;
+        v[1] = -small;
+        v[2] = small;
+        v[3] = big;
+    }
+    for (int a = 0; a < q; ++a) {
+        double h = hermite(q + 1, v[a]);
+        w[a] = factorial(q) / (h * h);
     }
 }
 
-/* Kernels of Eqs. (KH) and (KtildeH), row-major K[k*4 + k']. */
-void vo_kernels(double K[NV * NV], double Kt[NV * NV])
+void vo_quadrature(double v[NV], double w[NV]) { vo_quadrature_q(4, v, w); }
+
+/* Kernels of Eqs. (KH) and (KtildeH) for order Q, row-major K[k*Q + k']. */
+void vo_kernels_q(int q, double *K, double *Kt)
 {
     double v[NV], w[NV];
-    vo_quadrature(v, w);
-    for (int k = 0; k < NV; ++k) {
-        for (int kp = 0; kp < NV; ++kp) {
+    vo_quadrature_q(q, v, w);
+    for (int k = 0; k < q; ++k) {
+        for (int kp = 0; kp < q; ++kp) {
             double sk = 0.0, skt = 0.0;
-            for (int l = 0; l < NV; ++l) {
+            for (int l = 0; l < q; ++l) {
                 double hk = hermite(l + 1, v[k]);
                 sk += hk * hermite(l, v[kp]) / factorial(l);
                 double inner = hermite(l + 1, v[kp]);
                 if (l > 0) inner += (double)l * hermite(l - 1, v[kp]);
                 skt += hk * inner / factorial(l);
             }
-            K[k * NV + kp] = -w[k] * sk;
-            Kt[k * NV + kp] = -w[k] * skt;
+            K[k * q + kp] = -w[k] * sk;
+            Kt[k * q + kp] = -w[k] * skt;
         }
     }
 }
 
-/* BGK target, Eq. (feq_Q=4), T0 = 1. */
-static double feq_k(double n, double wk, double va, double vb, double ut, double up)
+void vo_kernels(double K[NV * NV], double Kt[NV * NV]) { vo_kernels_q(4, K, Kt); }
+
+/* BGK target, T0 = 1: Eq. (feq_Q=4) to third order for Q = 4, Eq. (feq_Q=3) to second
+ * order for Q = 3. */
+static double feq_k(int q, double n, double wk, double va, double vb, double ut, double up)
 {
     double xi = va * ut + vb * up;
     double u2 = ut * ut + up * up;
+    if (q == 3) return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2));
     return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
 }
 
 /* Initial state for a temperature T (reading R11): the Hermite projection of
- * the Maxwellian to third order with a^(2) = n[uu + (T-1) delta] and
- * a^(3) = n[uuu + (T-1)(u delta)_sym] (Eqs. feq_series, feq_discrete with the
- * coefficients of a Maxwellian at temperature T). Reduces to feq_k at T = 1. */
-static double finit_k(double n, double wk, double va, double vb, double ut, double up, double T)
+ * the Maxwellian with a^(2) = n[uu + (T-1) delta] and a^(3) = n[uuu + (T-1)(u delta)_sym]
+ * (Eqs. feq_series, feq_discrete with the coefficients of a Maxwellian at temperature T),
+ * to the order of the quadrature (third for Q = 4, second for Q = 3).  Reduces to feq_k
+ * at T = 1. */
+static double finit_k(int q, double n, double wk, double va, double vb, double ut, double up, double T)
 {
-    if (T == 1.0) return feq_k(n, wk, va, vb, ut, up);
+    if (T == 1.0) return feq_k(q, n, wk, va, vb, ut, up);
     double xi = va * ut + vb * up;
     double u2 = ut * ut + up * up;
     double v2 = va * va + vb * vb;
     double dT = T - 1.0;
     double second = xi * xi - u2 + dT * (v2 - 2.0);
+    if (q == 3) return n * wk * (1.0 + xi + 0.5 * second);
     double third = xi * (xi * xi - 3.0 * u2) + 3.0 * dT * xi * (v2 - 4.0);
     return n * wk * (1.0 + xi + 0.5 * second + third / 6.0);
 }
 
-void vo_equilibrium(double n, double ut, double up, double T, double out[NK])
+void vo_equilibrium_q(int q, double n, double ut, double up, double T, double *out)
 {
     double v[NV], w[NV];
-    vo_quadrature(v, w);
-    for (int a = 0; a < NV; ++a)
-        for (int b = 0; b < NV; ++b)
-            out[4 * a + b] = finit_k(n, w[a] * w[b], v[a], v[b], ut, up, T);
+    vo_quadrature_q(q, v, w);
+    for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b)
+            out[q * a + b] = finit_k(q, n, w[a] * w[b], v[a], v[b], ut, up, T);
+}
+
+void vo_equilibrium(double n, double ut, double up, double T, double out[NK])
+{
+    vo_equilibrium_q(4, n, ut, up, T, out);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -180,6 +200,7 @@ double vo_weno5(double a, double b, double c, double d, double e, double eps)
 enum { VO_WENO5 = 0, VO_U1 = 1, VO_U2 = 2, VO_U3 = 3 };
 
 typedef struct vo_state {
+    int q, nk;             /* quadrature order Q (3: D2Q9, 4: D2Q16) and Q^2 populations */
     int nt, np;
     double tau, dt, eps, R;
     int filter;            /* polar ring filter on/off (not in the paper) */
@@ -222,12 +243,15 @@ static int filter_block(const vo_state *o, int i)
     return b;
 }
 
-vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R, int filter)
+vo_state *vo_create_q(int q, int nt, int np, double tau, double dt, double eps, double R, int filter)
 {
+    if (q != 3 && q != 4) return NULL;
     if (nt < 6 || np < 1 || (np != 1 && np % 2 != 0)) return NULL;
     if (!(tau > 0.0) || !(dt > 0.0) || !(eps > 0.0) || !(R > 0.0)) return NULL;
     vo_state *o = (vo_state *)calloc(1, sizeof(vo_state));
     if (!o) return NULL;
+    o->q = q;
+    o->nk = q * q;
     o->nt = nt;
     o->np = np;
     o->tau = tau;
@@ -237,8 +261,8 @@ vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R,
     o->filter = filter ? 1 : 0;
     o->dth = M_PI / (double)nt;
     o->dph = 2.0 * M_PI / (double)np;
-    vo_quadrature(o->v, o->w);
-    vo_kernels(o->K, o->Kt);
+    vo_quadrature_q(q, o->v, o->w);
+    vo_kernels_q(q, o->K, o->Kt);
     o->sin_t = (double *)malloc(sizeof(double) * nt);
     o->cos_t = (double *)malloc(sizeof(double) * nt);
     o->cot_t = (double *)malloc(sizeof(double) * nt);
@@ -272,13 +296,13 @@ vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R,
             }
         }
     for (int i = 0; i < nt; ++i) o->fblock[i] = filter_block(o, i);
-    size_t n = plane(o) * NK;
+    size_t n = plane(o) * (size_t)o->nk;
     o->f = (double *)calloc(n, sizeof(double));
     o->f1 = (double *)calloc(n, sizeof(double));
     o->f2 = (double *)calloc(n, sizeof(double));
     o->L = (double *)calloc(n, sizeof(double));
-    o->Ft = (double *)calloc((size_t)NK * (size_t)(nt + 1) * (size_t)np, sizeof(double));
-    o->Fp = (double *)calloc((size_t)NK * (size_t)nt * (size_t)(np + 1), sizeof(double));
+    o->Ft = (double *)calloc((size_t)o->nk * (size_t)(nt + 1) * (size_t)np, sizeof(double));
+    o->Fp = (double *)calloc((size_t)o->nk * (size_t)nt * (size_t)(np + 1), sizeof(double));
     if (!o->sin_t || !o->cos_t || !o->cot_t || !o->sin_f || !o->cos_f || !o->fblock || !o->f || !o->f1 ||
         !o->f2 || !o->L || !o->Ft || !o->Fp) {
         free(o->sin_t); free(o->cos_t); free(o->cot_t); free(o->sin_f); free(o->cos_f); free(o->fblock);
@@ -287,6 +311,11 @@ vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R,
         return NULL;
     }
     return o;
+}
+
+vo_state *vo_create(int nt, int np, double tau, double dt, double eps, double R, int filter)
+{
+    return vo_create_q(4, nt, np, tau, dt, eps, R, filter);
 }
 
 void vo_destroy(vo_state *o)
@@ -339,7 +368,7 @@ static double g_theta(const vo_state *o, const double *f, int k, int i, int j)
     if (i >= 0 && i < nt) return o->sin_t[i] * f[idx(o, k, i, j)];
     int half = o->np / 2;
     int jj = wrap_col(o, j + half);
-    int kk = NK - 1 - k;
+    int kk = o->nk - 1 - k;
     int ii;
     if (i < 0) ii = -1 - i;           /* theta_{-m} = -theta_{m-1} */
     else ii = 2 * nt - 1 - i;         /* theta beyond pi mirrors into the last rows */
@@ -354,7 +383,7 @@ static double f_theta(const vo_state *o, const double *f, int k, int i, int j)
     if (i >= 0 && i < nt) return f[idx(o, k, i, j)];
     int jj = wrap_col(o, j + o->np / 2);
     int ii = (i < 0) ? -1 - i : 2 * nt - 1 - i;
-    return f[idx(o, NK - 1 - k, ii, jj)];
+    return f[idx(o, o->nk - 1 - k, ii, jj)];
 }
 
 /* Interface value from the upwind-ordered values a..e (a furthest upwind, c the
@@ -380,7 +409,7 @@ static double recon(const vo_state *o, double a, double b, double c, double d, d
  * (Eq. Komissarov_scheme with V = v_theta). */
 static double flux_theta(const vo_state *o, const double *f, int k, int i, int j)
 {
-    double vth = o->v[k / 4];
+    double vth = o->v[k / o->q];
     double (*val)(const vo_state *, const double *, int, int, int) = o->komissarov ? f_theta : g_theta;
     double gh;
     if (vth > 0.0) {
@@ -396,7 +425,7 @@ static double flux_theta(const vo_state *o, const double *f, int k, int i, int j
 /* Phi flux through the interface between columns j-1 and j (j = 0..np). */
 static double flux_phi(const vo_state *o, const double *f, int k, int i, int j)
 {
-    double vph = o->v[k % 4];
+    double vph = o->v[k % o->q];
     const double *row = f + idx(o, k, i, 0);
     double gh;
     if (vph > 0.0) {
@@ -420,13 +449,13 @@ static double operator_L(vo_state *o, const double *g, double *L)
     /* interface fluxes */
 #pragma omp parallel for schedule(static)
     for (int i = 0; i <= nt; ++i)
-        for (int k = 0; k < NK; ++k)
+        for (int k = 0; k < o->nk; ++k)
             for (int j = 0; j < np; ++j)
                 o->Ft[((size_t)k * (size_t)(nt + 1) + (size_t)i) * (size_t)np + (size_t)j] =
                     flux_theta(o, g, k, i, j);
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < nt; ++i)
-        for (int k = 0; k < NK; ++k)
+        for (int k = 0; k < o->nk; ++k)
             for (int j = 0; j <= np; ++j)
                 o->Fp[((size_t)k * (size_t)nt + (size_t)i) * (size_t)(np + 1) + (size_t)j] =
                     flux_phi(o, g, k, i, j);
@@ -435,24 +464,24 @@ static double operator_L(vo_state *o, const double *g, double *L)
     for (int i = 0; i < nt; ++i) {
         for (int j = 0; j < np; ++j) {
             double gk[NK];
-            for (int k = 0; k < NK; ++k) gk[k] = g[idx(o, k, i, j)];
+            for (int k = 0; k < o->nk; ++k) gk[k] = g[idx(o, k, i, j)];
             /* moments, Eq. (f_moments_sum), summed in ascending k */
             double n = 0.0, jt = 0.0, jp = 0.0;
-            for (int k = 0; k < NK; ++k) {
+            for (int k = 0; k < o->nk; ++k) {
                 n += gk[k];
-                jt += gk[k] * o->v[k / 4];
-                jp += gk[k] * o->v[k % 4];
+                jt += gk[k] * o->v[k / o->q];
+                jp += gk[k] * o->v[k % o->q];
             }
             double ut = jt / n, up = jp / n;
-            for (int k = 0; k < NK; ++k) {
-                int a = k / 4, b = k % 4;
+            for (int k = 0; k < o->nk; ++k) {
+                int q = o->q, a = k / q, b = k % q;
                 double va = o->v[a], vb = o->v[b];
-                double feq = feq_k(n, o->w[a] * o->w[b], va, vb, ut, up);
+                double feq = feq_k(q, n, o->w[a] * o->w[b], va, vb, ut, up);
                 /* velocity derivatives, Eq. (df) */
                 double kg = 0.0, ktg = 0.0;
-                for (int m = 0; m < NV; ++m) {
-                    kg += o->K[a * NV + m] * gk[4 * m + b];
-                    ktg += o->Kt[b * NV + m] * gk[4 * a + m];
+                for (int m = 0; m < q; ++m) {
+                    kg += o->K[a * q + m] * gk[q * m + b];
+                    ktg += o->Kt[b * q + m] * gk[q * a + m];
                 }
                 double force = o->cot_t[i] / R * (vb * vb * kg - va * ktg);
                 double ftp = o->Ft[((size_t)k * (size_t)(nt + 1) + (size_t)(i + 1)) * (size_t)np + (size_t)j];
@@ -469,7 +498,7 @@ static double operator_L(vo_state *o, const double *g, double *L)
     }
 
     double s = 0.0;
-    for (int k = 0; k < NK; ++k)
+    for (int k = 0; k < o->nk; ++k)
         for (int j = 0; j < np; ++j) {
             double fs = o->Ft[((size_t)k * (size_t)(nt + 1) + (size_t)nt) * (size_t)np + (size_t)j];
             double fn = o->Ft[((size_t)k * (size_t)(nt + 1)) * (size_t)np + (size_t)j];
@@ -489,7 +518,7 @@ static void polar_filter(vo_state *o, double *g)
     for (int i = 0; i < nt; ++i) {
         int b = o->fblock[i];
         if (b <= 1) continue;
-        for (int k = 0; k < NK; ++k) {
+        for (int k = 0; k < o->nk; ++k) {
             double *row = g + idx(o, k, i, 0);
             for (int j0 = 0; j0 < np; j0 += b) {
                 double s = 0.0;
@@ -504,7 +533,7 @@ static void polar_filter(vo_state *o, double *g)
 /* One SSP-RK3 step, Sec. 3.7. */
 static void rk3_step(vo_state *o)
 {
-    size_t n = plane(o) * NK;
+    size_t n = plane(o) * (size_t)o->nk;
     double dt = o->dt;
     double *f = o->f, *f1 = o->f1, *f2 = o->f2, *L = o->L;
 
@@ -537,7 +566,7 @@ static double total_mass(const vo_state *o, const double *f);
 int vo_set_populations(vo_state *o, const double *src)
 {
     if (!o || !src) return -1;
-    memcpy(o->f, src, plane(o) * NK * sizeof(double));
+    memcpy(o->f, src, plane(o) * (size_t)o->nk * sizeof(double));
     o->t = 0.0;
     o->steps = 0;
     o->pole_budget = 0.0;
@@ -548,7 +577,7 @@ int vo_set_populations(vo_state *o, const double *src)
 int vo_get_populations(const vo_state *o, double *dst)
 {
     if (!o || !dst) return -1;
-    memcpy(dst, o->f, plane(o) * NK * sizeof(double));
+    memcpy(dst, o->f, plane(o) * (size_t)o->nk * sizeof(double));
     return 0;
 }
 
@@ -559,10 +588,10 @@ int vo_init_moments(vo_state *o, const double *rho, const double *ut, const doub
         for (int j = 0; j < o->np; ++j) {
             size_t c = (size_t)i * (size_t)o->np + (size_t)j;
             double temp = T ? T[c] : 1.0;
-            for (int a = 0; a < NV; ++a)
-                for (int b = 0; b < NV; ++b)
-                    o->f[idx(o, 4 * a + b, i, j)] =
-                        finit_k(rho[c], o->w[a] * o->w[b], o->v[a], o->v[b], ut[c], up[c], temp);
+            for (int a = 0; a < o->q; ++a)
+                for (int b = 0; b < o->q; ++b)
+                    o->f[idx(o, o->q * a + b, i, j)] =
+                        finit_k(o->q, rho[c], o->w[a] * o->w[b], o->v[a], o->v[b], ut[c], up[c], temp);
         }
     o->t = 0.0;
     o->steps = 0;
@@ -585,19 +614,19 @@ int vo_moments(const vo_state *o, double *rho, double *ut, double *up, double *T
         for (int j = 0; j < o->np; ++j) {
             size_t c = (size_t)i * (size_t)o->np + (size_t)j;
             double n = 0.0, jt = 0.0, jp = 0.0;
-            for (int k = 0; k < NK; ++k) {
+            for (int k = 0; k < o->nk; ++k) {
                 double fk = o->f[idx(o, k, i, j)];
                 n += fk;
-                jt += fk * o->v[k / 4];
-                jp += fk * o->v[k % 4];
+                jt += fk * o->v[k / o->q];
+                jp += fk * o->v[k % o->q];
             }
             rho[c] = n;
             ut[c] = jt / n;
             up[c] = jp / n;
             if (T) {
                 double e = 0.0;
-                for (int k = 0; k < NK; ++k) {
-                    double ct = o->v[k / 4] - ut[c], cp = o->v[k % 4] - up[c];
+                for (int k = 0; k < o->nk; ++k) {
+                    double ct = o->v[k / o->q] - ut[c], cp = o->v[k % o->q] - up[c];
                     e += o->f[idx(o, k, i, j)] * (ct * ct + cp * cp);
                 }
                 T[c] = e / (2.0 * n);
@@ -614,8 +643,8 @@ double vo_operator(vo_state *o, const double *g, double *L, double *Ft, double *
 {
     double *Lbuf = L ? L : o->L;
     double m = operator_L(o, g, Lbuf);
-    if (Ft) memcpy(Ft, o->Ft, sizeof(double) * (size_t)NK * (size_t)(o->nt + 1) * (size_t)o->np);
-    if (Fp) memcpy(Fp, o->Fp, sizeof(double) * (size_t)NK * (size_t)o->nt * (size_t)(o->np + 1));
+    if (Ft) memcpy(Ft, o->Ft, sizeof(double) * (size_t)o->nk * (size_t)(o->nt + 1) * (size_t)o->np);
+    if (Fp) memcpy(Fp, o->Fp, sizeof(double) * (size_t)o->nk * (size_t)o->nt * (size_t)(o->np + 1));
     return m;
 }
 
@@ -627,7 +656,7 @@ static double total_mass(const vo_state *o, const double *f)
         double row = 0.0;
         for (int j = 0; j < o->np; ++j) {
             double n = 0.0;
-            for (int k = 0; k < NK; ++k) n += f[idx(o, k, i, j)];
+            for (int k = 0; k < o->nk; ++k) n += f[idx(o, k, i, j)];
             row += n;
         }
         m += o->sin_t[i] * row * area;
@@ -651,10 +680,10 @@ int vo_diagnostics(const vo_state *o, double out[10])
             double ph = ((double)j + 0.5) * o->dph;
             double sp = sin(ph), cp = cos(ph);
             double n = 0.0, jt = 0.0, jp = 0.0, e = 0.0;
-            for (int k = 0; k < NK; ++k) {
+            for (int k = 0; k < o->nk; ++k) {
                 double fk = o->f[idx(o, k, i, j)];
                 if (!isfinite(fk)) bad = 1;
-                double va = o->v[k / 4], vb = o->v[k % 4];
+                double va = o->v[k / o->q], vb = o->v[k % o->q];
                 n += fk;
                 jt += fk * va;
                 jp += fk * vb;
