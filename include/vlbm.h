@@ -56,7 +56,7 @@ extern "C" {
 #define VLBM_ERR_TIMEOUT     -5  /* a bounded device-side wait gave up */
 
 /* Velocity sets (App. A): the enum value is the quadrature order Q. */
-#define VLBM_D2Q9  3             /* reserved: returns VLBM_ERR_UNSUPPORTED */
+#define VLBM_D2Q9  3             /* Q = 3 (App. A.1): 9 populations, second-order equilibrium; FP64 path */
 #define VLBM_D2Q16 4
 
 /* Advection schemes (Sec. 3.5): WENO-5, Eqs. (fluxes_W5)-(WENO5_sigma), or the
@@ -107,7 +107,8 @@ typedef struct vlbm_diag {
 VLBM_API void vlbm_default_options(vlbm_options *opt);
 
 /* Creates a solver on an n_theta x n_phi grid.
- *   velocity_set: VLBM_D2Q16 (VLBM_D2Q9 -> VLBM_ERR_UNSUPPORTED).
+ *   velocity_set: VLBM_D2Q16 (16 populations, Eq. feq_Q=4), or VLBM_D2Q9 (9 populations,
+ *   Eq. feq_Q=3, kernels of Eq. Q3_kernels; VLBM_FP64 only, VLBM_FP32 -> VLBM_ERR_UNSUPPORTED).
  *   n_theta >= 6 (three WENO ghost rows per pole), n_phi even or 1,
  *   n_theta <= 65536, n_phi <= 65536; tau > 0 (BGK relaxation time, Sec. 3.2);
  *   dt > 0 (the caller chooses it; see vlbm_max_stable_dt); opt may be NULL.
@@ -116,8 +117,8 @@ VLBM_API void vlbm_default_options(vlbm_options *opt);
 VLBM_API int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
                 const vlbm_options *opt, vlbm_t **out);
 
-/* Sets f to the equilibrium of the given moments (Eq. feq_Q=4); with T != NULL
- * the third-order Hermite projection of a Maxwellian at temperature T is used
+/* Sets f to the equilibrium of the given moments (Eq. feq_Q=4, or feq_Q=3 for D2Q9); with T != NULL
+ * the Hermite projection (third order; second for D2Q9) of a Maxwellian at temperature T is used
  * instead (the BGK target stays at T0 = 1).  Resets t, steps and the pole-flux
  * budget.  Host arrays, layout [n_theta][n_phi]; T may be NULL. */
 VLBM_API int vlbm_init_moments(vlbm_t *h, const double *rho, const double *u_theta, const double *u_phi,
@@ -140,7 +141,7 @@ VLBM_API int vlbm_sync(vlbm_t *h);
  * if T != NULL, T = sum_k f_k |v_k - u|^2 / (2 n).  Host outputs [n_theta][n_phi]. */
 VLBM_API int vlbm_moments(vlbm_t *h, double *rho, double *u_theta, double *u_phi, double *T);
 
-/* Copies the populations out / in as FP64 host arrays [16][n_theta][n_phi]
+/* Copies the populations out / in as FP64 host arrays [Q^2][n_theta][n_phi] (k = Q k_theta + k_phi)
  * (checkpoint / resume; the FP32 path converts to and from f = w_k rho_ref + delta f).
  * vlbm_set_populations resets t, steps and the pole-flux budget. */
 VLBM_API int vlbm_get_populations(vlbm_t *h, double *f);

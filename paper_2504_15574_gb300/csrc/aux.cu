@@ -20,11 +20,11 @@ __device__ __forceinline__ void ghost_source(const Layout &L, int k, int r, int 
     rs = r;
     if (r < 0) {
         rs = -1 - r;
-        ks = NK - 1 - k;
+        ks = L.nk - 1 - k;
         shift = L.np / 2;
     } else if (r >= L.nt) {
         rs = 2 * L.nt - 1 - r;
-        ks = NK - 1 - k;
+        ks = L.nk - 1 - k;
         shift = L.np / 2;
     }
     int cc = (c + shift) % L.np;
@@ -77,8 +77,8 @@ __global__ void diag_rows_kernel(const double *f, const Layout L, const double *
         double sp, cp;
         sincos(ph, &sp, &cp);
         double n = 0.0, jt = 0.0, jp = 0.0, e = 0.0, bad = 0.0;
-        for (int k = 0; k < NK; ++k) {
-            const double va = c.v[k / 4], vb = c.v[k % 4];
+        for (int k = 0; k < c.q * c.q; ++k) {
+            const double va = c.v[k / c.q], vb = c.v[k % c.q];
             const double fk = f[L.at(k, i, j)];
             if (!isfinite(fk)) bad = 1.0;
             n += fk;
@@ -164,19 +164,19 @@ __global__ void pole_budget_kernel(const double *pole3, int np, double R, double
 
 void launch_fill_ghosts_f64(double *f, const Layout &L, cudaStream_t s)
 {
-    dim3 grid((L.np + 2 * GC + 127) / 128, L.nt + 2 * GR, NK);
+    dim3 grid((L.np + 2 * GC + 127) / 128, L.nt + 2 * GR, L.nk);
     fill_ghosts_kernel<<<grid, 128, 0, s>>>(f, L);
 }
 
 void launch_pack_f64(const double *f, const Layout &L, double *dense, cudaStream_t s)
 {
-    dim3 grid((L.np + 127) / 128, L.nt, NK);
+    dim3 grid((L.np + 127) / 128, L.nt, L.nk);
     pack_f64_kernel<<<grid, 128, 0, s>>>(f, L, dense);
 }
 
 void launch_unpack_f64(const double *dense, const Layout &L, double *f, cudaStream_t s)
 {
-    dim3 grid((L.np + 127) / 128, L.nt, NK);
+    dim3 grid((L.np + 127) / 128, L.nt, L.nk);
     unpack_f64_kernel<<<grid, 128, 0, s>>>(dense, L, f);
 }
 

@@ -63,7 +63,7 @@ __device__ __forceinline__ void store_with_images(T *f, const Layout &L, int k, 
         int jj = j + np / 2;
         if (jj >= np) jj -= np;
         int r = (i < GR) ? (-1 - i) : (2 * L.nt - 1 - i);
-        put_row(NK - 1 - k, r, jj);
+        put_row(L.nk - 1 - k, r, jj);
     }
 }
 
@@ -76,16 +76,15 @@ __global__ void __launch_bounds__(128) stage_f64_kernel(const StageD p)
     const double *g = p.in;
     const double eps = p.eps;
 
+    const int q = p.c.q, nk = q * q;
     double gk[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) gk[k] = g[L.at(k, i, j)];
+    for (int k = 0; k < nk; ++k) gk[k] = g[L.at(k, i, j)];
 
     double n = 0.0, jt = 0.0, jp = 0.0;
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
+    for (int k = 0; k < nk; ++k) {
         n += gk[k];
-        jt += gk[k] * p.c.v[k / 4];
-        jp += gk[k] * p.c.v[k % 4];
+        jt += gk[k] * p.c.v[k / q];
+        jp += gk[k] * p.c.v[k % q];
     }
     const double ut = jt / n, up = jp / n;
     const double sin_i = p.sin_ext[i + GR];
@@ -93,20 +92,21 @@ __global__ void __launch_bounds__(128) stage_f64_kernel(const StageD p)
     const double R = p.R;
 
 #pragma unroll 1
-    for (int k = 0; k < NK; ++k) {
-        const int a = k / 4, b = k % 4;
+    for (int k = 0; k < nk; ++k) {
+        const int a = k / q, b = k % q;
         const double va = p.c.v[a], vb = p.c.v[b];
         // equilibrium (T0 = 1)
         const double xi = va * ut + vb * up;
         const double u2 = ut * ut + up * up;
         const double wk = p.c.w[a] * p.c.w[b];
-        const double feq = n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
+        // Eq. feq_Q=4 (third order), or Eq. feq_Q=3 (second order) for D2Q9
+        const double feq = (q == 3) ? n * wk * (1.0 + xi + 0.5 * (xi * xi - u2))
+                                    : n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
         // velocity derivatives: K on k_theta at fixed k_phi, Ktilde on k_phi at fixed k_theta
         double kg = 0.0, ktg = 0.0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            kg += p.c.K[a * 4 + m] * gk[4 * m + b];
-            ktg += p.c.Kt[b * 4 + m] * gk[4 * a + m];
+        for (int m = 0; m < q; ++m) {
+            kg += p.c.K[a * q + m] * gk[q * m + b];
+            ktg += p.c.Kt[b * q + m] * gk[q * a + m];
         }
         const double force = cot_i / R * (vb * vb * kg - va * ktg);
 
@@ -164,15 +164,20 @@ __global__ void __launch_bounds__(128) stage_f64_kernel(const StageD p)
 
 // Initial populations: third-order Hermite projection of a Maxwellian at T
 // (T = 1: the BGK equilibrium, Eq. feq_Q=4).
-__device__ __forceinline__ double finit(double n, double wk, double va, double vb, double ut, double up,
+// (q = 3: the same projection to second order, Eq. feq_Q=3 at T = 1.)
+__device__ __forceinline__ double finit(int q, double n, double wk, double va, double vb, double ut, double up,
                                         double T)
 {
     const double xi = va * ut + vb * up;
     const double u2 = ut * ut + up * up;
-    if (T == 1.0) return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
+    if (T == 1.0) {
+        if (q == 3) return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2));
+        return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
+    }
     const double v2 = va * va + vb * vb;
     const double dT = T - 1.0;
     const double second = xi * xi - u2 + dT * (v2 - 2.0);
+    if (q == 3) return n * wk * (1.0 + xi + 0.5 * second);
     const double third = xi * (xi * xi - 3.0 * u2) + 3.0 * dT * xi * (v2 - 4.0);
     return n * wk * (1.0 + xi + 0.5 * second + third / 6.0);
 }
@@ -186,9 +191,10 @@ __global__ void init_kernel(T *f, const Layout L, const double *rho, const doubl
     if (j >= L.np) return;
     const size_t cell = (size_t)i * L.np + j;
     const double tt = temp ? temp[cell] : 1.0;
-    for (int k = 0; k < NK; ++k) {
-        const int a = k / 4, b = k % 4;
-        double v = finit(rho[cell], c.w[a] * c.w[b], c.v[a], c.v[b], ut[cell], up[cell], tt);
+    const int q = c.q;
+    for (int k = 0; k < q * q; ++k) {
+        const int a = k / q, b = k % q;
+        double v = finit(q, rho[cell], c.w[a] * c.w[b], c.v[a], c.v[b], ut[cell], up[cell], tt);
         if (rho_ref != 0.0) v -= c.w[a] * c.w[b] * rho_ref;
         f[L.at(k, i, j)] = (T)v;
     }
@@ -201,17 +207,18 @@ __global__ void moments_kernel(const T *f, const Layout L, double *rho, double *
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= L.np) return;
+    const int q = c.q, nk = q * q;
     double fk[NK];
-    for (int k = 0; k < NK; ++k) {
+    for (int k = 0; k < nk; ++k) {
         double v = (double)f[L.at(k, i, j)];
-        if (rho_ref != 0.0) v = c.w[k / 4] * c.w[k % 4] * rho_ref + v;
+        if (rho_ref != 0.0) v = c.w[k / q] * c.w[k % q] * rho_ref + v;
         fk[k] = v;
     }
     double n = 0.0, jt = 0.0, jp = 0.0;
-    for (int k = 0; k < NK; ++k) {
+    for (int k = 0; k < nk; ++k) {
         n += fk[k];
-        jt += fk[k] * c.v[k / 4];
-        jp += fk[k] * c.v[k % 4];
+        jt += fk[k] * c.v[k / q];
+        jp += fk[k] * c.v[k % q];
     }
     const size_t cell = (size_t)i * L.np + j;
     const double u1 = jt / n, u2 = jp / n;
@@ -220,8 +227,8 @@ __global__ void moments_kernel(const T *f, const Layout L, double *rho, double *
     up[cell] = u2;
     if (temp) {
         double e = 0.0;
-        for (int k = 0; k < NK; ++k) {
-            const double ct = c.v[k / 4] - u1, cp = c.v[k % 4] - u2;
+        for (int k = 0; k < nk; ++k) {
+            const double ct = c.v[k / q] - u1, cp = c.v[k % q] - u2;
             e += fk[k] * (ct * ct + cp * cp);
         }
         temp[cell] = e / (2.0 * n);
@@ -273,7 +280,7 @@ void launch_moments_f64(const double *f, const Layout &L, double *rho, double *u
 void launch_filter_f64(double *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s)
 {
     if (nrows <= 0) return;
-    dim3 grid((L.np / 2 + 127) / 128 + 1, nrows, NK);
+    dim3 grid((L.np / 2 + 127) / 128 + 1, nrows, L.nk);
     filter_kernel<double><<<grid, 128, 0, s>>>(f, L, rows, blocks, nrows);
 }
 

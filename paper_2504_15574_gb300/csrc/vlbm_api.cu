@@ -59,32 +59,41 @@ double fact(int l)
     return r;
 }
 
-void velocity_tables(VelD &c)
+// Velocity set of order q: ascending roots of He_q (q = 4: x^4 - 6x^2 + 3, App. A.2; q = 3:
+// x^3 - 3x, App. A.1), weights q!/He_{q+1}(v)^2 (Eq. GH_weights), kernels of Eqs. (KH), (KtildeH)
+// row-major q x q.
+void velocity_tables(VelD &c, int q)
 {
-    // ascending roots of He_4 = x^4 - 6x^2 + 3; weights Q!/He_5(v)^2 (Eq. GH_weights)
-    const double outer = std::sqrt(3.0 + std::sqrt(6.0));
-    const double inner = std::sqrt(3.0 - std::sqrt(6.0));
-    c.v[0] = -outer;
-    c.v[1] = -inner;
-    c.v[2] = inner;
-    c.v[3] = outer;
-    for (int a = 0; a < 4; ++a) {
-        const double h = hermite_he(5, c.v[a]);
-        c.w[a] = fact(4) / (h * h);
+    c = VelD{};
+    c.q = q;
+    if (q == 3) {
+        c.v[0] = -std::sqrt(3.0);
+        c.v[1] = 0.0;
+        c.v[2] = std::sqrt(3.0);
+    } else {
+        const double outer = std::sqrt(3.0 + std::sqrt(6.0));
+        const double inner = std::sqrt(3.0 - std::sqrt(6.0));
+        c.v[0] = -outer;
+        c.v[1] = -inner;
+        c.v[2] = inner;
+        c.v[3] = outer;
     }
-    // Eqs. (KH), (KtildeH)
-    for (int k = 0; k < 4; ++k)
-        for (int kp = 0; kp < 4; ++kp) {
+    for (int a = 0; a < q; ++a) {
+        const double h = hermite_he(q + 1, c.v[a]);
+        c.w[a] = fact(q) / (h * h);
+    }
+    for (int k = 0; k < q; ++k)
+        for (int kp = 0; kp < q; ++kp) {
             double sk = 0.0, skt = 0.0;
-            for (int l = 0; l < 4; ++l) {
+            for (int l = 0; l < q; ++l) {
                 const double hk = hermite_he(l + 1, c.v[k]);
                 sk += hk * hermite_he(l, c.v[kp]) / fact(l);
                 double inner_l = hermite_he(l + 1, c.v[kp]);
                 if (l > 0) inner_l += (double)l * hermite_he(l - 1, c.v[kp]);
                 skt += hk * inner_l / fact(l);
             }
-            c.K[k * 4 + kp] = -c.w[k] * sk;
-            c.Kt[k * 4 + kp] = -c.w[k] * skt;
+            c.K[k * q + kp] = -c.w[k] * sk;
+            c.Kt[k * q + kp] = -c.w[k] * skt;
         }
 }
 
@@ -454,8 +463,8 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
 {
     if (!out) return fail(nullptr, VLBM_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (velocity_set == VLBM_D2Q9) return fail(nullptr, VLBM_ERR_UNSUPPORTED, "D2Q9 is not implemented");
-    if (velocity_set != VLBM_D2Q16) return fail(nullptr, VLBM_ERR_ARG, "unknown velocity set");
+    if (velocity_set != VLBM_D2Q9 && velocity_set != VLBM_D2Q16)
+        return fail(nullptr, VLBM_ERR_ARG, "unknown velocity set");
     if (n_theta < 6 || n_theta > 65536) return fail(nullptr, VLBM_ERR_ARG, "n_theta must be in [6, 65536]");
     if (n_phi < 1 || n_phi > 65536 || (n_phi != 1 && n_phi % 2 != 0))
         return fail(nullptr, VLBM_ERR_ARG, "n_phi must be 1 or even, at most 65536");
@@ -467,6 +476,8 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     if (o.precision != VLBM_FP64 && o.precision != VLBM_FP32) return fail(nullptr, VLBM_ERR_ARG, "bad precision");
     if (!(o.weno_eps > 0.0) || !(o.radius > 0.0)) return fail(nullptr, VLBM_ERR_ARG, "weno_eps and radius must be > 0");
     if (o.scheme < VLBM_WENO5 || o.scheme > VLBM_U3) return fail(nullptr, VLBM_ERR_ARG, "unknown advection scheme");
+    if (velocity_set == VLBM_D2Q9 && o.precision != VLBM_FP64)
+        return fail(nullptr, VLBM_ERR_UNSUPPORTED, "D2Q9 runs on the FP64 path only");
     if (o.precision == VLBM_FP32 && o.scheme == VLBM_WENO5 && o.komissarov)
         return fail(nullptr, VLBM_ERR_UNSUPPORTED, "the FP32 path runs the Komissarov flux with the upwind schemes only");
 
@@ -489,8 +500,9 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     h->L.np = n_phi;
     h->L.pitch = ((n_phi + 2 * GC) + 3) / 4 * 4;
     h->L.plane = (size_t)(n_theta + 2 * GR) * (size_t)h->L.pitch;
-    h->arr_bytes = (size_t)NK * h->L.plane * h->elem;
-    velocity_tables(h->vd);
+    h->L.nk = velocity_set * velocity_set;
+    h->arr_bytes = (size_t)h->L.nk * h->L.plane * h->elem;
+    velocity_tables(h->vd, velocity_set);
     row_tables(n_theta, h->sin_t, h->cos_t);
 
     auto bail = [&](int rc) {
@@ -620,7 +632,7 @@ int vlbm_init_moments(vlbm_t *h, const double *rho, const double *u_theta, const
 int vlbm_set_populations(vlbm_t *h, const double *f)
 {
     if (!h || !f) return fail(h, VLBM_ERR_ARG, "NULL argument");
-    const size_t n = (size_t)NK * h->nt * h->np;
+    const size_t n = (size_t)h->L.nk * h->nt * h->np;
     if (!h->d_dense) {
         int rc = dalloc(h, (void **)&h->d_dense, n * sizeof(double));
         if (rc) return rc;
@@ -649,7 +661,7 @@ int vlbm_set_populations(vlbm_t *h, const double *f)
 int vlbm_get_populations(vlbm_t *h, double *f)
 {
     if (!h || !f) return fail(h, VLBM_ERR_ARG, "NULL argument");
-    const size_t n = (size_t)NK * h->nt * h->np;
+    const size_t n = (size_t)h->L.nk * h->nt * h->np;
     if (!h->d_dense) {
         int rc = dalloc(h, (void **)&h->d_dense, n * sizeof(double));
         if (rc) return rc;
@@ -696,7 +708,7 @@ int vlbm_step(vlbm_t *h, int n)
     int rc = vlbm_step_async(h, n);
     if (rc) return rc;
     if (h->guard && n > 0) {
-        if (h->prec == VLBM_FP64) launch_guard_f64((const double *)h->F, NK * h->L.plane, h->d_flags + 1, h->stream);
+        if (h->prec == VLBM_FP64) launch_guard_f64((const double *)h->F, h->L.nk * h->L.plane, h->d_flags + 1, h->stream);
         else launch_guard_f32((const float *)h->F, NK * h->L.plane, h->d_flags + 1, h->stream);
         CK(h, cudaGetLastError());
     }
@@ -753,9 +765,9 @@ int vlbm_diagnostics(vlbm_t *h, vlbm_diag *out)
 int vlbm_max_stable_dt(int n_theta, int n_phi, int velocity_set, double tau, int polar_filter, double *out)
 {
     if (!out) return VLBM_ERR_ARG;
-    if (velocity_set == VLBM_D2Q9) return VLBM_ERR_UNSUPPORTED;
-    if (velocity_set != VLBM_D2Q16 || n_theta < 6 || n_phi < 1 || !(tau > 0.0)) return VLBM_ERR_ARG;
-    const double vmax = std::sqrt(3.0 + std::sqrt(6.0));
+    if ((velocity_set != VLBM_D2Q9 && velocity_set != VLBM_D2Q16) || n_theta < 6 || n_phi < 1 || !(tau > 0.0))
+        return VLBM_ERR_ARG;
+    const double vmax = (velocity_set == VLBM_D2Q9) ? std::sqrt(3.0) : std::sqrt(3.0 + std::sqrt(6.0));
     const double dth = M_PI / n_theta, dph = 2.0 * M_PI / n_phi;
     double lim = polar_filter ? dth : std::fmin(dth, std::sin(dth / 2.0) * dph);
     if (n_phi == 1) lim = dth;

@@ -30,13 +30,15 @@ constexpr int GC = 4;    // ghost columns per side (3 needed, 4 keeps TMA x-coor
 struct Layout {
     int nt, np, pitch;
     size_t plane;        // (nt + 2 GR) * pitch elements
+    int nk = NK;         // population planes (Q^2: 16 for D2Q16, 9 for D2Q9)
     __host__ __device__ size_t at(int k, int r, int c) const {
         return (size_t)k * plane + (size_t)(r + GR) * (size_t)pitch + (size_t)(c + GC);
     }
 };
 
 // Velocity-space constants (App. A.2): v ascending, 1-D weights, kernels.
-struct VelD { double v[4], w[4], K[16], Kt[16]; };
+// Velocity set of order q (3: D2Q9, 4: D2Q16): v, w per 1-D index; K, Kt row-major q x q.
+struct VelD { double v[4], w[4], K[16], Kt[16]; int q; };
 
 // ---- FP64 stage (parity path) -------------------------------------------------
 struct StageD {

@@ -225,7 +225,8 @@ class Solver:
     """One vLBM solver on the GPU: ``Solver(n_theta, n_phi, tau, dt, precision="fp64"|"fp32")``."""
 
     def __init__(self, n_theta, n_phi, tau, dt, precision="fp64", eps=1e-6, R=1.0, polar_filter=False,
-                 guard=True, stream=None, rho_ref=0.0, tile_rows=0, scheme="weno5", komissarov=False):
+                 guard=True, stream=None, rho_ref=0.0, tile_rows=0, scheme="weno5", komissarov=False,
+                 velocity_set="d2q16"):
         o = vlbm_default_options()
         o.scheme = SCHEMES[scheme]
         o.komissarov = int(bool(komissarov))
@@ -240,7 +241,9 @@ class Solver:
         self.n_theta, self.n_phi = int(n_theta), int(n_phi)
         self.tau, self.dt = float(tau), float(dt)
         self.precision = "fp32" if o.precision == VLBM_FP32 else "fp64"
-        self.h = vlbm_create(n_theta, n_phi, VLBM_D2Q16, tau, dt, o)
+        vs = {"d2q16": VLBM_D2Q16, "d2q9": VLBM_D2Q9}[velocity_set]
+        self.nk = vs * vs
+        self.h = vlbm_create(n_theta, n_phi, vs, tau, dt, o)
 
     @property
     def shape(self):
@@ -268,12 +271,12 @@ class Solver:
         return (rho, ut, up, T) if with_T else (rho, ut, up)
 
     def get_populations(self):
-        f = np.empty((NK,) + self.shape)
+        f = np.empty((self.nk,) + self.shape)
         vlbm_get_populations(self.h, f)
         return f
 
     def set_populations(self, f):
-        vlbm_set_populations(self.h, _host(f, (NK,) + self.shape))
+        vlbm_set_populations(self.h, _host(f, (self.nk,) + self.shape))
 
     def diagnostics(self):
         return vlbm_diagnostics(self.h)

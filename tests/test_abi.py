@@ -50,9 +50,12 @@ def test_max_stable_dt_needs_no_gpu(lib):
     assert dt == pytest.approx(0.25 * min(dth, math.sin(dth / 2) * (2 * math.pi / 64)) / vmax, rel=1e-15)
     assert vlbm.vlbm_max_stable_dt(32, 64, 1.0, polar_filter=True) == pytest.approx(0.25 * dth / vmax, rel=1e-15)
     assert vlbm.vlbm_max_stable_dt(32, 64, 1e-9) == 1e-9      # capped at tau
+    # D2Q9: the largest velocity is sqrt(3)
+    assert vlbm.vlbm_max_stable_dt(32, 64, 1.0, polar_filter=True, velocity_set=vlbm.VLBM_D2Q9) == \
+        pytest.approx(0.25 * dth / math.sqrt(3.0), rel=1e-15)
     with pytest.raises(vlbm.VlbmError) as e:
-        vlbm.vlbm_max_stable_dt(32, 64, 1.0, velocity_set=vlbm.VLBM_D2Q9)
-    assert e.value.code == vlbm.VLBM_ERR_UNSUPPORTED
+        vlbm.vlbm_max_stable_dt(32, 64, 1.0, velocity_set=5)
+    assert e.value.code == vlbm.VLBM_ERR_ARG
 
 
 @pytest.mark.parametrize("args,code", [
@@ -61,7 +64,6 @@ def test_max_stable_dt_needs_no_gpu(lib):
     ((32, 64, 4, 0.0, 1e-3), -1),     # tau <= 0
     ((32, 64, 4, 0.1, -1.0), -1),     # dt <= 0
     ((32, 64, 7, 0.1, 1e-3), -1),     # unknown velocity set
-    ((32, 64, 3, 0.1, 1e-3), -2),     # D2Q9 reserved
 ])
 def test_create_rejects_bad_arguments_before_the_gpu(lib, args, code):
     from paper_2504_15574_gb300 import vlbm
@@ -69,6 +71,15 @@ def test_create_rejects_bad_arguments_before_the_gpu(lib, args, code):
         vlbm.vlbm_create(*args)
     assert e.value.code == code
     assert vlbm.vlbm_last_error()
+
+
+def test_create_refuses_d2q9_on_the_fp32_path_before_the_gpu(lib):
+    from paper_2504_15574_gb300 import vlbm
+    o = vlbm.vlbm_default_options()
+    o.precision = vlbm.VLBM_FP32
+    with pytest.raises(vlbm.VlbmError) as e:
+        vlbm.vlbm_create(32, 64, vlbm.VLBM_D2Q9, 0.1, 1e-3, o)
+    assert e.value.code == vlbm.VLBM_ERR_UNSUPPORTED
 
 
 def test_null_handles_are_argument_errors(lib):

@@ -30,13 +30,13 @@ def V():
 
 
 def run_pair(V, nt, np_, tau, dt, ic, steps, precision="fp64", polar_filter=False, eps=1e-6, scheme="weno5",
-             komissarov=False):
+             komissarov=False, velocity_set="d2q16"):
     rho, ut, up, T = ic
     o = oracle.Oracle(nt, np_, tau=tau, dt=dt, eps=eps, polar_filter=polar_filter, scheme=scheme,
-                      komissarov=komissarov)
+                      komissarov=komissarov, q=3 if velocity_set == "d2q9" else 4)
     o.init_moments(rho, ut, up, T)
     g = V.Solver(nt, np_, tau, dt, precision=precision, polar_filter=polar_filter, eps=eps, scheme=scheme,
-                 komissarov=komissarov)
+                 komissarov=komissarov, velocity_set=velocity_set)
     g.init_moments(rho, ut, up, T)
     o.step(steps)
     g.step(steps)
@@ -134,6 +134,31 @@ def test_fp64_schemes_match_oracle(V, scheme, komissarov, nt, np_, filt):
     if komissarov:
         # no flux crosses a pole
         assert g.diagnostics()["pole_flux"] == 0.0
+
+
+D2Q9_CASES = [
+    # (name, nt, np, filter, scheme, komissarov, ic-factory with T)
+    ("vortices_16x32", 16, 32, False, "weno5", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 5, umax=0.08)),
+    ("shock_T_24x16", 24, 16, False, "weno5", False, lambda nt, np_: inputs.shock_cap(nt, np_, cap=0.3)),
+    ("filter_u3_komissarov_16x32", 16, 32, True, "u3", True,
+     lambda nt, np_: inputs.gaussian_vortices(nt, np_, 6, umax=0.08)),
+    ("ragged_13x10_u2", 13, 10, False, "u2", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 2)),
+]
+
+
+@pytest.mark.parametrize("case", D2Q9_CASES, ids=[c[0] for c in D2Q9_CASES])
+def test_fp64_d2q9_matches_oracle(V, case):
+    """The D2Q9 velocity set (App. A.1, Eqs. feq_Q=3, Q3_kernels) on the FP64 path."""
+    name, nt, np_, filt, scheme, kom, ic = case
+    tau, dth, vmax = 0.02, math.pi / nt, math.sqrt(3.0)
+    dt = 0.125 * dth / vmax if filt else min(0.25 * min(dth, math.sin(dth / 2) * 2 * math.pi / np_) / vmax, tau)
+    o, g = run_pair(V, nt, np_, tau, dt, ic(nt, np_), 40, polar_filter=filt, scheme=scheme, komissarov=kom,
+                    velocity_set="d2q9")
+    e = errors(g.moments(), o.moments())
+    assert e["rho"] <= FP64_TOL and e["u"] <= FP64_TOL, e
+    assert g.get_populations().shape == (9, nt, np_)
+    d_g, d_o = g.diagnostics(), o.diagnostics()
+    assert d_g["mass"] == pytest.approx(d_o["mass"], rel=1e-12)
 
 
 # ---- FP32 deviation path ------------------------------------------------------------
