@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--scheme", default="weno5", choices=["weno5", "u1", "u2", "u3"],
                     help="advection scheme (the headline workload is weno5)")
     ap.add_argument("--komissarov", action="store_true", help="Komissarov theta flux (upwind schemes)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="population storage (the headline workload is fp32)")
+    ap.add_argument("--velocity-set", default="d2q16", choices=["d2q16", "d2q9"], help="d2q9 runs in fp64 only")
     args = ap.parse_args()
     global NT, NP, DT
     NT, NP = args.n_theta, args.n_phi
@@ -145,13 +148,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(steps, warmup, budget_s, scheme="weno5", komissarov=False):
+def oracle_sample(steps, warmup, budget_s, scheme="weno5", komissarov=False, q=4):
     """The FP64 CPU oracle on the same workload (1024 x 2048 shock cap): `warmup` full RK3 steps
     (at most one), then up to `steps` timed full RK3 steps, stopping once `budget_s` seconds of
     timed work have run.  Returns (MLUPS, seconds, steps timed, threads)."""
     import oracle
     from paper_2504_15574_gb300 import inputs
-    o = oracle.Oracle(NT, NP, tau=TAU, dt=DT, polar_filter=True, scheme=scheme, komissarov=komissarov)
+    o = oracle.Oracle(NT, NP, tau=TAU, dt=DT, polar_filter=True, scheme=scheme, komissarov=komissarov, q=q)
     o.init_moments(*inputs.shock_cap(NT, NP))
     if warmup:
         o.step(1)
@@ -165,8 +168,16 @@ def oracle_sample(steps, warmup, budget_s, scheme="weno5", komissarov=False):
     return NT * NP * done / el / 1e6, el, done, cores
 
 
+def qcount(args):
+    return 9 if getattr(args, "velocity_set", "d2q16") == "d2q9" else 16
+
+
 def workload_name(args):
     w = WORKLOAD.replace("1024x2048", f"{NT}x{NP}")
+    if getattr(args, "velocity_set", "d2q16") == "d2q9":
+        w = w.replace("D2Q16 (Q=16)", "D2Q9 (Q=9)")
+    if getattr(args, "precision", "fp32") == "fp64":
+        w = w.replace("FP32 deviation storage", "FP64 populations")
     if args.scheme != "weno5":
         w = w.replace("WENO-5", args.scheme.upper() + (" + Komissarov theta flux" if args.komissarov else ""))
     return w
@@ -176,14 +187,15 @@ def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    val, el, done, cores = oracle_sample(args.steps, args.warmup, 60.0, args.scheme, args.komissarov)
+    val, el, done, cores = oracle_sample(args.steps, args.warmup, 60.0, args.scheme, args.komissarov,
+                                         3 if args.velocity_set == "d2q9" else 4)
     sample = (f"{done} of the {args.steps} requested full RK3 steps of the 1024x2048 workload "
               f"(timed work bounded at 60 s; {el:.1f} s) after {min(args.warmup, 1)} warm-up step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": done, "warmup": args.warmup, "ms_per_step": el / done * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args), "n_theta": NT, "n_phi": NP, "Q": 16, "parallelism": "host cores"},
+        "config": {"workload": workload_name(args), "n_theta": NT, "n_phi": NP, "Q": qcount(args), "parallelism": "host cores"},
         "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -201,8 +213,8 @@ def run_ours(args):
     stream = torch.cuda.Stream()          # a real stream: the library captures CUDA graphs on it
     torch.cuda.set_stream(stream)
     rho, ut, up, T = inputs.shock_cap(NT, NP)
-    s = vlbm.Solver(NT, NP, TAU, DT, precision="fp32", polar_filter=True, stream=stream.cuda_stream,
-                    scheme=args.scheme, komissarov=args.komissarov)
+    s = vlbm.Solver(NT, NP, TAU, DT, precision=args.precision, polar_filter=True, stream=stream.cuda_stream,
+                    scheme=args.scheme, komissarov=args.komissarov, velocity_set=args.velocity_set)
     s.init_moments(rho, ut, up, T)
 
     def barrier():
@@ -231,7 +243,9 @@ def run_ours(args):
     # per-kernel time, CUDA events on the launching stream (vlbm_profile_step): the three
     # stage kernels and the polar filter after each
     stage_ms, filter_ms, launches_per_step = s.profile_step(max(5, min(args.steps, 20)))
-    alg_bytes = cells * sum(BYTES_PER_CELL_STAGE)
+    # 64 B per cell per array for FP32 D2Q16; scaled by the population count and element size
+    scale = (9 if args.velocity_set == "d2q9" else 16) / 16 * (2 if args.precision == "fp64" else 1)
+    alg_bytes = cells * sum(BYTES_PER_CELL_STAGE) * scale
     achieved = alg_bytes / (sum(stage_ms) * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
     traffic = committed_traffic(args)
@@ -253,7 +267,8 @@ def run_ours(args):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu:
-            val, el, done, cores = oracle_sample(1000, 1, 15.0, args.scheme, args.komissarov)
+            val, el, done, cores = oracle_sample(1000, 1, 15.0, args.scheme, args.komissarov,
+                                                 3 if args.velocity_set == "d2q9" else 4)
             cpu = {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                    "sample": f"{done} full RK3 steps of the 1024x2048 workload after 1 warm-up step "
                              f"(bounded at 15 s of timed work; {el:.1f} s)"}
@@ -261,9 +276,10 @@ def run_ours(args):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
             "config": {"workload": workload_name(args), "n_theta": NT, "n_phi": NP,
-                       "Q": 16, "global_batch": world,
+                       "Q": qcount(args), "global_batch": world,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (three 134 MB population arrays per replica)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
