@@ -9,7 +9,8 @@
 // This path exists to reproduce an FP64 reference evaluation of the method
 // operation for operation: every expression below is evaluated in a fixed
 // order with no FMA contraction, divisions where the method divides, and sums
-// over populations in ascending k.  It is not the throughput path (that is
+// over populations in ascending k.  Each interface flux is computed once (two
+// face kernels into global buffers), then one kernel updates the cells.  It is not the throughput path (that is
 // stage_f32.cu); it shares the ghost-row layout so that all reads are plain
 // loads.
 #include "vlbm_internal.h"
@@ -67,6 +68,52 @@ __device__ __forceinline__ void store_with_images(T *f, const Layout &L, int k, 
     }
 }
 
+// Theta flux through interface fi (between rows fi-1 and fi, fi = 0..nt) of population k:
+// the reconstruction on the nodal g = sin f of rows fi-3..fi+2 (ghost rows with their own,
+// negative, sine), or (Komissarov) on f itself times v_theta sin(theta_fi).
+__global__ void __launch_bounds__(128) faces_theta_f64_kernel(const StageD p)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int fi = blockIdx.y;
+    const int k = blockIdx.z;
+    if (j >= p.L.np) return;
+    const Layout L = p.L;
+    const double *g = p.in;
+    const double va = p.c.v[k / p.c.q];
+    double gt[6];
+#pragma unroll
+    for (int o = 0; o < 6; ++o)
+        gt[o] = p.komissarov ? g[L.at(k, fi - 3 + o, j)] : p.sin_ext[fi + o] * g[L.at(k, fi - 3 + o, j)];
+    const double r = (va > 0.0) ? recon(p.scheme, gt[0], gt[1], gt[2], gt[3], gt[4], p.eps)
+                                : recon(p.scheme, gt[5], gt[4], gt[3], gt[2], gt[1], p.eps);
+    const double flux = p.komissarov ? va * p.sin_f[fi] * r : va * r;
+    p.Ft[((size_t)k * (L.nt + 1) + fi) * L.np + j] = flux;
+    if (p.pole) {
+        if (fi == 0) p.pole[(size_t)k * L.np + j] = flux;
+        if (fi == L.nt) p.pole[((size_t)NK + k) * L.np + j] = flux;
+    }
+}
+
+// Phi flux through interface fj (between columns fj-1 and fj, fj = 0..np) of row i.
+__global__ void __launch_bounds__(128) faces_phi_f64_kernel(const StageD p)
+{
+    const int fj = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    const int k = blockIdx.z;
+    if (fj > p.L.np) return;
+    const Layout L = p.L;
+    const double *g = p.in;
+    const double vb = p.c.v[k % p.c.q];
+    double gp[6];
+#pragma unroll
+    for (int o = 0; o < 6; ++o) gp[o] = g[L.at(k, i, fj - 3 + o)];
+    const double r = (vb > 0.0) ? recon(p.scheme, gp[0], gp[1], gp[2], gp[3], gp[4], p.eps)
+                                : recon(p.scheme, gp[5], gp[4], gp[3], gp[2], gp[1], p.eps);
+    p.Fp[((size_t)k * L.nt + i) * (L.np + 1) + fj] = vb * r;
+}
+
+// One cell: moments, equilibrium, force, BGK, the flux differences of the interface
+// fluxes above and the stage combination, in the oracle's operation order.
 __global__ void __launch_bounds__(128) stage_f64_kernel(const StageD p)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,7 +121,6 @@ __global__ void __launch_bounds__(128) stage_f64_kernel(const StageD p)
     if (i >= p.L.nt || j >= p.L.np) return;
     const Layout L = p.L;
     const double *g = p.in;
-    const double eps = p.eps;
 
     const int q = p.c.q, nk = q * q;
     double gk[NK];
@@ -109,40 +155,10 @@ __global__ void __launch_bounds__(128) stage_f64_kernel(const StageD p)
             ktg += p.c.Kt[b * q + m] * gk[q * a + m];
         }
         const double force = cot_i / R * (vb * vb * kg - va * ktg);
-
-        // theta faces i (north) and i+1 (south) on the nodal g = sin f, or (Komissarov) on f
-        // (ghost rows hold the mapped population's f) times the interface sine
-        const int sc = p.scheme;
-        double gt[7];
-#pragma unroll
-        for (int o = 0; o < 7; ++o)
-            gt[o] = p.komissarov ? g[L.at(k, i - 3 + o, j)] : p.sin_ext[i + o] * g[L.at(k, i - 3 + o, j)];
-        double rn, rs;
-        if (va > 0.0) {
-            rn = recon(sc, gt[0], gt[1], gt[2], gt[3], gt[4], eps);
-            rs = recon(sc, gt[1], gt[2], gt[3], gt[4], gt[5], eps);
-        } else {
-            rn = recon(sc, gt[5], gt[4], gt[3], gt[2], gt[1], eps);
-            rs = recon(sc, gt[6], gt[5], gt[4], gt[3], gt[2], eps);
-        }
-        const double fn = p.komissarov ? va * p.sin_f[i] * rn : va * rn;
-        const double fs = p.komissarov ? va * p.sin_f[i + 1] * rs : va * rs;
-        // phi faces j (west) and j+1 (east)
-        double gp[7];
-#pragma unroll
-        for (int o = 0; o < 7; ++o) gp[o] = g[L.at(k, i, j - 3 + o)];
-        double fw, fe;
-        if (vb > 0.0) {
-            fw = vb * recon(sc, gp[0], gp[1], gp[2], gp[3], gp[4], eps);
-            fe = vb * recon(sc, gp[1], gp[2], gp[3], gp[4], gp[5], eps);
-        } else {
-            fw = vb * recon(sc, gp[5], gp[4], gp[3], gp[2], gp[1], eps);
-            fe = vb * recon(sc, gp[6], gp[5], gp[4], gp[3], gp[2], eps);
-        }
-        if (p.pole) {
-            if (i == 0) p.pole[(size_t)k * L.np + j] = fn;
-            if (i == L.nt - 1) p.pole[((size_t)NK + k) * L.np + j] = fs;
-        }
+        const double fn = p.Ft[((size_t)k * (L.nt + 1) + i) * L.np + j];
+        const double fs = p.Ft[((size_t)k * (L.nt + 1) + i + 1) * L.np + j];
+        const double fw = p.Fp[((size_t)k * L.nt + i) * (L.np + 1) + j];
+        const double fe = p.Fp[((size_t)k * L.nt + i) * (L.np + 1) + j + 1];
         const double adv_t = p.komissarov ? -(fs - fn) / (R * (p.cos_f[i] - p.cos_f[i + 1]))
                                           : -(fs - fn) / (R * sin_i * p.dth);
         const double adv_p = -(fe - fw) / (R * sin_i * p.dph);
@@ -258,6 +274,9 @@ __global__ void filter_kernel(T *f, const Layout L, const int *rows, const int *
 
 void launch_stage_f64(const StageD &p, cudaStream_t s)
 {
+    // every interface flux once (as the oracle), then the cells
+    faces_theta_f64_kernel<<<dim3((p.L.np + 127) / 128, p.L.nt + 1, p.L.nk), 128, 0, s>>>(p);
+    faces_phi_f64_kernel<<<dim3((p.L.np + 1 + 127) / 128, p.L.nt, p.L.nk), 128, 0, s>>>(p);
     dim3 block(32, 4);
     dim3 grid((p.L.np + 31) / 32, (p.L.nt + 3) / 4);
     stage_f64_kernel<<<grid, block, 0, s>>>(p);

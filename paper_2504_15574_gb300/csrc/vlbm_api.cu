@@ -364,6 +364,8 @@ void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
             p.komissarov = h->komissarov;
             p.sin_f = h->d_sin_f;
             p.cos_f = h->d_cos_f;
+            p.Ft = h->d_ft;
+            p.Fp = h->d_fp;
             if (part != 2) launch_stage_f64(p, s);
             if (h->nfrows && part != 1) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         } else {
@@ -379,7 +381,7 @@ void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
 int kernels_per_step(const vlbm_t *h)
 {
     int n = 3 + (h->nfrows ? 3 : 0);
-    if (h->prec == VLBM_FP64) n += 1;
+    if (h->prec == VLBM_FP64) n += 3 * 2 + 1;   // two face kernels per stage and the pole budget
     return n;
 }
 
@@ -554,6 +556,10 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     }
     if ((rc = upload(h, &h->d_sin_f, h->sin_f.data(), h->sin_f.size())) ||
         (rc = upload(h, &h->d_cos_f, h->cos_f.data(), h->cos_f.size())))
+        return bail(rc);
+    if (h->prec == VLBM_FP64 &&
+        ((rc = dalloc(h, (void **)&h->d_ft, sizeof(double) * h->L.nk * (size_t)(n_theta + 1) * n_phi)) ||
+         (rc = dalloc(h, (void **)&h->d_fp, sizeof(double) * h->L.nk * (size_t)n_theta * (n_phi + 1)))))
         return bail(rc);
     // polar filter rows
     if (h->filter) {
@@ -819,7 +825,7 @@ void vlbm_destroy(vlbm_t *h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_sin_f, h->d_cos_f, h->d_isp,
-                    h->d_sfc,
+                    h->d_sfc, h->d_ft, h->d_fp,
                     h->d_rref, h->d_dsin, h->d_d2sin,
                     h->d_face, h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
                     h->d_part, h->d_diag, h->d_flags};

@@ -26,6 +26,7 @@ struct vlbm {
     std::vector<double> sin_f, cos_f;                 // theta interfaces fi = 0..nt (theta = fi dtheta)
     double *d_sin_f = nullptr, *d_cos_f = nullptr;
     float *d_isp = nullptr, *d_sfc = nullptr;         // FP32 upwind schemes: 1/sin per padded row, interface sines
+    double *d_ft = nullptr, *d_fp = nullptr;          // FP64 path: interface flux buffers of one stage
     std::vector<double> sin_t, cos_t;
     // FP32 tables
     float2 *d_rref = nullptr;

@@ -55,6 +55,7 @@ struct StageD {
     int scheme;            // VLBM_WENO5 .. VLBM_U3
     int komissarov;        // theta flux in the Komissarov form
     const double *sin_f, *cos_f;   // per theta interface fi = 0..nt (theta = fi dtheta)
+    double *Ft, *Fp;       // interface fluxes: theta [nk][nt+1][np], phi [nk][nt][np+1]
 };
 void launch_stage_f64(const StageD &p, cudaStream_t s);
 
