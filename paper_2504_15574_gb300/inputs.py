@@ -76,6 +76,45 @@ def sound_parabola(n_theta: int, n_phi: int = 1, U0: float = 1e-5):
     return np.ones_like(TH), U0 * (math.pi - TH) * TH, np.zeros_like(TH), None
 
 
+def rotated_frame(n_theta: int, n_phi: int, alpha: float):
+    """Geometry of a grid rotated by alpha about the y axis (App. C, Eqs. transf, transf_inv).
+
+    For every cell (theta', phi') of the n_theta x n_phi grid, the coordinates (theta, phi)
+    of the same point in the original frame, and the 2 x 2 matrix M (shape [2, 2, nt, np])
+    that maps original-frame vielbein components (u^theta, u^phi) at that point to the
+    grid's components (u^theta', u^phi'): the Cartesian rotation x' = R_2(alpha) x applied
+    to u^theta e_theta + u^phi e_phi, projected on e_theta', e_phi'."""
+    TH, PH = _grid(n_theta, n_phi)
+    ca, sa = math.cos(alpha), math.sin(alpha)
+    # the cell's position in the grid's (primed) Cartesian frame, then x = R_2(alpha)^T x'
+    xp, yp, zp = np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)
+    x = ca * xp - sa * zp
+    y = yp
+    z = sa * xp + ca * zp
+    th = np.arccos(np.clip(z, -1.0, 1.0))
+    ph = np.mod(np.arctan2(y, x), 2 * math.pi)
+
+    def rot(v):   # x' = R_2(alpha) x
+        return np.stack([ca * v[0] + sa * v[2], v[1], -sa * v[0] + ca * v[2]])
+
+    e_th = rot(np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)]))
+    e_ph = rot(np.stack([-np.sin(ph), np.cos(ph), np.zeros_like(ph)]))
+    ep_th = np.stack([np.cos(TH) * np.cos(PH), np.cos(TH) * np.sin(PH), -np.sin(TH)])
+    ep_ph = np.stack([-np.sin(PH), np.cos(PH), np.zeros_like(PH)])
+    M = np.array([[(ep_th * e_th).sum(0), (ep_th * e_ph).sum(0)],
+                  [(ep_ph * e_th).sum(0), (ep_ph * e_ph).sum(0)]])
+    return th, ph, M
+
+
+def sound_parabola_rotated(n_theta: int, n_phi: int, U0: float = 1e-5, alpha: float = -math.pi / 2):
+    """The axisymmetric sound-wave start of sound_parabola about an axis tilted by alpha:
+    on the grid rotated by alpha (App. C), u = U0 (pi - theta) theta e_theta of the
+    original frame, rho = 1."""
+    th, _, M = rotated_frame(n_theta, n_phi, alpha)
+    ut0 = U0 * (math.pi - th) * th
+    return np.ones_like(th), M[0, 0] * ut0, M[1, 0] * ut0, None
+
+
 def shear_uniform(n_theta: int, n_phi: int = 1, V0: float = 1e-5):
     """Axisymmetric shear-wave start: u^phi = V0, rho = 1."""
     TH, _ = _grid(n_theta, n_phi)
