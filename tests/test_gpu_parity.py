@@ -63,6 +63,8 @@ CASES = {
     # the sound wave about an axis in the equatorial plane (App. C, alpha = -pi/2): flow across the
     # pole rows and the phi seam
     "sound_rotated_32x32": (32, 32, 2e-3, 1e-4, lambda: inputs.sound_parabola_rotated(32, 32, 1e-3), 200, False),
+    # the spherical shock tube of Sec. 4.3 (density ratio 8), through shock formation
+    "riemann_256x1": (256, 1, 2e-4, 2e-5, lambda: inputs.riemann_cap(256, 1), 400, False),
 }
 
 
@@ -182,6 +184,7 @@ FP32_CASES = {
     "filter_wide_blocks_64x8192": (1e-7, 2e-4, 2e-5),
     "filter_window_blocks_8x32768": (1e-7, 2e-4, 2e-5),
     "sound_rotated_32x32": (1e-8, 5e-5, 2e-5),
+    "riemann_256x1": (2.5e-5, 3e-5, 2e-5),
 }
 
 
