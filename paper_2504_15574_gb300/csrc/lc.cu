@@ -511,17 +511,17 @@ __global__ void outputs_kernel(const float *Y, int CO, int H, int W, float3 scal
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// Moments (rho, u^theta, u^phi, T) of the FP32 pair layout (dg = s (f - w rho_ref)) in FP32
+// Moments (rho, u^theta, u^phi, T) of the FP32 pair layout (dg = ks s (f - w rho_ref)) in FP32
 // arithmetic on the deviations: n = rho_ref + sum dg / s, j = sum v dg / s (the reference
 // state carries no momentum), and T - 1 = (rho_ref |u|^2 + sum df |v - u|^2 - 2 dn) / (2 n),
 // using sum_k w_k |v_k|^2 = 2 (T0 = 1); stored as FP64 for the feature kernel.
 __global__ void lc_moments_kernel(const float2 *f, const Layout L, const VelD c, double rho_ref,
-                                  const double *sin_t, double *mom)
+                                  const double *sin_t, double ks, double *mom)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= L.np) return;
-    const float inv_s = (float)(1.0 / sin_t[i]);
+    const float inv_s = (float)(1.0 / (ks * sin_t[i]));
     float2 g[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) g[q] = f[L.at(q, i, j)];
@@ -559,7 +559,7 @@ __global__ void lc_moments_kernel(const float2 *f, const Layout L, const VelD c,
 // feq' - feq = w [ (rho' - rho) P' + rho (P' - P) ] and P' - P expanded in dxi = v . du and
 // d(u^2) = du . (2u + du).
 __global__ void nudge_kernel(float2 *f, const Layout L, const double *mom, const double *delta, const double *mean,
-                             double wsum, const VelD c, const double *sin_t)
+                             double wsum, const VelD c, const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
@@ -571,7 +571,7 @@ __global__ void nudge_kernel(float2 *f, const Layout L, const double *mom, const
     const float ut2 = ut + dut, up2 = up + dup;
     const float usq = ut * ut + up * up, usq2 = ut2 * ut2 + up2 * up2;
     const float dusq = dut * (ut + ut2) + dup * (up + up2);
-    const float s = (float)sin_t[i];
+    const float s = (float)(ks * sin_t[i]);
     for (int q = 0; q < 8; ++q) {
         const int g = q >> 2, b = q & 3;
         float2 v = f[L.at(q, i, j)];
@@ -697,18 +697,18 @@ void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double
     sum_kernel<<<1, 256, 0, s>>>(part, nb, mean);
 }
 
-void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref, const double *sin_t, double *mom,
-                cudaStream_t s)
+void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref, const double *sin_t, double ks,
+                double *mom, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt);
-    lc_moments_kernel<<<grid, 128, 0, s>>>(f, L, c, rho_ref, sin_t, mom);
+    lc_moments_kernel<<<grid, 128, 0, s>>>(f, L, c, rho_ref, sin_t, ks, mom);
 }
 
 void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,
-              const VelD &c, const double *sin_t, cudaStream_t s)
+              const VelD &c, const double *sin_t, double ks, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt);
-    nudge_kernel<<<grid, 128, 0, s>>>(f, L, mom, delta, mean, wsum, c, sin_t);
+    nudge_kernel<<<grid, 128, 0, s>>>(f, L, mom, delta, mean, wsum, c, sin_t, ks);
 }
 
 }  // namespace vk

@@ -140,12 +140,12 @@ int check_solver(vlbm_lc_t *n, vlbm_t *h)
 // synchronisation: moments, forward pass, outputs (drho area mean), nudge, ghost fill.
 int enqueue_correction(vlbm_lc_t *n, vlbm_t *h, cudaStream_t s)
 {
-    lc_moments((const float2 *)h->F, h->L, h->vd, h->rho_ref, h->d_sin_t, h->d_mom, s);
+    lc_moments((const float2 *)h->F, h->L, h->vd, h->rho_ref, h->d_sin_t, h->kscale, h->d_mom, s);
     int rc;
     if ((rc = forward(n, h->d_mom, s, false))) return rc;
     const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
     lc_outputs(n->d_y, LC_COUT, n->H, n->W, sc, n->d_sin, n->d_out, n->d_part, n->d_scal + 1, s);
-    lc_nudge((float2 *)h->F, h->L, h->d_mom, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, s);
+    lc_nudge((float2 *)h->F, h->L, h->d_mom, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, h->kscale, s);
     launch_fill_ghosts_f32((float2 *)h->F, h->L, s);
     LCK(n, cudaGetLastError());
     return VLBM_OK;

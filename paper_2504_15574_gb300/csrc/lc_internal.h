@@ -46,12 +46,13 @@ void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g
 void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
                  const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *Xp,
                  cudaStream_t s);
-// (rho, u^theta, u^phi, T) [4][H][W] of a solver's FP32 state, FP32 arithmetic on the deviations.
-void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref, const double *sin_t, double *mom,
-                cudaStream_t s);
+// (rho, u^theta, u^phi, T) [4][H][W] of a solver's FP32 state (state scale ks), FP32 arithmetic
+// on the deviations.
+void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref, const double *sin_t, double ks,
+                double *mom, cudaStream_t s);
 void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
                 double *mean, cudaStream_t s);
 void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,
-              const VelD &c, const double *sin_t, cudaStream_t s);
+              const VelD &c, const double *sin_t, double ks, cudaStream_t s);
 
 }  // namespace vk

@@ -1,10 +1,12 @@
 // stage_f32.cu -- FP32 deviation-storage path (the throughput path).
 //
-// State.  The device array holds dg = sin(theta) (f - w_k rho_ref) in FP32: the
+// State.  The device array holds dg = k sin(theta) (f - w_k rho_ref) in FP32: the
 // deviation from the reference state w_k rho_ref (rho_ref an FP64 constant),
 // premultiplied by sin(theta) so that the stage input is directly the nodal
 // variable of the theta flux (arXiv 2504.15574 Eq. discrete_advection_sphere, read
-// as a finite-difference WENO on g = sin(theta) f).  Populations are stored in
+// as a finite-difference WENO on g = sin(theta) f), and by the run's state scale k,
+// a power of two (exact) that puts the WENO regulariser 4 eps k^2 near 1.
+// Populations are stored in
 // pairs: pair p = 4 g + b holds populations (a = 2g, b) and (a = 2g + 1, b) as one
 // float2, so that both members share the sign of v_theta and the value of v_phi
 // and every per-population operation runs as one packed f32x2 instruction.
@@ -17,20 +19,24 @@
 //   1. one TMA box (8 pair planes x (TY+6) x (TX+8) float2) into shared memory;
 //   2. phi faces and theta faces of all pairs, each face once, into shared memory
 //      (WENO-5, Eqs. fluxes_W5, WENO5_delta, WENO5_sigma).  On dg the phi weights
-//      use eps sin^2(theta) (the WENO weights are invariant under g -> s g with
-//      eps -> s^2 eps; each (sigma + eps) is evaluated divided by its eps), and
-//      the theta weights are those of the full
-//      g = sin(theta) w_k rho_ref + dg: each smoothness form is the dg part plus
-//      w_k rho_ref times the form of sin(theta) (FP64 table).  The reconstruction
-//      is written P2 + wbar1 (P1 - P2) + wbar3 (P3 - P2); its reference part is
-//      the ideal-weight interpolant (folded, with the force of the reference
-//      state, into the FP64-derived tendency rref) minus corr, plus the weight
-//      terms, which use the full forms;
+//      use the regulariser 4 eps s^2 k^2 (the WENO weights are invariant under
+//      g -> s g with eps -> s^2 eps, and every smoothness term is evaluated as
+//      4 k^2 (sigma + eps), a common factor of the ratios); the theta weights are
+//      those of the full g = k sin(theta) w_k rho_ref + dg: each smoothness form is
+//      the dg part plus k w_k rho_ref times the form of sin(theta) (FP64 table).  The
+//      reconstruction is written P2 + wbar1 (P1 - P2) + wbar3 (P3 - P2); its
+//      reference part is the ideal-weight interpolant (folded, with the force of the
+//      reference state, into the FP64-derived tendency rref) minus corr, plus the
+//      weight terms, which use the full forms.  Face values carry the stage's dt
+//      share and their metric factor;
 //   3. per cell: moments (Eq. f_moments_sum), equilibrium (Eq. feq_Q=4), BGK,
 //      force through K^H / Ktilde^H (Eq. df), flux differences and the stage
 //      combination, all on dg (the operator commutes with the row factor), then
 //      the store of the cell and of its ghost images.
 #include "vlbm_internal.h"
+
+#include <algorithm>
+#include <cmath>
 
 namespace vk {
 
@@ -48,7 +54,7 @@ struct __align__(128) SmemT {
     float2 ds2[TY + 2 * GR];            // (dsin, dsin) at the tile rows
     float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
     float2 cw[NP2][TY + 1];             // -w rho_ref corr per pair and theta face row
-    float2 rr[TY][NP2];                 // s rref per cell row and pair
+    float2 rr[TY][NP2];                 // dte s rref per cell row and pair
     float2 isp2[TY + 2 * GR];           // upwind schemes, Komissarov: (1/sin, 1/sin) at the tile rows
     float2 sf2[TY + 1];                 // upwind schemes, Komissarov: interface sines of the face rows
     RowF rowc[TY];
@@ -106,42 +112,39 @@ __device__ __forceinline__ bool wait_phase(unsigned long long *bar, unsigned par
     }
 }
 
-// Stencil linear forms on upwind-ordered values a..e (packed pairs).
-struct Forms { f2 p2, A1, B1, A2, B2, A3, B3; };
-
-__device__ __forceinline__ Forms forms(f2 a, f2 b, f2 c, f2 d, f2 e)
+// Nonlinear combination of WENO-5 (Eqs. fluxes_W5, WENO5_delta, WENO5_sigma) on the
+// scaled state: P2 + wbar1 (A1 - A2)/3 + wbar3 (A2 - A3)/6 with wbar_i = d_i q_j q_k / sum
+// and q_i = t_i^2, where t_i = B_i^2 + 13/3 A_i^2 + E = 4 k^2 (sigma_i + eps) for the
+// unscaled forms (sigma_i = 13/12 A_i^2 + 1/4 B_i^2).  The weights are ratios, so the
+// common factor 4 k^2 cancels; the state scale k is chosen with E = 4 eps k^2 near 1,
+// so t_i >= E sin^2(theta) keeps the products q_j q_k clear of FP32 underflow down to
+// the pole rows, and they overflow only for sigma_i above ~1e9 eps.
+__device__ __forceinline__ f2 weno_mix(f2 t1, f2 t2, f2 t3, f2 d12, f2 d23, f2 p2)
 {
-    const f2 m2 = splat(-2.0f), m4 = splat(-4.0f), p3 = splat(3.0f);
-    Forms F;
-    F.A1 = fma2(m2, b, add2(a, c));
-    F.B1 = fma2(p3, c, fma2(m4, b, a));
-    F.A2 = fma2(m2, c, add2(b, d));
-    F.B2 = sub2(b, d);
-    F.A3 = fma2(m2, d, add2(c, e));
-    F.B3 = fma2(p3, c, fma2(m4, d, e));
-    // P2 = (-b + 5c + 2d) / 6
-    F.p2 = fma2(splat(5.0f / 6.0f), c, fma2(splat(1.0f / 3.0f), d, mul2(splat(-1.0f / 6.0f), b)));
-    return F;
-}
-
-// P2 + wbar1 (A1 - A2)/3 + wbar3 (A2 - A3)/6 with wbar_i = d_i q_j q_k / sum,
-// q_i = (sigma_i + eps)^2, sigma_i = 13/12 A_i^2 + 1/4 B_i^2.  The weights are
-// ratios, so every (sigma_i + eps) is evaluated divided by eps (kinv = 1/eps):
-// then q_i >= 1 and the products q_j q_k neither underflow (eps sin^2 reaches
-// 1e-12 at the pole rows) nor overflow for sigma_i up to ~1e9 eps.
-__device__ __forceinline__ f2 weno_combine(const Forms &F, float kinv)
-{
-    const f2 c13 = splat((13.0f / 12.0f) * kinv), c14 = splat(0.25f * kinv), one = splat(1.0f);
-    const f2 s1 = fma2(mul2(F.A1, c13), F.A1, fma2(mul2(F.B1, c14), F.B1, one));
-    const f2 s2 = fma2(mul2(F.A2, c13), F.A2, fma2(mul2(F.B2, c14), F.B2, one));
-    const f2 s3 = fma2(mul2(F.A3, c13), F.A3, fma2(mul2(F.B3, c14), F.B3, one));
-    const f2 q1 = mul2(s1, s1), q2 = mul2(s2, s2), q3 = mul2(s3, s3);
+    const f2 q1 = mul2(t1, t1), q2 = mul2(t2, t2), q3 = mul2(t3, t3);
     const f2 q23 = mul2(q2, q3), q12 = mul2(q1, q2);
     const f2 sum = fma2(splat(0.1f), q23, fma2(splat(0.6f), mul2(q1, q3), mul2(splat(0.3f), q12)));
     const f2 r = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
     // 0.1/3 q23 (A1 - A2) + 0.3/6 q12 (A2 - A3)
-    const f2 num = fma2(mul2(splat(0.1f / 3.0f), q23), sub2(F.A1, F.A2), mul2(mul2(splat(0.05f), q12), sub2(F.A2, F.A3)));
-    return fma2(num, r, F.p2);
+    const f2 num = fma2(mul2(splat(0.1f / 3.0f), q23), d12, mul2(mul2(splat(0.05f), q12), d23));
+    return fma2(num, r, p2);
+}
+
+// WENO-5 interface value of the upwind-ordered values a..e (packed pairs), E the
+// regulariser of the row.  The stencil forms are built from the first differences
+// d1..d4: A_i = d_{i+1} - d_i, B1 = A1 + 2 d2, |B2| = |d2 + d3|, B3 = A3 - 2 d3 and
+// P2 = c + (d2 + 2 d3)/6.
+__device__ __forceinline__ f2 weno_face(f2 a, f2 b, f2 c, f2 d, f2 e, f2 E)
+{
+    const f2 two = splat(2.0f), m2 = splat(-2.0f), c133 = splat(13.0f / 3.0f);
+    const f2 d1 = sub2(b, a), d2 = sub2(c, b), d3 = sub2(d, c), d4 = sub2(e, d);
+    const f2 A1 = sub2(d2, d1), A2 = sub2(d3, d2), A3 = sub2(d4, d3);
+    const f2 B1 = fma2(two, d2, A1), B2 = add2(d2, d3), B3 = fma2(m2, d3, A3);
+    const f2 t1 = fma2(B1, B1, fma2(mul2(A1, c133), A1, E));
+    const f2 t2 = fma2(B2, B2, fma2(mul2(A2, c133), A2, E));
+    const f2 t3 = fma2(B3, B3, fma2(mul2(A3, c133), A3, E));
+    const f2 p2 = fma2(splat(1.0f / 3.0f), d3, fma2(splat(1.0f / 6.0f), d2, c));
+    return weno_mix(t1, t2, t3, sub2(A1, A2), sub2(A2, A3), p2);
 }
 
 // Writes v at pair-plane cell (p, i, j) and at its ghost images.
@@ -186,6 +189,11 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const float2 *in = (stage == 1) ? R.F : (stage == 2) ? R.A : R.B;
     float2 *out = (stage == 1) ? R.A : (stage == 2) ? R.B : R.F;
     (void)in;
+    // SSP-RK3 (Sec. 3.7): the stage output is cF F0 + cG G + dte L[G] with (cF, cG, dte / dt) =
+    // (0, 1, 1), (3/4, 1/4, 1/4), (1/3, 2/3, 2/3)
+    // (the scalar constants use explicit roundings: no contraction may differ between the
+    // standalone and the batch kernel, whose results must agree bit for bit)
+    const float dte = (stage == 1) ? R.dt : __fmul_rn((stage == 2) ? 0.25f : (2.0f / 3.0f), R.dt);
 
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -223,7 +231,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             S.rowc[t] = R.row[min(i0 + t, L.nt - 1)];
         } else if ((t -= TY) < TY * NP2) {
             const int ry = t >> 3, q = t & 7;
-            S.rr[ry][q] = R.rref[(size_t)min(i0 + ry, L.nt - 1) * NP2 + q];
+            S.rr[ry][q] = mul2(R.rref[(size_t)min(i0 + ry, L.nt - 1) * NP2 + q], splat(dte));
         } else if (LIN && (t -= TY * NP2) < SR) {
             S.isp2[t] = splat(R.isp[i0 + t]);
         } else if (LIN && (t -= SR) < TY + 1) {
@@ -240,23 +248,27 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         return false;
     }
 
+    // Every face value below is premultiplied by the stage's dt share dte and by the
+    // metric factor of its difference (1/(R sin dphi) for phi, 1/(R dtheta) for the
+    // WENO-5 and plain upwind theta fluxes), so the cell update takes plain differences.
     // ---- phi faces: warp = cell row fy, lane = face fx (west face of column fx)
     if constexpr (LIN) {
         // upwind schemes on dg: x_up2, x_up, x_down are the columns fx-2, fx-1, fx for v > 0
         // and fx+1, fx, fx-1 for v < 0 (shared column = column + GC)
         const int fy = warp;
         const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
+        const f2 sp = splat(__fmul_rn(S.rowc[fy].inv_dph, dte));
 #pragma unroll
         for (int q = 0; q < NP2; ++q) {
             const f2 vb = c.vphi2[q & 3];
             const f2 *row = &S.tile[q][fy + GR][0];
             const f2 rec = (vb.x > 0.0f) ? fma2(l0, row[lane + 2], fma2(l1, row[lane + 3], mul2(l2, row[lane + 4])))
                                          : fma2(l0, row[lane + 5], fma2(l1, row[lane + 4], mul2(l2, row[lane + 3])));
-            S.fp[q][fy][lane] = mul2(vb, rec);
+            S.fp[q][fy][lane] = mul2(mul2(vb, sp), rec);
         }
         if (tid < NP2 * TY) {
             const int q = tid / TY, ry = tid - (tid / TY) * TY;
-            const f2 vb = c.vphi2[q & 3];
+            const f2 vb = mul2(c.vphi2[q & 3], splat(__fmul_rn(S.rowc[ry].inv_dph, dte)));
             const f2 *row = &S.tile[q][ry + GR][0];
             const int fx = TX;
             const f2 rec = (vb.x > 0.0f) ? fma2(l0, row[fx + 2], fma2(l1, row[fx + 3], mul2(l2, row[fx + 4])))
@@ -265,41 +277,49 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         }
     } else {
         const int fy = warp;
-        const float kinv = S.rowc[fy].kphi;
-#pragma unroll 2
-        for (int q = 0; q < NP2; ++q) {
-            const f2 vb = c.vphi2[q & 3];
-            const f2 *row = &S.tile[q][fy + GR][0];
-            Forms F;
-            if (vb.x > 0.0f) {   // columns fx-3 .. fx+1  (shared column = column + GC)
-                F = forms(row[lane + 1], row[lane + 2], row[lane + 3], row[lane + 4], row[lane + 5]);
-            } else {             // columns fx+2 .. fx-2
-                F = forms(row[lane + 6], row[lane + 5], row[lane + 4], row[lane + 3], row[lane + 2]);
+        const f2 E = splat(S.rowc[fy].ephi);
+        const f2 sp = splat(__fmul_rn(S.rowc[fy].inv_dph, dte));
+        // b outer: both pairs of a b share v_phi, its sign and the scaled velocity
+#pragma unroll 1
+        for (int b = 0; b < 4; ++b) {
+            const f2 vb = mul2(c.vphi2[b], sp);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const int q = 4 * g + b;
+                const f2 *row = &S.tile[q][fy + GR][0];
+                f2 r;
+                if (vb.x > 0.0f)   // columns fx-3 .. fx+1  (shared column = column + GC)
+                    r = weno_face(row[lane + 1], row[lane + 2], row[lane + 3], row[lane + 4], row[lane + 5], E);
+                else               // columns fx+2 .. fx-2
+                    r = weno_face(row[lane + 6], row[lane + 5], row[lane + 4], row[lane + 3], row[lane + 2], E);
+                S.fp[q][fy][lane] = mul2(vb, r);
             }
-            S.fp[q][fy][lane] = mul2(vb, weno_combine(F, kinv));
         }
         // east face of the last column: NP2 x TY (pair, row) combinations
         if (tid < NP2 * TY) {
             const int q = tid / TY, ry = tid - (tid / TY) * TY;
-            const f2 vb = c.vphi2[q & 3];
+            const f2 vb = mul2(c.vphi2[q & 3], splat(__fmul_rn(S.rowc[ry].inv_dph, dte)));
+            const f2 Er = splat(S.rowc[ry].ephi);
             const f2 *row = &S.tile[q][ry + GR][0];
             const int fx = TX;
-            Forms F = (vb.x > 0.0f) ? forms(row[fx + 1], row[fx + 2], row[fx + 3], row[fx + 4], row[fx + 5])
-                                    : forms(row[fx + 6], row[fx + 5], row[fx + 4], row[fx + 3], row[fx + 2]);
-            S.fp[q][ry][fx] = mul2(vb, weno_combine(F, S.rowc[ry].kphi));
+            const f2 r = (vb.x > 0.0f) ? weno_face(row[fx + 1], row[fx + 2], row[fx + 3], row[fx + 4], row[fx + 5], Er)
+                                       : weno_face(row[fx + 6], row[fx + 5], row[fx + 4], row[fx + 3], row[fx + 2], Er);
+            S.fp[q][ry][fx] = mul2(vb, r);
         }
     }
 
     // ---- upwind schemes, theta faces: warp = pair, lane = column; the column's values are dg
     // (nodal g = sin f), or for the Komissarov flux df = dg / sin (ghost rows: the mapped
-    // population's df), then v_theta times the interface sine times the reconstruction
+    // population's df), then v_theta times the interface sine times the reconstruction.
+    // These faces carry dte only: the cell update applies 1/(R dtheta), or the Komissarov
+    // row factor s / (R dcos).
     if constexpr (LIN) {
         const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
         const bool kom = R.komissarov != 0;
 #pragma unroll 1
         for (int q = warp; q < NP2; q += NT / 32) {
             const int g = q >> 2;
-            const f2 vt = c.vth[g];
+            const f2 vt = mul2(c.vth[g], splat(dte));
             const f2 *col = &S.tile[q][0][lane + GC];
             f2 x[SR];
 #pragma unroll
@@ -317,23 +337,22 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
 
     // ---- WENO-5 theta faces: warp = pair, lane = column, marching over the TY+1 face rows.
     // Consecutive faces share their second differences (the smoothness forms of the
-    // three candidate stencils are centred on consecutive rows).  With x the tile
-    // column (rows 0..SR-1), for v > 0 face fy uses x[fy..fy+4] in upwind order,
-    // for v < 0 it uses x[fy+5..fy+1].  The smoothness forms are those of the full
-    // g = dg + w rho_ref sin(theta) (first and second differences of sin from the
-    // FP64 tables); P2 is taken on dg alone.
+    // three candidate stencils are centred on consecutive rows) and the row terms
+    // 13/3 A^2 + E.  With x the tile column (rows 0..SR-1), for v > 0 face fy uses
+    // x[fy..fy+4] in upwind order, for v < 0 it uses x[fy+5..fy+1].  The smoothness
+    // forms are those of the full g = dg + w rho_ref sin(theta) (first and second
+    // differences of sin from the FP64 tables); P2 is taken on dg alone.
     if constexpr (!LIN) {
-        const float kinv = R.ktheta;
-        const f2 c13 = splat((13.0f / 12.0f) * kinv), c14 = splat(0.25f * kinv), one = splat(1.0f);
+        const f2 E = splat(R.e_theta), c133 = splat(13.0f / 3.0f);
         const f2 two = splat(2.0f), m2 = splat(-2.0f);
 #pragma unroll 1
         for (int q = warp; q < NP2; q += NT / 32) {
             const int g = q >> 2;
             const f2 wr = R.wr[q];
-            const f2 vt = c.vth[g];
+            const f2 vt = mul2(c.vth[g], splat(__fmul_rn(dte, R.inv_dth)));
             const f2 *col = &S.tile[q][0][lane + GC];
             // values are produced one row ahead of their first use (face fy needs rows up to fy+5)
-            f2 x[SR], dd[SR], dfu[SR], D2[SR], Qp[SR];
+            f2 x[SR], dd[SR], dfu[SR], D2[SR], Qa[SR];
 #pragma unroll
             for (int r = 0; r < 5; ++r) x[r] = col[r * SC];
 #pragma unroll
@@ -344,7 +363,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
 #pragma unroll
             for (int r = 1; r < 4; ++r) {
                 D2[r] = fma2(wr, S.d2s2[r], sub2(dd[r + 1], dd[r]));
-                Qp[r] = fma2(mul2(D2[r], c13), D2[r], one);
+                Qa[r] = fma2(mul2(D2[r], c133), D2[r], E);
             }
 #pragma unroll
             for (int fy = 0; fy <= TY; ++fy) {
@@ -354,11 +373,11 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                     dd[r] = sub2(x[r], x[r - 1]);
                     dfu[r] = fma2(wr, S.ds2[r], dd[r]);
                     D2[r - 1] = fma2(wr, S.d2s2[r - 1], sub2(dd[r], dd[r - 1]));
-                    Qp[r - 1] = fma2(mul2(D2[r - 1], c13), D2[r - 1], one);
+                    Qa[r - 1] = fma2(mul2(D2[r - 1], c133), D2[r - 1], E);
                 }
                 f2 B1, B2, B3, Q1, Q2, Q3, d12, d23, p2;
                 if (g) {   // v_theta > 0: a..e = x[fy..fy+4]
-                    Q1 = Qp[fy + 1]; Q2 = Qp[fy + 2]; Q3 = Qp[fy + 3];
+                    Q1 = Qa[fy + 1]; Q2 = Qa[fy + 2]; Q3 = Qa[fy + 3];
                     B1 = fma2(two, dfu[fy + 2], D2[fy + 1]);
                     B2 = add2(dfu[fy + 2], dfu[fy + 3]);
                     B3 = fma2(m2, dfu[fy + 3], D2[fy + 3]);
@@ -366,7 +385,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                     d23 = sub2(D2[fy + 2], D2[fy + 3]);
                     p2 = fma2(splat(1.0f / 6.0f), dd[fy + 2], fma2(splat(1.0f / 3.0f), dd[fy + 3], x[fy + 2]));
                 } else {   // v_theta < 0: a..e = x[fy+5..fy+1]
-                    Q1 = Qp[fy + 4]; Q2 = Qp[fy + 3]; Q3 = Qp[fy + 2];
+                    Q1 = Qa[fy + 4]; Q2 = Qa[fy + 3]; Q3 = Qa[fy + 2];
                     B1 = fma2(m2, dfu[fy + 4], D2[fy + 4]);
                     B2 = add2(dfu[fy + 4], dfu[fy + 3]);
                     B3 = fma2(two, dfu[fy + 3], D2[fy + 2]);
@@ -374,16 +393,10 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                     d23 = sub2(D2[fy + 3], D2[fy + 2]);
                     p2 = fma2(splat(-1.0f / 6.0f), dd[fy + 4], fma2(splat(-1.0f / 3.0f), dd[fy + 3], x[fy + 3]));
                 }
-                const f2 s1 = fma2(mul2(B1, c14), B1, Q1);
-                const f2 s2 = fma2(mul2(B2, c14), B2, Q2);
-                const f2 s3 = fma2(mul2(B3, c14), B3, Q3);
-                const f2 q1 = mul2(s1, s1), q2 = mul2(s2, s2), q3 = mul2(s3, s3);
-                const f2 q23 = mul2(q2, q3), q12 = mul2(q1, q2);
-                const f2 sum = fma2(splat(0.1f), q23, fma2(splat(0.6f), mul2(q1, q3), mul2(splat(0.3f), q12)));
-                const f2 rr = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
-                const f2 num = fma2(mul2(splat(0.1f / 3.0f), q23), d12, mul2(mul2(splat(0.05f), q12), d23));
                 // the reference part of P2 is the ideal-weight interpolant minus corr
-                S.ft[q][fy][lane] = mul2(vt, fma2(num, rr, add2(S.cw[q][fy], p2)));
+                const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23,
+                                      add2(S.cw[q][fy], p2));
+                S.ft[q][fy][lane] = mul2(vt, v);
             }
         }
     }
@@ -403,7 +416,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     f2 G[NP2];
 #pragma unroll
     for (int q = 0; q < NP2; ++q) G[q] = S.tile[q][cy + GR][cx + GC];
-    // moments of delta f = dg / s
+    // moments of delta f = dg / (k s)
     f2 sn = G[0], sjt = mul2(c.vth[0], G[0]), sjp = mul2(c.vphi2[0], G[0]);
 #pragma unroll
     for (int q = 1; q < NP2; ++q) {
@@ -418,9 +431,19 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const float up = (sjp.x + sjp.y) * rc.inv_s * nin;
     const float u2 = fmaf(ut, ut, up * up);
     const f2 h0 = splat(-0.5f * u2), h1 = splat(fmaf(-0.5f, u2, 1.0f));
-    const f2 ut2 = splat(ut), snn = splat(rc.s * n), sg2 = splat(SG);
-    const f2 cot2 = splat(rc.cotR), idph = splat(rc.inv_dph), mtau = splat(-R.tau_inv);
-    // theta flux difference to the dg tendency: 1/(R dtheta), or s / (R dcos) for the Komissarov flux
+    // BGK share of the update: dg is weighted by cG - dte/tau and s feq_dev by dte/tau.  The
+    // second weight is taken as the exact FP32 complement sc = cG0 - RN(cG0 - dte/tau), so
+    // the two sum to the stage's weight of dg exactly and the collision (which conserves
+    // sum_k) leaves no systematic drift of the mass; likewise the stage-3 weight of F0 is
+    // the exact complement 1 - RN(2/3).
+    const float cg0 = (stage == 1) ? 1.0f : (stage == 2) ? 0.25f : (2.0f / 3.0f);
+    const float cgv = __fsub_rn(cg0, __fmul_rn(dte, R.tau_inv));
+    const float sc = __fsub_rn(cg0, cgv);
+    const f2 ut2 = splat(ut), up2 = splat(up), snn = splat(__fmul_rn(__fmul_rn(sc, rc.s), n)), sg2 = splat(__fmul_rn(sc, SG));
+    const f2 ncot = splat(__fmul_rn(-dte, rc.cotR));
+    const f2 cG = splat(cgv);
+    const f2 cF = splat((stage == 2) ? 0.75f : __fsub_rn(1.0f, 2.0f / 3.0f));
+    // upwind theta faces: 1/(R dtheta), or s / (R dcos) for the Komissarov flux
     const f2 idth = splat((LIN && R.komissarov) ? rc.kth : R.inv_dth);
 
     f2 o[NP2];
@@ -428,28 +451,21 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     for (int q = 0; q < NP2; ++q) {
         const int g = q >> 2, b = q & 3;
         // equilibrium deviation times s: w (s dn + s n poly(xi)), poly = xi + (xi^2-u^2)/2 + xi(xi^2-3u^2)/6
-        const f2 xi = fma2(c.vth[g], ut2, mul2(c.vphi2[b], splat(up)));
+        const f2 xi = fma2(c.vth[g], ut2, mul2(c.vphi2[b], up2));
         const f2 poly = fma2(xi, fma2(xi, fma2(xi, splat(1.0f / 6.0f), splat(0.5f)), h1), h0);
-        const f2 sfeq = mul2(c.w2[q], fma2(snn, poly, sg2));
         // force on dg: K along k_theta (pairs (0,b),(1,b) and (2,b),(3,b), with swapped partners), Ktilde along k_phi
         const f2 P0 = G[b], P1 = G[4 + b];
         const f2 kg = fma2(c.kpair[g][0], P0, fma2(c.kpair[g][1], swap2(P0), fma2(c.kpair[g][2], P1, mul2(c.kpair[g][3], swap2(P1)))));
         const f2 *Gg = G + 4 * g;
         const f2 ktg = fma2(c.Kt2[4 * b], Gg[0], fma2(c.Kt2[4 * b + 1], Gg[1], fma2(c.Kt2[4 * b + 2], Gg[2], mul2(c.Kt2[4 * b + 3], Gg[3]))));
-        const f2 force = mul2(cot2, fma2(c.vphisq2[b], kg, mul2(c.mvth[g], ktg)));
-        // flux differences
-        const f2 adv_t = mul2(sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]), idth);
-        const f2 adv_p = mul2(sub2(S.fp[q][cy][cx], S.fp[q][cy][cx + 1]), idph);
-        // L on dg: advection - force - (dg - s feq_dev)/tau + s rref
-        f2 Lq = sub2(add2(add2(adv_t, adv_p), S.rr[cy][q]), force);
-        Lq = fma2(sub2(G[q], sfeq), mtau, Lq);
-        if (stage == 1) {
-            o[q] = fma2(splat(R.dt), Lq, G[q]);
-        } else if (stage == 2) {
-            o[q] = fma2(splat(0.25f * R.dt), Lq, fma2(splat(0.75f), F0[q], mul2(splat(0.25f), G[q])));
-        } else {
-            o[q] = fma2(splat((2.0f / 3.0f) * R.dt), Lq, fma2(splat(1.0f / 3.0f), F0[q], mul2(splat(2.0f / 3.0f), G[q])));
-        }
+        // dte times: flux differences + s rref - force + s feq_dev / tau
+        const f2 adv_t = LIN ? mul2(sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]), idth) : sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]);
+        const f2 adv_p = sub2(S.fp[q][cy][cx], S.fp[q][cy][cx + 1]);
+        f2 a = add2(add2(adv_t, adv_p), S.rr[cy][q]);
+        a = fma2(ncot, fma2(c.vphisq2[b], kg, mul2(c.mvth[g], ktg)), a);
+        a = fma2(c.w2[q], fma2(snn, poly, sg2), a);
+        o[q] = fma2(cG, G[q], a);
+        if (stage != 1) o[q] = fma2(cF, F0[q], o[q]);
     }
     const bool plain = (i >= GR && i < L.nt - GR && j >= GC && j < L.np - GC);
     if (plain) {
@@ -526,14 +542,14 @@ __device__ __forceinline__ int pair_of(int k) { return 4 * ((k >> 2) >> 1) + (k 
 __device__ __forceinline__ int member_of(int k) { return (k >> 2) & 1; }
 
 __global__ void init_f32_kernel(f2 *f, const Layout L, const double *rho, const double *ut, const double *up,
-                                const double *temp, const VelD c, double rho_ref, const double *sin_t)
+                                const double *temp, const VelD c, double rho_ref, const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= L.np) return;
     const size_t cell = (size_t)i * L.np + j;
     const double tt = temp ? temp[cell] : 1.0;
-    const double s = sin_t[i];
+    const double s = ks * sin_t[i];
     float v[16];
     for (int k = 0; k < NK; ++k) {
         const int a = k / 4, b = k % 4;
@@ -547,12 +563,12 @@ __global__ void init_f32_kernel(f2 *f, const Layout L, const double *rho, const 
 }
 
 __global__ void moments_f32_kernel(const f2 *f, const Layout L, double *rho, double *ut, double *up, double *temp,
-                                   const VelD c, double rho_ref, const double *sin_t)
+                                   const VelD c, double rho_ref, const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= L.np) return;
-    const double inv_s = 1.0 / sin_t[i];
+    const double inv_s = 1.0 / (ks * sin_t[i]);
     double fk[NK];
     for (int k = 0; k < NK; ++k) {
         const f2 pr = f[L.at(pair_of(k), i, j)];
@@ -581,18 +597,18 @@ __global__ void moments_f32_kernel(const f2 *f, const Layout L, double *rho, dou
 }
 
 __global__ void pack_f32_kernel(const f2 *f, const Layout L, double *dense, const VelD c, double rho_ref,
-                                const double *sin_t)
+                                const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y, k = blockIdx.z;
     if (j >= L.np) return;
     const f2 pr = f[L.at(pair_of(k), i, j)];
-    const double d = (double)(member_of(k) ? pr.y : pr.x) / sin_t[i];
+    const double d = (double)(member_of(k) ? pr.y : pr.x) / (ks * sin_t[i]);
     dense[((size_t)k * L.nt + i) * L.np + j] = c.w[k / 4] * c.w[k % 4] * rho_ref + d;
 }
 
 __global__ void unpack_f32_kernel(const double *dense, const Layout L, f2 *f, const VelD c, double rho_ref,
-                                  const double *sin_t)
+                                  const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y, q = blockIdx.z;
@@ -601,7 +617,7 @@ __global__ void unpack_f32_kernel(const double *dense, const Layout L, f2 *f, co
     float m[2];
     for (int h = 0; h < 2; ++h) {
         const int a = 2 * g + h, k = 4 * a + b;
-        m[h] = (float)(sin_t[i] * (dense[((size_t)k * L.nt + i) * L.np + j] - c.w[a] * c.w[b] * rho_ref));
+        m[h] = (float)(ks * sin_t[i] * (dense[((size_t)k * L.nt + i) * L.np + j] - c.w[a] * c.w[b] * rho_ref));
     }
     f[L.at(q, i, j)] = make_float2(m[0], m[1]);
 }
@@ -834,10 +850,10 @@ constexpr int DIAG_THREADS = 256;
 constexpr int NDIAG = 6;
 
 __global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *sin_t, const double *cos_t,
-                                     const VelD c, double area, double rho_ref, double *part)
+                                     const VelD c, double area, double rho_ref, double ks, double *part)
 {
     const int i = blockIdx.x;
-    const double st = sin_t[i], ct = cos_t[i], inv_s = 1.0 / st;
+    const double st = sin_t[i], ct = cos_t[i], inv_s = 1.0 / (ks * st);
     const double dph = 6.283185307179586476925286766559 / L.np;
     double acc[NDIAG] = {0, 0, 0, 0, 0, 0};
     for (int j = threadIdx.x; j < L.np; j += DIAG_THREADS) {
@@ -931,32 +947,39 @@ void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2
     }
 }
 
+double f32_state_scale(double eps)
+{
+    int m = (int)std::lround(std::log2(0.5 / std::sqrt(eps)));
+    m = std::max(-60, std::min(60, m));
+    return std::ldexp(1.0, m);
+}
+
 void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,
-                     const double *T, const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s)
+                     const double *T, const VelD &c, double rho_ref, const double *sin_t, double ks, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt);
-    init_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref, sin_t);
+    init_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref, sin_t, ks);
 }
 
 void launch_moments_f32(const float2 *f, const Layout &L, double *rho, double *ut, double *up, double *T,
-                        const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s)
+                        const VelD &c, double rho_ref, const double *sin_t, double ks, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt);
-    moments_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref, sin_t);
+    moments_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref, sin_t, ks);
 }
 
 void launch_pack_f32(const float2 *f, const Layout &L, double *dense, const VelD &c, double rho_ref,
-                     const double *sin_t, cudaStream_t s)
+                     const double *sin_t, double ks, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt, NK);
-    pack_f32_kernel<<<grid, 128, 0, s>>>(f, L, dense, c, rho_ref, sin_t);
+    pack_f32_kernel<<<grid, 128, 0, s>>>(f, L, dense, c, rho_ref, sin_t, ks);
 }
 
 void launch_unpack_f32(const double *dense, const Layout &L, float2 *f, const VelD &c, double rho_ref,
-                       const double *sin_t, cudaStream_t s)
+                       const double *sin_t, double ks, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt, NP2);
-    unpack_f32_kernel<<<grid, 128, 0, s>>>(dense, L, f, c, rho_ref, sin_t);
+    unpack_f32_kernel<<<grid, 128, 0, s>>>(dense, L, f, c, rho_ref, sin_t, ks);
 }
 
 void launch_fill_ghosts_f32(float2 *f, const Layout &L, cudaStream_t s)
@@ -979,9 +1002,10 @@ void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *b
 }
 
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,
-                            const VelD &c, double area, double rho_ref, double *part, double *out, cudaStream_t s)
+                            const VelD &c, double area, double rho_ref, double ks, double *part, double *out,
+                            cudaStream_t s)
 {
-    diag_rows_f32_kernel<<<L.nt, DIAG_THREADS, 0, s>>>(f, L, sin_t, cos_t, c, area, rho_ref, part);
+    diag_rows_f32_kernel<<<L.nt, DIAG_THREADS, 0, s>>>(f, L, sin_t, cos_t, c, area, rho_ref, ks, part);
     launch_diag_final(part, L.nt, out, s);
 }
 

@@ -164,7 +164,7 @@ int build_f32_tables(vlbm_t *h)
     const double R = h->R, dth = M_PI / nt, dph = 2.0 * M_PI / h->np;
     const VelD &c = h->vd;
     VelC &f = h->vc;
-    const double rr = h->rho_ref;
+    const double rr = h->rho_ref, ks = h->kscale;
     for (int g = 0; g < 2; ++g) {
         f.vth[g] = make_float2((float)c.v[2 * g], (float)c.v[2 * g + 1]);
         f.mvth[g] = make_float2((float)-c.v[2 * g], (float)-c.v[2 * g + 1]);
@@ -182,7 +182,7 @@ int build_f32_tables(vlbm_t *h)
     for (int q = 0; q < 8; ++q) {
         const int g = q / 4, b = q % 4;
         f.w2[q] = make_float2((float)(c.w[2 * g] * c.w[b]), (float)(c.w[2 * g + 1] * c.w[b]));
-        run.wr[q] = make_float2((float)(c.w[2 * g] * c.w[b] * rr), (float)(c.w[2 * g + 1] * c.w[b] * rr));
+        run.wr[q] = make_float2((float)(ks * c.w[2 * g] * c.w[b] * rr), (float)(ks * c.w[2 * g + 1] * c.w[b] * rr));
     }
     for (int q = 0; q < 16; ++q) f.Kt2[q] = make_float2((float)c.Kt[q], (float)c.Kt[q]);
     run.rho_ref = (float)rr;
@@ -232,11 +232,11 @@ int build_f32_tables(vlbm_t *h)
     for (int i = 0; i < nt; ++i) {
         const double s = h->sin_t[i], cot = h->cos_t[i] / h->sin_t[i];
         RowF rc;
-        rc.s = (float)s;
-        rc.inv_s = (float)(1.0 / s);
+        rc.s = (float)(ks * s);
+        rc.inv_s = (float)(1.0 / (ks * s));
         rc.inv_dph = (float)(1.0 / (R * s * dph));
         rc.cotR = (float)(cot / R);
-        rc.kphi = (float)(1.0 / (h->eps * s * s));
+        rc.ephi = (float)(4.0 * h->eps * s * s * ks * ks);
         rc.kth = (float)(s / (R * (h->cos_f[i] - h->cos_f[i + 1])));
         rc.pad1 = rc.pad2 = 0.0f;
         row[i] = rc;
@@ -260,7 +260,7 @@ int build_f32_tables(vlbm_t *h)
                 ktw += c.Kt[b * 4 + m] * c.w[a] * c.w[m] * rr;
             }
             const double force = cot / R * (vb * vb * kw - va * ktw);
-            rk[k] = s * (adv - force);
+            rk[k] = ks * s * (adv - force);
         }
         for (int q = 0; q < 8; ++q) {
             const int g = q / 4, b = q % 4;
@@ -302,7 +302,7 @@ int build_f32_tables(vlbm_t *h)
     run.L = h->L;
     run.tau_inv = (float)(1.0 / h->tau);
     run.dt = (float)h->dt;
-    run.ktheta = (float)(1.0 / h->eps);
+    run.e_theta = (float)(4.0 * h->eps * ks * ks);
     run.inv_dth = (float)(1.0 / (h->R * (M_PI / h->nt)));
     run.tiles_x = (h->np + F32_TILE_COLS - 1) / F32_TILE_COLS;
     return VLBM_OK;
@@ -490,6 +490,7 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     h->tau = tau;
     h->dt = dt;
     h->eps = o.weno_eps;
+    h->kscale = (o.precision == VLBM_FP32) ? f32_state_scale(o.weno_eps) : 1.0;
     h->R = o.radius;
     h->filter = o.polar_filter ? 1 : 0;
     h->guard = o.guard ? 1 : 0;
@@ -629,7 +630,7 @@ int vlbm_init_moments(vlbm_t *h, const double *rho, const double *u_theta, const
             drop_graphs(h);
         }
         launch_init_f32((float2 *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->rho_ref,
-                        h->d_sin_t, h->stream);
+                        h->d_sin_t, h->kscale, h->stream);
     }
     CK(h, cudaGetLastError());
     return after_reset(h);
@@ -658,7 +659,7 @@ int vlbm_set_populations(vlbm_t *h, const double *f)
             if (rc) return rc;
             drop_graphs(h);
         }
-        launch_unpack_f32(h->d_dense, h->L, (float2 *)h->F, h->vd, h->rho_ref, h->d_sin_t, h->stream);
+        launch_unpack_f32(h->d_dense, h->L, (float2 *)h->F, h->vd, h->rho_ref, h->d_sin_t, h->kscale, h->stream);
     }
     CK(h, cudaGetLastError());
     return after_reset(h);
@@ -673,7 +674,7 @@ int vlbm_get_populations(vlbm_t *h, double *f)
         if (rc) return rc;
     }
     if (h->prec == VLBM_FP64) launch_pack_f64((const double *)h->F, h->L, h->d_dense, h->stream);
-    else launch_pack_f32((const float2 *)h->F, h->L, h->d_dense, h->vd, h->rho_ref, h->d_sin_t, h->stream);
+    else launch_pack_f32((const float2 *)h->F, h->L, h->d_dense, h->vd, h->rho_ref, h->d_sin_t, h->kscale, h->stream);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(f, h->d_dense, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -730,7 +731,7 @@ int vlbm_moments(vlbm_t *h, double *rho, double *u_theta, double *u_phi, double 
         launch_moments_f64((const double *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->stream);
     else
         launch_moments_f32((const float2 *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd,
-                           h->rho_ref, h->d_sin_t, h->stream);
+                           h->rho_ref, h->d_sin_t, h->kscale, h->stream);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(u_theta, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -749,7 +750,7 @@ int vlbm_diagnostics(vlbm_t *h, vlbm_diag *out)
                                h->stream);
     else
         launch_diagnostics_f32((const float2 *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->vd, area, h->rho_ref,
-                               h->d_part, h->d_diag, h->stream);
+                               h->kscale, h->d_part, h->d_diag, h->stream);
     CK(h, cudaGetLastError());
     double v[8];
     CK(h, cudaMemcpyAsync(v, h->d_diag, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

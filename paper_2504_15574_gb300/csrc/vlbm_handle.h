@@ -47,6 +47,7 @@ struct vlbm {
     vk::RunF run{};    // FP32 path: per-run stage parameters
     int ty = 8;    // FP32 path: tile rows
     double rho_ref = 0.0, rho_ref_opt = 0.0;
+    double kscale = 1.0;   // FP32 path: state scale k (a power of two), dg = k sin (f - w rho_ref)
     long long steps = 0;
     double mass0 = 0.0;
     std::string err;

@@ -60,25 +60,28 @@ struct StageD {
 void launch_stage_f64(const StageD &p, cudaStream_t s);
 
 // ---- FP32 deviation stage (throughput path) -------------------------------------
-// The FP32 array holds dg = sin(theta) (f - w_k rho_ref) in 8 pair planes of float2:
-// pair p = 4 g + b holds populations (2g, b) and (2g+1, b).
+// The FP32 array holds dg = k sin(theta) (f - w_k rho_ref) in 8 pair planes of float2:
+// pair p = 4 g + b holds populations (2g, b) and (2g+1, b).  k is the power of two of the
+// run's state scale (f32_state_scale): scaling by it is exact, so every value is k times
+// the unscaled one bit for bit, and it sets the WENO regulariser 4 eps k^2 near 1.
 // Per theta face and upwind direction: the smoothness linear forms of the stencil applied to
 // sin(theta) and corr = 0.1 (P1-P2) + 0.3 (P3-P2) of sin(theta) (ideal-weight interpolant minus P2).
 struct FaceConst { float sa1, sb1, sa2, sb2, sa3, sb3, corr, pad; };
-// Per interior row: s = sin(theta), 1/s, 1/(R s dphi), cot(theta)/R, 1/(eps s^2), and for the
-// Komissarov theta flux kth = s / (R (cos theta_{i-1/2} - cos theta_{i+1/2})).
-struct RowF { float s, inv_s, inv_dph, cotR, kphi, kth, pad1, pad2; };
+// Per interior row: k s (s = sin(theta)), 1/(k s), 1/(R s dphi), cot(theta)/R, the phi WENO
+// regulariser ephi = 4 eps s^2 k^2 (the WENO on f has eps; on dg = k s f its forms carry k s),
+// and for the Komissarov theta flux kth = s / (R (cos theta_{i-1/2} - cos theta_{i+1/2})).
+struct RowF { float s, inv_s, inv_dph, cotR, ephi, kth, pad1, pad2; };
 // Per-run parameters of the FP32 stage: one solver, or one member of a batch.
 struct RunF {
     float2 *F, *A, *B;         // dg at the step start, after stage 1, after stage 2 (pair layout)
     const FaceConst *face;     // [nt+1][2]: face between rows fi-1 and fi, dir 0: v>0, 1: v<0
     const RowF *row;           // [nt]
-    const float2 *rref;        // [nt][8] s * (FP64-derived tendency of the reference state)
+    const float2 *rref;        // [nt][8] k s * (FP64-derived tendency of the reference state)
     const float *dsin;         // [nt + 2GR + 8] sin(pr) - sin(pr-1) at padded row pr (0 where undefined)
     const float *d2sin;        // [nt + 2GR + 8] sin(pr-1) - 2 sin(pr) + sin(pr+1)
     Layout L;
-    float tau_inv, dt, ktheta, inv_dth;   // ktheta = 1/eps, inv_dth = 1/(R dtheta)
-    float2 wr[8];              // w_k rho_ref per pair
+    float tau_inv, dt, e_theta, inv_dth;  // e_theta = 4 eps k^2, inv_dth = 1/(R dtheta)
+    float2 wr[8];              // k w_k rho_ref per pair
     float rho_ref;
     int tiles_x;               // tiles per row of this run for the launch's tile shape
     // upwind schemes U1-U3 (Eq. fluxes_U1-3): interface value = lin0 x_up2 + lin1 x_up + lin2 x_down
@@ -113,20 +116,25 @@ void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2
                             int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s);
 int stage_f32_max_ctas_per_sm(int ty);
 
+// State scale k of the FP32 storage for WENO regulariser eps: the power of two nearest
+// 1 / (2 sqrt(eps)), so that 4 eps k^2 lies in [1/2, 2].
+double f32_state_scale(double eps);
+// The conversions below take the run's state scale ks (dg = ks sin(theta) (f - w rho_ref)).
 void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,
-                     const double *T, const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s);
+                     const double *T, const VelD &c, double rho_ref, const double *sin_t, double ks, cudaStream_t s);
 void launch_moments_f32(const float2 *f, const Layout &L, double *rho, double *ut, double *up, double *T,
-                        const VelD &c, double rho_ref, const double *sin_t, cudaStream_t s);
+                        const VelD &c, double rho_ref, const double *sin_t, double ks, cudaStream_t s);
 void launch_pack_f32(const float2 *f, const Layout &L, double *dense, const VelD &c, double rho_ref,
-                     const double *sin_t, cudaStream_t s);
+                     const double *sin_t, double ks, cudaStream_t s);
 void launch_unpack_f32(const double *dense, const Layout &L, float2 *f, const VelD &c, double rho_ref,
-                       const double *sin_t, cudaStream_t s);
+                       const double *sin_t, double ks, cudaStream_t s);
 void launch_fill_ghosts_f32(float2 *f, const Layout &L, cudaStream_t s);
 void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s);
 // Polar filter of every (run, row, block size) item of a batch on the output array of `stage`.
 void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int stage, cudaStream_t s);
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,
-                            const VelD &c, double area, double rho_ref, double *part, double *out, cudaStream_t s);
+                            const VelD &c, double area, double rho_ref, double ks, double *part, double *out,
+                            cudaStream_t s);
 
 // ---- FP64 helpers -------------------------------------------------------------------
 void launch_init_f64(double *f, const Layout &L, const double *rho, const double *ut, const double *up,
