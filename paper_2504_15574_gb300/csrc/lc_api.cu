@@ -345,7 +345,7 @@ int vlbm_lc_rollout(vlbm_lc_t *n, vlbm_t *h, int steps)
     if ((rc = check_solver(n, h))) return rc;
     if (steps < 0) return lfail(n, VLBM_ERR_ARG, "negative step count");
     if (steps == 0) return VLBM_OK;
-    if (!h->d_face) return lfail(n, VLBM_ERR_ARG, "FP32 state not initialised");
+    if (!h->d_row) return lfail(n, VLBM_ERR_ARG, "FP32 state not initialised");
     if (n->g_solver != h && n->g_exec) {
         cudaGraphExecDestroy(n->g_exec);
         n->g_exec = nullptr;

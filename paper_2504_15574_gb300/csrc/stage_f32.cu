@@ -24,11 +24,12 @@
 //      4 k^2 (sigma + eps), a common factor of the ratios); the theta weights are
 //      those of the full g = k sin(theta) w_k rho_ref + dg: each smoothness form is
 //      the dg part plus k w_k rho_ref times the form of sin(theta) (FP64 table).  The
-//      reconstruction is written P2 + wbar1 (P1 - P2) + wbar3 (P3 - P2); its
-//      reference part is the ideal-weight interpolant (folded, with the force of the
-//      reference state, into the FP64-derived tendency rref) minus corr, plus the
-//      weight terms, which use the full forms.  Face values carry the stage's dt
-//      share and their metric factor;
+//      reconstruction is written P2 + wbar1 (P1 - P2) + wbar3 (P3 - P2); P2 of the
+//      reference part is linear in sin(theta), so its flux difference is folded, with
+//      the force of the reference state, into the FP64-derived tendency rref, and the
+//      weight terms use the full forms.  Each phi face row is walked by a few threads
+//      that keep the columns' differences in registers.  Face values carry the
+//      stage's dt share and their metric factor;
 //   3. per cell: moments (Eq. f_moments_sum), equilibrium (Eq. feq_Q=4), BGK,
 //      force through K^H / Ktilde^H (Eq. df), flux differences and the stage
 //      combination, all on dg (the operator commutes with the row factor), then
@@ -44,7 +45,7 @@ namespace {
 
 constexpr int TX = F32_TILE_COLS;
 constexpr int NP2 = 8;                 // population pairs
-constexpr int SC = TX + 2 * GC;        // tile columns in shared memory
+constexpr int SC = F32_BOX_COLS;       // tile columns in shared memory (TX + 2 GC + 2)
 
 template <int TY>
 struct __align__(128) SmemT {
@@ -53,7 +54,6 @@ struct __align__(128) SmemT {
     float2 fp[NP2][TY][TX + 1];         // phi faces: face fx between cell columns fx-1 and fx
     float2 ds2[TY + 2 * GR];            // (dsin, dsin) at the tile rows
     float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
-    float2 cw[NP2][TY + 1];             // -w rho_ref corr per pair and theta face row
     float2 rr[TY][NP2];                 // dte s rref per cell row and pair
     float2 isp2[TY + 2 * GR];           // upwind schemes, Komissarov: (1/sin, 1/sin) at the tile rows
     float2 sf2[TY + 1];                 // upwind schemes, Komissarov: interface sines of the face rows
@@ -61,6 +61,9 @@ struct __align__(128) SmemT {
     RunF run;                           // batch kernel: this tile's run
     unsigned long long bar;
 };
+
+// three CTAs of 8 tile rows per SM: 228 KB of shared memory per SM, 1 KB reserved per CTA
+static_assert(3 * (sizeof(SmemT<8>) + 128 + 1024) <= 228 * 1024, "stage tile exceeds a third of an SM's shared memory");
 
 typedef float2 f2;
 
@@ -130,21 +133,79 @@ __device__ __forceinline__ f2 weno_mix(f2 t1, f2 t2, f2 t3, f2 d12, f2 d23, f2 p
     return fma2(num, r, p2);
 }
 
-// WENO-5 interface value of the upwind-ordered values a..e (packed pairs), E the
-// regulariser of the row.  The stencil forms are built from the first differences
-// d1..d4: A_i = d_{i+1} - d_i, B1 = A1 + 2 d2, |B2| = |d2 + d3|, B3 = A3 - 2 d3 and
-// P2 = c + (d2 + 2 d3)/6.
-__device__ __forceinline__ f2 weno_face(f2 a, f2 b, f2 c, f2 d, f2 e, f2 E)
+// WENO-5 phi faces f0 .. f0 + NF - 1 of one row of one pair plane.  In upwind order a..e the
+// stencil forms are built from the first differences d1..d4: A_i = d_{i+1} - d_i,
+// B1 = A1 + 2 d2, |B2| = |d2 + d3|, B3 = A3 - 2 d3 and P2 = c + (d2 + 2 d3)/6.  The faces are
+// walked in order so that
+// every column's first difference d[m] = x[m] - x[m-1], second difference A[m] = d[m+1] - d[m]
+// (centred at m) and row term Q[m] = 13/3 A[m]^2 + E are formed once, and so is each
+// A difference (d23 of a face is d12 of the next).  DIR = +1 for v_phi > 0 (face fx reads
+// shared columns fx+1 .. fx+5 in upwind order), -1 for v_phi < 0 (fx+6 .. fx+2).  The
+// columns are read as 16-byte pairs starting at shared column f0 + LO (even).  Face j's
+// value times vb goes to out[j] for j < nst.
+template <int NF, int DIR>
+__device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2 *out, int nst)
 {
+    constexpr int LO = (DIR > 0) ? 0 : 2;
+    constexpr int NX = ((NF + 5) + 1) & ~1;
     const f2 two = splat(2.0f), m2 = splat(-2.0f), c133 = splat(13.0f / 3.0f);
-    const f2 d1 = sub2(b, a), d2 = sub2(c, b), d3 = sub2(d, c), d4 = sub2(e, d);
-    const f2 A1 = sub2(d2, d1), A2 = sub2(d3, d2), A3 = sub2(d4, d3);
-    const f2 B1 = fma2(two, d2, A1), B2 = add2(d2, d3), B3 = fma2(m2, d3, A3);
-    const f2 t1 = fma2(B1, B1, fma2(mul2(A1, c133), A1, E));
-    const f2 t2 = fma2(B2, B2, fma2(mul2(A2, c133), A2, E));
-    const f2 t3 = fma2(B3, B3, fma2(mul2(A3, c133), A3, E));
-    const f2 p2 = fma2(splat(1.0f / 3.0f), d3, fma2(splat(1.0f / 6.0f), d2, c));
-    return weno_mix(t1, t2, t3, sub2(A1, A2), sub2(A2, A3), p2);
+    const float4 *src = reinterpret_cast<const float4 *>(row + f0 + LO);
+    f2 x[NX], d[NX], A[NX], Q[NX];
+#pragma unroll
+    for (int m = 0; m < NX / 2; ++m) {
+        const float4 v = src[m];
+        x[2 * m] = make_float2(v.x, v.y);
+        x[2 * m + 1] = make_float2(v.z, v.w);
+    }
+    if constexpr (DIR > 0) {
+        // face j: a..e = x[j+1..j+5]; A1..A3 = A[j+2..j+4], d2 = d[j+3], d3 = d[j+4], c = x[j+3]
+#pragma unroll
+        for (int m = 2; m <= 4; ++m) d[m] = sub2(x[m], x[m - 1]);
+#pragma unroll
+        for (int m = 2; m <= 3; ++m) {
+            A[m] = sub2(d[m + 1], d[m]);
+            Q[m] = fma2(mul2(A[m], c133), A[m], E);
+        }
+        f2 d12 = sub2(A[2], A[3]);
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            d[j + 5] = sub2(x[j + 5], x[j + 4]);
+            A[j + 4] = sub2(d[j + 5], d[j + 4]);
+            Q[j + 4] = fma2(mul2(A[j + 4], c133), A[j + 4], E);
+            const f2 B1 = fma2(two, d[j + 3], A[j + 2]);
+            const f2 B2 = add2(d[j + 3], d[j + 4]);
+            const f2 B3 = fma2(m2, d[j + 4], A[j + 4]);
+            const f2 p2 = fma2(splat(1.0f / 3.0f), d[j + 4], fma2(splat(1.0f / 6.0f), d[j + 3], x[j + 3]));
+            const f2 d23 = sub2(A[j + 3], A[j + 4]);
+            const f2 v = weno_mix(fma2(B1, B1, Q[j + 2]), fma2(B2, B2, Q[j + 3]), fma2(B3, B3, Q[j + 4]), d12, d23, p2);
+            if (j < nst) out[j] = mul2(vb, v);
+            d12 = d23;
+        }
+    } else {
+        // face j: a..e = x[j+4..j]; A1..A3 = A[j+3], A[j+2], A[j+1], d2 = -d[j+3], d3 = -d[j+2], c = x[j+2]
+#pragma unroll
+        for (int m = 1; m <= 3; ++m) d[m] = sub2(x[m], x[m - 1]);
+#pragma unroll
+        for (int m = 1; m <= 2; ++m) {
+            A[m] = sub2(d[m + 1], d[m]);
+            Q[m] = fma2(mul2(A[m], c133), A[m], E);
+        }
+        f2 d23 = sub2(A[2], A[1]);
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            d[j + 4] = sub2(x[j + 4], x[j + 3]);
+            A[j + 3] = sub2(d[j + 4], d[j + 3]);
+            Q[j + 3] = fma2(mul2(A[j + 3], c133), A[j + 3], E);
+            const f2 B1 = fma2(m2, d[j + 3], A[j + 3]);
+            const f2 B2 = add2(d[j + 2], d[j + 3]);
+            const f2 B3 = fma2(two, d[j + 2], A[j + 1]);
+            const f2 p2 = fma2(splat(-1.0f / 3.0f), d[j + 2], fma2(splat(-1.0f / 6.0f), d[j + 3], x[j + 2]));
+            const f2 d12 = sub2(A[j + 3], A[j + 2]);
+            const f2 v = weno_mix(fma2(B1, B1, Q[j + 3]), fma2(B2, B2, Q[j + 2]), fma2(B3, B3, Q[j + 1]), d12, d23, p2);
+            if (j < nst) out[j] = mul2(vb, v);
+            d23 = d12;
+        }
+    }
 }
 
 // Writes v at pair-plane cell (p, i, j) and at its ghost images.
@@ -222,12 +283,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             S.ds2[t] = splat(R.dsin[i0 + t]);
         } else if ((t -= SR) < SR) {
             S.d2s2[t] = splat(R.d2sin[i0 + t]);
-        } else if ((t -= SR) < NP2 * (TY + 1)) {
-            const int q = t / (TY + 1), fy = t - q * (TY + 1);
-            const int fi = min(i0 + fy, L.nt);
-            const float corr = R.face[2 * fi + ((q >> 2) ? 0 : 1)].corr;
-            S.cw[q][fy] = make_float2(-R.wr[q].x * corr, -R.wr[q].y * corr);
-        } else if ((t -= NP2 * (TY + 1)) < TY) {
+        } else if ((t -= SR) < TY) {
             S.rowc[t] = R.row[min(i0 + t, L.nt - 1)];
         } else if ((t -= TY) < TY * NP2) {
             const int ry = t >> 3, q = t & 7;
@@ -276,35 +332,21 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             S.fp[q][ry][fx] = mul2(vb, rec);
         }
     } else {
-        const int fy = warp;
-        const f2 E = splat(S.rowc[fy].ephi);
-        const f2 sp = splat(__fmul_rn(S.rowc[fy].inv_dph, dte));
-        // b outer: both pairs of a b share v_phi, its sign and the scaled velocity
+        // WENO-5: warp = pair (pairs warp, warp + TY, ...), lane = (segment sg, row r); segment sg
+        // walks faces SEG sg .. SEG sg + SEG of row r (the last is the next segment's first, so
+        // only the last segment stores it: the east face of the tile)
+        constexpr int NSEG = 32 / TY, SEG = TX / NSEG;
+        const int r = lane % TY, sg = lane / TY, f0 = sg * SEG;
+        const f2 E = splat(S.rowc[r].ephi);
+        const f2 sp = splat(__fmul_rn(S.rowc[r].inv_dph, dte));
+        const int nst = (sg == NSEG - 1) ? SEG + 1 : SEG;
 #pragma unroll 1
-        for (int b = 0; b < 4; ++b) {
-            const f2 vb = mul2(c.vphi2[b], sp);
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                const int q = 4 * g + b;
-                const f2 *row = &S.tile[q][fy + GR][0];
-                f2 r;
-                if (vb.x > 0.0f)   // columns fx-3 .. fx+1  (shared column = column + GC)
-                    r = weno_face(row[lane + 1], row[lane + 2], row[lane + 3], row[lane + 4], row[lane + 5], E);
-                else               // columns fx+2 .. fx-2
-                    r = weno_face(row[lane + 6], row[lane + 5], row[lane + 4], row[lane + 3], row[lane + 2], E);
-                S.fp[q][fy][lane] = mul2(vb, r);
-            }
-        }
-        // east face of the last column: NP2 x TY (pair, row) combinations
-        if (tid < NP2 * TY) {
-            const int q = tid / TY, ry = tid - (tid / TY) * TY;
-            const f2 vb = mul2(c.vphi2[q & 3], splat(__fmul_rn(S.rowc[ry].inv_dph, dte)));
-            const f2 Er = splat(S.rowc[ry].ephi);
-            const f2 *row = &S.tile[q][ry + GR][0];
-            const int fx = TX;
-            const f2 r = (vb.x > 0.0f) ? weno_face(row[fx + 1], row[fx + 2], row[fx + 3], row[fx + 4], row[fx + 5], Er)
-                                       : weno_face(row[fx + 6], row[fx + 5], row[fx + 4], row[fx + 3], row[fx + 2], Er);
-            S.fp[q][ry][fx] = mul2(vb, r);
+        for (int q = warp; q < NP2; q += NT / 32) {
+            const f2 vb = mul2(c.vphi2[q & 3], sp);
+            const f2 *row = &S.tile[q][r + GR][0];
+            f2 *out = &S.fp[q][r][f0];
+            if (vb.x > 0.0f) phi_march<SEG + 1, 1>(row, f0, E, vb, out, nst);
+            else phi_march<SEG + 1, -1>(row, f0, E, vb, out, nst);
         }
     }
 
@@ -393,9 +435,8 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                     d23 = sub2(D2[fy + 3], D2[fy + 2]);
                     p2 = fma2(splat(-1.0f / 6.0f), dd[fy + 4], fma2(splat(-1.0f / 3.0f), dd[fy + 3], x[fy + 3]));
                 }
-                // the reference part of P2 is the ideal-weight interpolant minus corr
-                const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23,
-                                      add2(S.cw[q][fy], p2));
+                // P2 of the reference part is in the FP64-derived tendency rref
+                const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
                 S.ft[q][fy][lane] = mul2(vt, v);
             }
         }

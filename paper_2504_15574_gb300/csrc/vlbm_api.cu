@@ -201,8 +201,9 @@ int build_f32_tables(vlbm_t *h)
     run.lin1 = (float)lin[1];
     run.lin2 = (float)lin[2];
     run.komissarov = h->komissarov;
-    // faces fi = 0..nt between rows fi-1 and fi; upwind-ordered sine stencils
-    std::vector<FaceConst> face(2 * (size_t)(nt + 1));
+    // the interface value of sin(theta) at faces fi = 0..nt (between rows fi-1 and fi) per
+    // upwind direction: for WENO-5 the candidate P2 (the kernel adds the nonlinear weight terms
+    // of the full g to P2 of the deviation), for the upwind schemes their linear stencil
     std::vector<double> plin(2 * (size_t)(nt + 1));
     for (int fi = 0; fi <= nt; ++fi)
         for (int dir = 0; dir < 2; ++dir) {
@@ -211,20 +212,8 @@ int build_f32_tables(vlbm_t *h)
                 const int r = (dir == 0) ? (fi - 3 + m) : (fi + 2 - m);
                 x[m] = sin_padded(h->sin_t, nt, r + GR);
             }
-            const double a = x[0], b = x[1], cc = x[2], d = x[3], e = x[4];
-            FaceConst F;
-            const double A1 = a - 2 * b + cc, A2 = b - 2 * cc + d, A3 = cc - 2 * d + e;
-            F.sa1 = (float)A1;
-            F.sb1 = (float)(a - 4 * b + 3 * cc);
-            F.sa2 = (float)A2;
-            F.sb2 = (float)(b - d);
-            F.sa3 = (float)A3;
-            F.sb3 = (float)(3 * cc - 4 * d + e);
-            F.corr = (float)(0.1 * (A1 - A2) / 3.0 + 0.3 * (A2 - A3) / 6.0);
-            F.pad = 0.0f;
-            face[2 * fi + dir] = F;
-            // the interface value of sin(theta) itself: WENO-5 with ideal weights, or the upwind stencil
-            plin[2 * fi + dir] = (h->scheme == VLBM_WENO5) ? (2 * a - 13 * b + 47 * cc + 27 * d - 3 * e) / 60.0
+            const double b = x[1], cc = x[2], d = x[3];
+            plin[2 * fi + dir] = (h->scheme == VLBM_WENO5) ? (-b + 5 * cc + 2 * d) / 6.0
                                                            : lin[0] * b + lin[1] * cc + lin[2] * d;
         }
     std::vector<RowF> row(nt);
@@ -246,9 +235,9 @@ int build_f32_tables(vlbm_t *h)
             const double va = c.v[a], vb = c.v[b];
             const double wr = c.w[a] * c.w[b] * rr;
             const int dir = va > 0 ? 0 : 1;
-            // theta advection of the reference part (WENO-5: with ideal weights; the upwind
-            // schemes are linear, so theirs is exact; Komissarov: the interface sines of
-            // v_theta w rho_ref), and its force
+            // theta advection of the reference part (WENO-5: its P2; the upwind schemes are
+            // linear, so theirs is exact; Komissarov: the interface sines of v_theta w rho_ref),
+            // and its force
             double adv;
             if (h->komissarov)
                 adv = -va * wr * (h->sin_f[i + 1] - h->sin_f[i]) / (R * (h->cos_f[i] - h->cos_f[i + 1]));
@@ -288,13 +277,11 @@ int build_f32_tables(vlbm_t *h)
     run.sfc = h->d_sfc;
     if ((rc = upload(h, &h->d_dsin, ds.data(), ds.size()))) return rc;
     if ((rc = upload(h, &h->d_d2sin, d2s.data(), d2s.size()))) return rc;
-    if ((rc = upload(h, &h->d_face, face.data(), face.size()))) return rc;
     if ((rc = upload(h, &h->d_row, row.data(), row.size()))) return rc;
     if ((rc = upload(h, &h->d_rref, rref.data(), rref.size()))) return rc;
     run.F = (float2 *)h->F;
     run.A = (float2 *)h->A;
     run.B = (float2 *)h->B;
-    run.face = h->d_face;
     run.row = h->d_row;
     run.rref = h->d_rref;
     run.dsin = h->d_dsin;
@@ -323,7 +310,7 @@ int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0)
     // pair planes of float2, described as 8-byte elements
     cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)(h->nt + 2 * GR), (cuuint64_t)(NK / 2)};
     cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * sizeof(float2), (cuuint64_t)h->L.plane * sizeof(float2)};
-    cuuint32_t box[3] = {(cuuint32_t)(F32_TILE_COLS + 2 * GC), (cuuint32_t)(ty + 2 * GR), (cuuint32_t)(NK / 2)};
+    cuuint32_t box[3] = {(cuuint32_t)F32_BOX_COLS, (cuuint32_t)(ty + 2 * GR), (cuuint32_t)(NK / 2)};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -624,7 +611,7 @@ int vlbm_init_moments(vlbm_t *h, const double *rho, const double *u_theta, const
         std::vector<double> r(rho, rho + n);
         const double old = h->rho_ref;
         choose_rho_ref(h, r);
-        if (old != h->rho_ref || !h->d_face) {
+        if (old != h->rho_ref || !h->d_row) {
             int rc = build_f32_tables(h);
             if (rc) return rc;
             drop_graphs(h);
@@ -654,7 +641,7 @@ int vlbm_set_populations(vlbm_t *h, const double *f)
             for (size_t c = 0; c < cells; ++c) rho[c] += f[(size_t)k * cells + c];
         const double old = h->rho_ref;
         choose_rho_ref(h, rho);
-        if (old != h->rho_ref || !h->d_face) {
+        if (old != h->rho_ref || !h->d_row) {
             int rc = build_f32_tables(h);
             if (rc) return rc;
             drop_graphs(h);
@@ -684,7 +671,7 @@ int vlbm_get_populations(vlbm_t *h, double *f)
 int vlbm_step_async(vlbm_t *h, int n)
 {
     if (!h || n < 0) return fail(h, VLBM_ERR_ARG, "bad handle or step count");
-    if (h->prec == VLBM_FP32 && !h->d_face) return fail(h, VLBM_ERR_ARG, "FP32 state not initialised");
+    if (h->prec == VLBM_FP32 && !h->d_row) return fail(h, VLBM_ERR_ARG, "FP32 state not initialised");
     if (n == 0) return VLBM_OK;
     int rc;
     if (!h->g1 && (rc = build_graph(h, 1, &h->g1))) return rc;
@@ -787,7 +774,7 @@ int vlbm_max_stable_dt(int n_theta, int n_phi, int velocity_set, double tau, int
 int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches)
 {
     if (!h || n < 1) return fail(h, VLBM_ERR_ARG, "bad handle or step count");
-    if (h->prec == VLBM_FP32 && !h->d_face) return fail(h, VLBM_ERR_ARG, "FP32 state not initialised");
+    if (h->prec == VLBM_FP32 && !h->d_row) return fail(h, VLBM_ERR_ARG, "FP32 state not initialised");
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int q = 0; q < n; ++q) {
         for (int st = 1; st <= 3; ++st) {
@@ -828,7 +815,7 @@ void vlbm_destroy(vlbm_t *h)
     void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_sin_f, h->d_cos_f, h->d_isp,
                     h->d_sfc, h->d_ft, h->d_fp,
                     h->d_rref, h->d_dsin, h->d_d2sin,
-                    h->d_face, h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
+                    h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
                     h->d_part, h->d_diag, h->d_flags};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -904,7 +891,7 @@ int batch_refresh(vlbm_batch_t *b)
     std::vector<int2> work;
     for (int r = 0; r < nr; ++r) {
         vlbm_t *h = b->runs[r];
-        if (!h->d_face) return bfail(b, VLBM_ERR_ARG, "run " + std::to_string(r) + " is not initialised");
+        if (!h->d_row) return bfail(b, VLBM_ERR_ARG, "run " + std::to_string(r) + " is not initialised");
         runs[r] = h->run;
         int rc;
         if ((rc = encode_map(h, &tms[3 * r + 0], h->F, b->ty)) || (rc = encode_map(h, &tms[3 * r + 1], h->A, b->ty)) ||

@@ -31,7 +31,6 @@ struct vlbm {
     // FP32 tables
     float2 *d_rref = nullptr;
     float *d_dsin = nullptr, *d_d2sin = nullptr;
-    vk::FaceConst *d_face = nullptr;
     vk::RowF *d_row = nullptr;
     // polar filter
     int *d_frows = nullptr, *d_fblocks = nullptr;

@@ -64,9 +64,6 @@ void launch_stage_f64(const StageD &p, cudaStream_t s);
 // pair p = 4 g + b holds populations (2g, b) and (2g+1, b).  k is the power of two of the
 // run's state scale (f32_state_scale): scaling by it is exact, so every value is k times
 // the unscaled one bit for bit, and it sets the WENO regulariser 4 eps k^2 near 1.
-// Per theta face and upwind direction: the smoothness linear forms of the stencil applied to
-// sin(theta) and corr = 0.1 (P1-P2) + 0.3 (P3-P2) of sin(theta) (ideal-weight interpolant minus P2).
-struct FaceConst { float sa1, sb1, sa2, sb2, sa3, sb3, corr, pad; };
 // Per interior row: k s (s = sin(theta)), 1/(k s), 1/(R s dphi), cot(theta)/R, the phi WENO
 // regulariser ephi = 4 eps s^2 k^2 (the WENO on f has eps; on dg = k s f its forms carry k s),
 // and for the Komissarov theta flux kth = s / (R (cos theta_{i-1/2} - cos theta_{i+1/2})).
@@ -74,7 +71,6 @@ struct RowF { float s, inv_s, inv_dph, cotR, ephi, kth, pad1, pad2; };
 // Per-run parameters of the FP32 stage: one solver, or one member of a batch.
 struct RunF {
     float2 *F, *A, *B;         // dg at the step start, after stage 1, after stage 2 (pair layout)
-    const FaceConst *face;     // [nt+1][2]: face between rows fi-1 and fi, dir 0: v>0, 1: v<0
     const RowF *row;           // [nt]
     const float2 *rref;        // [nt][8] k s * (FP64-derived tendency of the reference state)
     const float *dsin;         // [nt + 2GR + 8] sin(pr) - sin(pr-1) at padded row pr (0 where undefined)
@@ -105,6 +101,10 @@ struct VelC {
 };
 
 constexpr int F32_TILE_COLS = 32;
+// Columns of the TMA box (and of the shared tile row): the tile's 32 plus GC on each side plus 2.
+// A row pitch of 42 float2 puts the 16-byte loads of 8 consecutive rows at one column in 8
+// different bank groups (21 r mod 8 is a permutation), which the phi-face walk relies on.
+constexpr int F32_BOX_COLS = F32_TILE_COLS + 2 * GC + 2;
 constexpr int F32_TILE_ROWS_MAX = 8;
 // One stage of one run, tile rows ty (4 or 8).  tm describes the stage input array.
 cudaError_t prepare_stage_f32();   // sets the kernels' dynamic shared-memory limits
