@@ -232,12 +232,17 @@ __device__ __forceinline__ void store_images(f2 *f, const Layout &L, int p, int 
 
 // One stage of one TY x TX tile of one run.  The mbarrier is initialised by the
 // caller; `parity` is the phase this tile's load completes.  Returns false if
-// the tile load did not arrive in time (every thread of the CTA agrees).
+// the tile load did not arrive in time (every thread of the CTA agrees).  tm is the
+// stage input's box map (42 x (TY+6) x 8); tmo and tmf are the tile-core maps (32 x TY
+// x 8) of the stage output and of the step's start values F: tiles clear of every ghost
+// image store their output with one TMA store through tmo, and stages 2 and 3 prefetch
+// their tile of F into L2 through tmf.
 // LIN: the upwind schemes U1-U3 (Eq. fluxes_U1-3, optionally with the Komissarov theta flux)
 // instead of WENO-5.
 template <int TY, bool LIN>
-__device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int stage, const CUtensorMap *tm, int bx,
-                                           int by, SmemT<TY> &S, unsigned parity, unsigned *err)
+__device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int stage, const CUtensorMap *tm,
+                                           const CUtensorMap *tmo, const CUtensorMap *tmf, int bx, int by,
+                                           SmemT<TY> &S, unsigned parity, unsigned *err)
 {
     constexpr int SR = TY + 2 * GR;
     constexpr int NT = TY * 32;
@@ -267,14 +272,13 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             "l"(reinterpret_cast<unsigned long long>(tm)), "r"(q0), "r"(i0), "r"(0), "r"(smem_u32(&S.bar))
             : "memory");
     }
-    // stages 2, 3: pull this thread's cell of the step's start values toward L2 now
-    if (stage != 1) {
-        const int pi = i0 + warp, pj = q0 + lane;
-        if (pi < L.nt && pj < L.np) {
-#pragma unroll
-            for (int q = 0; q < NP2; ++q)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(R.F + L.at(q, pi, pj)));
-        }
+    // stages 2, 3: pull the tile's step start values toward L2 now (one bulk prefetch; parts
+    // outside the array are ignored)
+    if (stage != 1 && tid == 32) {
+        asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                         reinterpret_cast<unsigned long long>(tmf)),
+                     "r"(q0 + GC), "r"(i0 + GR), "r"(0)
+                     : "memory");
     }
     // per-tile tables while the tile is in flight
     {
@@ -334,7 +338,10 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     } else {
         // WENO-5: warp = pair (pairs warp, warp + TY, ...), lane = (segment sg, row r); segment sg
         // walks faces SEG sg .. SEG sg + SEG of row r (the last is the next segment's first, so
-        // only the last segment stores it: the east face of the tile)
+        // only the last segment stores it: the east face of the tile).  (Giving the extra face
+        // to the last segment's warps alone, with 8-face walks elsewhere, did 8 % less phi work
+        // but ran 8 % slower; a second pair of unrolled walks in the instruction stream is the
+        // likely cost.)
         constexpr int NSEG = 32 / TY, SEG = TX / NSEG;
         const int r = lane % TY, sg = lane / TY, f0 = sg * SEG;
         const f2 E = splat(S.rowc[r].ephi);
@@ -508,6 +515,27 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         o[q] = fma2(cG, G[q], a);
         if (stage != 1) o[q] = fma2(cF, F0[q], o[q]);
     }
+    // tiles clear of the ghost images (no pole-row or seam image to write, no ragged edge):
+    // the output tile goes through shared memory (the theta-face array, read by now) and
+    // leaves with one TMA store; the issuing thread waits until the store has read it
+    const bool core = (i0 >= GR && i0 + TY <= L.nt - GR && q0 >= GC && q0 + TX <= L.np - GC);
+    if (core) {
+        f2 *ob = &S.ft[0][0][0];   // [NP2][TY][TX]
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NP2; ++q) ob[(q * TY + cy) * TX + cx] = o[q];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                             reinterpret_cast<unsigned long long>(tmo)),
+                         "r"(q0 + GC), "r"(i0 + GR), "r"(0), "r"(smem_u32(ob))
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+        return true;
+    }
     const bool plain = (i >= GR && i < L.nt - GR && j >= GC && j < L.np - GC);
     if (plain) {
 #pragma unroll
@@ -521,6 +549,8 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
 
 template <int TY, bool LIN>
 __global__ void __launch_bounds__(TY * 32, 24 / TY) stage_f32_kernel(const __grid_constant__ CUtensorMap tm,
+                                                                      const __grid_constant__ CUtensorMap tmo,
+                                                                      const __grid_constant__ CUtensorMap tmf,
                                                                       const RunF R, const VelC c, int stage,
                                                                       unsigned *err)
 {
@@ -530,12 +560,13 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) stage_f32_kernel(const __gri
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    stage_tile<TY, LIN>(R, c, stage, &tm, blockIdx.x, blockIdx.y, S, 0u, err);
+    stage_tile<TY, LIN>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, blockIdx.y, S, 0u, err);
 }
 
 // Persistent batch stage: CTA b takes work items b, b + gridDim.x, ...; a work item
 // is (run, tile index within the run).  The run's parameters are copied into
-// shared memory per item.
+// shared memory per item.  tms holds 6 maps per run: the box maps of F, A, B, then
+// the tile-core maps of F, A, B.
 template <int TY, bool LIN>
 __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const RunF *runs, const CUtensorMap *tms,
                                                                             const int2 *work, int ntiles, const VelC c,
@@ -557,7 +588,9 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const
         }
         __syncthreads();
         const int tx = S.run.tiles_x;
-        if (!stage_tile<TY, LIN>(S.run, c, stage, tms + 3 * w.x + (stage - 1), w.y % tx, w.y / tx, S, parity, err))
+        const CUtensorMap *tr = tms + 6 * w.x;
+        if (!stage_tile<TY, LIN>(S.run, c, stage, tr + (stage - 1), tr + 3 + stage % 3, tr + 3, w.y % tx, w.y / tx, S,
+                                 parity, err))
             return;
         parity ^= 1u;
         __syncthreads();   // every thread is done with this tile's shared memory
@@ -963,16 +996,16 @@ int stage_f32_max_ctas_per_sm(int ty)
     return n;
 }
 
-void launch_stage_f32(const CUtensorMap &tm_in, const RunF &run, const VelC &c, int stage, int ty, bool lin,
-                      unsigned *err, cudaStream_t s)
+void launch_stage_f32(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f, const RunF &run,
+                      const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s)
 {
     const dim3 grid((run.L.np + TX - 1) / TX, (run.L.nt + ty - 1) / ty);
     if (ty == 4) {
-        if (lin) stage_f32_kernel<4, true><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, run, c, stage, err);
-        else stage_f32_kernel<4, false><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, run, c, stage, err);
+        if (lin) stage_f32_kernel<4, true><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
+        else stage_f32_kernel<4, false><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
     } else {
-        if (lin) stage_f32_kernel<8, true><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, run, c, stage, err);
-        else stage_f32_kernel<8, false><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, run, c, stage, err);
+        if (lin) stage_f32_kernel<8, true><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
+        else stage_f32_kernel<8, false><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
     }
 }
 

@@ -295,7 +295,10 @@ int build_f32_tables(vlbm_t *h)
     return VLBM_OK;
 }
 
-int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0)
+// Tensor map of an FP32 pair array: the stage input box (F32_BOX_COLS x (ty + 2 GR) x 8 pairs,
+// anchored GC columns and GR rows before the tile) or, with core set, the tile itself
+// (F32_TILE_COLS x ty x 8).
+int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0, bool core = false)
 {
     if (ty == 0) ty = h->ty;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -310,7 +313,8 @@ int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0)
     // pair planes of float2, described as 8-byte elements
     cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)(h->nt + 2 * GR), (cuuint64_t)(NK / 2)};
     cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * sizeof(float2), (cuuint64_t)h->L.plane * sizeof(float2)};
-    cuuint32_t box[3] = {(cuuint32_t)F32_BOX_COLS, (cuuint32_t)(ty + 2 * GR), (cuuint32_t)(NK / 2)};
+    cuuint32_t box[3] = {(cuuint32_t)(core ? F32_TILE_COLS : F32_BOX_COLS), (cuuint32_t)(core ? ty : ty + 2 * GR),
+                         (cuuint32_t)(NK / 2)};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -357,7 +361,9 @@ void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
             if (h->nfrows && part != 1) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         } else {
             const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
-            if (part != 2) launch_stage_f32(tm, h->run, h->vc, st, h->ty, h->scheme != VLBM_WENO5, h->d_flags, s);
+            const CUtensorMap &tmo = (st == 1) ? h->tmAc : (st == 2) ? h->tmBc : h->tmFc;
+            if (part != 2)
+                launch_stage_f32(tm, tmo, h->tmFc, h->run, h->vc, st, h->ty, h->scheme != VLBM_WENO5, h->d_flags, s);
             if (h->nfrows && part != 1) launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         }
     }
@@ -582,7 +588,8 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
         }
     if (h->prec == VLBM_FP32) {
         if ((rc = encode_map(h, &h->tmF, h->F)) || (rc = encode_map(h, &h->tmA, h->A)) ||
-            (rc = encode_map(h, &h->tmB, h->B)))
+            (rc = encode_map(h, &h->tmB, h->B)) || (rc = encode_map(h, &h->tmFc, h->F, 0, true)) ||
+            (rc = encode_map(h, &h->tmAc, h->A, 0, true)) || (rc = encode_map(h, &h->tmBc, h->B, 0, true)))
             return bail(rc);
         // the stage kernel needs more than the default 48 KB of dynamic shared
         // memory; set that once here, outside any graph capture
@@ -887,15 +894,17 @@ int batch_refresh(vlbm_batch_t *b)
     if (!b->dirty) return VLBM_OK;
     const int nr = (int)b->runs.size();
     std::vector<RunF> runs(nr);
-    std::vector<CUtensorMap> tms(3 * (size_t)nr);
+    std::vector<CUtensorMap> tms(6 * (size_t)nr);
     std::vector<int2> work;
     for (int r = 0; r < nr; ++r) {
         vlbm_t *h = b->runs[r];
         if (!h->d_row) return bfail(b, VLBM_ERR_ARG, "run " + std::to_string(r) + " is not initialised");
         runs[r] = h->run;
         int rc;
-        if ((rc = encode_map(h, &tms[3 * r + 0], h->F, b->ty)) || (rc = encode_map(h, &tms[3 * r + 1], h->A, b->ty)) ||
-            (rc = encode_map(h, &tms[3 * r + 2], h->B, b->ty)))
+        CUtensorMap *t = &tms[6 * (size_t)r];
+        if ((rc = encode_map(h, t + 0, h->F, b->ty)) || (rc = encode_map(h, t + 1, h->A, b->ty)) ||
+            (rc = encode_map(h, t + 2, h->B, b->ty)) || (rc = encode_map(h, t + 3, h->F, b->ty, true)) ||
+            (rc = encode_map(h, t + 4, h->A, b->ty, true)) || (rc = encode_map(h, t + 5, h->B, b->ty, true)))
             return bfail(b, rc, h->err);
         const int tx = runs[r].tiles_x, tyn = (h->nt + b->ty - 1) / b->ty;
         for (int t = 0; t < tx * tyn; ++t) work.push_back(make_int2(r, t));
@@ -919,11 +928,11 @@ int batch_refresh(vlbm_batch_t *b)
         BCK(b, cudaMemcpy(b->d_fitems, fitems.data(), sizeof(int4) * fitems.size(), cudaMemcpyHostToDevice));
     }
     if (!b->d_runs) BCK(b, cudaMalloc(&b->d_runs, sizeof(RunF) * nr));
-    if (!b->d_tms) BCK(b, cudaMalloc(&b->d_tms, sizeof(CUtensorMap) * 3 * nr));
+    if (!b->d_tms) BCK(b, cudaMalloc(&b->d_tms, sizeof(CUtensorMap) * 6 * nr));
     if (b->d_work) cudaFree(b->d_work);
     BCK(b, cudaMalloc(&b->d_work, sizeof(int2) * work.size()));
     BCK(b, cudaMemcpy(b->d_runs, runs.data(), sizeof(RunF) * nr, cudaMemcpyHostToDevice));
-    BCK(b, cudaMemcpy(b->d_tms, tms.data(), sizeof(CUtensorMap) * 3 * nr, cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_tms, tms.data(), sizeof(CUtensorMap) * 6 * nr, cudaMemcpyHostToDevice));
     BCK(b, cudaMemcpy(b->d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice));
     batch_drop_graphs(b);
     b->dirty = false;

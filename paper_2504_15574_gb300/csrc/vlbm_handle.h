@@ -39,7 +39,8 @@ struct vlbm {
     double *d_pole = nullptr, *d_budget = nullptr, *d_mom = nullptr, *d_dense = nullptr;
     double *d_part = nullptr, *d_diag = nullptr;
     unsigned *d_flags = nullptr, *h_flags = nullptr;
-    CUtensorMap tmF{}, tmA{}, tmB{};
+    CUtensorMap tmF{}, tmA{}, tmB{};      // FP32 path: box maps (stage inputs)
+    CUtensorMap tmFc{}, tmAc{}, tmBc{};   // FP32 path: tile-core maps (stage outputs, F prefetch)
     cudaGraphExec_t g1 = nullptr, g16 = nullptr;
     vk::VelD vd{};
     vk::VelC vc{};     // FP32 path: packed velocity constants

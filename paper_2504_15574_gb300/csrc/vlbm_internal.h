@@ -106,12 +106,15 @@ constexpr int F32_TILE_COLS = 32;
 // different bank groups (21 r mod 8 is a permutation), which the phi-face walk relies on.
 constexpr int F32_BOX_COLS = F32_TILE_COLS + 2 * GC + 2;
 constexpr int F32_TILE_ROWS_MAX = 8;
-// One stage of one run, tile rows ty (4 or 8).  tm describes the stage input array.
+// One stage of one run, tile rows ty (4 or 8).  tm_in is the box map (F32_BOX_COLS x (ty + 2 GR)
+// x 8) of the stage input array; tm_out and tm_f are the tile-core maps (F32_TILE_COLS x ty x 8)
+// of the stage output array and of F (the step's start values).
 cudaError_t prepare_stage_f32();   // sets the kernels' dynamic shared-memory limits
-void launch_stage_f32(const CUtensorMap &tm_in, const RunF &run, const VelC &c, int stage, int ty, bool lin,
-                      unsigned *err, cudaStream_t s);
+void launch_stage_f32(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f, const RunF &run,
+                      const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s);
 // One stage of a batch: a persistent grid of `ctas` CTAs walks `ntiles` work items
-// (run, tile) over the run table `runs` (device) and tensor maps `tms` ([run][3], device).
+// (run, tile) over the run table `runs` (device) and tensor maps `tms` (device, [run][6]: the box
+// maps of F, A, B, then the tile-core maps of F, A, B).
 void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
                             int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s);
 int stage_f32_max_ctas_per_sm(int ty);
