@@ -202,6 +202,17 @@ def riemann_cap(n_theta: int, n_phi: int = 1, rho1: float = 1.0, rho2: float = 0
     return rho, z, z.copy(), None
 
 
+def riemann_cap_rotated(n_theta: int, n_phi: int, alpha: float = -math.pi / 2, rho1: float = 1.0,
+                        rho2: float = 0.125, theta_disc: float = math.pi / 10):
+    """The riemann_cap start about an axis tilted by alpha (App. C, Fig. riemann_2D): on the
+    grid rotated by alpha, rho1 where the original-frame polar angle is below theta_disc,
+    rho2 beyond, fluid at rest."""
+    th, _, _ = rotated_frame(n_theta, n_phi, alpha)
+    rho = np.where(th < theta_disc, rho1, rho2)
+    z = np.zeros_like(th)
+    return rho, z, z.copy(), None
+
+
 def gaussian_vortices(n_theta: int, n_phi: int, run: int, umax: float = 0.05):
     """2-8 Gaussian vortices psi_i = A_i exp(-d_i^2 / (2 r_i^2)) at random centres.
 

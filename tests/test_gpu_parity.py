@@ -65,6 +65,12 @@ CASES = {
     "sound_rotated_32x32": (32, 32, 2e-3, 1e-4, lambda: inputs.sound_parabola_rotated(32, 32, 1e-3), 200, False),
     # the spherical shock tube of Sec. 4.3 (density ratio 8), through shock formation
     "riemann_256x1": (256, 1, 2e-4, 2e-5, lambda: inputs.riemann_cap(256, 1), 400, False),
+    # the shock tube about an axis in the grid's equatorial plane (App. C, Fig. riemann_2D), to
+    # t = 1: the shock crosses the rotated grid's pole rows; without and with the polar filter
+    "riemann_rotated_32x32": (32, 32, 0.02, clamped_dt(32, 32, 0.02), lambda: inputs.riemann_cap_rotated(32, 32), 969,
+                              False),
+    "riemann_rotated_filter_32x32": (32, 32, 0.02, literal_dt(32), lambda: inputs.riemann_cap_rotated(32, 32), 95,
+                                     True),
 }
 
 
@@ -186,6 +192,8 @@ FP32_CASES = {
     "filter_window_blocks_8x32768": (1e-7, 2e-4, 2e-5),
     "sound_rotated_32x32": (1e-8, 5e-5, 2e-5),
     "riemann_256x1": (2.5e-5, 3e-5, 2e-5),
+    "riemann_rotated_32x32": (4e-6, 1e-5, 1e-5),
+    "riemann_rotated_filter_32x32": (4e-6, 1e-5, 1e-5),
 }
 
 
