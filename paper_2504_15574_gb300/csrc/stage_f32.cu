@@ -50,8 +50,9 @@ constexpr int SC = F32_BOX_COLS;       // tile columns in shared memory (TX + 2 
 template <int TY>
 struct __align__(128) SmemT {
     float2 tile[NP2][TY + 2 * GR][SC];  // TMA destination (must stay first)
-    float2 ft[NP2][TY + 1][TX];         // theta faces: face fy between cell rows fy-1 and fy
-    float2 fp[NP2][TY][TX + 1];         // phi faces: face fx between cell columns fx-1 and fx
+    float2 adv[NP2][TY][TX + 1];        // per cell and pair: dte (flux differences + s rref); row
+                                        // stride TX+1 keeps the phi walkers' stores conflict-free
+    float2 ob[NP2][TY][TX];             // output tile staged for the TMA store
     float2 ds2[TY + 2 * GR];            // (dsin, dsin) at the tile rows
     float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
     float2 rr[TY][NP2];                 // dte s rref per cell row and pair
@@ -115,6 +116,33 @@ __device__ __forceinline__ bool wait_phase(unsigned long long *bar, unsigned par
     }
 }
 
+// Upwind-scheme phi faces f0 .. f0 + NF - 1 of one row of one pair plane (Eq. fluxes_U1-3):
+// face value l0 x_up2 + l1 x_up + l2 x_down with x_up2, x_up, x_down the shared columns
+// fx+2, fx+3, fx+4 for DIR = +1 (v_phi > 0) and fx+5, fx+4, fx+3 for DIR = -1, read as
+// 16-byte pairs from shared column f0 + 2.  The flux difference of cell f0 + j - 1 goes to
+// out[j-1] as for phi_march.
+template <int NF, int DIR>
+__device__ __forceinline__ void phi_march_lin(const f2 *row, int f0, f2 l0, f2 l1, f2 l2, f2 vb, f2 *out)
+{
+    constexpr int NX = ((NF + 3) + 1) & ~1;
+    const float4 *src = reinterpret_cast<const float4 *>(row + f0 + 2);
+    f2 x[NX];
+#pragma unroll
+    for (int m = 0; m < NX / 2; ++m) {
+        const float4 v = src[m];
+        x[2 * m] = make_float2(v.x, v.y);
+        x[2 * m + 1] = make_float2(v.z, v.w);
+    }
+    f2 prev;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+        const f2 v = (DIR > 0) ? fma2(l0, x[j], fma2(l1, x[j + 1], mul2(l2, x[j + 2])))
+                               : fma2(l0, x[j + 3], fma2(l1, x[j + 2], mul2(l2, x[j + 1])));
+        if (j > 0) out[j - 1] = mul2(vb, sub2(prev, v));
+        prev = v;
+    }
+}
+
 // Nonlinear combination of WENO-5 (Eqs. fluxes_W5, WENO5_delta, WENO5_sigma) on the
 // scaled state: P2 + wbar1 (A1 - A2)/3 + wbar3 (A2 - A3)/6 with wbar_i = d_i q_j q_k / sum
 // and q_i = t_i^2, where t_i = B_i^2 + 13/3 A_i^2 + E = 4 k^2 (sigma_i + eps) for the
@@ -141,10 +169,10 @@ __device__ __forceinline__ f2 weno_mix(f2 t1, f2 t2, f2 t3, f2 d12, f2 d23, f2 p
 // (centred at m) and row term Q[m] = 13/3 A[m]^2 + E are formed once, and so is each
 // A difference (d23 of a face is d12 of the next).  DIR = +1 for v_phi > 0 (face fx reads
 // shared columns fx+1 .. fx+5 in upwind order), -1 for v_phi < 0 (fx+6 .. fx+2).  The
-// columns are read as 16-byte pairs starting at shared column f0 + LO (even).  Face j's
-// value times vb goes to out[j] for j < nst.
+// columns are read as 16-byte pairs starting at shared column f0 + LO (even).  The flux
+// difference of cell f0 + j - 1, vb times (face j-1 - face j), goes to out[j-1].
 template <int NF, int DIR>
-__device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2 *out, int nst)
+__device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2 *out)
 {
     constexpr int LO = (DIR > 0) ? 0 : 2;
     constexpr int NX = ((NF + 5) + 1) & ~1;
@@ -166,7 +194,7 @@ __device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2
             A[m] = sub2(d[m + 1], d[m]);
             Q[m] = fma2(mul2(A[m], c133), A[m], E);
         }
-        f2 d12 = sub2(A[2], A[3]);
+        f2 d12 = sub2(A[2], A[3]), prev;
 #pragma unroll
         for (int j = 0; j < NF; ++j) {
             d[j + 5] = sub2(x[j + 5], x[j + 4]);
@@ -178,7 +206,8 @@ __device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2
             const f2 p2 = fma2(splat(1.0f / 3.0f), d[j + 4], fma2(splat(1.0f / 6.0f), d[j + 3], x[j + 3]));
             const f2 d23 = sub2(A[j + 3], A[j + 4]);
             const f2 v = weno_mix(fma2(B1, B1, Q[j + 2]), fma2(B2, B2, Q[j + 3]), fma2(B3, B3, Q[j + 4]), d12, d23, p2);
-            if (j < nst) out[j] = mul2(vb, v);
+            if (j > 0) out[j - 1] = mul2(vb, sub2(prev, v));
+            prev = v;
             d12 = d23;
         }
     } else {
@@ -190,7 +219,7 @@ __device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2
             A[m] = sub2(d[m + 1], d[m]);
             Q[m] = fma2(mul2(A[m], c133), A[m], E);
         }
-        f2 d23 = sub2(A[2], A[1]);
+        f2 d23 = sub2(A[2], A[1]), prev;
 #pragma unroll
         for (int j = 0; j < NF; ++j) {
             d[j + 4] = sub2(x[j + 4], x[j + 3]);
@@ -202,7 +231,8 @@ __device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2
             const f2 p2 = fma2(splat(-1.0f / 3.0f), d[j + 2], fma2(splat(-1.0f / 6.0f), d[j + 3], x[j + 2]));
             const f2 d12 = sub2(A[j + 3], A[j + 2]);
             const f2 v = weno_mix(fma2(B1, B1, Q[j + 3]), fma2(B2, B2, Q[j + 2]), fma2(B3, B3, Q[j + 1]), d12, d23, p2);
-            if (j < nst) out[j] = mul2(vb, v);
+            if (j > 0) out[j - 1] = mul2(vb, sub2(prev, v));
+            prev = v;
             d23 = d12;
         }
     }
@@ -298,7 +328,8 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             S.sf2[t] = splat(R.sfc[i0 + t]);
         }
     }
-    __syncthreads();
+    // (the barrier of the load wait also publishes the tables; the caller has made the
+    // mbarrier's initialisation visible to every thread before this tile began)
     const bool ok = __syncthreads_and(wait_phase(&S.bar, parity, 1000000000ull));
     if (!ok) {
         // the copy did not complete within 1 s: flag it, give it one more bounded
@@ -310,57 +341,44 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
 
     // Every face value below is premultiplied by the stage's dt share dte and by the
     // metric factor of its difference (1/(R sin dphi) for phi, 1/(R dtheta) for the
-    // WENO-5 and plain upwind theta fluxes), so the cell update takes plain differences.
-    // ---- phi faces: warp = cell row fy, lane = face fx (west face of column fx)
-    if constexpr (LIN) {
-        // upwind schemes on dg: x_up2, x_up, x_down are the columns fx-2, fx-1, fx for v > 0
-        // and fx+1, fx, fx-1 for v < 0 (shared column = column + GC)
-        const int fy = warp;
-        const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
-        const f2 sp = splat(__fmul_rn(S.rowc[fy].inv_dph, dte));
-#pragma unroll
-        for (int q = 0; q < NP2; ++q) {
-            const f2 vb = c.vphi2[q & 3];
-            const f2 *row = &S.tile[q][fy + GR][0];
-            const f2 rec = (vb.x > 0.0f) ? fma2(l0, row[lane + 2], fma2(l1, row[lane + 3], mul2(l2, row[lane + 4])))
-                                         : fma2(l0, row[lane + 5], fma2(l1, row[lane + 4], mul2(l2, row[lane + 3])));
-            S.fp[q][fy][lane] = mul2(mul2(vb, sp), rec);
-        }
-        if (tid < NP2 * TY) {
-            const int q = tid / TY, ry = tid - (tid / TY) * TY;
-            const f2 vb = mul2(c.vphi2[q & 3], splat(__fmul_rn(S.rowc[ry].inv_dph, dte)));
-            const f2 *row = &S.tile[q][ry + GR][0];
-            const int fx = TX;
-            const f2 rec = (vb.x > 0.0f) ? fma2(l0, row[fx + 2], fma2(l1, row[fx + 3], mul2(l2, row[fx + 4])))
-                                         : fma2(l0, row[fx + 5], fma2(l1, row[fx + 4], mul2(l2, row[fx + 3])));
-            S.fp[q][ry][fx] = mul2(vb, rec);
-        }
-    } else {
-        // WENO-5: warp = pair (pairs warp, warp + TY, ...), lane = (segment sg, row r); segment sg
-        // walks faces SEG sg .. SEG sg + SEG of row r (the last is the next segment's first, so
-        // only the last segment stores it: the east face of the tile).  (Giving the extra face
-        // to the last segment's warps alone, with 8-face walks elsewhere, did 8 % less phi work
-        // but ran 8 % slower; a second pair of unrolled walks in the instruction stream is the
-        // likely cost.)
+    // WENO-5 and plain upwind theta fluxes).  Each walker turns its consecutive faces into
+    // the flux differences of the cells between them: the phi walkers write them to adv,
+    // the theta walker of the same warp and pair adds its difference and the reference
+    // tendency, so that the cell update reads one value per pair.
+    // ---- phi: warp = pair (pairs warp, warp + TY, ...), lane = (segment sg, row r); segment
+    // sg walks faces SEG sg .. SEG sg + SEG of row r for its SEG cells
+    {
         constexpr int NSEG = 32 / TY, SEG = TX / NSEG;
         const int r = lane % TY, sg = lane / TY, f0 = sg * SEG;
-        const f2 E = splat(S.rowc[r].ephi);
         const f2 sp = splat(__fmul_rn(S.rowc[r].inv_dph, dte));
-        const int nst = (sg == NSEG - 1) ? SEG + 1 : SEG;
+        if constexpr (LIN) {
+            const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
 #pragma unroll 1
-        for (int q = warp; q < NP2; q += NT / 32) {
-            const f2 vb = mul2(c.vphi2[q & 3], sp);
-            const f2 *row = &S.tile[q][r + GR][0];
-            f2 *out = &S.fp[q][r][f0];
-            if (vb.x > 0.0f) phi_march<SEG + 1, 1>(row, f0, E, vb, out, nst);
-            else phi_march<SEG + 1, -1>(row, f0, E, vb, out, nst);
+            for (int q = warp; q < NP2; q += NT / 32) {
+                const f2 vb = mul2(c.vphi2[q & 3], sp);
+                const f2 *row = &S.tile[q][r + GR][0];
+                f2 *out = &S.adv[q][r][f0];
+                if (vb.x > 0.0f) phi_march_lin<SEG + 1, 1>(row, f0, l0, l1, l2, vb, out);
+                else phi_march_lin<SEG + 1, -1>(row, f0, l0, l1, l2, vb, out);
+            }
+        } else {
+            const f2 E = splat(S.rowc[r].ephi);
+#pragma unroll 1
+            for (int q = warp; q < NP2; q += NT / 32) {
+                const f2 vb = mul2(c.vphi2[q & 3], sp);
+                const f2 *row = &S.tile[q][r + GR][0];
+                f2 *out = &S.adv[q][r][f0];
+                if (vb.x > 0.0f) phi_march<SEG + 1, 1>(row, f0, E, vb, out);
+                else phi_march<SEG + 1, -1>(row, f0, E, vb, out);
+            }
         }
     }
+    __syncwarp();   // the theta walker reads the cells this warp's phi walkers wrote
 
     // ---- upwind schemes, theta faces: warp = pair, lane = column; the column's values are dg
     // (nodal g = sin f), or for the Komissarov flux df = dg / sin (ghost rows: the mapped
     // population's df), then v_theta times the interface sine times the reconstruction.
-    // These faces carry dte only: the cell update applies 1/(R dtheta), or the Komissarov
+    // These faces carry dte only: their differences take 1/(R dtheta), or the Komissarov
     // row factor s / (R dcos).
     if constexpr (LIN) {
         const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
@@ -370,7 +388,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             const int g = q >> 2;
             const f2 vt = mul2(c.vth[g], splat(dte));
             const f2 *col = &S.tile[q][0][lane + GC];
-            f2 x[SR];
+            f2 x[SR], prev;
 #pragma unroll
             for (int r = 0; r < SR; ++r) x[r] = kom ? mul2(col[r * SC], S.isp2[r]) : col[r * SC];
 #pragma unroll
@@ -378,8 +396,13 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                 // face fy lies between tile rows fy-1 and fy (x index = tile row + GR)
                 const f2 rec = g ? fma2(l0, x[fy + 1], fma2(l1, x[fy + 2], mul2(l2, x[fy + 3])))
                                  : fma2(l0, x[fy + 4], fma2(l1, x[fy + 3], mul2(l2, x[fy + 2])));
-                const f2 fl = mul2(vt, rec);
-                S.ft[q][fy][lane] = kom ? mul2(fl, S.sf2[fy]) : fl;
+                const f2 fl = kom ? mul2(mul2(vt, rec), S.sf2[fy]) : mul2(vt, rec);
+                if (fy > 0) {
+                    const int cy = fy - 1;
+                    const f2 idth = splat(kom ? S.rowc[cy].kth : R.inv_dth);
+                    S.adv[q][cy][lane] = add2(fma2(sub2(prev, fl), idth, S.adv[q][cy][lane]), S.rr[cy][q]);
+                }
+                prev = fl;
             }
         }
     }
@@ -401,7 +424,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             const f2 vt = mul2(c.vth[g], splat(__fmul_rn(dte, R.inv_dth)));
             const f2 *col = &S.tile[q][0][lane + GC];
             // values are produced one row ahead of their first use (face fy needs rows up to fy+5)
-            f2 x[SR], dd[SR], dfu[SR], D2[SR], Qa[SR];
+            f2 x[SR], dd[SR], dfu[SR], D2[SR], Qa[SR], prev;
 #pragma unroll
             for (int r = 0; r < 5; ++r) x[r] = col[r * SC];
 #pragma unroll
@@ -444,7 +467,11 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                 }
                 // P2 of the reference part is in the FP64-derived tendency rref
                 const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
-                S.ft[q][fy][lane] = mul2(vt, v);
+                if (fy > 0) {
+                    const int cy = fy - 1;
+                    S.adv[q][cy][lane] = add2(fma2(vt, sub2(prev, v), S.adv[q][cy][lane]), S.rr[cy][q]);
+                }
+                prev = v;
             }
         }
     }
@@ -491,8 +518,6 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const f2 ncot = splat(__fmul_rn(-dte, rc.cotR));
     const f2 cG = splat(cgv);
     const f2 cF = splat((stage == 2) ? 0.75f : __fsub_rn(1.0f, 2.0f / 3.0f));
-    // upwind theta faces: 1/(R dtheta), or s / (R dcos) for the Komissarov flux
-    const f2 idth = splat((LIN && R.komissarov) ? rc.kth : R.inv_dth);
 
     f2 o[NP2];
 #pragma unroll
@@ -507,21 +532,18 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         const f2 *Gg = G + 4 * g;
         const f2 ktg = fma2(c.Kt2[4 * b], Gg[0], fma2(c.Kt2[4 * b + 1], Gg[1], fma2(c.Kt2[4 * b + 2], Gg[2], mul2(c.Kt2[4 * b + 3], Gg[3]))));
         // dte times: flux differences + s rref - force + s feq_dev / tau
-        const f2 adv_t = LIN ? mul2(sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]), idth) : sub2(S.ft[q][cy][cx], S.ft[q][cy + 1][cx]);
-        const f2 adv_p = sub2(S.fp[q][cy][cx], S.fp[q][cy][cx + 1]);
-        f2 a = add2(add2(adv_t, adv_p), S.rr[cy][q]);
+        f2 a = S.adv[q][cy][cx];
         a = fma2(ncot, fma2(c.vphisq2[b], kg, mul2(c.mvth[g], ktg)), a);
         a = fma2(c.w2[q], fma2(snn, poly, sg2), a);
         o[q] = fma2(cG, G[q], a);
         if (stage != 1) o[q] = fma2(cF, F0[q], o[q]);
     }
     // tiles clear of the ghost images (no pole-row or seam image to write, no ragged edge):
-    // the output tile goes through shared memory (the theta-face array, read by now) and
-    // leaves with one TMA store; the issuing thread waits until the store has read it
+    // the output tile is staged in shared memory and leaves with one TMA store; the issuing
+    // thread waits until the store has read it
     const bool core = (i0 >= GR && i0 + TY <= L.nt - GR && q0 >= GC && q0 + TX <= L.np - GC);
     if (core) {
-        f2 *ob = &S.ft[0][0][0];   // [NP2][TY][TX]
-        __syncthreads();
+        f2 *ob = &S.ob[0][0][0];
 #pragma unroll
         for (int q = 0; q < NP2; ++q) ob[(q * TY + cy) * TX + cx] = o[q];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -560,6 +582,7 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) stage_f32_kernel(const __gri
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();   // no thread may poll the barrier before its initialisation is visible
     stage_tile<TY, LIN>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, blockIdx.y, S, 0u, err);
 }
 
