@@ -52,7 +52,8 @@ struct __align__(128) SmemT {
     float2 tile[NP2][TY + 2 * GR][SC];  // TMA destination (must stay first)
     float2 adv[NP2][TY][TX + 1];        // per cell and pair: dte (flux differences + s rref); row
                                         // stride TX+1 keeps the phi walkers' stores conflict-free
-    float2 ob[NP2][TY][TX];             // output tile staged for the TMA store
+    float2 ob[NP2][TY][TX];             // stages 2, 3: the tile of F (TMA load); then the output
+                                        // tile staged for the TMA store
     float2 ds2[TY + 2 * GR];            // (dsin, dsin) at the tile rows
     float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
     float2 rr[TY][NP2];                 // dte s rref per cell row and pair
@@ -264,9 +265,9 @@ __device__ __forceinline__ void store_images(f2 *f, const Layout &L, int p, int 
 // caller; `parity` is the phase this tile's load completes.  Returns false if
 // the tile load did not arrive in time (every thread of the CTA agrees).  tm is the
 // stage input's box map (42 x (TY+6) x 8); tmo and tmf are the tile-core maps (32 x TY
-// x 8) of the stage output and of the step's start values F: tiles clear of every ghost
-// image store their output with one TMA store through tmo, and stages 2 and 3 prefetch
-// their tile of F into L2 through tmf.
+// x 8) of the stage output and of the step's start values F: stages 2 and 3 load their
+// tile of F through tmf into the staging buffer with the input box, and tiles clear of
+// every ghost image store their output from there with one TMA store through tmo.
 // LIN: the upwind schemes U1-U3 (Eq. fluxes_U1-3, optionally with the Komissarov theta flux)
 // instead of WENO-5.
 template <int TY, bool LIN>
@@ -277,6 +278,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     constexpr int SR = TY + 2 * GR;
     constexpr int NT = TY * 32;
     constexpr unsigned TILE_BYTES = NP2 * SR * SC * sizeof(float2);
+    constexpr unsigned CORE_BYTES = NP2 * TY * TX * sizeof(float2);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int q0 = bx * TX;
@@ -294,21 +296,22 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.bar)),
-                     "r"(TILE_BYTES)
+                     "r"(stage == 1 ? TILE_BYTES : TILE_BYTES + CORE_BYTES)
                      : "memory");
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.tile[0][0][0])),
             "l"(reinterpret_cast<unsigned long long>(tm)), "r"(q0), "r"(i0), "r"(0), "r"(smem_u32(&S.bar))
             : "memory");
-    }
-    // stages 2, 3: pull the tile's step start values toward L2 now (one bulk prefetch; parts
-    // outside the array are ignored)
-    if (stage != 1 && tid == 32) {
-        asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
-                         reinterpret_cast<unsigned long long>(tmf)),
-                     "r"(q0 + GC), "r"(i0 + GR), "r"(0)
-                     : "memory");
+        // stages 2, 3: the tile's step start values F into the staging buffer (parts outside
+        // the array read as zero and belong to no cell)
+        if (stage != 1)
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.ob[0][0][0])),
+                "l"(reinterpret_cast<unsigned long long>(tmf)), "r"(q0 + GC), "r"(i0 + GR), "r"(0),
+                "r"(smem_u32(&S.bar))
+                : "memory");
     }
     // per-tile tables while the tile is in flight
     {
@@ -481,11 +484,12 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const int cy = warp, cx = lane;
     const int i = i0 + cy, j = q0 + cx;
     if (i >= L.nt || j >= L.np) return true;
-    // start the global loads of the step's own-cell start values early
+    // the step's start values of this cell (stages 2, 3; the slots this thread's output
+    // overwrites below)
     f2 F0[NP2];
     if (stage != 1) {
 #pragma unroll
-        for (int q = 0; q < NP2; ++q) F0[q] = R.F[L.at(q, i, j)];
+        for (int q = 0; q < NP2; ++q) F0[q] = S.ob[q][cy][cx];
     }
     const RowF rc = S.rowc[cy];
     f2 G[NP2];
