@@ -120,10 +120,10 @@ __device__ __forceinline__ bool wait_phase(unsigned long long *bar, unsigned par
 // Upwind-scheme phi faces f0 .. f0 + NF - 1 of one row of one pair plane (Eq. fluxes_U1-3):
 // face value l0 x_up2 + l1 x_up + l2 x_down with x_up2, x_up, x_down the shared columns
 // fx+2, fx+3, fx+4 for DIR = +1 (v_phi > 0) and fx+5, fx+4, fx+3 for DIR = -1, read as
-// 16-byte pairs from shared column f0 + 2.  The flux difference of cell f0 + j - 1 goes to
-// out[j-1] as for phi_march.
+// 16-byte pairs from shared column f0 + 2.  The flux difference of cell f0 + j - 1 plus base
+// goes to out[j-1] as for phi_march.
 template <int NF, int DIR>
-__device__ __forceinline__ void phi_march_lin(const f2 *row, int f0, f2 l0, f2 l1, f2 l2, f2 vb, f2 *out)
+__device__ __forceinline__ void phi_march_lin(const f2 *row, int f0, f2 l0, f2 l1, f2 l2, f2 vb, f2 base, f2 *out)
 {
     constexpr int NX = ((NF + 3) + 1) & ~1;
     const float4 *src = reinterpret_cast<const float4 *>(row + f0 + 2);
@@ -139,7 +139,7 @@ __device__ __forceinline__ void phi_march_lin(const f2 *row, int f0, f2 l0, f2 l
     for (int j = 0; j < NF; ++j) {
         const f2 v = (DIR > 0) ? fma2(l0, x[j], fma2(l1, x[j + 1], mul2(l2, x[j + 2])))
                                : fma2(l0, x[j + 3], fma2(l1, x[j + 2], mul2(l2, x[j + 1])));
-        if (j > 0) out[j - 1] = mul2(vb, sub2(prev, v));
+        if (j > 0) out[j - 1] = fma2(vb, sub2(prev, v), base);
         prev = v;
     }
 }
@@ -171,9 +171,9 @@ __device__ __forceinline__ f2 weno_mix(f2 t1, f2 t2, f2 t3, f2 d12, f2 d23, f2 p
 // A difference (d23 of a face is d12 of the next).  DIR = +1 for v_phi > 0 (face fx reads
 // shared columns fx+1 .. fx+5 in upwind order), -1 for v_phi < 0 (fx+6 .. fx+2).  The
 // columns are read as 16-byte pairs starting at shared column f0 + LO (even).  The flux
-// difference of cell f0 + j - 1, vb times (face j-1 - face j), goes to out[j-1].
+// difference of cell f0 + j - 1, vb times (face j-1 - face j), plus base goes to out[j-1].
 template <int NF, int DIR>
-__device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2 *out)
+__device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2 base, f2 *out)
 {
     constexpr int LO = (DIR > 0) ? 0 : 2;
     constexpr int NX = ((NF + 5) + 1) & ~1;
@@ -207,7 +207,7 @@ __device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2
             const f2 p2 = fma2(splat(1.0f / 3.0f), d[j + 4], fma2(splat(1.0f / 6.0f), d[j + 3], x[j + 3]));
             const f2 d23 = sub2(A[j + 3], A[j + 4]);
             const f2 v = weno_mix(fma2(B1, B1, Q[j + 2]), fma2(B2, B2, Q[j + 3]), fma2(B3, B3, Q[j + 4]), d12, d23, p2);
-            if (j > 0) out[j - 1] = mul2(vb, sub2(prev, v));
+            if (j > 0) out[j - 1] = fma2(vb, sub2(prev, v), base);
             prev = v;
             d12 = d23;
         }
@@ -232,7 +232,7 @@ __device__ __forceinline__ void phi_march(const f2 *row, int f0, f2 E, f2 vb, f2
             const f2 p2 = fma2(splat(-1.0f / 3.0f), d[j + 2], fma2(splat(-1.0f / 6.0f), d[j + 3], x[j + 2]));
             const f2 d12 = sub2(A[j + 3], A[j + 2]);
             const f2 v = weno_mix(fma2(B1, B1, Q[j + 3]), fma2(B2, B2, Q[j + 2]), fma2(B3, B3, Q[j + 1]), d12, d23, p2);
-            if (j > 0) out[j - 1] = mul2(vb, sub2(prev, v));
+            if (j > 0) out[j - 1] = fma2(vb, sub2(prev, v), base);
             prev = v;
             d23 = d12;
         }
@@ -345,9 +345,9 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     // Every face value below is premultiplied by the stage's dt share dte and by the
     // metric factor of its difference (1/(R sin dphi) for phi, 1/(R dtheta) for the
     // WENO-5 and plain upwind theta fluxes).  Each walker turns its consecutive faces into
-    // the flux differences of the cells between them: the phi walkers write them to adv,
-    // the theta walker of the same warp and pair adds its difference and the reference
-    // tendency, so that the cell update reads one value per pair.
+    // the flux differences of the cells between them: the phi walkers write them, plus the
+    // reference tendency, to adv, and the theta walker of the same warp and pair adds its
+    // difference, so that the cell update reads one value per pair.
     // ---- phi: warp = pair (pairs warp, warp + TY, ...), lane = (segment sg, row r); segment
     // sg walks faces SEG sg .. SEG sg + SEG of row r for its SEG cells
     {
@@ -361,8 +361,8 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                 const f2 vb = mul2(c.vphi2[q & 3], sp);
                 const f2 *row = &S.tile[q][r + GR][0];
                 f2 *out = &S.adv[q][r][f0];
-                if (vb.x > 0.0f) phi_march_lin<SEG + 1, 1>(row, f0, l0, l1, l2, vb, out);
-                else phi_march_lin<SEG + 1, -1>(row, f0, l0, l1, l2, vb, out);
+                if (vb.x > 0.0f) phi_march_lin<SEG + 1, 1>(row, f0, l0, l1, l2, vb, S.rr[r][q], out);
+                else phi_march_lin<SEG + 1, -1>(row, f0, l0, l1, l2, vb, S.rr[r][q], out);
             }
         } else {
             const f2 E = splat(S.rowc[r].ephi);
@@ -371,8 +371,8 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                 const f2 vb = mul2(c.vphi2[q & 3], sp);
                 const f2 *row = &S.tile[q][r + GR][0];
                 f2 *out = &S.adv[q][r][f0];
-                if (vb.x > 0.0f) phi_march<SEG + 1, 1>(row, f0, E, vb, out);
-                else phi_march<SEG + 1, -1>(row, f0, E, vb, out);
+                if (vb.x > 0.0f) phi_march<SEG + 1, 1>(row, f0, E, vb, S.rr[r][q], out);
+                else phi_march<SEG + 1, -1>(row, f0, E, vb, S.rr[r][q], out);
             }
         }
     }
@@ -403,7 +403,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                 if (fy > 0) {
                     const int cy = fy - 1;
                     const f2 idth = splat(kom ? S.rowc[cy].kth : R.inv_dth);
-                    S.adv[q][cy][lane] = add2(fma2(sub2(prev, fl), idth, S.adv[q][cy][lane]), S.rr[cy][q]);
+                    S.adv[q][cy][lane] = fma2(sub2(prev, fl), idth, S.adv[q][cy][lane]);
                 }
                 prev = fl;
             }
@@ -427,7 +427,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             const f2 vt = mul2(c.vth[g], splat(__fmul_rn(dte, R.inv_dth)));
             const f2 *col = &S.tile[q][0][lane + GC];
             // values are produced one row ahead of their first use (face fy needs rows up to fy+5)
-            f2 x[SR], dd[SR], dfu[SR], D2[SR], Qa[SR], prev;
+            f2 x[SR], dd[SR], dfu[SR], D2[SR], Qa[SR], prev, dcarry;
 #pragma unroll
             for (int r = 0; r < 5; ++r) x[r] = col[r * SC];
 #pragma unroll
@@ -451,13 +451,16 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                     Qa[r - 1] = fma2(mul2(D2[r - 1], c133), D2[r - 1], E);
                 }
                 f2 B1, B2, B3, Q1, Q2, Q3, d12, d23, p2;
+                // the A differences of consecutive faces overlap: d12 of face fy + 1 is d23 of
+                // face fy for v > 0, and d23 of face fy + 1 is d12 of face fy for v < 0
                 if (g) {   // v_theta > 0: a..e = x[fy..fy+4]
                     Q1 = Qa[fy + 1]; Q2 = Qa[fy + 2]; Q3 = Qa[fy + 3];
                     B1 = fma2(two, dfu[fy + 2], D2[fy + 1]);
                     B2 = add2(dfu[fy + 2], dfu[fy + 3]);
                     B3 = fma2(m2, dfu[fy + 3], D2[fy + 3]);
-                    d12 = sub2(D2[fy + 1], D2[fy + 2]);
+                    d12 = fy ? dcarry : sub2(D2[fy + 1], D2[fy + 2]);
                     d23 = sub2(D2[fy + 2], D2[fy + 3]);
+                    dcarry = d23;
                     p2 = fma2(splat(1.0f / 6.0f), dd[fy + 2], fma2(splat(1.0f / 3.0f), dd[fy + 3], x[fy + 2]));
                 } else {   // v_theta < 0: a..e = x[fy+5..fy+1]
                     Q1 = Qa[fy + 4]; Q2 = Qa[fy + 3]; Q3 = Qa[fy + 2];
@@ -465,14 +468,15 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
                     B2 = add2(dfu[fy + 4], dfu[fy + 3]);
                     B3 = fma2(two, dfu[fy + 3], D2[fy + 2]);
                     d12 = sub2(D2[fy + 4], D2[fy + 3]);
-                    d23 = sub2(D2[fy + 3], D2[fy + 2]);
+                    d23 = fy ? dcarry : sub2(D2[fy + 3], D2[fy + 2]);
+                    dcarry = d12;
                     p2 = fma2(splat(-1.0f / 6.0f), dd[fy + 4], fma2(splat(-1.0f / 3.0f), dd[fy + 3], x[fy + 3]));
                 }
                 // P2 of the reference part is in the FP64-derived tendency rref
                 const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
                 if (fy > 0) {
                     const int cy = fy - 1;
-                    S.adv[q][cy][lane] = add2(fma2(vt, sub2(prev, v), S.adv[q][cy][lane]), S.rr[cy][q]);
+                    S.adv[q][cy][lane] = fma2(vt, sub2(prev, v), S.adv[q][cy][lane]);
                 }
                 prev = v;
             }
@@ -496,13 +500,11 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
 #pragma unroll
     for (int q = 0; q < NP2; ++q) G[q] = S.tile[q][cy + GR][cx + GC];
     // moments of delta f = dg / (k s)
-    f2 sn = G[0], sjt = mul2(c.vth[0], G[0]), sjp = mul2(c.vphi2[0], G[0]);
-#pragma unroll
-    for (int q = 1; q < NP2; ++q) {
-        sn = add2(sn, G[q]);
-        sjt = fma2(c.vth[q >> 2], G[q], sjt);
-        sjp = fma2(c.vphi2[q & 3], G[q], sjp);
-    }
+    // (from the sums over b at each g and over g at each b: v_theta depends on g, v_phi on b)
+    const f2 T0 = add2(add2(G[0], G[1]), add2(G[2], G[3])), T1 = add2(add2(G[4], G[5]), add2(G[6], G[7]));
+    const f2 S0 = add2(G[0], G[4]), S1 = add2(G[1], G[5]), S2 = add2(G[2], G[6]), S3 = add2(G[3], G[7]);
+    const f2 sn = add2(T0, T1), sjt = fma2(c.vth[1], T1, mul2(c.vth[0], T0));
+    const f2 sjp = fma2(c.vphi2[3], S3, fma2(c.vphi2[2], S2, fma2(c.vphi2[1], S1, mul2(c.vphi2[0], S0))));
     const float SG = sn.x + sn.y;                         // sum_k dg_k = s dn
     const float n = fmaf(SG, rc.inv_s, R.rho_ref);
     const float nin = 1.0f / n;
