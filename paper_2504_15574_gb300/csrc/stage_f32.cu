@@ -149,16 +149,20 @@ __device__ __forceinline__ void phi_march_lin(const f2 *row, int f0, f2 l0, f2 l
 // and q_i = t_i^2, where t_i = B_i^2 + 13/3 A_i^2 + E = 4 k^2 (sigma_i + eps) for the
 // unscaled forms (sigma_i = 13/12 A_i^2 + 1/4 B_i^2).  The weights are ratios, so the
 // common factor 4 k^2 cancels; the state scale k is chosen with E = 4 eps k^2 near 1,
-// so t_i >= E sin^2(theta) keeps the products q_j q_k clear of FP32 underflow down to
-// the pole rows, and they overflow only for sigma_i above ~1e9 eps.
+// so t_i >= E sin^2(theta) keeps every q_i a normal FP32 number down to the pole rows.
+// Numerator and denominator are divided by 0.1 q2 and multiplied by 3: with q1' = 1.5 q1,
+//   correction = (q3 d12 + q1' d23) / (3 q3 + q1' (6 + 12 q3 / q2)),
+// which needs no product of two q's; where q1' q3 / q2 overflows (q2 negligible beside
+// q1 and q3) the reciprocal is 0 and the value is P2, the limit of the weights there.
 __device__ __forceinline__ f2 weno_mix(f2 t1, f2 t2, f2 t3, f2 d12, f2 d23, f2 p2)
 {
     const f2 q1 = mul2(t1, t1), q2 = mul2(t2, t2), q3 = mul2(t3, t3);
-    const f2 q23 = mul2(q2, q3), q12 = mul2(q1, q2);
-    const f2 sum = fma2(splat(0.1f), q23, fma2(splat(0.6f), mul2(q1, q3), mul2(splat(0.3f), q12)));
-    const f2 r = make_float2(rcp_approx(sum.x), rcp_approx(sum.y));
-    // 0.1/3 q23 (A1 - A2) + 0.3/6 q12 (A2 - A3)
-    const f2 num = fma2(mul2(splat(0.1f / 3.0f), q23), d12, mul2(mul2(splat(0.05f), q12), d23));
+    const f2 q1p = mul2(q1, splat(1.5f));
+    const f2 r2 = make_float2(rcp_approx(q2.x), rcp_approx(q2.y));
+    const f2 w = fma2(mul2(q3, splat(12.0f)), r2, splat(6.0f));
+    const f2 den = fma2(q1p, w, mul2(q3, splat(3.0f)));
+    const f2 num = fma2(q3, d12, mul2(q1p, d23));
+    const f2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
     return fma2(num, r, p2);
 }
 
