@@ -536,14 +536,19 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         // equilibrium deviation times s: w (s dn + s n poly(xi)), poly = xi + (xi^2-u^2)/2 + xi(xi^2-3u^2)/6
         const f2 xi = fma2(c.vth[g], ut2, mul2(c.vphi2[b], up2));
         const f2 poly = fma2(xi, fma2(xi, fma2(xi, splat(1.0f / 6.0f), splat(0.5f)), h1), h0);
-        // force on dg: K along k_theta (pairs (0,b),(1,b) and (2,b),(3,b), with swapped partners), Ktilde along k_phi
+        // force bracket on dg: K along k_theta (pairs (0,b),(1,b) with swapped partners), Ktilde
+        // along k_phi (pairs (g,0..3)), the velocity factors folded into the coefficients
         const f2 P0 = G[b], P1 = G[4 + b];
-        const f2 kg = fma2(c.kpair[g][0], P0, fma2(c.kpair[g][1], swap2(P0), fma2(c.kpair[g][2], P1, mul2(c.kpair[g][3], swap2(P1)))));
         const f2 *Gg = G + 4 * g;
-        const f2 ktg = fma2(c.Kt2[4 * b], Gg[0], fma2(c.Kt2[4 * b + 1], Gg[1], fma2(c.Kt2[4 * b + 2], Gg[2], mul2(c.Kt2[4 * b + 3], Gg[3]))));
+        f2 fb = mul2(c.kf[q][0], P0);
+        fb = fma2(c.kf[q][1], swap2(P0), fb);
+        fb = fma2(c.kf[q][2], P1, fb);
+        fb = fma2(c.kf[q][3], swap2(P1), fb);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) fb = fma2(c.ktf[q][m], Gg[m], fb);
         // dte times: flux differences + s rref - force + s feq_dev / tau
         f2 a = S.adv[q][cy][cx];
-        a = fma2(ncot, fma2(c.vphisq2[b], kg, mul2(c.mvth[g], ktg)), a);
+        a = fma2(ncot, fb, a);
         a = fma2(c.w2[q], fma2(snn, poly, sg2), a);
         o[q] = fma2(cG, G[q], a);
         if (stage != 1) o[q] = fma2(cF, F0[q], o[q]);

@@ -165,26 +165,21 @@ int build_f32_tables(vlbm_t *h)
     const VelD &c = h->vd;
     VelC &f = h->vc;
     const double rr = h->rho_ref, ks = h->kscale;
-    for (int g = 0; g < 2; ++g) {
-        f.vth[g] = make_float2((float)c.v[2 * g], (float)c.v[2 * g + 1]);
-        f.mvth[g] = make_float2((float)-c.v[2 * g], (float)-c.v[2 * g + 1]);
-        const int a0 = 2 * g, a1 = 2 * g + 1;
-        f.kpair[g][0] = make_float2((float)c.K[a0 * 4 + 0], (float)c.K[a1 * 4 + 1]);
-        f.kpair[g][1] = make_float2((float)c.K[a0 * 4 + 1], (float)c.K[a1 * 4 + 0]);
-        f.kpair[g][2] = make_float2((float)c.K[a0 * 4 + 2], (float)c.K[a1 * 4 + 3]);
-        f.kpair[g][3] = make_float2((float)c.K[a0 * 4 + 3], (float)c.K[a1 * 4 + 2]);
-    }
-    for (int b = 0; b < 4; ++b) {
-        f.vphi2[b] = make_float2((float)c.v[b], (float)c.v[b]);
-        f.vphisq2[b] = make_float2((float)(c.v[b] * c.v[b]), (float)(c.v[b] * c.v[b]));
-    }
+    for (int g = 0; g < 2; ++g) f.vth[g] = make_float2((float)c.v[2 * g], (float)c.v[2 * g + 1]);
+    for (int b = 0; b < 4; ++b) f.vphi2[b] = make_float2((float)c.v[b], (float)c.v[b]);
     RunF &run = h->run;
     for (int q = 0; q < 8; ++q) {
-        const int g = q / 4, b = q % 4;
-        f.w2[q] = make_float2((float)(c.w[2 * g] * c.w[b]), (float)(c.w[2 * g + 1] * c.w[b]));
-        run.wr[q] = make_float2((float)(ks * c.w[2 * g] * c.w[b] * rr), (float)(ks * c.w[2 * g + 1] * c.w[b] * rr));
+        const int g = q / 4, b = q % 4, a0 = 2 * g, a1 = 2 * g + 1;
+        f.w2[q] = make_float2((float)(c.w[a0] * c.w[b]), (float)(c.w[a1] * c.w[b]));
+        run.wr[q] = make_float2((float)(ks * c.w[a0] * c.w[b] * rr), (float)(ks * c.w[a1] * c.w[b] * rr));
+        const double vb2 = c.v[b] * c.v[b];
+        f.kf[q][0] = make_float2((float)(vb2 * c.K[a0 * 4 + 0]), (float)(vb2 * c.K[a1 * 4 + 1]));
+        f.kf[q][1] = make_float2((float)(vb2 * c.K[a0 * 4 + 1]), (float)(vb2 * c.K[a1 * 4 + 0]));
+        f.kf[q][2] = make_float2((float)(vb2 * c.K[a0 * 4 + 2]), (float)(vb2 * c.K[a1 * 4 + 3]));
+        f.kf[q][3] = make_float2((float)(vb2 * c.K[a0 * 4 + 3]), (float)(vb2 * c.K[a1 * 4 + 2]));
+        for (int m = 0; m < 4; ++m)
+            f.ktf[q][m] = make_float2((float)(-c.v[a0] * c.Kt[b * 4 + m]), (float)(-c.v[a1] * c.Kt[b * 4 + m]));
     }
-    for (int q = 0; q < 16; ++q) f.Kt2[q] = make_float2((float)c.Kt[q], (float)c.Kt[q]);
     run.rho_ref = (float)rr;
 
     // upwind schemes (Eq. fluxes_U1-3): value = lin0 x_up2 + lin1 x_up + lin2 x_down

@@ -91,13 +91,16 @@ struct RunF {
 // multiply packed operands.
 struct VelC {
     float2 vth[2];       // (v[2g], v[2g+1])
-    float2 mvth[2];      // -(v[2g], v[2g+1])
     float2 vphi2[4];     // (v[b], v[b])
-    float2 vphisq2[4];   // (v[b]^2, v[b]^2)
     float2 w2[8];        // (w[2g] w[b], w[2g+1] w[b])
-    float2 kpair[2][4];  // K along k_theta as pair coefficients: (K[2g][0],K[2g+1][1]), (K[2g][1],K[2g+1][0]),
-                         // (K[2g][2],K[2g+1][3]), (K[2g][3],K[2g+1][2])
-    float2 Kt2[16];      // (Ktilde[b][m], Ktilde[b][m])
+    // The force bracket of Eq. df for pair q = 4g + b, v_phi^2 (K g) - v_theta (Ktilde g), as
+    // 8 packed coefficients (each an FP64 product rounded once): kf along k_theta on the
+    // operands (P0, swap P0, P1, swap P1) with P0, P1 the pairs (0, b), (1, b):
+    // v[b]^2 (K[2g][0], K[2g+1][1]), v[b]^2 (K[2g][1], K[2g+1][0]), v[b]^2 (K[2g][2], K[2g+1][3]),
+    // v[b]^2 (K[2g][3], K[2g+1][2]); ktf along k_phi on the pairs (g, m), m = 0..3:
+    // -(v[2g] Ktilde[b][m], v[2g+1] Ktilde[b][m]).
+    float2 kf[8][4];
+    float2 ktf[8][4];
 };
 
 constexpr int F32_TILE_COLS = 32;
