@@ -511,7 +511,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const f2 sjp = fma2(c.vphi2[3], S3, fma2(c.vphi2[2], S2, fma2(c.vphi2[1], S1, mul2(c.vphi2[0], S0))));
     const float SG = sn.x + sn.y;                         // sum_k dg_k = s dn
     const float n = fmaf(SG, rc.inv_s, R.rho_ref);
-    const float nin = 1.0f / n;
+    const float nin = rcp_approx(n);
     const float ut = (sjt.x + sjt.y) * rc.inv_s * nin;
     const float up = (sjp.x + sjp.y) * rc.inv_s * nin;
     const float u2 = fmaf(ut, ut, up * up);
@@ -524,7 +524,13 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const float cg0 = (stage == 1) ? 1.0f : (stage == 2) ? 0.25f : (2.0f / 3.0f);
     const float cgv = __fsub_rn(cg0, __fmul_rn(dte, R.tau_inv));
     const float sc = __fsub_rn(cg0, cgv);
-    const f2 ut2 = splat(ut), up2 = splat(up), snn = splat(__fmul_rn(__fmul_rn(sc, rc.s), n)), sg2 = splat(__fmul_rn(sc, SG));
+    // the equilibrium deviation times sc s: w (s dn + s n poly(xi)) sc, poly = xi + (xi^2 - u^2)/2
+    // + xi (xi^2 - 3 u^2)/6 = xi^3/6 + xi^2/2 + (1 - u^2/2) xi - u^2/2, its Horner coefficients
+    // scaled by sc s n once per cell (and sc s dn folded into the constant term)
+    const float sns = __fmul_rn(__fmul_rn(sc, rc.s), n);
+    const f2 ut2 = splat(ut), up2 = splat(up);
+    const f2 e3 = splat(__fmul_rn(sns, 1.0f / 6.0f)), e2 = splat(__fmul_rn(sns, 0.5f));
+    const f2 e1 = splat(__fmul_rn(sns, h1.x)), e0 = splat(__fmaf_rn(sns, h0.x, __fmul_rn(sc, SG)));
     const f2 ncot = splat(__fmul_rn(-dte, rc.cotR));
     const f2 cG = splat(cgv);
     const f2 cF = splat((stage == 2) ? 0.75f : __fsub_rn(1.0f, 2.0f / 3.0f));
@@ -533,9 +539,9 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
 #pragma unroll
     for (int q = 0; q < NP2; ++q) {
         const int g = q >> 2, b = q & 3;
-        // equilibrium deviation times s: w (s dn + s n poly(xi)), poly = xi + (xi^2-u^2)/2 + xi(xi^2-3u^2)/6
+        // xi = v . u; the equilibrium deviation times sc s, without w
         const f2 xi = fma2(c.vth[g], ut2, mul2(c.vphi2[b], up2));
-        const f2 poly = fma2(xi, fma2(xi, fma2(xi, splat(1.0f / 6.0f), splat(0.5f)), h1), h0);
+        const f2 feq = fma2(xi, fma2(xi, fma2(xi, e3, e2), e1), e0);
         // force bracket on dg: K along k_theta (pairs (0,b),(1,b) with swapped partners), Ktilde
         // along k_phi (pairs (g,0..3)), the velocity factors folded into the coefficients
         const f2 P0 = G[b], P1 = G[4 + b];
@@ -549,7 +555,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         // dte times: flux differences + s rref - force + s feq_dev / tau
         f2 a = S.adv[q][cy][cx];
         a = fma2(ncot, fb, a);
-        a = fma2(c.w2[q], fma2(snn, poly, sg2), a);
+        a = fma2(c.w2[q], feq, a);
         o[q] = fma2(cG, G[q], a);
         if (stage != 1) o[q] = fma2(cF, F0[q], o[q]);
     }
