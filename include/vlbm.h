@@ -202,7 +202,8 @@ VLBM_API int vlbm_batch_moments(vlbm_batch_t *b, int run, double *rho, double *u
 /* Populations of run `run` as FP64 host array [16][n_theta][n_phi] (as vlbm_get_populations). */
 VLBM_API int vlbm_batch_get_populations(vlbm_batch_t *b, int run, double *f);
 /* Launch schedule: tile rows (4 or 8; tiles are 32 columns wide) and persistent CTAs
- * per SM (0: the occupancy limit). */
+ * per SM (0: the occupancy limit; -1: one CTA per (run, tile) work item, a grid over all
+ * tiles instead of a persistent one). */
 VLBM_API int vlbm_batch_set_schedule(vlbm_batch_t *b, int tile_rows, int ctas_per_sm);
 /* Autotuner: times every schedule (tile rows x CTAs per SM) on the batch's own
  * state, restores the state, and applies the fastest.  With cache_path != NULL the

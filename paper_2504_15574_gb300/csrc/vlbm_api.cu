@@ -936,6 +936,7 @@ int batch_refresh(vlbm_batch_t *b)
 
 int batch_ctas(const vlbm_batch_t *b)
 {
+    if (b->ctas_per_sm < 0) return std::max(1, b->ntiles);   // one CTA per work item
     const int per = b->ctas_per_sm > 0 ? b->ctas_per_sm : stage_f32_max_ctas_per_sm(b->ty);
     return std::max(1, std::min(b->ntiles, per * b->nsm));
 }
@@ -1107,7 +1108,7 @@ int vlbm_batch_get_populations(vlbm_batch_t *b, int run, double *f)
 
 int vlbm_batch_set_schedule(vlbm_batch_t *b, int tile_rows, int ctas_per_sm)
 {
-    if (!b || (tile_rows != 4 && tile_rows != 8) || ctas_per_sm < 0) return bfail(b, VLBM_ERR_ARG, "bad schedule");
+    if (!b || (tile_rows != 4 && tile_rows != 8) || ctas_per_sm < -1) return bfail(b, VLBM_ERR_ARG, "bad schedule");
     if (ctas_per_sm > stage_f32_max_ctas_per_sm(tile_rows)) return bfail(b, VLBM_ERR_ARG, "ctas_per_sm above occupancy");
     if (tile_rows != b->ty) b->dirty = true;
     b->ty = tile_rows;
@@ -1204,7 +1205,8 @@ int vlbm_batch_tune(vlbm_batch_t *b, const char *cache_path, int *tile_rows, int
         best = 1e300;
         for (int ty : {4, 8}) {
             const int maxc = stage_f32_max_ctas_per_sm(ty);
-            for (int c = 1; c <= maxc; ++c) {
+            for (int c = -1; c <= maxc; ++c) {
+                if (c == 0) continue;   // (0 is the occupancy limit, already among 1..maxc)
                 if ((rc = vlbm_batch_set_schedule(b, ty, c))) return rc;
                 double ms = 0.0;
                 if ((rc = vlbm_batch_profile(b, 2, &ms, nullptr))) return rc;
