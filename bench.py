@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--komissarov", action="store_true", help="Komissarov theta flux (upwind schemes)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="population storage (the headline workload is fp32)")
-    ap.add_argument("--velocity-set", default="d2q16", choices=["d2q16", "d2q9"], help="d2q9 runs in fp64 only")
+    ap.add_argument("--velocity-set", default="d2q16", choices=["d2q16", "d2q9"])
     args = ap.parse_args()
     global NT, NP, DT
     NT, NP = args.n_theta, args.n_phi
@@ -84,10 +84,11 @@ def committed_traffic(args):
     """DRAM bytes of the three stage launches of one step from the committed ncu summary of
     this scheme at 1024 x 2048 (null there once the kernel has changed since the capture,
     and null for another grid or a scheme without a summary)."""
-    if (NT, NP) != (1024, 2048):
+    if (NT, NP) != (1024, 2048) or args.precision != "fp32":
         return None
-    name = "stage_f32_1024x2048.md" if args.scheme == "weno5" else \
-        f"stage_f32_{args.scheme}{'k' if args.komissarov else ''}_1024x2048.md"
+    vs = "_d2q9" if args.velocity_set == "d2q9" else ""
+    name = f"stage_f32{vs}_1024x2048.md" if args.scheme == "weno5" else \
+        f"stage_f32{vs}_{args.scheme}{'k' if args.komissarov else ''}_1024x2048.md"
     path = os.path.join(ROOT, "profiles", name)
     try:
         for line in open(path):
@@ -284,7 +285,8 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (three 134 MB population arrays per replica)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "stage_f32_kernel (3 launches per step; bytes and traffic per step)",
+                         "kernel": ("stage_f32_kernel" if args.precision == "fp32" else "stage_f64 kernels")
+                         + " (3 stages per step; bytes and traffic per step)",
                          "stage_ms": stage_ms, "filter_ms": filter_ms},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d / e2e_steps,

@@ -56,7 +56,7 @@ extern "C" {
 #define VLBM_ERR_TIMEOUT     -5  /* a bounded device-side wait gave up */
 
 /* Velocity sets (App. A): the enum value is the quadrature order Q. */
-#define VLBM_D2Q9  3             /* Q = 3 (App. A.1): 9 populations, second-order equilibrium; FP64 path */
+#define VLBM_D2Q9  3             /* Q = 3 (App. A.1): 9 populations, second-order equilibrium */
 #define VLBM_D2Q16 4
 
 /* Advection schemes (Sec. 3.5): WENO-5, Eqs. (fluxes_W5)-(WENO5_sigma), or the
@@ -108,7 +108,8 @@ VLBM_API void vlbm_default_options(vlbm_options *opt);
 
 /* Creates a solver on an n_theta x n_phi grid.
  *   velocity_set: VLBM_D2Q16 (16 populations, Eq. feq_Q=4), or VLBM_D2Q9 (9 populations,
- *   Eq. feq_Q=3, kernels of Eq. Q3_kernels; VLBM_FP64 only, VLBM_FP32 -> VLBM_ERR_UNSUPPORTED).
+ *   Eq. feq_Q=3, kernels of Eq. Q3_kernels; both precisions, FP32 stored in five population
+ *   pairs, the fifth with one empty member).
  *   n_theta >= 6 (three WENO ghost rows per pole), n_phi even or 1,
  *   n_theta <= 65536, n_phi <= 65536; tau > 0 (BGK relaxation time, Sec. 3.2);
  *   dt > 0 (the caller chooses it; see vlbm_max_stable_dt); opt may be NULL.
@@ -266,7 +267,7 @@ VLBM_API int vlbm_lc_apply(vlbm_lc_t *lc, vlbm_t *h);
  * vlbm_lc_apply), enqueued on the solver's stream as a captured CUDA graph (built on
  * the first call for this solver; rebuilt after vlbm_lc_set_scales or for another
  * solver) with no host synchronisation between steps; returns after the last step
- * with the solver's status (vlbm_sync).  h must be FP32 on the network's grid. */
+ * with the solver's status (vlbm_sync).  h must be FP32 D2Q16 on the network's grid. */
 VLBM_API int vlbm_lc_rollout(vlbm_lc_t *lc, vlbm_t *h, int steps);
 VLBM_API const char *vlbm_lc_last_error(const vlbm_lc_t *lc);
 VLBM_API void vlbm_lc_destroy(vlbm_lc_t *lc);

@@ -131,8 +131,8 @@ int backward(vlbm_lc_t *n)
 int check_solver(vlbm_lc_t *n, vlbm_t *h)
 {
     if (!n || !h) return VLBM_ERR_ARG;
-    if (h->prec != VLBM_FP32 || h->nt != n->H || h->np != n->W)
-        return lfail(n, VLBM_ERR_ARG, "the solver must be FP32 on the network's grid");
+    if (h->prec != VLBM_FP32 || h->vd.q != 4 || h->nt != n->H || h->np != n->W)
+        return lfail(n, VLBM_ERR_ARG, "the solver must be FP32 D2Q16 on the network's grid");
     return VLBM_OK;
 }
 
@@ -146,7 +146,7 @@ int enqueue_correction(vlbm_lc_t *n, vlbm_t *h, cudaStream_t s)
     const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
     lc_outputs(n->d_y, LC_COUT, n->H, n->W, sc, n->d_sin, n->d_out, n->d_part, n->d_scal + 1, s);
     lc_nudge((float2 *)h->F, h->L, h->d_mom, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, h->kscale, s);
-    launch_fill_ghosts_f32((float2 *)h->F, h->L, s);
+    launch_fill_ghosts_f32((float2 *)h->F, h->L, h->vd.q, s);
     LCK(n, cudaGetLastError());
     return VLBM_OK;
 }

@@ -36,6 +36,7 @@
 //      the store of the cell and of its ghost images.
 #include "vlbm_internal.h"
 
+#include <cstddef>
 #include <algorithm>
 #include <cmath>
 
@@ -44,19 +45,21 @@ namespace vk {
 namespace {
 
 constexpr int TX = F32_TILE_COLS;
-constexpr int NP2 = 8;                 // population pairs
+constexpr int NP2 = 8;                 // population pairs of D2Q16
 constexpr int SC = F32_BOX_COLS;       // tile columns in shared memory (TX + 2 GC + 2)
 
-template <int TY>
+// NPP pair planes: 8 for D2Q16, 5 for D2Q9
+template <int TY, int NPP = NP2>
 struct __align__(128) SmemT {
-    float2 tile[NP2][TY + 2 * GR][SC];  // TMA destination (must stay first)
-    float2 adv[NP2][TY][TX + 1];        // per cell and pair: dte (flux differences + s rref); row
+    float2 tile[NPP][TY + 2 * GR][SC];  // TMA destination (must stay first)
+    float2 adv[NPP][TY][TX + 1];        // per cell and pair: dte (flux differences + s rref); row
                                         // stride TX+1 keeps the phi walkers' stores conflict-free
-    float2 ob[NP2][TY][TX];             // stages 2, 3: the tile of F (TMA load); then the output
-                                        // tile staged for the TMA store
+    __align__(128) float2 ob[NPP][TY][TX];   // stages 2, 3: the tile of F (TMA load); then the output
+                                             // tile staged for the TMA store (TMA wants 128-byte
+                                             // aligned shared memory)
     float2 ds2[TY + 2 * GR];            // (dsin, dsin) at the tile rows
     float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
-    float2 rr[TY][NP2];                 // dte s rref per cell row and pair
+    float2 rr[TY][NPP];                 // dte s rref per cell row and pair
     float2 isp2[TY + 2 * GR];           // upwind schemes, Komissarov: (1/sin, 1/sin) at the tile rows
     float2 sf2[TY + 1];                 // upwind schemes, Komissarov: interface sines of the face rows
     RowF rowc[TY];
@@ -64,6 +67,14 @@ struct __align__(128) SmemT {
     unsigned long long bar;
 };
 
+// TMA shared-memory operands start on 128-byte boundaries (the dynamic buffer itself is 128-aligned)
+typedef SmemT<8> Smem8;
+typedef SmemT<4> Smem4;
+typedef SmemT<8, 5> Smem8q3;
+typedef SmemT<4, 5> Smem4q3;
+static_assert(offsetof(Smem8, tile) == 0 && offsetof(Smem8, ob) % 128 == 0 && offsetof(Smem4, ob) % 128 == 0 &&
+                  offsetof(Smem8q3, ob) % 128 == 0 && offsetof(Smem4q3, ob) % 128 == 0,
+              "TMA operands in shared memory must be 128-byte aligned");
 // three CTAs of 8 tile rows per SM: 228 KB of shared memory per SM, 1 KB reserved per CTA
 static_assert(3 * (sizeof(SmemT<8>) + 128 + 1024) <= 228 * 1024, "stage tile exceeds a third of an SM's shared memory");
 
@@ -251,19 +262,53 @@ __device__ __forceinline__ void put_cols(f2 *f, const Layout &L, int p, int r, i
     for (int m = 1; c + m * L.np < L.np + GC; ++m) f[L.at(p, r, c + m * L.np)] = v;
 }
 
+// One member (slot s = 2 p + m) of a pair-plane cell and its periodic images.
+__device__ __forceinline__ void put_cols_slot(f2 *f, const Layout &L, int s, int r, int c, float v)
+{
+    float *base = reinterpret_cast<float *>(f) + (s & 1);
+    base[2 * L.at(s >> 1, r, c)] = v;
+    for (int m = 1; c - m * L.np >= -GC; ++m) base[2 * L.at(s >> 1, r, c - m * L.np)] = v;
+    for (int m = 1; c + m * L.np < L.np + GC; ++m) base[2 * L.at(s >> 1, r, c + m * L.np)] = v;
+}
+
 __device__ __forceinline__ int image_pair(int p) { return 4 * (1 - (p >> 2)) + (3 - (p & 3)); }
 
-__device__ __forceinline__ void store_images(f2 *f, const Layout &L, int p, int i, int j, f2 v)
+// The pole image of pair p's value v (cell in row i, column j) beyond the pole: -v of the mirrored
+// populations at column j + n_phi/2 of the mirrored ghost row.  D2Q16 maps a pair onto a pair with
+// its members swapped; in general each member goes to the slot of its own image.
+__device__ __forceinline__ void store_pole_image(f2 *f, const Layout &L, int q, int p, int i, int j, f2 v)
 {
-    put_cols(f, L, p, i, j, v);
-    if (i < GR || i >= L.nt - GR) {
-        int jj = j + L.np / 2;
-        if (jj >= L.np) jj -= L.np;
-        const int r = (i < GR) ? (-1 - i) : (2 * L.nt - 1 - i);
+    int jj = j + L.np / 2;
+    if (jj >= L.np) jj -= L.np;
+    const int r = (i < GR) ? (-1 - i) : (2 * L.nt - 1 - i);
+    if (q == 4) {
         put_cols(f, L, image_pair(p), r, jj, make_float2(-v.y, -v.x));
+    } else {
+        put_cols_slot(f, L, f32_image_slot(q, 2 * p), r, jj, -v.x);
+        put_cols_slot(f, L, f32_image_slot(q, 2 * p + 1), r, jj, -v.y);
     }
 }
 
+__device__ __forceinline__ void store_images(f2 *f, const Layout &L, int q, int p, int i, int j, f2 v)
+{
+    put_cols(f, L, p, i, j, v);
+    if (i < GR || i >= L.nt - GR) store_pole_image(f, L, q, p, i, j, v);
+}
+
+
+// Velocity constants of a velocity set's pairs as the stage kernel reads them.
+template <int Q> struct VelOf { typedef VelC type; };
+template <> struct VelOf<3> { typedef VelC3 type; };
+// (v_theta, v_theta) of pair q's members, and whether the pair's theta upwind side is below
+__device__ __forceinline__ f2 pair_vth(const VelC &c, int q) { return c.vth[q >> 2]; }
+__device__ __forceinline__ f2 pair_vth(const VelC3 &c, int q) { return c.vt2[q]; }
+__device__ __forceinline__ bool pair_thpos(const VelC &, int q) { return (q >> 2) != 0; }
+__device__ __forceinline__ bool pair_thpos(const VelC3 &c, int q) { return c.thdir[q] > 0; }
+// (v_phi, v_phi) of pair q's members, and the sign of the pair's phi flux (0: none)
+__device__ __forceinline__ f2 pair_vph(const VelC &c, int q) { return c.vphi2[q & 3]; }
+__device__ __forceinline__ f2 pair_vph(const VelC3 &c, int q) { return c.vb2[q]; }
+__device__ __forceinline__ int pair_phdir(const VelC &c, int q) { return c.vphi2[q & 3].x > 0.0f ? 1 : -1; }
+__device__ __forceinline__ int pair_phdir(const VelC3 &c, int q) { return c.phdir[q]; }
 
 // One stage of one TY x TX tile of one run.  The mbarrier is initialised by the
 // caller; `parity` is the phase this tile's load completes.  Returns false if
@@ -274,15 +319,18 @@ __device__ __forceinline__ void store_images(f2 *f, const Layout &L, int p, int 
 // every ghost image store their output from there with one TMA store through tmo.
 // LIN: the upwind schemes U1-U3 (Eq. fluxes_U1-3, optionally with the Komissarov theta flux)
 // instead of WENO-5.
-template <int TY, bool LIN>
-__device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int stage, const CUtensorMap *tm,
-                                           const CUtensorMap *tmo, const CUtensorMap *tmf, int bx, int by,
-                                           SmemT<TY> &S, unsigned parity, unsigned *err)
+// Q: the velocity set (4: D2Q16, 3: D2Q9 in five pairs).
+template <int TY, bool LIN, int Q>
+__device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q>::type &c, int stage,
+                                           const CUtensorMap *tm, const CUtensorMap *tmo, const CUtensorMap *tmf,
+                                           int bx, int by, SmemT<TY, (Q == 3 ? 5 : NP2)> &S, unsigned parity,
+                                           unsigned *err)
 {
+    constexpr int NPQ = (Q == 3) ? 5 : NP2;   // pair planes
     constexpr int SR = TY + 2 * GR;
     constexpr int NT = TY * 32;
-    constexpr unsigned TILE_BYTES = NP2 * SR * SC * sizeof(float2);
-    constexpr unsigned CORE_BYTES = NP2 * TY * TX * sizeof(float2);
+    constexpr unsigned TILE_BYTES = NPQ * SR * SC * sizeof(float2);
+    constexpr unsigned CORE_BYTES = NPQ * TY * TX * sizeof(float2);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int q0 = bx * TX;
@@ -326,10 +374,10 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
             S.d2s2[t] = splat(R.d2sin[i0 + t]);
         } else if ((t -= SR) < TY) {
             S.rowc[t] = R.row[min(i0 + t, L.nt - 1)];
-        } else if ((t -= TY) < TY * NP2) {
-            const int ry = t >> 3, q = t & 7;
-            S.rr[ry][q] = mul2(R.rref[(size_t)min(i0 + ry, L.nt - 1) * NP2 + q], splat(dte));
-        } else if (LIN && (t -= TY * NP2) < SR) {
+        } else if ((t -= TY) < TY * NPQ) {
+            const int ry = t / NPQ, q = t - (t / NPQ) * NPQ;
+            S.rr[ry][q] = mul2(R.rref[(size_t)min(i0 + ry, L.nt - 1) * NPQ + q], splat(dte));
+        } else if (LIN && (t -= TY * NPQ) < SR) {
             S.isp2[t] = splat(R.isp[i0 + t]);
         } else if (LIN && (t -= SR) < TY + 1) {
             S.sf2[t] = splat(R.sfc[i0 + t]);
@@ -361,22 +409,28 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         if constexpr (LIN) {
             const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
 #pragma unroll 1
-            for (int q = warp; q < NP2; q += NT / 32) {
-                const f2 vb = mul2(c.vphi2[q & 3], sp);
+            for (int q = warp; q < NPQ; q += NT / 32) {
+                const f2 vb = mul2(pair_vph(c, q), sp);
                 const f2 *row = &S.tile[q][r + GR][0];
                 f2 *out = &S.adv[q][r][f0];
-                if (vb.x > 0.0f) phi_march_lin<SEG + 1, 1>(row, f0, l0, l1, l2, vb, S.rr[r][q], out);
-                else phi_march_lin<SEG + 1, -1>(row, f0, l0, l1, l2, vb, S.rr[r][q], out);
+                const int dir = pair_phdir(c, q);
+                if (dir > 0) phi_march_lin<SEG + 1, 1>(row, f0, l0, l1, l2, vb, S.rr[r][q], out);
+                else if (dir < 0) phi_march_lin<SEG + 1, -1>(row, f0, l0, l1, l2, vb, S.rr[r][q], out);
+                else
+                    for (int j = 0; j < SEG; ++j) out[j] = S.rr[r][q];
             }
         } else {
             const f2 E = splat(S.rowc[r].ephi);
 #pragma unroll 1
-            for (int q = warp; q < NP2; q += NT / 32) {
-                const f2 vb = mul2(c.vphi2[q & 3], sp);
+            for (int q = warp; q < NPQ; q += NT / 32) {
+                const f2 vb = mul2(pair_vph(c, q), sp);
                 const f2 *row = &S.tile[q][r + GR][0];
                 f2 *out = &S.adv[q][r][f0];
-                if (vb.x > 0.0f) phi_march<SEG + 1, 1>(row, f0, E, vb, S.rr[r][q], out);
-                else phi_march<SEG + 1, -1>(row, f0, E, vb, S.rr[r][q], out);
+                const int dir = pair_phdir(c, q);
+                if (dir > 0) phi_march<SEG + 1, 1>(row, f0, E, vb, S.rr[r][q], out);
+                else if (dir < 0) phi_march<SEG + 1, -1>(row, f0, E, vb, S.rr[r][q], out);
+                else
+                    for (int j = 0; j < SEG; ++j) out[j] = S.rr[r][q];
             }
         }
     }
@@ -391,9 +445,9 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
         const bool kom = R.komissarov != 0;
 #pragma unroll 1
-        for (int q = warp; q < NP2; q += NT / 32) {
-            const int g = q >> 2;
-            const f2 vt = mul2(c.vth[g], splat(dte));
+        for (int q = warp; q < NPQ; q += NT / 32) {
+            const bool g = pair_thpos(c, q);
+            const f2 vt = mul2(pair_vth(c, q), splat(dte));
             const f2 *col = &S.tile[q][0][lane + GC];
             f2 x[SR], prev;
 #pragma unroll
@@ -425,10 +479,10 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
         const f2 E = splat(R.e_theta), c133 = splat(13.0f / 3.0f);
         const f2 two = splat(2.0f), m2 = splat(-2.0f);
 #pragma unroll 1
-        for (int q = warp; q < NP2; q += NT / 32) {
-            const int g = q >> 2;
+        for (int q = warp; q < NPQ; q += NT / 32) {
+            const bool g = pair_thpos(c, q);
             const f2 wr = R.wr[q];
-            const f2 vt = mul2(c.vth[g], splat(__fmul_rn(dte, R.inv_dth)));
+            const f2 vt = mul2(pair_vth(c, q), splat(__fmul_rn(dte, R.inv_dth)));
             const f2 *col = &S.tile[q][0][lane + GC];
             // values are produced one row ahead of their first use (face fy needs rows up to fy+5)
             f2 x[SR], dd[SR], dfu[SR], D2[SR], Qa[SR], prev, dcarry;
@@ -494,21 +548,35 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     if (i >= L.nt || j >= L.np) return true;
     // the step's start values of this cell (stages 2, 3; the slots this thread's output
     // overwrites below)
-    f2 F0[NP2];
+    f2 F0[NPQ];
     if (stage != 1) {
 #pragma unroll
-        for (int q = 0; q < NP2; ++q) F0[q] = S.ob[q][cy][cx];
+        for (int q = 0; q < NPQ; ++q) F0[q] = S.ob[q][cy][cx];
     }
     const RowF rc = S.rowc[cy];
-    f2 G[NP2];
+    f2 G[NPQ];
 #pragma unroll
-    for (int q = 0; q < NP2; ++q) G[q] = S.tile[q][cy + GR][cx + GC];
+    for (int q = 0; q < NPQ; ++q) G[q] = S.tile[q][cy + GR][cx + GC];
     // moments of delta f = dg / (k s)
-    // (from the sums over b at each g and over g at each b: v_theta depends on g, v_phi on b)
-    const f2 T0 = add2(add2(G[0], G[1]), add2(G[2], G[3])), T1 = add2(add2(G[4], G[5]), add2(G[6], G[7]));
-    const f2 S0 = add2(G[0], G[4]), S1 = add2(G[1], G[5]), S2 = add2(G[2], G[6]), S3 = add2(G[3], G[7]);
-    const f2 sn = add2(T0, T1), sjt = fma2(c.vth[1], T1, mul2(c.vth[0], T0));
-    const f2 sjp = fma2(c.vphi2[3], S3, fma2(c.vphi2[2], S2, fma2(c.vphi2[1], S1, mul2(c.vphi2[0], S0))));
+    f2 sn, sjt, sjp;
+    if constexpr (Q == 4) {
+        // (from the sums over b at each g and over g at each b: v_theta depends on g, v_phi on b)
+        const f2 T0 = add2(add2(G[0], G[1]), add2(G[2], G[3])), T1 = add2(add2(G[4], G[5]), add2(G[6], G[7]));
+        const f2 S0 = add2(G[0], G[4]), S1 = add2(G[1], G[5]), S2 = add2(G[2], G[6]), S3 = add2(G[3], G[7]);
+        sn = add2(T0, T1);
+        sjt = fma2(c.vth[1], T1, mul2(c.vth[0], T0));
+        sjp = fma2(c.vphi2[3], S3, fma2(c.vphi2[2], S2, fma2(c.vphi2[1], S1, mul2(c.vphi2[0], S0))));
+    } else {
+        sn = G[0];
+        sjt = mul2(c.vt2[0], G[0]);
+        sjp = mul2(c.vb2[0], G[0]);
+#pragma unroll
+        for (int q = 1; q < NPQ; ++q) {
+            sn = add2(sn, G[q]);
+            sjt = fma2(c.vt2[q], G[q], sjt);
+            sjp = fma2(c.vb2[q], G[q], sjp);
+        }
+    }
     const float SG = sn.x + sn.y;                         // sum_k dg_k = s dn
     const float n = fmaf(SG, rc.inv_s, R.rho_ref);
     const float nin = rcp_approx(n);
@@ -525,33 +593,63 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const float cgv = __fsub_rn(cg0, __fmul_rn(dte, R.tau_inv));
     const float sc = __fsub_rn(cg0, cgv);
     // the equilibrium deviation times sc s: w (s dn + s n poly(xi)) sc, poly = xi + (xi^2 - u^2)/2
-    // + xi (xi^2 - 3 u^2)/6 = xi^3/6 + xi^2/2 + (1 - u^2/2) xi - u^2/2, its Horner coefficients
+    // + xi (xi^2 - 3 u^2)/6 = xi^3/6 + xi^2/2 + (1 - u^2/2) xi - u^2/2 (D2Q16, Eq. feq_Q=4; D2Q9
+    // stops at the second order, Eq. feq_Q=3: xi^2/2 + xi - u^2/2), its Horner coefficients
     // scaled by sc s n once per cell (and sc s dn folded into the constant term)
     const float sns = __fmul_rn(__fmul_rn(sc, rc.s), n);
     const f2 ut2 = splat(ut), up2 = splat(up);
     const f2 e3 = splat(__fmul_rn(sns, 1.0f / 6.0f)), e2 = splat(__fmul_rn(sns, 0.5f));
-    const f2 e1 = splat(__fmul_rn(sns, h1.x)), e0 = splat(__fmaf_rn(sns, h0.x, __fmul_rn(sc, SG)));
+    const f2 e1 = splat(Q == 4 ? __fmul_rn(sns, h1.x) : sns), e0 = splat(__fmaf_rn(sns, h0.x, __fmul_rn(sc, SG)));
+    // D2Q9 force brackets per slot (see below)
+    float fbs[2 * NPQ];
+    if constexpr (Q == 3) {
+        // slot sources of the six terms of each slot's bracket (slot s = 2 p + m, population
+        // (a, b)): the populations (a', b), a' = 0..2, then (a, b'), b' = 0..2; slot 9 is empty
+        constexpr int SRC[10][6] = {{0, 1, 4, 0, 8, 2}, {0, 1, 4, 1, 7, 3}, {2, 3, 6, 0, 8, 2}, {2, 3, 6, 1, 7, 3},
+                                    {0, 1, 4, 4, 5, 6}, {8, 7, 5, 4, 5, 6}, {2, 3, 6, 4, 5, 6}, {8, 7, 5, 1, 7, 3},
+                                    {8, 7, 5, 0, 8, 2}, {9, 9, 9, 9, 9, 9}};
+        float gs[10];
+#pragma unroll
+        for (int q = 0; q < NPQ; ++q) {
+            gs[2 * q] = G[q].x;
+            gs[2 * q + 1] = G[q].y;
+        }
+#pragma unroll
+        for (int t = 0; t < 10; ++t) {
+            float acc = __fmul_rn(c.fcoef[t][0], gs[SRC[t][0]]);
+#pragma unroll
+            for (int m = 1; m < 6; ++m) acc = __fmaf_rn(c.fcoef[t][m], gs[SRC[t][m]], acc);
+            fbs[t] = acc;
+        }
+    }
     const f2 ncot = splat(__fmul_rn(-dte, rc.cotR));
     const f2 cG = splat(cgv);
     const f2 cF = splat((stage == 2) ? 0.75f : __fsub_rn(1.0f, 2.0f / 3.0f));
 
-    f2 o[NP2];
+    f2 o[NPQ];
 #pragma unroll
-    for (int q = 0; q < NP2; ++q) {
-        const int g = q >> 2, b = q & 3;
+    for (int q = 0; q < NPQ; ++q) {
         // xi = v . u; the equilibrium deviation times sc s, without w
-        const f2 xi = fma2(c.vth[g], ut2, mul2(c.vphi2[b], up2));
-        const f2 feq = fma2(xi, fma2(xi, fma2(xi, e3, e2), e1), e0);
-        // force bracket on dg: K along k_theta (pairs (0,b),(1,b) with swapped partners), Ktilde
-        // along k_phi (pairs (g,0..3)), the velocity factors folded into the coefficients
-        const f2 P0 = G[b], P1 = G[4 + b];
-        const f2 *Gg = G + 4 * g;
-        f2 fb = mul2(c.kf[q][0], P0);
-        fb = fma2(c.kf[q][1], swap2(P0), fb);
-        fb = fma2(c.kf[q][2], P1, fb);
-        fb = fma2(c.kf[q][3], swap2(P1), fb);
+        f2 xi, feq, fb;
+        if constexpr (Q == 4) {
+            const int g = q >> 2, b = q & 3;
+            xi = fma2(c.vth[g], ut2, mul2(c.vphi2[b], up2));
+            feq = fma2(xi, fma2(xi, fma2(xi, e3, e2), e1), e0);
+            // force bracket on dg: K along k_theta (pairs (0,b),(1,b) with swapped partners), Ktilde
+            // along k_phi (pairs (g,0..3)), the velocity factors folded into the coefficients
+            const f2 P0 = G[b], P1 = G[4 + b];
+            const f2 *Gg = G + 4 * g;
+            fb = mul2(c.kf[q][0], P0);
+            fb = fma2(c.kf[q][1], swap2(P0), fb);
+            fb = fma2(c.kf[q][2], P1, fb);
+            fb = fma2(c.kf[q][3], swap2(P1), fb);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) fb = fma2(c.ktf[q][m], Gg[m], fb);
+            for (int m = 0; m < 4; ++m) fb = fma2(c.ktf[q][m], Gg[m], fb);
+        } else {
+            xi = fma2(c.vt2[q], ut2, mul2(c.vb2[q], up2));
+            feq = fma2(xi, fma2(xi, e2, e1), e0);
+            fb = make_float2(fbs[2 * q], fbs[2 * q + 1]);
+        }
         // dte times: flux differences + s rref - force + s feq_dev / tau
         f2 a = S.adv[q][cy][cx];
         a = fma2(ncot, fb, a);
@@ -566,7 +664,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     if (core) {
         f2 *ob = &S.ob[0][0][0];
 #pragma unroll
-        for (int q = 0; q < NP2; ++q) ob[(q * TY + cy) * TX + cx] = o[q];
+        for (int q = 0; q < NPQ; ++q) ob[(q * TY + cy) * TX + cx] = o[q];
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -582,29 +680,30 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const VelC &c, int sta
     const bool plain = (i >= GR && i < L.nt - GR && j >= GC && j < L.np - GC);
     if (plain) {
 #pragma unroll
-        for (int q = 0; q < NP2; ++q) out[L.at(q, i, j)] = o[q];
+        for (int q = 0; q < NPQ; ++q) out[L.at(q, i, j)] = o[q];
     } else {
 #pragma unroll
-        for (int q = 0; q < NP2; ++q) store_images(out, L, q, i, j, o[q]);
+        for (int q = 0; q < NPQ; ++q) store_images(out, L, Q, q, i, j, o[q]);
     }
     return true;
 }
 
-template <int TY, bool LIN>
+template <int TY, bool LIN, int Q>
 __global__ void __launch_bounds__(TY * 32, 24 / TY) stage_f32_kernel(const __grid_constant__ CUtensorMap tm,
                                                                       const __grid_constant__ CUtensorMap tmo,
                                                                       const __grid_constant__ CUtensorMap tmf,
-                                                                      const RunF R, const VelC c, int stage,
-                                                                      unsigned *err)
+                                                                      const RunF R, const typename VelOf<Q>::type c,
+                                                                      int stage, unsigned *err)
 {
+    typedef SmemT<TY, (Q == 3 ? 5 : NP2)> Smem;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SmemT<TY> &S = *reinterpret_cast<SmemT<TY> *>(smem_raw);
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();   // no thread may poll the barrier before its initialisation is visible
-    stage_tile<TY, LIN>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, blockIdx.y, S, 0u, err);
+    stage_tile<TY, LIN, Q>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, blockIdx.y, S, 0u, err);
 }
 
 // Persistent batch stage: CTA b takes work items b, b + gridDim.x, ...; a work item
@@ -633,8 +732,8 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const
         __syncthreads();
         const int tx = S.run.tiles_x;
         const CUtensorMap *tr = tms + 6 * w.x;
-        if (!stage_tile<TY, LIN>(S.run, c, stage, tr + (stage - 1), tr + 3 + stage % 3, tr + 3, w.y % tx, w.y / tx, S,
-                                 parity, err))
+        if (!stage_tile<TY, LIN, 4>(S.run, c, stage, tr + (stage - 1), tr + 3 + stage % 3, tr + 3, w.y % tx,
+                                    w.y / tx, S, parity, err))
             return;
         parity ^= 1u;
         __syncthreads();   // every thread is done with this tile's shared memory
@@ -643,21 +742,32 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const
 
 // ---- FP32 layout helpers (FP64 arithmetic) -----------------------------------------
 
-__device__ __forceinline__ double finit64(double n, double wk, double va, double vb, double ut, double up, double T)
+// Hermite projection of a Maxwellian at T: third order for q = 4 (Eq. feq_Q=4 at T = 1),
+// second order for q = 3 (Eq. feq_Q=3 at T = 1)
+__device__ __forceinline__ double finit64(int q, double n, double wk, double va, double vb, double ut, double up,
+                                          double T)
 {
     const double xi = va * ut + vb * up;
     const double u2 = ut * ut + up * up;
-    if (T == 1.0) return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
+    if (T == 1.0) {
+        if (q == 3) return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2));
+        return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
+    }
     const double v2 = va * va + vb * vb;
     const double dT = T - 1.0;
     const double second = xi * xi - u2 + dT * (v2 - 2.0);
+    if (q == 3) return n * wk * (1.0 + xi + 0.5 * second);
     const double third = xi * (xi * xi - 3.0 * u2) + 3.0 * dT * xi * (v2 - 4.0);
     return n * wk * (1.0 + xi + 0.5 * second + third / 6.0);
 }
 
-// population k = 4a + b lives in pair 4 (a/2) + b, member a % 2
-__device__ __forceinline__ int pair_of(int k) { return 4 * ((k >> 2) >> 1) + (k & 3); }
-__device__ __forceinline__ int member_of(int k) { return (k >> 2) & 1; }
+// population k of a velocity set of order q: the value of its slot (pair plane, member)
+__device__ __forceinline__ float slot_value(const f2 *f, const Layout &L, int q, int k, int i, int j)
+{
+    const int sl = f32_slot_of_pop(q, k);
+    const f2 pr = f[L.at(sl >> 1, i, j)];
+    return (sl & 1) ? pr.y : pr.x;
+}
 
 __global__ void init_f32_kernel(f2 *f, const Layout L, const double *rho, const double *ut, const double *up,
                                 const double *temp, const VelD c, double rho_ref, const double *sin_t, double ks)
@@ -668,15 +778,16 @@ __global__ void init_f32_kernel(f2 *f, const Layout L, const double *rho, const 
     const size_t cell = (size_t)i * L.np + j;
     const double tt = temp ? temp[cell] : 1.0;
     const double s = ks * sin_t[i];
-    float v[16];
-    for (int k = 0; k < NK; ++k) {
-        const int a = k / 4, b = k % 4;
+    const int q = c.q;
+    float v[NK];
+    for (int k = 0; k < q * q; ++k) {
+        const int a = k / q, b = k % q;
         const double wk = c.w[a] * c.w[b];
-        v[k] = (float)(s * (finit64(rho[cell], wk, c.v[a], c.v[b], ut[cell], up[cell], tt) - wk * rho_ref));
+        v[k] = (float)(s * (finit64(q, rho[cell], wk, c.v[a], c.v[b], ut[cell], up[cell], tt) - wk * rho_ref));
     }
-    for (int q = 0; q < NP2; ++q) {
-        const int g = q >> 2, b = q & 3;
-        f[L.at(q, i, j)] = make_float2(v[4 * (2 * g) + b], v[4 * (2 * g + 1) + b]);
+    for (int p = 0; p < f32_pairs(q); ++p) {
+        const int k0 = f32_pop_of_slot(q, 2 * p), k1 = f32_pop_of_slot(q, 2 * p + 1);
+        f[L.at(p, i, j)] = make_float2(k0 < 0 ? 0.0f : v[k0], k1 < 0 ? 0.0f : v[k1]);
     }
 }
 
@@ -686,18 +797,16 @@ __global__ void moments_f32_kernel(const f2 *f, const Layout L, double *rho, dou
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= L.np) return;
+    const int q = c.q, nk = q * q;
     const double inv_s = 1.0 / (ks * sin_t[i]);
     double fk[NK];
-    for (int k = 0; k < NK; ++k) {
-        const f2 pr = f[L.at(pair_of(k), i, j)];
-        const double d = (double)(member_of(k) ? pr.y : pr.x) * inv_s;
-        fk[k] = c.w[k / 4] * c.w[k % 4] * rho_ref + d;
-    }
+    for (int k = 0; k < nk; ++k)
+        fk[k] = c.w[k / q] * c.w[k % q] * rho_ref + (double)slot_value(f, L, q, k, i, j) * inv_s;
     double n = 0.0, jt = 0.0, jp = 0.0;
-    for (int k = 0; k < NK; ++k) {
+    for (int k = 0; k < nk; ++k) {
         n += fk[k];
-        jt += fk[k] * c.v[k / 4];
-        jp += fk[k] * c.v[k % 4];
+        jt += fk[k] * c.v[k / q];
+        jp += fk[k] * c.v[k % q];
     }
     const size_t cell = (size_t)i * L.np + j;
     const double u1 = jt / n, u2 = jp / n;
@@ -706,41 +815,46 @@ __global__ void moments_f32_kernel(const f2 *f, const Layout L, double *rho, dou
     up[cell] = u2;
     if (temp) {
         double e = 0.0;
-        for (int k = 0; k < NK; ++k) {
-            const double ct = c.v[k / 4] - u1, cp = c.v[k % 4] - u2;
+        for (int k = 0; k < nk; ++k) {
+            const double ct = c.v[k / q] - u1, cp = c.v[k % q] - u2;
             e += fk[k] * (ct * ct + cp * cp);
         }
         temp[cell] = e / (2.0 * n);
     }
 }
 
+// one population plane k < q^2 per blockIdx.z
 __global__ void pack_f32_kernel(const f2 *f, const Layout L, double *dense, const VelD c, double rho_ref,
                                 const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y, k = blockIdx.z;
+    const int i = blockIdx.y, k = blockIdx.z, q = c.q;
     if (j >= L.np) return;
-    const f2 pr = f[L.at(pair_of(k), i, j)];
-    const double d = (double)(member_of(k) ? pr.y : pr.x) / (ks * sin_t[i]);
-    dense[((size_t)k * L.nt + i) * L.np + j] = c.w[k / 4] * c.w[k % 4] * rho_ref + d;
+    const double d = (double)slot_value(f, L, q, k, i, j) / (ks * sin_t[i]);
+    dense[((size_t)k * L.nt + i) * L.np + j] = c.w[k / q] * c.w[k % q] * rho_ref + d;
 }
 
+// one pair plane per blockIdx.z (the empty slot of D2Q9 is written as zero)
 __global__ void unpack_f32_kernel(const double *dense, const Layout L, f2 *f, const VelD c, double rho_ref,
                                   const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y, q = blockIdx.z;
+    const int i = blockIdx.y, p = blockIdx.z, q = c.q;
     if (j >= L.np) return;
-    const int g = q >> 2, b = q & 3;
     float m[2];
     for (int h = 0; h < 2; ++h) {
-        const int a = 2 * g + h, k = 4 * a + b;
+        const int k = f32_pop_of_slot(q, 2 * p + h);
+        if (k < 0) {
+            m[h] = 0.0f;
+            continue;
+        }
+        const int a = k / q, b = k % q;
         m[h] = (float)(ks * sin_t[i] * (dense[((size_t)k * L.nt + i) * L.np + j] - c.w[a] * c.w[b] * rho_ref));
     }
-    f[L.at(q, i, j)] = make_float2(m[0], m[1]);
+    f[L.at(p, i, j)] = make_float2(m[0], m[1]);
 }
 
-__global__ void fill_ghosts_f32_kernel(f2 *f, const Layout L)
+__global__ void fill_ghosts_f32_kernel(f2 *f, const Layout L, int vq)
 {
     const int c = (int)(blockIdx.x * blockDim.x + threadIdx.x) - GC;
     const int r = (int)blockIdx.y - GR;
@@ -756,14 +870,24 @@ __global__ void fill_ghosts_f32_kernel(f2 *f, const Layout L)
         rs = 2 * L.nt - 1 - r;
         pole = true;
     }
-    if (pole) {
-        qs = image_pair(q);
-        shift = L.np / 2;
-    }
+    if (pole) shift = L.np / 2;
     int cc = (c + shift) % L.np;
     if (cc < 0) cc += L.np;
-    const f2 v = f[L.at(qs, rs, cc)];
-    f[L.at(q, r, c)] = pole ? make_float2(-v.y, -v.x) : v;
+    if (!pole) {
+        f[L.at(q, r, c)] = f[L.at(qs, rs, cc)];
+    } else if (vq == 4) {
+        const f2 v = f[L.at(image_pair(q), rs, cc)];
+        f[L.at(q, r, c)] = make_float2(-v.y, -v.x);
+    } else {
+        // each member from the slot of its own image
+        float m[2];
+        for (int h = 0; h < 2; ++h) {
+            const int is = f32_image_slot(vq, 2 * q + h);
+            const f2 v = f[L.at(is >> 1, rs, cc)];
+            m[h] = -((is & 1) ? v.y : v.x);
+        }
+        f[L.at(q, r, c)] = make_float2(m[0], m[1]);
+    }
 }
 
 // Polar ring filter, one CTA per (filtered row, pair plane).  The row is walked in
@@ -821,16 +945,11 @@ __device__ __forceinline__ f2 ff_mean(FF a, float inv_b)
 }
 
 // ghost images of cell (p, i, j): periodic columns and, on the first/last GR rows, the pole image
-__device__ __forceinline__ void store_ghosts(f2 *f, const Layout &L, int p, int i, int j, f2 v)
+__device__ __forceinline__ void store_ghosts(f2 *f, const Layout &L, int vq, int p, int i, int j, f2 v)
 {
     for (int m = 1; j - m * L.np >= -GC; ++m) f[L.at(p, i, j - m * L.np)] = v;
     for (int m = 1; j + m * L.np < L.np + GC; ++m) f[L.at(p, i, j + m * L.np)] = v;
-    if (i < GR || i >= L.nt - GR) {
-        int jj = j + L.np / 2;
-        if (jj >= L.np) jj -= L.np;
-        const int r = (i < GR) ? (-1 - i) : (2 * L.nt - 1 - i);
-        put_cols(f, L, image_pair(p), r, jj, make_float2(-v.y, -v.x));
-    }
+    if (i < GR || i >= L.nt - GR) store_pole_image(f, L, vq, p, i, j, v);
 }
 
 // means of the aligned blocks of B columns within one thread's FILT_COLS columns (n valid)
@@ -853,8 +972,9 @@ __device__ __forceinline__ void thread_block_means(f2 (&v)[FILT_COLS], int n, fl
     }
 }
 
-// Filters row i (block size b) of pair plane q; called by all FILT_THREADS threads of a CTA.
-__device__ __forceinline__ void filter_row_f32(f2 *f, const Layout &L, int i, int b, int q)
+// Filters row i (block size b) of pair plane q of a velocity set of order vq; called by all
+// FILT_THREADS threads of a CTA.
+__device__ __forceinline__ void filter_row_f32(f2 *f, const Layout &L, int vq, int i, int b, int q)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const float inv_b = 1.0f / (float)b;   // exact: b is a power of two
@@ -918,7 +1038,7 @@ __device__ __forceinline__ void filter_row_f32(f2 *f, const Layout &L, int i, in
                 for (int m = 0; m < n; ++m) row[c0 + m] = v[m];
             }
             if (ghost_row || c0 < GC || c0 + n > L.np - GC) {
-                for (int m = 0; m < n; ++m) store_ghosts(f, L, q, i, c0 + m, v[m]);
+                for (int m = 0; m < n; ++m) store_ghosts(f, L, vq, q, i, c0 + m, v[m]);
             }
         }
         return;
@@ -943,15 +1063,15 @@ __device__ __forceinline__ void filter_row_f32(f2 *f, const Layout &L, int i, in
         for (int k = 1; k < FILT_THREADS / 32; ++k) a = ff_add(a, wpart[k]);
         __syncthreads();
         const f2 mean = ff_mean(a, inv_b);
-        for (int c = t; c < b; c += FILT_THREADS) store_images(f, L, q, i, blk * b + c, mean);
+        for (int c = t; c < b; c += FILT_THREADS) store_images(f, L, vq, q, i, blk * b + c, mean);
     }
 }
 
 // One CTA per (filtered row, pair plane) of one run.
-__global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const Layout L, const int *rows,
+__global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const Layout L, int vq, const int *rows,
                                                                    const int *blocks)
 {
-    filter_row_f32(f, L, rows[blockIdx.x], blocks[blockIdx.x], blockIdx.y);
+    filter_row_f32(f, L, vq, rows[blockIdx.x], blocks[blockIdx.x], blockIdx.y);
 }
 
 // One CTA per (run, filtered row) item of a batch and pair plane: the row of the
@@ -961,7 +1081,7 @@ __global__ void __launch_bounds__(FILT_THREADS) batch_filter_f32_kernel(const Ru
     const int4 it = items[blockIdx.x];   // (run, row, block size, unused)
     const RunF &R = runs[it.x];
     f2 *out = (stage == 1) ? R.A : (stage == 2) ? R.B : R.F;
-    filter_row_f32(out, R.L, it.y, it.z, blockIdx.y);
+    filter_row_f32(out, R.L, 4, it.y, it.z, blockIdx.y);
 }
 
 constexpr int DIAG_THREADS = 256;
@@ -978,12 +1098,12 @@ __global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *
         double sp, cp;
         sincos((j + 0.5) * dph, &sp, &cp);
         double n = 0.0, jt = 0.0, jp = 0.0, e = 0.0, bad = 0.0;
-        for (int k = 0; k < NK; ++k) {
-            const double va = c.v[k / 4], vb = c.v[k % 4];
-            const f2 pr = f[L.at(pair_of(k), i, j)];
-            const double d = (double)(member_of(k) ? pr.y : pr.x);
+        const int q = c.q;
+        for (int k = 0; k < q * q; ++k) {
+            const double va = c.v[k / q], vb = c.v[k % q];
+            const double d = (double)slot_value(f, L, q, k, i, j);
             if (!isfinite(d)) bad = 1.0;
-            const double fk = c.w[k / 4] * c.w[k % 4] * rho_ref + d * inv_s;
+            const double fk = c.w[k / q] * c.w[k % q] * rho_ref + d * inv_s;
             n += fk;
             jt += fk * va;
             jp += fk * vb;
@@ -1011,14 +1131,17 @@ __global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *
 
 }  // namespace
 
-template <int TY>
-static size_t smem_bytes() { return sizeof(SmemT<TY>) + 128; }
+template <int TY, int Q = 4>
+static size_t smem_bytes() { return sizeof(SmemT<TY, (Q == 3 ? 5 : NP2)>) + 128; }
 
 template <int TY, bool LIN>
 cudaError_t prepare_one()
 {
-    cudaError_t e = cudaFuncSetAttribute(stage_f32_kernel<TY, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(stage_f32_kernel<TY, LIN, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_bytes<TY>());
+    if (e) return e;
+    e = cudaFuncSetAttribute(stage_f32_kernel<TY, LIN, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<TY, 3>());
     if (e) return e;
     return cudaFuncSetAttribute(batch_stage_f32_kernel<TY, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes<TY>());
@@ -1040,17 +1163,31 @@ int stage_f32_max_ctas_per_sm(int ty)
     return n;
 }
 
-void launch_stage_f32(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f, const RunF &run,
-                      const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s)
+template <int Q>
+static void launch_stage_q(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
+                           const RunF &run, const typename VelOf<Q>::type &c, int stage, int ty, bool lin,
+                           unsigned *err, cudaStream_t s)
 {
     const dim3 grid((run.L.np + TX - 1) / TX, (run.L.nt + ty - 1) / ty);
     if (ty == 4) {
-        if (lin) stage_f32_kernel<4, true><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
-        else stage_f32_kernel<4, false><<<grid, 128, smem_bytes<4>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
+        if (lin) stage_f32_kernel<4, true, Q><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
+        else stage_f32_kernel<4, false, Q><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
     } else {
-        if (lin) stage_f32_kernel<8, true><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
-        else stage_f32_kernel<8, false><<<grid, 256, smem_bytes<8>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
+        if (lin) stage_f32_kernel<8, true, Q><<<grid, 256, smem_bytes<8, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
+        else stage_f32_kernel<8, false, Q><<<grid, 256, smem_bytes<8, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
     }
+}
+
+void launch_stage_f32(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f, const RunF &run,
+                      const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s)
+{
+    launch_stage_q<4>(tm_in, tm_out, tm_f, run, c, stage, ty, lin, err, s);
+}
+
+void launch_stage_f32_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
+                         const RunF &run, const VelC3 &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s)
+{
+    launch_stage_q<3>(tm_in, tm_out, tm_f, run, c, stage, ty, lin, err, s);
 }
 
 void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
@@ -1089,21 +1226,21 @@ void launch_moments_f32(const float2 *f, const Layout &L, double *rho, double *u
 void launch_pack_f32(const float2 *f, const Layout &L, double *dense, const VelD &c, double rho_ref,
                      const double *sin_t, double ks, cudaStream_t s)
 {
-    dim3 grid((L.np + 127) / 128, L.nt, NK);
+    dim3 grid((L.np + 127) / 128, L.nt, c.q * c.q);
     pack_f32_kernel<<<grid, 128, 0, s>>>(f, L, dense, c, rho_ref, sin_t, ks);
 }
 
 void launch_unpack_f32(const double *dense, const Layout &L, float2 *f, const VelD &c, double rho_ref,
                        const double *sin_t, double ks, cudaStream_t s)
 {
-    dim3 grid((L.np + 127) / 128, L.nt, NP2);
+    dim3 grid((L.np + 127) / 128, L.nt, f32_pairs(c.q));
     unpack_f32_kernel<<<grid, 128, 0, s>>>(dense, L, f, c, rho_ref, sin_t, ks);
 }
 
-void launch_fill_ghosts_f32(float2 *f, const Layout &L, cudaStream_t s)
+void launch_fill_ghosts_f32(float2 *f, const Layout &L, int q, cudaStream_t s)
 {
-    dim3 grid((L.np + 2 * GC + 127) / 128, L.nt + 2 * GR, NP2);
-    fill_ghosts_f32_kernel<<<grid, 128, 0, s>>>(f, L);
+    dim3 grid((L.np + 2 * GC + 127) / 128, L.nt + 2 * GR, f32_pairs(q));
+    fill_ghosts_f32_kernel<<<grid, 128, 0, s>>>(f, L, q);
 }
 
 void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int stage, cudaStream_t s)
@@ -1112,11 +1249,12 @@ void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, in
     batch_filter_f32_kernel<<<dim3(nitems, NP2), FILT_THREADS, 0, s>>>(runs, items, stage);
 }
 
-void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s)
+void launch_filter_f32(float2 *f, const Layout &L, int q, const int *rows, const int *blocks, int nrows,
+                       cudaStream_t s)
 {
     if (nrows <= 0) return;
-    dim3 grid(nrows, NP2);
-    filter_f32_kernel<<<grid, FILT_THREADS, 0, s>>>(f, L, rows, blocks);
+    dim3 grid(nrows, f32_pairs(q));
+    filter_f32_kernel<<<grid, FILT_THREADS, 0, s>>>(f, L, q, rows, blocks);
 }
 
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,

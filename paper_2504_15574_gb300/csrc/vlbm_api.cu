@@ -163,22 +163,70 @@ int build_f32_tables(vlbm_t *h)
     const int nt = h->nt;
     const double R = h->R, dth = M_PI / nt, dph = 2.0 * M_PI / h->np;
     const VelD &c = h->vd;
-    VelC &f = h->vc;
+    const int q = c.q, npq = f32_pairs(q);
     const double rr = h->rho_ref, ks = h->kscale;
-    for (int g = 0; g < 2; ++g) f.vth[g] = make_float2((float)c.v[2 * g], (float)c.v[2 * g + 1]);
-    for (int b = 0; b < 4; ++b) f.vphi2[b] = make_float2((float)c.v[b], (float)c.v[b]);
     RunF &run = h->run;
-    for (int q = 0; q < 8; ++q) {
-        const int g = q / 4, b = q % 4, a0 = 2 * g, a1 = 2 * g + 1;
-        f.w2[q] = make_float2((float)(c.w[a0] * c.w[b]), (float)(c.w[a1] * c.w[b]));
-        run.wr[q] = make_float2((float)(ks * c.w[a0] * c.w[b] * rr), (float)(ks * c.w[a1] * c.w[b] * rr));
-        const double vb2 = c.v[b] * c.v[b];
-        f.kf[q][0] = make_float2((float)(vb2 * c.K[a0 * 4 + 0]), (float)(vb2 * c.K[a1 * 4 + 1]));
-        f.kf[q][1] = make_float2((float)(vb2 * c.K[a0 * 4 + 1]), (float)(vb2 * c.K[a1 * 4 + 0]));
-        f.kf[q][2] = make_float2((float)(vb2 * c.K[a0 * 4 + 2]), (float)(vb2 * c.K[a1 * 4 + 3]));
-        f.kf[q][3] = make_float2((float)(vb2 * c.K[a0 * 4 + 3]), (float)(vb2 * c.K[a1 * 4 + 2]));
-        for (int m = 0; m < 4; ++m)
-            f.ktf[q][m] = make_float2((float)(-c.v[a0] * c.Kt[b * 4 + m]), (float)(-c.v[a1] * c.Kt[b * 4 + m]));
+    if (q == 4) {
+        VelC &f = h->vc;
+        for (int g = 0; g < 2; ++g) f.vth[g] = make_float2((float)c.v[2 * g], (float)c.v[2 * g + 1]);
+        for (int b = 0; b < 4; ++b) f.vphi2[b] = make_float2((float)c.v[b], (float)c.v[b]);
+        for (int p = 0; p < 8; ++p) {
+            const int g = p / 4, b = p % 4, a0 = 2 * g, a1 = 2 * g + 1;
+            f.w2[p] = make_float2((float)(c.w[a0] * c.w[b]), (float)(c.w[a1] * c.w[b]));
+            const double vb2 = c.v[b] * c.v[b];
+            f.kf[p][0] = make_float2((float)(vb2 * c.K[a0 * 4 + 0]), (float)(vb2 * c.K[a1 * 4 + 1]));
+            f.kf[p][1] = make_float2((float)(vb2 * c.K[a0 * 4 + 1]), (float)(vb2 * c.K[a1 * 4 + 0]));
+            f.kf[p][2] = make_float2((float)(vb2 * c.K[a0 * 4 + 2]), (float)(vb2 * c.K[a1 * 4 + 3]));
+            f.kf[p][3] = make_float2((float)(vb2 * c.K[a0 * 4 + 3]), (float)(vb2 * c.K[a1 * 4 + 2]));
+            for (int m = 0; m < 4; ++m)
+                f.ktf[p][m] = make_float2((float)(-c.v[a0] * c.Kt[b * 4 + m]), (float)(-c.v[a1] * c.Kt[b * 4 + m]));
+        }
+    } else {
+        // D2Q9 in five pairs: per member its velocity and weight (0 for the empty slot), per
+        // pair the common sign of the nonzero v_theta and v_phi, per slot the force bracket's
+        // coefficients v_phi^2 K[a][a'] (on population (a', b)) and -v_theta Ktilde[b][b'] (on (a, b'))
+        VelC3 &f = h->vc3;
+        f = VelC3{};
+        for (int p = 0; p < npq; ++p) {
+            float vt[2], vb[2], w[2];
+            int sth = 0, sph = 0;
+            for (int m = 0; m < 2; ++m) {
+                const int k = f32_pop_of_slot(q, 2 * p + m);
+                vt[m] = vb[m] = w[m] = 0.0f;
+                if (k < 0) continue;
+                const int a = k / q, b = k % q;
+                vt[m] = (float)c.v[a];
+                vb[m] = (float)c.v[b];
+                w[m] = (float)(c.w[a] * c.w[b]);
+                const int st = (c.v[a] > 0) - (c.v[a] < 0), sp = (c.v[b] > 0) - (c.v[b] < 0);
+                if ((st && sth && st != sth) || (sp && sph && sp != sph))
+                    return fail(h, VLBM_ERR_UNSUPPORTED, "FP32 pair members with opposite velocity signs");
+                if (st) sth = st;
+                if (sp) sph = sp;
+            }
+            f.vt2[p] = make_float2(vt[0], vt[1]);
+            f.vb2[p] = make_float2(vb[0], vb[1]);
+            f.w2[p] = make_float2(w[0], w[1]);
+            f.thdir[p] = sth;
+            f.phdir[p] = sph;
+        }
+        for (int t = 0; t < 2 * npq; ++t) {
+            const int k = f32_pop_of_slot(q, t);
+            if (k < 0) continue;
+            const int a = k / q, b = k % q;
+            for (int m = 0; m < 3; ++m) {
+                f.fcoef[t][m] = (float)(c.v[b] * c.v[b] * c.K[a * 3 + m]);
+                f.fcoef[t][3 + m] = (float)(-c.v[a] * c.Kt[b * 3 + m]);
+            }
+        }
+    }
+    for (int p = 0; p < npq; ++p) {
+        double wr[2];
+        for (int m = 0; m < 2; ++m) {
+            const int k = f32_pop_of_slot(q, 2 * p + m);
+            wr[m] = (k < 0) ? 0.0 : ks * c.w[k / q] * c.w[k % q] * rr;
+        }
+        run.wr[p] = make_float2((float)wr[0], (float)wr[1]);
     }
     run.rho_ref = (float)rr;
 
@@ -212,7 +260,7 @@ int build_f32_tables(vlbm_t *h)
                                                            : lin[0] * b + lin[1] * cc + lin[2] * d;
         }
     std::vector<RowF> row(nt);
-    std::vector<float2> rref((size_t)nt * 8);
+    std::vector<float2> rref((size_t)nt * npq);
     for (int i = 0; i < nt; ++i) {
         const double s = h->sin_t[i], cot = h->cos_t[i] / h->sin_t[i];
         RowF rc;
@@ -224,9 +272,9 @@ int build_f32_tables(vlbm_t *h)
         rc.kth = (float)(s / (R * (h->cos_f[i] - h->cos_f[i + 1])));
         rc.pad1 = rc.pad2 = 0.0f;
         row[i] = rc;
-        double rk[16];
-        for (int k = 0; k < 16; ++k) {
-            const int a = k / 4, b = k % 4;
+        double rk[NK];
+        for (int k = 0; k < q * q; ++k) {
+            const int a = k / q, b = k % q;
             const double va = c.v[a], vb = c.v[b];
             const double wr = c.w[a] * c.w[b] * rr;
             const int dir = va > 0 ? 0 : 1;
@@ -239,16 +287,17 @@ int build_f32_tables(vlbm_t *h)
             else
                 adv = -va * wr * (plin[2 * (i + 1) + dir] - plin[2 * i + dir]) / (R * s * dth);
             double kw = 0.0, ktw = 0.0;
-            for (int m = 0; m < 4; ++m) {
-                kw += c.K[a * 4 + m] * c.w[m] * c.w[b] * rr;
-                ktw += c.Kt[b * 4 + m] * c.w[a] * c.w[m] * rr;
+            for (int m = 0; m < q; ++m) {
+                kw += c.K[a * q + m] * c.w[m] * c.w[b] * rr;
+                ktw += c.Kt[b * q + m] * c.w[a] * c.w[m] * rr;
             }
             const double force = cot / R * (vb * vb * kw - va * ktw);
             rk[k] = ks * s * (adv - force);
         }
-        for (int q = 0; q < 8; ++q) {
-            const int g = q / 4, b = q % 4;
-            rref[(size_t)i * 8 + q] = make_float2((float)rk[4 * (2 * g) + b], (float)rk[4 * (2 * g + 1) + b]);
+        for (int p = 0; p < npq; ++p) {
+            const int k0 = f32_pop_of_slot(q, 2 * p), k1 = f32_pop_of_slot(q, 2 * p + 1);
+            rref[(size_t)i * npq + p] =
+                make_float2(k0 < 0 ? 0.0f : (float)rk[k0], k1 < 0 ? 0.0f : (float)rk[k1]);
         }
     }
     // differences of sin at padded rows (pr-1, pr, pr+1 inside [0, nt + 2GR))
@@ -290,9 +339,9 @@ int build_f32_tables(vlbm_t *h)
     return VLBM_OK;
 }
 
-// Tensor map of an FP32 pair array: the stage input box (F32_BOX_COLS x (ty + 2 GR) x 8 pairs,
-// anchored GC columns and GR rows before the tile) or, with core set, the tile itself
-// (F32_TILE_COLS x ty x 8).
+// Tensor map of an FP32 pair array: the stage input box (F32_BOX_COLS x (ty + 2 GR) x all pair
+// planes, anchored GC columns and GR rows before the tile) or, with core set, the tile itself
+// (F32_TILE_COLS x ty x all pair planes: 8 for D2Q16, 5 for D2Q9).
 int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0, bool core = false)
 {
     if (ty == 0) ty = h->ty;
@@ -306,10 +355,11 @@ int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0, bool core = fa
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     // pair planes of float2, described as 8-byte elements
-    cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)(h->nt + 2 * GR), (cuuint64_t)(NK / 2)};
+    const int npq = f32_pairs(h->vd.q);
+    cuuint64_t dims[3] = {(cuuint64_t)h->L.pitch, (cuuint64_t)(h->nt + 2 * GR), (cuuint64_t)npq};
     cuuint64_t strides[2] = {(cuuint64_t)h->L.pitch * sizeof(float2), (cuuint64_t)h->L.plane * sizeof(float2)};
     cuuint32_t box[3] = {(cuuint32_t)(core ? F32_TILE_COLS : F32_BOX_COLS), (cuuint32_t)(core ? ty : ty + 2 * GR),
-                         (cuuint32_t)(NK / 2)};
+                         (cuuint32_t)npq};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -357,9 +407,13 @@ void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
         } else {
             const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
             const CUtensorMap &tmo = (st == 1) ? h->tmAc : (st == 2) ? h->tmBc : h->tmFc;
-            if (part != 2)
-                launch_stage_f32(tm, tmo, h->tmFc, h->run, h->vc, st, h->ty, h->scheme != VLBM_WENO5, h->d_flags, s);
-            if (h->nfrows && part != 1) launch_filter_f32((float2 *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
+            const bool lin = h->scheme != VLBM_WENO5;
+            if (part != 2) {
+                if (h->vd.q == 3) launch_stage_f32_q3(tm, tmo, h->tmFc, h->run, h->vc3, st, h->ty, lin, h->d_flags, s);
+                else launch_stage_f32(tm, tmo, h->tmFc, h->run, h->vc, st, h->ty, lin, h->d_flags, s);
+            }
+            if (h->nfrows && part != 1)
+                launch_filter_f32((float2 *)out, h->L, h->vd.q, h->d_frows, h->d_fblocks, h->nfrows, s);
         }
     }
     if (!stage_only && h->prec == VLBM_FP64)
@@ -397,7 +451,7 @@ void drop_graphs(vlbm_t *h)
 int after_reset(vlbm_t *h)
 {
     if (h->prec == VLBM_FP64) launch_fill_ghosts_f64((double *)h->F, h->L, h->stream);
-    else launch_fill_ghosts_f32((float2 *)h->F, h->L, h->stream);
+    else launch_fill_ghosts_f32((float2 *)h->F, h->L, h->vd.q, h->stream);
     CK(h, cudaMemsetAsync(h->d_budget, 0, sizeof(double), h->stream));
     CK(h, cudaMemsetAsync(h->d_flags, 0, sizeof(unsigned) * 4, h->stream));
     CK(h, cudaGetLastError());
@@ -466,8 +520,6 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     if (o.precision != VLBM_FP64 && o.precision != VLBM_FP32) return fail(nullptr, VLBM_ERR_ARG, "bad precision");
     if (!(o.weno_eps > 0.0) || !(o.radius > 0.0)) return fail(nullptr, VLBM_ERR_ARG, "weno_eps and radius must be > 0");
     if (o.scheme < VLBM_WENO5 || o.scheme > VLBM_U3) return fail(nullptr, VLBM_ERR_ARG, "unknown advection scheme");
-    if (velocity_set == VLBM_D2Q9 && o.precision != VLBM_FP64)
-        return fail(nullptr, VLBM_ERR_UNSUPPORTED, "D2Q9 runs on the FP64 path only");
     if (o.precision == VLBM_FP32 && o.scheme == VLBM_WENO5 && o.komissarov)
         return fail(nullptr, VLBM_ERR_UNSUPPORTED, "the FP32 path runs the Komissarov flux with the upwind schemes only");
 
@@ -492,7 +544,9 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     h->L.pitch = ((n_phi + 2 * GC) + 3) / 4 * 4;
     h->L.plane = (size_t)(n_theta + 2 * GR) * (size_t)h->L.pitch;
     h->L.nk = velocity_set * velocity_set;
-    h->arr_bytes = (size_t)h->L.nk * h->L.plane * h->elem;
+    // FP32: pair planes of float2 (D2Q9's fifth pair has one empty member)
+    h->arr_bytes = (h->prec == VLBM_FP64) ? (size_t)h->L.nk * h->L.plane * sizeof(double)
+                                          : (size_t)f32_pairs(velocity_set) * h->L.plane * sizeof(float2);
     velocity_tables(h->vd, velocity_set);
     row_tables(n_theta, h->sin_t, h->cos_t);
 
@@ -639,7 +693,7 @@ int vlbm_set_populations(vlbm_t *h, const double *f)
     } else {
         const size_t cells = (size_t)h->nt * h->np;
         std::vector<double> rho(cells, 0.0);
-        for (int k = 0; k < NK; ++k)
+        for (int k = 0; k < h->L.nk; ++k)
             for (size_t c = 0; c < cells; ++c) rho[c] += f[(size_t)k * cells + c];
         const double old = h->rho_ref;
         choose_rho_ref(h, rho);
@@ -705,7 +759,7 @@ int vlbm_step(vlbm_t *h, int n)
     if (rc) return rc;
     if (h->guard && n > 0) {
         if (h->prec == VLBM_FP64) launch_guard_f64((const double *)h->F, h->L.nk * h->L.plane, h->d_flags + 1, h->stream);
-        else launch_guard_f32((const float *)h->F, NK * h->L.plane, h->d_flags + 1, h->stream);
+        else launch_guard_f32((const float *)h->F, h->arr_bytes / sizeof(float), h->d_flags + 1, h->stream);
         CK(h, cudaGetLastError());
     }
     return vlbm_sync(h);
@@ -1152,7 +1206,7 @@ int vlbm_batch_step(vlbm_batch_t *b, int n)
     int rc = vlbm_batch_step_async(b, n);
     if (rc) return rc;
     if (b->guard && n > 0) {
-        for (vlbm_t *h : b->runs) launch_guard_f32((const float *)h->F, NK * h->L.plane, b->d_flags + 1, b->stream);
+        for (vlbm_t *h : b->runs) launch_guard_f32((const float *)h->F, h->arr_bytes / sizeof(float), b->d_flags + 1, b->stream);
         BCK(b, cudaGetLastError());
     }
     return vlbm_batch_sync(b);

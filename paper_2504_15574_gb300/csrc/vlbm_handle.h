@@ -44,6 +44,7 @@ struct vlbm {
     cudaGraphExec_t g1 = nullptr, g16 = nullptr;
     vk::VelD vd{};
     vk::VelC vc{};     // FP32 path: packed velocity constants
+    vk::VelC3 vc3{};   // FP32 path, D2Q9: the same for the five pairs
     vk::RunF run{};    // FP32 path: per-run stage parameters
     int ty = 8;    // FP32 path: tile rows
     double rho_ref = 0.0, rho_ref_opt = 0.0;

@@ -87,6 +87,39 @@ struct RunF {
     const float *sfc;          // [nt + 1 + 8] sin(fi dtheta) of theta interface fi (0 at both poles)
 };
 
+// Population slots of the FP32 pair layout: slot s = 2 p + m is member m of pair plane p.
+// D2Q16 (q = 4): pair p = 4 g + b holds (a, b) = (2g, b) and (2g + 1, b), which share the sign
+// of v_theta and the value of v_phi.  D2Q9 (q = 3): five pairs whose members share the sign of
+// each velocity component or have it zero (a member with a zero component has no flux along
+// it, so it rides with either direction): (0,0)&(1,0), (0,2)&(1,2), (2,0)&(2,1), (2,2)&(1,1),
+// and (0,1) with an always-zero slot.  Population k = q a + b; the pole image of k is
+// q^2 - 1 - k (velocity reversed).
+__host__ __device__ inline int f32_pairs(int q) { return q == 3 ? 5 : 8; }
+__host__ __device__ inline int f32_pop_of_slot(int q, int s)   // -1: the always-zero slot
+{
+    if (q == 3) {
+        const int t[10] = {0, 3, 2, 5, 6, 7, 8, 4, 1, -1};
+        return t[s];
+    }
+    const int p = s >> 1, m = s & 1;
+    return 4 * (2 * (p >> 2) + m) + (p & 3);
+}
+__host__ __device__ inline int f32_slot_of_pop(int q, int k)
+{
+    if (q == 3) {
+        const int t[9] = {0, 8, 2, 1, 7, 3, 4, 5, 6};
+        return t[k];
+    }
+    const int a = k >> 2, b = k & 3;
+    return 2 * (4 * (a >> 1) + b) + (a & 1);
+}
+// slot of the pole image of slot s (the always-zero slot maps to itself)
+__host__ __device__ inline int f32_image_slot(int q, int s)
+{
+    const int k = f32_pop_of_slot(q, s);
+    return k < 0 ? s : f32_slot_of_pop(q, q * q - 1 - k);
+}
+
 // Velocity-space constants shared by every run, pre-duplicated into pairs where they
 // multiply packed operands.
 struct VelC {
@@ -103,6 +136,16 @@ struct VelC {
     float2 ktf[8][4];
 };
 
+// The same for D2Q9 (q = 3) in its five pairs: per pair the members' velocities and weights
+// (zero for the empty slot), the sign of the pair's nonzero v_theta and v_phi (0: no phi
+// flux in the pair), and per slot the six force-bracket coefficients v_phi^2 K[a][a'] on the
+// populations (a', b), a' = 0..2, then -v_theta Ktilde[b][b'] on (a, b'), b' = 0..2.
+struct VelC3 {
+    float2 vt2[5], vb2[5], w2[5];
+    int thdir[5], phdir[5];
+    float fcoef[10][6];
+};
+
 constexpr int F32_TILE_COLS = 32;
 // Columns of the TMA box (and of the shared tile row): the tile's 32 plus GC on each side plus 2.
 // A row pitch of 42 float2 puts the 16-byte loads of 8 consecutive rows at one column in 8
@@ -115,6 +158,9 @@ constexpr int F32_TILE_ROWS_MAX = 8;
 cudaError_t prepare_stage_f32();   // sets the kernels' dynamic shared-memory limits
 void launch_stage_f32(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f, const RunF &run,
                       const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s);
+// The same for D2Q9 (five pair planes; tensor maps of depth 5).
+void launch_stage_f32_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
+                         const RunF &run, const VelC3 &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s);
 // One stage of a batch: a persistent grid of `ctas` CTAs walks `ntiles` work items
 // (run, tile) over the run table `runs` (device) and tensor maps `tms` (device, [run][6]: the box
 // maps of F, A, B, then the tile-core maps of F, A, B).
@@ -134,8 +180,10 @@ void launch_pack_f32(const float2 *f, const Layout &L, double *dense, const VelD
                      const double *sin_t, double ks, cudaStream_t s);
 void launch_unpack_f32(const double *dense, const Layout &L, float2 *f, const VelD &c, double rho_ref,
                        const double *sin_t, double ks, cudaStream_t s);
-void launch_fill_ghosts_f32(float2 *f, const Layout &L, cudaStream_t s);
-void launch_filter_f32(float2 *f, const Layout &L, const int *rows, const int *blocks, int nrows, cudaStream_t s);
+// (q: the velocity set's order, which fixes the pair planes and the pole images of the slots)
+void launch_fill_ghosts_f32(float2 *f, const Layout &L, int q, cudaStream_t s);
+void launch_filter_f32(float2 *f, const Layout &L, int q, const int *rows, const int *blocks, int nrows,
+                       cudaStream_t s);
 // Polar filter of every (run, row, block size) item of a batch on the output array of `stage`.
 void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int stage, cudaStream_t s);
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,

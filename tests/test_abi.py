@@ -73,12 +73,14 @@ def test_create_rejects_bad_arguments_before_the_gpu(lib, args, code):
     assert vlbm.vlbm_last_error()
 
 
-def test_create_refuses_d2q9_on_the_fp32_path_before_the_gpu(lib):
+@pytest.mark.parametrize("velocity_set", [3, 4])
+def test_create_refuses_fp32_weno_with_komissarov_before_the_gpu(lib, velocity_set):
     from paper_2504_15574_gb300 import vlbm
     o = vlbm.vlbm_default_options()
     o.precision = vlbm.VLBM_FP32
+    o.komissarov = 1
     with pytest.raises(vlbm.VlbmError) as e:
-        vlbm.vlbm_create(32, 64, vlbm.VLBM_D2Q9, 0.1, 1e-3, o)
+        vlbm.vlbm_create(32, 64, velocity_set, 0.1, 1e-3, o)
     assert e.value.code == vlbm.VLBM_ERR_UNSUPPORTED
 
 

@@ -232,6 +232,64 @@ def test_fp32_schemes_match_oracle_within_stated_bound(V, scheme, komissarov, nt
     assert e["u"] <= FP32_SCHEME_TOL["u"], e
 
 
+# FP32 D2Q9: five pair planes (four pairs whose members share the sign of each nonzero velocity
+# component, one population beside an always-zero slot), the same kernel as D2Q16.  Stated bounds
+# of the same origin as above, each above the worst GB300 value.
+D2Q9_FP32_CASES = D2Q9_CASES + [
+    # several 8 x 32 tiles in both directions with ragged last ones
+    ("vortices_40x100", 40, 100, False, "weno5", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 4, umax=0.08)),
+    ("filter_sound_64x128", 64, 128, True, "weno5", False, lambda nt, np_: inputs.sound_legendre(nt, np_, 3)),
+]
+D2Q9_FP32_TOL = {
+    # name: (tol_rho, tol_drho, tol_u)
+    "vortices_16x32": (1e-7, 2e-4, 2e-5),
+    "shock_T_24x16": (1e-5, 1e-5, 1e-4),
+    "filter_u3_komissarov_16x32": (1e-7, 2e-4, 2e-5),
+    "ragged_13x10_u2": (1e-7, 2e-4, 2e-5),
+    # (its density deviation is ~3e-5 of rho: drho measures FP32 rounding on a tiny scale)
+    "vortices_40x100": (1e-7, 1e-3, 2e-5),
+    "filter_sound_64x128": (1e-7, 2e-4, 2e-5),
+}
+
+
+def d2q9_dt(nt, np_, tau, filt):
+    dth, vmax = math.pi / nt, math.sqrt(3.0)
+    return 0.125 * dth / vmax if filt else min(0.25 * min(dth, math.sin(dth / 2) * 2 * math.pi / np_) / vmax, tau)
+
+
+@pytest.mark.parametrize("case", D2Q9_FP32_CASES, ids=[c[0] for c in D2Q9_FP32_CASES])
+def test_fp32_d2q9_matches_oracle_within_stated_bound(V, case):
+    """The D2Q9 velocity set (App. A.1, Eqs. feq_Q=3, Q3_kernels) on the FP32 deviation path."""
+    name, nt, np_, filt, scheme, kom, ic = case
+    tau = 0.02
+    o, g = run_pair(V, nt, np_, tau, d2q9_dt(nt, np_, tau, filt), ic(nt, np_), 40, precision="fp32",
+                    polar_filter=filt, scheme=scheme, komissarov=kom, velocity_set="d2q9")
+    e = errors(g.moments(), o.moments())
+    print(name, e)
+    tol_rho, tol_drho, tol_u = D2Q9_FP32_TOL[name]
+    assert e["rho"] <= tol_rho and e["drho"] <= tol_drho, e
+    assert e["u"] <= tol_u, e
+    f, fo = g.get_populations(), o.get_populations()
+    assert f.shape == (9, nt, np_)
+    np.testing.assert_allclose(f, fo, rtol=0, atol=1e-5 * np.abs(fo).max())
+    # the populations in and out again through the five-pair layout: FP32 rounding of the deviations
+    g.set_populations(fo)
+    np.testing.assert_allclose(g.get_populations(), fo, rtol=0, atol=1e-7 * np.abs(fo).max())
+
+
+def test_fp32_d2q9_full_size_1024x2048_one_step(V):
+    """D2Q9 at the throughput grid size (shock cap at T = 1.5, WENO-5, polar filter): one step,
+    every cell against the oracle."""
+    nt, np_, tau = 1024, 2048, 1e-3
+    dt = 0.25 * (math.pi / nt) / math.sqrt(3.0)
+    o, g = run_pair(V, nt, np_, tau, dt, inputs.shock_cap(nt, np_), 1, precision="fp32", polar_filter=True,
+                    velocity_set="d2q9")
+    e = errors(g.moments(), o.moments())
+    print(e)
+    assert e["rho"] <= 1e-6 and e["drho"] <= 1e-6, e
+    assert e["u"] <= 1e-5, e
+
+
 def test_fp32_weno_with_komissarov_is_refused(V):
     with pytest.raises(V.VlbmError) as ex:
         V.Solver(16, 32, 0.02, 1e-4, precision="fp32", komissarov=True)
