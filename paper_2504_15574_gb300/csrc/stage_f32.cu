@@ -57,6 +57,9 @@ struct __align__(128) SmemT {
     __align__(128) float2 ob[NPP][TY][TX];   // stages 2, 3: the tile of F (TMA load); then the output
                                              // tile staged for the TMA store (TMA wants 128-byte
                                              // aligned shared memory)
+    // D2Q9 with 8 warps: the theta walkers' flux differences of the four flux pairs, written
+    // beside adv by other warps than the phi walkers' (one element otherwise)
+    float2 advT[NPP == 5 ? 4 : 1][NPP == 5 ? TY : 1][NPP == 5 ? TX + 1 : 1];
     float2 ds2[TY + 2 * GR];            // (dsin, dsin) at the tile rows
     float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
     float2 rr[TY][NPP];                 // dte s rref per cell row and pair
@@ -327,8 +330,15 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
                                            unsigned *err)
 {
     constexpr int NPQ = (Q == 3) ? 5 : NP2;   // pair planes
+    constexpr int NFQ = (Q == 3) ? 4 : NP2;   // pairs with fluxes (D2Q9's fifth: the rest population)
     constexpr int SR = TY + 2 * GR;
     constexpr int NT = TY * 32;
+    constexpr int NW = NT / 32;
+    // warps of the face phases: D2Q16 and 4-warp D2Q9 tiles walk a pair's phi faces and then its
+    // theta faces on one warp (pairs warp, warp + NW, ...); 8-warp D2Q9 tiles walk the four
+    // pairs' phi faces on warps 0-3 and their theta faces on warps 4-7, into advT
+    constexpr bool SPLIT = (Q == 3) && (NW == 2 * NFQ);
+    constexpr int FSTEP = SPLIT ? NFQ : NW;
     constexpr unsigned TILE_BYTES = NPQ * SR * SC * sizeof(float2);
     constexpr unsigned CORE_BYTES = NPQ * TY * TX * sizeof(float2);
     const int tid = threadIdx.x;
@@ -409,7 +419,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
         if constexpr (LIN) {
             const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
 #pragma unroll 1
-            for (int q = warp; q < NPQ; q += NT / 32) {
+            for (int q = warp; q < (SPLIT ? (warp < NFQ ? NFQ : 0) : NFQ); q += FSTEP) {
                 const f2 vb = mul2(pair_vph(c, q), sp);
                 const f2 *row = &S.tile[q][r + GR][0];
                 f2 *out = &S.adv[q][r][f0];
@@ -422,7 +432,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
         } else {
             const f2 E = splat(S.rowc[r].ephi);
 #pragma unroll 1
-            for (int q = warp; q < NPQ; q += NT / 32) {
+            for (int q = warp; q < (SPLIT ? (warp < NFQ ? NFQ : 0) : NFQ); q += FSTEP) {
                 const f2 vb = mul2(pair_vph(c, q), sp);
                 const f2 *row = &S.tile[q][r + GR][0];
                 f2 *out = &S.adv[q][r][f0];
@@ -445,7 +455,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
         const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
         const bool kom = R.komissarov != 0;
 #pragma unroll 1
-        for (int q = warp; q < NPQ; q += NT / 32) {
+        for (int q = SPLIT ? warp - NFQ : warp; q >= 0 && q < NFQ; q += FSTEP) {
             const bool g = pair_thpos(c, q);
             const f2 vt = mul2(pair_vth(c, q), splat(dte));
             const f2 *col = &S.tile[q][0][lane + GC];
@@ -461,7 +471,8 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
                 if (fy > 0) {
                     const int cy = fy - 1;
                     const f2 idth = splat(kom ? S.rowc[cy].kth : R.inv_dth);
-                    S.adv[q][cy][lane] = fma2(sub2(prev, fl), idth, S.adv[q][cy][lane]);
+                    if constexpr (SPLIT) S.advT[q][cy][lane] = mul2(sub2(prev, fl), idth);
+                    else S.adv[q][cy][lane] = fma2(sub2(prev, fl), idth, S.adv[q][cy][lane]);
                 }
                 prev = fl;
             }
@@ -479,7 +490,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
         const f2 E = splat(R.e_theta), c133 = splat(13.0f / 3.0f);
         const f2 two = splat(2.0f), m2 = splat(-2.0f);
 #pragma unroll 1
-        for (int q = warp; q < NPQ; q += NT / 32) {
+        for (int q = SPLIT ? warp - NFQ : warp; q >= 0 && q < NFQ; q += FSTEP) {
             const bool g = pair_thpos(c, q);
             const f2 wr = R.wr[q];
             const f2 vt = mul2(pair_vth(c, q), splat(__fmul_rn(dte, R.inv_dth)));
@@ -534,7 +545,8 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
                 const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
                 if (fy > 0) {
                     const int cy = fy - 1;
-                    S.adv[q][cy][lane] = fma2(vt, sub2(prev, v), S.adv[q][cy][lane]);
+                    if constexpr (SPLIT) S.advT[q][cy][lane] = mul2(vt, sub2(prev, v));
+                    else S.adv[q][cy][lane] = fma2(vt, sub2(prev, v), S.adv[q][cy][lane]);
                 }
                 prev = v;
             }
@@ -603,22 +615,29 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
     // D2Q9 force brackets per slot (see below)
     float fbs[2 * NPQ];
     if constexpr (Q == 3) {
-        // slot sources of the six terms of each slot's bracket (slot s = 2 p + m, population
-        // (a, b)): the populations (a', b), a' = 0..2, then (a, b'), b' = 0..2; slot 9 is empty
-        constexpr int SRC[10][6] = {{0, 1, 4, 0, 8, 2}, {0, 1, 4, 1, 7, 3}, {2, 3, 6, 0, 8, 2}, {2, 3, 6, 1, 7, 3},
-                                    {0, 1, 4, 4, 5, 6}, {8, 7, 5, 4, 5, 6}, {2, 3, 6, 4, 5, 6}, {8, 7, 5, 1, 7, 3},
-                                    {8, 7, 5, 0, 8, 2}, {9, 9, 9, 9, 9, 9}};
+        // the six terms of slot t's bracket (population (a, b)) act on the populations (a', b),
+        // a' = 0..2, then (a, b'), b' = 0..2, read from their slots
         float gs[10];
 #pragma unroll
         for (int q = 0; q < NPQ; ++q) {
             gs[2 * q] = G[q].x;
             gs[2 * q + 1] = G[q].y;
         }
+        // the population of each slot: the K terms vanish where v_phi = 0 (b = 1), the Ktilde terms
+        // where v_theta = 0 (a = 1), both for the empty slot; leaving out these exact zeros
+        // changes no rounding (fma(0, x, acc) = acc)
 #pragma unroll
         for (int t = 0; t < 10; ++t) {
-            float acc = __fmul_rn(c.fcoef[t][0], gs[SRC[t][0]]);
+            const int k = f32_pop_of_slot(3, t);
+            float acc = 0.0f;
+            bool first = true;
 #pragma unroll
-            for (int m = 1; m < 6; ++m) acc = __fmaf_rn(c.fcoef[t][m], gs[SRC[t][m]], acc);
+            for (int m = 0; m < 6; ++m) {
+                if (k < 0 || (m < 3 && k % 3 == 1) || (m >= 3 && k / 3 == 1)) continue;
+                const int src = f32_slot_of_pop(3, m < 3 ? 3 * m + k % 3 : 3 * (k / 3) + (m - 3));
+                acc = first ? __fmul_rn(c.fcoef[t][m], gs[src]) : __fmaf_rn(c.fcoef[t][m], gs[src], acc);
+                first = false;
+            }
             fbs[t] = acc;
         }
     }
@@ -650,8 +669,12 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
             feq = fma2(xi, fma2(xi, e2, e1), e0);
             fb = make_float2(fbs[2 * q], fbs[2 * q + 1]);
         }
-        // dte times: flux differences + s rref - force + s feq_dev / tau
-        f2 a = S.adv[q][cy][cx];
+        // dte times: flux differences + s rref - force + s feq_dev / tau (the rest population
+        // of D2Q9 has no flux: its share is the reference tendency alone)
+        f2 a;
+        if (q >= NFQ) a = S.rr[cy][q];
+        else if constexpr (SPLIT) a = add2(S.adv[q][cy][cx], S.advT[q][cy][cx]);
+        else a = S.adv[q][cy][cx];
         a = fma2(ncot, fb, a);
         a = fma2(c.w2[q], feq, a);
         o[q] = fma2(cG, G[q], a);

@@ -89,32 +89,32 @@ struct RunF {
 
 // Population slots of the FP32 pair layout: slot s = 2 p + m is member m of pair plane p.
 // D2Q16 (q = 4): pair p = 4 g + b holds (a, b) = (2g, b) and (2g + 1, b), which share the sign
-// of v_theta and the value of v_phi.  D2Q9 (q = 3): five pairs whose members share the sign of
-// each velocity component or have it zero (a member with a zero component has no flux along
-// it, so it rides with either direction): (0,0)&(1,0), (0,2)&(1,2), (2,0)&(2,1), (2,2)&(1,1),
-// and (0,1) with an always-zero slot.  Population k = q a + b; the pole image of k is
-// q^2 - 1 - k (velocity reversed).
-__host__ __device__ inline int f32_pairs(int q) { return q == 3 ? 5 : 8; }
-__host__ __device__ inline int f32_pop_of_slot(int q, int s)   // -1: the always-zero slot
+// of v_theta and the value of v_phi.  D2Q9 (q = 3): four pairs whose members share the sign of
+// each nonzero velocity component (a member with a zero component has no flux along it, so it
+// rides with either direction), (0,0)&(0,1), (0,2)&(1,2), (2,0)&(1,0), (2,2)&(2,1), and the
+// rest population (1,1), which has no flux at all, beside an always-zero slot.  Population
+// k = q a + b; the pole image of k is q^2 - 1 - k (velocity reversed).
+__host__ __device__ constexpr inline int f32_pairs(int q) { return q == 3 ? 5 : 8; }
+__host__ __device__ constexpr inline int f32_pop_of_slot(int q, int s)   // -1: the always-zero slot
 {
     if (q == 3) {
-        const int t[10] = {0, 3, 2, 5, 6, 7, 8, 4, 1, -1};
+        const int t[10] = {0, 1, 2, 5, 6, 3, 8, 7, 4, -1};
         return t[s];
     }
     const int p = s >> 1, m = s & 1;
     return 4 * (2 * (p >> 2) + m) + (p & 3);
 }
-__host__ __device__ inline int f32_slot_of_pop(int q, int k)
+__host__ __device__ constexpr inline int f32_slot_of_pop(int q, int k)
 {
     if (q == 3) {
-        const int t[9] = {0, 8, 2, 1, 7, 3, 4, 5, 6};
+        const int t[9] = {0, 1, 2, 5, 8, 3, 4, 7, 6};
         return t[k];
     }
     const int a = k >> 2, b = k & 3;
     return 2 * (4 * (a >> 1) + b) + (a & 1);
 }
 // slot of the pole image of slot s (the always-zero slot maps to itself)
-__host__ __device__ inline int f32_image_slot(int q, int s)
+__host__ __device__ constexpr inline int f32_image_slot(int q, int s)
 {
     const int k = f32_pop_of_slot(q, s);
     return k < 0 ? s : f32_slot_of_pop(q, q * q - 1 - k);

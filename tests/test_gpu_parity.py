@@ -233,22 +233,22 @@ def test_fp32_schemes_match_oracle_within_stated_bound(V, scheme, komissarov, nt
 
 
 # FP32 D2Q9: five pair planes (four pairs whose members share the sign of each nonzero velocity
-# component, one population beside an always-zero slot), the same kernel as D2Q16.  Stated bounds
-# of the same origin as above, each above the worst GB300 value.
+# component, the rest population beside an always-zero slot), the same kernel as D2Q16.  Stated
+# bounds of the same origin as above.
 D2Q9_FP32_CASES = D2Q9_CASES + [
     # several 8 x 32 tiles in both directions with ragged last ones
     ("vortices_40x100", 40, 100, False, "weno5", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 4, umax=0.08)),
     ("filter_sound_64x128", 64, 128, True, "weno5", False, lambda nt, np_: inputs.sound_legendre(nt, np_, 3)),
 ]
 D2Q9_FP32_TOL = {
-    # name: (tol_rho, tol_drho, tol_u)
-    "vortices_16x32": (1e-7, 2e-4, 2e-5),
-    "shock_T_24x16": (1e-5, 1e-5, 1e-4),
-    "filter_u3_komissarov_16x32": (1e-7, 2e-4, 2e-5),
-    "ragged_13x10_u2": (1e-7, 2e-4, 2e-5),
+    # name: (tol_rho, tol_drho, tol_u), about 5x the worst GB300 value
+    "vortices_16x32": (3e-8, 6e-6, 3e-6),
+    "shock_T_24x16": (4e-7, 7e-7, 2e-6),
+    "filter_u3_komissarov_16x32": (1e-7, 2e-5, 1e-5),
+    "ragged_13x10_u2": (4e-8, 4e-6, 5e-6),
     # (its density deviation is ~3e-5 of rho: drho measures FP32 rounding on a tiny scale)
-    "vortices_40x100": (1e-7, 1e-3, 2e-5),
-    "filter_sound_64x128": (1e-7, 2e-4, 2e-5),
+    "vortices_40x100": (5e-8, 2e-3, 3e-6),
+    "filter_sound_64x128": (1e-9, 2e-6, 3e-6),
 }
 
 
