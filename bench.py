@@ -173,6 +173,14 @@ def qcount(args):
     return 9 if getattr(args, "velocity_set", "d2q16") == "d2q9" else 16
 
 
+def array_mb(args):
+    """Bytes of one population array (with ghost rows and columns) in MB: FP32 stores pair
+    planes of float2 (8 for D2Q16, 5 for D2Q9), FP64 one plane of doubles per population."""
+    pitch = (NP + 8 + 3) // 4 * 4
+    planes = (5 if args.velocity_set == "d2q9" else 8) if args.precision == "fp32" else qcount(args)
+    return planes * (NT + 6) * pitch * 8 / 1e6
+
+
 def workload_name(args):
     w = WORKLOAD.replace("1024x2048", f"{NT}x{NP}")
     if getattr(args, "velocity_set", "d2q16") == "d2q9":
@@ -282,7 +290,7 @@ def run_ours(args):
             "config": {"workload": workload_name(args), "n_theta": NT, "n_phi": NP,
                        "Q": qcount(args), "global_batch": world,
                        "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (three 134 MB population arrays per replica)"},
+                       "l2": f"inputs larger than L2 (three {array_mb(args):.0f} MB population arrays per replica)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": ("stage_f32_kernel" if args.precision == "fp32" else "stage_f64 kernels")
