@@ -78,8 +78,10 @@ typedef SmemT<4, 5> Smem4q3;
 static_assert(offsetof(Smem8, tile) == 0 && offsetof(Smem8, ob) % 128 == 0 && offsetof(Smem4, ob) % 128 == 0 &&
                   offsetof(Smem8q3, ob) % 128 == 0 && offsetof(Smem4q3, ob) % 128 == 0,
               "TMA operands in shared memory must be 128-byte aligned");
-// three CTAs of 8 tile rows per SM: 228 KB of shared memory per SM, 1 KB reserved per CTA
+// three CTAs of 8 tile rows per SM for D2Q16, four for D2Q9 (whose registers are capped at 64 to
+// let four fit): 228 KB of shared memory per SM, 1 KB reserved per CTA
 static_assert(3 * (sizeof(SmemT<8>) + 128 + 1024) <= 228 * 1024, "stage tile exceeds a third of an SM's shared memory");
+static_assert(4 * (sizeof(SmemT<8, 5>) + 128 + 1024) <= 228 * 1024, "D2Q9 stage tile exceeds a quarter of an SM's shared memory");
 
 typedef float2 f2;
 
@@ -712,7 +714,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
 }
 
 template <int TY, bool LIN, int Q>
-__global__ void __launch_bounds__(TY * 32, 24 / TY) stage_f32_kernel(const __grid_constant__ CUtensorMap tm,
+__global__ void __launch_bounds__(TY * 32, (Q == 3 ? 32 : 24) / TY) stage_f32_kernel(const __grid_constant__ CUtensorMap tm,
                                                                       const __grid_constant__ CUtensorMap tmo,
                                                                       const __grid_constant__ CUtensorMap tmf,
                                                                       const RunF R, const typename VelOf<Q>::type c,
