@@ -362,7 +362,7 @@ int vlbm_lc_rollout(vlbm_lc_t *n, vlbm_t *h, int steps)
             return rc;
         }
         if (e != cudaSuccess) return lfail(n, VLBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&n->g_exec, g, 0);
+        e = cudaGraphInstantiate(&n->g_exec, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return lfail(n, VLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
         n->g_solver = h;

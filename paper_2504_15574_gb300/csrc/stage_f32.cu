@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(TY * 32, (Q == 3 ? 32 : 24) / TY) stage_f32_ke
                                                                       const __grid_constant__ CUtensorMap tmo,
                                                                       const __grid_constant__ CUtensorMap tmf,
                                                                       const RunF R, const typename VelOf<Q>::type c,
-                                                                      int stage, unsigned *err)
+                                                                      int stage, const TileRows rows, unsigned *err)
 {
     typedef SmemT<TY, (Q == 3 ? 5 : NP2)> Smem;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -728,7 +728,8 @@ __global__ void __launch_bounds__(TY * 32, (Q == 3 ? 32 : 24) / TY) stage_f32_ke
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();   // no thread may poll the barrier before its initialisation is visible
-    stage_tile<TY, LIN, Q>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, blockIdx.y, S, 0u, err);
+    const int by = rows.first + (int)blockIdx.y + ((int)blockIdx.y >= rows.split ? rows.skip : 0);
+    stage_tile<TY, LIN, Q>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, by, S, 0u, err);
 }
 
 // Persistent batch stage: CTA b takes work items b, b + gridDim.x, ...; a work item
@@ -1191,28 +1192,31 @@ int stage_f32_max_ctas_per_sm(int ty)
 template <int Q>
 static void launch_stage_q(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
                            const RunF &run, const typename VelOf<Q>::type &c, int stage, int ty, bool lin,
-                           unsigned *err, cudaStream_t s)
+                           TileRows rows, unsigned *err, cudaStream_t s)
 {
-    const dim3 grid((run.L.np + TX - 1) / TX, (run.L.nt + ty - 1) / ty);
+    if (rows.count < 0) rows = TileRows{0, (run.L.nt + ty - 1) / ty, 1 << 30, 0};
+    if (rows.count == 0) return;
+    const dim3 grid((run.L.np + TX - 1) / TX, rows.count);
     if (ty == 4) {
-        if (lin) stage_f32_kernel<4, true, Q><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
-        else stage_f32_kernel<4, false, Q><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
+        if (lin) stage_f32_kernel<4, true, Q><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, err);
+        else stage_f32_kernel<4, false, Q><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, err);
     } else {
-        if (lin) stage_f32_kernel<8, true, Q><<<grid, 256, smem_bytes<8, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
-        else stage_f32_kernel<8, false, Q><<<grid, 256, smem_bytes<8, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, err);
+        if (lin) stage_f32_kernel<8, true, Q><<<grid, 256, smem_bytes<8, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, err);
+        else stage_f32_kernel<8, false, Q><<<grid, 256, smem_bytes<8, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, err);
     }
 }
 
 void launch_stage_f32(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f, const RunF &run,
-                      const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s)
+                      const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s, TileRows rows)
 {
-    launch_stage_q<4>(tm_in, tm_out, tm_f, run, c, stage, ty, lin, err, s);
+    launch_stage_q<4>(tm_in, tm_out, tm_f, run, c, stage, ty, lin, rows, err, s);
 }
 
 void launch_stage_f32_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
-                         const RunF &run, const VelC3 &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s)
+                         const RunF &run, const VelC3 &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s,
+                         TileRows rows)
 {
-    launch_stage_q<3>(tm_in, tm_out, tm_f, run, c, stage, ty, lin, err, s);
+    launch_stage_q<3>(tm_in, tm_out, tm_f, run, c, stage, ty, lin, rows, err, s);
 }
 
 void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,

@@ -368,11 +368,54 @@ int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0, bool core = fa
     return VLBM_OK;
 }
 
+void launch_stage_f32_any(vlbm_t *h, int st, cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0})
+{
+    const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
+    const CUtensorMap &tmo = (st == 1) ? h->tmAc : (st == 2) ? h->tmBc : h->tmFc;
+    const bool lin = h->scheme != VLBM_WENO5;
+    if (h->vd.q == 3) launch_stage_f32_q3(tm, tmo, h->tmFc, h->run, h->vc3, st, h->ty, lin, h->d_flags, s, rows);
+    else launch_stage_f32(tm, tmo, h->tmFc, h->run, h->vc, st, h->ty, lin, h->d_flags, s, rows);
+}
+
+// One FP32 RK3 step with the polar filter.  The tile rows touching a filtered row and the filter
+// run on stream2, created with the highest priority so that their CTAs go first; the tile rows
+// clear of the filtered rows run on the handle's stream.  A stage's interior launch reads rows
+// that the previous stage's filter leaves alone, so it waits for that stage's two launches only
+// and runs beside the filter; the polar launch waits for the previous stage's interior launch
+// and, in stream order, its polar launch and filter.  The step starts and ends joined on the
+// handle's stream.
+void enqueue_split_step(vlbm_t *h)
+{
+    cudaStream_t s = h->stream, s2 = h->stream2;
+    const int tiles_y = (h->nt + h->ty - 1) / h->ty, nb = h->band_hi - h->band_lo;
+    const TileRows inner{h->band_lo, nb, 1 << 30, 0};
+    const TileRows polar{0, tiles_y - nb, h->band_lo, nb};
+    cudaEvent_t *evP = h->evs + 1, *evI = h->evs + 4;
+    cudaEventRecord(h->evs[0], s);
+    cudaStreamWaitEvent(s2, h->evs[0], 0);
+    for (int st = 1; st <= 3; ++st) {
+        void *out = (st == 1) ? h->A : (st == 2) ? h->B : h->F;
+        if (st > 1) cudaStreamWaitEvent(s2, evI[st - 2], 0);
+        launch_stage_f32_any(h, st, s2, polar);
+        cudaEventRecord(evP[st - 1], s2);
+        launch_filter_f32((float2 *)out, h->L, h->vd.q, h->d_frows, h->d_fblocks, h->nfrows, s2);
+        if (st > 1) cudaStreamWaitEvent(s, evP[st - 2], 0);
+        launch_stage_f32_any(h, st, s, inner);
+        cudaEventRecord(evI[st - 1], s);
+    }
+    cudaEventRecord(h->evs[0], s2);
+    cudaStreamWaitEvent(s, h->evs[0], 0);
+}
+
 // Enqueues one RK3 step (all stages, filters, budget) on the handle's stream.  With
 // stage_only = 1..3, only that stage; part 1 launches its stage kernel alone, part 2
 // its polar filter alone (part 0: both).
 void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
 {
+    if (h->prec == VLBM_FP32 && !stage_only && h->band_hi > h->band_lo) {
+        enqueue_split_step(h);
+        return;
+    }
     cudaStream_t s = h->stream;
     const size_t pole_per = (size_t)2 * NK * h->np;
     for (int st = 1; st <= 3; ++st) {
@@ -405,13 +448,7 @@ void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
             if (part != 2) launch_stage_f64(p, s);
             if (h->nfrows && part != 1) launch_filter_f64((double *)out, h->L, h->d_frows, h->d_fblocks, h->nfrows, s);
         } else {
-            const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
-            const CUtensorMap &tmo = (st == 1) ? h->tmAc : (st == 2) ? h->tmBc : h->tmFc;
-            const bool lin = h->scheme != VLBM_WENO5;
-            if (part != 2) {
-                if (h->vd.q == 3) launch_stage_f32_q3(tm, tmo, h->tmFc, h->run, h->vc3, st, h->ty, lin, h->d_flags, s);
-                else launch_stage_f32(tm, tmo, h->tmFc, h->run, h->vc, st, h->ty, lin, h->d_flags, s);
-            }
+            if (part != 2) launch_stage_f32_any(h, st, s);
             if (h->nfrows && part != 1)
                 launch_filter_f32((float2 *)out, h->L, h->vd.q, h->d_frows, h->d_fblocks, h->nfrows, s);
         }
@@ -422,7 +459,7 @@ void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
 
 int kernels_per_step(const vlbm_t *h)
 {
-    int n = 3 + (h->nfrows ? 3 : 0);
+    int n = 3 + (h->nfrows ? 3 : 0) + (h->band_hi > h->band_lo ? 3 : 0);
     if (h->prec == VLBM_FP64) n += 3 * 2 + 1;   // two face kernels per stage and the pole budget
     return n;
 }
@@ -434,7 +471,8 @@ int build_graph(vlbm_t *h, int nsteps, cudaGraphExec_t *exec)
     for (int q = 0; q < nsteps; ++q) enqueue_step(h);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return fail(h, VLBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(exec, g, 0);
+    // (node priorities: the kernels captured from the high-priority stream keep it)
+    e = cudaGraphInstantiate(exec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, VLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     return VLBM_OK;
@@ -618,6 +656,30 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
         if (h->nfrows &&
             ((rc = upload(h, &h->d_frows, rows.data(), rows.size())) || (rc = upload(h, &h->d_fblocks, blocks.data(), blocks.size()))))
             return bail(rc);
+        // FP32: the tile rows whose stage input box (GR rows beyond the tile on each side)
+        // touches no filtered row
+        int iN = -1, iS = n_theta;
+        for (int i : rows) {
+            if (2 * i < n_theta) iN = std::max(iN, i);
+            else iS = std::min(iS, i);
+        }
+        const int ty = h->ty, lo = (iN + GR + 1 + ty - 1) / ty;
+        const int hi = (iS - GR - ty >= 0) ? (iS - GR - ty) / ty + 1 : 0;
+        if (h->prec == VLBM_FP32 && h->nfrows && hi > lo) {
+            h->band_lo = lo;
+            h->band_hi = hi;
+            int least = 0, greatest = 0;
+            cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            if (cudaStreamCreateWithPriority(&h->stream2, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+                h->err = "cudaStreamCreate failed";
+                return bail(VLBM_ERR_CUDA);
+            }
+            for (cudaEvent_t &e : h->evs)
+                if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                    h->err = "cudaEventCreate failed";
+                    return bail(VLBM_ERR_CUDA);
+                }
+        }
     }
     if ((rc = dalloc(h, (void **)&h->d_pole, sizeof(double) * 3 * 2 * NK * (size_t)n_phi)) ||
         (rc = dalloc(h, (void **)&h->d_budget, sizeof(double) * 8)) ||
@@ -878,6 +940,9 @@ void vlbm_destroy(vlbm_t *h)
     if (h->h_flags) cudaFreeHost(h->h_flags);
     for (int q = 0; q < 4; ++q)
         if (h->ev[q]) cudaEventDestroy(h->ev[q]);
+    for (cudaEvent_t e : h->evs)
+        if (e) cudaEventDestroy(e);
+    if (h->stream2) cudaStreamDestroy(h->stream2);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

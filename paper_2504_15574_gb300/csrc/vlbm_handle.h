@@ -53,6 +53,13 @@ struct vlbm {
     double mass0 = 0.0;
     std::string err;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // FP32 path with the polar filter: the stage launches of the tile rows touching a filtered
+    // row and the filter run on stream2 (highest priority), beside the launches of the tile rows
+    // [band_lo, band_hi), clear of every filtered row, on stream; evs order the two (none when
+    // the band is empty)
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t evs[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int band_lo = 0, band_hi = 0;
     double prof_ms[3] = {0, 0, 0};
     size_t dev_bytes = 0;
 };

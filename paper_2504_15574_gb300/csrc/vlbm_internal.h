@@ -156,11 +156,16 @@ constexpr int F32_TILE_ROWS_MAX = 8;
 // x 8) of the stage input array; tm_out and tm_f are the tile-core maps (F32_TILE_COLS x ty x 8)
 // of the stage output array and of F (the step's start values).
 cudaError_t prepare_stage_f32();   // sets the kernels' dynamic shared-memory limits
+// The tile rows one stage launch covers: count rows of tiles from tile row `first`, skipping
+// `skip` tile rows after the first `split` of them (count < 0: every tile row of the grid).
+struct TileRows { int first, count, split, skip; };
 void launch_stage_f32(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f, const RunF &run,
-                      const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s);
+                      const VelC &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s,
+                      TileRows rows = TileRows{0, -1, 0, 0});
 // The same for D2Q9 (five pair planes; tensor maps of depth 5).
 void launch_stage_f32_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
-                         const RunF &run, const VelC3 &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s);
+                         const RunF &run, const VelC3 &c, int stage, int ty, bool lin, unsigned *err, cudaStream_t s,
+                         TileRows rows = TileRows{0, -1, 0, 0});
 // One stage of a batch: a persistent grid of `ctas` CTAs walks `ntiles` work items
 // (run, tile) over the run table `runs` (device) and tensor maps `tms` (device, [run][6]: the box
 // maps of F, A, B, then the tile-core maps of F, A, B).

@@ -60,6 +60,10 @@ CASES = {
                                    lambda: inputs.gaussian_vortices(64, 8192, 6), 3, True),
     # polar filter blocks wider than one 2048-column window (b = 8192 on the pole rows)
     "filter_window_blocks_8x32768": (8, 32768, 0.01, 0.01, lambda: inputs.gaussian_vortices(8, 32768, 7), 3, True),
+    # filtered rows 0-9 and 118-127: the FP32 stage runs its tile rows 2-13 on a second stream
+    # beside the filter of the polar rows
+    "filter_bands_128x256": (128, 256, 0.01, literal_dt(128) / 2, lambda: inputs.gaussian_vortices(128, 256, 7), 40,
+                             True),
     # the sound wave about an axis in the equatorial plane (App. C, alpha = -pi/2): flow across the
     # pole rows and the phi seam
     "sound_rotated_32x32": (32, 32, 2e-3, 1e-4, lambda: inputs.sound_parabola_rotated(32, 32, 1e-3), 200, False),
@@ -190,6 +194,7 @@ FP32_CASES = {
     "wide_row_8x4096": (1e-7, 1e-3, 5e-7),
     "filter_wide_blocks_64x8192": (1e-7, 2e-4, 2e-5),
     "filter_window_blocks_8x32768": (1e-7, 2e-4, 2e-5),
+    "filter_bands_128x256": (1e-7, 2e-4, 2e-5),
     "sound_rotated_32x32": (1e-8, 5e-5, 2e-5),
     "riemann_256x1": (2.5e-5, 3e-5, 2e-5),
     "riemann_rotated_32x32": (4e-6, 1e-5, 1e-5),
