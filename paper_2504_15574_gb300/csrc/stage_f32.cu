@@ -13,10 +13,14 @@
 // Layout of vlbm_internal.h with 8 pair planes of float2 elements.  Pole ghost
 // rows hold -dg of the mirrored pair with swapped members (the ghost's sine is
 // negative, Eq. bcs_theta maps v -> -v); ghost columns hold periodic images.
+// D2Q9 (App. A.1, template parameter Q = 3) runs through the same code in five pair
+// planes: four pairs whose members share the sign of each nonzero velocity component
+// and the rest population beside an always-zero slot (slot maps in vlbm_internal.h);
+// its pole images go member by member to the slot of the mirrored population.
 //
 // One stage (Sec. 3.7) of L[f] (Eq. Lf) per kernel launch, for a tile of TY x TX
-// cells and all 16 populations:
-//   1. one TMA box (8 pair planes x (TY+6) x (TX+8) float2) into shared memory;
+// cells and all populations (a launch may cover a subset of the tile rows):
+//   1. one TMA box (all pair planes x (TY+6) x (TX+10) float2) into shared memory;
 //   2. phi faces and theta faces of all pairs, each face once, into shared memory
 //      (WENO-5, Eqs. fluxes_W5, WENO5_delta, WENO5_sigma).  On dg the phi weights
 //      use the regulariser 4 eps s^2 k^2 (the WENO weights are invariant under
@@ -30,7 +34,7 @@
 //      weight terms use the full forms.  Each phi face row is walked by a few threads
 //      that keep the columns' differences in registers.  Face values carry the
 //      stage's dt share and their metric factor;
-//   3. per cell: moments (Eq. f_moments_sum), equilibrium (Eq. feq_Q=4), BGK,
+//   3. per cell: moments (Eq. f_moments_sum), equilibrium (Eq. feq_Q=4, or feq_Q=3), BGK,
 //      force through K^H / Ktilde^H (Eq. df), flux differences and the stage
 //      combination, all on dg (the operator commutes with the row factor), then
 //      the store of the cell and of its ghost images.
