@@ -50,7 +50,7 @@ extern "C" {
 /* Return codes. */
 #define VLBM_OK               0
 #define VLBM_ERR_ARG         -1  /* invalid argument (size, pointer, parameter) */
-#define VLBM_ERR_UNSUPPORTED -2  /* valid request this build does not implement */
+#define VLBM_ERR_UNSUPPORTED -2  /* valid request the library does not implement */
 #define VLBM_ERR_CUDA        -3  /* CUDA error, including no device and out of memory */
 #define VLBM_ERR_NONFINITE   -4  /* the non-finite guard found a NaN/Inf population */
 #define VLBM_ERR_TIMEOUT     -5  /* a bounded device-side wait gave up */
