@@ -1192,6 +1192,16 @@ int vlbm_batch_create(int nruns, const int *n_theta, const int *n_phi, const dou
             vlbm_batch_destroy(b);
             return bfail(nullptr, rc, m);
         }
+        // a member's steps are the batch's launches: it needs no stream of its own for the
+        // split filter schedule
+        for (cudaEvent_t &e : h->evs)
+            if (e) {
+                cudaEventDestroy(e);
+                e = nullptr;
+            }
+        if (h->stream2) cudaStreamDestroy(h->stream2);
+        h->stream2 = nullptr;
+        h->band_lo = h->band_hi = 0;
         b->runs.push_back(h);
     }
     if (cudaMalloc(&b->d_flags, 4 * sizeof(unsigned)) != cudaSuccess ||
