@@ -244,6 +244,9 @@ D2Q9_FP32_CASES = D2Q9_CASES + [
     # several 8 x 32 tiles in both directions with ragged last ones
     ("vortices_40x100", 40, 100, False, "weno5", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 4, umax=0.08)),
     ("filter_sound_64x128", 64, 128, True, "weno5", False, lambda nt, np_: inputs.sound_legendre(nt, np_, 3)),
+    # the smallest grid (every cell a pole-row cell beside a ghost column) and the axisymmetric one
+    ("minimum_6x2", 6, 2, False, "weno5", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 8, umax=0.1)),
+    ("sound_1d_64x1", 64, 1, False, "weno5", False, lambda nt, np_: inputs.sound_parabola(nt, np_, 1e-3)),
 ]
 D2Q9_FP32_TOL = {
     # name: (tol_rho, tol_drho, tol_u), about 5x the worst GB300 value
@@ -254,6 +257,8 @@ D2Q9_FP32_TOL = {
     # (its density deviation is ~3e-5 of rho: drho measures FP32 rounding on a tiny scale)
     "vortices_40x100": (5e-8, 2e-3, 3e-6),
     "filter_sound_64x128": (1e-9, 2e-6, 3e-6),
+    "minimum_6x2": (1e-7, 1e-5, 8e-6),
+    "sound_1d_64x1": (5e-9, 3e-6, 6e-6),
 }
 
 
