@@ -30,7 +30,7 @@ import numpy as np
 
 from . import inputs, vlbm
 
-VMAX = math.sqrt(3 + math.sqrt(6))
+VMAX = {"d2q16": math.sqrt(3 + math.sqrt(6)), "d2q9": math.sqrt(3.0)}
 
 
 def closed_form(kind, ell, tau, t):
@@ -42,14 +42,14 @@ def closed_form(kind, ell, tau, t):
     return math.exp(-tau * (lam2 - 2) * t)
 
 
-def run(kind, ell, tau, literal, precision, nt=256, np_=512, steps=10000, reports=10):
-    dth = math.pi / nt
+def run(kind, ell, tau, literal, precision, nt=256, np_=512, steps=10000, reports=10, velocity_set="d2q16"):
+    dth, vmax = math.pi / nt, VMAX[velocity_set]
     if literal:
-        dt = 0.25 * dth / VMAX
+        dt = 0.25 * dth / vmax
     else:
-        dt = min(0.25 * min(dth, math.sin(dth / 2) * 2 * math.pi / np_) / VMAX, tau)
+        dt = min(0.25 * min(dth, math.sin(dth / 2) * 2 * math.pi / np_) / vmax, tau)
     start = inputs.sound_legendre(nt, np_, ell) if kind == "sound" else inputs.shear_legendre(nt, np_, ell)
-    s = vlbm.Solver(nt, np_, tau, dt, precision=precision, polar_filter=literal)
+    s = vlbm.Solver(nt, np_, tau, dt, precision=precision, polar_filter=literal, velocity_set=velocity_set)
     s.init_moments(*start[:3])
     T, _ = inputs.cell_centres(nt, np_)
     w = np.sin(T)[:, None] * np.ones((1, np_))
@@ -76,6 +76,7 @@ def run(kind, ell, tau, literal, precision, nt=256, np_=512, steps=10000, report
         rows.append((t, a, cf))
     s.close()
     return {"kind": kind, "ell": ell, "tau": tau, "dt": dt, "filter": literal, "precision": precision,
+            "velocity_set": velocity_set,
             "t_end": done * dt, "a_end": rows[-1][1], "closed_end": rows[-1][2], "max_abs_dev": worst,
             "mlups": nt * np_ * done / dev_s / 1e6}
 
@@ -84,9 +85,23 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--velocity-set", default="d2q16", choices=["d2q16", "d2q9"],
+                    help="d2q9: the FP32 runs only")
     a = ap.parse_args(argv)
     vlbm.load()
     res = []
+    if a.velocity_set == "d2q9":
+        for literal in (False, True):
+            for tau in (0.005, 0.02):
+                for kind in ("sound", "shear"):
+                    for ell in (1, 2, 3, 4):
+                        r = run(kind, ell, tau, literal, "fp32", steps=a.steps, velocity_set="d2q9")
+                        res.append(r)
+                        print(json.dumps(r), flush=True)
+        if a.out:
+            with open(a.out, "w") as fh:
+                json.dump(res, fh)
+        return
     for literal in (False, True):
         for tau in (0.005, 0.02):
             for kind in ("sound", "shear"):
