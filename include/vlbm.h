@@ -158,12 +158,16 @@ VLBM_API int vlbm_max_stable_dt(int n_theta, int n_phi, int velocity_set, double
                        double *out);
 
 /* Per-kernel time of the stages, and the number of kernels one step launches.
- * vlbm_profile_step runs n steps launching each stage kernel and each polar
- * filter individually between CUDA events on the handle's stream and stores,
- * in ms_per_stage[0..2], the mean device time of stage kernel 1, 2, 3 and in
+ * vlbm_profile_step runs n steps launching each stage kernel (over the whole grid)
+ * and each polar filter individually between CUDA events on the handle's stream and
+ * stores, in ms_per_stage[0..2], the mean device time of stage kernel 1, 2, 3 and in
  * ms_per_stage[3..5] that of the polar filter after stage 1, 2, 3 (0 when the
- * filter is off); ms_per_stage (6 doubles) may be NULL.  Returns the launch
- * count per step in *launches (may be NULL). */
+ * filter is off); ms_per_stage (6 doubles) may be NULL.  The steps give the same
+ * state as vlbm_step's.  Returns in *launches (may be NULL) the launch count of one
+ * vlbm_step step: 3 stage launches, plus 3 filters with the filter on, plus (FP32
+ * with the filter, when some tile rows are clear of every filtered row) 3 more
+ * stage launches, the stage then being split into polar and interior tile rows
+ * that run on two streams. */
 VLBM_API int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches);
 
 /* Bytes of device memory the handle holds. */
