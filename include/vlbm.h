@@ -28,7 +28,10 @@
  *     the call returns (the library copies, it keeps no host pointer).  The
  *     library owns its device memory and the handle.
  *   - Threading: a handle is used by one host thread at a time.  Its kernels
- *     run on the stream given in vlbm_options (NULL: a stream the handle owns).
+ *     run on the stream given in vlbm_options (NULL: a stream the handle owns);
+ *     an FP32 step with the polar filter also forks onto a second stream the
+ *     handle owns (highest priority) and joins back before the step ends, so all
+ *     work is ordered on the handle's stream as seen by the caller.
  *   - Errors: every int-returning call returns VLBM_OK or a negative code;
  *     vlbm_last_error() gives a message.  A NULL handle or buffer is VLBM_ERR_ARG.
  */
