@@ -247,6 +247,8 @@ D2Q9_FP32_CASES = D2Q9_CASES + [
     # the smallest grid (every cell a pole-row cell beside a ghost column) and the axisymmetric one
     ("minimum_6x2", 6, 2, False, "weno5", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 8, umax=0.1)),
     ("sound_1d_64x1", 64, 1, False, "weno5", False, lambda nt, np_: inputs.sound_parabola(nt, np_, 1e-3)),
+    ("u1_vortices_24x48", 24, 48, False, "u1", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 10, umax=0.08)),
+    ("u3_filter_32x64", 32, 64, True, "u3", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 11, umax=0.08)),
 ]
 D2Q9_FP32_TOL = {
     # name: (tol_rho, tol_drho, tol_u), about 5x the worst GB300 value
@@ -259,6 +261,8 @@ D2Q9_FP32_TOL = {
     "filter_sound_64x128": (1e-9, 2e-6, 3e-6),
     "minimum_6x2": (1e-7, 1e-5, 8e-6),
     "sound_1d_64x1": (5e-9, 3e-6, 6e-6),
+    "u1_vortices_24x48": (3e-8, 9e-6, 3e-6),
+    "u3_filter_32x64": (4e-8, 1.1e-5, 5e-6),
 }
 
 
