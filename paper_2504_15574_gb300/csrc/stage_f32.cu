@@ -41,6 +41,7 @@
 #include "vlbm_internal.h"
 
 #include <cstddef>
+#include <cstring>
 #include <algorithm>
 #include <cmath>
 
@@ -52,10 +53,33 @@ constexpr int TX = F32_TILE_COLS;
 constexpr int NP2 = 8;                 // population pairs of D2Q16
 constexpr int SC = F32_BOX_COLS;       // tile columns in shared memory (TX + 2 GC + 2)
 
-// NPP pair planes: 8 for D2Q16, 5 for D2Q9
-template <int TY, int NPP = NP2>
+// Per-tile tables of one stage, for the tile's rows: the sine differences (FP64-derived) and the
+// upwind schemes' 1/sin and interface sines at the padded tile rows, the per-row constants and the
+// reference tendency times the stage's dt share of the cell rows.  The batch kernel fills them per
+// thread from its run's arrays; the standalone solver keeps one per tile row and stage in device
+// memory (built on the host with the same FP32 roundings) and copies it with the tile's box.
+template <int TY, int NPP>
+struct __align__(16) TabT {
+    float2 ds2[TY + 2 * GR];    // (dsin, dsin) at the tile rows
+    float2 d2s2[TY + 2 * GR];   // (d2sin, d2sin) at the tile rows
+    float2 isp2[TY + 2 * GR];   // upwind schemes, Komissarov: (1/sin, 1/sin) at the tile rows
+    float2 sf2[TY + 1];         // upwind schemes, Komissarov: interface sines of the face rows
+    float2 rr[TY][NPP];         // dte s rref per cell row and pair
+    RowF rowc[TY];
+};
+
+// The stage input's box of one tile: all pair planes x (TY + 6) rows x SC columns (a TMA
+// destination: 128-byte aligned, and its size a multiple of 128 so that consecutive boxes are too)
+template <int TY, int NPP>
+struct __align__(128) BoxT {
+    float2 v[NPP][TY + 2 * GR][SC];
+};
+
+// NPP pair planes: 8 for D2Q16, 5 for D2Q9.  NBUF box buffers and NTAB table buffers: one each for
+// the one-tile CTAs; the persistent stage kernel alternates two table buffers.
+template <int TY, int NPP = NP2, int NBUF = 1, int NTAB = NBUF>
 struct __align__(128) SmemT {
-    float2 tile[NPP][TY + 2 * GR][SC];  // TMA destination (must stay first)
+    BoxT<TY, NPP> tile[NBUF];           // TMA destinations (must stay first)
     float2 adv[NPP][TY][TX + 1];        // per cell and pair: dte (flux differences + s rref); row
                                         // stride TX+1 keeps the phi walkers' stores conflict-free
     __align__(128) float2 ob[NPP][TY][TX];   // stages 2, 3: the tile of F (TMA load); then the output
@@ -64,14 +88,10 @@ struct __align__(128) SmemT {
     // D2Q9 with 8 warps: the theta walkers' flux differences of the four flux pairs, written
     // beside adv by other warps than the phi walkers' (one element otherwise)
     float2 advT[NPP == 5 ? 4 : 1][NPP == 5 ? TY : 1][NPP == 5 ? TX + 1 : 1];
-    float2 ds2[TY + 2 * GR];            // (dsin, dsin) at the tile rows
-    float2 d2s2[TY + 2 * GR];           // (d2sin, d2sin) at the tile rows
-    float2 rr[TY][NPP];                 // dte s rref per cell row and pair
-    float2 isp2[TY + 2 * GR];           // upwind schemes, Komissarov: (1/sin, 1/sin) at the tile rows
-    float2 sf2[TY + 1];                 // upwind schemes, Komissarov: interface sines of the face rows
-    RowF rowc[TY];
+    TabT<TY, NPP> tab[NTAB];
     RunF run;                           // batch kernel: this tile's run
-    unsigned long long bar;
+    unsigned long long bar[NBUF];       // box (and tables; one-tile CTAs: also the tile of F)
+    unsigned long long barF;            // persistent kernel: the tile of F
 };
 
 // TMA shared-memory operands start on 128-byte boundaries (the dynamic buffer itself is 128-aligned)
@@ -79,13 +99,23 @@ typedef SmemT<8> Smem8;
 typedef SmemT<4> Smem4;
 typedef SmemT<8, 5> Smem8q3;
 typedef SmemT<4, 5> Smem4q3;
+typedef SmemT<8, NP2, 1, 2> SmemQ8;
+typedef SmemT<8, 5, 1, 2> SmemQ8q3;
 static_assert(offsetof(Smem8, tile) == 0 && offsetof(Smem8, ob) % 128 == 0 && offsetof(Smem4, ob) % 128 == 0 &&
-                  offsetof(Smem8q3, ob) % 128 == 0 && offsetof(Smem4q3, ob) % 128 == 0,
+                  offsetof(Smem8q3, ob) % 128 == 0 && offsetof(Smem4q3, ob) % 128 == 0 &&
+                  offsetof(SmemQ8, ob) % 128 == 0 && offsetof(SmemQ8q3, ob) % 128 == 0 &&
+                  sizeof(BoxT<8, NP2>) % 128 == 0 && sizeof(BoxT<8, 5>) % 128 == 0,
               "TMA operands in shared memory must be 128-byte aligned");
+static_assert(offsetof(SmemQ8, tab) % 16 == 0 && offsetof(SmemQ8q3, tab) % 16 == 0 &&
+                  sizeof(TabT<8, NP2>) % 16 == 0 && sizeof(TabT<8, 5>) % 16 == 0,
+              "bulk copies of the tile tables need 16-byte alignment and sizes");
 // three CTAs of 8 tile rows per SM for D2Q16, four for D2Q9 (whose registers are capped at 64 to
 // let four fit): 228 KB of shared memory per SM, 1 KB reserved per CTA
 static_assert(3 * (sizeof(SmemT<8>) + 128 + 1024) <= 228 * 1024, "stage tile exceeds a third of an SM's shared memory");
 static_assert(4 * (sizeof(SmemT<8, 5>) + 128 + 1024) <= 228 * 1024, "D2Q9 stage tile exceeds a quarter of an SM's shared memory");
+// persistent stage kernel with one box buffer: three CTAs per SM
+static_assert(3 * (sizeof(SmemQ8) + 128 + 1024) <= 228 * 1024 && 3 * (sizeof(SmemQ8q3) + 128 + 1024) <= 228 * 1024,
+              "persistent single-buffer tiles");
 
 typedef float2 f2;
 
@@ -319,21 +349,43 @@ __device__ __forceinline__ f2 pair_vph(const VelC3 &c, int q) { return c.vb2[q];
 __device__ __forceinline__ int pair_phdir(const VelC &c, int q) { return c.vphi2[q & 3].x > 0.0f ? 1 : -1; }
 __device__ __forceinline__ int pair_phdir(const VelC3 &c, int q) { return c.phdir[q]; }
 
-// One stage of one TY x TX tile of one run.  The mbarrier is initialised by the
-// caller; `parity` is the phase this tile's load completes.  Returns false if
-// the tile load did not arrive in time (every thread of the CTA agrees).  tm is the
-// stage input's box map (42 x (TY+6) x 8); tmo and tmf are the tile-core maps (32 x TY
-// x 8) of the stage output and of the step's start values F: stages 2 and 3 load their
-// tile of F through tmf into the staging buffer with the input box, and tiles clear of
-// every ghost image store their output from there with one TMA store through tmo.
-// LIN: the upwind schemes U1-U3 (Eq. fluxes_U1-3, optionally with the Komissarov theta flux)
-// instead of WENO-5.
-// Q: the velocity set (4: D2Q16, 3: D2Q9 in five pairs).
-template <int TY, bool LIN, int Q>
-__device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q>::type &c, int stage,
-                                           const CUtensorMap *tm, const CUtensorMap *tmo, const CUtensorMap *tmf,
-                                           int bx, int by, SmemT<TY, (Q == 3 ? 5 : NP2)> &S, unsigned parity,
-                                           unsigned *err)
+// The stage's dt share (SSP-RK3, Sec. 3.7): the stage output is cF F0 + cG G + dte L[G] with
+// (cF, cG, dte / dt) = (0, 1, 1), (3/4, 1/4, 1/4), (1/3, 2/3, 2/3).  (The scalar constants use
+// explicit roundings: no contraction may differ between the standalone and the batch kernel, whose
+// results must agree bit for bit, nor from the host's copy of the tile tables.)
+__device__ __forceinline__ float stage_dte(int stage, float dt)
+{
+    return (stage == 1) ? dt : __fmul_rn((stage == 2) ? 0.25f : (2.0f / 3.0f), dt);
+}
+
+// The tile tables of tile row i0 filled by the CTA's threads from the run's arrays (the batch kernel).
+template <int TY, int NPP, bool LIN>
+__device__ __forceinline__ void fill_tab(TabT<TY, NPP> &T, const RunF &R, int i0, float dte)
+{
+    constexpr int SR = TY + 2 * GR;
+    int t = threadIdx.x;
+    if (t < SR) {
+        T.ds2[t] = splat(R.dsin[i0 + t]);
+    } else if ((t -= SR) < SR) {
+        T.d2s2[t] = splat(R.d2sin[i0 + t]);
+    } else if ((t -= SR) < TY) {
+        T.rowc[t] = R.row[min(i0 + t, R.L.nt - 1)];
+    } else if ((t -= TY) < TY * NPP) {
+        const int ry = t / NPP, q = t - (t / NPP) * NPP;
+        T.rr[ry][q] = mul2(R.rref[(size_t)min(i0 + ry, R.L.nt - 1) * NPP + q], splat(dte));
+    } else if (LIN && (t -= TY * NPP) < SR) {
+        T.isp2[t] = splat(R.isp[i0 + t]);
+    } else if (LIN && (t -= SR) < TY + 1) {
+        T.sf2[t] = splat(R.sfc[i0 + t]);
+    }
+}
+
+// Face phase of one stage of one TY x TX tile (q0 = bx TX, i0 = by TY) whose input box and
+// tables are in tile buffer b of S: the phi and theta faces of every pair into S.adv (and S.advT).
+// Ends without a barrier.
+template <int TY, bool LIN, int Q, class Sm>
+__device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q>::type &c, float dte, Sm &S,
+                                           int b, int tb)
 {
     constexpr int NPQ = (Q == 3) ? 5 : NP2;   // pair planes
     constexpr int NFQ = (Q == 3) ? 4 : NP2;   // pairs with fluxes (D2Q9's fifth: the rest population)
@@ -345,71 +397,12 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
     // pairs' phi faces on warps 0-3 and their theta faces on warps 4-7, into advT
     constexpr bool SPLIT = (Q == 3) && (NW == 2 * NFQ);
     constexpr int FSTEP = SPLIT ? NFQ : NW;
-    constexpr unsigned TILE_BYTES = NPQ * SR * SC * sizeof(float2);
-    constexpr unsigned CORE_BYTES = NPQ * TY * TX * sizeof(float2);
+    (void)SR; (void)NFQ; (void)FSTEP; (void)SPLIT;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int q0 = bx * TX;
-    const int i0 = by * TY;
-    const Layout L = R.L;
-    const float2 *in = (stage == 1) ? R.F : (stage == 2) ? R.A : R.B;
-    float2 *out = (stage == 1) ? R.A : (stage == 2) ? R.B : R.F;
-    (void)in;
-    // SSP-RK3 (Sec. 3.7): the stage output is cF F0 + cG G + dte L[G] with (cF, cG, dte / dt) =
-    // (0, 1, 1), (3/4, 1/4, 1/4), (1/3, 2/3, 2/3)
-    // (the scalar constants use explicit roundings: no contraction may differ between the
-    // standalone and the batch kernel, whose results must agree bit for bit)
-    const float dte = (stage == 1) ? R.dt : __fmul_rn((stage == 2) ? 0.25f : (2.0f / 3.0f), R.dt);
-
-    if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.bar)),
-                     "r"(stage == 1 ? TILE_BYTES : TILE_BYTES + CORE_BYTES)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.tile[0][0][0])),
-            "l"(reinterpret_cast<unsigned long long>(tm)), "r"(q0), "r"(i0), "r"(0), "r"(smem_u32(&S.bar))
-            : "memory");
-        // stages 2, 3: the tile's step start values F into the staging buffer (parts outside
-        // the array read as zero and belong to no cell)
-        if (stage != 1)
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.ob[0][0][0])),
-                "l"(reinterpret_cast<unsigned long long>(tmf)), "r"(q0 + GC), "r"(i0 + GR), "r"(0),
-                "r"(smem_u32(&S.bar))
-                : "memory");
-    }
-    // per-tile tables while the tile is in flight
-    {
-        int t = tid;
-        if (t < SR) {
-            S.ds2[t] = splat(R.dsin[i0 + t]);
-        } else if ((t -= SR) < SR) {
-            S.d2s2[t] = splat(R.d2sin[i0 + t]);
-        } else if ((t -= SR) < TY) {
-            S.rowc[t] = R.row[min(i0 + t, L.nt - 1)];
-        } else if ((t -= TY) < TY * NPQ) {
-            const int ry = t / NPQ, q = t - (t / NPQ) * NPQ;
-            S.rr[ry][q] = mul2(R.rref[(size_t)min(i0 + ry, L.nt - 1) * NPQ + q], splat(dte));
-        } else if (LIN && (t -= TY * NPQ) < SR) {
-            S.isp2[t] = splat(R.isp[i0 + t]);
-        } else if (LIN && (t -= SR) < TY + 1) {
-            S.sf2[t] = splat(R.sfc[i0 + t]);
-        }
-    }
-    // (the barrier of the load wait also publishes the tables; the caller has made the
-    // mbarrier's initialisation visible to every thread before this tile began)
-    const bool ok = __syncthreads_and(wait_phase(&S.bar, parity, 1000000000ull));
-    if (!ok) {
-        // the copy did not complete within 1 s: flag it, give it one more bounded
-        // second to land in this CTA's shared memory, then leave
-        if (tid == 0) atomicOr(err, 1u);
-        wait_phase(&S.bar, parity, 1000000000ull);
-        return false;
-    }
-
+    (void)tid;
+    const BoxT<TY, NPQ> &box = S.tile[b];
+    const TabT<TY, NPQ> &tab = S.tab[tb];
     // Every face value below is premultiplied by the stage's dt share dte and by the
     // metric factor of its difference (1/(R sin dphi) for phi, 1/(R dtheta) for the
     // WENO-5 and plain upwind theta fluxes).  Each walker turns its consecutive faces into
@@ -421,32 +414,32 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
     {
         constexpr int NSEG = 32 / TY, SEG = TX / NSEG;
         const int r = lane % TY, sg = lane / TY, f0 = sg * SEG;
-        const f2 sp = splat(__fmul_rn(S.rowc[r].inv_dph, dte));
+        const f2 sp = splat(__fmul_rn(tab.rowc[r].inv_dph, dte));
         if constexpr (LIN) {
             const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
 #pragma unroll 1
             for (int q = warp; q < (SPLIT ? (warp < NFQ ? NFQ : 0) : NFQ); q += FSTEP) {
                 const f2 vb = mul2(pair_vph(c, q), sp);
-                const f2 *row = &S.tile[q][r + GR][0];
+                const f2 *row = &box.v[q][r + GR][0];
                 f2 *out = &S.adv[q][r][f0];
                 const int dir = pair_phdir(c, q);
-                if (dir > 0) phi_march_lin<SEG + 1, 1>(row, f0, l0, l1, l2, vb, S.rr[r][q], out);
-                else if (dir < 0) phi_march_lin<SEG + 1, -1>(row, f0, l0, l1, l2, vb, S.rr[r][q], out);
+                if (dir > 0) phi_march_lin<SEG + 1, 1>(row, f0, l0, l1, l2, vb, tab.rr[r][q], out);
+                else if (dir < 0) phi_march_lin<SEG + 1, -1>(row, f0, l0, l1, l2, vb, tab.rr[r][q], out);
                 else
-                    for (int j = 0; j < SEG; ++j) out[j] = S.rr[r][q];
+                    for (int j = 0; j < SEG; ++j) out[j] = tab.rr[r][q];
             }
         } else {
-            const f2 E = splat(S.rowc[r].ephi);
+            const f2 E = splat(tab.rowc[r].ephi);
 #pragma unroll 1
             for (int q = warp; q < (SPLIT ? (warp < NFQ ? NFQ : 0) : NFQ); q += FSTEP) {
                 const f2 vb = mul2(pair_vph(c, q), sp);
-                const f2 *row = &S.tile[q][r + GR][0];
+                const f2 *row = &box.v[q][r + GR][0];
                 f2 *out = &S.adv[q][r][f0];
                 const int dir = pair_phdir(c, q);
-                if (dir > 0) phi_march<SEG + 1, 1>(row, f0, E, vb, S.rr[r][q], out);
-                else if (dir < 0) phi_march<SEG + 1, -1>(row, f0, E, vb, S.rr[r][q], out);
+                if (dir > 0) phi_march<SEG + 1, 1>(row, f0, E, vb, tab.rr[r][q], out);
+                else if (dir < 0) phi_march<SEG + 1, -1>(row, f0, E, vb, tab.rr[r][q], out);
                 else
-                    for (int j = 0; j < SEG; ++j) out[j] = S.rr[r][q];
+                    for (int j = 0; j < SEG; ++j) out[j] = tab.rr[r][q];
             }
         }
     }
@@ -464,19 +457,19 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
         for (int q = SPLIT ? warp - NFQ : warp; q >= 0 && q < NFQ; q += FSTEP) {
             const bool g = pair_thpos(c, q);
             const f2 vt = mul2(pair_vth(c, q), splat(dte));
-            const f2 *col = &S.tile[q][0][lane + GC];
+            const f2 *col = &box.v[q][0][lane + GC];
             f2 x[SR], prev;
 #pragma unroll
-            for (int r = 0; r < SR; ++r) x[r] = kom ? mul2(col[r * SC], S.isp2[r]) : col[r * SC];
+            for (int r = 0; r < SR; ++r) x[r] = kom ? mul2(col[r * SC], tab.isp2[r]) : col[r * SC];
 #pragma unroll
             for (int fy = 0; fy <= TY; ++fy) {
                 // face fy lies between tile rows fy-1 and fy (x index = tile row + GR)
                 const f2 rec = g ? fma2(l0, x[fy + 1], fma2(l1, x[fy + 2], mul2(l2, x[fy + 3])))
                                  : fma2(l0, x[fy + 4], fma2(l1, x[fy + 3], mul2(l2, x[fy + 2])));
-                const f2 fl = kom ? mul2(mul2(vt, rec), S.sf2[fy]) : mul2(vt, rec);
+                const f2 fl = kom ? mul2(mul2(vt, rec), tab.sf2[fy]) : mul2(vt, rec);
                 if (fy > 0) {
                     const int cy = fy - 1;
-                    const f2 idth = splat(kom ? S.rowc[cy].kth : R.inv_dth);
+                    const f2 idth = splat(kom ? tab.rowc[cy].kth : R.inv_dth);
                     if constexpr (SPLIT) S.advT[q][cy][lane] = mul2(sub2(prev, fl), idth);
                     else S.adv[q][cy][lane] = fma2(sub2(prev, fl), idth, S.adv[q][cy][lane]);
                 }
@@ -500,7 +493,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
             const bool g = pair_thpos(c, q);
             const f2 wr = R.wr[q];
             const f2 vt = mul2(pair_vth(c, q), splat(__fmul_rn(dte, R.inv_dth)));
-            const f2 *col = &S.tile[q][0][lane + GC];
+            const f2 *col = &box.v[q][0][lane + GC];
             // values are produced one row ahead of their first use (face fy needs rows up to fy+5)
             f2 x[SR], dd[SR], dfu[SR], D2[SR], Qa[SR], prev, dcarry;
 #pragma unroll
@@ -508,11 +501,11 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
 #pragma unroll
             for (int r = 1; r < 5; ++r) {
                 dd[r] = sub2(x[r], x[r - 1]);
-                dfu[r] = fma2(wr, S.ds2[r], dd[r]);
+                dfu[r] = fma2(wr, tab.ds2[r], dd[r]);
             }
 #pragma unroll
             for (int r = 1; r < 4; ++r) {
-                D2[r] = fma2(wr, S.d2s2[r], sub2(dd[r + 1], dd[r]));
+                D2[r] = fma2(wr, tab.d2s2[r], sub2(dd[r + 1], dd[r]));
                 Qa[r] = fma2(mul2(D2[r], c133), D2[r], E);
             }
 #pragma unroll
@@ -521,8 +514,8 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
                     const int r = fy + 5;
                     x[r] = col[r * SC];
                     dd[r] = sub2(x[r], x[r - 1]);
-                    dfu[r] = fma2(wr, S.ds2[r], dd[r]);
-                    D2[r - 1] = fma2(wr, S.d2s2[r - 1], sub2(dd[r], dd[r - 1]));
+                    dfu[r] = fma2(wr, tab.ds2[r], dd[r]);
+                    D2[r - 1] = fma2(wr, tab.d2s2[r - 1], sub2(dd[r], dd[r - 1]));
                     Qa[r - 1] = fma2(mul2(D2[r - 1], c133), D2[r - 1], E);
                 }
                 f2 B1, B2, B3, Q1, Q2, Q3, d12, d23, p2;
@@ -558,12 +551,51 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
             }
         }
     }
-    __syncthreads();
+}
 
+// The stage input of this thread's cell (warp = cell row, lane = column) from tile buffer b.
+template <int TY, int NPQ, class Sm>
+__device__ __forceinline__ void load_cell_g(const Sm &S, int b, f2 *G)
+{
+    const int cy = threadIdx.x >> 5, cx = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < NPQ; ++q) G[q] = S.tile[b].v[q][cy + GR][cx + GC];
+}
+
+// Cell phase of one stage of one tile after the face phase (and a barrier): per cell the
+// moments, equilibrium, force, BGK, flux differences and stage combination, then the store of
+// the tile (one TMA store through tmo from S.ob for tiles clear of every ghost image, with a
+// barrier inside; per cell with its images otherwise).  In stages 2 and 3, S.ob holds the tile
+// of F when this begins.  Threads of cells outside the grid return early.
+template <int TY, bool LIN, int Q, class Sm>
+__device__ __forceinline__ void tile_cells(const RunF &R, const typename VelOf<Q>::type &c, int stage, float dte,
+                                           const CUtensorMap *tmo, int bx, int by, Sm &S, int b, int tb,
+                                           const f2 *Gin)
+{
+    constexpr int NPQ = (Q == 3) ? 5 : NP2;   // pair planes
+    constexpr int NFQ = (Q == 3) ? 4 : NP2;   // pairs with fluxes (D2Q9's fifth: the rest population)
+    constexpr int SR = TY + 2 * GR;
+    constexpr int NT = TY * 32;
+    constexpr int NW = NT / 32;
+    // warps of the face phases: D2Q16 and 4-warp D2Q9 tiles walk a pair's phi faces and then its
+    // theta faces on one warp (pairs warp, warp + NW, ...); 8-warp D2Q9 tiles walk the four
+    // pairs' phi faces on warps 0-3 and their theta faces on warps 4-7, into advT
+    constexpr bool SPLIT = (Q == 3) && (NW == 2 * NFQ);
+    constexpr int FSTEP = SPLIT ? NFQ : NW;
+    (void)SR; (void)NFQ; (void)FSTEP; (void)SPLIT;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    (void)tid;
+    const int q0 = bx * TX;
+    const int i0 = by * TY;
+    const Layout L = R.L;
+    float2 *out = (stage == 1) ? R.A : (stage == 2) ? R.B : R.F;
+    const BoxT<TY, NPQ> &box = S.tile[b];
+    const TabT<TY, NPQ> &tab = S.tab[tb];
     // ---- one cell per thread: warp = cell row, lane = column
     const int cy = warp, cx = lane;
     const int i = i0 + cy, j = q0 + cx;
-    if (i >= L.nt || j >= L.np) return true;
+    if (i >= L.nt || j >= L.np) return;
     // the step's start values of this cell (stages 2, 3; the slots this thread's output
     // overwrites below)
     f2 F0[NPQ];
@@ -571,10 +603,11 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
 #pragma unroll
         for (int q = 0; q < NPQ; ++q) F0[q] = S.ob[q][cy][cx];
     }
-    const RowF rc = S.rowc[cy];
+    const RowF rc = tab.rowc[cy];
     f2 G[NPQ];
 #pragma unroll
-    for (int q = 0; q < NPQ; ++q) G[q] = S.tile[q][cy + GR][cx + GC];
+    for (int q = 0; q < NPQ; ++q) G[q] = Gin[q];
+    (void)box;
     // moments of delta f = dg / (k s)
     f2 sn, sjt, sjp;
     if constexpr (Q == 4) {
@@ -678,7 +711,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
         // dte times: flux differences + s rref - force + s feq_dev / tau (the rest population
         // of D2Q9 has no flux: its share is the reference tendency alone)
         f2 a;
-        if (q >= NFQ) a = S.rr[cy][q];
+        if (q >= NFQ) a = tab.rr[cy][q];
         else if constexpr (SPLIT) a = add2(S.adv[q][cy][cx], S.advT[q][cy][cx]);
         else a = S.adv[q][cy][cx];
         a = fma2(ncot, fb, a);
@@ -704,7 +737,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
         }
-        return true;
+        return;
     }
     const bool plain = (i >= GR && i < L.nt - GR && j >= GC && j < L.np - GC);
     if (plain) {
@@ -714,6 +747,69 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
 #pragma unroll
         for (int q = 0; q < NPQ; ++q) store_images(out, L, Q, q, i, j, o[q]);
     }
+}
+
+// One stage of one TY x TX tile of one run.  The mbarrier is initialised by the
+// caller; `parity` is the phase this tile's load completes.  Returns false if
+// the tile load did not arrive in time (every thread of the CTA agrees).  tm is the
+// stage input's box map (42 x (TY+6) x 8); tmo and tmf are the tile-core maps (32 x TY
+// x 8) of the stage output and of the step's start values F: stages 2 and 3 load their
+// tile of F through tmf into the staging buffer with the input box, and tiles clear of
+// every ghost image store their output from there with one TMA store through tmo.
+// LIN: the upwind schemes U1-U3 (Eq. fluxes_U1-3, optionally with the Komissarov theta flux)
+// instead of WENO-5.
+// Q: the velocity set (4: D2Q16, 3: D2Q9 in five pairs).
+template <int TY, bool LIN, int Q>
+__device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q>::type &c, int stage,
+                                           const CUtensorMap *tm, const CUtensorMap *tmo, const CUtensorMap *tmf,
+                                           int bx, int by, SmemT<TY, (Q == 3 ? 5 : NP2)> &S, unsigned parity,
+                                           unsigned *err)
+{
+    constexpr int NPQ = (Q == 3) ? 5 : NP2;
+    constexpr unsigned TILE_BYTES = NPQ * (TY + 2 * GR) * SC * sizeof(float2);
+    constexpr unsigned CORE_BYTES = NPQ * TY * TX * sizeof(float2);
+    const int tid = threadIdx.x;
+    const int q0 = bx * TX;
+    const int i0 = by * TY;
+    const float dte = stage_dte(stage, R.dt);
+
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.bar[0])),
+                     "r"(stage == 1 ? TILE_BYTES : TILE_BYTES + CORE_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.tile[0].v[0][0][0])),
+            "l"(reinterpret_cast<unsigned long long>(tm)), "r"(q0), "r"(i0), "r"(0), "r"(smem_u32(&S.bar[0]))
+            : "memory");
+        // stages 2, 3: the tile's step start values F into the staging buffer (parts outside
+        // the array read as zero and belong to no cell)
+        if (stage != 1)
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.ob[0][0][0])),
+                "l"(reinterpret_cast<unsigned long long>(tmf)), "r"(q0 + GC), "r"(i0 + GR), "r"(0),
+                "r"(smem_u32(&S.bar[0]))
+                : "memory");
+    }
+    // per-tile tables while the tile is in flight
+    fill_tab<TY, NPQ, LIN>(S.tab[0], R, i0, dte);
+    // (the barrier of the load wait also publishes the tables; the caller has made the
+    // mbarrier's initialisation visible to every thread before this tile began)
+    const bool ok = __syncthreads_and(wait_phase(&S.bar[0], parity, 1000000000ull));
+    if (!ok) {
+        // the copy did not complete within 1 s: flag it, give it one more bounded
+        // second to land in this CTA's shared memory, then leave
+        if (tid == 0) atomicOr(err, 1u);
+        wait_phase(&S.bar[0], parity, 1000000000ull);
+        return false;
+    }
+    tile_faces<TY, LIN, Q>(R, c, dte, S, 0, 0);
+    __syncthreads();
+    f2 G[NPQ];
+    load_cell_g<TY, NPQ>(S, 0, G);
+    tile_cells<TY, LIN, Q>(R, c, stage, dte, tmo, bx, by, S, 0, 0, G);
     return true;
 }
 
@@ -728,12 +824,129 @@ __global__ void __launch_bounds__(TY * 32, (Q == 3 ? 32 : 24) / TY) stage_f32_ke
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar[0])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();   // no thread may poll the barrier before its initialisation is visible
     const int by = rows.first + (int)blockIdx.y + ((int)blockIdx.y >= rows.split ? rows.skip : 0);
     stage_tile<TY, LIN, Q>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, by, S, 0u, err);
+}
+
+// Persistent stage kernel (8 tile rows, three CTAs per SM): CTA b takes the launch's tiles
+// b, b + G, b + 2G, ... (G = gridDim.x, tiles numbered row-major over the launch's tile rows) so
+// that the copies of its next tile are in flight while it computes one: right after the face phase
+// the cell phase takes its cells' stage inputs into registers, and the box and tables of the next
+// tile are issued into the freed box buffer (the tables alternate between two buffers) while this
+// tile's cells are computed and stored; the tile of F (stages 2, 3) of the next tile is issued as
+// soon as this tile's output has left the staging buffer.  tabs holds this stage's tables of every
+// tile row of the grid.  A copy that does not arrive within 1 s sets *err; the CTA then waits
+// (bounded) for its other copies in flight and leaves.
+template <bool LIN, int Q>
+__global__ void __launch_bounds__(256, 3)
+    stage_f32_persist_kernel(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmo,
+                             const __grid_constant__ CUtensorMap tmf, const RunF R,
+                             const typename VelOf<Q>::type c, int stage, const TileRows rows,
+                             const TabT<8, (Q == 3 ? 5 : NP2)> *tabs, unsigned *err)
+{
+    constexpr int TY = 8;
+    constexpr int NPQ = (Q == 3) ? 5 : NP2;
+    typedef SmemT<TY, NPQ, 1, 2> Smem;
+    constexpr unsigned BOX_BYTES = NPQ * (TY + 2 * GR) * SC * sizeof(float2);
+    constexpr unsigned TAB_BYTES = sizeof(TabT<TY, NPQ>);
+    constexpr unsigned CORE_BYTES = NPQ * TY * TX * sizeof(float2);
+    constexpr unsigned long long LIMIT_NS = 1000000000ull;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int ntx = (R.L.np + TX - 1) / TX;
+    const int total = ntx * rows.count;
+    const int G = (int)gridDim.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.barF)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();   // no thread may poll a barrier before its initialisation is visible
+    // launch tile t -> (bx, by)
+    auto tile_xy = [&](int t, int &bx, int &by) {
+        const int ly = t / ntx;
+        bx = t - ly * ntx;
+        by = rows.first + ly + (ly >= rows.split ? rows.skip : 0);
+    };
+    // (issued by thread 0) the box of tile t and its tables into table buffer tb
+    auto issue_box = [&](int t, int tb) {
+        int bx, by;
+        tile_xy(t, bx, by);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.bar[0])),
+                     "r"(BOX_BYTES + TAB_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.tile[0].v[0][0][0])),
+            "l"(reinterpret_cast<unsigned long long>(&tm)), "r"(bx * TX), "r"(by * TY), "r"(0),
+            "r"(smem_u32(&S.bar[0]))
+            : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(&S.tab[tb])),
+                     "l"(reinterpret_cast<unsigned long long>(tabs + by)), "r"(TAB_BYTES), "r"(smem_u32(&S.bar[0]))
+                     : "memory");
+    };
+    // (issued by thread 0, stages 2 and 3) the tile of F of tile t into the staging buffer
+    auto issue_f = [&](int t) {
+        int bx, by;
+        tile_xy(t, bx, by);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&S.barF)),
+                     "r"(CORE_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(&S.ob[0][0][0])),
+            "l"(reinterpret_cast<unsigned long long>(&tmf)), "r"(bx * TX + GC), "r"(by * TY + GR), "r"(0),
+            "r"(smem_u32(&S.barF))
+            : "memory");
+    };
+    int t = (int)blockIdx.x;
+    if (tid == 0 && t < total) {
+        issue_box(t, 0);
+        if (stage != 1) issue_f(t);
+    }
+    const float dte = stage_dte(stage, R.dt);
+    for (int k = 0; t < total; ++k, t += G) {
+        const int tb = k & 1;
+        const unsigned par = k & 1;   // phase of tile k on the box barrier and on the F barrier
+        const bool box_ok = __syncthreads_and(wait_phase(&S.bar[0], par, LIMIT_NS));
+        bool ok = box_ok, next_box = false;
+        if (ok) {
+            int bx, by;
+            tile_xy(t, bx, by);
+            tile_faces<TY, LIN, Q>(R, c, dte, S, 0, tb);
+            __syncthreads();
+            f2 Gc[NPQ];
+            load_cell_g<TY, NPQ>(S, 0, Gc);
+            __syncthreads();   // the box buffer is free: the next tile's copies go now
+            next_box = t + G < total;
+            if (tid == 0 && next_box) issue_box(t + G, tb ^ 1);
+            if (stage != 1) ok = __syncthreads_and(wait_phase(&S.barF, par, LIMIT_NS));
+            if (ok) {
+                tile_cells<TY, LIN, Q>(R, c, stage, dte, &tmo, bx, by, S, 0, tb, Gc);
+                __syncthreads();   // this tile's tables and the staging buffer are free
+                if (tid == 0 && stage != 1 && t + G < total) issue_f(t + G);
+                continue;
+            }
+        }
+        // a copy did not arrive within 1 s: flag it, give this CTA's copies still in flight one
+        // more bounded second each to land in its shared memory, then leave
+        if (tid == 0) {
+            atomicOr(err, 1u);
+            if (!box_ok) wait_phase(&S.bar[0], par, LIMIT_NS);
+            if (next_box) wait_phase(&S.bar[0], par ^ 1, LIMIT_NS);
+            if (stage != 1) wait_phase(&S.barF, par, LIMIT_NS);
+        }
+        __syncthreads();
+        return;
+    }
 }
 
 // Persistent batch stage: CTA b takes work items b, b + gridDim.x, ...; a work item
@@ -748,7 +961,7 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SmemT<TY> &S = *reinterpret_cast<SmemT<TY> *>(smem_raw);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar[0])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     unsigned parity = 0;
@@ -1164,6 +1377,39 @@ __global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *
 template <int TY, int Q = 4>
 static size_t smem_bytes() { return sizeof(SmemT<TY, (Q == 3 ? 5 : NP2)>) + 128; }
 
+// Shared memory of the persistent stage kernel
+template <int Q>
+static size_t persist_smem() { return sizeof(SmemT<8, (Q == 3 ? 5 : NP2), 1, 2>) + 128; }
+
+// Resident CTAs of one persistent stage-kernel instance on the current device (CTAs per SM x SMs),
+// looked up once per device (first from prepare_stage_f32, outside any stream capture)
+template <bool LIN, int Q>
+static int persist_grid()
+{
+    static int dev_cached = -1, grid = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev != dev_cached) {
+        int per = 0, nsm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, stage_f32_persist_kernel<LIN, Q>, 256,
+                                                          persist_smem<Q>()) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        grid = per * nsm;
+        dev_cached = dev;
+    }
+    return grid;
+}
+
+template <bool LIN, int Q>
+static cudaError_t prepare_persist()
+{
+    const cudaError_t e = cudaFuncSetAttribute(stage_f32_persist_kernel<LIN, Q>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persist_smem<Q>());
+    if (e) return e;
+    return persist_grid<LIN, Q>() > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
 template <int TY, bool LIN>
 cudaError_t prepare_one()
 {
@@ -1180,9 +1426,56 @@ cudaError_t prepare_one()
 cudaError_t prepare_stage_f32()
 {
     cudaError_t e;
-    if ((e = prepare_one<8, false>()) || (e = prepare_one<4, false>()) || (e = prepare_one<8, true>()))
+    if ((e = prepare_one<8, false>()) || (e = prepare_one<4, false>()) || (e = prepare_one<8, true>()) ||
+        (e = prepare_one<4, true>()))
         return e;
-    return prepare_one<4, true>();
+    if ((e = prepare_persist<false, 4>()) || (e = prepare_persist<true, 4>()) || (e = prepare_persist<false, 3>()))
+        return e;
+    return prepare_persist<true, 3>();
+}
+
+size_t f32_tile_table_bytes(int q) { return q == 3 ? sizeof(TabT<8, 5>) : sizeof(TabT<8, NP2>); }
+
+// The persistent kernel's tile tables, built on the host with the roundings of fill_tab (the
+// products rref * dte are single FP32 multiplications on both sides, dte as stage_dte):
+// [stage 1..3][tile row] for 8-row tiles.
+template <int NPP>
+static void fill_tile_tables_q(int nt, float dt, const float *ds, const float *d2s, const float *isp,
+                               const float *sfc, const RowF *row, const float2 *rref, unsigned char *out)
+{
+    constexpr int TY = 8, SR = TY + 2 * GR;
+    const int tiles_y = (nt + TY - 1) / TY;
+    TabT<TY, NPP> *T = reinterpret_cast<TabT<TY, NPP> *>(out);
+    const float two3 = 2.0f / 3.0f, quarter = 0.25f;
+    for (int stage = 1; stage <= 3; ++stage) {
+        const float dte = (stage == 1) ? dt : ((stage == 2) ? quarter : two3) * dt;
+        for (int by = 0; by < tiles_y; ++by) {
+            TabT<TY, NPP> &t = T[(stage - 1) * tiles_y + by];
+            memset(&t, 0, sizeof t);
+            const int i0 = by * TY;
+            for (int r = 0; r < SR; ++r) {
+                t.ds2[r] = make_float2(ds[i0 + r], ds[i0 + r]);
+                t.d2s2[r] = make_float2(d2s[i0 + r], d2s[i0 + r]);
+                t.isp2[r] = make_float2(isp[i0 + r], isp[i0 + r]);
+            }
+            for (int r = 0; r < TY + 1; ++r) t.sf2[r] = make_float2(sfc[i0 + r], sfc[i0 + r]);
+            for (int r = 0; r < TY; ++r) {
+                const int i = std::min(i0 + r, nt - 1);
+                t.rowc[r] = row[i];
+                for (int p = 0; p < NPP; ++p) {
+                    const float2 v = rref[(size_t)i * NPP + p];
+                    t.rr[r][p] = make_float2(v.x * dte, v.y * dte);
+                }
+            }
+        }
+    }
+}
+
+void f32_fill_tile_tables(int q, int nt, float dt, const float *ds, const float *d2s, const float *isp,
+                          const float *sfc, const RowF *row, const float2 *rref, unsigned char *out)
+{
+    if (q == 3) fill_tile_tables_q<5>(nt, dt, ds, d2s, isp, sfc, row, rref, out);
+    else fill_tile_tables_q<NP2>(nt, dt, ds, d2s, isp, sfc, row, rref, out);
 }
 
 int stage_f32_max_ctas_per_sm(int ty)
@@ -1191,6 +1484,41 @@ int stage_f32_max_ctas_per_sm(int ty)
     if (ty == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<4, false>, 128, smem_bytes<4>());
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<8, false>, 256, smem_bytes<8>());
     return n;
+}
+
+template <int Q>
+static void launch_persist_q(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
+                             const RunF &run, const typename VelOf<Q>::type &c, int stage, bool lin, TileRows rows,
+                             const void *tabs, unsigned *err, cudaStream_t s)
+{
+    if (rows.count < 0) rows = TileRows{0, (run.L.nt + 7) / 8, 1 << 30, 0};
+    if (rows.count == 0) return;
+    typedef TabT<8, (Q == 3 ? 5 : NP2)> Tab;
+    const int tiles_y = (run.L.nt + 7) / 8;
+    const Tab *tab = reinterpret_cast<const Tab *>(tabs) + (size_t)(stage - 1) * tiles_y;
+    const int total = ((run.L.np + TX - 1) / TX) * rows.count;
+    const size_t smem = persist_smem<Q>();
+    if (lin) {
+        const int grid = std::min(total, persist_grid<true, Q>());
+        stage_f32_persist_kernel<true, Q><<<grid, 256, smem, s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, tab, err);
+    } else {
+        const int grid = std::min(total, persist_grid<false, Q>());
+        stage_f32_persist_kernel<false, Q><<<grid, 256, smem, s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, tab, err);
+    }
+}
+
+void launch_stage_f32_persist(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
+                              const RunF &run, const VelC &c, int stage, bool lin, const void *tabs, unsigned *err,
+                              cudaStream_t s, TileRows rows)
+{
+    launch_persist_q<4>(tm_in, tm_out, tm_f, run, c, stage, lin, rows, tabs, err, s);
+}
+
+void launch_stage_f32_persist_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
+                                 const RunF &run, const VelC3 &c, int stage, bool lin, const void *tabs,
+                                 unsigned *err, cudaStream_t s, TileRows rows)
+{
+    launch_persist_q<3>(tm_in, tm_out, tm_f, run, c, stage, lin, rows, tabs, err, s);
 }
 
 template <int Q>

@@ -336,6 +336,14 @@ int build_f32_tables(vlbm_t *h)
     run.e_theta = (float)(4.0 * h->eps * ks * ks);
     run.inv_dth = (float)(1.0 / (h->R * (M_PI / h->nt)));
     run.tiles_x = (h->np + F32_TILE_COLS - 1) / F32_TILE_COLS;
+    // the persistent stage kernel's per-tile-row tables of the three stages (8-row tiles)
+    if (h->ty == 8) {
+        const size_t per = f32_tile_table_bytes(q), n = 3 * (size_t)((nt + 7) / 8) * per;
+        std::vector<unsigned char> tabs(n);
+        f32_fill_tile_tables(q, nt, run.dt, ds.data(), d2s.data(), isp.data(), sfc.data(), row.data(), rref.data(),
+                             tabs.data());
+        if ((rc = upload(h, &h->d_tabs, tabs.data(), tabs.size()))) return rc;
+    }
     return VLBM_OK;
 }
 
@@ -373,6 +381,16 @@ void launch_stage_f32_any(vlbm_t *h, int st, cudaStream_t s, TileRows rows = Til
     const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
     const CUtensorMap &tmo = (st == 1) ? h->tmAc : (st == 2) ? h->tmBc : h->tmFc;
     const bool lin = h->scheme != VLBM_WENO5;
+    if (h->ty == 8 && lin) {
+        // the upwind schemes: the persistent kernel, whose next tile's copies are in flight during
+        // the cell phase (their lighter faces leave the one-tile kernel's loads exposed; for WENO-5
+        // the one-tile kernel with three resident CTAs per SM measured faster)
+        if (h->vd.q == 3)
+            launch_stage_f32_persist_q3(tm, tmo, h->tmFc, h->run, h->vc3, st, lin, h->d_tabs, h->d_flags, s, rows);
+        else
+            launch_stage_f32_persist(tm, tmo, h->tmFc, h->run, h->vc, st, lin, h->d_tabs, h->d_flags, s, rows);
+        return;
+    }
     if (h->vd.q == 3) launch_stage_f32_q3(tm, tmo, h->tmFc, h->run, h->vc3, st, h->ty, lin, h->d_flags, s, rows);
     else launch_stage_f32(tm, tmo, h->tmFc, h->run, h->vc, st, h->ty, lin, h->d_flags, s, rows);
 }
@@ -932,7 +950,7 @@ void vlbm_destroy(vlbm_t *h)
     drop_graphs(h);
     void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_sin_f, h->d_cos_f, h->d_isp,
                     h->d_sfc, h->d_ft, h->d_fp,
-                    h->d_rref, h->d_dsin, h->d_d2sin,
+                    h->d_rref, h->d_dsin, h->d_d2sin, h->d_tabs,
                     h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
                     h->d_part, h->d_diag, h->d_flags};
     for (void *p : bufs)

@@ -32,6 +32,7 @@ struct vlbm {
     float2 *d_rref = nullptr;
     float *d_dsin = nullptr, *d_d2sin = nullptr;
     vk::RowF *d_row = nullptr;
+    unsigned char *d_tabs = nullptr;                  // persistent stage kernel: tile tables [stage][tile row]
     // polar filter
     int *d_frows = nullptr, *d_fblocks = nullptr;
     int nfrows = 0;

@@ -172,6 +172,20 @@ void launch_stage_f32_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, co
 void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
                             int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s);
 int stage_f32_max_ctas_per_sm(int ty);
+// The persistent stage kernel (8 tile rows, one CTA per resident slot, the next tile's copies in
+// flight during the cell phase):
+// its per-tile-row tables [stage 1..3][tile row] (f32_tile_table_bytes(q) each) are built on
+// the host from the run's FP32 row arrays (ds, d2s, isp: padded rows; sfc: interfaces; row, rref:
+// interior rows) and passed as tabs.
+size_t f32_tile_table_bytes(int q);
+void f32_fill_tile_tables(int q, int nt, float dt, const float *ds, const float *d2s, const float *isp,
+                          const float *sfc, const RowF *row, const float2 *rref, unsigned char *out);
+void launch_stage_f32_persist(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
+                              const RunF &run, const VelC &c, int stage, bool lin, const void *tabs, unsigned *err,
+                              cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0});
+void launch_stage_f32_persist_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
+                                 const RunF &run, const VelC3 &c, int stage, bool lin, const void *tabs,
+                                 unsigned *err, cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0});
 
 // State scale k of the FP32 storage for WENO regulariser eps: the power of two nearest
 // 1 / (2 sqrt(eps)), so that 4 eps k^2 lies in [1/2, 2].
