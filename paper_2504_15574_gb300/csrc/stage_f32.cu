@@ -89,6 +89,8 @@ struct __align__(128) SmemT {
     // beside adv by other warps than the phi walkers' (one element otherwise)
     float2 advT[NPP == 5 ? 4 : 1][NPP == 5 ? TY : 1][NPP == 5 ? TX + 1 : 1];
     TabT<TY, NPP> tab[NTAB];
+    double polew[2][NPP];               // pole faces of the tile (north, south): per pair, v_theta-weighted
+                                        // face values summed over the tile's columns
     RunF run;                           // batch kernel: this tile's run
     unsigned long long bar[NBUF];       // box (and tables; one-tile CTAs: also the tile of F)
     unsigned long long barF;            // persistent kernel: the tile of F
@@ -380,12 +382,23 @@ __device__ __forceinline__ void fill_tab(TabT<TY, NPP> &T, const RunF &R, int i0
     }
 }
 
+// A pole face's contribution of one pair and column: v_theta times the face value of each member,
+// in FP64, summed over the warp's columns (xor butterfly: every lane ends with the same sum, formed
+// in the same order); lane 0 stores it.
+__device__ __forceinline__ void pole_face(double *slot, f2 vth, f2 v, bool valid)
+{
+    double x = valid ? fma((double)vth.x, (double)v.x, (double)vth.y * (double)v.y) : 0.0;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) x += __shfl_xor_sync(0xffffffffu, x, m);
+    if ((threadIdx.x & 31) == 0) *slot = x;
+}
+
 // Face phase of one stage of one TY x TX tile (q0 = bx TX, i0 = by TY) whose input box and
 // tables are in tile buffer b of S: the phi and theta faces of every pair into S.adv (and S.advT).
 // Ends without a barrier.
 template <int TY, bool LIN, int Q, class Sm>
 __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q>::type &c, float dte, Sm &S,
-                                           int b, int tb)
+                                           int b, int tb, int bx, int by)
 {
     constexpr int NPQ = (Q == 3) ? 5 : NP2;   // pair planes
     constexpr int NFQ = (Q == 3) ? 4 : NP2;   // pairs with fluxes (D2Q9's fifth: the rest population)
@@ -445,6 +458,15 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
     }
     __syncwarp();   // the theta walker reads the cells this warp's phi walkers wrote
 
+    // Pole faces (face 0 of the first tile row, face n_theta - i0 of the last): each theta walker
+    // also records its pair's v_theta-weighted face values there for the pole mass-flux budget.
+    // The face value is the reconstruction of dg (the reference part's is added on the host side).
+    const int i0f = by * TY;
+    const bool pole_n = R.pole_part != nullptr && i0f == 0;
+    const int pole_s = (R.pole_part != nullptr && i0f + TY >= R.L.nt) ? R.L.nt - i0f : -1;
+    const bool col_ok = bx * TX + lane < R.L.np;
+    (void)pole_n; (void)pole_s; (void)col_ok;
+
     // ---- upwind schemes, theta faces: warp = pair, lane = column; the column's values are dg
     // (nodal g = sin f), or for the Komissarov flux df = dg / sin (ghost rows: the mapped
     // population's df), then v_theta times the interface sine times the reconstruction.
@@ -467,6 +489,7 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
                 const f2 rec = g ? fma2(l0, x[fy + 1], fma2(l1, x[fy + 2], mul2(l2, x[fy + 3])))
                                  : fma2(l0, x[fy + 4], fma2(l1, x[fy + 3], mul2(l2, x[fy + 2])));
                 const f2 fl = kom ? mul2(mul2(vt, rec), tab.sf2[fy]) : mul2(vt, rec);
+                if (fy == 0 ? pole_n : fy == pole_s) pole_face(&S.polew[fy == 0 ? 0 : 1][q], pair_vth(c, q), rec, col_ok);
                 if (fy > 0) {
                     const int cy = fy - 1;
                     const f2 idth = splat(kom ? tab.rowc[cy].kth : R.inv_dth);
@@ -542,6 +565,7 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
                 }
                 // P2 of the reference part is in the FP64-derived tendency rref
                 const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
+                if (fy == 0 ? pole_n : fy == pole_s) pole_face(&S.polew[fy == 0 ? 0 : 1][q], pair_vth(c, q), v, col_ok);
                 if (fy > 0) {
                     const int cy = fy - 1;
                     if constexpr (SPLIT) S.advT[q][cy][lane] = mul2(vt, sub2(prev, v));
@@ -592,6 +616,16 @@ __device__ __forceinline__ void tile_cells(const RunF &R, const typename VelOf<Q
     float2 *out = (stage == 1) ? R.A : (stage == 2) ? R.B : R.F;
     const BoxT<TY, NPQ> &box = S.tile[b];
     const TabT<TY, NPQ> &tab = S.tab[tb];
+    // the tile's pole-face partials (the face phase's per-pair sums, added in pair order)
+    if (R.pole_part != nullptr && tid == 0) {
+        const size_t base = (size_t)(stage - 1) * 2 * R.tiles_x + bx;
+        for (int pole = 0; pole < 2; ++pole) {
+            if (pole == 0 ? i0 != 0 : i0 + TY < L.nt) continue;
+            double sum = 0.0;
+            for (int q = 0; q < NFQ; ++q) sum += S.polew[pole][q];
+            R.pole_part[base + (size_t)pole * R.tiles_x] = sum;
+        }
+    }
     // ---- one cell per thread: warp = cell row, lane = column
     const int cy = warp, cx = lane;
     const int i = i0 + cy, j = q0 + cx;
@@ -805,7 +839,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
         wait_phase(&S.bar[0], parity, 1000000000ull);
         return false;
     }
-    tile_faces<TY, LIN, Q>(R, c, dte, S, 0, 0);
+    tile_faces<TY, LIN, Q>(R, c, dte, S, 0, 0, bx, by);
     __syncthreads();
     f2 G[NPQ];
     load_cell_g<TY, NPQ>(S, 0, G);
@@ -921,7 +955,7 @@ __global__ void __launch_bounds__(256, 3)
         if (ok) {
             int bx, by;
             tile_xy(t, bx, by);
-            tile_faces<TY, LIN, Q>(R, c, dte, S, 0, tb);
+            tile_faces<TY, LIN, Q>(R, c, dte, S, 0, tb, bx, by);
             __syncthreads();
             f2 Gc[NPQ];
             load_cell_g<TY, NPQ>(S, 0, Gc);
@@ -985,25 +1019,6 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const
 
 // ---- FP32 layout helpers (FP64 arithmetic) -----------------------------------------
 
-// Hermite projection of a Maxwellian at T: third order for q = 4 (Eq. feq_Q=4 at T = 1),
-// second order for q = 3 (Eq. feq_Q=3 at T = 1)
-__device__ __forceinline__ double finit64(int q, double n, double wk, double va, double vb, double ut, double up,
-                                          double T)
-{
-    const double xi = va * ut + vb * up;
-    const double u2 = ut * ut + up * up;
-    if (T == 1.0) {
-        if (q == 3) return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2));
-        return n * wk * (1.0 + xi + 0.5 * (xi * xi - u2) + xi * (xi * xi - 3.0 * u2) / 6.0);
-    }
-    const double v2 = va * va + vb * vb;
-    const double dT = T - 1.0;
-    const double second = xi * xi - u2 + dT * (v2 - 2.0);
-    if (q == 3) return n * wk * (1.0 + xi + 0.5 * second);
-    const double third = xi * (xi * xi - 3.0 * u2) + 3.0 * dT * xi * (v2 - 4.0);
-    return n * wk * (1.0 + xi + 0.5 * second + third / 6.0);
-}
-
 // population k of a velocity set of order q: the value of its slot (pair plane, member)
 __device__ __forceinline__ float slot_value(const f2 *f, const Layout &L, int q, int k, int i, int j)
 {
@@ -1012,57 +1027,87 @@ __device__ __forceinline__ float slot_value(const f2 *f, const Layout &L, int q,
     return (sl & 1) ? pr.y : pr.x;
 }
 
+// Velocity-set constants in FP32 for the conversions between moments and the stored deviations:
+// per population k (slot order of f32_pop_of_slot) v_theta, v_phi, |v|^2 and the weight.
+struct VelF { float va[NK], vb[NK], v2[NK], w[NK]; int q; };
+
+// Initial state in the FP32 deviation form (no FP64 arithmetic per population): per cell
+// dn = rho - rho_ref and T - 1 in FP64 (one subtraction each), then per population the deviation
+// f_k - w_k rho_ref = w_k (dn + n (P_k - 1)) of the Hermite projection of the Maxwellian at (rho, u,
+// T) (Eq. feq_Q=4 at T = 1: third order; with T != 1 the a^(2), a^(3) terms of the projection;
+// D2Q9, Eq. feq_Q=3: second order), P_k - 1 = xi + (xi^2 - u^2 + dT (|v|^2 - 2)) / 2
+// [+ (xi (xi^2 - 3 u^2) + 3 dT xi (|v|^2 - 4)) / 6], in FP32 on the small terms; stored as
+// k s times it.
 __global__ void init_f32_kernel(f2 *f, const Layout L, const double *rho, const double *ut, const double *up,
-                                const double *temp, const VelD c, double rho_ref, const double *sin_t, double ks)
+                                const double *temp, const VelF c, double rho_ref, const float *ks_s)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= L.np) return;
     const size_t cell = (size_t)i * L.np + j;
-    const double tt = temp ? temp[cell] : 1.0;
-    const double s = ks * sin_t[i];
+    const float dn = (float)(rho[cell] - rho_ref);
+    const float n = (float)rho[cell];
+    const float dT = temp ? (float)(temp[cell] - 1.0) : 0.0f;
+    const float u1 = (float)ut[cell], u2v = (float)up[cell];
+    const float usq = fmaf(u1, u1, u2v * u2v);
+    const float s = ks_s[i];
     const int q = c.q;
-    float v[NK];
-    for (int k = 0; k < q * q; ++k) {
-        const int a = k / q, b = k % q;
-        const double wk = c.w[a] * c.w[b];
-        v[k] = (float)(s * (finit64(q, rho[cell], wk, c.v[a], c.v[b], ut[cell], up[cell], tt) - wk * rho_ref));
+    float v[2 * NP2];
+#pragma unroll
+    for (int t = 0; t < 2 * NP2; ++t) {
+        if (t >= 2 * f32_pairs(q)) break;
+        const int k = f32_pop_of_slot(q, t);
+        if (k < 0) {
+            v[t] = 0.0f;
+            continue;
+        }
+        const float xi = fmaf(c.va[k], u1, c.vb[k] * u2v);
+        float pm1 = xi + 0.5f * fmaf(dT, c.v2[k] - 2.0f, fmaf(xi, xi, -usq));
+        if (q == 4) pm1 += (xi * fmaf(3.0f * dT, c.v2[k] - 4.0f, fmaf(xi, xi, -3.0f * usq))) * (1.0f / 6.0f);
+        v[t] = s * (c.w[k] * fmaf(n, pm1, dn));
     }
-    for (int p = 0; p < f32_pairs(q); ++p) {
-        const int k0 = f32_pop_of_slot(q, 2 * p), k1 = f32_pop_of_slot(q, 2 * p + 1);
-        f[L.at(p, i, j)] = make_float2(k0 < 0 ? 0.0f : v[k0], k1 < 0 ? 0.0f : v[k1]);
-    }
+    for (int p = 0; p < f32_pairs(q); ++p) f[L.at(p, i, j)] = make_float2(v[2 * p], v[2 * p + 1]);
 }
 
+// Moments in the FP32 deviation form: sums of the stored deviations per cell in FP32, the density
+// rho_ref + dn with the reference added in FP64, u = j / n, and T - 1 from the small terms
+// (rho_ref |u|^2 + sum_k df_k |v_k - u|^2 - 2 dn) / (2 n) (the reference state's sum_k w_k |v_k|^2 =
+// 2 T0, its odd moments vanish; Eq. f_moments_sum).
 __global__ void moments_f32_kernel(const f2 *f, const Layout L, double *rho, double *ut, double *up, double *temp,
-                                   const VelD c, double rho_ref, const double *sin_t, double ks)
+                                   const VelF c, double rho_ref, const float *inv_ks_s)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= L.np) return;
-    const int q = c.q, nk = q * q;
-    const double inv_s = 1.0 / (ks * sin_t[i]);
-    double fk[NK];
-    for (int k = 0; k < nk; ++k)
-        fk[k] = c.w[k / q] * c.w[k % q] * rho_ref + (double)slot_value(f, L, q, k, i, j) * inv_s;
-    double n = 0.0, jt = 0.0, jp = 0.0;
-    for (int k = 0; k < nk; ++k) {
-        n += fk[k];
-        jt += fk[k] * c.v[k / q];
-        jp += fk[k] * c.v[k % q];
+    const int q = c.q;
+    float sn = 0.0f, sjt = 0.0f, sjp = 0.0f, sv2 = 0.0f;
+    for (int p = 0; p < f32_pairs(q); ++p) {
+        const f2 pr = f[L.at(p, i, j)];
+        for (int m = 0; m < 2; ++m) {
+            const int k = f32_pop_of_slot(q, 2 * p + m);
+            if (k < 0) continue;
+            const float x = m ? pr.y : pr.x;
+            sn += x;
+            sjt = fmaf(c.va[k], x, sjt);
+            sjp = fmaf(c.vb[k], x, sjp);
+            sv2 = fmaf(c.v2[k], x, sv2);
+        }
     }
+    const float is = inv_ks_s[i];
+    const float dn = sn * is, jt = sjt * is, jp = sjp * is;
+    const double n = rho_ref + (double)dn;
+    const float nf = (float)n;
+    const float u1 = jt / nf, u2 = jp / nf;
     const size_t cell = (size_t)i * L.np + j;
-    const double u1 = jt / n, u2 = jp / n;
     rho[cell] = n;
     ut[cell] = u1;
     up[cell] = u2;
     if (temp) {
-        double e = 0.0;
-        for (int k = 0; k < nk; ++k) {
-            const double ct = c.v[k / q] - u1, cp = c.v[k % q] - u2;
-            e += fk[k] * (ct * ct + cp * cp);
-        }
-        temp[cell] = e / (2.0 * n);
+        const float usq = fmaf(u1, u1, u2 * u2);
+        // sum_k df_k |v_k - u|^2 = sum df |v|^2 - 2 u . j + |u|^2 dn
+        const float dev = fmaf(usq, dn, fmaf(-2.0f, fmaf(u1, jt, u2 * jp), sv2 * is));
+        const float tm1 = fmaf((float)rho_ref, usq, dev - 2.0f * dn) / (2.0f * nf);
+        temp[cell] = 1.0 + (double)tm1;
     }
 }
 
@@ -1330,46 +1375,144 @@ __global__ void __launch_bounds__(FILT_THREADS) batch_filter_f32_kernel(const Ru
 constexpr int DIAG_THREADS = 256;
 constexpr int NDIAG = 6;
 
+// FP64 diagnostics of the FP32 state, one CTA per row: the density deviations of every cell are
+// summed in FP64 (each stored value converted once; mass = area (rho_ref sin(theta) n_phi +
+// sum dg / k)), the momentum and energy sums per cell in FP32 and accumulated in FP64 with the
+// per-column cos(phi), sin(phi) tables, the non-finite check on the FP32 cell sum.  The same
+// fixed-order tree as the FP64 path combines the thread partials.
 __global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *sin_t, const double *cos_t,
-                                     const VelD c, double area, double rho_ref, double ks, double *part)
+                                     const double *cph, const double *sph, const VelF c, double area, double rho_ref,
+                                     double ks, double *part)
 {
     const int i = blockIdx.x;
-    const double st = sin_t[i], ct = cos_t[i], inv_s = 1.0 / (ks * st);
-    const double dph = 6.283185307179586476925286766559 / L.np;
-    double acc[NDIAG] = {0, 0, 0, 0, 0, 0};
+    const double st = sin_t[i], ct = cos_t[i];
+    const int q = c.q;
+    // per thread: sum dg, sum jt cos(phi), jt sin(phi), jp sin(phi), jp cos(phi), sum jt, sum e, bad
+    double a_n = 0, a_tc = 0, a_ts = 0, a_ps = 0, a_pc = 0, a_t = 0, a_e = 0, bad = 0;
     for (int j = threadIdx.x; j < L.np; j += DIAG_THREADS) {
-        double sp, cp;
-        sincos((j + 0.5) * dph, &sp, &cp);
-        double n = 0.0, jt = 0.0, jp = 0.0, e = 0.0, bad = 0.0;
-        const int q = c.q;
-        for (int k = 0; k < q * q; ++k) {
-            const double va = c.v[k / q], vb = c.v[k % q];
-            const double d = (double)slot_value(f, L, q, k, i, j);
-            if (!isfinite(d)) bad = 1.0;
-            const double fk = c.w[k / q] * c.w[k % q] * rho_ref + d * inv_s;
-            n += fk;
-            jt += fk * va;
-            jp += fk * vb;
-            e += fk * (va * va + vb * vb);
+        double sg = 0.0;
+        float sjt = 0.0f, sjp = 0.0f, se = 0.0f, chk = 0.0f;
+        for (int p = 0; p < f32_pairs(q); ++p) {
+            const f2 pr = f[L.at(p, i, j)];
+            for (int m = 0; m < 2; ++m) {
+                const int k = f32_pop_of_slot(q, 2 * p + m);
+                if (k < 0) continue;
+                const float x = m ? pr.y : pr.x;
+                sg += (double)x;
+                chk += x;
+                sjt = fmaf(c.va[k], x, sjt);
+                sjp = fmaf(c.vb[k], x, sjp);
+                se = fmaf(c.v2[k], x, se);
+            }
         }
-        const double dA = st * area;
-        acc[0] += n * dA;
-        acc[1] += (jt * ct * cp - jp * sp) * dA;
-        acc[2] += (jt * ct * sp + jp * cp) * dA;
-        acc[3] += (-jt * st) * dA;
-        acc[4] += 0.5 * e * dA;
-        acc[5] += bad;
+        if (!isfinite(chk)) bad += 1.0;
+        a_n += sg;
+        a_tc = fma((double)sjt, cph[j], a_tc);
+        a_ts = fma((double)sjt, sph[j], a_ts);
+        a_ps = fma((double)sjp, sph[j], a_ps);
+        a_pc = fma((double)sjp, cph[j], a_pc);
+        a_t += (double)sjt;
+        a_e += (double)se;
     }
-    __shared__ double red[NDIAG][DIAG_THREADS];
-    for (int qq = 0; qq < NDIAG; ++qq) red[qq][threadIdx.x] = acc[qq];
+    __shared__ double red[8][DIAG_THREADS];
+    red[0][threadIdx.x] = a_n;
+    red[1][threadIdx.x] = a_tc;
+    red[2][threadIdx.x] = a_ts;
+    red[3][threadIdx.x] = a_ps;
+    red[4][threadIdx.x] = a_pc;
+    red[5][threadIdx.x] = a_t;
+    red[6][threadIdx.x] = a_e;
+    red[7][threadIdx.x] = bad;
     __syncthreads();
     for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w)
-            for (int qq = 0; qq < NDIAG; ++qq) red[qq][threadIdx.x] += red[qq][threadIdx.x + w];
+            for (int qq = 0; qq < 8; ++qq) red[qq][threadIdx.x] += red[qq][threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0)
-        for (int qq = 0; qq < NDIAG; ++qq) part[(size_t)qq * L.nt + i] = red[qq][0];
+    if (threadIdx.x == 0) {
+        // per cell: n sin = rho_ref sin + sum dg / k; sin j = sum v dg / k; sin sum f |v|^2 =
+        // 2 rho_ref sin + sum |v|^2 dg / k (sum_k w_k = 1, sum_k w_k |v_k|^2 = 2, odd moments 0)
+        const double ik = area / ks;
+        part[0 * (size_t)L.nt + i] = fma(rho_ref * st * L.np, area, red[0][0] * ik);
+        part[1 * (size_t)L.nt + i] = (ct * red[1][0] - red[3][0]) * ik;
+        part[2 * (size_t)L.nt + i] = (ct * red[2][0] + red[4][0]) * ik;
+        part[3 * (size_t)L.nt + i] = -st * red[5][0] * ik;
+        part[4 * (size_t)L.nt + i] = 0.5 * fma(2.0 * rho_ref * st * L.np, area, red[6][0] * ik);
+        part[5 * (size_t)L.nt + i] = red[7][0];
+    }
+}
+
+// Pole mass-flux budget of one FP32 step: m_s = -R dphi (F_south - F_north) per stage with
+// F = sum over columns and populations of v_theta times the pole face's reconstruction
+// (part / k for the deviations plus the reference state's ref_n, ref_s), then
+// budget += dt (m1/6 + m2/6 + 2 m3/3) (the SSP-RK3 weights of the stages' tendencies, Sec. 3.7).
+// One warp; the tile partials are added in column order.
+__global__ void pole_budget_f32_kernel(const double *part, int ntx, double ref_n, double ref_s, double inv_ks,
+                                       double R, double dph, double dt, double *budget)
+{
+    double m[3];
+    for (int st = 0; st < 3; ++st) {
+        double fl[2];
+        for (int pole = 0; pole < 2; ++pole) {
+            const double *p = part + ((size_t)st * 2 + pole) * ntx;
+            double x = 0.0;
+            for (int b = threadIdx.x; b < ntx; b += 32) x += p[b];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            fl[pole] = x;
+        }
+        m[st] = -R * dph * ((fl[1] * inv_ks + ref_s) - (fl[0] * inv_ks + ref_n));
+    }
+    if (threadIdx.x == 0) *budget += dt * (m[0] / 6.0 + m[1] / 6.0 + 2.0 * m[2] / 3.0);
+}
+
+// Reference density of the FP32 storage on the device: the area-weighted mean of rho,
+// sum_i sin_i sum_j rho_ij / (n_phi sum_i sin_i).  Row sums (one CTA per row, fixed tree), then
+// one CTA adds the rows in order of a fixed tree; the value is the same on every call for the same rho.
+__global__ void rho_rows_kernel(const double *rho, int np, double *rowsum)
+{
+    __shared__ double red[DIAG_THREADS];
+    const int i = blockIdx.x;
+    double x = 0.0;
+    for (int j = threadIdx.x; j < np; j += DIAG_THREADS) x += rho[(size_t)i * np + j];
+    red[threadIdx.x] = x;
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) rowsum[i] = red[0];
+}
+
+__global__ void rho_mean_kernel(const double *rowsum, const double *sin_t, int nt, int np, double *out)
+{
+    __shared__ double num[DIAG_THREADS], den[DIAG_THREADS];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nt; i += DIAG_THREADS) {
+        a = fma(sin_t[i], rowsum[i], a);
+        b += sin_t[i];
+    }
+    num[threadIdx.x] = a;
+    den[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = DIAG_THREADS / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            num[threadIdx.x] += num[threadIdx.x + w];
+            den[threadIdx.x] += den[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = num[0] / (den[0] * np);
+}
+
+// rho = sum_k f_k per cell of a dense [nk][nt][np] population array
+__global__ void density_of_populations_kernel(const double *dense, int nk, size_t cells, double *rho)
+{
+    const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= cells) return;
+    double n = 0.0;
+    for (int k = 0; k < nk; ++k) n += dense[(size_t)k * cells + x];
+    rho[x] = n;
 }
 
 }  // namespace
@@ -1570,18 +1713,51 @@ double f32_state_scale(double eps)
     return std::ldexp(1.0, m);
 }
 
+// FP32 copies of a velocity set's constants per population
+static VelF vel_f32(const VelD &c)
+{
+    VelF v{};
+    v.q = c.q;
+    for (int k = 0; k < c.q * c.q; ++k) {
+        const int a = k / c.q, b = k % c.q;
+        v.va[k] = (float)c.v[a];
+        v.vb[k] = (float)c.v[b];
+        v.v2[k] = (float)(c.v[a] * c.v[a] + c.v[b] * c.v[b]);
+        v.w[k] = (float)(c.w[a] * c.w[b]);
+    }
+    return v;
+}
+
 void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,
-                     const double *T, const VelD &c, double rho_ref, const double *sin_t, double ks, cudaStream_t s)
+                     const double *T, const VelD &c, double rho_ref, const float *ks_s, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt);
-    init_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref, sin_t, ks);
+    init_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, vel_f32(c), rho_ref, ks_s);
 }
 
 void launch_moments_f32(const float2 *f, const Layout &L, double *rho, double *ut, double *up, double *T,
-                        const VelD &c, double rho_ref, const double *sin_t, double ks, cudaStream_t s)
+                        const VelD &c, double rho_ref, const float *inv_ks_s, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt);
-    moments_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, c, rho_ref, sin_t, ks);
+    moments_f32_kernel<<<grid, 128, 0, s>>>(f, L, rho, ut, up, T, vel_f32(c), rho_ref, inv_ks_s);
+}
+
+void launch_pole_budget_f32(const double *part, int ntx, double ref_n, double ref_s, double ks, double R, double dph,
+                            double dt, double *budget, cudaStream_t s)
+{
+    pole_budget_f32_kernel<<<1, 32, 0, s>>>(part, ntx, ref_n, ref_s, 1.0 / ks, R, dph, dt, budget);
+}
+
+void launch_rho_ref(const double *rho, int nt, int np, const double *sin_t, double *rowsum, double *out,
+                    cudaStream_t s)
+{
+    rho_rows_kernel<<<nt, DIAG_THREADS, 0, s>>>(rho, np, rowsum);
+    rho_mean_kernel<<<1, DIAG_THREADS, 0, s>>>(rowsum, sin_t, nt, np, out);
+}
+
+void launch_density_of_populations(const double *dense, int nk, size_t cells, double *rho, cudaStream_t s)
+{
+    density_of_populations_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(dense, nk, cells, rho);
 }
 
 void launch_pack_f32(const float2 *f, const Layout &L, double *dense, const VelD &c, double rho_ref,
@@ -1619,10 +1795,11 @@ void launch_filter_f32(float2 *f, const Layout &L, int q, const int *rows, const
 }
 
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,
-                            const VelD &c, double area, double rho_ref, double ks, double *part, double *out,
-                            cudaStream_t s)
+                            const double *cph, const double *sph, const VelD &c, double area, double rho_ref,
+                            double ks, double *part, double *out, cudaStream_t s)
 {
-    diag_rows_f32_kernel<<<L.nt, DIAG_THREADS, 0, s>>>(f, L, sin_t, cos_t, c, area, rho_ref, ks, part);
+    diag_rows_f32_kernel<<<L.nt, DIAG_THREADS, 0, s>>>(f, L, sin_t, cos_t, cph, sph, vel_f32(c), area, rho_ref, ks,
+                                                        part);
     launch_diag_final(part, L.nt, out, s);
 }
 

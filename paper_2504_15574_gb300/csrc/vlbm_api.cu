@@ -259,8 +259,27 @@ int build_f32_tables(vlbm_t *h)
             plin[2 * fi + dir] = (h->scheme == VLBM_WENO5) ? (-b + 5 * cc + 2 * d) / 6.0
                                                            : lin[0] * b + lin[1] * cc + lin[2] * d;
         }
+    // the reference state's pole fluxes summed over the columns: n_phi sum_k v_theta w_k rho_ref times
+    // the pole face's interface value of sin (its reconstruction per upwind direction); no flux
+    // crosses a pole with the Komissarov interface sines
+    h->pole_ref[0] = h->pole_ref[1] = 0.0;
+    if (!h->komissarov)
+        for (int k = 0; k < q * q; ++k) {
+            const int a = k / q, b = k % q;
+            const int dir = c.v[a] > 0 ? 0 : 1;
+            const double wr = c.w[a] * c.w[b] * rr;
+            h->pole_ref[0] += c.v[a] * wr * plin[2 * 0 + dir];
+            h->pole_ref[1] += c.v[a] * wr * plin[2 * (size_t)nt + dir];
+        }
+    h->pole_ref[0] *= h->np;
+    h->pole_ref[1] *= h->np;
     std::vector<RowF> row(nt);
     std::vector<float2> rref((size_t)nt * npq);
+    std::vector<float> kss(nt), ikss(nt);
+    for (int i = 0; i < nt; ++i) {
+        kss[i] = (float)(ks * h->sin_t[i]);
+        ikss[i] = (float)(1.0 / (ks * h->sin_t[i]));
+    }
     for (int i = 0; i < nt; ++i) {
         const double s = h->sin_t[i], cot = h->cos_t[i] / h->sin_t[i];
         RowF rc;
@@ -336,6 +355,9 @@ int build_f32_tables(vlbm_t *h)
     run.e_theta = (float)(4.0 * h->eps * ks * ks);
     run.inv_dth = (float)(1.0 / (h->R * (M_PI / h->nt)));
     run.tiles_x = (h->np + F32_TILE_COLS - 1) / F32_TILE_COLS;
+    run.pole_part = h->komissarov ? nullptr : h->d_pole_part;
+    if ((rc = upload(h, &h->d_kss, kss.data(), kss.size())) || (rc = upload(h, &h->d_ikss, ikss.data(), ikss.size())))
+        return rc;
     // the persistent stage kernel's per-tile-row tables of the three stages (8-row tiles)
     if (h->ty == 8) {
         const size_t per = f32_tile_table_bytes(q), n = 3 * (size_t)((nt + 7) / 8) * per;
@@ -395,6 +417,13 @@ void launch_stage_f32_any(vlbm_t *h, int st, cudaStream_t s, TileRows rows = Til
     else launch_stage_f32(tm, tmo, h->tmFc, h->run, h->vc, st, h->ty, lin, h->d_flags, s, rows);
 }
 
+// The FP32 step's pole mass-flux budget from the stage kernels' pole partials
+void launch_budget_f32(vlbm_t *h, cudaStream_t s)
+{
+    launch_pole_budget_f32(h->d_pole_part, h->run.tiles_x, h->pole_ref[0], h->pole_ref[1], h->kscale, h->R,
+                           2.0 * M_PI / h->np, h->dt, h->d_budget, s);
+}
+
 // One FP32 RK3 step with the polar filter.  The tile rows touching a filtered row and the filter
 // run on stream2, created with the highest priority so that their CTAs go first; the tile rows
 // clear of the filtered rows run on the handle's stream.  A stage's interior launch reads rows
@@ -421,6 +450,8 @@ void enqueue_split_step(vlbm_t *h)
         launch_stage_f32_any(h, st, s, inner);
         cudaEventRecord(evI[st - 1], s);
     }
+    // the step's pole budget: its partials come from the polar launches, all on stream2
+    if (h->run.pole_part) launch_budget_f32(h, s2);
     cudaEventRecord(h->evs[0], s2);
     cudaStreamWaitEvent(s, h->evs[0], 0);
 }
@@ -473,12 +504,14 @@ void enqueue_step(vlbm_t *h, int stage_only = 0, int part = 0)
     }
     if (!stage_only && h->prec == VLBM_FP64)
         launch_pole_budget(h->d_pole, h->np, h->R, 2.0 * M_PI / h->np, h->dt, h->d_budget, s);
+    if (!stage_only && h->prec == VLBM_FP32 && h->run.pole_part) launch_budget_f32(h, s);
 }
 
 int kernels_per_step(const vlbm_t *h)
 {
     int n = 3 + (h->nfrows ? 3 : 0) + (h->band_hi > h->band_lo ? 3 : 0);
     if (h->prec == VLBM_FP64) n += 3 * 2 + 1;   // two face kernels per stage and the pole budget
+    else if (h->run.pole_part) n += 1;          // the pole budget
     return n;
 }
 
@@ -519,20 +552,22 @@ int after_reset(vlbm_t *h)
     return VLBM_OK;
 }
 
-// rho_ref of the FP32 deviation storage: the option, else the area-weighted mean density.
-void choose_rho_ref(vlbm_t *h, const std::vector<double> &rho)
+// rho_ref of the FP32 deviation storage: the option, else the area-weighted mean of the density
+// field d_rho (device, [nt][np]), reduced on the device in a fixed order (the same value on every
+// call for the same field) and read back.
+int choose_rho_ref(vlbm_t *h, const double *d_rho)
 {
     if (h->rho_ref_opt > 0.0) {
         h->rho_ref = h->rho_ref_opt;
-        return;
+        return VLBM_OK;
     }
-    double num = 0.0, den = 0.0;
-    for (int i = 0; i < h->nt; ++i)
-        for (int j = 0; j < h->np; ++j) {
-            num += h->sin_t[i] * rho[(size_t)i * h->np + j];
-            den += h->sin_t[i];
-        }
-    h->rho_ref = num / den;
+    launch_rho_ref(d_rho, h->nt, h->np, h->d_sin_t, h->d_part, h->d_scalar, h->stream);
+    CK(h, cudaGetLastError());
+    double v = 0.0;
+    CK(h, cudaMemcpyAsync(&v, h->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->rho_ref = v;
+    return VLBM_OK;
 }
 
 }  // namespace
@@ -706,6 +741,20 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
         (rc = dalloc(h, (void **)&h->d_diag, sizeof(double) * 8)) ||
         (rc = dalloc(h, (void **)&h->d_flags, sizeof(unsigned) * 4)))
         return bail(rc);
+    if (h->prec == VLBM_FP32) {
+        // FP32 diagnostics: cos and sin of the column angles; the stage kernels' pole partials
+        std::vector<double> cph(n_phi), sph(n_phi);
+        const double dph = 2.0 * M_PI / n_phi;
+        for (int j = 0; j < n_phi; ++j) {
+            cph[j] = std::cos((j + 0.5) * dph);
+            sph[j] = std::sin((j + 0.5) * dph);
+        }
+        const int ntx = (n_phi + F32_TILE_COLS - 1) / F32_TILE_COLS;
+        if ((rc = upload(h, &h->d_cph, cph.data(), cph.size())) || (rc = upload(h, &h->d_sph, sph.data(), sph.size())) ||
+            (rc = dalloc(h, (void **)&h->d_pole_part, sizeof(double) * 3 * 2 * (size_t)ntx)) ||
+            (rc = dalloc(h, (void **)&h->d_scalar, sizeof(double) * 8)))
+            return bail(rc);
+    }
     if (cudaMallocHost((void **)&h->h_flags, sizeof(unsigned) * 4) != cudaSuccess) {
         h->err = "cudaMallocHost failed";
         return bail(VLBM_ERR_CUDA);
@@ -744,16 +793,16 @@ int vlbm_init_moments(vlbm_t *h, const double *rho, const double *u_theta, const
     if (h->prec == VLBM_FP64) {
         launch_init_f64((double *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->stream);
     } else {
-        std::vector<double> r(rho, rho + n);
         const double old = h->rho_ref;
-        choose_rho_ref(h, r);
+        int rc = choose_rho_ref(h, d);
+        if (rc) return rc;
         if (old != h->rho_ref || !h->d_row) {
-            int rc = build_f32_tables(h);
+            rc = build_f32_tables(h);
             if (rc) return rc;
             drop_graphs(h);
         }
         launch_init_f32((float2 *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->rho_ref,
-                        h->d_sin_t, h->kscale, h->stream);
+                        h->d_kss, h->stream);
     }
     CK(h, cudaGetLastError());
     return after_reset(h);
@@ -772,13 +821,13 @@ int vlbm_set_populations(vlbm_t *h, const double *f)
         launch_unpack_f64(h->d_dense, h->L, (double *)h->F, h->stream);
     } else {
         const size_t cells = (size_t)h->nt * h->np;
-        std::vector<double> rho(cells, 0.0);
-        for (int k = 0; k < h->L.nk; ++k)
-            for (size_t c = 0; c < cells; ++c) rho[c] += f[(size_t)k * cells + c];
+        launch_density_of_populations(h->d_dense, h->L.nk, cells, h->d_mom, h->stream);
+        CK(h, cudaGetLastError());
         const double old = h->rho_ref;
-        choose_rho_ref(h, rho);
+        int rc = choose_rho_ref(h, h->d_mom);
+        if (rc) return rc;
         if (old != h->rho_ref || !h->d_row) {
-            int rc = build_f32_tables(h);
+            rc = build_f32_tables(h);
             if (rc) return rc;
             drop_graphs(h);
         }
@@ -854,7 +903,7 @@ int vlbm_moments(vlbm_t *h, double *rho, double *u_theta, double *u_phi, double 
         launch_moments_f64((const double *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd, h->stream);
     else
         launch_moments_f32((const float2 *)h->F, h->L, d, d + n, d + 2 * n, T ? d + 3 * n : nullptr, h->vd,
-                           h->rho_ref, h->d_sin_t, h->kscale, h->stream);
+                           h->rho_ref, h->d_ikss, h->stream);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemcpyAsync(u_theta, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -872,8 +921,8 @@ int vlbm_diagnostics(vlbm_t *h, vlbm_diag *out)
         launch_diagnostics_f64((const double *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->vd, area, h->d_part, h->d_diag,
                                h->stream);
     else
-        launch_diagnostics_f32((const float2 *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->vd, area, h->rho_ref,
-                               h->kscale, h->d_part, h->d_diag, h->stream);
+        launch_diagnostics_f32((const float2 *)h->F, h->L, h->d_sin_t, h->d_cos_t, h->d_cph, h->d_sph, h->vd, area,
+                               h->rho_ref, h->kscale, h->d_part, h->d_diag, h->stream);
     CK(h, cudaGetLastError());
     double v[8];
     CK(h, cudaMemcpyAsync(v, h->d_diag, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -887,7 +936,7 @@ int vlbm_diagnostics(vlbm_t *h, vlbm_diag *out)
     out->momentum[2] = v[3];
     out->energy = v[4];
     out->nonfinite = v[5] > 0.0 ? 1 : 0;
-    out->pole_flux = (h->prec == VLBM_FP64) ? v[6] : NAN;
+    out->pole_flux = v[6];
     out->mass0 = h->mass0;
     return VLBM_OK;
 }
@@ -926,9 +975,11 @@ int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches)
             acc[st - 1] += ms;
             acc[st + 2] += h->nfrows ? mf : 0.0f;
         }
-        // the step's pole budget (FP64), outside the timed launches
+        // the step's pole budget, outside the timed launches
         if (h->prec == VLBM_FP64)
             launch_pole_budget(h->d_pole, h->np, h->R, 2.0 * M_PI / h->np, h->dt, h->d_budget, h->stream);
+        else if (h->run.pole_part)
+            launch_budget_f32(h, h->stream);
     }
     CK(h, cudaGetLastError());
     h->steps += n;
@@ -950,7 +1001,8 @@ void vlbm_destroy(vlbm_t *h)
     drop_graphs(h);
     void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_sin_f, h->d_cos_f, h->d_isp,
                     h->d_sfc, h->d_ft, h->d_fp,
-                    h->d_rref, h->d_dsin, h->d_d2sin, h->d_tabs,
+                    h->d_rref, h->d_dsin, h->d_d2sin, h->d_tabs, h->d_kss, h->d_ikss, h->d_cph, h->d_sph,
+                    h->d_pole_part, h->d_scalar,
                     h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
                     h->d_part, h->d_diag, h->d_flags};
     for (void *p : bufs)
@@ -1032,6 +1084,7 @@ int batch_refresh(vlbm_batch_t *b)
         vlbm_t *h = b->runs[r];
         if (!h->d_row) return bfail(b, VLBM_ERR_ARG, "run " + std::to_string(r) + " is not initialised");
         runs[r] = h->run;
+        runs[r].pole_part = nullptr;   // batches report no pole budget
         int rc;
         CUtensorMap *t = &tms[6 * (size_t)r];
         if ((rc = encode_map(h, t + 0, h->F, b->ty)) || (rc = encode_map(h, t + 1, h->A, b->ty)) ||

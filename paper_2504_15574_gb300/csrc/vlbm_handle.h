@@ -33,6 +33,11 @@ struct vlbm {
     float *d_dsin = nullptr, *d_d2sin = nullptr;
     vk::RowF *d_row = nullptr;
     unsigned char *d_tabs = nullptr;                  // persistent stage kernel: tile tables [stage][tile row]
+    float *d_kss = nullptr, *d_ikss = nullptr;        // k sin(theta), 1 / (k sin(theta)) per interior row (FP32)
+    double *d_cph = nullptr, *d_sph = nullptr;        // cos, sin of the column angles (FP32 diagnostics)
+    double *d_pole_part = nullptr;                    // FP32 pole partials [3][2][tiles_x] (RunF.pole_part)
+    double pole_ref[2] = {0.0, 0.0};                  // reference state's pole fluxes (north, south)
+    double *d_scalar = nullptr;                       // device scratch: the reference density
     // polar filter
     int *d_frows = nullptr, *d_fblocks = nullptr;
     int nfrows = 0;

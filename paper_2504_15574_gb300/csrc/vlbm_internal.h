@@ -85,6 +85,10 @@ struct RunF {
     int komissarov;            // theta flux in the Komissarov form (upwind schemes)
     const float *isp;          // [nt + 2GR + 8] 1/sin at padded row pr (negative at ghost rows)
     const float *sfc;          // [nt + 1 + 8] sin(fi dtheta) of theta interface fi (0 at both poles)
+    // pole mass-flux budget (NULL: not recorded): per stage, pole (north, south) and tile column, the
+    // sum over the tile's columns and populations of v_theta times the theta-face value of dg on the
+    // pole face, [3][2][tiles_x]
+    double *pole_part;
 };
 
 // Population slots of the FP32 pair layout: slot s = 2 p + m is member m of pair plane p.
@@ -190,11 +194,14 @@ void launch_stage_f32_persist_q3(const CUtensorMap &tm_in, const CUtensorMap &tm
 // State scale k of the FP32 storage for WENO regulariser eps: the power of two nearest
 // 1 / (2 sqrt(eps)), so that 4 eps k^2 lies in [1/2, 2].
 double f32_state_scale(double eps);
-// The conversions below take the run's state scale ks (dg = ks sin(theta) (f - w rho_ref)).
+// Conversions between moments and the FP32 deviations, in the FP32 deviation form (FP64 only for
+// rho - rho_ref, T - 1 and rho_ref + dn): ks_s[i] = k sin(theta_i) and inv_ks_s[i] = 1 / (k sin(theta_i))
+// as FP32 per interior row.
 void launch_init_f32(float2 *f, const Layout &L, const double *rho, const double *ut, const double *up,
-                     const double *T, const VelD &c, double rho_ref, const double *sin_t, double ks, cudaStream_t s);
+                     const double *T, const VelD &c, double rho_ref, const float *ks_s, cudaStream_t s);
 void launch_moments_f32(const float2 *f, const Layout &L, double *rho, double *ut, double *up, double *T,
-                        const VelD &c, double rho_ref, const double *sin_t, double ks, cudaStream_t s);
+                        const VelD &c, double rho_ref, const float *inv_ks_s, cudaStream_t s);
+// The conversions below take the run's state scale ks (dg = ks sin(theta) (f - w rho_ref)).
 void launch_pack_f32(const float2 *f, const Layout &L, double *dense, const VelD &c, double rho_ref,
                      const double *sin_t, double ks, cudaStream_t s);
 void launch_unpack_f32(const double *dense, const Layout &L, float2 *f, const VelD &c, double rho_ref,
@@ -205,9 +212,21 @@ void launch_filter_f32(float2 *f, const Layout &L, int q, const int *rows, const
                        cudaStream_t s);
 // Polar filter of every (run, row, block size) item of a batch on the output array of `stage`.
 void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int stage, cudaStream_t s);
+// FP64 diagnostics of an FP32 state (cph, sph: cos and sin of the column angles, FP64 [np]); out as
+// launch_diagnostics_f64.  part: diag_partials(L) doubles of scratch.
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,
-                            const VelD &c, double area, double rho_ref, double ks, double *part, double *out,
-                            cudaStream_t s);
+                            const double *cph, const double *sph, const VelD &c, double area, double rho_ref,
+                            double ks, double *part, double *out, cudaStream_t s);
+// Pole mass-flux budget of one FP32 step from the stage kernels' pole partials ([3][2][ntx], RunF.pole_part):
+// budget += dt (m1/6 + m2/6 + 2 m3/3), m_s = -R dphi ((S_south / ks + ref_s) - (S_north / ks + ref_n)) with
+// ref_n, ref_s the reference state's v_theta-weighted pole fluxes summed over the columns.
+void launch_pole_budget_f32(const double *part, int ntx, double ref_n, double ref_s, double ks, double R, double dph,
+                            double dt, double *budget, cudaStream_t s);
+// Area-weighted mean of a device density field (rowsum: nt doubles of scratch; out: one double).
+void launch_rho_ref(const double *rho, int nt, int np, const double *sin_t, double *rowsum, double *out,
+                    cudaStream_t s);
+// rho = sum_k f_k of a dense [nk][cells] population array.
+void launch_density_of_populations(const double *dense, int nk, size_t cells, double *rho, cudaStream_t s);
 
 // ---- FP64 helpers -------------------------------------------------------------------
 void launch_init_f64(double *f, const Layout &L, const double *rho, const double *ut, const double *up,
