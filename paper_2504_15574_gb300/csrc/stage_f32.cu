@@ -393,6 +393,56 @@ __device__ __forceinline__ void pole_face(double *slot, f2 vth, f2 v, bool valid
     if ((threadIdx.x & 31) == 0) *slot = x;
 }
 
+// The theta-face value at face fy of pair q and this lane's column (the reconstruction of dg that
+// the theta walkers form there; the same operations in the same order).
+template <int TY, bool LIN, class VC, class Box, class Tab>
+__device__ __forceinline__ f2 theta_face_value(const RunF &R, const VC &c, const Box &box, const Tab &tab, int q,
+                                               int fy, int lane)
+{
+    const f2 *col = &box.v[q][0][lane + GC];
+    const bool g = pair_thpos(c, q);
+    if constexpr (LIN) {
+        const f2 l0 = splat(R.lin0), l1 = splat(R.lin1), l2 = splat(R.lin2);
+        return g ? fma2(l0, col[(fy + 1) * SC], fma2(l1, col[(fy + 2) * SC], mul2(l2, col[(fy + 3) * SC])))
+                 : fma2(l0, col[(fy + 4) * SC], fma2(l1, col[(fy + 3) * SC], mul2(l2, col[(fy + 2) * SC])));
+    } else {
+        const f2 E = splat(R.e_theta), c133 = splat(13.0f / 3.0f), two = splat(2.0f), m2 = splat(-2.0f);
+        const f2 wr = R.wr[q];
+        f2 x[6], dd[6], dfu[6], D2[6], Qa[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) x[m] = col[(fy + m) * SC];
+#pragma unroll
+        for (int m = 1; m < 6; ++m) {
+            dd[m] = sub2(x[m], x[m - 1]);
+            dfu[m] = fma2(wr, tab.ds2[fy + m], dd[m]);
+        }
+#pragma unroll
+        for (int m = 1; m < 5; ++m) {
+            D2[m] = fma2(wr, tab.d2s2[fy + m], sub2(dd[m + 1], dd[m]));
+            Qa[m] = fma2(mul2(D2[m], c133), D2[m], E);
+        }
+        f2 B1, B2, B3, Q1, Q2, Q3, d12, d23, p2;
+        if (g) {
+            Q1 = Qa[1]; Q2 = Qa[2]; Q3 = Qa[3];
+            B1 = fma2(two, dfu[2], D2[1]);
+            B2 = add2(dfu[2], dfu[3]);
+            B3 = fma2(m2, dfu[3], D2[3]);
+            d12 = sub2(D2[1], D2[2]);
+            d23 = sub2(D2[2], D2[3]);
+            p2 = fma2(splat(1.0f / 6.0f), dd[2], fma2(splat(1.0f / 3.0f), dd[3], x[2]));
+        } else {
+            Q1 = Qa[4]; Q2 = Qa[3]; Q3 = Qa[2];
+            B1 = fma2(m2, dfu[4], D2[4]);
+            B2 = add2(dfu[4], dfu[3]);
+            B3 = fma2(two, dfu[3], D2[2]);
+            d12 = sub2(D2[4], D2[3]);
+            d23 = sub2(D2[3], D2[2]);
+            p2 = fma2(splat(-1.0f / 6.0f), dd[4], fma2(splat(-1.0f / 3.0f), dd[3], x[3]));
+        }
+        return weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
+    }
+}
+
 // Face phase of one stage of one TY x TX tile (q0 = bx TX, i0 = by TY) whose input box and
 // tables are in tile buffer b of S: the phi and theta faces of every pair into S.adv (and S.advT).
 // Ends without a barrier.
@@ -458,15 +508,6 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
     }
     __syncwarp();   // the theta walker reads the cells this warp's phi walkers wrote
 
-    // Pole faces (face 0 of the first tile row, face n_theta - i0 of the last): each theta walker
-    // also records its pair's v_theta-weighted face values there for the pole mass-flux budget.
-    // The face value is the reconstruction of dg (the reference part's is added on the host side).
-    const int i0f = by * TY;
-    const bool pole_n = R.pole_part != nullptr && i0f == 0;
-    const int pole_s = (R.pole_part != nullptr && i0f + TY >= R.L.nt) ? R.L.nt - i0f : -1;
-    const bool col_ok = bx * TX + lane < R.L.np;
-    (void)pole_n; (void)pole_s; (void)col_ok;
-
     // ---- upwind schemes, theta faces: warp = pair, lane = column; the column's values are dg
     // (nodal g = sin f), or for the Komissarov flux df = dg / sin (ghost rows: the mapped
     // population's df), then v_theta times the interface sine times the reconstruction.
@@ -489,7 +530,6 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
                 const f2 rec = g ? fma2(l0, x[fy + 1], fma2(l1, x[fy + 2], mul2(l2, x[fy + 3])))
                                  : fma2(l0, x[fy + 4], fma2(l1, x[fy + 3], mul2(l2, x[fy + 2])));
                 const f2 fl = kom ? mul2(mul2(vt, rec), tab.sf2[fy]) : mul2(vt, rec);
-                if (fy == 0 ? pole_n : fy == pole_s) pole_face(&S.polew[fy == 0 ? 0 : 1][q], pair_vth(c, q), rec, col_ok);
                 if (fy > 0) {
                     const int cy = fy - 1;
                     const f2 idth = splat(kom ? tab.rowc[cy].kth : R.inv_dth);
@@ -565,7 +605,6 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
                 }
                 // P2 of the reference part is in the FP64-derived tendency rref
                 const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
-                if (fy == 0 ? pole_n : fy == pole_s) pole_face(&S.polew[fy == 0 ? 0 : 1][q], pair_vth(c, q), v, col_ok);
                 if (fy > 0) {
                     const int cy = fy - 1;
                     if constexpr (SPLIT) S.advT[q][cy][lane] = mul2(vt, sub2(prev, v));
@@ -573,6 +612,24 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
                 }
                 prev = v;
             }
+        }
+    }
+
+    // Pole faces (face 0 of the first tile row, face n_theta - i0 of the last tile row): for the
+    // pole mass-flux budget each pair's theta-face value there, the reconstruction of dg exactly
+    // as its walker formed it (the reference part's is added on the host side), is evaluated
+    // once more and its v_theta-weighted sum over the tile's columns recorded.  Only the tiles on
+    // a pole do this, outside the walkers.
+    const int i0f = by * TY;
+    const bool pole_n = R.pole_part != nullptr && i0f == 0;
+    const int pole_s = (R.pole_part != nullptr && i0f + TY >= R.L.nt) ? R.L.nt - i0f : -1;
+    if (pole_n || pole_s >= 0) {
+        const bool col_ok = bx * TX + lane < R.L.np;
+#pragma unroll 1
+        for (int q = SPLIT ? warp - NFQ : warp; q >= 0 && q < NFQ; q += FSTEP) {
+            if (pole_n) pole_face(&S.polew[0][q], pair_vth(c, q), theta_face_value<TY, LIN>(R, c, box, tab, q, 0, lane), col_ok);
+            if (pole_s >= 0)
+                pole_face(&S.polew[1][q], pair_vth(c, q), theta_face_value<TY, LIN>(R, c, box, tab, q, pole_s, lane), col_ok);
         }
     }
 }
