@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--n-theta", type=int, default=1024)
     ap.add_argument("--n-phi", type=int, default=2048)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle cpu_baseline leg")
+    ap.add_argument("--repeats", type=int, default=0,
+                    help="repeats of the timed steps (0: at least 5, until ~0.5 s of steps, at most 50)")
     ap.add_argument("--scheme", default="weno5", choices=["weno5", "u1", "u2", "u3"],
                     help="advection scheme (the headline workload is weno5)")
     ap.add_argument("--komissarov", action="store_true", help="Komissarov theta flux (upwind schemes)")
@@ -315,7 +317,8 @@ def run_ours(args):
             ev1.record(stream)
             barrier()
             times.append(ev0.elapsed_time(ev1))
-            done = len(times) >= 5 and (sum(times) >= 500.0 or len(times) >= 50)
+            done = (len(times) >= args.repeats) if args.repeats > 0 else \
+                (len(times) >= 5 and (sum(times) >= 500.0 or len(times) >= 50))
             if world > 1:
                 # every rank takes the same number of repeats: rank 0's decision
                 flag = torch.tensor([1 if done else 0], device="cuda")

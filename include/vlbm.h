@@ -173,6 +173,15 @@ VLBM_API int vlbm_max_stable_dt(int n_theta, int n_phi, int velocity_set, double
  * that run on two streams. */
 VLBM_API int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches);
 
+/* Limit, in seconds (0 <= limit <= 10, default 1), of the FP32 stage kernels' first wait for a
+ * tile's asynchronous copies.  A copy that has not arrived by then makes the kernel flag a
+ * timeout, wait (at most one more second) for its copies in flight and leave the tile, and the
+ * next vlbm_step / vlbm_sync returns VLBM_ERR_TIMEOUT; the state is then undefined (finite) and
+ * the handle keeps the flag until the next vlbm_init_moments / vlbm_set_populations.  A limit
+ * of 0 gives up whenever the copies have not landed at the first test, which exercises that path
+ * on purpose.  The step graphs are rebuilt on the next step.  FP64 handles:
+ * VLBM_ERR_UNSUPPORTED (no such waits). */
+VLBM_API int vlbm_set_wait_limit(vlbm_t *h, double seconds);
 /* Bytes of device memory the handle holds. */
 VLBM_API size_t vlbm_device_bytes(const vlbm_t *h);
 
@@ -280,26 +289,29 @@ VLBM_API const char *vlbm_lc_last_error(const vlbm_lc_t *lc);
 VLBM_API void vlbm_lc_destroy(vlbm_lc_t *lc);
 
 /* ---- Diagnostics without device allocation --------------------------------------
- * The paper has no counterpart to this entry point; it serves callers that cannot
- * call cudaMalloc where they need the numbers: code running while a stream is
- * captured into a CUDA graph, latency-bound loops that cannot afford an
- * allocation's device synchronisation, and hosts whose device memory comes from
- * their own pool.  It reduces a population array the caller owns and writes to a
- * device buffer the caller owns; the library allocates nothing.
+ * The paper has no counterpart to this entry point.  It serves callers that cannot
+ * call cudaMalloc where they need the numbers: hosts whose device memory comes from
+ * their own pool or is held to a fixed budget (a library must not grow or fragment
+ * it), and latency-bound loops that cannot afford the device synchronisation an
+ * allocation can cause.  It reduces a population array the caller owns and writes
+ * to a device buffer the caller owns; the library allocates nothing.
  *
- *   f_dev:   device pointer, FP64 populations, dense layout [16][n_theta][n_phi]
- *            (the layout of vlbm_get_populations), read only;
+ *   f_dev:   device pointer, FP64 populations of the D2Q16 set, dense layout
+ *            [16][n_theta][n_phi] (the layout of vlbm_get_populations for D2Q16), read
+ *            only.  Arrays of another velocity set (D2Q9: 9 planes) are not supported
+ *            and the call cannot tell them apart: it would read 16 planes.
  *   out_dev: device pointer to 6 doubles: mass, Cartesian momentum x, y, z, energy
  *            sum_k f_k |v_k|^2 / 2 (area element R^2 sin(theta) dtheta dphi, as in
- *            vlbm_diagnostics) and the count of rows holding a NaN/Inf population;
+ *            vlbm_diagnostics) and the number of cells holding a NaN or Inf population;
  *   stream:  cudaStream_t to run on (NULL: the legacy default stream).  The call
  *            only enqueues; the caller synchronises before reading out_dev.
  * Scratch: a fixed array inside the library sized for n_theta <= VLBM_NOALLOC_MAX_ROWS
  * (768 KiB per GPU that loads the library, held until exit); larger grids return
- * VLBM_ERR_ARG.  The first call on each device looks up that array's address and
- * should come before any stream capture.  All calls share the one array, so calls
- * whose kernels overlap on the GPU race with each other.  Errors:
- * VLBM_ERR_ARG / VLBM_ERR_CUDA, message in vlbm_noalloc_last_error(). */
+ * VLBM_ERR_ARG.  The first call on each device looks up that array's address (with
+ * the device current) and caches it: make that first call before any stream capture;
+ * the cached address does not survive a cudaDeviceReset of the device.  All calls
+ * share the one array, so calls whose kernels overlap on the GPU race with each
+ * other.  Errors: VLBM_ERR_ARG / VLBM_ERR_CUDA, message in vlbm_noalloc_last_error(). */
 #define VLBM_NOALLOC_MAX_ROWS 16384
 VLBM_API int vlbm_diagnostics_noalloc(const double *f_dev, int n_theta, int n_phi, double radius, double *out_dev,
                                       void *stream);

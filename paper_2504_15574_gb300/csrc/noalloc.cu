@@ -2,20 +2,20 @@
 // device allocation.
 //
 // Some callers cannot call cudaMalloc at the point where they need these
-// numbers: code that runs while a stream is being captured into a CUDA graph
-// (cudaMalloc is not a stream operation and breaks the capture), real-time or
-// latency-bound loops where an allocation's implicit device synchronisation is
-// not acceptable, and hosts whose memory is handed out by their own pool and
-// must not be fragmented by a library.  For them, vlbm_diagnostics_noalloc
-// reduces a population array the caller already owns, using a fixed scratch
-// array compiled into the library instead of memory from cudaMalloc.
+// numbers: hosts whose device memory is handed out by their own pool or held to a
+// fixed budget, which a library must not grow or fragment behind their back, and
+// latency-bound loops where the implicit device synchronisation an allocation can
+// cause is not acceptable.  For them, vlbm_diagnostics_noalloc reduces a
+// population array the caller already owns, using a fixed scratch array compiled
+// into the library instead of memory from cudaMalloc.
 //
 // The scratch is a file-scope __device__ array of VLBM_NOALLOC_MAX_ROWS x 6
 // doubles (768 KiB); every GPU that loads the library holds it until the
 // process exits.  Host code cannot use the array's name as a device address, so
 // the first call on each device looks its address up with cudaGetSymbolAddress
 // (with that device current) and caches it; that first call should therefore
-// come before any stream capture.  All calls share the one array: calls whose
+// come before any stream capture, and the cached address does not survive a
+// cudaDeviceReset of that device.  All calls share the one array: calls whose
 // kernels overlap on the GPU (on different streams) race on it.  The per-row
 // partial sums are fully rewritten by every call, so nothing in the scratch has
 // to start at zero.
@@ -69,7 +69,7 @@ __global__ void noalloc_rows_kernel(const double *f, int nt, int np, double radi
         acc[2] += (jt * ct * sp + jp * cp) * dA;
         acc[3] += (-jt * st) * dA;
         acc[4] += 0.5 * e * dA;
-        acc[5] += bad;
+        acc[5] += bad;   // one per cell holding a NaN or Inf population
     }
     __shared__ double red[NQ][NOALLOC_THREADS];
     for (int q = 0; q < NQ; ++q) red[q][threadIdx.x] = acc[q];

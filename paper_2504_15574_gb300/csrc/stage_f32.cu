@@ -150,22 +150,28 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 }
 
 // Waits for the mbarrier phase with the given parity for at most limit_ns; false on timeout.
+// The phase is first tested without blocking; limit_ns = 0 gives up right there (a test of the
+// timeout path), otherwise try_wait (which may suspend the thread for a while) is polled with the
+// elapsed global time checked after every attempt.
 __device__ __forceinline__ bool wait_phase(unsigned long long *bar, unsigned parity, unsigned long long limit_ns)
 {
-    unsigned long long t0 = 0;
-    for (unsigned it = 0;; ++it) {
-        unsigned done;
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred P; mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (limit_ns == 0) return false;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
         asm volatile(
             "{ .reg .pred P; mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2; selp.u32 %0, 1, 0, P; }"
             : "=r"(done)
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
-        if ((it & 255u) == 0u) {
-            const unsigned long long t = globaltimer_ns();
-            if (it == 0u) t0 = t;
-            else if (t - t0 > limit_ns) return false;
-        }
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -446,7 +452,7 @@ __device__ __forceinline__ f2 theta_face_value(const RunF &R, const VC &c, const
 // Face phase of one stage of one TY x TX tile (q0 = bx TX, i0 = by TY) whose input box and
 // tables are in tile buffer b of S: the phi and theta faces of every pair into S.adv (and S.advT).
 // Ends without a barrier.
-template <int TY, bool LIN, int Q, class Sm>
+template <int TY, bool LIN, int Q, bool KW = false, class Sm>
 __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q>::type &c, float dte, Sm &S,
                                            int b, int tb, int bx, int by)
 {
@@ -548,6 +554,11 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
     // x[fy..fy+4] in upwind order, for v < 0 it uses x[fy+5..fy+1].  The smoothness
     // forms are those of the full g = dg + w rho_ref sin(theta) (first and second
     // differences of sin from the FP64 tables); P2 is taken on dg alone.
+    // KW: WENO-5 with the Komissarov theta flux (Eqs. Komissarov_scheme, Komissarov_sin_cos): the
+    // reconstruction is of f (the column's values are df = dg / sin; the reference part of f is
+    // the constant w rho_ref, which leaves every difference alone), the face flux carries the
+    // interface sine, and the difference of two faces the row factor s / (R dcos) (the reference
+    // state's Komissarov flux difference is in rref).
     if constexpr (!LIN) {
         const f2 E = splat(R.e_theta), c133 = splat(13.0f / 3.0f);
         const f2 two = splat(2.0f), m2 = splat(-2.0f);
@@ -555,30 +566,30 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
         for (int q = SPLIT ? warp - NFQ : warp; q >= 0 && q < NFQ; q += FSTEP) {
             const bool g = pair_thpos(c, q);
             const f2 wr = R.wr[q];
-            const f2 vt = mul2(pair_vth(c, q), splat(__fmul_rn(dte, R.inv_dth)));
+            const f2 vt = KW ? mul2(pair_vth(c, q), splat(dte)) : mul2(pair_vth(c, q), splat(__fmul_rn(dte, R.inv_dth)));
             const f2 *col = &box.v[q][0][lane + GC];
             // values are produced one row ahead of their first use (face fy needs rows up to fy+5)
             f2 x[SR], dd[SR], dfu[SR], D2[SR], Qa[SR], prev, dcarry;
 #pragma unroll
-            for (int r = 0; r < 5; ++r) x[r] = col[r * SC];
+            for (int r = 0; r < 5; ++r) x[r] = KW ? mul2(col[r * SC], tab.isp2[r]) : col[r * SC];
 #pragma unroll
             for (int r = 1; r < 5; ++r) {
                 dd[r] = sub2(x[r], x[r - 1]);
-                dfu[r] = fma2(wr, tab.ds2[r], dd[r]);
+                dfu[r] = KW ? dd[r] : fma2(wr, tab.ds2[r], dd[r]);
             }
 #pragma unroll
             for (int r = 1; r < 4; ++r) {
-                D2[r] = fma2(wr, tab.d2s2[r], sub2(dd[r + 1], dd[r]));
+                D2[r] = KW ? sub2(dd[r + 1], dd[r]) : fma2(wr, tab.d2s2[r], sub2(dd[r + 1], dd[r]));
                 Qa[r] = fma2(mul2(D2[r], c133), D2[r], E);
             }
 #pragma unroll
             for (int fy = 0; fy <= TY; ++fy) {
                 {   // extend the window to row fy + 5
                     const int r = fy + 5;
-                    x[r] = col[r * SC];
+                    x[r] = KW ? mul2(col[r * SC], tab.isp2[r]) : col[r * SC];
                     dd[r] = sub2(x[r], x[r - 1]);
-                    dfu[r] = fma2(wr, tab.ds2[r], dd[r]);
-                    D2[r - 1] = fma2(wr, tab.d2s2[r - 1], sub2(dd[r], dd[r - 1]));
+                    dfu[r] = KW ? dd[r] : fma2(wr, tab.ds2[r], dd[r]);
+                    D2[r - 1] = KW ? sub2(dd[r], dd[r - 1]) : fma2(wr, tab.d2s2[r - 1], sub2(dd[r], dd[r - 1]));
                     Qa[r - 1] = fma2(mul2(D2[r - 1], c133), D2[r - 1], E);
                 }
                 f2 B1, B2, B3, Q1, Q2, Q3, d12, d23, p2;
@@ -604,11 +615,13 @@ __device__ __forceinline__ void tile_faces(const RunF &R, const typename VelOf<Q
                     p2 = fma2(splat(-1.0f / 6.0f), dd[fy + 4], fma2(splat(-1.0f / 3.0f), dd[fy + 3], x[fy + 3]));
                 }
                 // P2 of the reference part is in the FP64-derived tendency rref
-                const f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
+                f2 v = weno_mix(fma2(B1, B1, Q1), fma2(B2, B2, Q2), fma2(B3, B3, Q3), d12, d23, p2);
+                if constexpr (KW) v = mul2(v, tab.sf2[fy]);   // face flux / (v_theta dte): interface sine
                 if (fy > 0) {
                     const int cy = fy - 1;
-                    if constexpr (SPLIT) S.advT[q][cy][lane] = mul2(vt, sub2(prev, v));
-                    else S.adv[q][cy][lane] = fma2(vt, sub2(prev, v), S.adv[q][cy][lane]);
+                    const f2 vk = KW ? mul2(vt, splat(tab.rowc[cy].kth)) : vt;
+                    if constexpr (SPLIT) S.advT[q][cy][lane] = mul2(vk, sub2(prev, v));
+                    else S.adv[q][cy][lane] = fma2(vk, sub2(prev, v), S.adv[q][cy][lane]);
                 }
                 prev = v;
             }
@@ -850,7 +863,7 @@ __device__ __forceinline__ void tile_cells(const RunF &R, const typename VelOf<Q
 // LIN: the upwind schemes U1-U3 (Eq. fluxes_U1-3, optionally with the Komissarov theta flux)
 // instead of WENO-5.
 // Q: the velocity set (4: D2Q16, 3: D2Q9 in five pairs).
-template <int TY, bool LIN, int Q>
+template <int TY, bool LIN, int Q, bool KW = false>
 __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q>::type &c, int stage,
                                            const CUtensorMap *tm, const CUtensorMap *tmo, const CUtensorMap *tmf,
                                            int bx, int by, SmemT<TY, (Q == 3 ? 5 : NP2)> &S, unsigned parity,
@@ -885,18 +898,18 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
                 : "memory");
     }
     // per-tile tables while the tile is in flight
-    fill_tab<TY, NPQ, LIN>(S.tab[0], R, i0, dte);
+    fill_tab<TY, NPQ, LIN || KW>(S.tab[0], R, i0, dte);
     // (the barrier of the load wait also publishes the tables; the caller has made the
     // mbarrier's initialisation visible to every thread before this tile began)
-    const bool ok = __syncthreads_and(wait_phase(&S.bar[0], parity, 1000000000ull));
+    const bool ok = __syncthreads_and(wait_phase(&S.bar[0], parity, R.wait_ns));
     if (!ok) {
-        // the copy did not complete within 1 s: flag it, give it one more bounded
-        // second to land in this CTA's shared memory, then leave
+        // the copy did not complete within the wait limit (1 s unless set otherwise): flag it,
+        // give it one more bounded second to land in this CTA's shared memory, then leave
         if (tid == 0) atomicOr(err, 1u);
         wait_phase(&S.bar[0], parity, 1000000000ull);
         return false;
     }
-    tile_faces<TY, LIN, Q>(R, c, dte, S, 0, 0, bx, by);
+    tile_faces<TY, LIN, Q, KW>(R, c, dte, S, 0, 0, bx, by);
     __syncthreads();
     f2 G[NPQ];
     load_cell_g<TY, NPQ>(S, 0, G);
@@ -904,7 +917,7 @@ __device__ __forceinline__ bool stage_tile(const RunF &R, const typename VelOf<Q
     return true;
 }
 
-template <int TY, bool LIN, int Q>
+template <int TY, bool LIN, int Q, bool KW = false>
 __global__ void __launch_bounds__(TY * 32, (Q == 3 ? 32 : 24) / TY) stage_f32_kernel(const __grid_constant__ CUtensorMap tm,
                                                                       const __grid_constant__ CUtensorMap tmo,
                                                                       const __grid_constant__ CUtensorMap tmf,
@@ -920,7 +933,7 @@ __global__ void __launch_bounds__(TY * 32, (Q == 3 ? 32 : 24) / TY) stage_f32_ke
     }
     __syncthreads();   // no thread may poll the barrier before its initialisation is visible
     const int by = rows.first + (int)blockIdx.y + ((int)blockIdx.y >= rows.split ? rows.skip : 0);
-    stage_tile<TY, LIN, Q>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, by, S, 0u, err);
+    stage_tile<TY, LIN, Q, KW>(R, c, stage, &tm, &tmo, &tmf, blockIdx.x, by, S, 0u, err);
 }
 
 // Persistent stage kernel (8 tile rows, three CTAs per SM): CTA b takes the launch's tiles
@@ -930,8 +943,8 @@ __global__ void __launch_bounds__(TY * 32, (Q == 3 ? 32 : 24) / TY) stage_f32_ke
 // tile are issued into the freed box buffer (the tables alternate between two buffers) while this
 // tile's cells are computed and stored; the tile of F (stages 2, 3) of the next tile is issued as
 // soon as this tile's output has left the staging buffer.  tabs holds this stage's tables of every
-// tile row of the grid.  A copy that does not arrive within 1 s sets *err; the CTA then waits
-// (bounded) for its other copies in flight and leaves.
+// tile row of the grid.  A copy that does not arrive within the run's wait limit sets *err; the
+// CTA then waits (bounded, 1 s) for its other copies in flight and leaves.
 template <bool LIN, int Q>
 __global__ void __launch_bounds__(256, 3)
     stage_f32_persist_kernel(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmo,
@@ -1007,7 +1020,7 @@ __global__ void __launch_bounds__(256, 3)
     for (int k = 0; t < total; ++k, t += G) {
         const int tb = k & 1;
         const unsigned par = k & 1;   // phase of tile k on the box barrier and on the F barrier
-        const bool box_ok = __syncthreads_and(wait_phase(&S.bar[0], par, LIMIT_NS));
+        const bool box_ok = __syncthreads_and(wait_phase(&S.bar[0], par, R.wait_ns));
         bool ok = box_ok, next_box = false;
         if (ok) {
             int bx, by;
@@ -1019,7 +1032,7 @@ __global__ void __launch_bounds__(256, 3)
             __syncthreads();   // the box buffer is free: the next tile's copies go now
             next_box = t + G < total;
             if (tid == 0 && next_box) issue_box(t + G, tb ^ 1);
-            if (stage != 1) ok = __syncthreads_and(wait_phase(&S.barF, par, LIMIT_NS));
+            if (stage != 1) ok = __syncthreads_and(wait_phase(&S.barF, par, R.wait_ns));
             if (ok) {
                 tile_cells<TY, LIN, Q>(R, c, stage, dte, &tmo, bx, by, S, 0, tb, Gc);
                 __syncthreads();   // this tile's tables and the staging buffer are free
@@ -1027,8 +1040,9 @@ __global__ void __launch_bounds__(256, 3)
                 continue;
             }
         }
-        // a copy did not arrive within 1 s: flag it, give this CTA's copies still in flight one
-        // more bounded second each to land in its shared memory, then leave
+        // a copy did not arrive within the wait limit (1 s unless set otherwise): flag it, give
+        // this CTA's copies still in flight one more bounded second each to land in its shared
+        // memory, then leave
         if (tid == 0) {
             atomicOr(err, 1u);
             if (!box_ok) wait_phase(&S.bar[0], par, LIMIT_NS);
@@ -1619,6 +1633,14 @@ cudaError_t prepare_one()
     e = cudaFuncSetAttribute(stage_f32_kernel<TY, LIN, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes<TY, 3>());
     if (e) return e;
+    if (!LIN) {   // WENO-5 with the Komissarov theta flux
+        e = cudaFuncSetAttribute(stage_f32_kernel<TY, false, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes<TY>());
+        if (e) return e;
+        e = cudaFuncSetAttribute(stage_f32_kernel<TY, false, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes<TY, 3>());
+        if (e) return e;
+    }
     return cudaFuncSetAttribute(batch_stage_f32_kernel<TY, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes<TY>());
 }
@@ -1729,6 +1751,11 @@ static void launch_stage_q(const CUtensorMap &tm_in, const CUtensorMap &tm_out, 
     if (rows.count < 0) rows = TileRows{0, (run.L.nt + ty - 1) / ty, 1 << 30, 0};
     if (rows.count == 0) return;
     const dim3 grid((run.L.np + TX - 1) / TX, rows.count);
+    if (!lin && run.komissarov) {   // WENO-5 with the Komissarov theta flux
+        if (ty == 4) stage_f32_kernel<4, false, Q, true><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, err);
+        else stage_f32_kernel<8, false, Q, true><<<grid, 256, smem_bytes<8, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, err);
+        return;
+    }
     if (ty == 4) {
         if (lin) stage_f32_kernel<4, true, Q><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, err);
         else stage_f32_kernel<4, false, Q><<<grid, 128, smem_bytes<4, Q>(), s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, err);

@@ -356,6 +356,7 @@ int build_f32_tables(vlbm_t *h)
     run.inv_dth = (float)(1.0 / (h->R * (M_PI / h->nt)));
     run.tiles_x = (h->np + F32_TILE_COLS - 1) / F32_TILE_COLS;
     run.pole_part = h->komissarov ? nullptr : h->d_pole_part;
+    run.wait_ns = h->wait_ns;
     if ((rc = upload(h, &h->d_kss, kss.data(), kss.size())) || (rc = upload(h, &h->d_ikss, ikss.data(), ikss.size())))
         return rc;
     // the persistent stage kernel's per-tile-row tables of the three stages (8-row tiles)
@@ -611,8 +612,6 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     if (o.precision != VLBM_FP64 && o.precision != VLBM_FP32) return fail(nullptr, VLBM_ERR_ARG, "bad precision");
     if (!(o.weno_eps > 0.0) || !(o.radius > 0.0)) return fail(nullptr, VLBM_ERR_ARG, "weno_eps and radius must be > 0");
     if (o.scheme < VLBM_WENO5 || o.scheme > VLBM_U3) return fail(nullptr, VLBM_ERR_ARG, "unknown advection scheme");
-    if (o.precision == VLBM_FP32 && o.scheme == VLBM_WENO5 && o.komissarov)
-        return fail(nullptr, VLBM_ERR_UNSUPPORTED, "the FP32 path runs the Komissarov flux with the upwind schemes only");
 
     vlbm_t *h = new vlbm_t();
     h->nt = n_theta;
@@ -990,6 +989,16 @@ int vlbm_profile_step(vlbm_t *h, int n, double *ms_per_stage, int *launches)
     return vlbm_sync(h);
 }
 
+int vlbm_set_wait_limit(vlbm_t *h, double seconds)
+{
+    if (!h || !(seconds >= 0.0) || seconds > 10.0) return fail(h, VLBM_ERR_ARG, "wait limit must be in [0, 10] s");
+    if (h->prec != VLBM_FP32) return fail(h, VLBM_ERR_UNSUPPORTED, "only the FP32 stage kernels wait on copies");
+    h->wait_ns = (unsigned long long)(seconds * 1e9);
+    h->run.wait_ns = h->wait_ns;
+    drop_graphs(h);   // the captured launches hold the old parameters
+    return VLBM_OK;
+}
+
 size_t vlbm_device_bytes(const vlbm_t *h) { return h ? h->dev_bytes : 0; }
 
 const char *vlbm_last_error(const vlbm_t *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -1236,6 +1245,8 @@ int vlbm_batch_create(int nruns, const int *n_theta, const int *n_phi, const dou
     vlbm_default_options(&o);
     if (opt) o = *opt;
     if (o.precision != VLBM_FP32) return bfail(nullptr, VLBM_ERR_UNSUPPORTED, "batches run the FP32 path only");
+    if (o.scheme == VLBM_WENO5 && o.komissarov)
+        return bfail(nullptr, VLBM_ERR_UNSUPPORTED, "batches run the Komissarov flux with the upwind schemes only");
     vlbm_batch_t *b = new vlbm_batch_t();
     b->guard = o.guard ? 1 : 0;
     int dev = 0;

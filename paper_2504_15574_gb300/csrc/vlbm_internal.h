@@ -89,6 +89,9 @@ struct RunF {
     // sum over the tile's columns and populations of v_theta times the theta-face value of dg on the
     // pole face, [3][2][tiles_x]
     double *pole_part;
+    // limit of the stage kernels' first wait for a tile's copies (ns; the second, after which
+    // the CTA leaves, is always 1 s)
+    unsigned long long wait_ns;
 };
 
 // Population slots of the FP32 pair layout: slot s = 2 p + m is member m of pair plane p.

@@ -68,6 +68,7 @@ SIGNATURES = {
     "vlbm_max_stable_dt": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                           _PD]),
     "vlbm_profile_step": (ctypes.c_int, [_H, ctypes.c_int, _PD, ctypes.POINTER(ctypes.c_int)]),
+    "vlbm_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_double]),
     "vlbm_device_bytes": (ctypes.c_size_t, [_H]),
     "vlbm_last_error": (ctypes.c_char_p, [_H]),
     "vlbm_destroy": (None, [_H]),
@@ -188,6 +189,10 @@ def vlbm_diagnostics(h) -> dict:
     return {"time": d.time, "steps": d.steps, "mass": d.mass, "px": d.momentum[0], "py": d.momentum[1],
             "pz": d.momentum[2], "energy": d.energy, "pole_flux": d.pole_flux, "mass0": d.mass0,
             "nonfinite": d.nonfinite}
+
+
+def vlbm_set_wait_limit(h, seconds):
+    _check(load().vlbm_set_wait_limit(h, float(seconds)), h)
 
 
 def vlbm_max_stable_dt(n_theta, n_phi, tau, polar_filter=False, velocity_set=VLBM_D2Q16) -> float:
@@ -477,9 +482,10 @@ class LearnedCorrection:
 
 
 def vlbm_diagnostics_noalloc(f_dev_ptr, n_theta, n_phi, radius, out_dev_ptr, stream=None):
-    """Diagnostics of a caller-owned device array with no allocation in the library
-    (for callers that cannot call cudaMalloc, e.g. inside a graph capture).  Takes raw
-    device addresses; enqueues on `stream` and returns without waiting."""
+    """Diagnostics of a caller-owned D2Q16 device array with no allocation in the library
+    (for callers that cannot call cudaMalloc where they need the numbers: their own memory
+    pool or budget, latency-bound loops).  Takes raw device addresses; enqueues on `stream`
+    and returns without waiting.  out[5] counts the cells holding a NaN or Inf population."""
     rc = load().vlbm_diagnostics_noalloc(ctypes.c_void_p(f_dev_ptr), int(n_theta), int(n_phi), float(radius),
                                          ctypes.c_void_p(out_dev_ptr), stream)
     if rc != VLBM_OK:

@@ -239,8 +239,6 @@ def test_fp32_schemes_match_oracle_within_stated_bound(V, scheme, komissarov, nt
     """The FP32 deviation path with the upwind fluxes (the reference state's part of their linear
     flux differences is exact in the FP64-derived tendency) and the Komissarov theta flux
     (reconstruction on df = dg / sin, interface sines), against the oracle."""
-    if scheme == "weno5" and komissarov:
-        pytest.skip("the FP32 path runs the Komissarov flux with the upwind schemes only")
     tau = 0.02
     dt = literal_dt(nt) / 2 if filt else clamped_dt(nt, np_, tau)
     ic = inputs.gaussian_vortices(nt, np_, 3, umax=0.08)
@@ -264,6 +262,8 @@ D2Q9_FP32_CASES = D2Q9_CASES + [
     ("sound_1d_64x1", 64, 1, False, "weno5", False, lambda nt, np_: inputs.sound_parabola(nt, np_, 1e-3)),
     ("u1_vortices_24x48", 24, 48, False, "u1", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 10, umax=0.08)),
     ("u3_filter_32x64", 32, 64, True, "u3", False, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 11, umax=0.08)),
+    # WENO-5 with the Komissarov theta flux
+    ("w5k_vortices_16x32", 16, 32, False, "weno5", True, lambda nt, np_: inputs.gaussian_vortices(nt, np_, 12, umax=0.08)),
 ]
 D2Q9_FP32_TOL = {
     # name: (tol_rho, tol_drho, tol_u), about 5x the worst GB300 value
@@ -278,6 +278,7 @@ D2Q9_FP32_TOL = {
     "sound_1d_64x1": (5e-9, 3e-6, 6e-6),
     "u1_vortices_24x48": (3e-8, 9e-6, 3e-6),
     "u3_filter_32x64": (4e-8, 1.1e-5, 5e-6),
+    "w5k_vortices_16x32": (3e-8, 6e-6, 2e-6),
 }
 
 
@@ -339,10 +340,17 @@ def test_fp32_split_filter_schedule_equals_single_launch_schedule_bitwise(V, vel
     b.close()
 
 
-def test_fp32_weno_with_komissarov_is_refused(V):
-    with pytest.raises(V.VlbmError) as ex:
-        V.Solver(16, 32, 0.02, 1e-4, precision="fp32", komissarov=True)
-    assert ex.value.code == -2
+def test_fp32_weno_with_komissarov_full_size_1024x2048_one_step(V):
+    """WENO-5 with the Komissarov theta flux (the paper's W5+K variant, Sec. 3.5) at the throughput
+    grid size on the FP32 path, every cell against the oracle."""
+    nt, np_, tau = 1024, 2048, 1e-3
+    o, g = run_pair(V, nt, np_, tau, literal_dt(nt), inputs.shock_cap(nt, np_), 1, precision="fp32",
+                    polar_filter=True, scheme="weno5", komissarov=True)
+    e = errors(g.moments(), o.moments())
+    print("w5k full size", e)
+    assert e["rho"] <= 1e-6 and e["drho"] <= 1e-6, e
+    assert e["u"] <= 1e-5, e
+    assert g.diagnostics()["pole_flux"] == 0.0
 
 
 def test_fp32_u3_komissarov_full_size_1024x2048_one_step(V):
@@ -415,3 +423,28 @@ def test_rest_state_fp32_tendency_matches_oracle(V):
     v, w = oracle.quadrature()
     W = np.outer(w, w).reshape(16, 1, 1)
     assert np.abs((fg - W) - (fo - W)).max() <= 1e-9
+
+
+@pytest.mark.parametrize("scheme", ["weno5", "u3"])
+def test_fp32_tile_wait_that_runs_out_reports_a_timeout(V, scheme):
+    """The stage kernels' bounded wait for a tile's copies: with a limit of 0 (give up when the
+    copies have not landed at the first test), kernels give up (after recording the timeout and
+    letting their copies land),
+    vlbm_step returns VLBM_ERR_TIMEOUT, and a fresh handle then steps normally (the one-tile
+    WENO-5 kernel and the persistent kernel of the upwind schemes)."""
+    nt, np_ = 256, 512
+    kw = dict(precision="fp32", polar_filter=True, scheme=scheme, komissarov=scheme != "weno5")
+    ic = inputs.gaussian_vortices(nt, np_, 2)
+    g = V.Solver(nt, np_, 0.01, literal_dt(nt) / 2, **kw)
+    g.init_moments(*ic)
+    V.vlbm_set_wait_limit(g.h, 0.0)
+    with pytest.raises(V.VlbmError) as ex:
+        g.step(4)
+    assert ex.value.code == V.VLBM_ERR_TIMEOUT
+    g.close()
+    h = V.Solver(nt, np_, 0.01, literal_dt(nt) / 2, **kw)
+    h.init_moments(*ic)
+    h.step(4)
+    r, ut, up = h.moments()
+    assert np.isfinite(r).all() and abs(r.mean() - 1.0) < 1e-2
+    h.close()

@@ -1,8 +1,9 @@
 """vlbm_diagnostics_noalloc: the diagnostics of a caller-owned device array for
-callers that cannot call cudaMalloc (graph capture, latency-bound loops, their
-own memory pools).  Its output must agree with vlbm_diagnostics on the same
-populations, on two calls in a row (the shared scratch keeps the last call's
-contents), and it must refuse grids beyond its fixed scratch size.
+callers that cannot call cudaMalloc where they need the numbers (their own
+memory pools or budgets, latency-bound loops).  Its output must agree with
+vlbm_diagnostics on the same populations, on two calls in a row (the shared
+scratch keeps the last call's contents), count the cells that hold a NaN or Inf,
+and refuse grids beyond its fixed scratch size.
 
 This file is named to be collected last."""
 import numpy as np
@@ -53,3 +54,28 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
         vlbm.vlbm_diagnostics_noalloc(f.data_ptr(), 16385, 2, 1.0, out.data_ptr())
     assert e.value.code == vlbm.VLBM_ERR_ARG
     assert "16384" in str(e.value)
+
+
+def test_noalloc_counts_the_cells_holding_a_nonfinite_population():
+    require_gpu()
+    import torch
+
+    from paper_2504_15574_gb300 import vlbm
+    vlbm.load()
+    nt, np_ = 12, 16
+    s = vlbm.Solver(nt, np_, 0.02, 1e-4)
+    s.init_moments(*inputs.gaussian_vortices(nt, np_, run=4))
+    f = s.get_populations()
+    s.close()
+    # two cells of row 3 (one with two bad populations), one cell of row 9 (an infinity)
+    f[2, 3, 5] = np.nan
+    f[7, 3, 5] = np.nan
+    f[11, 3, 6] = np.nan
+    f[0, 9, 0] = np.inf
+    f_dev = torch.from_numpy(f).to("cuda")
+    for call in range(2):
+        out = torch.zeros(6, dtype=torch.float64, device="cuda")
+        vlbm.vlbm_diagnostics_noalloc(f_dev.data_ptr(), nt, np_, 1.0, out.data_ptr(),
+                                      torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert out[5].item() == 3.0, (call, out[5].item())
