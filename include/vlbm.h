@@ -91,6 +91,9 @@ typedef struct vlbm_options {
                            (Komissarov_sin_cos): -d/dcos(theta) of v_theta sin(theta_{s+-1/2}) times
                            the reconstruction of f at the interfaces theta_{s+-1/2} = (s - 1/2 +- 1/2)
                            dtheta; no flux crosses a pole; default 0 */
+    int velocity_set;   /* vlbm_batch_create only: the members' velocity set, VLBM_D2Q16 (default; 0
+                           also means D2Q16) or VLBM_D2Q9; vlbm_create takes it as an argument and
+                           ignores this field */
 } vlbm_options;
 
 /* Diagnostics in FP64 (not in the paper).  Area element R^2 sin(theta) dtheta dphi. */
@@ -101,7 +104,9 @@ typedef struct vlbm_diag {
     double momentum[3]; /* Cartesian sum rho (u^theta e_theta + u^phi e_phi) dA */
     double energy;      /* sum_k f_k |v_k|^2 / 2 dA (reported; the isothermal BGK does not conserve it) */
     double pole_flux;   /* sum over steps of dt * RK-weighted mass flux through both poles;
-                           mass - mass0 - pole_flux vanishes to round-off (FP64 path) */
+                           mass - mass0 - pole_flux vanishes to round-off on the FP64 path and to
+                           the rounding of the FP32 state's updates on the FP32 path (0 with the
+                           Komissarov theta flux: no flux crosses a pole) */
     double mass0;       /* mass at the last init/set */
     int nonfinite;      /* 1 if any population is NaN/Inf */
 } vlbm_diag;
@@ -202,7 +207,9 @@ typedef struct vlbm_batch vlbm_batch_t;
 
 /* Creates nruns FP32 solvers; arrays of length nruns give each run's grid, tau
  * and dt (same constraints as vlbm_create).  opt->precision must be VLBM_FP32
- * (VLBM_ERR_UNSUPPORTED otherwise); opt->stream is the batch's stream. */
+ * (VLBM_ERR_UNSUPPORTED otherwise); opt->stream is the batch's stream;
+ * opt->velocity_set the members' velocity set (D2Q16 or D2Q9).  WENO-5 with the
+ * Komissarov theta flux is not offered for batches (VLBM_ERR_UNSUPPORTED). */
 VLBM_API int vlbm_batch_create(int nruns, const int *n_theta, const int *n_phi, const double *tau,
                                const double *dt, const vlbm_options *opt, vlbm_batch_t **out);
 /* Initial moments of run `run` (as vlbm_init_moments).  Every run must be
@@ -263,9 +270,11 @@ VLBM_API int vlbm_lc_num_params(const vlbm_lc_t *lc);
 VLBM_API int vlbm_lc_get_weights(vlbm_lc_t *lc, float *w);
 /* Sets the weights and resets the Adam state. */
 VLBM_API int vlbm_lc_set_weights(vlbm_lc_t *lc, const float *w);
-/* in_scale[14] divides the 14 data channels (rho-1, u^theta, u^phi, T-1 and the ten
+/* in_scale[14] (> 0) divides the 14 data channels (rho-1, u^theta, u^phi, T-1 and the ten
  * differences in the order above; each scaled input is then clamped to [-8, 8]);
- * out_scale[3] multiplies the outputs. */
+ * out_scale[3] (>= 0) multiplies the outputs.  An output scale of 0 drops that output from
+ * predictions and corrections (e.g. 0 for drho: a velocity-only correction); training with
+ * it returns VLBM_ERR_ARG. */
 VLBM_API int vlbm_lc_set_scales(vlbm_lc_t *lc, const double *in_scale, const double *out_scale);
 /* Forward pass: outputs in physical units (drho not mean-corrected). */
 VLBM_API int vlbm_lc_predict(vlbm_lc_t *lc, const double *inputs, double *outputs);

@@ -283,7 +283,8 @@ int vlbm_lc_set_scales(vlbm_lc_t *n, const double *in_scale, const double *out_s
     for (int q = 0; q < LC_NSCALE; ++q)
         if (!(in_scale[q] > 0.0)) return lfail(n, VLBM_ERR_ARG, "scales must be > 0");
     for (int q = 0; q < 3; ++q)
-        if (!(out_scale[q] > 0.0)) return lfail(n, VLBM_ERR_ARG, "scales must be > 0");
+        if (!(out_scale[q] >= 0.0) || !std::isfinite(out_scale[q]))
+            return lfail(n, VLBM_ERR_ARG, "output scales must be >= 0");
     for (int q = 0; q < LC_NSCALE; ++q) n->in_scale[q] = (float)in_scale[q];
     if (n->g_exec) {   // the scales are kernel arguments of the captured rollout step
         cudaGraphExecDestroy(n->g_exec);
@@ -305,9 +306,18 @@ int vlbm_lc_predict(vlbm_lc_t *n, const double *inputs, double *outputs)
     return VLBM_OK;
 }
 
+// training needs every output scale nonzero (the loss is taken on the scaled outputs)
+static int check_trainable(vlbm_lc_t *n)
+{
+    for (int q = 0; q < 3; ++q)
+        if (!(n->out_scale[q] > 0.0f)) return lfail(n, VLBM_ERR_ARG, "an output with scale 0 cannot be trained");
+    return VLBM_OK;
+}
+
 int vlbm_lc_gradients(vlbm_lc_t *n, const double *inputs, const double *targets, double *loss, float *grad)
 {
     if (!n || !inputs || !targets) return VLBM_ERR_ARG;
+    if (int rc0 = check_trainable(n)) return rc0;
     int rc;
     if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n, n->d_in, n->stream)) || (rc = backward(n))) return rc;
     if (loss) LCK(n, cudaMemcpyAsync(loss, n->d_scal, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
@@ -319,6 +329,7 @@ int vlbm_lc_gradients(vlbm_lc_t *n, const double *inputs, const double *targets,
 int vlbm_lc_train_step(vlbm_lc_t *n, const double *inputs, const double *targets, float lr, double *loss)
 {
     if (!n || !inputs || !targets || !(lr > 0.0f)) return VLBM_ERR_ARG;
+    if (int rc0 = check_trainable(n)) return rc0;
     int rc;
     if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n, n->d_in, n->stream)) || (rc = backward(n))) return rc;
     n->t += 1;

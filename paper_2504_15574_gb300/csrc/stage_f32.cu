@@ -1058,13 +1058,15 @@ __global__ void __launch_bounds__(256, 3)
 // is (run, tile index within the run).  The run's parameters are copied into
 // shared memory per item.  tms holds 6 maps per run: the box maps of F, A, B, then
 // the tile-core maps of F, A, B.
-template <int TY, bool LIN>
+template <int TY, bool LIN, int Q>
 __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const RunF *runs, const CUtensorMap *tms,
-                                                                            const int2 *work, int ntiles, const VelC c,
+                                                                            const int2 *work, int ntiles,
+                                                                            const typename VelOf<Q>::type c,
                                                                             int stage, unsigned *err)
 {
+    typedef SmemT<TY, (Q == 3 ? 5 : NP2)> Smem;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    SmemT<TY> &S = *reinterpret_cast<SmemT<TY> *>(smem_raw);
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.bar[0])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1080,7 +1082,7 @@ __global__ void __launch_bounds__(TY * 32, 24 / TY) batch_stage_f32_kernel(const
         __syncthreads();
         const int tx = S.run.tiles_x;
         const CUtensorMap *tr = tms + 6 * w.x;
-        if (!stage_tile<TY, LIN, 4>(S.run, c, stage, tr + (stage - 1), tr + 3 + stage % 3, tr + 3, w.y % tx,
+        if (!stage_tile<TY, LIN, Q>(S.run, c, stage, tr + (stage - 1), tr + 3 + stage % 3, tr + 3, w.y % tx,
                                     w.y / tx, S, parity, err))
             return;
         parity ^= 1u;
@@ -1435,12 +1437,13 @@ __global__ void __launch_bounds__(FILT_THREADS) filter_f32_kernel(f2 *f, const L
 
 // One CTA per (run, filtered row) item of a batch and pair plane: the row of the
 // run's output array of `stage`.
-__global__ void __launch_bounds__(FILT_THREADS) batch_filter_f32_kernel(const RunF *runs, const int4 *items, int stage)
+__global__ void __launch_bounds__(FILT_THREADS) batch_filter_f32_kernel(const RunF *runs, const int4 *items, int vq,
+                                                                         int stage)
 {
     const int4 it = items[blockIdx.x];   // (run, row, block size, unused)
     const RunF &R = runs[it.x];
     f2 *out = (stage == 1) ? R.A : (stage == 2) ? R.B : R.F;
-    filter_row_f32(out, R.L, 4, it.y, it.z, blockIdx.y);
+    filter_row_f32(out, R.L, vq, it.y, it.z, blockIdx.y);
 }
 
 constexpr int DIAG_THREADS = 256;
@@ -1641,7 +1644,10 @@ cudaError_t prepare_one()
                                  (int)smem_bytes<TY, 3>());
         if (e) return e;
     }
-    return cudaFuncSetAttribute(batch_stage_f32_kernel<TY, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(batch_stage_f32_kernel<TY, LIN, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<TY, 3>());
+    if (e) return e;
+    return cudaFuncSetAttribute(batch_stage_f32_kernel<TY, LIN, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_bytes<TY>());
 }
 
@@ -1700,11 +1706,16 @@ void f32_fill_tile_tables(int q, int nt, float dt, const float *ds, const float 
     else fill_tile_tables_q<NP2>(nt, dt, ds, d2s, isp, sfc, row, rref, out);
 }
 
-int stage_f32_max_ctas_per_sm(int ty)
+int stage_f32_max_ctas_per_sm(int ty, int q)
 {
     int n = 0;
-    if (ty == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<4, false>, 128, smem_bytes<4>());
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<8, false>, 256, smem_bytes<8>());
+    if (q == 3) {
+        if (ty == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<4, false, 3>, 128, smem_bytes<4, 3>());
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<8, false, 3>, 256, smem_bytes<8, 3>());
+    } else {
+        if (ty == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<4, false, 4>, 128, smem_bytes<4>());
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_stage_f32_kernel<8, false, 4>, 256, smem_bytes<8>());
+    }
     return n;
 }
 
@@ -1778,16 +1789,30 @@ void launch_stage_f32_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, co
     launch_stage_q<3>(tm_in, tm_out, tm_f, run, c, stage, ty, lin, rows, err, s);
 }
 
+template <int Q>
+static void launch_batch_q(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles,
+                           const typename VelOf<Q>::type &c, int stage, int ty, bool lin, int ctas, unsigned *err,
+                           cudaStream_t s)
+{
+    if (ty == 4) {
+        if (lin) batch_stage_f32_kernel<4, true, Q><<<ctas, 128, smem_bytes<4, Q>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+        else batch_stage_f32_kernel<4, false, Q><<<ctas, 128, smem_bytes<4, Q>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+    } else {
+        if (lin) batch_stage_f32_kernel<8, true, Q><<<ctas, 256, smem_bytes<8, Q>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+        else batch_stage_f32_kernel<8, false, Q><<<ctas, 256, smem_bytes<8, Q>(), s>>>(runs, tms, work, ntiles, c, stage, err);
+    }
+}
+
 void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
                             int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s)
 {
-    if (ty == 4) {
-        if (lin) batch_stage_f32_kernel<4, true><<<ctas, 128, smem_bytes<4>(), s>>>(runs, tms, work, ntiles, c, stage, err);
-        else batch_stage_f32_kernel<4, false><<<ctas, 128, smem_bytes<4>(), s>>>(runs, tms, work, ntiles, c, stage, err);
-    } else {
-        if (lin) batch_stage_f32_kernel<8, true><<<ctas, 256, smem_bytes<8>(), s>>>(runs, tms, work, ntiles, c, stage, err);
-        else batch_stage_f32_kernel<8, false><<<ctas, 256, smem_bytes<8>(), s>>>(runs, tms, work, ntiles, c, stage, err);
-    }
+    launch_batch_q<4>(runs, tms, work, ntiles, c, stage, ty, lin, ctas, err, s);
+}
+
+void launch_batch_stage_f32_q3(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles,
+                               const VelC3 &c, int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s)
+{
+    launch_batch_q<3>(runs, tms, work, ntiles, c, stage, ty, lin, ctas, err, s);
 }
 
 double f32_state_scale(double eps)
@@ -1864,10 +1889,10 @@ void launch_fill_ghosts_f32(float2 *f, const Layout &L, int q, cudaStream_t s)
     fill_ghosts_f32_kernel<<<grid, 128, 0, s>>>(f, L, q);
 }
 
-void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int stage, cudaStream_t s)
+void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int q, int stage, cudaStream_t s)
 {
     if (nitems <= 0) return;
-    batch_filter_f32_kernel<<<dim3(nitems, NP2), FILT_THREADS, 0, s>>>(runs, items, stage);
+    batch_filter_f32_kernel<<<dim3(nitems, f32_pairs(q)), FILT_THREADS, 0, s>>>(runs, items, q, stage);
 }
 
 void launch_filter_f32(float2 *f, const Layout &L, int q, const int *rows, const int *blocks, int nrows,

@@ -592,6 +592,7 @@ void vlbm_default_options(vlbm_options *opt)
     opt->tile_rows = 0;
     opt->scheme = VLBM_WENO5;
     opt->komissarov = 0;
+    opt->velocity_set = VLBM_D2Q16;
 }
 
 int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt, const vlbm_options *opt,
@@ -1041,7 +1042,9 @@ struct vlbm_batch {
     int nfitems = 0;
     bool dirty = true;
     int guard = 1;
+    int q = 4;   // members' velocity set order (4: D2Q16, 3: D2Q9)
     VelC vc{};
+    VelC3 vc3{};
     unsigned *d_flags = nullptr, *h_flags = nullptr;
     cudaGraphExec_t g1 = nullptr, g16 = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -1103,6 +1106,7 @@ int batch_refresh(vlbm_batch_t *b)
         const int tx = runs[r].tiles_x, tyn = (h->nt + b->ty - 1) / b->ty;
         for (int t = 0; t < tx * tyn; ++t) work.push_back(make_int2(r, t));
         b->vc = h->vc;
+        b->vc3 = h->vc3;
     }
     b->ntiles = (int)work.size();
     std::vector<int4> fitems;
@@ -1136,7 +1140,7 @@ int batch_refresh(vlbm_batch_t *b)
 int batch_ctas(const vlbm_batch_t *b)
 {
     if (b->ctas_per_sm < 0) return std::max(1, b->ntiles);   // one CTA per work item
-    const int per = b->ctas_per_sm > 0 ? b->ctas_per_sm : stage_f32_max_ctas_per_sm(b->ty);
+    const int per = b->ctas_per_sm > 0 ? b->ctas_per_sm : stage_f32_max_ctas_per_sm(b->ty, b->q);
     return std::max(1, std::min(b->ntiles, per * b->nsm));
 }
 
@@ -1144,10 +1148,15 @@ void batch_enqueue_step(vlbm_batch_t *b)
 {
     const int ctas = batch_ctas(b);
     for (int st = 1; st <= 3; ++st) {
-        launch_batch_stage_f32(b->d_runs, b->d_tms, b->d_work, b->ntiles, b->vc, st, b->ty,
-                               b->runs.front()->scheme != VLBM_WENO5, ctas, b->d_flags, b->stream);
+        const bool lin = b->runs.front()->scheme != VLBM_WENO5;
+        if (b->q == 3)
+            launch_batch_stage_f32_q3(b->d_runs, b->d_tms, b->d_work, b->ntiles, b->vc3, st, b->ty, lin, ctas,
+                                      b->d_flags, b->stream);
+        else
+            launch_batch_stage_f32(b->d_runs, b->d_tms, b->d_work, b->ntiles, b->vc, st, b->ty, lin, ctas,
+                                   b->d_flags, b->stream);
         // one polar-filter launch over the filtered rows of every run
-        launch_batch_filter_f32(b->d_runs, b->d_fitems, b->nfitems, st, b->stream);
+        launch_batch_filter_f32(b->d_runs, b->d_fitems, b->nfitems, b->q, st, b->stream);
     }
 }
 
@@ -1173,7 +1182,8 @@ std::string batch_signature(const vlbm_batch_t *b)
     std::vector<std::pair<int, int>> g;
     for (const vlbm_t *h : b->runs) g.push_back({h->nt, h->np});
     std::sort(g.begin(), g.end());
-    std::string key = std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount) + "sm|";
+    std::string key = std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount) + "sm|" +
+                      (b->q == 3 ? "d2q9|" : "");
     for (size_t i = 0; i < g.size();) {
         size_t j = i;
         while (j < g.size() && g[j] == g[i]) ++j;
@@ -1247,8 +1257,12 @@ int vlbm_batch_create(int nruns, const int *n_theta, const int *n_phi, const dou
     if (o.precision != VLBM_FP32) return bfail(nullptr, VLBM_ERR_UNSUPPORTED, "batches run the FP32 path only");
     if (o.scheme == VLBM_WENO5 && o.komissarov)
         return bfail(nullptr, VLBM_ERR_UNSUPPORTED, "batches run the Komissarov flux with the upwind schemes only");
+    if (o.velocity_set != 0 && o.velocity_set != VLBM_D2Q16 && o.velocity_set != VLBM_D2Q9)
+        return bfail(nullptr, VLBM_ERR_ARG, "unknown velocity set");
+    const int vset = (o.velocity_set == VLBM_D2Q9) ? VLBM_D2Q9 : VLBM_D2Q16;
     vlbm_batch_t *b = new vlbm_batch_t();
     b->guard = o.guard ? 1 : 0;
+    b->q = (vset == VLBM_D2Q9) ? 3 : 4;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         delete b;
@@ -1268,7 +1282,7 @@ int vlbm_batch_create(int nruns, const int *n_theta, const int *n_phi, const dou
     o.tile_rows = 8;
     for (int r = 0; r < nruns; ++r) {
         vlbm_t *h = nullptr;
-        int rc = vlbm_create(n_theta[r], n_phi[r], VLBM_D2Q16, tau[r], dt[r], &o, &h);
+        int rc = vlbm_create(n_theta[r], n_phi[r], vset, tau[r], dt[r], &o, &h);
         if (rc) {
             std::string m = "run " + std::to_string(r) + ": " + vlbm_last_error(nullptr);
             vlbm_batch_destroy(b);
@@ -1320,7 +1334,8 @@ int vlbm_batch_get_populations(vlbm_batch_t *b, int run, double *f)
 int vlbm_batch_set_schedule(vlbm_batch_t *b, int tile_rows, int ctas_per_sm)
 {
     if (!b || (tile_rows != 4 && tile_rows != 8) || ctas_per_sm < -1) return bfail(b, VLBM_ERR_ARG, "bad schedule");
-    if (ctas_per_sm > stage_f32_max_ctas_per_sm(tile_rows)) return bfail(b, VLBM_ERR_ARG, "ctas_per_sm above occupancy");
+    if (ctas_per_sm > stage_f32_max_ctas_per_sm(tile_rows, b->q))
+        return bfail(b, VLBM_ERR_ARG, "ctas_per_sm above occupancy");
     if (tile_rows != b->ty) b->dirty = true;
     b->ty = tile_rows;
     b->ctas_per_sm = ctas_per_sm;
@@ -1415,7 +1430,7 @@ int vlbm_batch_tune(vlbm_batch_t *b, const char *cache_path, int *tile_rows, int
         }
         best = 1e300;
         for (int ty : {4, 8}) {
-            const int maxc = stage_f32_max_ctas_per_sm(ty);
+            const int maxc = stage_f32_max_ctas_per_sm(ty, b->q);
             for (int c = -1; c <= maxc; ++c) {
                 if (c == 0) continue;   // (0 is the occupancy limit, already among 1..maxc)
                 if ((rc = vlbm_batch_set_schedule(b, ty, c))) return rc;

@@ -178,7 +178,11 @@ void launch_stage_f32_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, co
 // maps of F, A, B, then the tile-core maps of F, A, B).
 void launch_batch_stage_f32(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles, const VelC &c,
                             int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s);
-int stage_f32_max_ctas_per_sm(int ty);
+// The same for D2Q9 members (five pair planes).
+void launch_batch_stage_f32_q3(const RunF *runs, const CUtensorMap *tms, const int2 *work, int ntiles,
+                               const VelC3 &c, int stage, int ty, bool lin, int ctas, unsigned *err, cudaStream_t s);
+// Resident CTAs per SM of the batch stage kernel for tile rows ty and velocity set order q.
+int stage_f32_max_ctas_per_sm(int ty, int q = 4);
 // The persistent stage kernel (8 tile rows, one CTA per resident slot, the next tile's copies in
 // flight during the cell phase):
 // its per-tile-row tables [stage 1..3][tile row] (f32_tile_table_bytes(q) each) are built on
@@ -214,7 +218,7 @@ void launch_fill_ghosts_f32(float2 *f, const Layout &L, int q, cudaStream_t s);
 void launch_filter_f32(float2 *f, const Layout &L, int q, const int *rows, const int *blocks, int nrows,
                        cudaStream_t s);
 // Polar filter of every (run, row, block size) item of a batch on the output array of `stage`.
-void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int stage, cudaStream_t s);
+void launch_batch_filter_f32(const RunF *runs, const int4 *items, int nitems, int q, int stage, cudaStream_t s);
 // FP64 diagnostics of an FP32 state (cph, sph: cos and sin of the column angles, FP64 [np]); out as
 // launch_diagnostics_f64.  part: diag_partials(L) doubles of scratch.
 void launch_diagnostics_f32(const float2 *f, const Layout &L, const double *sin_t, const double *cos_t,

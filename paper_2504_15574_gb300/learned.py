@@ -270,25 +270,41 @@ def train(setup: Setup, X, Y, epochs=4, lr=2e-3, seed=1, log=None, net=None):
     return net, hist
 
 
-def evaluate(setup: Setup, net, seeds, n_steps, spinup=20):
-    """Rollouts from the downsampled fine start: errors after n_steps coarse steps and wall times."""
+def evaluate(setup: Setup, net, seeds, n_steps, spinup=20, start="fine"):
+    """Rollouts of n_steps coarse steps after a spin-up of `spinup` coarse steps: errors against
+    the downsampled fine run and wall times.  start = "fine": the coarse runs start from the
+    downsampled fine state after the spin-up (the fine run does the spin-up); "analytic": every run
+    starts from the analytic start on its own grid at t = 0 and runs spin-up + n_steps (the
+    protocol of plain_runs_at)."""
     fb = setup.fine_batch(seeds)
     fb.step(spinup * setup.substeps)
-    starts = [downsample_populations(fb.get_populations(r), setup.factor) for r in range(len(seeds))]
+    if start == "fine":
+        starts = [downsample_populations(fb.get_populations(r), setup.factor) for r in range(len(seeds))]
     t0 = time.perf_counter()
     fb.step(n_steps * setup.substeps)
     t_fine = (time.perf_counter() - t0) / (n_steps * len(seeds))
     refs = [downsample(*fb.moments(r, with_T=True)) for r in range(len(seeds))]
     fb.close()
-    res = {"plain": [], "learned": []}
+    res = {"plain": [], "learned": [], "learned_u": []}
     times = {}
-    for mode in ("plain", "learned"):
+    for mode in ("plain", "learned", "learned_u"):
         cs = setup.coarse_solver()
         el = 0.0
+        if mode == "learned_u":
+            # the velocity-only correction: the same network with its density output dropped
+            out_scale = net.out_scale.copy()
+            net.set_scales(net.in_scale, (0.0, out_scale[1], out_scale[2]))
         for r in range(len(seeds)):
-            cs.set_populations(starts[r])
+            if start == "fine":
+                cs.set_populations(starts[r])
+            else:
+                cs.init_moments(*inputs.gaussian_vortices(*setup.coarse, run=seeds[r])[:3])
+                if mode != "plain":
+                    net.rollout(cs, spinup)
+                else:
+                    cs.step(spinup)
             t0 = time.perf_counter()
-            if mode == "learned":
+            if mode != "plain":
                 net.rollout(cs, n_steps)
             else:
                 cs.step(n_steps)
@@ -299,8 +315,10 @@ def evaluate(setup: Setup, net, seeds, n_steps, spinup=20):
                               "rho": rel_l2(rho - 1.0, ref[0] - 1.0)})
         times[mode] = el / (n_steps * len(seeds))
         cs.close()
+        if mode == "learned_u":
+            net.set_scales(net.in_scale, out_scale)
     # a coarse step stands for `substeps` fine steps; the batch advanced all seeds together
-    out = {"seeds": list(seeds), "coarse_steps": n_steps, "t_end": n_steps * setup.dt_c,
+    out = {"seeds": list(seeds), "coarse_steps": n_steps, "t_end": n_steps * setup.dt_c, "start": start,
            "grid_coarse": list(setup.coarse), "grid_fine": list(setup.fine),
            "vort_err_plain_per_seed": [e["vort"] for e in res["plain"]],
            "vort_err_learned_per_seed": [e["vort"] for e in res["learned"]],
@@ -308,10 +326,73 @@ def evaluate(setup: Setup, net, seeds, n_steps, spinup=20):
            "vort_err_learned": float(np.mean([e["vort"] for e in res["learned"]])),
            "rho_err_plain": float(np.mean([e["rho"] for e in res["plain"]])),
            "rho_err_learned": float(np.mean([e["rho"] for e in res["learned"]])),
+           "vort_err_learned_u_per_seed": [e["vort"] for e in res["learned_u"]],
+           "rho_err_learned_u_per_seed": [e["rho"] for e in res["learned_u"]],
+           "rho_err_plain_per_seed": [e["rho"] for e in res["plain"]],
+           "vort_err_learned_u": float(np.mean([e["vort"] for e in res["learned_u"]])),
+           "rho_err_learned_u": float(np.mean([e["rho"] for e in res["learned_u"]])),
            "ms_per_coarse_step_plain": times["plain"] * 1e3, "ms_per_coarse_step_learned": times["learned"] * 1e3,
            "ms_fine_per_coarse_step": t_fine * 1e3}
     out["speedup_learned_vs_fine"] = out["ms_fine_per_coarse_step"] / out["ms_per_coarse_step_learned"]
     return out
+
+
+def plain_runs_at(setup: Setup, seeds, n_steps, grids, spinup=20, start="analytic"):
+    """Plain FP32 runs at intermediate grids (integer multiples m of the coarse grid, m < factor)
+    to the time the learned rollouts of `evaluate` reach (spin-up + n_steps coarse steps, each grid
+    at its own clamped dt dividing the coarse one); their m x m block means on the coarse grid
+    against the fine run's.  start = "analytic": each grid from the analytic start on itself at
+    t = 0; "fine": from the fine state after the spin-up, block-averaged onto the grid (only for m
+    dividing the fine factor; other grids are skipped), as `evaluate` starts the coarse runs.
+    Returns per grid the mean vorticity and rho - 1 errors and the wall time per coarse-step span."""
+    fb = setup.fine_batch(seeds)
+    fb.step(spinup * setup.substeps)
+    fstart = [fb.get_populations(r) for r in range(len(seeds))] if start == "fine" else None
+    fb.step(n_steps * setup.substeps)
+    refs = [downsample(*fb.moments(r, with_T=True)) for r in range(len(seeds))]
+    fb.close()
+    out = []
+    for m in grids:
+        if start == "fine" and setup.factor % m:
+            continue
+        g = (setup.coarse[0] * m, setup.coarse[1] * m)
+        sub = setup.substeps if m == setup.factor else \
+            math.ceil(setup.dt_c / clamped_dt(*g, setup.tau) - 1e-9)
+        dt = setup.dt_c / sub
+        ev, er, el = [], [], 0.0
+        for k, sd in enumerate(seeds):
+            s = vlbm.Solver(*g, setup.tau, dt, precision="fp32", polar_filter=setup.polar_filter, guard=False)
+            if start == "fine":
+                s.set_populations(downsample_populations(fstart[k], setup.factor // m))
+            else:
+                s.init_moments(*inputs.gaussian_vortices(*g, run=sd)[:3])
+                s.step(spinup * sub)
+            t0 = time.perf_counter()
+            s.step(n_steps * sub)
+            el += time.perf_counter() - t0
+            rho, ut, up, T = s.moments(with_T=True)
+            s.close()
+            d = downsample(rho, ut, up, T, factor=m) if m > 1 else (rho, ut, up, T)
+            ref = refs[seeds.index(sd)]
+            ev.append(rel_l2(vorticity(d[1], d[2]), vorticity(ref[1], ref[2])))
+            er.append(rel_l2(d[0] - 1.0, ref[0] - 1.0))
+        out.append({"grid": list(g), "steps_per_coarse_step": sub, "vort_err": float(np.mean(ev)),
+                    "rho_err": float(np.mean(er)), "vort_err_per_seed": ev,
+                    "ms_per_coarse_step": el / (n_steps * len(seeds)) * 1e3})
+    return out
+
+
+def equal_error_grid(points, target):
+    """The resolution multiple m* at which the plain error equals `target`, and the plain time per
+    coarse-step span there, interpolated log-log between the two grids that bracket it; None if no
+    pair brackets it.  points: [(m, error, ms)] in increasing m."""
+    for (m0, e0, t0), (m1, e1, t1) in zip(points, points[1:]):
+        if (e0 - target) * (e1 - target) <= 0 and e0 > 0 and e1 > 0 and e0 != e1:
+            a = (math.log(target) - math.log(e0)) / (math.log(e1) - math.log(e0))
+            m = math.exp(math.log(m0) + a * (math.log(m1) - math.log(m0)))
+            ms = math.exp(math.log(t0) + a * (math.log(t1) - math.log(t0)))
+            return m, ms
+    return None
 
 
 def main(argv=None):
@@ -328,6 +409,12 @@ def main(argv=None):
     ap.add_argument("--eval-seeds", type=int, default=4)
     ap.add_argument("--eval-steps", type=int, nargs="+", default=[300, 1000])
     ap.add_argument("--out", default=None)
+    ap.add_argument("--start", choices=["fine", "analytic"], default="fine",
+                    help="rollout starts: the downsampled fine state after the spin-up, or every grid's own analytic start")
+    ap.add_argument("--save-net", default=None, help="write the trained weights and scales (.npz)")
+    ap.add_argument("--load-net", default=None, help="read weights and scales (.npz) instead of making data and training")
+    ap.add_argument("--equal-error", type=int, nargs="*", default=[],
+                    help="resolution multiples of the coarse grid for plain runs at each horizon (e.g. 2 3)")
     ap.add_argument("--timing-steps", type=int, default=0,
                     help="only time this many corrected coarse steps of an untrained network (no data, no training)")
     a = ap.parse_args(argv)
@@ -349,24 +436,47 @@ def main(argv=None):
         net.close()
         return
     seeds = list(range(1000, 1000 + a.train_seeds))
-    t0 = time.perf_counter()
-    if a.targets == "drift":
-        X, Y = make_drift_samples(setup, seeds, a.windows, spinup=a.spinup)
+    if a.load_net:
+        z = np.load(a.load_net)
+        net = vlbm.LearnedCorrection(*setup.coarse, seed=1, in_scale=z["in_scale"], out_scale=z["out_scale"])
+        net.set_weights(z["weights"])
+        X, hist, t_data, t_train = [], [], 0.0, 0.0
     else:
-        X, Y = make_samples(setup, seeds, a.steps, spinup=a.spinup)
-    t_data = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    net, hist = train(setup, X, Y, epochs=a.epochs, log=print)
-    t_train = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        if a.targets == "drift":
+            X, Y = make_drift_samples(setup, seeds, a.windows, spinup=a.spinup)
+        else:
+            X, Y = make_samples(setup, seeds, a.steps, spinup=a.spinup)
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        net, hist = train(setup, X, Y, epochs=a.epochs, log=print)
+        t_train = time.perf_counter() - t0
+    if a.save_net:
+        np.savez(a.save_net, weights=net.get_weights(), in_scale=net.in_scale, out_scale=net.out_scale)
     out = {"grid_coarse": list(setup.coarse), "grid_fine": list(setup.fine), "polar_filter": setup.polar_filter,
            "dt_coarse": setup.dt_c, "fine_steps_per_coarse_step": setup.substeps, "targets": a.targets,
            "samples": int(len(X)), "loss_history": hist, "seconds_data": t_data, "seconds_train": t_train,
            "horizons": []}
     for n in a.eval_steps:
-        res = evaluate(setup, net, list(range(5000, 5000 + a.eval_seeds)), n, spinup=a.spinup)
+        eseeds = list(range(5000, 5000 + a.eval_seeds))
+        res = evaluate(setup, net, eseeds, n, spinup=a.spinup, start=a.start)
+        if a.equal_error:
+            pr = plain_runs_at(setup, eseeds, n, sorted(a.equal_error), spinup=a.spinup, start=a.start)
+            res["plain_grids"] = pr
+            pts = [(1, res["vort_err_plain"], res["ms_per_coarse_step_plain"])] + \
+                  [(p["grid"][0] // setup.coarse[0], p["vort_err"], p["ms_per_coarse_step"]) for p in pr] + \
+                  [(setup.factor, 1e-300, res["ms_fine_per_coarse_step"])]
+            res["equal_error"] = {}
+            for key in ("learned", "learned_u"):
+                hit = equal_error_grid(pts[:-1], res[f"vort_err_{key}"])
+                res["equal_error"][key] = None if hit is None else {
+                    "multiple": hit[0], "ms_plain": hit[1],
+                    "time_ratio_plain_over_learned": hit[1] / res[f"ms_per_coarse_step_{'learned'}"]}
         out["horizons"].append(res)
-        print(json.dumps({k: res[k] for k in ("coarse_steps", "vort_err_plain", "vort_err_learned", "rho_err_plain",
-                                              "rho_err_learned", "speedup_learned_vs_fine")}))
+        print(json.dumps({k: res[k] for k in ("coarse_steps", "vort_err_plain", "vort_err_learned", "vort_err_learned_u",
+                                              "rho_err_plain", "rho_err_learned", "rho_err_learned_u",
+                                              "speedup_learned_vs_fine") + (("plain_grids", "equal_error")
+                                                                            if a.equal_error else ())}))
     line = json.dumps(out)
     print(line)
     if a.out:

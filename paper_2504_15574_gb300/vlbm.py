@@ -37,7 +37,7 @@ class vlbm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("weno_eps", ctypes.c_double), ("radius", ctypes.c_double),
                 ("polar_filter", ctypes.c_int), ("guard", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("rho_ref", ctypes.c_double), ("tile_rows", ctypes.c_int), ("scheme", ctypes.c_int),
-                ("komissarov", ctypes.c_int)]
+                ("komissarov", ctypes.c_int), ("velocity_set", ctypes.c_int)]
 
 
 SCHEMES = {"weno5": 0, "u1": 1, "u2": 2, "u3": 3}
@@ -324,7 +324,7 @@ class Batch:
     grids: list of (n_theta, n_phi); tau, dt: scalars or per-run sequences."""
 
     def __init__(self, grids, tau, dt, eps=1e-6, R=1.0, polar_filter=False, guard=True, stream=None,
-                 scheme="weno5", komissarov=False):
+                 scheme="weno5", komissarov=False, velocity_set="d2q16"):
         lib = load()
         n = len(grids)
         self.grids = [(int(a), int(b)) for a, b in grids]
@@ -341,6 +341,8 @@ class Batch:
         o.stream = stream
         o.scheme = SCHEMES[scheme]
         o.komissarov = int(bool(komissarov))
+        o.velocity_set = VLBM_D2Q9 if velocity_set == "d2q9" else VLBM_D2Q16
+        self.q = 3 if velocity_set == "d2q9" else 4
         self.b = _H()
         _bcheck(lib.vlbm_batch_create(n, nt, np_, _p(taus), _p(dts), ctypes.byref(o), ctypes.byref(self.b)))
 
@@ -369,7 +371,7 @@ class Batch:
         return (rho, ut, up, T) if with_T else (rho, ut, up)
 
     def get_populations(self, run):
-        f = np.empty((NK,) + self.grids[run])
+        f = np.empty((self.q * self.q,) + self.grids[run])
         _bcheck(load().vlbm_batch_get_populations(self.b, int(run), _p(f)), self.b)
         return f
 

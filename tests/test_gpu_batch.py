@@ -120,3 +120,36 @@ def test_batch_rejects_fp64(V):
         t = np.array([1e-3])
         V._bcheck(V.load().vlbm_batch_create(1, nt, np_, V._p(t), V._p(t), ctypes.byref(o), ctypes.byref(h)))
     assert e.value.code == V.VLBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("schedule,scheme,filt", [((8, 0), "weno5", False), ((8, -1), "weno5", True),
+                                                  ((4, 2), "u3", True)])
+def test_d2q9_batch_members_equal_standalone_solvers_bitwise(V, schedule, scheme, filt):
+    """A batch of D2Q9 runs (App. A.1; five pair planes per member, the batched filter over
+    them): every member advances as a standalone D2Q9 FP32 solver with the same tile rows, bit
+    for bit.  (With 8-row tiles the D2Q9 tile walks its phi and theta faces on different warps
+    into two tendency arrays that the cell adds; with 4-row tiles on the same warp into one:
+    the last bit of a flux difference may differ between the two tile shapes.)"""
+    vmax = 3.0 ** 0.5
+    dts = [min(0.25 * min(np.pi / nt, np.sin(np.pi / nt / 2) * 2 * np.pi / np_) / vmax, TAU) for nt, np_ in GRIDS]
+    kw = dict(polar_filter=filt, scheme=scheme, komissarov=scheme != "weno5")
+    b = V.Batch(GRIDS, TAU, dts, velocity_set="d2q9", **kw)
+    for r, (nt, np_) in enumerate(GRIDS):
+        b.init_moments(r, *inputs.gaussian_vortices(nt, np_, run=200 + r))
+    b.set_schedule(*schedule)
+    b.step(20)
+    for r, (nt, np_) in enumerate(GRIDS):
+        s = V.Solver(nt, np_, TAU, dts[r], precision="fp32", velocity_set="d2q9", tile_rows=schedule[0], **kw)
+        s.init_moments(*inputs.gaussian_vortices(nt, np_, run=200 + r))
+        s.step(20)
+        for x, y in zip(b.moments(r), s.moments()):
+            assert np.array_equal(x, y), (r, schedule)
+        assert np.array_equal(b.get_populations(r), s.get_populations())
+        s.close()
+    b.close()
+
+
+def test_batch_refuses_weno_with_komissarov(V):
+    with pytest.raises(V.VlbmError) as ex:
+        V.Batch(GRIDS, TAU, 1e-4, komissarov=True)
+    assert ex.value.code == V.VLBM_ERR_UNSUPPORTED
