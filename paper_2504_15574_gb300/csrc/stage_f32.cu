@@ -950,7 +950,7 @@ __global__ void __launch_bounds__(256, 3)
     stage_f32_persist_kernel(const __grid_constant__ CUtensorMap tm, const __grid_constant__ CUtensorMap tmo,
                              const __grid_constant__ CUtensorMap tmf, const RunF R,
                              const typename VelOf<Q>::type c, int stage, const TileRows rows,
-                             const TabT<8, (Q == 3 ? 5 : NP2)> *tabs, unsigned *err)
+                             const TabT<8, (Q == 3 ? 5 : NP2)> *tabs, unsigned *err, unsigned *ctr)
 {
     constexpr int TY = 8;
     constexpr int NPQ = (Q == 3) ? 5 : NP2;
@@ -1011,13 +1011,17 @@ __global__ void __launch_bounds__(256, 3)
             "r"(smem_u32(&S.barF))
             : "memory");
     };
+    // Tiles are handed out dynamically: the first is blockIdx.x, each further one the next
+    // value of the launch's counter ctr[0] (+ G), taken when its copies are issued; the CTA that
+    // leaves last (counted in ctr[1]) resets both counters for the next launch of this slot.
+    __shared__ int next_tile;
     int t = (int)blockIdx.x;
     if (tid == 0 && t < total) {
         issue_box(t, 0);
         if (stage != 1) issue_f(t);
     }
     const float dte = stage_dte(stage, R.dt);
-    for (int k = 0; t < total; ++k, t += G) {
+    for (int k = 0; t < total; ++k) {
         const int tb = k & 1;
         const unsigned par = k & 1;   // phase of tile k on the box barrier and on the F barrier
         const bool box_ok = __syncthreads_and(wait_phase(&S.bar[0], par, R.wait_ns));
@@ -1030,13 +1034,18 @@ __global__ void __launch_bounds__(256, 3)
             f2 Gc[NPQ];
             load_cell_g<TY, NPQ>(S, 0, Gc);
             __syncthreads();   // the box buffer is free: the next tile's copies go now
-            next_box = t + G < total;
-            if (tid == 0 && next_box) issue_box(t + G, tb ^ 1);
+            if (tid == 0) {
+                const int tn = G + (int)atomicAdd(&ctr[0], 1u);
+                next_tile = tn;
+                next_box = tn < total;
+                if (next_box) issue_box(tn, tb ^ 1);
+            }
             if (stage != 1) ok = __syncthreads_and(wait_phase(&S.barF, par, R.wait_ns));
             if (ok) {
                 tile_cells<TY, LIN, Q>(R, c, stage, dte, &tmo, bx, by, S, 0, tb, Gc);
-                __syncthreads();   // this tile's tables and the staging buffer are free
-                if (tid == 0 && stage != 1 && t + G < total) issue_f(t + G);
+                __syncthreads();   // this tile's tables and the staging buffer are free; next_tile is set
+                t = next_tile;
+                if (tid == 0 && stage != 1 && t < total) issue_f(t);
                 continue;
             }
         }
@@ -1050,7 +1059,14 @@ __global__ void __launch_bounds__(256, 3)
             if (stage != 1) wait_phase(&S.barF, par, LIMIT_NS);
         }
         __syncthreads();
-        return;
+        break;
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&ctr[1], 1u) == (unsigned)G - 1u) {
+            atomicExch(&ctr[0], 0u);
+            atomicExch(&ctr[1], 0u);
+        }
     }
 }
 
@@ -1722,7 +1738,7 @@ int stage_f32_max_ctas_per_sm(int ty, int q)
 template <int Q>
 static void launch_persist_q(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
                              const RunF &run, const typename VelOf<Q>::type &c, int stage, bool lin, TileRows rows,
-                             const void *tabs, unsigned *err, cudaStream_t s)
+                             const void *tabs, unsigned *err, unsigned *ctr, cudaStream_t s)
 {
     if (rows.count < 0) rows = TileRows{0, (run.L.nt + 7) / 8, 1 << 30, 0};
     if (rows.count == 0) return;
@@ -1733,25 +1749,25 @@ static void launch_persist_q(const CUtensorMap &tm_in, const CUtensorMap &tm_out
     const size_t smem = persist_smem<Q>();
     if (lin) {
         const int grid = std::min(total, persist_grid<true, Q>());
-        stage_f32_persist_kernel<true, Q><<<grid, 256, smem, s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, tab, err);
+        stage_f32_persist_kernel<true, Q><<<grid, 256, smem, s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, tab, err, ctr);
     } else {
         const int grid = std::min(total, persist_grid<false, Q>());
-        stage_f32_persist_kernel<false, Q><<<grid, 256, smem, s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, tab, err);
+        stage_f32_persist_kernel<false, Q><<<grid, 256, smem, s>>>(tm_in, tm_out, tm_f, run, c, stage, rows, tab, err, ctr);
     }
 }
 
 void launch_stage_f32_persist(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
                               const RunF &run, const VelC &c, int stage, bool lin, const void *tabs, unsigned *err,
-                              cudaStream_t s, TileRows rows)
+                              unsigned *ctr, cudaStream_t s, TileRows rows)
 {
-    launch_persist_q<4>(tm_in, tm_out, tm_f, run, c, stage, lin, rows, tabs, err, s);
+    launch_persist_q<4>(tm_in, tm_out, tm_f, run, c, stage, lin, rows, tabs, err, ctr, s);
 }
 
 void launch_stage_f32_persist_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
                                  const RunF &run, const VelC3 &c, int stage, bool lin, const void *tabs,
-                                 unsigned *err, cudaStream_t s, TileRows rows)
+                                 unsigned *err, unsigned *ctr, cudaStream_t s, TileRows rows)
 {
-    launch_persist_q<3>(tm_in, tm_out, tm_f, run, c, stage, lin, rows, tabs, err, s);
+    launch_persist_q<3>(tm_in, tm_out, tm_f, run, c, stage, lin, rows, tabs, err, ctr, s);
 }
 
 template <int Q>

@@ -399,7 +399,9 @@ int encode_map(vlbm_t *h, CUtensorMap *m, void *base, int ty = 0, bool core = fa
     return VLBM_OK;
 }
 
-void launch_stage_f32_any(vlbm_t *h, int st, cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0})
+// slot: the persistent kernel's tile counters (0: whole-grid launches, 1: polar band, 2: interior band;
+// launches that may overlap take different slots)
+void launch_stage_f32_any(vlbm_t *h, int st, cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0}, int slot = 0)
 {
     const CUtensorMap &tm = (st == 1) ? h->tmF : (st == 2) ? h->tmA : h->tmB;
     const CUtensorMap &tmo = (st == 1) ? h->tmAc : (st == 2) ? h->tmBc : h->tmFc;
@@ -408,10 +410,12 @@ void launch_stage_f32_any(vlbm_t *h, int st, cudaStream_t s, TileRows rows = Til
         // the upwind schemes: the persistent kernel, whose next tile's copies are in flight during
         // the cell phase (their lighter faces leave the one-tile kernel's loads exposed; for WENO-5
         // the one-tile kernel with three resident CTAs per SM measured faster)
+        unsigned *ctr = h->d_ctr + 2 * slot;
         if (h->vd.q == 3)
-            launch_stage_f32_persist_q3(tm, tmo, h->tmFc, h->run, h->vc3, st, lin, h->d_tabs, h->d_flags, s, rows);
+            launch_stage_f32_persist_q3(tm, tmo, h->tmFc, h->run, h->vc3, st, lin, h->d_tabs, h->d_flags, ctr, s,
+                                        rows);
         else
-            launch_stage_f32_persist(tm, tmo, h->tmFc, h->run, h->vc, st, lin, h->d_tabs, h->d_flags, s, rows);
+            launch_stage_f32_persist(tm, tmo, h->tmFc, h->run, h->vc, st, lin, h->d_tabs, h->d_flags, ctr, s, rows);
         return;
     }
     if (h->vd.q == 3) launch_stage_f32_q3(tm, tmo, h->tmFc, h->run, h->vc3, st, h->ty, lin, h->d_flags, s, rows);
@@ -444,11 +448,11 @@ void enqueue_split_step(vlbm_t *h)
     for (int st = 1; st <= 3; ++st) {
         void *out = (st == 1) ? h->A : (st == 2) ? h->B : h->F;
         if (st > 1) cudaStreamWaitEvent(s2, evI[st - 2], 0);
-        launch_stage_f32_any(h, st, s2, polar);
+        launch_stage_f32_any(h, st, s2, polar, 1);
         cudaEventRecord(evP[st - 1], s2);
         launch_filter_f32((float2 *)out, h->L, h->vd.q, h->d_frows, h->d_fblocks, h->nfrows, s2);
         if (st > 1) cudaStreamWaitEvent(s, evP[st - 2], 0);
-        launch_stage_f32_any(h, st, s, inner);
+        launch_stage_f32_any(h, st, s, inner, 2);
         cudaEventRecord(evI[st - 1], s);
     }
     // the step's pole budget: its partials come from the polar launches, all on stream2
@@ -752,6 +756,7 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
         const int ntx = (n_phi + F32_TILE_COLS - 1) / F32_TILE_COLS;
         if ((rc = upload(h, &h->d_cph, cph.data(), cph.size())) || (rc = upload(h, &h->d_sph, sph.data(), sph.size())) ||
             (rc = dalloc(h, (void **)&h->d_pole_part, sizeof(double) * 3 * 2 * (size_t)ntx)) ||
+            (rc = dalloc(h, (void **)&h->d_ctr, sizeof(unsigned) * 6)) ||
             (rc = dalloc(h, (void **)&h->d_scalar, sizeof(double) * 8)))
             return bail(rc);
     }
@@ -1012,7 +1017,7 @@ void vlbm_destroy(vlbm_t *h)
     void *bufs[] = {h->F, h->A, h->B, h->d_sin_ext, h->d_cot, h->d_sin_t, h->d_cos_t, h->d_sin_f, h->d_cos_f, h->d_isp,
                     h->d_sfc, h->d_ft, h->d_fp,
                     h->d_rref, h->d_dsin, h->d_d2sin, h->d_tabs, h->d_kss, h->d_ikss, h->d_cph, h->d_sph,
-                    h->d_pole_part, h->d_scalar,
+                    h->d_pole_part, h->d_scalar, h->d_ctr,
                     h->d_row, h->d_frows, h->d_fblocks, h->d_pole, h->d_budget, h->d_mom, h->d_dense,
                     h->d_part, h->d_diag, h->d_flags};
     for (void *p : bufs)

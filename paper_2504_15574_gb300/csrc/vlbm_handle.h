@@ -38,6 +38,7 @@ struct vlbm {
     double *d_pole_part = nullptr;                    // FP32 pole partials [3][2][tiles_x] (RunF.pole_part)
     double pole_ref[2] = {0.0, 0.0};                  // reference state's pole fluxes (north, south)
     double *d_scalar = nullptr;                       // device scratch: the reference density
+    unsigned *d_ctr = nullptr;                        // persistent stage kernel: tile counters, 3 slots x 2
     unsigned long long wait_ns = 1000000000ull;       // FP32 stage kernels: first wait limit on a tile's copies
     // polar filter
     int *d_frows = nullptr, *d_fblocks = nullptr;

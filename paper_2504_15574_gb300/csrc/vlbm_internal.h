@@ -191,12 +191,14 @@ int stage_f32_max_ctas_per_sm(int ty, int q = 4);
 size_t f32_tile_table_bytes(int q);
 void f32_fill_tile_tables(int q, int nt, float dt, const float *ds, const float *d2s, const float *isp,
                           const float *sfc, const RowF *row, const float2 *rref, unsigned char *out);
+// ctr: two zeroed unsigned counters per launch slot (launches that may run at the same time need
+// different slots); the kernel leaves them zeroed.
 void launch_stage_f32_persist(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
                               const RunF &run, const VelC &c, int stage, bool lin, const void *tabs, unsigned *err,
-                              cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0});
+                              unsigned *ctr, cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0});
 void launch_stage_f32_persist_q3(const CUtensorMap &tm_in, const CUtensorMap &tm_out, const CUtensorMap &tm_f,
                                  const RunF &run, const VelC3 &c, int stage, bool lin, const void *tabs,
-                                 unsigned *err, cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0});
+                                 unsigned *err, unsigned *ctr, cudaStream_t s, TileRows rows = TileRows{0, -1, 0, 0});
 
 // State scale k of the FP32 storage for WENO regulariser eps: the power of two nearest
 // 1 / (2 sqrt(eps)), so that 4 eps k^2 lies in [1/2, 2].
