@@ -73,15 +73,16 @@ def test_create_rejects_bad_arguments_before_the_gpu(lib, args, code):
     assert vlbm.vlbm_last_error()
 
 
-@pytest.mark.parametrize("velocity_set", [3, 4])
-def test_create_refuses_fp32_weno_with_komissarov_before_the_gpu(lib, velocity_set):
+@pytest.mark.parametrize("velocity_set", ["d2q16", "d2q9"])
+def test_batch_refuses_weno_with_komissarov_before_the_gpu(lib, velocity_set):
+    # single runs take WENO-5 with the Komissarov theta flux on both paths; batches
+    # offer that flux with the upwind schemes only
     from paper_2504_15574_gb300 import vlbm
-    o = vlbm.vlbm_default_options()
-    o.precision = vlbm.VLBM_FP32
-    o.komissarov = 1
     with pytest.raises(vlbm.VlbmError) as e:
-        vlbm.vlbm_create(32, 64, velocity_set, 0.1, 1e-3, o)
+        vlbm.Batch([(32, 64), (16, 32)], 0.1, 1e-3, scheme="weno5", komissarov=True,
+                   velocity_set=velocity_set)
     assert e.value.code == vlbm.VLBM_ERR_UNSUPPORTED
+    assert "upwind" in str(e.value)
 
 
 def test_null_handles_are_argument_errors(lib):
