@@ -11,6 +11,15 @@ condition of arXiv 2504.15574 Sec. 3.6 applied to moments); loss = the
 sin(theta)-area-weighted mean over cells and the 3 channels of
 (y - target / out_scale)^2.  Parameters are one flat FP32/FP64 vector, per layer
 W[co][ci][3][3] then b[co].
+
+Output forms.  "direct": the three outputs are (drho, du^theta, du^phi) / out_scale.
+"stream": output 0 times out_scale[0] is a stream function psi on the cell grid and
+the correction is its curl, du = (d_phi psi / (R sin theta), -d_theta psi / R), in
+centred differences with psi continued across a pole as a scalar (the row on the
+opposite meridian); drho = 0.  The discrete velocity has zero centred divergence, so
+the correction moves the vorticity without launching sound waves.  Its loss is the
+sin(theta)-area-weighted mean over cells and the 2 velocity channels of
+((du - target) / out_scale)^2.
 """
 from __future__ import annotations
 
@@ -160,15 +169,59 @@ def forward(params, inputs, in_scale, quantize=None):
     return x, cache
 
 
-def loss_and_grad(params, inputs, targets, in_scale, out_scale, quantize=None):
+def stream_velocity(psi, R=1.0):
+    """The curl of a stream function psi [H][W] on the cell grid: (du^theta, du^phi) =
+    (d_phi psi / (R sin theta), -d_theta psi / R) with centred differences; beyond a pole
+    psi is the row on the opposite meridian (a scalar: no sign change)."""
+    H, W = psi.shape
+    dth, dph = math.pi / H, 2.0 * math.pi / W
+    sin_t = np.sin((np.arange(H) + 0.5) * dth)
+    e = pad(psi[None], [])[0]
+    ut = (e[1:-1, 2:] - e[1:-1, :-2]) / (2.0 * R * dph * sin_t[:, None])
+    up = -(e[2:, 1:-1] - e[:-2, 1:-1]) / (2.0 * R * dth)
+    return ut, up
+
+
+def stream_velocity_adjoint(gt, gp, R=1.0):
+    """The gradient with respect to psi of sum(gt du^theta + gp du^phi), du = stream_velocity(psi)."""
+    H, W = gt.shape
+    dth, dph = math.pi / H, 2.0 * math.pi / W
+    sin_t = np.sin((np.arange(H) + 0.5) * dth)
+    ge = np.zeros((H + 2, W + 2))
+    a = gt / (2.0 * R * dph * sin_t[:, None])
+    ge[1:-1, 2:] += a
+    ge[1:-1, :-2] -= a
+    b = gp / (2.0 * R * dth)
+    ge[2:, 1:-1] -= b
+    ge[:-2, 1:-1] += b
+    return unpad(ge[None], [])[0]
+
+
+def outputs(y, out_scale, form="direct", R=1.0):
+    """The correction (drho, du^theta, du^phi) [3][H][W] in physical units from the net output."""
+    if form == "direct":
+        return np.stack([y[c] * out_scale[c] for c in range(3)])
+    ut, up = stream_velocity(y[0] * out_scale[0], R)
+    return np.stack([np.zeros_like(ut), ut, up])
+
+
+def loss_and_grad(params, inputs, targets, in_scale, out_scale, quantize=None, form="direct", R=1.0):
     """Loss and d loss / d params by explicit backpropagation."""
     y, cache = forward(params, inputs, in_scale, quantize)
     H, W = y.shape[1:]
     aw = area_weights(H, W)
-    t = np.stack([targets[c] / out_scale[c] for c in range(3)])
-    r = y - t
-    loss = float((aw[None] * r * r).sum() / 3.0)
-    g = 2.0 * aw[None] * r / 3.0
+    if form == "direct":
+        t = np.stack([targets[c] / out_scale[c] for c in range(3)])
+        r = y - t
+        loss = float((aw[None] * r * r).sum() / 3.0)
+        g = 2.0 * aw[None] * r / 3.0
+    else:
+        ut, up = stream_velocity(y[0] * out_scale[0], R)
+        rt = (ut - targets[1]) / out_scale[1]
+        rp = (up - targets[2]) / out_scale[2]
+        loss = float((aw * (rt * rt + rp * rp)).sum() / 2.0)
+        g = np.zeros_like(y)
+        g[0] = out_scale[0] * stream_velocity_adjoint(aw * rt / out_scale[1], aw * rp / out_scale[2], R)
     grads = []
     layers = unflatten(params)
     for l in range(len(LAYERS) - 1, -1, -1):

@@ -88,3 +88,79 @@ def test_theta_differences_continue_smooth_fields_across_the_poles():
     assert np.allclose(L.difference(up, True, L.D6, 0), 0.0, atol=1e-12)
     # the wrong sign rule (a velocity treated as a scalar) breaks it at the pole rows
     assert not np.allclose(L.difference(ut, False, L.D6, 0), lam ** 3 * ut, atol=1e-6)
+
+
+# ---- the stream-function output form -------------------------------------------------------
+
+def _grid(H, W):
+    th = (np.arange(H) + 0.5) * np.pi / H
+    ph = (np.arange(W) + 0.5) * 2 * np.pi / W
+    return np.meshgrid(th, ph, indexing="ij"), np.pi / H, 2 * np.pi / W
+
+
+@pytest.mark.parametrize("R", [1.0, 2.5])
+def test_stream_velocity_of_rotations_is_their_centred_difference_in_closed_form(R):
+    # psi = cos(theta): solid rotation about the axis, du^phi = sin(theta) sin(dth)/dth / R on
+    # every row (cos is even, so the pole continuation is cos itself); psi = sin(theta) cos(phi):
+    # rotation about a horizontal axis, odd across a pole exactly like its opposite-meridian image
+    H, W = 10, 16
+    (TH, PH), dth, dph = _grid(H, W)
+    ut, up = L.stream_velocity(np.cos(TH), R)
+    assert np.allclose(ut, 0.0, atol=1e-14)
+    assert np.allclose(up, np.sin(TH) * np.sin(dth) / dth / R, rtol=1e-12, atol=0)
+    ut, up = L.stream_velocity(np.sin(TH) * np.cos(PH), R)
+    assert np.allclose(ut, -np.sin(PH) * np.sin(dph) / dph / R, rtol=1e-12, atol=1e-15)
+    assert np.allclose(up, -np.cos(TH) * np.cos(PH) * np.sin(dth) / dth / R, rtol=1e-12, atol=1e-15)
+
+
+def test_stream_velocity_has_zero_centred_divergence_including_the_pole_rows():
+    # div u = (d_theta (sin u^theta) + d_phi u^phi) / (R sin theta) in centred differences, the
+    # velocity continued across a pole as a vector (opposite meridian, components negated)
+    H, W, R = 8, 12, 1.7
+    rng = np.random.default_rng(3)
+    psi = rng.normal(size=(H, W))
+    ut, up = L.stream_velocity(psi, R)
+    (TH, _), dth, dph = _grid(H, W)
+    st = np.sin(TH[:, 0])
+    ute = L.pad(ut[None], [0])[0]
+    upe = L.pad(up[None], [0])[0]
+    ste = np.concatenate([[-st[0]], st, [-st[-1]]])   # sin theta at the ghost rows: negative
+    flux = ste[:, None] * ute
+    div = ((flux[2:, 1:-1] - flux[:-2, 1:-1]) / (2 * dth) + (upe[1:-1, 2:] - upe[1:-1, :-2]) / (2 * dph)) / (R * st[:, None])
+    assert np.abs(div).max() <= 1e-12 * np.abs(ut).max()
+    # a velocity that is not a curl (du^theta = cos(theta)) has a divergence there
+    flux = ste[:, None] * L.pad(np.cos(TH)[None], [0])[0]
+    assert np.abs((flux[2:, 1:-1] - flux[:-2, 1:-1])).max() > 0.1
+
+
+def test_stream_velocity_adjoint_is_the_transpose():
+    H, W, R = 7, 10, 1.3
+    rng = np.random.default_rng(4)
+    psi, gt, gp = rng.normal(size=(3, H, W))
+    ut, up = L.stream_velocity(psi, R)
+    lhs = (gt * ut + gp * up).sum()
+    rhs = (psi * L.stream_velocity_adjoint(gt, gp, R)).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+
+
+def test_stream_form_backprop_matches_finite_differences():
+    H, W = 6, 8
+    x, t = _sample(H, W, 5)
+    p = L.init_params(9)
+    p[-3:] = [0.02, 0.0, 0.0]
+    ins, outs = [1e-3, 2e-2, 2e-2, 1e-2] + [1e-3] * 10, [1e-5, 1e-4, 1e-4]
+    loss, g = L.loss_and_grad(p, x, t, ins, outs, form="stream", R=1.5)
+    # outputs 1 and 2 do not enter the stream form: their weights get no gradient
+    nw3 = 3 * 32 * 9
+    w3 = g[-(nw3 + 3):-3].reshape(3, 32, 3, 3)
+    assert np.all(w3[1:] == 0.0) and np.all(g[-2:] == 0.0) and np.abs(w3[0]).max() > 0
+    rng = np.random.default_rng(2)
+    idx = rng.choice(p.size, 40, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        lp, _ = L.loss_and_grad(p + e, x, t, ins, outs, form="stream", R=1.5)
+        lm, _ = L.loss_and_grad(p - e, x, t, ins, outs, form="stream", R=1.5)
+        fd = (lp - lm) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9 * max(1.0, abs(loss)))
