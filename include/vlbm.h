@@ -276,7 +276,22 @@ VLBM_API int vlbm_lc_set_weights(vlbm_lc_t *lc, const float *w);
  * predictions and corrections (e.g. 0 for drho: a velocity-only correction); training with
  * it returns VLBM_ERR_ARG. */
 VLBM_API int vlbm_lc_set_scales(vlbm_lc_t *lc, const double *in_scale, const double *out_scale);
-/* Forward pass: outputs in physical units (drho not mean-corrected). */
+/* Output forms of vlbm_lc_set_output_form. */
+#define VLBM_LC_DIRECT 0
+#define VLBM_LC_STREAM 1
+/* The form of the correction (not in the paper).  VLBM_LC_DIRECT (the default): the three
+ * outputs times out_scale are (drho, du^theta, du^phi).  VLBM_LC_STREAM: output 0 times
+ * out_scale[0] is a stream function psi on the cell grid of a sphere of the given radius, and
+ * the correction is its curl, drho = 0, du^theta = d_phi psi / (R sin theta), du^phi =
+ * -d_theta psi / R, in centred differences with psi continued across a pole by the row on the
+ * opposite meridian (column + n_phi/2).  That correction has zero centred divergence: it moves
+ * the vorticity without launching sound waves.  Training then fits the velocity targets
+ * (residuals scaled by out_scale[1], out_scale[2]; the mean over cells and the two channels)
+ * and ignores the drho target; outputs 1 and 2 of the network are unused.  vlbm_lc_apply and
+ * vlbm_lc_rollout require radius = the solver's (VLBM_ERR_ARG otherwise).  VLBM_ERR_ARG for
+ * an unknown form or radius <= 0.  Rebuilds the rollout graph. */
+VLBM_API int vlbm_lc_set_output_form(vlbm_lc_t *lc, int form, double radius);
+/* Forward pass: the correction in physical units (drho not mean-corrected). */
 VLBM_API int vlbm_lc_predict(vlbm_lc_t *lc, const double *inputs, double *outputs);
 /* Loss and its gradient with respect to every parameter (grad: num_params floats; either may be NULL). */
 VLBM_API int vlbm_lc_gradients(vlbm_lc_t *lc, const double *inputs, const double *targets, double *loss,
@@ -290,8 +305,8 @@ VLBM_API int vlbm_lc_train_step(vlbm_lc_t *lc, const double *inputs, const doubl
 VLBM_API int vlbm_lc_apply(vlbm_lc_t *lc, vlbm_t *h);
 /* Learned-coarse rollout: `steps` times (one RK3 step of h, then the correction of
  * vlbm_lc_apply), enqueued on the solver's stream as a captured CUDA graph (built on
- * the first call for this solver; rebuilt after vlbm_lc_set_scales or for another
- * solver) with no host synchronisation between steps; returns after the last step
+ * the first call for this solver; rebuilt after vlbm_lc_set_scales,
+ * vlbm_lc_set_output_form or for another solver) with no host synchronisation between steps; returns after the last step
  * with the solver's status (vlbm_sync).  h must be FP32 D2Q16 on the network's grid. */
 VLBM_API int vlbm_lc_rollout(vlbm_lc_t *lc, vlbm_t *h, int steps);
 VLBM_API const char *vlbm_lc_last_error(const vlbm_lc_t *lc);

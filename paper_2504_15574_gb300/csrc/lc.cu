@@ -511,6 +511,104 @@ __global__ void outputs_kernel(const float *Y, int CO, int H, int W, float3 scal
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// ---- stream-function output form: output 0 times s0 is psi, the correction its centred curl
+// du^theta = s0 (psi[i][j+1] - psi[i][j-1]) / (2 R dphi sin theta_i),
+// du^phi = -s0 (psi[i+1][j] - psi[i-1][j]) / (2 R dtheta); a row beyond a pole is the edge row on
+// the opposite meridian (column + W/2; psi is a scalar: no sign change).
+
+// output 0 of cell (i, j), rows beyond a pole and columns wrapped as above
+__device__ __forceinline__ double psi_at(const float *Y, int CO, int H, int W, int i, int j)
+{
+    if (i < 0) {
+        i = 0;
+        j += W / 2;
+    } else if (i >= H) {
+        i = H - 1;
+        j += W / 2;
+    }
+    j %= W;
+    if (j < 0) j += W;
+    return (double)Y[((size_t)i * W + j) * CO];
+}
+
+__device__ __forceinline__ void stream_uv(const float *Y, int CO, const LcStream &g, const double *sin_t, int i,
+                                          int j, double &ut, double &up)
+{
+    ut = g.s0 * (psi_at(Y, CO, g.H, g.W, i, j + 1) - psi_at(Y, CO, g.H, g.W, i, j - 1)) /
+         (2.0 * g.R * g.dph * sin_t[i]);
+    up = -g.s0 * (psi_at(Y, CO, g.H, g.W, i + 1, j) - psi_at(Y, CO, g.H, g.W, i - 1, j)) / (2.0 * g.R * g.dth);
+}
+
+// loss of the stream form: the sin-area-weighted mean over cells and the two velocity channels of
+// ((du - target) / out_scale)^2; per cell the loss's derivatives by du^theta and du^phi into gv
+// [2][H][W]; per block partial sums of the loss
+__global__ void stream_loss_kernel(const float *Y, int CO, const double *target, const double *sin_t, LcStream g,
+                                   double inv_s1, double inv_s2, double wsum, double *gv, double *part)
+{
+    __shared__ double red[256];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int HW = g.H * g.W;
+    double l = 0.0;
+    if (c < HW) {
+        const int i = c / g.W, j = c - i * g.W;
+        double ut, up;
+        stream_uv(Y, CO, g, sin_t, i, j, ut, up);
+        const double w = sin_t[i] / wsum;
+        const double rt = (ut - target[(size_t)HW + c]) * inv_s1, rp = (up - target[2 * (size_t)HW + c]) * inv_s2;
+        l = 0.5 * w * (rt * rt + rp * rp);
+        gv[c] = w * rt * inv_s1;
+        gv[(size_t)HW + c] = w * rp * inv_s2;
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// gradient at the net output (dY [H][W][CO]): output 0 gets the adjoint of the curl applied to
+// gv (times s0), the other outputs 0
+__global__ void stream_adjoint_kernel(const double *gv, int CO, LcStream g, const double *sin_t, float *dY)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int H = g.H, W = g.W, HW = H * W;
+    if (c >= HW) return;
+    const int i = c / W, j = c - i * W;
+    const int jm = (j + W - 1) % W, jp = (j + 1) % W, jo = (j + W / 2) % W;
+    const double ka = 1.0 / (2.0 * g.R * g.dph * sin_t[i]), kb = 1.0 / (2.0 * g.R * g.dth);
+    const double *gt = gv, *gp = gv + HW;
+    // psi[i][j] enters du^theta of (i, j - 1) with + and of (i, j + 1) with -, du^phi of row
+    // i - 1 with - and of row i + 1 with +; at a pole row, also du^phi of the same row on the
+    // opposite meridian through the continuation
+    double d = ka * (gt[(size_t)i * W + jm] - gt[(size_t)i * W + jp]);
+    if (i > 0) d -= kb * gp[(size_t)(i - 1) * W + j];
+    else d += kb * gp[jo];
+    if (i < H - 1) d += kb * gp[(size_t)(i + 1) * W + j];
+    else d -= kb * gp[(size_t)(H - 1) * W + jo];
+    dY[(size_t)c * CO] = (float)(g.s0 * d);
+    for (int o = 1; o < CO; ++o) dY[(size_t)c * CO + o] = 0.0f;
+}
+
+// the stream form's correction (0, du^theta, du^phi) [3][H][W] in physical units; the drho
+// partial sums are 0
+__global__ void stream_outputs_kernel(const float *Y, int CO, LcStream g, const double *sin_t, double *out,
+                                      double *part)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int HW = g.H * g.W;
+    if (c < HW) {
+        const int i = c / g.W, j = c - i * g.W;
+        double ut, up;
+        stream_uv(Y, CO, g, sin_t, i, j, ut, up);
+        out[c] = 0.0;
+        out[(size_t)HW + c] = ut;
+        out[2 * (size_t)HW + c] = up;
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
+}
+
 // Moments (rho, u^theta, u^phi, T) of the FP32 pair layout (dg = ks s (f - w rho_ref)) in FP32
 // arithmetic on the deviations: n = rho_ref + sum dg / s, j = sum v dg / s (the reference
 // state carries no momentum), and T - 1 = (rho_ref |u|^2 + sum df |v - u|^2 - 2 dn) / (2 n),
@@ -661,6 +759,24 @@ void lc_loss(const float *Y, int CO, const double *target, const double *sin_t, 
     const int nb = (H * W + 255) / 256;
     loss_kernel<<<nb, 256, 0, s>>>(Y, CO, target, sin_t, H, W, inv_scale, wsum, dY, part);
     sum_kernel<<<1, 256, 0, s>>>(part, nb, loss);
+}
+
+void lc_stream_loss(const float *Y, int CO, const double *target, const double *sin_t, const LcStream &g,
+                    double inv_s1, double inv_s2, double wsum, double *gv, float *dY, double *part, double *loss,
+                    cudaStream_t s)
+{
+    const int nb = (g.H * g.W + 255) / 256;
+    stream_loss_kernel<<<nb, 256, 0, s>>>(Y, CO, target, sin_t, g, inv_s1, inv_s2, wsum, gv, part);
+    sum_kernel<<<1, 256, 0, s>>>(part, nb, loss);
+    stream_adjoint_kernel<<<nb, 256, 0, s>>>(gv, CO, g, sin_t, dY);
+}
+
+void lc_stream_outputs(const float *Y, int CO, const LcStream &g, const double *sin_t, double *out, double *part,
+                       double *mean, cudaStream_t s)
+{
+    const int nb = (g.H * g.W + 255) / 256;
+    stream_outputs_kernel<<<nb, 256, 0, s>>>(Y, CO, g, sin_t, out, part);
+    sum_kernel<<<1, 256, 0, s>>>(part, nb, mean);
 }
 
 void lc_adam(float *w, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps, float c1,

@@ -35,6 +35,9 @@ struct vlbm_lc {
     float in_scale[LC_NSCALE] = {1e-3f, 1e-2f, 1e-2f, 1e-3f, 1e-6f, 1e-6f, 1e-5f, 1e-5f, 1e-5f,
                                  1e-5f, 1e-5f, 1e-5f, 1e-5f, 1e-5f};
     float out_scale[3] = {1e-5f, 1e-4f, 1e-4f};
+    int form = VLBM_LC_DIRECT;   // output form (vlbm_lc_set_output_form)
+    double radius = 1.0;         // the stream form's sphere radius
+    double *d_gv = nullptr;      // stream form: the loss's derivatives by du^theta, du^phi [2][H][W]
     long long t = 0;
     std::vector<void *> bufs;
     cudaGraphExec_t g_exec = nullptr;   // vlbm_lc_rollout: one corrected step of solver g_solver
@@ -102,12 +105,34 @@ int forward(vlbm_lc_t *n, const double *in4, cudaStream_t s, bool keep = true)
     return VLBM_OK;
 }
 
+LcStream stream_geometry(const vlbm_lc_t *n)
+{
+    return LcStream{n->H, n->W, (double)n->out_scale[0], n->radius, M_PI / n->H, 2.0 * M_PI / n->W};
+}
+
+// the correction in physical units into d_out ([3][H][W]) and the area sum of its drho into
+// d_scal[1], from the forward pass's output d_y
+void enqueue_outputs(vlbm_lc_t *n, cudaStream_t s)
+{
+    if (n->form == VLBM_LC_STREAM) {
+        lc_stream_outputs(n->d_y, LC_COUT, stream_geometry(n), n->d_sin, n->d_out, n->d_part, n->d_scal + 1, s);
+    } else {
+        const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
+        lc_outputs(n->d_y, LC_COUT, n->H, n->W, sc, n->d_sin, n->d_out, n->d_part, n->d_scal + 1, s);
+    }
+}
+
 // loss and gradient of every parameter into d_g; loss into d_scal[0]
 int backward(vlbm_lc_t *n)
 {
     const int H = n->H, W = n->W, HW = H * W;
-    const float3 ios = make_float3(1.0f / n->out_scale[0], 1.0f / n->out_scale[1], 1.0f / n->out_scale[2]);
-    lc_loss(n->d_y, LC_COUT, n->d_tg, n->d_sin, H, W, ios, n->wsum, n->d_dy, n->d_part, n->d_scal, n->stream);
+    if (n->form == VLBM_LC_STREAM) {
+        lc_stream_loss(n->d_y, LC_COUT, n->d_tg, n->d_sin, stream_geometry(n), 1.0 / n->out_scale[1],
+                       1.0 / n->out_scale[2], n->wsum, n->d_gv, n->d_dy, n->d_part, n->d_scal, n->stream);
+    } else {
+        const float3 ios = make_float3(1.0f / n->out_scale[0], 1.0f / n->out_scale[1], 1.0f / n->out_scale[2]);
+        lc_loss(n->d_y, LC_COUT, n->d_tg, n->d_sin, H, W, ios, n->wsum, n->d_dy, n->d_part, n->d_scal, n->stream);
+    }
     // gradient at the output of layer l lives in d_dy with cop[l] channels
     for (int l = LC_LAYERS - 1; l >= 0; --l) {
         const int C = n->cop[l], CP = n->cop2[l];
@@ -133,6 +158,8 @@ int check_solver(vlbm_lc_t *n, vlbm_t *h)
     if (!n || !h) return VLBM_ERR_ARG;
     if (h->prec != VLBM_FP32 || h->vd.q != 4 || h->nt != n->H || h->np != n->W)
         return lfail(n, VLBM_ERR_ARG, "the solver must be FP32 D2Q16 on the network's grid");
+    if (n->form == VLBM_LC_STREAM && n->radius != h->R)
+        return lfail(n, VLBM_ERR_ARG, "the stream form's radius differs from the solver's");
     return VLBM_OK;
 }
 
@@ -143,8 +170,7 @@ int enqueue_correction(vlbm_lc_t *n, vlbm_t *h, cudaStream_t s)
     lc_moments((const float2 *)h->F, h->L, h->vd, h->rho_ref, h->d_sin_t, h->kscale, h->d_mom, s);
     int rc;
     if ((rc = forward(n, h->d_mom, s, false))) return rc;
-    const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
-    lc_outputs(n->d_y, LC_COUT, n->H, n->W, sc, n->d_sin, n->d_out, n->d_part, n->d_scal + 1, s);
+    enqueue_outputs(n, s);
     lc_nudge((float2 *)h->F, h->L, h->d_mom, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, h->kscale, s);
     launch_fill_ghosts_f32((float2 *)h->F, h->L, h->vd.q, s);
     LCK(n, cudaGetLastError());
@@ -230,6 +256,7 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
     A(&n->d_wpart, (size_t)n_theta * 9 * LC_HID * LC_HID);
     A(&n->d_bpart, (size_t)n_theta * LC_HID);
     A(&n->d_g9, (size_t)9 * LC_HID * LC_HID);
+    A(&n->d_gv, 2 * HW);
     if (rc) {
         vlbm_lc_destroy(n);
         return rc;
@@ -294,13 +321,26 @@ int vlbm_lc_set_scales(vlbm_lc_t *n, const double *in_scale, const double *out_s
     return VLBM_OK;
 }
 
+int vlbm_lc_set_output_form(vlbm_lc_t *n, int form, double radius)
+{
+    if (!n) return VLBM_ERR_ARG;
+    if (form != VLBM_LC_DIRECT && form != VLBM_LC_STREAM) return lfail(n, VLBM_ERR_ARG, "unknown output form");
+    if (!(radius > 0.0) || !std::isfinite(radius)) return lfail(n, VLBM_ERR_ARG, "radius must be > 0");
+    if (n->g_exec) {   // the form is part of the captured rollout step
+        cudaGraphExecDestroy(n->g_exec);
+        n->g_exec = nullptr;
+    }
+    n->form = form;
+    n->radius = radius;
+    return VLBM_OK;
+}
+
 int vlbm_lc_predict(vlbm_lc_t *n, const double *inputs, double *outputs)
 {
     if (!n || !inputs || !outputs) return VLBM_ERR_ARG;
     int rc;
     if ((rc = upload_io(n, inputs, nullptr)) || (rc = forward(n, n->d_in, n->stream))) return rc;
-    const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
-    lc_outputs(n->d_y, LC_COUT, n->H, n->W, sc, n->d_sin, n->d_out, n->d_part, n->d_scal + 1, n->stream);
+    enqueue_outputs(n, n->stream);
     LCK(n, cudaMemcpyAsync(outputs, n->d_out, sizeof(double) * 3 * n->H * n->W, cudaMemcpyDeviceToHost, n->stream));
     LCK(n, cudaStreamSynchronize(n->stream));
     return VLBM_OK;

@@ -54,5 +54,17 @@ void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double
                 double *mean, cudaStream_t s);
 void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,
               const VelD &c, const double *sin_t, double ks, cudaStream_t s);
+// Stream-function output form: output 0 times s0 is a stream function psi on the H x W cell grid
+// of a sphere of radius R (dth = pi / H, dph = 2 pi / W), the correction its centred curl
+// (0, d_phi psi / (R sin theta), -d_theta psi / R), psi continued across a pole as a scalar.
+struct LcStream { int H, W; double s0, R, dth, dph; };
+// Loss of the stream form against the velocity targets (channels 1, 2 of target [3][H][W]) scaled
+// by inv_s1, inv_s2; the gradient at the net output into dY [H][W][CO] (gv: [2][H][W] scratch).
+void lc_stream_loss(const float *Y, int CO, const double *target, const double *sin_t, const LcStream &g,
+                    double inv_s1, double inv_s2, double wsum, double *gv, float *dY, double *part, double *loss,
+                    cudaStream_t s);
+// The stream form's correction (0, du^theta, du^phi) [3][H][W]; *mean (the drho area sum) = 0.
+void lc_stream_outputs(const float *Y, int CO, const LcStream &g, const double *sin_t, double *out, double *part,
+                       double *mean, cudaStream_t s);
 
 }  // namespace vk

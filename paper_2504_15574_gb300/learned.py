@@ -11,7 +11,9 @@ moments toward the block-averaged state of a fine run.  Pieces:
   starts) advanced ``factor`` fine steps per coarse step; coarse rollouts beside
   them start from the block-averaged fine populations; after each coarse step the
   sample is (coarse moments, downsampled fine moments minus them);
-- ``train``: Adam on those samples;
+- ``train``: Adam on those samples, with the correction in the "direct" form
+  (drho, du^theta, du^phi) or the "stream" form (the centred curl of a predicted
+  stream function: divergence-free, drho = 0);
 - ``evaluate``: rollouts of plain coarse, coarse + correction and the fine run
   on held-out seeds; area-weighted relative L2 error of the vorticity (and of
   rho) against the downsampled fine run, and wall time per coarse step.
@@ -252,10 +254,18 @@ def scales(X, Y):
     return ins, outs
 
 
-def train(setup: Setup, X, Y, epochs=4, lr=2e-3, seed=1, log=None, net=None):
+def stream_scale(setup: Setup, outs):
+    """Output scale of the stream function: the velocity targets' spread times R times 8
+    coarse theta spacings (a correction varying over ~8 cells has that stream-function size)."""
+    return 0.5 * (outs[1] + outs[2]) * 8.0 * math.pi / setup.coarse[0]
+
+
+def train(setup: Setup, X, Y, epochs=4, lr=2e-3, seed=1, log=None, net=None, form="direct"):
     if net is None:
         ins, outs = scales(X, Y)
-        net = vlbm.LearnedCorrection(*setup.coarse, seed=seed, in_scale=ins, out_scale=outs)
+        if form == "stream":
+            outs = [stream_scale(setup, outs), outs[1], outs[2]]
+        net = vlbm.LearnedCorrection(*setup.coarse, seed=seed, in_scale=ins, out_scale=outs, form=form)
     rng = np.random.default_rng(seed)
     hist = []
     for ep in range(epochs):
@@ -285,9 +295,11 @@ def evaluate(setup: Setup, net, seeds, n_steps, spinup=20, start="fine"):
     t_fine = (time.perf_counter() - t0) / (n_steps * len(seeds))
     refs = [downsample(*fb.moments(r, with_T=True)) for r in range(len(seeds))]
     fb.close()
-    res = {"plain": [], "learned": [], "learned_u": []}
+    # learned_u (direct form only): the same network with its density output dropped
+    modes = ("plain", "learned", "learned_u") if net.form == "direct" else ("plain", "learned")
+    res = {m: [] for m in modes}
     times = {}
-    for mode in ("plain", "learned", "learned_u"):
+    for mode in modes:
         cs = setup.coarse_solver()
         el = 0.0
         if mode == "learned_u":
@@ -326,13 +338,16 @@ def evaluate(setup: Setup, net, seeds, n_steps, spinup=20, start="fine"):
            "vort_err_learned": float(np.mean([e["vort"] for e in res["learned"]])),
            "rho_err_plain": float(np.mean([e["rho"] for e in res["plain"]])),
            "rho_err_learned": float(np.mean([e["rho"] for e in res["learned"]])),
-           "vort_err_learned_u_per_seed": [e["vort"] for e in res["learned_u"]],
-           "rho_err_learned_u_per_seed": [e["rho"] for e in res["learned_u"]],
            "rho_err_plain_per_seed": [e["rho"] for e in res["plain"]],
-           "vort_err_learned_u": float(np.mean([e["vort"] for e in res["learned_u"]])),
-           "rho_err_learned_u": float(np.mean([e["rho"] for e in res["learned_u"]])),
+           "rho_err_learned_per_seed": [e["rho"] for e in res["learned"]],
+           "form": net.form,
            "ms_per_coarse_step_plain": times["plain"] * 1e3, "ms_per_coarse_step_learned": times["learned"] * 1e3,
            "ms_fine_per_coarse_step": t_fine * 1e3}
+    if "learned_u" in res:
+        out.update({"vort_err_learned_u_per_seed": [e["vort"] for e in res["learned_u"]],
+                    "rho_err_learned_u_per_seed": [e["rho"] for e in res["learned_u"]],
+                    "vort_err_learned_u": float(np.mean([e["vort"] for e in res["learned_u"]])),
+                    "rho_err_learned_u": float(np.mean([e["rho"] for e in res["learned_u"]]))})
     out["speedup_learned_vs_fine"] = out["ms_fine_per_coarse_step"] / out["ms_per_coarse_step_learned"]
     return out
 
@@ -415,12 +430,16 @@ def main(argv=None):
     ap.add_argument("--load-net", default=None, help="read weights and scales (.npz) instead of making data and training")
     ap.add_argument("--equal-error", type=int, nargs="*", default=[],
                     help="resolution multiples of the coarse grid for plain runs at each horizon (e.g. 2 3)")
+    ap.add_argument("--save-data", default=None, help="write the training samples (.npz)")
+    ap.add_argument("--load-data", default=None, help="read the training samples (.npz) instead of making them")
+    ap.add_argument("--form", choices=["direct", "stream"], default="direct",
+                    help="correction form: (drho, du) outputs, or the curl of a stream function")
     ap.add_argument("--timing-steps", type=int, default=0,
                     help="only time this many corrected coarse steps of an untrained network (no data, no training)")
     a = ap.parse_args(argv)
     setup = Setup(coarse=a.coarse, polar_filter=a.polar_filter)
     if a.timing_steps:
-        net = vlbm.LearnedCorrection(*setup.coarse, seed=1)
+        net = vlbm.LearnedCorrection(*setup.coarse, seed=1, form=a.form)
         cs = setup.coarse_solver()
         cs.init_moments(*inputs.gaussian_vortices(*setup.coarse, run=5000)[:3])
         net.rollout(cs, 3)
@@ -438,22 +457,31 @@ def main(argv=None):
     seeds = list(range(1000, 1000 + a.train_seeds))
     if a.load_net:
         z = np.load(a.load_net)
-        net = vlbm.LearnedCorrection(*setup.coarse, seed=1, in_scale=z["in_scale"], out_scale=z["out_scale"])
+        form = str(z["form"]) if "form" in z else "direct"
+        net = vlbm.LearnedCorrection(*setup.coarse, seed=1, in_scale=z["in_scale"], out_scale=z["out_scale"],
+                                     form=form)
         net.set_weights(z["weights"])
         X, hist, t_data, t_train = [], [], 0.0, 0.0
     else:
         t0 = time.perf_counter()
-        if a.targets == "drift":
+        if a.load_data:
+            z = np.load(a.load_data)
+            X, Y = z["X"], z["Y"]
+        elif a.targets == "drift":
             X, Y = make_drift_samples(setup, seeds, a.windows, spinup=a.spinup)
         else:
             X, Y = make_samples(setup, seeds, a.steps, spinup=a.spinup)
         t_data = time.perf_counter() - t0
+        if a.save_data:
+            np.savez(a.save_data, X=X, Y=Y)
         t0 = time.perf_counter()
-        net, hist = train(setup, X, Y, epochs=a.epochs, log=print)
+        net, hist = train(setup, X, Y, epochs=a.epochs, log=print, form=a.form)
         t_train = time.perf_counter() - t0
     if a.save_net:
-        np.savez(a.save_net, weights=net.get_weights(), in_scale=net.in_scale, out_scale=net.out_scale)
-    out = {"grid_coarse": list(setup.coarse), "grid_fine": list(setup.fine), "polar_filter": setup.polar_filter,
+        np.savez(a.save_net, weights=net.get_weights(), in_scale=net.in_scale, out_scale=net.out_scale,
+                 form=net.form)
+    out = {"form": net.form, "grid_coarse": list(setup.coarse), "grid_fine": list(setup.fine),
+           "polar_filter": setup.polar_filter,
            "dt_coarse": setup.dt_c, "fine_steps_per_coarse_step": setup.substeps, "targets": a.targets,
            "samples": int(len(X)), "loss_history": hist, "seconds_data": t_data, "seconds_train": t_train,
            "horizons": []}
@@ -468,15 +496,16 @@ def main(argv=None):
                   [(setup.factor, 1e-300, res["ms_fine_per_coarse_step"])]
             res["equal_error"] = {}
             for key in ("learned", "learned_u"):
+                if f"vort_err_{key}" not in res:
+                    continue
                 hit = equal_error_grid(pts[:-1], res[f"vort_err_{key}"])
                 res["equal_error"][key] = None if hit is None else {
                     "multiple": hit[0], "ms_plain": hit[1],
                     "time_ratio_plain_over_learned": hit[1] / res[f"ms_per_coarse_step_{'learned'}"]}
         out["horizons"].append(res)
-        print(json.dumps({k: res[k] for k in ("coarse_steps", "vort_err_plain", "vort_err_learned", "vort_err_learned_u",
-                                              "rho_err_plain", "rho_err_learned", "rho_err_learned_u",
-                                              "speedup_learned_vs_fine") + (("plain_grids", "equal_error")
-                                                                            if a.equal_error else ())}))
+        keys = ("coarse_steps", "vort_err_plain", "vort_err_learned", "vort_err_learned_u", "rho_err_plain",
+                "rho_err_learned", "rho_err_learned_u", "speedup_learned_vs_fine", "plain_grids", "equal_error")
+        print(json.dumps({k: res[k] for k in keys if k in res}))
     line = json.dumps(out)
     print(line)
     if a.out:

@@ -92,6 +92,7 @@ SIGNATURES = {
     "vlbm_lc_get_weights": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float)]),
     "vlbm_lc_set_weights": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float)]),
     "vlbm_lc_set_scales": (ctypes.c_int, [_H, _PD, _PD]),
+    "vlbm_lc_set_output_form": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_double]),
     "vlbm_lc_predict": (ctypes.c_int, [_H, _PD, _PD]),
     "vlbm_lc_gradients": (ctypes.c_int, [_H, _PD, _PD, _PD, ctypes.POINTER(ctypes.c_float)]),
     "vlbm_lc_train_step": (ctypes.c_int, [_H, _PD, _PD, ctypes.c_float, _PD]),
@@ -412,13 +413,23 @@ class LearnedCorrection:
     # scales of the 14 data channels: rho-1, u^theta, u^phi, T-1, then the ten differences
     DEFAULT_IN_SCALE = (1e-3, 1e-2, 1e-2, 1e-3) + (1e-6,) * 2 + (1e-5,) * 8
 
-    def __init__(self, n_theta, n_phi, seed=1, in_scale=DEFAULT_IN_SCALE, out_scale=(1e-5, 1e-4, 1e-4)):
+    FORMS = {"direct": 0, "stream": 1}
+
+    def __init__(self, n_theta, n_phi, seed=1, in_scale=DEFAULT_IN_SCALE, out_scale=(1e-5, 1e-4, 1e-4),
+                 form="direct", R=1.0):
         self.shape = (int(n_theta), int(n_phi))
         self.h = _H()
         rc = load().vlbm_lc_create(self.shape[0], self.shape[1], int(seed), ctypes.byref(self.h))
         if rc:
             raise VlbmError(rc, "vlbm_lc_create failed")
         self.set_scales(in_scale, out_scale)
+        self.set_output_form(form, R)
+
+    def set_output_form(self, form, R=1.0):
+        """"direct": outputs (drho, du^theta, du^phi); "stream": output 0 is a stream function
+        whose centred curl on a sphere of radius R is the velocity correction (drho = 0)."""
+        self._chk(load().vlbm_lc_set_output_form(self.h, self.FORMS[form], float(R)))
+        self.form, self.R = form, float(R)
 
     def _chk(self, rc):
         if rc != VLBM_OK:

@@ -89,4 +89,5 @@ def test_null_handles_are_argument_errors(lib):
     import ctypes
     assert lib.vlbm_step(None, 1) == -1
     assert lib.vlbm_moments(None, None, None, None, None) == -1
+    assert lib.vlbm_lc_set_output_form(None, 1, 1.0) == -1
     lib.vlbm_destroy(None)   # NULL-safe

@@ -207,3 +207,154 @@ def test_trained_correction_beats_the_plain_coarse_run_on_held_out_seeds(V):
         assert a < b, res
     # density is reported, not corrected toward the fine run: bounded, not worse than 3x
     assert res["rho_err_learned"] < 3.0 * res["rho_err_plain"], res
+
+
+# ---- the stream-function output form ----------------------------------------------------------
+
+STREAM_OUT = (3e-5, 1e-4, 1e-4)
+
+
+def _bf16_weights(p):
+    pw = p.copy()
+    o = 0
+    for ci, co in L.LAYERS:
+        pw[o:o + co * ci * 9] = _bf16(p[o:o + co * ci * 9])
+        o += co * ci * 9 + co
+    return pw
+
+
+@pytest.mark.parametrize("H,W,R", [(16, 32, 1.0), (24, 64, 1.3)])
+def test_stream_form_matches_fp64_reference(V, H, W, R):
+    """Correction (the curl of output 0), loss and every parameter gradient of the stream form
+    against the FP64 reference; outputs 1 and 2 get exactly no gradient."""
+    net = V.LearnedCorrection(H, W, seed=5, in_scale=IN_SCALE, out_scale=STREAM_OUT, form="stream", R=R)
+    p = net.get_weights().astype(np.float64)
+    p[-3:] = [0.3, -0.2, 0.1]
+    net.set_weights(p)
+    x, t = _sample(H, W, 13)
+    pw = _bf16_weights(p)
+    y_ref, _ = L.forward(pw, x, IN_SCALE, quantize=_bf16)
+    out_ref = L.outputs(y_ref, STREAM_OUT, "stream", R)
+    out = net.predict(x)
+    assert np.all(out[0] == 0.0)
+    scale = np.abs(out_ref[1:]).max()
+    # a centred difference of BF16-stored activations: ~2^-8 of the largest output per difference
+    assert np.abs(out[1:] - out_ref[1:]).max() <= 5e-2 * scale, np.abs(out[1:] - out_ref[1:]).max() / scale
+    loss, g = net.gradients(x, t)
+    loss_ref, g_ref = L.loss_and_grad(pw, x, t, IN_SCALE, STREAM_OUT, quantize=_bf16, form="stream", R=R)
+    assert loss == pytest.approx(loss_ref, rel=3e-2)
+    nw3 = 3 * 32 * 9
+    assert np.all(g[-(nw3 + 3):-3].reshape(3, 32, 3, 3)[1:] == 0.0) and np.all(g[-2:] == 0.0)
+    # the output gradient is the curl's adjoint, a difference of neighbouring cells' residuals, so
+    # the sums over cells behind every weight and bias gradient cancel more than in the direct
+    # form: layer 0's biases carry 3.6-4.7% in L2 (direct form 0.8-1.2%); the bound stays well
+    # below the ninth of a block that a mis-indexed tap or channel moves
+    # The output biases get no gradient at all in exact arithmetic (a uniform psi has no curl;
+    # outputs 1 and 2 are unused): their entries are rounding, checked against the weight block.
+    o = 0
+    for l, (ci, co) in enumerate(L.LAYERS):
+        for n in (co * ci * 9, co):
+            a, b = g[o:o + n], g_ref[o:o + n]
+            if l == len(L.LAYERS) - 1 and n == co:
+                assert np.abs(a).max() <= 1e-3 * np.abs(g[o - co * ci * 9:o]).max(), a
+                o += n
+                continue
+            l2 = np.linalg.norm(a - b) / np.linalg.norm(b)
+            worst = np.abs(a - b).max() / np.abs(b).max()
+            print("stream gradient block", o, n, "rel L2 %.3e worst %.3e" % (l2, worst))
+            assert l2 <= 8e-2 and worst <= 0.25, (o, l2, worst)
+            o += n
+
+
+def _centred_divergence(ut, up, R=1.0):
+    H, W = ut.shape
+    dth, dph = np.pi / H, 2 * np.pi / W
+    st = np.sin((np.arange(H) + 0.5) * dth)
+    ste = np.concatenate([[-st[0]], st, [-st[-1]]])
+    flux = ste[:, None] * L.pad(ut[None], [0])[0]
+    upe = L.pad(up[None], [0])[0]
+    return ((flux[2:, 1:-1] - flux[:-2, 1:-1]) / (2 * dth) + (upe[1:-1, 2:] - upe[1:-1, :-2]) / (2 * dph)) / (R * st[:, None])
+
+
+def test_stream_form_apply_adds_a_divergence_free_velocity_and_keeps_the_density(V):
+    H, W = 16, 32
+    net = V.LearnedCorrection(H, W, seed=4, in_scale=IN_SCALE, out_scale=(1e-3, 1e-4, 1e-4), form="stream")
+    p = net.get_weights()
+    p[-3:] = [1.0, 0.5, -0.5]
+    net.set_weights(p)
+    s = V.Solver(H, W, 2e-3, 1e-4, precision="fp32")
+    s.init_moments(*inputs.gaussian_vortices(H, W, run=6))
+    m0 = s.diagnostics()["mass"]
+    r0, ut0, up0, T0 = s.moments(with_T=True)
+    du = net.predict(np.stack([r0, ut0, up0, T0]))
+    net.apply(s)
+    m1 = s.diagnostics()["mass"]
+    r1, ut1, up1 = s.moments()
+    assert abs(m1 - m0) < 1e-6 * m0
+    # the density is left alone cell by cell (FP32 rounding of the nudge only)
+    assert np.abs(r1 - r0).max() <= 2e-6, np.abs(r1 - r0).max()
+    dut, dup = ut1 - ut0, up1 - up0
+    big = max(np.abs(du[1]).max(), np.abs(du[2]).max())
+    assert big > 1e-6
+    # the velocity moves by the network's curl (computed there from FP64 moments, in the solver
+    # from its FP32 state: the BF16 features may round differently in a few cells)
+    assert np.abs(dut - du[1]).max() <= 5e-2 * big and np.abs(dup - du[2]).max() <= 5e-2 * big
+    div = _centred_divergence(dut, dup)
+    assert np.abs(div).max() <= 1e-3 * big / (np.pi / H), np.abs(div).max() / (big / (np.pi / H))
+
+
+def test_stream_form_needs_the_solver_radius(V):
+    H, W = 16, 32
+    net = V.LearnedCorrection(H, W, seed=4, in_scale=IN_SCALE, out_scale=STREAM_OUT, form="stream", R=2.0)
+    s = V.Solver(H, W, 2e-3, 1e-4, precision="fp32")
+    s.init_moments(*inputs.gaussian_vortices(H, W, run=6))
+    with pytest.raises(V.VlbmError) as e:
+        net.apply(s)
+    assert e.value.code == V.VLBM_ERR_ARG and "radius" in str(e.value)
+    net.set_output_form("stream", 1.0)
+    net.apply(s)
+    with pytest.raises(V.VlbmError):
+        net.set_output_form("stream", -1.0)
+
+
+def test_stream_form_rollout_equals_stepping_and_applying_bitwise(V):
+    H, W = 16, 32
+    net = V.LearnedCorrection(H, W, seed=4, in_scale=IN_SCALE, out_scale=STREAM_OUT)
+    p = net.get_weights()
+    p[-3:] = [0.5, 0.3, -0.2]
+    net.set_weights(p)
+    a = V.Solver(H, W, 2e-3, 1e-4, precision="fp32", guard=False)
+    b = V.Solver(H, W, 2e-3, 1e-4, precision="fp32", guard=False)
+    for s in (a, b):
+        s.init_moments(*inputs.gaussian_vortices(H, W, run=6))
+    net.rollout(a, 2)                      # the direct form's graph, then rebuilt for the stream form
+    for _ in range(2):
+        b.step(1)
+        net.apply(b)
+    net.set_output_form("stream", 1.0)
+    net.rollout(a, 4)
+    for _ in range(4):
+        b.step(1)
+        net.apply(b)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    a.close()
+    b.close()
+
+
+def test_trained_stream_correction_beats_the_plain_run_and_keeps_its_density_error(V):
+    """The learned-coarse experiment of the direct-form test (coarse 32 x 64 from fine 128 x 256)
+    with the stream form after 1000 coarse steps: the corrected run's vorticity error is below
+    the plain run's on each held-out seed (by half on average when this was written), and, the
+    correction being divergence-free, its density error is no larger than the plain run's on
+    average (the direct form's is 2.5x the plain run's at this horizon)."""
+    from paper_2504_15574_gb300 import learned
+    setup = learned.Setup(coarse=(32, 64), polar_filter=False)
+    X, Y = learned.make_drift_samples(setup, list(range(1000, 1016)), 8, spinup=20)
+    net, _ = learned.train(setup, X, Y, epochs=6, form="stream")
+    res = learned.evaluate(setup, net, [5000, 5001, 5002, 5003], 1000, spinup=20)
+    print({k: res[k] for k in ("vort_err_plain", "vort_err_learned", "rho_err_plain", "rho_err_learned")})
+    assert np.all(np.isfinite(res["vort_err_learned_per_seed"]))
+    assert res["vort_err_learned"] < 0.7 * res["vort_err_plain"], res
+    for a, b in zip(res["vort_err_learned_per_seed"], res["vort_err_plain_per_seed"]):
+        assert a < b, res
+    assert res["rho_err_learned"] <= res["rho_err_plain"], res
