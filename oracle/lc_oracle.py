@@ -20,6 +20,10 @@ opposite meridian); drho = 0.  The discrete velocity has zero centred divergence
 the correction moves the vorticity without launching sound waves.  Its loss is the
 sin(theta)-area-weighted mean over cells and the 2 velocity channels of
 ((du - target) / out_scale)^2.
+"vorticity": output 0 times out_scale[0] is a vorticity correction w; psi solves the
+cell-centred finite-volume Poisson equation L psi = w - (area mean of w) on the sphere
+(no flux through the pole faces, whose sine is 0), and du is the curl of psi as in the
+stream form (same loss).  The network stays local; the solve makes psi the integral.
 """
 from __future__ import annotations
 
@@ -197,11 +201,75 @@ def stream_velocity_adjoint(gt, gp, R=1.0):
     return unpad(ge[None], [])[0]
 
 
+def laplacian_matrix(H, W, R=1.0):
+    """The cell-centred finite-volume Laplacian on the sphere as a dense [H W][H W] matrix (cell
+    (i, j) at row i W + j): (L psi)_ij = (s_{i+1/2} (psi_{i+1,j} - psi_ij) - s_{i-1/2} (psi_ij -
+    psi_{i-1,j})) / (R^2 s_i dth^2) + (psi_{i,j+1} - 2 psi_ij + psi_{i,j-1}) / (R^2 s_i^2 dph^2),
+    s at cell centres and at the faces theta = i dth; the pole faces have s = 0 (no flux), the
+    columns wrap."""
+    dth, dph = math.pi / H, 2.0 * math.pi / W
+    sc = np.sin((np.arange(H) + 0.5) * dth)
+    sf = np.sin(np.arange(H + 1) * dth)
+    sf[0] = sf[H] = 0.0
+    A = np.zeros((H * W, H * W))
+    for i in range(H):
+        for j in range(W):
+            r = i * W + j
+            kt = 1.0 / (R * R * sc[i] * dth * dth)
+            kp = 1.0 / (R * R * sc[i] * sc[i] * dph * dph)
+            if i > 0:
+                A[r, (i - 1) * W + j] += kt * sf[i]
+                A[r, r] -= kt * sf[i]
+            if i < H - 1:
+                A[r, (i + 1) * W + j] += kt * sf[i + 1]
+                A[r, r] -= kt * sf[i + 1]
+            A[r, i * W + (j + 1) % W] += kp
+            A[r, i * W + (j - 1) % W] += kp
+            A[r, r] -= 2.0 * kp
+    return A
+
+
+def area_mean_free(w):
+    """w minus its sin(theta)-area-weighted mean."""
+    H, W = w.shape
+    sc = np.sin((np.arange(H) + 0.5) * math.pi / H)[:, None] * np.ones((1, W))
+    return w - (sc * w).sum() / sc.sum()
+
+
+def poisson(w, R=1.0):
+    """A solution psi [H][W] of L psi = w - (area mean of w); its constant is irrelevant to the
+    curl (the least-squares solution of the singular dense system)."""
+    H, W = w.shape
+    rhs = area_mean_free(w).ravel()
+    psi = np.linalg.lstsq(laplacian_matrix(H, W, R), rhs, rcond=None)[0]
+    return psi.reshape(H, W)
+
+
+def vorticity_velocity(w, R=1.0):
+    """du of the vorticity form: the curl of the Poisson solution of the vorticity correction w."""
+    return stream_velocity(poisson(w, R), R)
+
+
+def vorticity_velocity_adjoint(gt, gp, R=1.0):
+    """The gradient with respect to w of sum(gt du^theta + gp du^phi), du = vorticity_velocity(w).
+    With S = diag(sin theta), S L is symmetric, so the adjoint of the solve is S P S^-1 on the
+    gradients the curl's adjoint leaves (which sum to zero); the mean removal's adjoint
+    subtracts S times their sum over the sum of S."""
+    H, W = gt.shape
+    sc = np.sin((np.arange(H) + 0.5) * math.pi / H)[:, None] * np.ones((1, W))
+    h = stream_velocity_adjoint(gt, gp, R)
+    v = sc * poisson(h / sc, R)
+    return v - sc * v.sum() / sc.sum()
+
+
 def outputs(y, out_scale, form="direct", R=1.0):
     """The correction (drho, du^theta, du^phi) [3][H][W] in physical units from the net output."""
     if form == "direct":
         return np.stack([y[c] * out_scale[c] for c in range(3)])
-    ut, up = stream_velocity(y[0] * out_scale[0], R)
+    if form == "stream":
+        ut, up = stream_velocity(y[0] * out_scale[0], R)
+    else:
+        ut, up = vorticity_velocity(y[0] * out_scale[0], R)
     return np.stack([np.zeros_like(ut), ut, up])
 
 
@@ -216,12 +284,14 @@ def loss_and_grad(params, inputs, targets, in_scale, out_scale, quantize=None, f
         loss = float((aw[None] * r * r).sum() / 3.0)
         g = 2.0 * aw[None] * r / 3.0
     else:
-        ut, up = stream_velocity(y[0] * out_scale[0], R)
+        vel, adj = (stream_velocity, stream_velocity_adjoint) if form == "stream" else \
+            (vorticity_velocity, vorticity_velocity_adjoint)
+        ut, up = vel(y[0] * out_scale[0], R)
         rt = (ut - targets[1]) / out_scale[1]
         rp = (up - targets[2]) / out_scale[2]
         loss = float((aw * (rt * rt + rp * rp)).sum() / 2.0)
         g = np.zeros_like(y)
-        g[0] = out_scale[0] * stream_velocity_adjoint(aw * rt / out_scale[1], aw * rp / out_scale[2], R)
+        g[0] = out_scale[0] * adj(aw * rt / out_scale[1], aw * rp / out_scale[2], R)
     grads = []
     layers = unflatten(params)
     for l in range(len(LAYERS) - 1, -1, -1):

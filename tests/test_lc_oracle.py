@@ -164,3 +164,103 @@ def test_stream_form_backprop_matches_finite_differences():
         lm, _ = L.loss_and_grad(p - e, x, t, ins, outs, form="stream", R=1.5)
         fd = (lp - lm) / (2 * h)
         assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9 * max(1.0, abs(loss)))
+
+
+# ---- the vorticity output form: finite-volume Poisson solve on the sphere --------------------
+
+def _cells(H, W):
+    (TH, PH), _, _ = _grid(H, W)
+    return TH, PH
+
+
+def test_laplacian_is_symmetric_in_the_area_weighted_product_with_constants_as_null_space():
+    H, W, R = 6, 8, 1.4
+    A = L.laplacian_matrix(H, W, R)
+    s = np.repeat(np.sin((np.arange(H) + 0.5) * np.pi / H), W)
+    SA = s[:, None] * A
+    assert np.allclose(SA, SA.T, atol=1e-12 * np.abs(SA).max())
+    assert np.abs(A @ np.ones(H * W)).max() <= 1e-12 * np.abs(A).max()
+    assert np.linalg.matrix_rank(A) == H * W - 1
+
+
+@pytest.mark.parametrize("R", [1.0, 2.0])
+def test_laplacian_of_spherical_harmonics_converges_at_second_order(R):
+    # Y_1^0 = cos(theta) and Y_2^1 = sin(theta) cos(theta) cos(phi) are eigenfunctions of the
+    # Laplacian with -l (l + 1) / R^2; the area-weighted L2 error of the discrete operator falls
+    # by ~4 per halving of the spacing
+    errs = []
+    for H in (16, 32, 64):
+        W = 2 * H
+        TH, PH = _cells(H, W)
+        A = L.laplacian_matrix(H, W, R) if H <= 32 else None
+        e = []
+        for f, lam in ((np.cos(TH), -2.0), (np.sin(TH) * np.cos(TH) * np.cos(PH), -6.0)):
+            if A is not None:
+                lf = (A @ f.ravel()).reshape(H, W)
+            else:   # the same stencil written out for the largest grid (a dense matrix is 67 MB)
+                dth, dph = np.pi / H, 2 * np.pi / W
+                sc = np.sin(TH[:, 0])
+                sf = np.sin(np.arange(H + 1) * dth)
+                sf[0] = sf[H] = 0.0
+                fl = np.zeros((H + 1, W))
+                fl[1:H] = sf[1:H, None] * (f[1:] - f[:-1])
+                lf = (fl[1:] - fl[:-1]) / (R * R * sc[:, None] * dth * dth) + \
+                    (np.roll(f, -1, 1) - 2 * f + np.roll(f, 1, 1)) / (R * R * sc[:, None] ** 2 * dph * dph)
+            w = np.sin(TH)
+            ref = lam / R ** 2 * f
+            e.append(np.sqrt((w * (lf - ref) ** 2).sum() / (w * ref ** 2).sum()))
+        errs.append(e)
+    errs = np.array(errs)
+    order = np.log2(errs[:-1] / errs[1:])
+    assert np.all(order > 1.8), order
+    # (a flux through the pole faces, e.g. to a ghost row across the pole, stops the convergence:
+    # order ~0 with a face sine of sin(dth/4))
+    assert errs[-1].max() < 2e-3
+
+
+def test_poisson_solves_the_mean_free_equation_and_recovers_a_harmonic():
+    H, W, R = 8, 12, 1.3
+    rng = np.random.default_rng(6)
+    w = rng.normal(size=(H, W))
+    psi = L.poisson(w, R)
+    A = L.laplacian_matrix(H, W, R)
+    res = (A @ psi.ravel()).reshape(H, W) - L.area_mean_free(w)
+    assert np.abs(res).max() <= 1e-10 * np.abs(w).max()
+    # psi = Y_2^1 is the solution for w = L Y_2^1 (up to a constant)
+    TH, PH = _cells(H, W)
+    y21 = np.sin(TH) * np.cos(TH) * np.cos(PH)
+    got = L.poisson((A @ y21.ravel()).reshape(H, W), R)
+    d = got - y21
+    assert np.abs(d - d.mean()).max() <= 1e-10
+
+
+def test_vorticity_velocity_adjoint_is_the_transpose():
+    H, W, R = 6, 10, 0.9
+    rng = np.random.default_rng(7)
+    w, gt, gp = rng.normal(size=(3, H, W))
+    ut, up = L.vorticity_velocity(w, R)
+    lhs = (gt * ut + gp * up).sum()
+    rhs = (w * L.vorticity_velocity_adjoint(gt, gp, R)).sum()
+    assert lhs == pytest.approx(rhs, rel=1e-10)
+    # the adjoint of the mean removal: a vorticity that is a multiple of 1 moves nothing
+    ut1, up1 = L.vorticity_velocity(np.full((H, W), 3.0), R)
+    assert np.abs(ut1).max() < 1e-12 and np.abs(up1).max() < 1e-12
+
+
+def test_vorticity_form_backprop_matches_finite_differences():
+    H, W = 6, 8
+    x, t = _sample(H, W, 6)
+    p = L.init_params(11)
+    p[-3:] = [0.02, 0.0, 0.0]
+    ins, outs = [1e-3, 2e-2, 2e-2, 1e-2] + [1e-3] * 10, [1e-3, 1e-4, 1e-4]
+    loss, g = L.loss_and_grad(p, x, t, ins, outs, form="vorticity", R=1.2)
+    rng = np.random.default_rng(3)
+    idx = rng.choice(p.size - 3, 30, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        lp, _ = L.loss_and_grad(p + e, x, t, ins, outs, form="vorticity", R=1.2)
+        lm, _ = L.loss_and_grad(p - e, x, t, ins, outs, form="vorticity", R=1.2)
+        fd = (lp - lm) / (2 * h)
+        assert fd == pytest.approx(g[i], rel=1e-5, abs=1e-9 * max(1.0, abs(loss)))
