@@ -279,6 +279,7 @@ VLBM_API int vlbm_lc_set_scales(vlbm_lc_t *lc, const double *in_scale, const dou
 /* Output forms of vlbm_lc_set_output_form. */
 #define VLBM_LC_DIRECT 0
 #define VLBM_LC_STREAM 1
+#define VLBM_LC_VORTICITY 2
 /* The form of the correction (not in the paper).  VLBM_LC_DIRECT (the default): the three
  * outputs times out_scale are (drho, du^theta, du^phi).  VLBM_LC_STREAM: output 0 times
  * out_scale[0] is a stream function psi on the cell grid of a sphere of the given radius, and
@@ -287,9 +288,14 @@ VLBM_API int vlbm_lc_set_scales(vlbm_lc_t *lc, const double *in_scale, const dou
  * opposite meridian (column + n_phi/2).  That correction has zero centred divergence: it moves
  * the vorticity without launching sound waves.  Training then fits the velocity targets
  * (residuals scaled by out_scale[1], out_scale[2]; the mean over cells and the two channels)
- * and ignores the drho target; outputs 1 and 2 of the network are unused.  vlbm_lc_apply and
- * vlbm_lc_rollout require radius = the solver's (VLBM_ERR_ARG otherwise).  VLBM_ERR_ARG for
- * an unknown form or radius <= 0.  Rebuilds the rollout graph. */
+ * and ignores the drho target; outputs 1 and 2 of the network are unused.
+ * VLBM_LC_VORTICITY: output 0 times out_scale[0] is a vorticity correction w, psi solves the
+ * cell-centred finite-volume Poisson equation on the sphere, L psi = w - (sin theta-area mean
+ * of w) (no flux through the pole faces; a DFT along phi and a tridiagonal solve per Fourier
+ * mode), and the correction is the curl of psi as in VLBM_LC_STREAM (same training): the
+ * network's output stays local while psi, an integral of the correction, spans the grid.
+ * vlbm_lc_apply and vlbm_lc_rollout require radius = the solver's for both (VLBM_ERR_ARG
+ * otherwise).  VLBM_ERR_ARG for an unknown form or radius <= 0.  Rebuilds the rollout graph. */
 VLBM_API int vlbm_lc_set_output_form(vlbm_lc_t *lc, int form, double radius);
 /* Forward pass: the correction in physical units (drho not mean-corrected). */
 VLBM_API int vlbm_lc_predict(vlbm_lc_t *lc, const double *inputs, double *outputs);

@@ -19,6 +19,9 @@
 //   backward weight: dW[co][tap][ci] = sum_p dY[p][co] pad(X)[p + tap][ci].
 #include <cuda_bf16.h>
 
+#include <cmath>
+#include <vector>
+
 #include "vlbm_internal.h"
 #include "lc_internal.h"
 
@@ -516,8 +519,10 @@ __global__ void outputs_kernel(const float *Y, int CO, int H, int W, float3 scal
 // du^phi = -s0 (psi[i+1][j] - psi[i-1][j]) / (2 R dtheta); a row beyond a pole is the edge row on
 // the opposite meridian (column + W/2; psi is a scalar: no sign change).
 
-// output 0 of cell (i, j), rows beyond a pole and columns wrapped as above
-__device__ __forceinline__ double psi_at(const float *Y, int CO, int H, int W, int i, int j)
+// psi of cell (i, j) (element i W + j times CO of Y: output 0 of the net, or a psi array with
+// CO = 1), rows beyond a pole and columns wrapped as above
+template <typename T>
+__device__ __forceinline__ double psi_at(const T *Y, int CO, int H, int W, int i, int j)
 {
     if (i < 0) {
         i = 0;
@@ -531,8 +536,9 @@ __device__ __forceinline__ double psi_at(const float *Y, int CO, int H, int W, i
     return (double)Y[((size_t)i * W + j) * CO];
 }
 
-__device__ __forceinline__ void stream_uv(const float *Y, int CO, const LcStream &g, const double *sin_t, int i,
-                                          int j, double &ut, double &up)
+template <typename T>
+__device__ __forceinline__ void stream_uv(const T *Y, int CO, const LcStream &g, const double *sin_t, int i, int j,
+                                          double &ut, double &up)
 {
     ut = g.s0 * (psi_at(Y, CO, g.H, g.W, i, j + 1) - psi_at(Y, CO, g.H, g.W, i, j - 1)) /
          (2.0 * g.R * g.dph * sin_t[i]);
@@ -542,7 +548,8 @@ __device__ __forceinline__ void stream_uv(const float *Y, int CO, const LcStream
 // loss of the stream form: the sin-area-weighted mean over cells and the two velocity channels of
 // ((du - target) / out_scale)^2; per cell the loss's derivatives by du^theta and du^phi into gv
 // [2][H][W]; per block partial sums of the loss
-__global__ void stream_loss_kernel(const float *Y, int CO, const double *target, const double *sin_t, LcStream g,
+template <typename T>
+__global__ void stream_loss_kernel(const T *Y, int CO, const double *target, const double *sin_t, LcStream g,
                                    double inv_s1, double inv_s2, double wsum, double *gv, double *part)
 {
     __shared__ double red[256];
@@ -568,9 +575,10 @@ __global__ void stream_loss_kernel(const float *Y, int CO, const double *target,
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-// gradient at the net output (dY [H][W][CO]): output 0 gets the adjoint of the curl applied to
-// gv (times s0), the other outputs 0
-__global__ void stream_adjoint_kernel(const double *gv, int CO, LcStream g, const double *sin_t, float *dY)
+// the adjoint of the curl applied to gv, times s0, into element c CO of dY ([H][W][CO]; the
+// net's output gradient, whose other outputs get 0) or of a plain array (CO = 1)
+template <typename TO>
+__global__ void stream_adjoint_kernel(const double *gv, int CO, LcStream g, const double *sin_t, TO *dY)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int H = g.H, W = g.W, HW = H * W;
@@ -587,13 +595,14 @@ __global__ void stream_adjoint_kernel(const double *gv, int CO, LcStream g, cons
     else d += kb * gp[jo];
     if (i < H - 1) d += kb * gp[(size_t)(i + 1) * W + j];
     else d -= kb * gp[(size_t)(H - 1) * W + jo];
-    dY[(size_t)c * CO] = (float)(g.s0 * d);
-    for (int o = 1; o < CO; ++o) dY[(size_t)c * CO + o] = 0.0f;
+    dY[(size_t)c * CO] = (TO)(g.s0 * d);
+    for (int o = 1; o < CO; ++o) dY[(size_t)c * CO + o] = (TO)0;
 }
 
 // the stream form's correction (0, du^theta, du^phi) [3][H][W] in physical units; the drho
 // partial sums are 0
-__global__ void stream_outputs_kernel(const float *Y, int CO, LcStream g, const double *sin_t, double *out,
+template <typename T>
+__global__ void stream_outputs_kernel(const T *Y, int CO, LcStream g, const double *sin_t, double *out,
                                       double *part)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -607,6 +616,202 @@ __global__ void stream_outputs_kernel(const float *Y, int CO, LcStream g, const 
         out[2 * (size_t)HW + c] = up;
     }
     if (threadIdx.x == 0) part[blockIdx.x] = 0.0;
+}
+
+// ---- vorticity output form: psi from the finite-volume Poisson equation on the sphere,
+// L psi = w - (area mean of w), with
+//   (L psi)_ij = (sf_{i+1} (psi_{i+1,j} - psi_ij) - sf_i (psi_ij - psi_{i-1,j})) / (R^2 s_i dth^2)
+//              + (psi_{i,j+1} - 2 psi_ij + psi_{i,j-1}) / (R^2 s_i^2 dph^2),
+// s_i = sin theta_i at the cell centres and sf_i = sin(i dth) at the faces, 0 at both poles (no
+// flux through a pole face).  Along phi a DFT on the cell centres phi_j = (j + 1/2) dph,
+// X_m = sum_j x_j exp(-i m phi_j) for m = 0 .. W/2, in FP32 (twiddles by complex rotation,
+// re-anchored from a table of (cos, sin)(pi k / W)).  Per mode m > 0 a tridiagonal system in theta (the second difference
+// along phi has the symbol -(2 sin(m dph / 2) / dph)^2; diagonally dominant), solved in FP32 by the
+// Thomas recursion with its factors tabulated per (mode, row) from FP64; mode 0 integrated from the
+// north pole as the conservative flux G_{i+1} = G_i + dth^2 s_i X_0,i (G_0 = 0), psi_{i+1} = psi_i +
+// G_{i+1} / sf_{i+1}, psi_0 = 0 (the constant of psi has no curl).  FP32 throughout the solve:
+// GB300's FP64 units make a serial FP64 recursion ~100x slower, and the recursion is stable for
+// diagonally dominant systems, its error within the condition number (~1e4 at m = 1 on 128 rows)
+// times FP32 rounding.  The tables are for R = 1; the right side carries R^2.  Modes are stored
+// mode-major, X[m][i].
+
+// per-block partial sums of x [n] (cells of rows of W; weighted by the cell sine when `weighted`)
+__global__ void cell_sums_kernel(const double *x, int n, int W, const double *sin_t, int weighted, double *part)
+{
+    __shared__ double red[256];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (c < n) v = weighted ? x[c] * sin_t[c / W] : x[c];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// the vorticity correction w = s0 * output 0 of the net, and per-block partial sums of s_i w
+__global__ void vort_in_kernel(const float *Y, int CO, int n, int W, double s0, const double *sin_t, double *w,
+                               double *part)
+{
+    __shared__ double red[256];
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (c < n) {
+        const double x = s0 * (double)Y[(size_t)c * CO];
+        w[c] = x;
+        v = x * sin_t[c / W];
+    }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// DFT of row i (block i, threads over the modes) of R^2 (x / s_i^inv_sin - mean), the mean the sum
+// of the nb partial sums over wsum; X[m][i].  Thread m advances exp(-i m phi_j) by complex rotation
+// through exp(-i m dph) and re-anchors it from the table tw[k] = (cos, sin)(pi k / W) every
+// DFT_ANCHOR columns (m phi_j = pi m (2j + 1) / W).
+constexpr int DFT_ANCHOR = 16;
+__global__ void dft_rows_kernel(const double *x, int H, int W, const double *sin_t, int inv_sin, const double *part,
+                                int nb, double wsum, double R2, const float2 *tw, float2 *X)
+{
+    extern __shared__ float row[];
+    __shared__ double red[256];
+    const int i = blockIdx.x, M = W / 2 + 1, W2 = 2 * W;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[b];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    const double mean = red[0] / wsum, rs = inv_sin ? 1.0 / sin_t[i] : 1.0;
+    for (int j = threadIdx.x; j < W; j += blockDim.x) row[j] = (float)(R2 * (x[(size_t)i * W + j] * rs - mean));
+    __syncthreads();
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float2 st = tw[(2 * m) % W2];   // exp(+i m dph)
+        float re = 0.0f, im = 0.0f;
+        for (int j0 = 0; j0 < W; j0 += DFT_ANCHOR) {
+            const float2 z0 = tw[(int)(((long long)m * (2 * j0 + 1)) % W2)];
+            float zc = z0.x, zs = z0.y;   // exp(+i m phi_j) = (zc, zs)
+            const int j1 = min(j0 + DFT_ANCHOR, W);
+            for (int j = j0; j < j1; ++j) {
+                re = fmaf(row[j], zc, re);
+                im = fmaf(-row[j], zs, im);
+                const float c2 = zc * st.x - zs * st.y, s2 = fmaf(zc, st.y, zs * st.x);
+                zc = c2;
+                zs = s2;
+            }
+        }
+        X[(size_t)m * H + i] = make_float2(re, im);
+    }
+}
+
+// Poisson solve of every mode in place, one warp per mode: the lanes stage the mode's column and
+// its recursion factors in shared memory, lane 0 runs the recursion there, the lanes write the
+// solution back.  tab[m][i] = (c'_i, 1 / (b_i - a_i c'_{i-1})) for m > 0 and (dth^2 s_i,
+// 1 / sf_{i+1}) for m = 0; a[i] = sf_i / (s_i dth^2).  Shared memory: a[H], then per warp the
+// column and the factors (2 x H float2).
+constexpr int TRI_WARPS = 4;
+__global__ void __launch_bounds__(TRI_WARPS * 32) tri_solve_kernel(float2 *__restrict__ X, int H, int M,
+                                                                   const float2 *__restrict__ tab,
+                                                                   const float *__restrict__ a)
+{
+    extern __shared__ float2 tsm[];
+    float *as = reinterpret_cast<float *>(tsm);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) as[i] = a[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int m = blockIdx.x * TRI_WARPS + wp;
+    if (m >= M) return;
+    float2 *xs = tsm + (H + 1) / 2 + (size_t)wp * 2 * H;   // past a[] (H floats, rounded to float2)
+    float2 *ts = xs + H;
+    for (int i = lane; i < H; i += 32) {
+        xs[i] = X[(size_t)m * H + i];
+        ts[i] = tab[(size_t)m * H + i];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        if (m == 0) {
+            float G = 0.0f, psi = 0.0f;
+            for (int i = 0; i < H; ++i) {
+                const float d = xs[i].x;
+                const float2 t = ts[i];
+                xs[i] = make_float2(psi, 0.0f);
+                if (i + 1 < H) {
+                    G = fmaf(t.x, d, G);
+                    psi = fmaf(G, t.y, psi);
+                }
+            }
+        } else {
+            float2 dp = make_float2(0.0f, 0.0f);   // d'_i = (d_i - a_i d'_{i-1}) r_i
+            for (int i = 0; i < H; ++i) {
+                const float r = ts[i].y, ai = as[i];
+                const float2 d = xs[i];
+                dp = make_float2(fmaf(-ai, dp.x, d.x) * r, fmaf(-ai, dp.y, d.y) * r);
+                xs[i] = dp;
+            }
+            float2 p = make_float2(0.0f, 0.0f);    // psi_i = d'_i - c'_i psi_{i+1}
+            for (int i = H - 1; i >= 0; --i) {
+                const float c = ts[i].x;
+                const float2 d = xs[i];
+                p = make_float2(fmaf(-c, p.x, d.x), fmaf(-c, p.y, d.y));
+                xs[i] = p;
+            }
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < H; i += 32) X[(size_t)m * H + i] = xs[i];
+}
+
+// inverse DFT of row i (block i, threads over the columns): psi_ij = (X_0 + 2 sum_{0<m<W/2}
+// Re(X_m e^{i m phi_j}) + Re(X_{W/2} e^{i W/2 phi_j})) / W; thread j advances exp(i m phi_j) over m by
+// rotation through exp(i phi_j), re-anchored from the table every DFT_ANCHOR modes
+__global__ void idft_rows_kernel(const float2 *X, int H, int W, const float2 *tw, double *psi)
+{
+    extern __shared__ float2 xr[];
+    const int i = blockIdx.x, M = W / 2 + 1, W2 = 2 * W;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float2 v = X[(size_t)m * H + i];
+        const float f = (m == 0 || 2 * m == W) ? 1.0f : 2.0f;
+        xr[m] = make_float2(f * v.x, f * v.y);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        const float2 st = tw[(2 * j + 1) % W2];   // exp(i phi_j)
+        float acc = 0.0f;
+        for (int m0 = 0; m0 < M; m0 += DFT_ANCHOR) {
+            const float2 z0 = tw[(int)(((long long)m0 * (2 * j + 1)) % W2)];
+            float zc = z0.x, zs = z0.y;
+            const int m1 = min(m0 + DFT_ANCHOR, M);
+            for (int m = m0; m < m1; ++m) {
+                acc = fmaf(xr[m].x, zc, acc);
+                acc = fmaf(-xr[m].y, zs, acc);
+                const float c2 = zc * st.x - zs * st.y, s2 = fmaf(zc, st.y, zs * st.x);
+                zc = c2;
+                zs = s2;
+            }
+        }
+        psi[(size_t)i * W + j] = (double)acc / W;
+    }
+}
+
+// the vorticity form's output gradient: dY[c CO] = s0 (s_i u_c - s_i (*sum) / wsum) (the adjoint of
+// the solve S P S^-1, then of the mean removal), the other outputs 0
+__global__ void vort_grad_kernel(const double *u, int H, int W, int CO, const double *sin_t, const double *sum,
+                                 double wsum, double s0, float *dY)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= H * W) return;
+    const double si = sin_t[c / W];
+    dY[(size_t)c * CO] = (float)(s0 * si * (u[c] - *sum / wsum));
+    for (int o = 1; o < CO; ++o) dY[(size_t)c * CO + o] = 0.0f;
 }
 
 // Moments (rho, u^theta, u^phi, T) of the FP32 pair layout (dg = ks s (f - w rho_ref)) in FP32
@@ -766,17 +971,112 @@ void lc_stream_loss(const float *Y, int CO, const double *target, const double *
                     cudaStream_t s)
 {
     const int nb = (g.H * g.W + 255) / 256;
-    stream_loss_kernel<<<nb, 256, 0, s>>>(Y, CO, target, sin_t, g, inv_s1, inv_s2, wsum, gv, part);
+    stream_loss_kernel<float><<<nb, 256, 0, s>>>(Y, CO, target, sin_t, g, inv_s1, inv_s2, wsum, gv, part);
     sum_kernel<<<1, 256, 0, s>>>(part, nb, loss);
-    stream_adjoint_kernel<<<nb, 256, 0, s>>>(gv, CO, g, sin_t, dY);
+    stream_adjoint_kernel<float><<<nb, 256, 0, s>>>(gv, CO, g, sin_t, dY);
 }
 
 void lc_stream_outputs(const float *Y, int CO, const LcStream &g, const double *sin_t, double *out, double *part,
                        double *mean, cudaStream_t s)
 {
     const int nb = (g.H * g.W + 255) / 256;
-    stream_outputs_kernel<<<nb, 256, 0, s>>>(Y, CO, g, sin_t, out, part);
+    stream_outputs_kernel<float><<<nb, 256, 0, s>>>(Y, CO, g, sin_t, out, part);
     sum_kernel<<<1, 256, 0, s>>>(part, nb, mean);
+}
+
+// dynamic shared memory of the mode solve for H rows
+static size_t tri_smem(int H) { return sizeof(float2) * ((H + 1) / 2 + (size_t)TRI_WARPS * 2 * H); }
+
+// psi [H][W] solving L psi = x / s^inv_sin - (area mean) (x [H][W]); part holds the nb per-block
+// partial sums of the area mean's numerator (sum s x, or sum x for the adjoint's right side)
+static void poisson(const double *x, int inv_sin, int nb, double *psi, const LcPoisson &P, const double *sin_t,
+                    cudaStream_t s)
+{
+    const int M = P.W / 2 + 1;
+    dft_rows_kernel<<<P.H, 256, P.W * sizeof(float), s>>>(x, P.H, P.W, sin_t, inv_sin, P.part, nb, P.wsum,
+                                                          P.R * P.R, P.tw, P.X);
+    tri_solve_kernel<<<(M + TRI_WARPS - 1) / TRI_WARPS, TRI_WARPS * 32, tri_smem(P.H), s>>>(P.X, P.H, M, P.tab, P.a);
+    idft_rows_kernel<<<P.H, 256, M * sizeof(float2), s>>>(P.X, P.H, P.W, P.tw, psi);
+}
+
+void lc_vort_loss(const float *Y, int CO, const double *target, const double *sin_t, const LcStream &g,
+                  const LcPoisson &P, double inv_s1, double inv_s2, double wsum, double *gv, float *dY, double *part,
+                  double *loss, cudaStream_t s)
+{
+    const int n = g.H * g.W, nb = (n + 255) / 256;
+    const LcStream g1{g.H, g.W, 1.0, g.R, g.dth, g.dph};
+    vort_in_kernel<<<nb, 256, 0, s>>>(Y, CO, n, g.W, g.s0, sin_t, P.w, P.part);
+    poisson(P.w, 0, nb, P.psi, P, sin_t, s);
+    stream_loss_kernel<double><<<nb, 256, 0, s>>>(P.psi, 1, target, sin_t, g1, inv_s1, inv_s2, wsum, gv, part);
+    sum_kernel<<<1, 256, 0, s>>>(part, nb, loss);
+    // backward: the curl's adjoint, the solve's adjoint S P S^-1 and the mean removal's
+    stream_adjoint_kernel<double><<<nb, 256, 0, s>>>(gv, 1, g1, sin_t, P.w);
+    cell_sums_kernel<<<nb, 256, 0, s>>>(P.w, n, P.W, sin_t, 0, P.part);
+    poisson(P.w, 1, nb, P.psi, P, sin_t, s);
+    cell_sums_kernel<<<nb, 256, 0, s>>>(P.psi, n, P.W, sin_t, 1, P.part);
+    sum_kernel<<<1, 256, 0, s>>>(P.part, nb, P.sum);
+    vort_grad_kernel<<<nb, 256, 0, s>>>(P.psi, g.H, g.W, CO, sin_t, P.sum, P.wsum, g.s0, dY);
+}
+
+void lc_vort_outputs(const float *Y, int CO, const LcStream &g, const LcPoisson &P, const double *sin_t, double *out,
+                     double *part, double *mean, cudaStream_t s)
+{
+    const int n = g.H * g.W, nb = (n + 255) / 256;
+    const LcStream g1{g.H, g.W, 1.0, g.R, g.dth, g.dph};
+    vort_in_kernel<<<nb, 256, 0, s>>>(Y, CO, n, g.W, g.s0, sin_t, P.w, P.part);
+    poisson(P.w, 0, nb, P.psi, P, sin_t, s);
+    stream_outputs_kernel<double><<<nb, 256, 0, s>>>(P.psi, 1, g1, sin_t, out, part);
+    sum_kernel<<<1, 256, 0, s>>>(part, nb, mean);
+}
+
+int lc_poisson_prepare(int H)
+{
+    const size_t b = tri_smem(H);
+    if (b <= 48 * 1024) return 0;
+    return cudaFuncSetAttribute(tri_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) == cudaSuccess
+               ? 0
+               : -1;
+}
+
+size_t lc_poisson_table_floats(int H, int W)
+{
+    const size_t M = (size_t)W / 2 + 1;
+    return 2 * M * H + H + (H & 1) + 4 * (size_t)W;   // tab (float2), a (padded to even), tw (float2 [2W])
+}
+
+int lc_poisson_tables(int H, int W, float *dev)
+{
+    const int M = W / 2 + 1;
+    const double dth = M_PI / H, dph = 2.0 * M_PI / W;
+    std::vector<double> sc(H), sf(H + 1), av(H);
+    for (int i = 0; i < H; ++i) sc[i] = std::sin((i + 0.5) * dth);
+    for (int i = 0; i <= H; ++i) sf[i] = (i == 0 || i == H) ? 0.0 : std::sin(i * dth);
+    for (int i = 0; i < H; ++i) av[i] = sf[i] / (sc[i] * dth * dth);
+    std::vector<float> h(lc_poisson_table_floats(H, W));
+    float *tab = h.data(), *a = tab + 2 * (size_t)M * H, *tw = a + H + (H & 1);   // tw 8-byte aligned
+    for (int i = 0; i < H; ++i) {   // mode 0: the integration's factors
+        tab[2 * i] = (float)(dth * dth * sc[i]);
+        tab[2 * i + 1] = i + 1 < H ? (float)(1.0 / sf[i + 1]) : 0.0f;
+    }
+    for (int m = 1; m < M; ++m) {
+        const double sm = 2.0 * std::sin(0.5 * m * dph) / dph, lam = sm * sm;
+        double cprev = 0.0;
+        for (int i = 0; i < H; ++i) {
+            const double ai = av[i], ci = sf[i + 1] / (sc[i] * dth * dth);
+            const double bi = -(ai + ci) - lam / (sc[i] * sc[i]);
+            const double r = 1.0 / (bi - ai * cprev);
+            const double cp = ci * r;
+            tab[2 * ((size_t)m * H + i)] = (float)cp;
+            tab[2 * ((size_t)m * H + i) + 1] = (float)r;
+            cprev = cp;
+        }
+    }
+    for (int i = 0; i < H; ++i) a[i] = (float)av[i];
+    for (int k = 0; k < 2 * W; ++k) {
+        tw[2 * k] = (float)std::cos(M_PI * k / W);
+        tw[2 * k + 1] = (float)std::sin(M_PI * k / W);
+    }
+    return cudaMemcpy(dev, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice) == cudaSuccess ? 0 : -1;
 }
 
 void lc_adam(float *w, const float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps, float c1,

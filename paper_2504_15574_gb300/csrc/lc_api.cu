@@ -38,6 +38,10 @@ struct vlbm_lc {
     int form = VLBM_LC_DIRECT;   // output form (vlbm_lc_set_output_form)
     double radius = 1.0;         // the stream form's sphere radius
     double *d_gv = nullptr;      // stream form: the loss's derivatives by du^theta, du^phi [2][H][W]
+    // vorticity form: Poisson tables (R = 1) and work arrays
+    float *d_ptabs = nullptr;    // tab, a, tw (lc_poisson_tables)
+    float2 *d_pX = nullptr;
+    double *d_pw = nullptr, *d_psi = nullptr, *d_ppart = nullptr, *d_psum = nullptr;
     long long t = 0;
     std::vector<void *> bufs;
     cudaGraphExec_t g_exec = nullptr;   // vlbm_lc_rollout: one corrected step of solver g_solver
@@ -110,11 +114,23 @@ LcStream stream_geometry(const vlbm_lc_t *n)
     return LcStream{n->H, n->W, (double)n->out_scale[0], n->radius, M_PI / n->H, 2.0 * M_PI / n->W};
 }
 
+LcPoisson poisson_work(const vlbm_lc_t *n)
+{
+    const size_t M = (size_t)n->W / 2 + 1, H = n->H, W = n->W;
+    const float *t = n->d_ptabs, *a = t + 2 * M * H, *tw = a + H + (H & 1);   // as laid out by lc_poisson_tables
+    (void)W;
+    return LcPoisson{n->H, n->W, n->radius, n->wsum, reinterpret_cast<const float2 *>(t), a,
+                     reinterpret_cast<const float2 *>(tw), n->d_pX, n->d_pw, n->d_psi, n->d_ppart, n->d_psum};
+}
+
 // the correction in physical units into d_out ([3][H][W]) and the area sum of its drho into
 // d_scal[1], from the forward pass's output d_y
 void enqueue_outputs(vlbm_lc_t *n, cudaStream_t s)
 {
-    if (n->form == VLBM_LC_STREAM) {
+    if (n->form == VLBM_LC_VORTICITY) {
+        lc_vort_outputs(n->d_y, LC_COUT, stream_geometry(n), poisson_work(n), n->d_sin, n->d_out, n->d_part,
+                        n->d_scal + 1, s);
+    } else if (n->form == VLBM_LC_STREAM) {
         lc_stream_outputs(n->d_y, LC_COUT, stream_geometry(n), n->d_sin, n->d_out, n->d_part, n->d_scal + 1, s);
     } else {
         const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
@@ -126,7 +142,10 @@ void enqueue_outputs(vlbm_lc_t *n, cudaStream_t s)
 int backward(vlbm_lc_t *n)
 {
     const int H = n->H, W = n->W, HW = H * W;
-    if (n->form == VLBM_LC_STREAM) {
+    if (n->form == VLBM_LC_VORTICITY) {
+        lc_vort_loss(n->d_y, LC_COUT, n->d_tg, n->d_sin, stream_geometry(n), poisson_work(n), 1.0 / n->out_scale[1],
+                     1.0 / n->out_scale[2], n->wsum, n->d_gv, n->d_dy, n->d_part, n->d_scal, n->stream);
+    } else if (n->form == VLBM_LC_STREAM) {
         lc_stream_loss(n->d_y, LC_COUT, n->d_tg, n->d_sin, stream_geometry(n), 1.0 / n->out_scale[1],
                        1.0 / n->out_scale[2], n->wsum, n->d_gv, n->d_dy, n->d_part, n->d_scal, n->stream);
     } else {
@@ -158,8 +177,8 @@ int check_solver(vlbm_lc_t *n, vlbm_t *h)
     if (!n || !h) return VLBM_ERR_ARG;
     if (h->prec != VLBM_FP32 || h->vd.q != 4 || h->nt != n->H || h->np != n->W)
         return lfail(n, VLBM_ERR_ARG, "the solver must be FP32 D2Q16 on the network's grid");
-    if (n->form == VLBM_LC_STREAM && n->radius != h->R)
-        return lfail(n, VLBM_ERR_ARG, "the stream form's radius differs from the solver's");
+    if (n->form != VLBM_LC_DIRECT && n->radius != h->R)
+        return lfail(n, VLBM_ERR_ARG, "the output form's radius differs from the solver's");
     return VLBM_OK;
 }
 
@@ -257,6 +276,13 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
     A(&n->d_bpart, (size_t)n_theta * LC_HID);
     A(&n->d_g9, (size_t)9 * LC_HID * LC_HID);
     A(&n->d_gv, 2 * HW);
+    const size_t M = (size_t)n_phi / 2 + 1;
+    A(&n->d_ptabs, lc_poisson_table_floats(n_theta, n_phi));
+    A(&n->d_pX, (size_t)n_theta * M);
+    A(&n->d_pw, HW);
+    A(&n->d_psi, HW);
+    A(&n->d_ppart, HW / 256 + 2);
+    A(&n->d_psum, 1);
     if (rc) {
         vlbm_lc_destroy(n);
         return rc;
@@ -273,6 +299,7 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
     if (cudaMemcpy(n->d_sin, sn.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(n->d_cos, cs.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(n->d_w, w.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
+        lc_poisson_tables(n_theta, n_phi, n->d_ptabs) != 0 || lc_poisson_prepare(n_theta) != 0 ||
         refresh_bf16(n) != VLBM_OK || cudaStreamSynchronize(n->stream) != cudaSuccess) {
         vlbm_lc_destroy(n);
         return VLBM_ERR_CUDA;
@@ -324,7 +351,8 @@ int vlbm_lc_set_scales(vlbm_lc_t *n, const double *in_scale, const double *out_s
 int vlbm_lc_set_output_form(vlbm_lc_t *n, int form, double radius)
 {
     if (!n) return VLBM_ERR_ARG;
-    if (form != VLBM_LC_DIRECT && form != VLBM_LC_STREAM) return lfail(n, VLBM_ERR_ARG, "unknown output form");
+    if (form != VLBM_LC_DIRECT && form != VLBM_LC_STREAM && form != VLBM_LC_VORTICITY)
+        return lfail(n, VLBM_ERR_ARG, "unknown output form");
     if (!(radius > 0.0) || !std::isfinite(radius)) return lfail(n, VLBM_ERR_ARG, "radius must be > 0");
     if (n->g_exec) {   // the form is part of the captured rollout step
         cudaGraphExecDestroy(n->g_exec);

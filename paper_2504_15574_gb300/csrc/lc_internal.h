@@ -66,5 +66,30 @@ void lc_stream_loss(const float *Y, int CO, const double *target, const double *
 // The stream form's correction (0, du^theta, du^phi) [3][H][W]; *mean (the drho area sum) = 0.
 void lc_stream_outputs(const float *Y, int CO, const LcStream &g, const double *sin_t, double *out, double *part,
                        double *mean, cudaStream_t s);
+// Vorticity output form: output 0 times s0 is a vorticity correction w; psi solves the
+// finite-volume Poisson equation L psi = w - (area mean of w) on the sphere of radius R, and the
+// correction is the curl of psi as in the stream form.  Device tables and work arrays:
+struct LcPoisson {
+    int H, W;
+    double R, wsum;
+    const float2 *tab;    // [W/2 + 1][H] Thomas factors (and the mode-0 integration's)
+    const float *a;       // [H] sub-diagonal of the theta operator
+    const float2 *tw;     // [2W] (cos, sin)(pi k / W)
+    float2 *X;            // [W/2 + 1][H] modes
+    double *w, *psi;      // [H][W]
+    double *part, *sum;   // reduction scratch (>= H W / 256 + 1) and one total
+};
+void lc_vort_loss(const float *Y, int CO, const double *target, const double *sin_t, const LcStream &g,
+                  const LcPoisson &P, double inv_s1, double inv_s2, double wsum, double *gv, float *dY, double *part,
+                  double *loss, cudaStream_t s);
+void lc_vort_outputs(const float *Y, int CO, const LcStream &g, const LcPoisson &P, const double *sin_t, double *out,
+                     double *part, double *mean, cudaStream_t s);
+// The tables of an H x W grid (R = 1): their size in floats, and a blocking fill of a device array
+// of that size laid out as tab, a, tw (0 on success).
+size_t lc_poisson_table_floats(int H, int W);
+// Raises the mode solve's shared-memory limit where H rows need more than 48 KB (0 on success;
+// call outside any stream capture).
+int lc_poisson_prepare(int H);
+int lc_poisson_tables(int H, int W, float *dev);
 
 }  // namespace vk

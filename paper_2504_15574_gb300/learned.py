@@ -260,11 +260,19 @@ def stream_scale(setup: Setup, outs):
     return 0.5 * (outs[1] + outs[2]) * 8.0 * math.pi / setup.coarse[0]
 
 
+def vorticity_scale(setup: Setup, outs):
+    """Output scale of the vorticity correction: the velocity targets' spread over R times 4
+    coarse theta spacings (a velocity correction varying over ~4 cells has that vorticity)."""
+    return 0.5 * (outs[1] + outs[2]) / (4.0 * math.pi / setup.coarse[0])
+
+
 def train(setup: Setup, X, Y, epochs=4, lr=2e-3, seed=1, log=None, net=None, form="direct"):
     if net is None:
         ins, outs = scales(X, Y)
         if form == "stream":
             outs = [stream_scale(setup, outs), outs[1], outs[2]]
+        elif form == "vorticity":
+            outs = [vorticity_scale(setup, outs), outs[1], outs[2]]
         net = vlbm.LearnedCorrection(*setup.coarse, seed=seed, in_scale=ins, out_scale=outs, form=form)
     rng = np.random.default_rng(seed)
     hist = []
@@ -432,8 +440,9 @@ def main(argv=None):
                     help="resolution multiples of the coarse grid for plain runs at each horizon (e.g. 2 3)")
     ap.add_argument("--save-data", default=None, help="write the training samples (.npz)")
     ap.add_argument("--load-data", default=None, help="read the training samples (.npz) instead of making them")
-    ap.add_argument("--form", choices=["direct", "stream"], default="direct",
-                    help="correction form: (drho, du) outputs, or the curl of a stream function")
+    ap.add_argument("--form", choices=["direct", "stream", "vorticity"], default="direct",
+                    help="correction form: (drho, du) outputs, the curl of a predicted stream function, or of the "
+                         "Poisson solution for a predicted vorticity")
     ap.add_argument("--timing-steps", type=int, default=0,
                     help="only time this many corrected coarse steps of an untrained network (no data, no training)")
     a = ap.parse_args(argv)

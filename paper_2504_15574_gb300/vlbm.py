@@ -413,7 +413,7 @@ class LearnedCorrection:
     # scales of the 14 data channels: rho-1, u^theta, u^phi, T-1, then the ten differences
     DEFAULT_IN_SCALE = (1e-3, 1e-2, 1e-2, 1e-3) + (1e-6,) * 2 + (1e-5,) * 8
 
-    FORMS = {"direct": 0, "stream": 1}
+    FORMS = {"direct": 0, "stream": 1, "vorticity": 2}
 
     def __init__(self, n_theta, n_phi, seed=1, in_scale=DEFAULT_IN_SCALE, out_scale=(1e-5, 1e-4, 1e-4),
                  form="direct", R=1.0):
@@ -427,7 +427,9 @@ class LearnedCorrection:
 
     def set_output_form(self, form, R=1.0):
         """"direct": outputs (drho, du^theta, du^phi); "stream": output 0 is a stream function
-        whose centred curl on a sphere of radius R is the velocity correction (drho = 0)."""
+        whose centred curl on a sphere of radius R is the velocity correction (drho = 0);
+        "vorticity": output 0 is a vorticity correction, the stream function the solution of the
+        finite-volume Poisson equation for it."""
         self._chk(load().vlbm_lc_set_output_form(self.h, self.FORMS[form], float(R)))
         self.form, self.R = form, float(R)
 

@@ -223,32 +223,35 @@ def _bf16_weights(p):
     return pw
 
 
+@pytest.mark.parametrize("form", ["stream", "vorticity"])
 @pytest.mark.parametrize("H,W,R", [(16, 32, 1.0), (24, 64, 1.3)])
-def test_stream_form_matches_fp64_reference(V, H, W, R):
-    """Correction (the curl of output 0), loss and every parameter gradient of the stream form
-    against the FP64 reference; outputs 1 and 2 get exactly no gradient."""
-    net = V.LearnedCorrection(H, W, seed=5, in_scale=IN_SCALE, out_scale=STREAM_OUT, form="stream", R=R)
+def test_stream_form_matches_fp64_reference(V, H, W, R, form):
+    """Correction (the curl of output 0, or of the Poisson solution for it), loss and every
+    parameter gradient of the divergence-free forms against the FP64 reference; outputs 1 and 2
+    get exactly no gradient."""
+    net = V.LearnedCorrection(H, W, seed=5, in_scale=IN_SCALE, out_scale=STREAM_OUT, form=form, R=R)
     p = net.get_weights().astype(np.float64)
     p[-3:] = [0.3, -0.2, 0.1]
     net.set_weights(p)
     x, t = _sample(H, W, 13)
     pw = _bf16_weights(p)
     y_ref, _ = L.forward(pw, x, IN_SCALE, quantize=_bf16)
-    out_ref = L.outputs(y_ref, STREAM_OUT, "stream", R)
+    out_ref = L.outputs(y_ref, STREAM_OUT, form, R)
     out = net.predict(x)
     assert np.all(out[0] == 0.0)
     scale = np.abs(out_ref[1:]).max()
     # a centred difference of BF16-stored activations: ~2^-8 of the largest output per difference
     assert np.abs(out[1:] - out_ref[1:]).max() <= 5e-2 * scale, np.abs(out[1:] - out_ref[1:]).max() / scale
     loss, g = net.gradients(x, t)
-    loss_ref, g_ref = L.loss_and_grad(pw, x, t, IN_SCALE, STREAM_OUT, quantize=_bf16, form="stream", R=R)
+    loss_ref, g_ref = L.loss_and_grad(pw, x, t, IN_SCALE, STREAM_OUT, quantize=_bf16, form=form, R=R)
     assert loss == pytest.approx(loss_ref, rel=3e-2)
     nw3 = 3 * 32 * 9
     assert np.all(g[-(nw3 + 3):-3].reshape(3, 32, 3, 3)[1:] == 0.0) and np.all(g[-2:] == 0.0)
     # the output gradient is the curl's adjoint, a difference of neighbouring cells' residuals, so
     # the sums over cells behind every weight and bias gradient cancel more than in the direct
-    # form: layer 0's biases carry 3.6-4.7% in L2 (direct form 0.8-1.2%); the bound stays well
-    # below the ninth of a block that a mis-indexed tap or channel moves
+    # form: the weight blocks carry up to 5.2% in L2, the bias blocks (plain sums over all cells,
+    # cancelling most) up to 8.3% (direct form: 0.5-1.2%); both bounds stay well below the error a
+    # mis-indexed tap (a ninth of a block) or a swapped channel (~100%) makes
     # The output biases get no gradient at all in exact arithmetic (a uniform psi has no curl;
     # outputs 1 and 2 are unused): their entries are rounding, checked against the weight block.
     o = 0
@@ -262,7 +265,7 @@ def test_stream_form_matches_fp64_reference(V, H, W, R):
             l2 = np.linalg.norm(a - b) / np.linalg.norm(b)
             worst = np.abs(a - b).max() / np.abs(b).max()
             print("stream gradient block", o, n, "rel L2 %.3e worst %.3e" % (l2, worst))
-            assert l2 <= 8e-2 and worst <= 0.25, (o, l2, worst)
+            assert l2 <= (8e-2 if n > co else 0.15) and worst <= 0.3, (o, l2, worst)
             o += n
 
 
@@ -276,9 +279,10 @@ def _centred_divergence(ut, up, R=1.0):
     return ((flux[2:, 1:-1] - flux[:-2, 1:-1]) / (2 * dth) + (upe[1:-1, 2:] - upe[1:-1, :-2]) / (2 * dph)) / (R * st[:, None])
 
 
-def test_stream_form_apply_adds_a_divergence_free_velocity_and_keeps_the_density(V):
+@pytest.mark.parametrize("form,s0", [("stream", 1e-3), ("vorticity", 1e-1)])
+def test_stream_form_apply_adds_a_divergence_free_velocity_and_keeps_the_density(V, form, s0):
     H, W = 16, 32
-    net = V.LearnedCorrection(H, W, seed=4, in_scale=IN_SCALE, out_scale=(1e-3, 1e-4, 1e-4), form="stream")
+    net = V.LearnedCorrection(H, W, seed=4, in_scale=IN_SCALE, out_scale=(s0, 1e-4, 1e-4), form=form)
     p = net.get_weights()
     p[-3:] = [1.0, 0.5, -0.5]
     net.set_weights(p)
@@ -317,7 +321,8 @@ def test_stream_form_needs_the_solver_radius(V):
         net.set_output_form("stream", -1.0)
 
 
-def test_stream_form_rollout_equals_stepping_and_applying_bitwise(V):
+@pytest.mark.parametrize("form", ["stream", "vorticity"])
+def test_stream_form_rollout_equals_stepping_and_applying_bitwise(V, form):
     H, W = 16, 32
     net = V.LearnedCorrection(H, W, seed=4, in_scale=IN_SCALE, out_scale=STREAM_OUT)
     p = net.get_weights()
@@ -331,7 +336,7 @@ def test_stream_form_rollout_equals_stepping_and_applying_bitwise(V):
     for _ in range(2):
         b.step(1)
         net.apply(b)
-    net.set_output_form("stream", 1.0)
+    net.set_output_form(form, 1.0)
     net.rollout(a, 4)
     for _ in range(4):
         b.step(1)
@@ -341,16 +346,17 @@ def test_stream_form_rollout_equals_stepping_and_applying_bitwise(V):
     b.close()
 
 
-def test_trained_stream_correction_beats_the_plain_run_and_keeps_its_density_error(V):
+@pytest.mark.parametrize("form", ["stream", "vorticity"])
+def test_trained_stream_correction_beats_the_plain_run_and_keeps_its_density_error(V, form):
     """The learned-coarse experiment of the direct-form test (coarse 32 x 64 from fine 128 x 256)
-    with the stream form after 1000 coarse steps: the corrected run's vorticity error is below
-    the plain run's on each held-out seed (by half on average when this was written), and, the
-    correction being divergence-free, its density error is no larger than the plain run's on
-    average (the direct form's is 2.5x the plain run's at this horizon)."""
+    with a divergence-free form after 1000 coarse steps: the corrected run's vorticity error is
+    below the plain run's on each held-out seed (0.44-0.50 of it on average when this was
+    written), and, the correction being divergence-free, its density error is no larger than the
+    plain run's on average (the direct form's is 2.5x the plain run's at this horizon)."""
     from paper_2504_15574_gb300 import learned
     setup = learned.Setup(coarse=(32, 64), polar_filter=False)
     X, Y = learned.make_drift_samples(setup, list(range(1000, 1016)), 8, spinup=20)
-    net, _ = learned.train(setup, X, Y, epochs=6, form="stream")
+    net, _ = learned.train(setup, X, Y, epochs=6, form=form)
     res = learned.evaluate(setup, net, [5000, 5001, 5002, 5003], 1000, spinup=20)
     print({k: res[k] for k in ("vort_err_plain", "vort_err_learned", "rho_err_plain", "rho_err_learned")})
     assert np.all(np.isfinite(res["vort_err_learned_per_seed"]))
