@@ -74,6 +74,34 @@ def dist_info():
     return rank, world, local
 
 
+def repeat_times(time_one, repeats, world, device):
+    """Times repeats of the timed region: time_one() runs one repeat (barriers inside) and returns
+    its milliseconds.  At least 5 repeats and until ~0.5 s has run (at most 50), or exactly
+    `repeats` when > 0; with world > 1 every rank takes rank 0's decision after each repeat, and
+    the returned times are the max over ranks, repeat by repeat."""
+    import torch
+    times = []
+    while True:
+        times.append(float(time_one()))
+        done = (len(times) >= repeats) if repeats > 0 else \
+            (len(times) >= 5 and (sum(times) >= 500.0 or len(times) >= 50))
+        if world > 1:
+            flag = torch.tensor([1 if done else 0], device=device)
+            torch.distributed.broadcast(flag, 0)
+            done = bool(int(flag.item()))
+        if done:
+            break
+    t = torch.tensor(times, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_mlups(cells, steps, world, ms):
+    """Lattice updates of all ranks' replicas over the (max-over-ranks) time, in millions per second."""
+    return cells * steps * world / (ms * 1e-3) / 1e6
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -308,31 +336,20 @@ def run_ours(args):
     # events on the library's stream, the repeat's time is the max over ranks, and the line
     # reports the median repeat with the spread.  The clocks are sampled over all repeats.
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    times = []
+
+    def time_one():
+        barrier()
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+        barrier()
+        return ev0.elapsed_time(ev1)
+
     with Clocks(local) as clk:
-        while True:
-            barrier()
-            ev0.record(stream)
-            s.step(args.steps)
-            ev1.record(stream)
-            barrier()
-            times.append(ev0.elapsed_time(ev1))
-            done = (len(times) >= args.repeats) if args.repeats > 0 else \
-                (len(times) >= 5 and (sum(times) >= 500.0 or len(times) >= 50))
-            if world > 1:
-                # every rank takes the same number of repeats: rank 0's decision
-                flag = torch.tensor([1 if done else 0], device="cuda")
-                torch.distributed.broadcast(flag, 0)
-                done = bool(int(flag.item()))
-            if done:
-                break
-    t = torch.tensor(times, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    times = [float(x) for x in t.cpu()]
+        times = repeat_times(time_one, args.repeats, world, "cuda")
     ms = statistics.median(times)
     cells = NT * NP
-    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(cells, args.steps, world, ms)
 
     # per-kernel time, CUDA events on the launching stream (vlbm_profile_step): the three
     # stage kernels and the polar filter after each
@@ -364,7 +381,7 @@ def run_ours(args):
     vlbm.vlbm_moments(s.h, *outs)
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e_val = cells * e2e_steps * world / e2e_s / 1e6
+    e2e_val = whole_job_mlups(cells, e2e_steps, world, e2e_s * 1e3)
     h2d = 4 * cells * 8
     d2h = 3 * cells * 8
 
@@ -383,8 +400,8 @@ def run_ours(args):
             "repeats": {"count": len(times), "statistic": "median",
                         "ms_per_step": {"min": min(times) / args.steps, "median": ms / args.steps,
                                         "max": max(times) / args.steps},
-                        "value_spread": [cells * args.steps * world / (max(times) * 1e-3) / 1e6,
-                                         cells * args.steps * world / (min(times) * 1e-3) / 1e6]},
+                        "value_spread": [whole_job_mlups(cells, args.steps, world, max(times)),
+                                         whole_job_mlups(cells, args.steps, world, min(times))]},
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(args), "n_theta": NT, "n_phi": NP,
