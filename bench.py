@@ -130,6 +130,21 @@ def committed_traffic(args):
     return None
 
 
+def committed_lane_ops(args):
+    """FP32 lane operations per cell and stage of the stage kernel, from the instruction classes of
+    the committed ncu summary (the default workload's WENO-5 D2Q16 FP32 stage only; else None)."""
+    if (NT, NP) != (1024, 2048) or args.precision != "fp32" or args.scheme != "weno5" or args.komissarov \
+            or args.velocity_set != "d2q16":
+        return None
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "stage_f32_1024x2048.md")):
+            if line.startswith("fp32_lane_ops_per_cell_stage:"):
+                return float(line.split(":", 1)[1].strip())
+    except OSError:
+        pass
+    return None
+
+
 class Clocks:
     """Samples the SM clock, power and clock-event reasons of one GPU every 10 ms during the
     timed region, through NVML (read-only queries of the driver's library); falls back to
@@ -394,6 +409,18 @@ def run_ours(args):
                    "sample": f"{done} full RK3 steps of the 1024x2048 workload after 1 warm-up step "
                              f"(bounded at 15 s of timed work; {el:.1f} s)"}
         clocks = clk.summary()
+        # the stage kernel against its FMA pipe: FP32 lane operations (committed ncu instruction
+        # classes) over the same event time, against 128 FP32 lanes per SM x SMs x the median SM
+        # clock sampled during the timed region
+        fma_roof = None
+        lane_ops = committed_lane_ops(args)
+        if lane_ops is not None and clocks.get("sm_mhz"):
+            nsm = torch.cuda.get_device_properties(local).multi_processor_count
+            ops = lane_ops * cells * 3 / (sum(stage_ms) * 1e-3) / 1e12
+            pk = 128 * nsm * clocks["sm_mhz"] * 1e6 / 1e12
+            fma_roof = {"bound": "alu", "pipe": "fma (FP32)", "achieved": ops, "peak": pk, "unit": "T lane-op/s",
+                        "frac": ops / pk, "lane_ops_per_cell_stage": lane_ops,
+                        "peak_from": f"128 FP32 lanes per SM x {nsm} SMs x {clocks['sm_mhz']:.0f} MHz (sampled)"}
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -408,6 +435,7 @@ def run_ours(args):
                        "Q": qcount(args), "global_batch": world,
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 (three {array_mb(args):.0f} MB population arrays per replica)"},
+            "fma_roofline": fma_roof,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": ("stage_f32_kernel" if args.precision == "fp32" else "stage_f64 kernels")
