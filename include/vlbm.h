@@ -295,7 +295,9 @@ VLBM_API int vlbm_lc_set_scales(vlbm_lc_t *lc, const double *in_scale, const dou
  * mode), and the correction is the curl of psi as in VLBM_LC_STREAM (same training): the
  * network's output stays local while psi, an integral of the correction, spans the grid.
  * vlbm_lc_apply and vlbm_lc_rollout require radius = the solver's for both (VLBM_ERR_ARG
- * otherwise).  VLBM_ERR_ARG for an unknown form or radius <= 0.  Rebuilds the rollout graph. */
+ * otherwise).  VLBM_ERR_ARG for an unknown form or radius <= 0; VLBM_ERR_UNSUPPORTED for the
+ * vorticity form on grids whose mode solve (one CTA per four modes staging 16 n_theta bytes per
+ * mode in shared memory) does not fit, n_theta above ~3,500.  Rebuilds the rollout graph. */
 VLBM_API int vlbm_lc_set_output_form(vlbm_lc_t *lc, int form, double radius);
 /* Forward pass: the correction in physical units (drho not mean-corrected). */
 VLBM_API int vlbm_lc_predict(vlbm_lc_t *lc, const double *inputs, double *outputs);

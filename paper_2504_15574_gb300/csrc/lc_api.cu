@@ -42,6 +42,7 @@ struct vlbm_lc {
     float *d_ptabs = nullptr;    // tab, a, tw (lc_poisson_tables)
     float2 *d_pX = nullptr;
     double *d_pw = nullptr, *d_psi = nullptr, *d_ppart = nullptr, *d_psum = nullptr;
+    bool vort_ok = false;        // the vorticity form's mode solve fits this grid
     long long t = 0;
     std::vector<void *> bufs;
     cudaGraphExec_t g_exec = nullptr;   // vlbm_lc_rollout: one corrected step of solver g_solver
@@ -299,11 +300,15 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
     if (cudaMemcpy(n->d_sin, sn.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(n->d_cos, cs.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(n->d_w, w.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
-        lc_poisson_tables(n_theta, n_phi, n->d_ptabs) != 0 || lc_poisson_prepare(n_theta) != 0 ||
+        lc_poisson_tables(n_theta, n_phi, n->d_ptabs) != 0 ||
         refresh_bf16(n) != VLBM_OK || cudaStreamSynchronize(n->stream) != cudaSuccess) {
         vlbm_lc_destroy(n);
         return VLBM_ERR_CUDA;
     }
+    // the vorticity form's mode solve needs shared memory growing with n_theta: on grids taller
+    // than one CTA can stage, that form alone is unavailable
+    n->vort_ok = lc_poisson_prepare(n_theta) == 0;
+    if (!n->vort_ok) cudaGetLastError();
     *out = n;
     return VLBM_OK;
 }
@@ -353,6 +358,8 @@ int vlbm_lc_set_output_form(vlbm_lc_t *n, int form, double radius)
     if (!n) return VLBM_ERR_ARG;
     if (form != VLBM_LC_DIRECT && form != VLBM_LC_STREAM && form != VLBM_LC_VORTICITY)
         return lfail(n, VLBM_ERR_ARG, "unknown output form");
+    if (form == VLBM_LC_VORTICITY && !n->vort_ok)
+        return lfail(n, VLBM_ERR_UNSUPPORTED, "the vorticity form's mode solve does not fit this many rows");
     if (!(radius > 0.0) || !std::isfinite(radius)) return lfail(n, VLBM_ERR_ARG, "radius must be > 0");
     if (n->g_exec) {   // the form is part of the captured rollout step
         cudaGraphExecDestroy(n->g_exec);

@@ -365,3 +365,15 @@ def test_trained_stream_correction_beats_the_plain_run_and_keeps_its_density_err
     for a, b in zip(res["vort_err_learned_per_seed"], res["vort_err_plain_per_seed"]):
         assert a < b, res
     assert res["rho_err_learned"] <= (1.0 if form == "stream" else 1.02) * res["rho_err_plain"], res
+
+
+def test_vorticity_form_is_refused_where_its_mode_solve_does_not_fit(V):
+    # 4000 rows: the mode solve would stage 16 x 4000 bytes per mode, four modes per CTA, more
+    # than a CTA's shared memory; the network itself and its other forms are unaffected
+    net = V.LearnedCorrection(4000, 2, seed=1, in_scale=IN_SCALE, out_scale=STREAM_OUT)
+    with pytest.raises(V.VlbmError) as e:
+        net.set_output_form("vorticity", 1.0)
+    assert e.value.code == V.VLBM_ERR_UNSUPPORTED
+    net.set_output_form("stream", 1.0)
+    net.set_output_form("direct", 1.0)
+    net.close()
