@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "vlbm_internal.h"
+#include "f32_images.cuh"
 #include "lc_internal.h"
 
 namespace vk {
@@ -409,9 +410,10 @@ __global__ void wgrad_layout_kernel(const float *g9, int CO, int CI, int COp, in
 // Value of a moment field at grid point (r, c) for -3 <= r < H + 3: columns wrap; a
 // row beyond a pole is the mirrored row on the opposite meridian (c + W/2), negated
 // for a velocity component (sgn = -1), as the pole condition of Sec. 3.6 maps it.
-__device__ __forceinline__ double lc_at(const double *a, int H, int W, int r, int c, double sgn)
+template <typename T>
+__device__ __forceinline__ T lc_at(const T *a, int H, int W, int r, int c, T sgn)
 {
-    double s = 1.0;
+    T s = 1;
     if (r < 0 || r >= H) {
         r = (r < 0) ? (-1 - r) : (2 * H - 1 - r);
         c += W / 2;
@@ -423,55 +425,70 @@ __device__ __forceinline__ double lc_at(const double *a, int H, int W, int r, in
 }
 
 // undivided 4th and 6th differences of a field along theta (dir 0) or phi (dir 1) at (i, j)
-__device__ __forceinline__ void lc_differences(const double *a, int H, int W, int i, int j, int dir, double sgn,
-                                               double &d4, double &d6)
+__device__ __forceinline__ void lc_differences(const float *a, int H, int W, int i, int j, int dir, float sgn,
+                                               float &d4, float &d6)
 {
-    double x[7];
+    float x[7];
 #pragma unroll
     for (int m = 0; m < 7; ++m)
         x[m] = dir ? lc_at(a, H, W, i, j + m - 3, sgn) : lc_at(a, H, W, i + m - 3, j, sgn);
-    d4 = x[1] - 4.0 * x[2] + 6.0 * x[3] - 4.0 * x[4] + x[5];
-    d6 = x[0] - 6.0 * x[1] + 15.0 * x[2] - 20.0 * x[3] + 15.0 * x[4] - 6.0 * x[5] + x[6];
+    d4 = x[1] - 4.0f * x[2] + 6.0f * x[3] - 4.0f * x[4] + x[5];
+    d6 = x[0] - 6.0f * x[1] + 15.0f * x[2] - 20.0f * x[3] + 15.0f * x[4] - 6.0f * x[5] + x[6];
 }
 
-// network input from the moments of a coarse solver (channel order in lc_internal.h):
-// the moments and their undivided 4th / 6th differences are formed in FP64, divided
-// by their scales and clamped to [-LC_CLAMP, LC_CLAMP] before the BF16 rounding (a
-// BF16 field could not resolve the high-order differences that carry a coarse
-// scheme's truncation error); the latitude channels let the translation-equivariant
-// convolutions depend on theta.
-__global__ void features_kernel(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                                const double *sin_t, const double *cos_t, const LcInScale sc, __nv_bfloat16 *Xp)
+// the network's FP32 moment deviations (rho - 1, u^theta, u^phi, T - 1) [4][H][W] of FP64 moments
+// (rho, u^theta, u^phi, T) [4][H][W]: the deviations are formed in FP64, then rounded
+__global__ void dev_of_moments_kernel(const double *in4, int n, float *dev)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    dev[c] = (float)(in4[c] - 1.0);
+    dev[(size_t)n + c] = (float)in4[(size_t)n + c];
+    dev[2 * (size_t)n + c] = (float)in4[2 * (size_t)n + c];
+    dev[3 * (size_t)n + c] = (float)(in4[3 * (size_t)n + c] - 1.0);
+}
+
+// network input from the moment deviations dev = (rho - 1, u^theta, u^phi, T - 1) [4][H][W]
+// (channel order in lc_internal.h): the deviations and their undivided 4th / 6th differences in
+// FP32 — on rho - 1, not rho, so that the differences keep the FP32 resolution of the deviation
+// (~1e-3 of rho: ~1e-10 absolute) rather than of rho — divided by their scales and clamped to
+// [-LC_CLAMP, LC_CLAMP] before the BF16 rounding (a BF16 field could not resolve the high-order
+// differences that carry a coarse scheme's truncation error); the latitude channels let the
+// translation-equivariant convolutions depend on theta.
+__global__ void features_kernel(const float *dev, int H, int W, const double *sin_t, const double *cos_t,
+                                const LcInScale sc, __nv_bfloat16 *Xp)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t HW = (size_t)H * W;
     if (i >= H * W) return;
     const int r = i / W, c = i - r * W;
-    double raw[LC_NSCALE];
-    raw[0] = rho[i] - 1.0;
+    const float *drho = dev, *ut = dev + HW, *up = dev + 2 * HW;
+    float raw[LC_NSCALE];
+    raw[0] = drho[i];
     raw[1] = ut[i];
     raw[2] = up[i];
-    raw[3] = T ? T[i] - 1.0 : 0.0;
-    double d4, d6;
-    lc_differences(rho, H, W, r, c, 0, 1.0, d4, d6);
+    raw[3] = dev[3 * HW + i];
+    float d4, d6;
+    lc_differences(drho, H, W, r, c, 0, 1.0f, d4, d6);
     raw[4] = d6;
-    lc_differences(rho, H, W, r, c, 1, 1.0, d4, d6);
+    lc_differences(drho, H, W, r, c, 1, 1.0f, d4, d6);
     raw[5] = d6;
-    lc_differences(ut, H, W, r, c, 0, -1.0, d4, d6);
+    lc_differences(ut, H, W, r, c, 0, -1.0f, d4, d6);
     raw[6] = d6;
     raw[10] = d4;
-    lc_differences(ut, H, W, r, c, 1, -1.0, d4, d6);
+    lc_differences(ut, H, W, r, c, 1, -1.0f, d4, d6);
     raw[7] = d6;
     raw[11] = d4;
-    lc_differences(up, H, W, r, c, 0, -1.0, d4, d6);
+    lc_differences(up, H, W, r, c, 0, -1.0f, d4, d6);
     raw[8] = d6;
     raw[12] = d4;
-    lc_differences(up, H, W, r, c, 1, -1.0, d4, d6);
+    lc_differences(up, H, W, r, c, 1, -1.0f, d4, d6);
     raw[9] = d6;
     raw[13] = d4;
     float v[LC_CIN];
 #pragma unroll
     for (int q = 0; q < LC_NSCALE; ++q) {
-        const float x = (float)(raw[q] * (double)sc.inv[q]);
+        const float x = raw[q] * sc.inv[q];
         v[q < 4 ? q : q + 2] = fminf(fmaxf(x, -LC_CLAMP), LC_CLAMP);
     }
     v[4] = (float)cos_t[r];
@@ -819,7 +836,7 @@ __global__ void vort_grad_kernel(const double *u, int H, int W, int CO, const do
 // state carries no momentum), and T - 1 = (rho_ref |u|^2 + sum df |v - u|^2 - 2 dn) / (2 n),
 // using sum_k w_k |v_k|^2 = 2 (T0 = 1); stored as FP64 for the feature kernel.
 __global__ void lc_moments_kernel(const float2 *f, const Layout L, const VelD c, double rho_ref,
-                                  const double *sin_t, double ks, double *mom)
+                                  const double *sin_t, double ks, float *dev)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
@@ -850,10 +867,10 @@ __global__ void lc_moments_kernel(const float2 *f, const Layout L, const VelD c,
     e *= inv_s;
     const float tm1 = ((float)rho_ref * (ut * ut + up * up) + e - 2.0f * dn) / (2.0f * n);
     const size_t HW = (size_t)L.nt * L.np, cell = (size_t)i * L.np + j;
-    mom[cell] = (double)n;
-    mom[HW + cell] = (double)ut;
-    mom[2 * HW + cell] = (double)up;
-    mom[3 * HW + cell] = 1.0 + (double)tm1;
+    dev[cell] = (float)(rho_ref - 1.0) + dn;   // rho - 1 at the resolution of the deviation
+    dev[HW + cell] = ut;
+    dev[2 * HW + cell] = up;
+    dev[3 * HW + cell] = tm1;
 }
 
 // f += feq(rho + drho - mean, u + du) - feq(rho, u) on the FP32 pair layout, the equilibrium
@@ -861,14 +878,14 @@ __global__ void lc_moments_kernel(const float2 *f, const Layout L, const VelD c,
 // with P(xi, u^2) = 1 + xi + (xi^2 - u^2)/2 + xi (xi^2 - 3 u^2)/6 (Eq. feq_Q=4 over n w),
 // feq' - feq = w [ (rho' - rho) P' + rho (P' - P) ] and P' - P expanded in dxi = v . du and
 // d(u^2) = du . (2u + du).
-__global__ void nudge_kernel(float2 *f, const Layout L, const double *mom, const double *delta, const double *mean,
+__global__ void nudge_kernel(float2 *f, const Layout L, const float *dev, const double *delta, const double *mean,
                              double wsum, const VelD c, const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
     if (j >= L.np) return;
     const size_t n = (size_t)L.nt * L.np, cell = (size_t)i * L.np + j;
-    const float rho = (float)mom[cell], ut = (float)mom[n + cell], up = (float)mom[2 * n + cell];
+    const float rho = 1.0f + dev[cell], ut = dev[n + cell], up = dev[2 * n + cell];
     const float drho = (float)(delta[cell] - (*mean) / wsum), dut = (float)delta[n + cell],
                 dup = (float)delta[2 * n + cell];
     const float ut2 = ut + dut, up2 = up + dup;
@@ -891,7 +908,7 @@ __global__ void nudge_kernel(float2 *f, const Layout L, const double *mom, const
         }
         v.x += s * d[0];
         v.y += s * d[1];
-        f[L.at(q, i, j)] = v;
+        store_images(f, L, 4, q, i, j, v);   // the cell and its ghost images
     }
 }
 
@@ -1098,11 +1115,15 @@ void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g
     wgrad_layout_kernel<<<(n + 255) / 256, 256, 0, s>>>(g9, CO, CI, COp, CIp, g);
 }
 
-void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                 const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *Xp,
-                 cudaStream_t s)
+void lc_features(const float *dev, int H, int W, const double *sin_t, const double *cos_t,
+                 const LcInScale &inv_scale, __nv_bfloat16 *Xp, cudaStream_t s)
 {
-    features_kernel<<<(H * W + 255) / 256, 256, 0, s>>>(rho, ut, up, T, H, W, sin_t, cos_t, inv_scale, Xp);
+    features_kernel<<<(H * W + 255) / 256, 256, 0, s>>>(dev, H, W, sin_t, cos_t, inv_scale, Xp);
+}
+
+void lc_dev_of_moments(const double *in4, int H, int W, float *dev, cudaStream_t s)
+{
+    dev_of_moments_kernel<<<(H * W + 255) / 256, 256, 0, s>>>(in4, H * W, dev);
 }
 
 void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
@@ -1114,17 +1135,17 @@ void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double
 }
 
 void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref, const double *sin_t, double ks,
-                double *mom, cudaStream_t s)
+                float *dev, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt);
-    lc_moments_kernel<<<grid, 128, 0, s>>>(f, L, c, rho_ref, sin_t, ks, mom);
+    lc_moments_kernel<<<grid, 128, 0, s>>>(f, L, c, rho_ref, sin_t, ks, dev);
 }
 
-void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,
+void lc_nudge(float2 *f, const Layout &L, const float *dev, const double *delta, const double *mean, double wsum,
               const VelD &c, const double *sin_t, double ks, cudaStream_t s)
 {
     dim3 grid((L.np + 127) / 128, L.nt);
-    nudge_kernel<<<grid, 128, 0, s>>>(f, L, mom, delta, mean, wsum, c, sin_t, ks);
+    nudge_kernel<<<grid, 128, 0, s>>>(f, L, dev, delta, mean, wsum, c, sin_t, ks);
 }
 
 }  // namespace vk

@@ -29,6 +29,7 @@ struct vlbm_lc {
     double *d_sin = nullptr, *d_cos = nullptr, *d_in = nullptr, *d_tg = nullptr, *d_out = nullptr, *d_part = nullptr, *d_scal = nullptr;
     __nv_bfloat16 *d_xp[LC_LAYERS] = {}, *d_z[LC_LAYERS] = {};
     float *d_y = nullptr, *d_dy = nullptr, *d_dxp = nullptr, *d_dx = nullptr;
+    float *d_dev = nullptr;      // the network's moment deviations (rho - 1, u^theta, u^phi, T - 1) [4][H][W]
     __nv_bfloat16 *d_dp = nullptr, *d_dpre = nullptr;
     float *d_wpart = nullptr, *d_bpart = nullptr, *d_g9 = nullptr;
     double wsum = 0.0;
@@ -91,16 +92,17 @@ int refresh_bf16(vlbm_lc_t *n)
     return VLBM_OK;
 }
 
-// forward pass on the moments in4 ([4][H][W] device, physical units), on stream s; output in d_y.
+// forward pass on the moment deviations dev ([4][H][W] device, FP32), on stream s; output in d_y.
 // keep: also store each hidden layer's unpadded activations (d_z) for the backward pass.
-int forward(vlbm_lc_t *n, const double *in4, cudaStream_t s, bool keep = true)
+int forward(vlbm_lc_t *n, const float *dev, cudaStream_t s, bool keep = true)
 {
     const int H = n->H, W = n->W, HW = H * W;
     LcInScale is;
     for (int q = 0; q < LC_NSCALE; ++q) is.inv[q] = 1.0f / n->in_scale[q];
     // the padded input of layer 0 (velocity channels, their differences and sin(theta) change
     // sign across a pole); each hidden layer writes the next layer's padded input itself
-    lc_features(in4, in4 + HW, in4 + 2 * (size_t)HW, in4 + 3 * (size_t)HW, H, W, n->d_sin, n->d_cos, is, n->d_xp[0], s);
+    (void)HW;
+    lc_features(dev, H, W, n->d_sin, n->d_cos, is, n->d_xp[0], s);
     for (int l = 0; l < LC_LAYERS; ++l) {
         const bool last = (l == LC_LAYERS - 1);
         lc_conv(l, n->d_xp[l], H + 2, W + 2, n->d_wf[l], n->d_w + n->boff[l], last ? n->d_y : nullptr,
@@ -184,15 +186,15 @@ int check_solver(vlbm_lc_t *n, vlbm_t *h)
 }
 
 // The correction of solver h's current state, enqueued on stream s without host
-// synchronisation: moments, forward pass, outputs (drho area mean), nudge, ghost fill.
+// synchronisation: moments, forward pass, outputs (drho area mean), nudge (which also writes each
+// cell's ghost images).
 int enqueue_correction(vlbm_lc_t *n, vlbm_t *h, cudaStream_t s)
 {
-    lc_moments((const float2 *)h->F, h->L, h->vd, h->rho_ref, h->d_sin_t, h->kscale, h->d_mom, s);
+    lc_moments((const float2 *)h->F, h->L, h->vd, h->rho_ref, h->d_sin_t, h->kscale, n->d_dev, s);
     int rc;
-    if ((rc = forward(n, h->d_mom, s, false))) return rc;
+    if ((rc = forward(n, n->d_dev, s, false))) return rc;
     enqueue_outputs(n, s);
-    lc_nudge((float2 *)h->F, h->L, h->d_mom, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, h->kscale, s);
-    launch_fill_ghosts_f32((float2 *)h->F, h->L, h->vd.q, s);
+    lc_nudge((float2 *)h->F, h->L, n->d_dev, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, h->kscale, s);
     LCK(n, cudaGetLastError());
     return VLBM_OK;
 }
@@ -200,7 +202,10 @@ int enqueue_correction(vlbm_lc_t *n, vlbm_t *h, cudaStream_t s)
 int upload_io(vlbm_lc_t *n, const double *inputs, const double *targets)
 {
     const size_t HW = (size_t)n->H * n->W;
-    if (inputs) LCK(n, cudaMemcpyAsync(n->d_in, inputs, 4 * HW * sizeof(double), cudaMemcpyHostToDevice, n->stream));
+    if (inputs) {
+        LCK(n, cudaMemcpyAsync(n->d_in, inputs, 4 * HW * sizeof(double), cudaMemcpyHostToDevice, n->stream));
+        lc_dev_of_moments(n->d_in, n->H, n->W, n->d_dev, n->stream);
+    }
     if (targets) LCK(n, cudaMemcpyAsync(n->d_tg, targets, 3 * HW * sizeof(double), cudaMemcpyHostToDevice, n->stream));
     return VLBM_OK;
 }
@@ -263,6 +268,7 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
     A(&n->d_sin, (size_t)n_theta);
     A(&n->d_cos, (size_t)n_theta);
     A(&n->d_in, 4 * HW);
+    A(&n->d_dev, 4 * HW);
     A(&n->d_tg, 3 * HW);
     A(&n->d_out, 3 * HW);
     A(&n->d_part, HW / 256 + 2);
@@ -374,7 +380,7 @@ int vlbm_lc_predict(vlbm_lc_t *n, const double *inputs, double *outputs)
 {
     if (!n || !inputs || !outputs) return VLBM_ERR_ARG;
     int rc;
-    if ((rc = upload_io(n, inputs, nullptr)) || (rc = forward(n, n->d_in, n->stream))) return rc;
+    if ((rc = upload_io(n, inputs, nullptr)) || (rc = forward(n, n->d_dev, n->stream))) return rc;
     enqueue_outputs(n, n->stream);
     LCK(n, cudaMemcpyAsync(outputs, n->d_out, sizeof(double) * 3 * n->H * n->W, cudaMemcpyDeviceToHost, n->stream));
     LCK(n, cudaStreamSynchronize(n->stream));
@@ -394,7 +400,7 @@ int vlbm_lc_gradients(vlbm_lc_t *n, const double *inputs, const double *targets,
     if (!n || !inputs || !targets) return VLBM_ERR_ARG;
     if (int rc0 = check_trainable(n)) return rc0;
     int rc;
-    if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n, n->d_in, n->stream)) || (rc = backward(n))) return rc;
+    if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n, n->d_dev, n->stream)) || (rc = backward(n))) return rc;
     if (loss) LCK(n, cudaMemcpyAsync(loss, n->d_scal, sizeof(double), cudaMemcpyDeviceToHost, n->stream));
     if (grad) LCK(n, cudaMemcpyAsync(grad, n->d_g, sizeof(float) * n->nparam, cudaMemcpyDeviceToHost, n->stream));
     LCK(n, cudaStreamSynchronize(n->stream));
@@ -406,7 +412,7 @@ int vlbm_lc_train_step(vlbm_lc_t *n, const double *inputs, const double *targets
     if (!n || !inputs || !targets || !(lr > 0.0f)) return VLBM_ERR_ARG;
     if (int rc0 = check_trainable(n)) return rc0;
     int rc;
-    if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n, n->d_in, n->stream)) || (rc = backward(n))) return rc;
+    if ((rc = upload_io(n, inputs, targets)) || (rc = forward(n, n->d_dev, n->stream)) || (rc = backward(n))) return rc;
     n->t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - std::pow(b1, (float)n->t), c2 = 1.0f - std::pow(b2, (float)n->t);

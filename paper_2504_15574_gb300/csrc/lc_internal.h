@@ -43,16 +43,19 @@ void lc_adam(float *w, const float *g, float *m, float *v, int n, float lr, floa
 void lc_weights_bf16(const float *w, int CO, int CI, int COp, int CIp, __nv_bfloat16 *fwd, int CIp2, int COp2,
                      __nv_bfloat16 *bwd, cudaStream_t s);
 void lc_wgrad_layout(const float *g9, int CO, int CI, int COp, int CIp, float *g, cudaStream_t s);
-void lc_features(const double *rho, const double *ut, const double *up, const double *T, int H, int W,
-                 const double *sin_t, const double *cos_t, const LcInScale &inv_scale, __nv_bfloat16 *Xp,
-                 cudaStream_t s);
-// (rho, u^theta, u^phi, T) [4][H][W] of a solver's FP32 state (state scale ks), FP32 arithmetic
-// on the deviations.
+// The padded layer-0 input from the moment deviations dev = (rho - 1, u^theta, u^phi, T - 1)
+// [4][H][W] (FP32).
+void lc_features(const float *dev, int H, int W, const double *sin_t, const double *cos_t,
+                 const LcInScale &inv_scale, __nv_bfloat16 *Xp, cudaStream_t s);
+// The deviations dev [4][H][W] (FP32) of FP64 moments (rho, u^theta, u^phi, T) [4][H][W].
+void lc_dev_of_moments(const double *in4, int H, int W, float *dev, cudaStream_t s);
+// The deviations (rho - 1, u^theta, u^phi, T - 1) [4][H][W] of a solver's FP32 state (state scale
+// ks), FP32 arithmetic on the stored deviations.
 void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref, const double *sin_t, double ks,
-                double *mom, cudaStream_t s);
+                float *dev, cudaStream_t s);
 void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double *sin_t, double *out, double *part,
                 double *mean, cudaStream_t s);
-void lc_nudge(float2 *f, const Layout &L, const double *mom, const double *delta, const double *mean, double wsum,
+void lc_nudge(float2 *f, const Layout &L, const float *dev, const double *delta, const double *mean, double wsum,
               const VelD &c, const double *sin_t, double ks, cudaStream_t s);
 // Stream-function output form: output 0 times s0 is a stream function psi on the H x W cell grid
 // of a sphere of radius R (dth = pi / H, dph = 2 pi / W), the correction its centred curl
