@@ -1502,19 +1502,21 @@ __global__ void diag_rows_f32_kernel(const f2 *f, const Layout L, const double *
 __global__ void pole_budget_f32_kernel(const double *part, int ntx, double ref_n, double ref_s, double inv_ks,
                                        double R, double dph, double dt, double *budget)
 {
-    double m[3];
-    for (int st = 0; st < 3; ++st) {
-        double fl[2];
-        for (int pole = 0; pole < 2; ++pole) {
-            const double *p = part + ((size_t)st * 2 + pole) * ntx;
-            double x = 0.0;
-            for (int b = threadIdx.x; b < ntx; b += 32) x += p[b];
+    // the six partial rows (stage, pole) are loaded together and reduced side by side: one memory
+    // round trip and six independent shuffle chains (each row summed in the same order as alone)
+    double x[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < ntx; b += 32) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            fl[pole] = x;
-        }
-        m[st] = -R * dph * ((fl[1] * inv_ks + ref_s) - (fl[0] * inv_ks + ref_n));
+        for (int k = 0; k < 6; ++k) x[k] += part[(size_t)k * ntx + b];
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) x[k] += __shfl_xor_sync(0xffffffffu, x[k], o);
+    }
+    double m[3];
+#pragma unroll
+    for (int st = 0; st < 3; ++st) m[st] = -R * dph * ((x[2 * st + 1] * inv_ks + ref_s) - (x[2 * st] * inv_ks + ref_n));
     if (threadIdx.x == 0) *budget += dt * (m[0] / 6.0 + m[1] / 6.0 + 2.0 * m[2] / 3.0);
 }
 
