@@ -878,8 +878,11 @@ __global__ void lc_moments_kernel(const float2 *f, const Layout L, const VelD c,
 // with P(xi, u^2) = 1 + xi + (xi^2 - u^2)/2 + xi (xi^2 - 3 u^2)/6 (Eq. feq_Q=4 over n w),
 // feq' - feq = w [ (rho' - rho) P' + rho (P' - P) ] and P' - P expanded in dxi = v . du and
 // d(u^2) = du . (2u + du).
+// FP32 velocities and weights of D2Q16 (each weight the FP64 product rounded once)
+struct VelN { float v[4], w[16]; };
+
 __global__ void nudge_kernel(float2 *f, const Layout L, const float *dev, const double *delta, const double *mean,
-                             double wsum, const VelD c, const double *sin_t, double ks)
+                             double wsum, const VelN c, const double *sin_t, double ks)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y;
@@ -892,14 +895,20 @@ __global__ void nudge_kernel(float2 *f, const Layout L, const float *dev, const 
     const float usq = ut * ut + up * up, usq2 = ut2 * ut2 + up2 * up2;
     const float dusq = dut * (ut + ut2) + dup * (up + up2);
     const float s = (float)(ks * sin_t[i]);
+    // the cell's eight pairs are read before any is written (the stores may alias the loads, so
+    // the loads would otherwise wait for one another)
+    float2 g8[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) g8[q] = f[L.at(q, i, j)];
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int g = q >> 2, b = q & 3;
-        float2 v = f[L.at(q, i, j)];
+        float2 v = g8[q];
         float d[2];
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             const int a = 2 * g + m;
-            const float va = (float)c.v[a], vb = (float)c.v[b], w = (float)(c.w[a] * c.w[b]);
+            const float va = c.v[a], vb = c.v[b], w = c.w[4 * a + b];
             const float xi = va * ut + vb * up, dxi = va * dut + vb * dup, xi2 = xi + dxi;
             const float P2 = 1.0f + xi2 + 0.5f * (xi2 * xi2 - usq2) + xi2 * (xi2 * xi2 - 3.0f * usq2) / 6.0f;
             const float dP = dxi + 0.5f * (dxi * (xi + xi2) - dusq) +
@@ -1144,8 +1153,12 @@ void lc_moments(const float2 *f, const Layout &L, const VelD &c, double rho_ref,
 void lc_nudge(float2 *f, const Layout &L, const float *dev, const double *delta, const double *mean, double wsum,
               const VelD &c, const double *sin_t, double ks, cudaStream_t s)
 {
+    VelN cn;
+    for (int a = 0; a < 4; ++a) cn.v[a] = (float)c.v[a];
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) cn.w[4 * a + b] = (float)(c.w[a] * c.w[b]);
     dim3 grid((L.np + 127) / 128, L.nt);
-    nudge_kernel<<<grid, 128, 0, s>>>(f, L, dev, delta, mean, wsum, c, sin_t, ks);
+    nudge_kernel<<<grid, 128, 0, s>>>(f, L, dev, delta, mean, wsum, cn, sin_t, ks);
 }
 
 }  // namespace vk
