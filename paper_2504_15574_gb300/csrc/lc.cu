@@ -110,9 +110,12 @@ __global__ void unpad_kernel(const float *dXp, int H, int W, int C, unsigned neg
 constexpr int CONV_PIX = 64;
 
 template <int CI, int CO>
+// part0 (optional): per CTA (index blockIdx.y gridDim.x + blockIdx.x) the sum over its pixels of
+// sin_t[row] times output channel 0 (the direct form's drho before its scale; FP64)
 __global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16 *Xp, int Hp, int Wp,
                                                        const __nv_bfloat16 *Wt, const float *bias, float *Yf,
-                                                       __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu)
+                                                       __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu,
+                                                       double *part0, const double *sin_t)
 {
     constexpr int XS = CI + 8;           // padded channel stride in shared memory (bank spread)
     constexpr int WS = 9 * CI + 8;
@@ -164,10 +167,12 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16 *Xp, i
         }
     }
     // epilogue: rows g and g+8 of the warp tile, columns 2t, 2t+1 of each n-block
+    double p0 = 0.0;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int x = x0 + pbase + g + 8 * half;
         if (x >= Wo) continue;
+        if (part0 && t == 0) p0 += (double)(acc[0][2 * half] + (bias ? bias[0] : 0.0f));
         const size_t o = ((size_t)y * Wo + x) * CO;
 #pragma unroll
         for (int nb = 0; nb < CO / 8; ++nb) {
@@ -190,6 +195,16 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const __nv_bfloat16 *Xp, i
                     *reinterpret_cast<__nv_bfloat162 *>(Ypad + ((size_t)prow * (Wo + 2) + pcol) * CO + co) = pr;
                 });
         }
+    }
+    if (part0) {   // (uniform over the CTA)
+        __shared__ double red[128];
+        red[tid] = p0 * sin_t[y];
+        __syncthreads();
+        for (int k = 64; k > 0; k >>= 1) {
+            if (tid < k) red[tid] += red[tid + k];
+            __syncthreads();
+        }
+        if (tid == 0) part0[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
     }
 }
 
@@ -881,20 +896,15 @@ __global__ void lc_moments_kernel(const float2 *f, const Layout L, const VelD c,
 // FP32 velocities and weights of D2Q16 (each weight the FP64 product rounded once)
 struct VelN { float v[4], w[16]; };
 
-__global__ void nudge_kernel(float2 *f, const Layout L, const float *dev, const double *delta, const double *mean,
-                             double wsum, const VelN c, const double *sin_t, double ks)
+// the nudge of cell (i, j) by the correction (drho, dut, dup), its stored populations and images
+__device__ __forceinline__ void nudge_cell(float2 *f, const Layout &L, const float *dev, int i, int j, float drho,
+                                           float dut, float dup, const VelN &c, float s)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = blockIdx.y;
-    if (j >= L.np) return;
     const size_t n = (size_t)L.nt * L.np, cell = (size_t)i * L.np + j;
     const float rho = 1.0f + dev[cell], ut = dev[n + cell], up = dev[2 * n + cell];
-    const float drho = (float)(delta[cell] - (*mean) / wsum), dut = (float)delta[n + cell],
-                dup = (float)delta[2 * n + cell];
     const float ut2 = ut + dut, up2 = up + dup;
     const float usq = ut * ut + up * up, usq2 = ut2 * ut2 + up2 * up2;
     const float dusq = dut * (ut + ut2) + dup * (up + up2);
-    const float s = (float)(ks * sin_t[i]);
     // the cell's eight pairs are read before any is written (the stores may alias the loads, so
     // the loads would otherwise wait for one another)
     float2 g8[8];
@@ -921,12 +931,52 @@ __global__ void nudge_kernel(float2 *f, const Layout L, const float *dev, const 
     }
 }
 
+__global__ void nudge_kernel(float2 *f, const Layout L, const float *dev, const double *delta, const double *mean,
+                             double wsum, const VelN c, const double *sin_t, double ks)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= L.np) return;
+    const size_t n = (size_t)L.nt * L.np, cell = (size_t)i * L.np + j;
+    const float drho = (float)(delta[cell] - (*mean) / wsum), dut = (float)delta[n + cell],
+                dup = (float)delta[2 * n + cell];
+    nudge_cell(f, L, dev, i, j, drho, dut, dup, c, (float)(ks * sin_t[i]));
+}
+
+// The direct form's nudge straight from the net output Y [H][W][CO] (scaled by sc) and the last
+// convolution's nparts partial sums of sin(theta) Y_0: each block reduces the partials to the area
+// mean of drho itself, so neither an outputs pass nor a separate reduction runs.
+__global__ void nudge_direct_kernel(float2 *f, const Layout L, const float *dev, const float *Y, int CO, float3 sc,
+                                    const double *part0, int nparts, double wsum, const VelN c,
+                                    const double *sin_t, double ks)
+{
+    __shared__ double red[128];
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) t += part0[b];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int k = 64; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    const double mean = red[0] * (double)sc.x / wsum;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= L.np) return;
+    const size_t cell = (size_t)i * L.np + j;
+    const float drho = (float)((double)Y[cell * CO] * (double)sc.x - mean);
+    const float dut = (float)((double)Y[cell * CO + 1] * (double)sc.y);
+    const float dup = (float)((double)Y[cell * CO + 2] * (double)sc.z);
+    nudge_cell(f, L, dev, i, j, drho, dut, dup, c, (float)(ks * sin_t[i]));
+}
+
 template <int CI, int CO>
 void conv_launch(const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias, float *Yf,
-                 __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s)
+                 __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s, double *part0 = nullptr,
+                 const double *sin_t = nullptr)
 {
     dim3 grid((Wp - 2 + CONV_PIX - 1) / CONV_PIX, Hp - 2);
-    conv3x3_kernel<CI, CO><<<grid, 128, 0, s>>>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu);
+    conv3x3_kernel<CI, CO><<<grid, 128, 0, s>>>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu, part0, sin_t);
 }
 
 template <int CI, int CO>
@@ -941,12 +991,15 @@ void wgrad_launch(const __nv_bfloat16 *dY, const __nv_bfloat16 *Xp, int H, int W
 // ---- the network ----------------------------------------------------------------------
 // Layer l: CI_l -> CO_l; padded channel counts: input 16 (4 used), hidden 32, output 8 (3 used).
 void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
-             float *Yf, __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s)
+             float *Yf, __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s, double *part0,
+             const double *sin_t)
 {
     if (layer == 0) conv_launch<LC_CIN, LC_HID>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu, s);
     else if (layer < LC_LAYERS - 1) conv_launch<LC_HID, LC_HID>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu, s);
-    else conv_launch<LC_HID, LC_COUT>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu, s);
+    else conv_launch<LC_HID, LC_COUT>(Xp, Hp, Wp, Wt, bias, Yf, Yb, Ypad, relu, s, part0, sin_t);
 }
+
+int lc_conv_ctas(int H, int W) { return ((W + CONV_PIX - 1) / CONV_PIX) * H; }
 
 // backward-data convolution of layer l >= 1: input dP [H+4][W+4][COp2], output dXp [H+2][W+2][CI_l]
 void lc_conv_bwd(int layer, const __nv_bfloat16 *dP, int H, int W, const __nv_bfloat16 *Wb, float *dXp, cudaStream_t s)
@@ -1159,6 +1212,18 @@ void lc_nudge(float2 *f, const Layout &L, const float *dev, const double *delta,
         for (int b = 0; b < 4; ++b) cn.w[4 * a + b] = (float)(c.w[a] * c.w[b]);
     dim3 grid((L.np + 127) / 128, L.nt);
     nudge_kernel<<<grid, 128, 0, s>>>(f, L, dev, delta, mean, wsum, cn, sin_t, ks);
+}
+
+void lc_nudge_direct(float2 *f, const Layout &L, const float *dev, const float *Y, int CO, float3 scale,
+                     const double *part0, int nparts, double wsum, const VelD &c, const double *sin_t, double ks,
+                     cudaStream_t s)
+{
+    VelN cn;
+    for (int a = 0; a < 4; ++a) cn.v[a] = (float)c.v[a];
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) cn.w[4 * a + b] = (float)(c.w[a] * c.w[b]);
+    dim3 grid((L.np + 127) / 128, L.nt);
+    nudge_direct_kernel<<<grid, 128, 0, s>>>(f, L, dev, Y, CO, scale, part0, nparts, wsum, cn, sin_t, ks);
 }
 
 }  // namespace vk

@@ -30,6 +30,7 @@ struct vlbm_lc {
     __nv_bfloat16 *d_xp[LC_LAYERS] = {}, *d_z[LC_LAYERS] = {};
     float *d_y = nullptr, *d_dy = nullptr, *d_dxp = nullptr, *d_dx = nullptr;
     float *d_dev = nullptr;      // the network's moment deviations (rho - 1, u^theta, u^phi, T - 1) [4][H][W]
+    double *d_cpart = nullptr;   // direct-form correction: the last layer's per-CTA sums of sin(theta) output 0
     __nv_bfloat16 *d_dp = nullptr, *d_dpre = nullptr;
     float *d_wpart = nullptr, *d_bpart = nullptr, *d_g9 = nullptr;
     double wsum = 0.0;
@@ -94,7 +95,8 @@ int refresh_bf16(vlbm_lc_t *n)
 
 // forward pass on the moment deviations dev ([4][H][W] device, FP32), on stream s; output in d_y.
 // keep: also store each hidden layer's unpadded activations (d_z) for the backward pass.
-int forward(vlbm_lc_t *n, const float *dev, cudaStream_t s, bool keep = true)
+// part0: the last layer's per-CTA partial sums of sin(theta) times output 0 (optional)
+int forward(vlbm_lc_t *n, const float *dev, cudaStream_t s, bool keep = true, double *part0 = nullptr)
 {
     const int H = n->H, W = n->W, HW = H * W;
     LcInScale is;
@@ -106,7 +108,8 @@ int forward(vlbm_lc_t *n, const float *dev, cudaStream_t s, bool keep = true)
     for (int l = 0; l < LC_LAYERS; ++l) {
         const bool last = (l == LC_LAYERS - 1);
         lc_conv(l, n->d_xp[l], H + 2, W + 2, n->d_wf[l], n->d_w + n->boff[l], last ? n->d_y : nullptr,
-                (last || !keep) ? nullptr : n->d_z[l], last ? nullptr : n->d_xp[l + 1], last ? 0 : 1, s);
+                (last || !keep) ? nullptr : n->d_z[l], last ? nullptr : n->d_xp[l + 1], last ? 0 : 1, s,
+                last ? part0 : nullptr, n->d_sin);
     }
     LCK(n, cudaGetLastError());
     return VLBM_OK;
@@ -192,6 +195,15 @@ int enqueue_correction(vlbm_lc_t *n, vlbm_t *h, cudaStream_t s)
 {
     lc_moments((const float2 *)h->F, h->L, h->vd, h->rho_ref, h->d_sin_t, h->kscale, n->d_dev, s);
     int rc;
+    if (n->form == VLBM_LC_DIRECT) {
+        // the output scaling and the area mean of drho ride on the last convolution and the nudge
+        if ((rc = forward(n, n->d_dev, s, false, n->d_cpart))) return rc;
+        const float3 sc = make_float3(n->out_scale[0], n->out_scale[1], n->out_scale[2]);
+        lc_nudge_direct((float2 *)h->F, h->L, n->d_dev, n->d_y, LC_COUT, sc, n->d_cpart, lc_conv_ctas(n->H, n->W),
+                        n->wsum, h->vd, n->d_sin, h->kscale, s);
+        LCK(n, cudaGetLastError());
+        return VLBM_OK;
+    }
     if ((rc = forward(n, n->d_dev, s, false))) return rc;
     enqueue_outputs(n, s);
     lc_nudge((float2 *)h->F, h->L, n->d_dev, n->d_out, n->d_scal + 1, n->wsum, h->vd, n->d_sin, h->kscale, s);
@@ -269,6 +281,7 @@ int vlbm_lc_create(int n_theta, int n_phi, unsigned long long seed, vlbm_lc_t **
     A(&n->d_cos, (size_t)n_theta);
     A(&n->d_in, 4 * HW);
     A(&n->d_dev, 4 * HW);
+    A(&n->d_cpart, (size_t)lc_conv_ctas(n_theta, n_phi));
     A(&n->d_tg, 3 * HW);
     A(&n->d_out, 3 * HW);
     A(&n->d_part, HW / 256 + 2);

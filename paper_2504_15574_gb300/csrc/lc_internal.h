@@ -26,8 +26,12 @@ struct LcInScale { float inv[LC_NSCALE]; };
 
 // Layer `layer` on the padded input Xp: FP32 pre-activations Yf, BF16 (ReLU) outputs Yb
 // [H][W][CO] and / or the next layer's padded input Ypad [H+2][W+2][CO] (any may be NULL).
+// part0 (last layer only; optional): per CTA of the launch (lc_conv_ctas of them) the sum over its
+// pixels of sin_t[row] times output 0.
 void lc_conv(int layer, const __nv_bfloat16 *Xp, int Hp, int Wp, const __nv_bfloat16 *Wt, const float *bias,
-             float *Yf, __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s);
+             float *Yf, __nv_bfloat16 *Yb, __nv_bfloat16 *Ypad, int relu, cudaStream_t s,
+             double *part0 = nullptr, const double *sin_t = nullptr);
+int lc_conv_ctas(int H, int W);
 void lc_conv_bwd(int layer, const __nv_bfloat16 *dP, int H, int W, const __nv_bfloat16 *Wb, float *dXp, cudaStream_t s);
 void lc_wgrad(int layer, const __nv_bfloat16 *dPre, const __nv_bfloat16 *Xp, int H, int W, float *part, float *partb,
               cudaStream_t s);
@@ -57,6 +61,11 @@ void lc_outputs(const float *Y, int CO, int H, int W, float3 scale, const double
                 double *mean, cudaStream_t s);
 void lc_nudge(float2 *f, const Layout &L, const float *dev, const double *delta, const double *mean, double wsum,
               const VelD &c, const double *sin_t, double ks, cudaStream_t s);
+// The direct form's nudge from the net output Y [H][W][CO] (times scale) and the last layer's
+// nparts partial sums of sin(theta) output 0 (the area mean of drho is removed).
+void lc_nudge_direct(float2 *f, const Layout &L, const float *dev, const float *Y, int CO, float3 scale,
+                     const double *part0, int nparts, double wsum, const VelD &c, const double *sin_t, double ks,
+                     cudaStream_t s);
 // Stream-function output form: output 0 times s0 is a stream function psi on the H x W cell grid
 // of a sphere of radius R (dth = pi / H, dph = 2 pi / W), the correction its centred curl
 // (0, d_phi psi / (R sin theta), -d_theta psi / R), psi continued across a pole as a scalar.
