@@ -247,7 +247,8 @@ VLBM_API void vlbm_batch_destroy(vlbm_batch_t *b);
  * between) on a coarse grid, mapping the moments (rho, u^theta, u^phi, T) of a
  * coarse FP32 solver, cos(theta) and sin(theta) of each row, and undivided 6th
  * differences of rho, u^theta, u^phi and 4th differences of u^theta, u^phi along
- * theta and along phi (formed in FP64), to a correction (drho, du^theta, du^phi)
+ * theta and along phi (formed in FP32 on the deviations rho - 1, u, T - 1), to a
+ * correction (drho, du^theta, du^phi)
  * toward a finer run.  Padding and the differences follow the sphere: periodic in
  * phi; beyond a pole, the row on the opposite meridian with the velocity
  * components (and their differences, and sin(theta)) negated (Sec. 3.6, Eq.
