@@ -106,10 +106,12 @@ class Setup:
     With the polar filter, dt follows the theta spacing (0.25 dtheta / v_max, capped at
     tau) and a coarse step is `factor` fine steps.  Without it, dt follows the pole
     rows (clamped rule, ~ 1 / (n_theta n_phi)) and a coarse step is `substeps` fine
-    steps (factor^2 for equal aspect ratios)."""
+    steps (factor^2 for equal aspect ratios).  tile_rows: the stage tile height of the
+    coarse and plain solvers (4 or 8; 0: the library's default)."""
 
-    def __init__(self, coarse=(128, 256), factor=4, tau=2e-3, polar_filter=True):
+    def __init__(self, coarse=(128, 256), factor=4, tau=2e-3, polar_filter=True, tile_rows=0):
         self.coarse = tuple(coarse)
+        self.tile_rows = int(tile_rows)
         self.factor = int(factor)
         self.fine = (self.coarse[0] * factor, self.coarse[1] * factor)
         self.tau = float(tau)
@@ -125,7 +127,7 @@ class Setup:
 
     def coarse_solver(self):
         return vlbm.Solver(*self.coarse, self.tau, self.dt_c, precision="fp32", polar_filter=self.polar_filter,
-                           guard=False)
+                           guard=False, tile_rows=self.tile_rows)
 
     def fine_batch(self, seeds):
         b = vlbm.Batch([self.fine] * len(seeds), self.tau, self.dt_f, polar_filter=self.polar_filter, guard=False)
@@ -384,7 +386,8 @@ def plain_runs_at(setup: Setup, seeds, n_steps, grids, spinup=20, start="analyti
         dt = setup.dt_c / sub
         ev, er, el = [], [], 0.0
         for k, sd in enumerate(seeds):
-            s = vlbm.Solver(*g, setup.tau, dt, precision="fp32", polar_filter=setup.polar_filter, guard=False)
+            s = vlbm.Solver(*g, setup.tau, dt, precision="fp32", polar_filter=setup.polar_filter, guard=False,
+                            tile_rows=setup.tile_rows)
             if start == "fine":
                 s.set_populations(downsample_populations(fstart[k], setup.factor // m))
             else:
@@ -423,6 +426,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--coarse", type=int, nargs=2, default=[128, 256])
     ap.add_argument("--polar-filter", action="store_true", help="filter on (dt by the theta spacing)")
+    ap.add_argument("--tile-rows", type=int, choices=[0, 4, 8], default=0,
+                    help="stage tile height of the coarse and plain solvers (0: the library's default, 8)")
     ap.add_argument("--targets", choices=["drift", "one-step"], default="drift")
     ap.add_argument("--train-seeds", type=int, default=32)
     ap.add_argument("--windows", type=int, default=16, help="drift targets: restart windows per seed")
@@ -446,7 +451,7 @@ def main(argv=None):
     ap.add_argument("--timing-steps", type=int, default=0,
                     help="only time this many corrected coarse steps of an untrained network (no data, no training)")
     a = ap.parse_args(argv)
-    setup = Setup(coarse=a.coarse, polar_filter=a.polar_filter)
+    setup = Setup(coarse=a.coarse, polar_filter=a.polar_filter, tile_rows=a.tile_rows)
     if a.timing_steps:
         net = vlbm.LearnedCorrection(*setup.coarse, seed=1, form=a.form)
         cs = setup.coarse_solver()
