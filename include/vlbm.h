@@ -315,8 +315,10 @@ VLBM_API int vlbm_lc_apply(vlbm_lc_t *lc, vlbm_t *h);
 /* Learned-coarse rollout: `steps` times (one RK3 step of h, then the correction of
  * vlbm_lc_apply), enqueued on the solver's stream as a captured CUDA graph (built on
  * the first call for this solver; rebuilt after vlbm_lc_set_scales,
- * vlbm_lc_set_output_form or for another solver) with no host synchronisation between steps; returns after the last step
- * with the solver's status (vlbm_sync).  h must be FP32 D2Q16 on the network's grid. */
+ * vlbm_lc_set_output_form, for another solver, and once the solver's step has new launch
+ * parameters: a vlbm_init_moments / vlbm_set_populations whose state changes the FP32 reference
+ * density, vlbm_set_wait_limit) with no host synchronisation between steps; returns after the
+ * last step with the solver's status (vlbm_sync).  h must be FP32 D2Q16 on the network's grid. */
 VLBM_API int vlbm_lc_rollout(vlbm_lc_t *lc, vlbm_t *h, int steps);
 VLBM_API const char *vlbm_lc_last_error(const vlbm_lc_t *lc);
 VLBM_API void vlbm_lc_destroy(vlbm_lc_t *lc);

@@ -49,6 +49,7 @@ struct vlbm_lc {
     std::vector<void *> bufs;
     cudaGraphExec_t g_exec = nullptr;   // vlbm_lc_rollout: one corrected step of solver g_solver
     vlbm_t *g_solver = nullptr;
+    unsigned long long g_gen = 0;       // the solver's step generation when g_exec was captured
 };
 
 namespace {
@@ -451,7 +452,9 @@ int vlbm_lc_rollout(vlbm_lc_t *n, vlbm_t *h, int steps)
     if (steps < 0) return lfail(n, VLBM_ERR_ARG, "negative step count");
     if (steps == 0) return VLBM_OK;
     if (!h->d_row) return lfail(n, VLBM_ERR_ARG, "FP32 state not initialised");
-    if (n->g_solver != h && n->g_exec) {
+    // the captured step holds the solver's launch parameters (its FP32 reference density among
+    // them): rebuild for another solver or once the solver has renewed them
+    if (n->g_exec && (n->g_solver != h || n->g_gen != h->step_gen)) {
         cudaGraphExecDestroy(n->g_exec);
         n->g_exec = nullptr;
     }
@@ -471,6 +474,7 @@ int vlbm_lc_rollout(vlbm_lc_t *n, vlbm_t *h, int steps)
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return lfail(n, VLBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
         n->g_solver = h;
+        n->g_gen = h->step_gen;
     }
     for (int q = 0; q < steps; ++q) LCK(n, cudaGraphLaunch(n->g_exec, h->stream));
     solver_count_steps(h, steps);

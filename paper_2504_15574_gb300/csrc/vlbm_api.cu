@@ -7,6 +7,7 @@
 // FP32 path, and enqueues steps as CUDA graphs on the handle's stream.
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -534,11 +535,17 @@ int build_graph(vlbm_t *h, int nsteps, cudaGraphExec_t *exec)
     return VLBM_OK;
 }
 
+// Generations of the captured step: unique over the process, so that a graph holding a solver's
+// step (the learned correction's rollout) can tell a rebuilt step, or another solver at the same
+// address, from the one it captured.
+std::atomic<unsigned long long> g_step_generation{0};
+
 void drop_graphs(vlbm_t *h)
 {
     if (h->g1) cudaGraphExecDestroy(h->g1);
     if (h->g16) cudaGraphExecDestroy(h->g16);
     h->g1 = h->g16 = nullptr;
+    h->step_gen = ++g_step_generation;
 }
 
 // After the populations changed from outside a step: ghosts, counters, mass0.
@@ -619,6 +626,7 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     if (o.scheme < VLBM_WENO5 || o.scheme > VLBM_U3) return fail(nullptr, VLBM_ERR_ARG, "unknown advection scheme");
 
     vlbm_t *h = new vlbm_t();
+    h->step_gen = ++g_step_generation;
     h->nt = n_theta;
     h->np = n_phi;
     h->prec = o.precision;

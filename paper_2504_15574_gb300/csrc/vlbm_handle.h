@@ -50,6 +50,9 @@ struct vlbm {
     CUtensorMap tmF{}, tmA{}, tmB{};      // FP32 path: box maps (stage inputs)
     CUtensorMap tmFc{}, tmAc{}, tmBc{};   // FP32 path: tile-core maps (stage outputs, F prefetch)
     cudaGraphExec_t g1 = nullptr, g16 = nullptr;
+    // generation of the step's launch parameters: renewed whenever g1 / g16 are dropped (new FP32
+    // reference density, wait limit), so graphs captured elsewhere from this step know to rebuild
+    unsigned long long step_gen = 0;
     vk::VelD vd{};
     vk::VelC vc{};     // FP32 path: packed velocity constants
     vk::VelC3 vc3{};   // FP32 path, D2Q9: the same for the five pairs

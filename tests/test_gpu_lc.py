@@ -190,6 +190,41 @@ def test_rollout_equals_stepping_and_applying_bitwise(V):
     b.close()
 
 
+def test_rollout_follows_a_new_state_of_the_same_solver(V):
+    """The captured corrected step holds the solver's launch parameters, the FP32 reference
+    density among them.  A new state of another mean density on the same solver (as the
+    learned-coarse evaluation does between seeds) must be rolled out with its own reference
+    density: equal, bit for bit, to stepping and applying from that state."""
+    H, W = 16, 32
+    net = V.LearnedCorrection(H, W, seed=4, in_scale=IN_SCALE, out_scale=OUT_SCALE)
+    p = net.get_weights()
+    p[-3:] = [0.5, 0.3, -0.2]
+    net.set_weights(p)
+    a = V.Solver(H, W, 2e-3, 1e-4, precision="fp32", guard=False)
+    b = V.Solver(H, W, 2e-3, 1e-4, precision="fp32", guard=False)
+    rho, ut, up, _ = inputs.gaussian_vortices(H, W, run=6)
+    a.init_moments(rho, ut, up)
+    net.rollout(a, 3)
+    for s in (a, b):
+        s.init_moments(1.02 * rho, ut, up)
+    net.rollout(a, 4)
+    for _ in range(4):
+        b.step(1)
+        net.apply(b)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    # the same through vlbm_set_populations, back at the first mean density
+    f = b.get_populations() / 1.02
+    a.set_populations(f)
+    b.set_populations(f)
+    net.rollout(a, 2)
+    for _ in range(2):
+        b.step(1)
+        net.apply(b)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    a.close()
+    b.close()
+
+
 def test_trained_correction_beats_the_plain_coarse_run_on_held_out_seeds(V):
     """Small learned-coarse experiment (coarse 32 x 64 from fine 128 x 256, clamped dt, 16
     fine steps per coarse step): trained on the per-step drift of the coarse run away from
