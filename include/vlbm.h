@@ -85,7 +85,8 @@ typedef struct vlbm_options {
     void *stream;       /* cudaStream_t to run on, or NULL for a stream the handle creates */
     double rho_ref;     /* VLBM_FP32 only: reference density of the deviation storage;
                            <= 0 means the area-weighted mean of the initial rho; default 0 */
-    int tile_rows;      /* VLBM_FP32 only: rows per stage tile, 4 or 8 (0: 8); tiles are 32 columns wide */
+    int tile_rows;      /* VLBM_FP32 only: rows per stage tile, 4 or 8 (0: 8; other values: VLBM_ERR_ARG);
+                           tiles are 32 columns wide */
     int scheme;         /* VLBM_WENO5 (default), VLBM_U1, VLBM_U2 or VLBM_U3, in theta and phi */
     int komissarov;     /* 1: theta flux in the Komissarov form of Eqs. (Komissarov_scheme),
                            (Komissarov_sin_cos): -d/dcos(theta) of v_theta sin(theta_{s+-1/2}) times

@@ -624,6 +624,8 @@ int vlbm_create(int n_theta, int n_phi, int velocity_set, double tau, double dt,
     if (o.precision != VLBM_FP64 && o.precision != VLBM_FP32) return fail(nullptr, VLBM_ERR_ARG, "bad precision");
     if (!(o.weno_eps > 0.0) || !(o.radius > 0.0)) return fail(nullptr, VLBM_ERR_ARG, "weno_eps and radius must be > 0");
     if (o.scheme < VLBM_WENO5 || o.scheme > VLBM_U3) return fail(nullptr, VLBM_ERR_ARG, "unknown advection scheme");
+    if (o.tile_rows != 0 && o.tile_rows != 4 && o.tile_rows != 8)
+        return fail(nullptr, VLBM_ERR_ARG, "tile_rows must be 0, 4 or 8");
 
     vlbm_t *h = new vlbm_t();
     h->step_gen = ++g_step_generation;

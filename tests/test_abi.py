@@ -73,6 +73,18 @@ def test_create_rejects_bad_arguments_before_the_gpu(lib, args, code):
     assert vlbm.vlbm_last_error()
 
 
+@pytest.mark.parametrize("tile_rows", [1, 5, 16, -4])
+def test_create_rejects_a_tile_height_other_than_4_or_8(lib, tile_rows):
+    from paper_2504_15574_gb300 import vlbm
+    o = vlbm.vlbm_default_options()
+    o.precision = vlbm.VLBM_FP32
+    o.tile_rows = tile_rows
+    with pytest.raises(vlbm.VlbmError) as e:
+        vlbm.vlbm_create(32, 64, 4, 0.1, 1e-3, o)
+    assert e.value.code == vlbm.VLBM_ERR_ARG
+    assert "tile_rows" in vlbm.vlbm_last_error()
+
+
 @pytest.mark.parametrize("velocity_set", ["d2q16", "d2q9"])
 def test_batch_refuses_weno_with_komissarov_before_the_gpu(lib, velocity_set):
     # single runs take WENO-5 with the Komissarov theta flux on both paths; batches
