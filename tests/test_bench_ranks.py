@@ -1,7 +1,9 @@
 """The multi-rank host logic of bench.py on CPU (gloo, world size 2): every rank takes rank 0's
 decision on the number of timed repeats, the reported times are the max over ranks repeat by
 repeat, and the value counts every rank's replica; under torchrun the reference arm runs on
-rank 0 only (the other ranks exit at once, printing nothing)."""
+rank 0 only (the other ranks exit at once, printing nothing), and rank 0's reference line carries
+the bench line's keys with the warm-up and timed steps it ran."""
+import json
 import os
 import socket
 import subprocess
@@ -78,3 +80,26 @@ def test_reference_arm_runs_on_rank0_only():
                         "--steps", "2", "--warmup", "1"], capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_line_on_rank0():
+    """The reference arm (the oracle on the host cores) prints one JSON line with the keys of the
+    bench line, the warm-up and timed steps it ran, and its cpu_baseline and e2e records."""
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "2"], capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["unit"] == "MLUPS" and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "2 of the 2 requested warm-up steps" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["ms_per_step"] == pytest.approx(1024 * 2048 / d["value"] / 1e3, rel=1e-9)
